@@ -1,0 +1,386 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test checks the oracle (``oracle.gb``) against a fact fixed by the paper,
+by mathematics or by an independent computation: closed forms, invariances,
+special cases that reduce to a textbook result, an independent brute-force
+time-domain simulation, and central finite differences.  A plausible mistake
+anywhere in the oracle (a dropped term, a wrong sign, a transposed operand, a
+wrong index or scale) fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import brute, gb
+from paper_2307_03763_gb300 import workloads as wk
+from tests import _data
+
+YEAR = gb.YEAR
+T2 = 2 * YEAR
+
+
+def _theta(rng, f0=1.5e-3, fdot=1e-17, A=1e-22):
+    return wk.source(f0, fdot, A, rng)
+
+
+# --------------------------------------------------------------------------
+# geometry (readings R3, R4)
+# --------------------------------------------------------------------------
+
+def test_orbit_is_rigid_equal_arm_triangle():
+    t = torch.linspace(0, YEAR, 257, dtype=torch.float64)
+    x = gb.spacecraft_positions(t)
+    for i, j in ((0, 1), (1, 2), (2, 0)):
+        d = torch.linalg.vector_norm(x[:, j] - x[:, i], dim=-1)
+        assert torch.allclose(d, torch.full_like(d, gb.ARM_L), rtol=1e-12, atol=0)
+    # guiding centre on a 1 AU circle in the ecliptic
+    centre = x.mean(1)
+    a = 2 * math.pi * t / YEAR
+    ref = torch.stack([gb.AU * torch.cos(a), gb.AU * torch.sin(a), 0 * a], -1)
+    assert (centre - ref).abs().max() < 1e-3 * gb.ARM_L * 1e-6
+    # the plane of the triangle is inclined by 60 degrees to the ecliptic
+    nrm = torch.linalg.cross(x[:, 1] - x[:, 0], x[:, 2] - x[:, 0])
+    cosang = (nrm[:, 2] / torch.linalg.vector_norm(nrm, dim=-1)).abs()
+    assert torch.allclose(cosang, torch.full_like(cosang, 0.5), atol=1e-9)
+
+
+def test_polarisation_tensor_is_transverse_traceless():
+    rng = np.random.default_rng(0)
+    th = torch.tensor(np.stack([_theta(rng) for _ in range(16)]))
+    f0, fdot, beta, lam, A, iota, psi, phi0 = th.unbind(-1)
+    k = gb.propagation_direction(beta, lam)
+    H = gb.polarisation_tensor(torch.ones_like(A), iota, psi, beta, lam)
+    assert torch.allclose(H, H.transpose(1, 2))
+    assert torch.einsum("bii->b", H).abs().max() < 1e-14
+    assert torch.einsum("bij,bj->bi", H, k.to(gb.C128)).abs().max() < 1e-14
+    # |H|^2 = A+^2 |E+|^2 + Ax^2 |Ex|^2 with |E+|^2 = |Ex|^2 = 2
+    Ap = 1 + torch.cos(iota) ** 2
+    Ax = -2 * torch.cos(iota)
+    norm2 = (H.abs() ** 2).sum((1, 2))
+    assert torch.allclose(norm2, 2 * (Ap ** 2 + Ax ** 2), rtol=1e-13)
+
+
+def test_transfer_frequency_matches_paper_threshold():
+    # Sec. II: the T channel is dropped below f*/2 = 1/(4 pi L) ~ 9.55 mHz (the
+    # printed 9.55 mHz corresponds to c ~ 3e8 m/s; see tests/golden/constants.txt)
+    golden = dict(l.split("=") for l in open(_golden("constants.txt")).read().split()
+                  if "=" in l)
+    half = gb.transfer_frequency(2.5e9) / 2
+    assert abs(half - float(golden["fstar_half_Hz"])) / half < 2e-3
+    assert abs(half - 299792458.0 / (4 * math.pi * 2.5e9)) < 1e-18
+
+
+def _golden(name):
+    import os
+    return os.path.join(os.path.dirname(__file__), "golden", name)
+
+
+# --------------------------------------------------------------------------
+# carrier bin (R7) and the DFT / heterodyne (R8)
+# --------------------------------------------------------------------------
+
+def test_carrier_bin_rule():
+    f0 = torch.tensor([100.49999999, 100.5, 100.2, 99.7], dtype=torch.float64)
+    fd = torch.tensor([0.0, 0.0, 0.8, -0.8], dtype=torch.float64)
+    q, delta = gb.carrier_bin(f0, fd, 1.0)
+    assert q.tolist() == [100, 101, 101, 99]
+    assert torch.allclose(delta, f0 - q.to(torch.float64))
+    rng = np.random.default_rng(3)
+    f0 = torch.tensor(rng.uniform(1e-4, 2e-2, 1000))
+    fd = torch.tensor(rng.uniform(-1e-15, 1e-13, 1000))
+    q, _ = gb.carrier_bin(f0, fd, T2)
+    mid = (f0 + 0.5 * fd * T2) * T2
+    assert ((q.to(torch.float64) - mid).abs() <= 0.5 + 1e-6).all()
+
+
+@pytest.mark.parametrize("delta", [0.0, 0.3, -0.45])
+def test_static_detector_reduces_to_dirichlet_kernel(delta):
+    # frozen constellation, fdot = 0: the slow part is s_0 exp(2 pi i delta n/N),
+    # whose DFT is the textbook Dirichlet kernel
+    rng = np.random.default_rng(4)
+    N, T = 64, T2
+    q0 = round(2e-3 * T)
+    th = _theta(rng, f0=(q0 + delta) / T, fdot=0.0)
+    q, sA, sE = gb.slow_part(torch.tensor(th[None]), N, T, static=True)
+    delta = th[0] * T - q0          # the exact offset of the rounded f0
+    n = torch.arange(N, dtype=torch.float64)
+    for s in (sA[0], sE[0]):
+        assert torch.allclose(s, s[0] * torch.exp(2j * math.pi * delta * n / N), rtol=1e-11, atol=0)
+    _, hA, _ = gb.template(torch.tensor(th[None]), N, T, static=True)
+    m = torch.arange(-(N // 2), N // 2, dtype=torch.float64)
+    s0 = sA[0, 0]
+    if delta == 0.0:
+        ref = torch.zeros(N, dtype=torch.complex128)
+        ref[N // 2] = N * s0
+    else:
+        # sum_n e^{i x n} = e^{i x (N-1)/2} sin(N x/2)/sin(x/2), x = 2 pi (delta - m)/N
+        x = math.pi * (delta - m)
+        ref = s0 * torch.exp(1j * x * (N - 1) / N) * torch.sin(x) / torch.sin(x / N)
+    ref = ref * T / (2 * N)
+    assert (hA[0] - ref).abs().max() <= 1e-11 * ref.abs().max()
+    assert int(q[0]) == q0
+
+
+def test_parseval_on_slow_part():
+    rng = np.random.default_rng(5)
+    th = torch.tensor(np.stack([_theta(rng) for _ in range(8)]))
+    _, sA, sE = gb.slow_part(th, 128, T2)
+    for s in (sA, sE):
+        S = gb.dft_centered(s)
+        assert torch.allclose((s.abs() ** 2).sum(-1), (S.abs() ** 2).sum(-1) / 128, rtol=1e-12)
+
+
+def test_dft_matches_library_fft():
+    rng = np.random.default_rng(6)
+    s = torch.tensor(rng.standard_normal((3, 256)) + 1j * rng.standard_normal((3, 256)))
+    S = gb.dft_centered(s)
+    ref = torch.fft.fftshift(torch.fft.fft(s, dim=-1), dim=-1)
+    assert (S - ref).abs().max() < 1e-11 * ref.abs().max()
+
+
+# --------------------------------------------------------------------------
+# invariances of the template (R4, R5)
+# --------------------------------------------------------------------------
+
+def test_template_linear_in_amplitude():
+    rng = np.random.default_rng(7)
+    th = np.stack([_theta(rng) for _ in range(4)])
+    q1, a1, e1 = gb.template(torch.tensor(th), 128, T2)
+    th2 = th.copy()
+    th2[:, 4] *= 3.7
+    q2, a2, e2 = gb.template(torch.tensor(th2), 128, T2)
+    assert torch.equal(q1, q2)
+    assert torch.allclose(a2, 3.7 * a1, rtol=1e-13, atol=0)
+    assert torch.allclose(e2, 3.7 * e1, rtol=1e-13, atol=0)
+
+
+def test_polarisation_angle_symmetries():
+    rng = np.random.default_rng(8)
+    th = np.stack([_theta(rng) for _ in range(4)])
+    _, a, e = gb.template(torch.tensor(th), 128, T2)
+    thp = th.copy()
+    thp[:, 6] += math.pi
+    _, ap, ep = gb.template(torch.tensor(thp), 128, T2)
+    thh = th.copy()
+    thh[:, 6] += math.pi / 2
+    _, ah, eh = gb.template(torch.tensor(thh), 128, T2)
+    scale = a.abs().max()
+    assert (ap - a).abs().max() < 1e-12 * scale and (ep - e).abs().max() < 1e-12 * scale
+    assert (ah + a).abs().max() < 1e-12 * scale and (eh + e).abs().max() < 1e-12 * scale
+
+
+def test_initial_phase_is_a_global_phase():
+    rng = np.random.default_rng(9)
+    th = np.stack([_theta(rng) for _ in range(4)])
+    _, a, e = gb.template(torch.tensor(th), 128, T2)
+    ths = th.copy()
+    ths[:, 7] += 0.731
+    _, a2, e2 = gb.template(torch.tensor(ths), 128, T2)
+    ph = np.exp(0.731j)
+    scale = a.abs().max()
+    assert (a2 - ph * a).abs().max() < 1e-12 * scale
+    assert (e2 - ph * e).abs().max() < 1e-12 * scale
+
+
+def test_sky_position_of_the_antipode_is_not_a_symmetry():
+    # guards against a response that ignores k (e.g. a dropped Doppler term)
+    rng = np.random.default_rng(10)
+    th = _theta(rng)
+    th2 = th.copy()
+    th2[2], th2[3] = -th[2], th[3] + math.pi
+    _, a, _ = gb.template(torch.tensor(th[None]), 128, T2)
+    _, b, _ = gb.template(torch.tensor(th2[None]), 128, T2)
+    assert (a - b).abs().max() > 0.1 * a.abs().max()
+
+
+# --------------------------------------------------------------------------
+# physics: fast/slow template vs brute-force time-domain simulation
+# --------------------------------------------------------------------------
+
+def _brute_vs_template(f0, fdot, dt, N, T, seed):
+    rng = np.random.default_rng(seed)
+    th = _theta(rng, f0=f0, fdot=fdot)
+    q, hA, hE = gb.template(torch.tensor(th[None]), N, T)
+    q = int(q[0])
+    bA, bE = brute.brute_force_spectrum(th, T, dt, np.arange(q - N // 2, q + N // 2))
+    scale = max(np.abs(bA).max(), np.abs(bE).max())
+    return max(np.abs(hA[0].numpy() - bA).max(), np.abs(hE[0].numpy() - bE).max()) / scale
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("f0_mhz,N,dt", [(1.5, 64, 60.0), (10.0, 256, 30.0)])
+def test_fast_slow_matches_brute_force_periodic(f0_mhz, N, dt):
+    # T = 1 yr, carrier exactly on a bin, fdot = 0: the slow part is periodic
+    # over T, so the N-sample DFT is exact and the only difference left is the
+    # physics approximation of the fast/slow split (emitter at t instead of
+    # t - L/c, rigid arm directions): O(v L / c^2 / L) ~ 1e-4.
+    T = YEAR
+    q = round(f0_mhz * 1e-3 * T)
+    err = _brute_vs_template(q / T, 0.0, dt, N, T, seed=11)
+    assert err < 1e-3, err
+
+
+@pytest.mark.slow
+def test_fast_slow_matches_brute_force_off_bin_with_chirp():
+    # delta = 0.3 bin and fdot != 0: the periodic extension of the slow part
+    # jumps at t = T, which costs O(1/N) of the peak with samples at n T/N
+    # (reading R8); measured 2.2e-2 at N = 128.  A sign error in delta, fdot
+    # or the heterodyne moves power by bins and fails by O(1).
+    T = YEAR
+    q = round(1.5e-3 * T)
+    err = _brute_vs_template((q + 0.3) / T, 1e-16, 60.0, 128, T, seed=12)
+    assert err < 5e-2, err
+
+
+# --------------------------------------------------------------------------
+# likelihood (Eqs. 2-3, 6-7; R9, R10)
+# --------------------------------------------------------------------------
+
+def _one_window(seed=13, N=128, shift=0):
+    wl = wk.tiny_window(seed=seed, n_cand=32, N=N)
+    k0, W, Nw, doff, coff, nc = wl.windows[0]
+    wl.windows[0] = (k0 + shift, W, Nw, doff, coff, nc)
+    dA, dE = _data.inject(wl)
+    return wl, dA, dE
+
+
+@pytest.mark.parametrize("shift", [0, 37, -100, 300])
+def test_loglik_equals_residual_norm(shift):
+    # Eq. 2 evaluated directly as -1/2 <d-h|d-h> over the window, with the
+    # template scattered onto the window grid (partly outside when shift != 0)
+    wl, dA, dE = _one_window(shift=shift)
+    k0, W, N, doff, coff, nc = wl.windows[0]
+    logL, dh, hh = gb.loglik(wl.windows, dA, dE, wl.w_A, wl.w_E, wl.theta, wl.T)
+    for b in range(0, nc, 7):
+        hA, hE = _data.template_on_window(wl.theta[b], k0, W, N, wl.T)
+        rA, rE = dA[doff:doff + W] - hA, dE[doff:doff + W] - hE
+        ref = -0.5 * (4 / wl.T) * (np.sum(wl.w_A * np.abs(rA) ** 2) + np.sum(wl.w_E * np.abs(rE) ** 2))
+        assert abs(float(logL[b]) - ref) <= 1e-10 * abs(ref)
+
+
+def test_inner_products_scale_with_amplitude():
+    wl, dA, dE = _one_window()
+    th = wl.theta.copy()
+    _, dh1, hh1 = gb.loglik(wl.windows, dA, dE, wl.w_A, wl.w_E, th, wl.T)
+    th[:, 4] *= 2.5
+    _, dh2, hh2 = gb.loglik(wl.windows, dA, dE, wl.w_A, wl.w_E, th, wl.T)
+    assert torch.allclose(dh2, 2.5 * dh1, rtol=1e-12)
+    assert torch.allclose(hh2, 6.25 * hh1, rtol=1e-12)
+    # Eq. 6: the SNR does not depend on A
+    assert torch.allclose(gb.snr(dh1, hh1), gb.snr(dh2, hh2), rtol=1e-12)
+
+
+def test_amplitude_max_maximises_loglik():
+    # Eq. 7: A_max is the stationary point of logL along A, where
+    # logL = <d|s'>^2 / (2 <s'|s'>) - <d|d>/2
+    wl, dA, dE = _one_window()
+    th = wl.theta[:4].copy()
+    win = [(wl.windows[0][0], wl.windows[0][1], wl.windows[0][2], 0, 0, 4)]
+    logL, dh, hh = gb.loglik(win, dA, dE, wl.w_A, wl.w_E, th, wl.T)
+    amax = gb.amplitude_max(torch.tensor(th[:, 4]), dh, hh)
+    th2 = th.copy()
+    th2[:, 4] = amax.numpy()
+    l2, dh2, hh2 = gb.loglik(win, dA, dE, wl.w_A, wl.w_E, th2, wl.T)
+    dd = -2 * (logL - dh + 0.5 * hh)
+    assert torch.allclose(l2, dh2 ** 2 / (2 * hh2) - dd / 2, rtol=1e-11)
+    for eps in (1e-3, -1e-3):
+        th3 = th2.copy()
+        th3[:, 4] *= 1 + eps
+        l3, _, _ = gb.loglik(win, dA, dE, wl.w_A, wl.w_E, th3, wl.T)
+        assert (l3 <= l2).all()
+
+
+def test_empty_window_and_disjoint_template():
+    wl, dA, dE = _one_window()
+    k0, W, N, doff, coff, nc = wl.windows[0]
+    win = [(k0 + 10 * N, W, N, doff, coff, nc)]            # template far outside
+    logL, dh, hh = gb.loglik(win, dA, dE, wl.w_A, wl.w_E, wl.theta, wl.T)
+    dd = (4 / wl.T) * (np.sum(wl.w_A * np.abs(dA) ** 2) + np.sum(wl.w_E * np.abs(dE) ** 2))
+    assert torch.all(dh == 0) and torch.all(hh == 0)
+    assert torch.allclose(logL, torch.full_like(logL, -dd / 2), rtol=1e-13)
+    win0 = [(k0, W, N, doff, coff, 0)]
+    logL0, _, _ = gb.loglik(win0, dA, dE, wl.w_A, wl.w_E, wl.theta, wl.T)
+    assert torch.all(logL0 == 0)
+
+
+def test_noise_only_inner_product_statistics():
+    # <n|n> over W bins and two channels is chi^2 with 4W degrees of freedom
+    # (mean 2 per channel and bin) when Re, Im ~ N(0, T S/4): pins the 4/T
+    # normalisation of R9 against the one-sided PSD convention of Eq. 3.
+    rng = np.random.default_rng(14)
+    T, W = T2, 4096
+    wins, _, _ = wk.layout([(round(2e-3 * T), W, W)], [0])
+    nA, nE, wA, wE = wk.noise_and_weights(wins, T, rng)
+    _, _, dd = gb.window_inner_products(wins[0][0], torch.tensor(nA), torch.tensor(nE),
+                                        torch.tensor(wA), torch.tensor(wE),
+                                        torch.zeros(0, dtype=torch.int64),
+                                        torch.zeros((0, 8), dtype=torch.complex128),
+                                        torch.zeros((0, 8), dtype=torch.complex128), T)
+    mean, sd = 4 * W, math.sqrt(8 * W)
+    assert abs(float(dd) - mean) < 5 * sd
+
+
+# --------------------------------------------------------------------------
+# gradient
+# --------------------------------------------------------------------------
+
+SCALES = None
+
+
+def _scales(T, A):
+    return np.array([1 / T, 1 / T ** 2, 1.0, 1.0, A, 1.0, 1.0, 1.0])
+
+
+def _fd_grad(win, dA, dE, wA, wE, th, T, rel=1e-3):
+    s = _scales(T, th[4])
+    g = np.zeros(8)
+    for i in range(8):
+        def D(h):
+            tp, tm = th.copy(), th.copy()
+            tp[i] += h
+            tm[i] -= h
+            lp = gb.loglik(win, dA, dE, wA, wE, tp[None], T)[0][0]
+            lm = gb.loglik(win, dA, dE, wA, wE, tm[None], T)[0][0]
+            return float(lp - lm) / (2 * h)
+        h = rel * s[i]
+        g[i] = (4 * D(h / 2) - D(h)) / 3      # Richardson
+    return g
+
+
+def test_gradient_matches_central_differences():
+    wl, dA, dE = _one_window(N=128)
+    k0, W, N, doff, _, _ = wl.windows[0]
+    win = [(k0, W, N, 0, 0, 1)]
+    rng = np.random.default_rng(15)
+    src = wl.sources[0][0]
+    for trial in range(3):
+        th = src.copy()
+        th[0] += rng.uniform(0.2, 0.6) / wl.T
+        th[2:4] += rng.uniform(-0.05, 0.05, 2)
+        th[5:8] += rng.uniform(-0.1, 0.1, 3)
+        th[4] *= 0.8
+        frac = ((th[0] + 0.5 * th[1] * wl.T) * wl.T) % 1.0
+        assert abs(frac - 0.5) > 0.01          # stay clear of a carrier-bin jump
+        _, g = gb.loglik_grad(win, dA, dE, wl.w_A, wl.w_E, th[None], wl.T)
+        gfd = _fd_grad(win, dA, dE, wl.w_A, wl.w_E, th, wl.T)
+        s = _scales(wl.T, th[4])
+        gn, gfn = g[0].numpy() * s, gfd * s
+        assert np.abs(gn - gfn).max() <= 1e-7 * np.abs(gn).sum(), (gn, gfn)
+
+
+def test_gradient_closed_forms_for_amplitude_and_phase():
+    # d logL/dA = (<d|h> - <h|h>)/A (h is linear in A);
+    # d logL/dphi0 = (4/T) sum w Im(d h*)  (h -> e^{i phi0} h, <h|h> fixed)
+    wl, dA, dE = _one_window()
+    k0, W, N, doff, _, _ = wl.windows[0]
+    th = wl.theta[:5]
+    win = [(k0, W, N, 0, 0, 5)]
+    _, dh, hh = gb.loglik(win, dA, dE, wl.w_A, wl.w_E, th, wl.T)
+    _, g = gb.loglik_grad(win, dA, dE, wl.w_A, wl.w_E, th, wl.T)
+    assert torch.allclose(g[:, 4], (dh - hh) / torch.tensor(th[:, 4]), rtol=1e-10)
+    for b in range(5):
+        hA, hE = _data.template_on_window(th[b], k0, W, N, wl.T)
+        ref = (4 / wl.T) * (np.sum(wl.w_A * (dA * hA.conj()).imag) + np.sum(wl.w_E * (dE * hE.conj()).imag))
+        assert abs(float(g[b, 7]) - ref) <= 1e-10 * abs(ref)
