@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Benchmark of the batched Galactic-binary likelihood path on GB300.
+
+One step = one 10,000-proposal posterior round on each of 16 frequency
+windows (N = 128 / 256 bins, T = 2 yr, one injected binary per window at SNR
+20-200, proposals from a Gaussian of 10x the Fisher width around it): the
+batched log-likelihood of all 160,000 proposals (one launch) followed by the
+16 independence Metropolis-Hastings chains built from them (one launch).
+
+Metric: GB logL evaluations per second (higher is better), for the mixed
+precision path (headline) and the plain FP64 path, with |dlogL| of the mixed
+path against FP64 stated, and seconds per 10k-sample posterior round.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own replica of the workload (different
+seed) on its own GPU with no collective on the data path (weak scaling); only
+the timing uses a barrier and a max over ranks.  Rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import math
+import os
+import shutil
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2307_03763_gb300 import workloads as wk  # noqa: E402
+
+METRIC = "GB logL evals/s (FP64 vs mixed, |dlogL| stated); s per 10k-sample posterior"
+UNIT = "evals/s"
+WORKLOAD = "posterior: 16 windows (N=128/256, f0 log-U[0.5,5] mHz), 10,000 proposals each, T=2 yr, dt=15 s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+# ---------------------------------------------------------------------------
+# workload construction (host; the template and its derivatives come from the
+# library's own waveform kernel)
+# ---------------------------------------------------------------------------
+
+def build_inputs(ctx, seed, dev):
+    wl = wk.posterior_windows(seed=seed)
+    T = wl.T
+    nwin = len(wl.windows)
+    src = np.array([wl.sources[w][0] for w in range(nwin)])     # A = 1
+
+    def templates(th):
+        """gb_waveform (fp64) of rows th for every window's N, scattered on its bins."""
+        outA = np.zeros((len(th), max(w[1] for w in wl.windows)), np.complex128)
+        outE = np.zeros_like(outA)
+        for w, (k0, W, N, doff, coff, nc) in enumerate(wl.windows):
+            rows = [i for i in range(len(th)) if i % nwin == w]
+            if not rows:
+                continue
+            hA, hE, q = ctx.waveform(torch.tensor(th[rows], device=dev), N, "fp64")
+            hA, hE, q = hA.cpu().numpy(), hE.cpu().numpy(), q.cpu().numpy()
+            for r, i in enumerate(rows):
+                j = q[r] - N // 2 + np.arange(N) - k0
+                ok = (j >= 0) & (j < W)
+                outA[i, j[ok]] = hA[r, ok]
+                outE[i, j[ok]] = hE[r, ok]
+        return outA, outE
+
+    def inner(aA, aE, bA, bE, w):
+        k0, W, N, doff, _, _ = wl.windows[w]
+        wa, we = wl.w_A[doff:doff + W], wl.w_E[doff:doff + W]
+        return (4.0 / T) * (np.sum(wa * (aA[:W] * bA[:W].conj()).real) + np.sum(we * (aE[:W] * bE[:W].conj()).real))
+
+    hA, hE = templates(src)
+    for w in range(nwin):
+        src[w, 4] = wl.meta["snr"][w] / math.sqrt(inner(hA[w], hE[w], hA[w], hE[w], w))
+    # Fisher matrix F_ij = <d_i h|d_j h> by central differences of the templates
+    scales = np.array([1 / T, 1 / T ** 2, 1, 1, 1, 1, 1, 1.0])
+    sig = np.zeros((nwin, 8))
+    J = []
+    for i in range(8):
+        step = 1e-4 * scales[i] * (src[:, 4] if i == 4 else 1.0)
+        tp, tm = src.copy(), src.copy()
+        tp[:, i] += step
+        tm[:, i] -= step
+        pA, pE = templates(tp)
+        mA, mE = templates(tm)
+        st = step if np.ndim(step) else np.full(nwin, step)
+        J.append(((pA - mA) / (2 * st[:, None]), (pE - mE) / (2 * st[:, None])))
+    for w in range(nwin):
+        F = np.array([[inner(J[i][0][w], J[i][1][w], J[j][0][w], J[j][1][w], w) for j in range(8)]
+                      for i in range(8)])
+        sig[w] = np.sqrt(np.abs(np.diag(np.linalg.pinv(F))))
+    # data = noise + injected sources
+    hA, hE = templates(src)
+    dA, dE = wl.noise_A.copy(), wl.noise_E.copy()
+    for w, (k0, W, N, doff, coff, nc) in enumerate(wl.windows):
+        dA[doff:doff + W] += hA[w, :W]
+        dE[doff:doff + W] += hE[w, :W]
+    rng = np.random.default_rng(wl.meta["proposal_seed"])
+    theta = np.empty((wl.n_cand, 8))
+    log_g = np.empty(wl.n_cand)
+    for w, (k0, W, N, doff, coff, nc) in enumerate(wl.windows):
+        theta[coff:coff + nc], log_g[coff:coff + nc] = wk.gaussian_proposals(src[w], 10 * sig[w], nc, rng)
+    return wl, dA, dE, theta, log_g
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.rows = []
+
+    def start(self):
+        exe = shutil.which("nvidia-smi")
+        if not exe:
+            return
+        self.proc = subprocess.Popen([exe, "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits", "-lms", "100"],
+                                     stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows if len(r) >= 8 for k in range(4)
+                          if r[4 + k].lower().startswith("active")})
+        power = [float(r[2]) for r in self.rows if len(r) >= 8 and r[2].replace(".", "").isdigit()]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work of the likelihood kernel (counted from the algorithm)
+# ---------------------------------------------------------------------------
+
+def flops_per_eval(N, f_hz, T):
+    """Floating-point operations of one evaluation (FMA = 2), mixed path.
+
+    Per sample (counted from the algorithm as the kernel states it, a
+    sincospi counted as 20): common double-word phase 108, three
+    per-spacecraft phase factors 93, f and a 4, three arms with their two
+    links 3 x (66 + 8 J), TDI, delay factor and the A/E projection 80; so
+    483 + 24 J.  FFT 2 x 5 N log2 N; window inner products 26 per bin.
+    J = 4 below 9.3 mHz (f/f* <= 0.489), 7 below 25.6 mHz.
+    """
+    xmax = f_hz / (299792458.0 / (2 * math.pi * 2.5e9))
+    J = 4 if xmax <= 0.489 else 7 if xmax <= 1.34 else 10
+    per_sample = 483 + 24 * J
+    return N * per_sample + 2 * 5 * N * math.log2(N) + 26 * N
+
+
+# ---------------------------------------------------------------------------
+
+def cpu_baseline(wl, dA, dE, theta, seconds=12.0):
+    """The FP64 oracle timed on this host's cores on a bounded sample."""
+    from oracle import gb as ogb
+    k0, W, N, doff, coff, nc = wl.windows[0]
+    n = 2000
+    win = [(k0, W, N, doff, 0, n)]
+    th = theta[coff:coff + n]
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        ogb.loglik(win, dA, dE, wl.w_A, wl.w_E, th, wl.T)
+        done += n
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": "window 0 (N=%d) of the posterior workload, %d proposals, repeated for %.0f s" % (N, n, dt)}
+
+
+def run_reference(args, rank, world):
+    """The oracle as it stands (CPU) on the same workload and metric."""
+    if rank != 0:
+        return
+    from oracle import gb as ogb
+    from oracle import mh as omh
+    wl = wk.posterior_windows()
+
+    def on_window(s, w):
+        k0, W, N, doff, _, _ = wl.windows[w]
+        q, hA, hE = ogb.template(torch.tensor(s[None]), N, wl.T)
+        j = int(q[0]) - N // 2 + np.arange(N) - k0
+        ok = (j >= 0) & (j < W)
+        a, e = np.zeros(W, np.complex128), np.zeros(W, np.complex128)
+        a[j[ok]], e[j[ok]] = hA[0].numpy()[ok], hE[0].numpy()[ok]
+        return a, e
+
+    dA, dE = wl.noise_A.copy(), wl.noise_E.copy()
+    srcs = []
+    for w, (k0, W, N, doff, coff, nc) in enumerate(wl.windows):
+        s = wl.sources[w][0].copy()
+        a, e = on_window(s, w)
+        hh = (4 / wl.T) * (np.sum(wl.w_A[doff:doff + W] * abs(a) ** 2) + np.sum(wl.w_E[doff:doff + W] * abs(e) ** 2))
+        s[4] = wl.meta["snr"][w] / math.sqrt(hh)
+        a, e = on_window(s, w)
+        dA[doff:doff + W] += a
+        dE[doff:doff + W] += e
+        srcs.append([s])
+    k0, W, N, doff, coff, nc = wl.windows[0]
+    n = 1000
+    rng = np.random.default_rng(1)
+    sig = np.array([0.3 / wl.T, 1e-19, 0.05, 0.05, 0.1 * srcs[0][0][4], 0.05, 0.05, 0.05])
+    th, lg = wk.gaussian_proposals(srcs[0][0], sig, n, rng)
+    lu = wk.log_uniforms(n, rng)
+    win = [(k0, W, N, doff, 0, n)]
+
+    def step():
+        l, _, _ = ogb.loglik(win, dA, dE, wl.w_A, wl.w_E, th, wl.T)
+        omh.mh_independence(l.numpy(), lg, lu, 1.0)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = n * args.steps / dt
+    sample = "window 0 (N=%d) of the posterior workload, %d proposals per step (logL + chain)" % (N, n)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": torch.get_num_threads(),
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=None, help="timed steps of the FP64 path (default: steps)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    from paper_2307_03763_gb300 import api, build
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    build.build()
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    ctx = api.Context(2 * wk.YEAR, device=dev.index)
+    wl, dA_h, dE_h, th_h, lg_h = build_inputs(ctx, wk.SEED_BASE + 2 + 1000 * rank, dev)
+    nwin, n = len(wl.windows), wl.windows[0][5]
+    T_ = lambda x, dt: torch.as_tensor(np.ascontiguousarray(x)).to(dev, dt)
+    dA, dE = T_(dA_h, torch.complex128), T_(dE_h, torch.complex128)
+    wA, wE = T_(wl.w_A, torch.float64), T_(wl.w_E, torch.float64)
+    theta = T_(th_h, torch.float64)
+    log_g = T_(lg_h.reshape(nwin, n), torch.float64)
+    log_u = T_(wl.log_u.reshape(nwin, n), torch.float64)
+    temp = torch.ones(nwin, dtype=torch.float64, device=dev)
+    logL = torch.empty(wl.n_cand, dtype=torch.float64, device=dev)
+    chain = torch.empty((nwin, n), dtype=torch.int32, device=dev)
+    acc = torch.empty(nwin, dtype=torch.int32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(prec):
+        ctx.loglik(wl.windows, dA, dE, wA, wE, theta, prec=prec, out=(logL, None, None))
+        ctx.mh_independence(logL.view(nwin, n), log_g, log_u, temp, out=(chain, acc))
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed(prec, steps):
+        """Per-step CUDA-event times (ms) of the step and of the likelihood launch alone."""
+        for _ in range(args.warmup):
+            step(prec)
+        barrier()
+        st, kt = [], []
+        for _ in range(steps):
+            flush.zero_()                      # L2 flush between timed steps
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            ctx.loglik(wl.windows, dA, dE, wA, wE, theta, prec=prec, out=(logL, None, None))
+            e1.record(stream)
+            ctx.mh_independence(logL.view(nwin, n), log_g, log_u, temp, out=(chain, acc))
+            e2.record(stream)
+            st.append((e0, e1, e2))
+        barrier()
+        step_ms = [a.elapsed_time(c) for a, b, c in st]
+        kern_ms = [a.elapsed_time(b) for a, b, c in st]
+        return float(np.sum(step_ms)), float(np.mean(kern_ms)), step_ms
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    # accuracy of the mixed path against the FP64 path on this workload
+    l64 = torch.empty_like(logL)
+    ctx.loglik(wl.windows, dA, dE, wA, wE, theta, prec="fp64", out=(l64, None, None))
+    lmx = torch.empty_like(logL)
+    ctx.loglik(wl.windows, dA, dE, wA, wE, theta, prec="mixed", out=(lmx, None, None))
+    dl = (lmx - l64).abs()
+    ctx.check()
+
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    tot_mx, kern_mx, steps_mx = timed("mixed", args.steps)
+    clk = clocks.stop()
+    fp64_steps = args.fp64_steps or args.steps
+    tot_64, kern_64, _ = timed("fp64", fp64_steps)
+    tot_mx, tot_64 = max_over_ranks(tot_mx), max_over_ranks(tot_64)
+
+    # end to end through the public API with host buffers: proposals and their
+    # log g, log u copied in from pinned memory each step, chain and logL out
+    pin = lambda x: torch.as_tensor(np.ascontiguousarray(x)).pin_memory()
+    h_th, h_lg, h_lu = pin(th_h), pin(lg_h.reshape(nwin, n)), pin(wl.log_u.reshape(nwin, n))
+    h_dA, h_dE, h_wA, h_wE = pin(dA_h), pin(dE_h), pin(wl.w_A), pin(wl.w_E)
+    h_chain = torch.empty((nwin, n), dtype=torch.int32).pin_memory()
+    h_logL = torch.empty(wl.n_cand, dtype=torch.float64).pin_memory()
+    ins = [(h_th, theta), (h_lg, log_g), (h_lu, log_u), (h_dA, dA), (h_dE, dE), (h_wA, wA), (h_wE, wE)]
+    h2d = sum(h.numel() * h.element_size() for h, _ in ins)
+    d2h = h_chain.numel() * 4 + h_logL.numel() * 8
+
+    def e2e_step():
+        for h, d in ins:
+            d.copy_(h, non_blocking=True)
+        step("mixed")
+        h_chain.copy_(chain, non_blocking=True)
+        h_logL.copy_(logL, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1))
+
+    if rank != 0:
+        return
+    evals = wl.n_cand * world
+    value = evals * args.steps / (tot_mx / 1e3)
+    value64 = evals * fp64_steps / (tot_64 / 1e3)
+    ms_step = tot_mx / args.steps
+    f_mid = np.array([w[0] + w[1] / 2 for w in wl.windows]) / wl.T
+    flops = sum(n * flops_per_eval(w[2], f, wl.T) for w, f in zip(wl.windows, f_mid))
+    fp32_peak = 152 * 128 * 2 * 2070e6 / 1e12
+    achieved = flops / (kern_mx / 1e3) / 1e12
+    traffic = None
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", "loglik_mixed_traffic.json")))
+        traffic = prof.get("bytes_per_launch")
+    except Exception:
+        pass
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64-phase", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": evals, "windows": nwin, "proposals_per_window": n,
+                   "l2": "flushed between timed steps (2x L2 buffer written)", "parallelism": "replicas"},
+        "s_per_10k_posterior": ms_step / 1e3 / nwin,
+        "fp64": {"value": value64, "unit": UNIT, "steps": fp64_steps, "ms_per_step": tot_64 / fp64_steps,
+                 "s_per_10k_posterior": tot_64 / fp64_steps / 1e3 / nwin, "loglik_ms": kern_64},
+        "mixed_vs_fp64": {"max_abs_dlogL": float(dl.max()), "p99_abs_dlogL": float(dl.quantile(0.99)),
+                          "median_abs_dlogL": float(dl.median()), "snr_range": [20, 200]},
+        "loglik_ms": kern_mx, "mh_ms": ms_step - kern_mx,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": traffic,
+                     "kernel": "loglik_mixed_kernel",
+                     "peak_note": "FP32 FMA peak from unit counts: 152 SM x 128 lanes x 2 x 2070 MHz"},
+        "e2e": {"value": evals * args.steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "clocks": clk,
+        "gpu_launches": 2 * args.steps,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, dA_h, dE_h, th_h)
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * gb.h -- C ABI of libgb, the GB300-native batched Galactic-binary likelihood.
+ *
+ * The library evaluates, for batches of 8-parameter Galactic-binary candidates
+ * grouped by frequency window, the TDI A/E template by the fast/slow
+ * decomposition and the noise-weighted inner products of Strub et al.,
+ * "Accelerating global parameter estimation of gravitational waves from
+ * Galactic binaries using a genetic algorithm and GPUs" (arXiv:2307.03763):
+ *
+ *   log-likelihood       log p(d|theta) = -1/2 <d - s|d - s>        (Eq. 2)
+ *   inner product        <x|y> = 4 Re int x~ y~* / S df             (Eq. 3)
+ *   channel sum, A and E sum over {A, E}; A = (Z-X)/sqrt2,
+ *                        E = (X-2Y+Z)/sqrt6                          (Eqs. 4-5)
+ *   SNR, best amplitude  rho = <d|s>/sqrt<s|s>, A_max = <d|s'>/<s'|s'> (Eqs. 6-7)
+ *   MH acceptance        min(1, [L_p/L_c g_c/g_p]^(1/T))            (Eq. 13, Alg. 4)
+ *
+ * Conventions the paper leaves open (it cites the waveform model) are fixed
+ * as follows and are the same in every entry point:
+ *   theta (8 doubles per candidate, this order):
+ *       f0 [Hz], fdot [Hz/s], beta [rad, ecliptic latitude],
+ *       lambda [rad, ecliptic longitude], A [strain amplitude],
+ *       iota [rad], psi [rad], phi0 [rad]
+ *   carrier bin  q = floor(f0 T + fdot T^2/2 + 1/2), one IEEE rounding per
+ *       operation in the order ((f0*T) + ((0.5*fdot)*T)*T) + 0.5
+ *   slow part sampled at t_n = n T/N, N-point DFT, template on bins
+ *       q - N/2 .. q + N/2 - 1 with h~(f_{q+m}) = (T/2N) S_m
+ *   inner product over window bins k0 .. k0+W-1:
+ *       <x|y> = (4/T) Re sum_k w_k x_k y_k*,  w_k = 1/S(f_k)
+ *   template bins outside the window are dropped.
+ *   Orbit: rigid equal-arm triangle (arm L) on the first-order heliocentric
+ *   orbit; first-generation equal-arm TDI.
+ *
+ * Memory: every array argument is a DEVICE pointer owned by the caller unless
+ * stated otherwise; complex arrays are interleaved (re, im) doubles.  The
+ * library owns only the context (orbit tables, twiddles, cached launch plans,
+ * a device status word).  All compute calls are asynchronous on `stream`
+ * (a cudaStream_t passed as void*; NULL = legacy default stream).
+ *
+ * Errors: every call returns GB_OK (0) or a negative code; gb_last_error()
+ * gives the message of the last failing call on that context.  Argument
+ * errors are detected on the host before anything is launched.  A candidate
+ * with a non-finite parameter gets NaN outputs and sets GB_EINVAL in the
+ * context's device status word, which gb_ctx_check() reads (synchronising).
+ */
+#ifndef GB_H
+#define GB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GB_OK        0
+#define GB_EINVAL   -1   /* bad argument (host check) or non-finite theta (device) */
+#define GB_ECUDA    -2   /* a CUDA runtime call failed */
+#define GB_ETIMEOUT -3   /* reserved: no entry point waits on another agent */
+#define GB_ENOMEM   -4   /* device allocation failed */
+
+#define GB_FP64   0      /* every step in IEEE double */
+#define GB_MIXED  1      /* phase and carrier offset in double-word arithmetic
+                            (>= 44 significant bits), response, FFT and inner
+                            products in float with compensated sums; inputs and
+                            outputs stay double */
+
+#define GB_N_MIN  32
+#define GB_N_MAX  1024
+
+typedef struct gb_ctx gb_ctx_t;
+
+/* Observation: T_obs [s], arm length L [m]; orbit_model 0 = rigid equal-arm
+ * first-order orbit (the only model). */
+typedef struct {
+    double  T_obs;
+    double  arm_L;
+    int32_t orbit_model;
+    int32_t reserved;
+} gb_obs_t;
+
+/* One frequency window (Sec. III.A-D: the data are analysed per segment and
+ * the inner-product integral is limited to it).
+ *   k0        first frequency bin of the window (f = k / T_obs)
+ *   data_off  index of the window's first bin in dA, dE, wA, wE
+ *   cand_off  first candidate row of the window in theta and the outputs
+ *   W         bins in the window (>= 0)
+ *   N         template samples, a power of two in [GB_N_MIN, GB_N_MAX]
+ *   n_cand    candidates of the window (>= 0)
+ * Windows may share data; candidate ranges must not overlap. */
+typedef struct {
+    int64_t k0;
+    int64_t data_off;
+    int64_t cand_off;
+    int32_t W;
+    int32_t N;
+    int32_t n_cand;
+    int32_t reserved;
+} gb_window_t;
+
+/* Create a context on CUDA device `device` and build its orbit and twiddle
+ * tables (allocates device memory; synchronous).  *ctx is NULL on failure.
+ * T_obs > 0, arm_L > 0, orbit_model == 0. */
+int gb_ctx_create(gb_ctx_t** ctx, const gb_obs_t* obs, int device);
+
+/* Free the context and everything it owns.  NULL is accepted. */
+int gb_ctx_destroy(gb_ctx_t* ctx);
+
+/* Message of the last failing call on `ctx` (never NULL; "" if none). */
+const char* gb_last_error(const gb_ctx_t* ctx);
+
+/* Synchronise the device, read and clear the context's status word.
+ * Returns GB_OK, or GB_EINVAL if a kernel met a non-finite parameter since
+ * the last check. */
+int gb_ctx_check(gb_ctx_t* ctx);
+
+/* Frequency-domain A/E templates (the signal model s(theta) of Sec. III,
+ * first paragraph, with the response of Eqs. 4-5).
+ *   theta  B x 8 doubles (device)
+ *   B      number of templates (>= 0)
+ *   N      template samples (power of two in [GB_N_MIN, GB_N_MAX])
+ *   hA, hE B x N complex (device, written): entry [b][j] is bin q_b - N/2 + j
+ *   q      B int64 carrier bins (device, written)
+ * prec = GB_MIXED computes the unit-amplitude template in float and scales
+ * it by A in double on output. */
+int gb_waveform(gb_ctx_t* ctx, int prec, const double* theta, int64_t B, int32_t N,
+                double* hA, double* hE, int64_t* q, void* stream);
+
+/* Batched log-likelihood over windows (Eq. 2 restricted to each window,
+ * Sec. III.D):  logL = <d|h> - <h|h>/2 - <d|d>/2.
+ *   win        n_win descriptors (HOST array, read during the call)
+ *   dA, dE     complex data of all windows (device, interleaved)
+ *   wA, wE     1/S per bin (device)
+ *   n_bins     length of dA, dE (complex entries), wA, wE; every window must
+ *              satisfy data_off + W <= n_bins (checked, else GB_EINVAL)
+ *   theta      candidate rows (device, n_rows x 8)
+ *   n_rows     rows of theta and of the outputs; every window must satisfy
+ *              cand_off + n_cand <= n_rows (checked, else GB_EINVAL)
+ *   logL       per candidate (device, written)
+ *   dh, hh     <d|h>, <h|h> per candidate (device, written; may be NULL) --
+ *              rho and A_max of Eqs. 6-7 follow from them
+ * Rows not covered by any window are not written.  The first call with a
+ * given window layout uploads a launch plan (synchronous allocation and
+ * copy); later calls with the identical layout reuse it and only launch. */
+int gb_loglik(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win,
+              const double* dA, const double* dE, const double* wA, const double* wE,
+              int64_t n_bins, const double* theta, int64_t n_rows,
+              double* logL, double* dh, double* hh, void* stream);
+
+/* Gradient of the log-likelihood, d logL / d theta, for every candidate, by
+ * the adjoint (reverse-mode) method: the template is recomputed, never
+ * stored.  Same inputs as gb_loglik; grad is n x 8 (device, written), in the
+ * theta order.  q is held fixed (its derivative is zero almost everywhere).
+ * logL (may be NULL) receives the log-likelihood. */
+int gb_loglik_grad(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win,
+                   const double* dA, const double* dE, const double* wA, const double* wE,
+                   int64_t n_bins, const double* theta, int64_t n_rows,
+                   double* logL, double* grad, void* stream);
+
+/* Independence Metropolis-Hastings chains from precomputed values
+ * (Sec. III.G, Alg. 4, Eq. 13).  Row r of each n_chains x n input is one
+ * chain:  logL (log-likelihood of proposal i), log_g (log proposal density),
+ * log_u (log of a U(0,1) variate), temperature (n_chains, > 0).
+ * For i = 1..n-1 with current state c:
+ *     Delta = (logL_i - logL_c)/T + (log_g_c - log_g_i)      (literal = 0)
+ *     Delta = ((logL_i - logL_c) + (log_g_c - log_g_i))/T    (literal = 1)
+ *     accept iff log_u_i < min(0, Delta)   (a NaN Delta rejects)
+ * chain_idx (n_chains x n int32, device, written): chain[0] = 0 and
+ * chain[i] = state after step i.  n_accept (n_chains int32, written). */
+int gb_mh_independence(gb_ctx_t* ctx, int32_t n_chains, int32_t n,
+                       const double* logL, const double* log_g, const double* log_u,
+                       const double* temperature, int32_t literal,
+                       int32_t* chain_idx, int32_t* n_accept, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB_H */

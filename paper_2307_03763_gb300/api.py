@@ -1,0 +1,220 @@
+"""Thin Python binding of libgb (``include/gb.h``): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels; this module checks
+tensor dtypes, devices and shapes, passes raw device pointers and the current
+CUDA stream, and turns nonzero status codes into exceptions.  There is no CPU
+fallback: if ``libgb.so`` is missing the import of the library raises.
+
+Tensors: theta float64 (n, 8) in the order (f0, fdot, beta, lambda, A, iota,
+psi, phi0); data complex128; weights 1/S float64; all on one CUDA device.
+"""
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+GB_OK, GB_EINVAL, GB_ECUDA, GB_ETIMEOUT, GB_ENOMEM = 0, -1, -2, -3, -4
+GB_FP64, GB_MIXED = 0, 1
+PRECISIONS = {"fp64": GB_FP64, "mixed": GB_MIXED, GB_FP64: GB_FP64, GB_MIXED: GB_MIXED}
+
+
+class GBError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libgb error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Window(ctypes.Structure):
+    _fields_ = [("k0", ctypes.c_int64), ("data_off", ctypes.c_int64), ("cand_off", ctypes.c_int64),
+                ("W", ctypes.c_int32), ("N", ctypes.c_int32), ("n_cand", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [("T_obs", ctypes.c_double), ("arm_L", ctypes.c_double), ("orbit_model", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+_LIB = None
+_P = ctypes.c_void_p
+_I32, _I64 = ctypes.c_int32, ctypes.c_int64
+
+_SIGNATURES = {
+    "gb_ctx_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(Obs), ctypes.c_int]),
+    "gb_ctx_destroy": (ctypes.c_int, [_P]),
+    "gb_last_error": (ctypes.c_char_p, [_P]),
+    "gb_ctx_check": (ctypes.c_int, [_P]),
+    "gb_waveform": (ctypes.c_int, [_P, ctypes.c_int, _P, _I64, _I32, _P, _P, _P, _P]),
+    "gb_loglik": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _I64, _P, _I64,
+                                 _P, _P, _P, _P]),
+    "gb_loglik_grad": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _I64, _P,
+                                      _I64, _P, _P, _P]),
+    "gb_mh_independence": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, _I32, _P, _P, _P]),
+}
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libgb.so (built in-tree by ``build.build()``); raise if it is missing."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError("libgb.so is not built (%s); run paper_2307_03763_gb300.build.build()" % path)
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _need(t, dtype, device, name, shape=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch.Tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if t.device != device:
+        raise ValueError("%s must be on %s, got %s" % (name, device, t.device))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+
+
+def windows_array(windows):
+    """ctypes array of gb_window_t from a sequence of (k0, W, N, data_off, cand_off, n_cand)."""
+    arr = (Window * max(1, len(windows)))()
+    for i, (k0, W, N, doff, coff, nc) in enumerate(windows):
+        arr[i] = Window(int(k0), int(doff), int(coff), int(W), int(N), int(nc), 0)
+    return arr
+
+
+class Context:
+    """A libgb context on one CUDA device (owns the orbit and twiddle tables)."""
+
+    def __init__(self, T_obs, arm_L=2.5e9, device=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libgb needs a CUDA device; none is available")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.T_obs = float(T_obs)
+        self.arm_L = float(arm_L)
+        h = ctypes.c_void_p()
+        obs = Obs(self.T_obs, self.arm_L, 0, 0)
+        rc = lib().gb_ctx_create(ctypes.byref(h), ctypes.byref(obs), self.device.index)
+        if rc != GB_OK:
+            raise GBError(rc, "gb_ctx_create failed")
+        self._h = h
+        self._win_cache = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gb_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != GB_OK:
+            raise GBError(rc, lib().gb_last_error(self._h).decode())
+
+    def check(self):
+        """Synchronise and raise if a kernel met a non-finite parameter."""
+        self._check(lib().gb_ctx_check(self._h))
+
+    def _windows(self, windows):
+        key = tuple(tuple(int(x) for x in w) for w in windows)
+        arr = self._win_cache.get(key)
+        if arr is None:
+            if len(self._win_cache) > 64:
+                self._win_cache.clear()
+            arr = windows_array(windows)
+            self._win_cache[key] = arr
+        return arr, len(windows)
+
+    def waveform(self, theta, N, prec="fp64"):
+        """A/E templates on bins q - N/2 .. q + N/2 - 1: returns hA, hE (B, N) complex128, q (B,) int64."""
+        B = theta.shape[0] if theta.dim() == 2 else -1
+        _need(theta, torch.float64, self.device, "theta", (B, 8))
+        hA = torch.empty((B, N), dtype=torch.complex128, device=self.device)
+        hE = torch.empty_like(hA)
+        q = torch.empty(B, dtype=torch.int64, device=self.device)
+        self._check(lib().gb_waveform(self._h, PRECISIONS[prec], _ptr(theta), B, int(N), _ptr(hA), _ptr(hE),
+                                      _ptr(q), _stream(self.device)))
+        return hA, hE, q
+
+    def _data_args(self, windows, dA, dE, wA, wE, theta):
+        nb = dA.shape[0]
+        _need(dA, torch.complex128, self.device, "dA", (nb,))
+        _need(dE, torch.complex128, self.device, "dE", (nb,))
+        _need(wA, torch.float64, self.device, "wA", (nb,))
+        _need(wE, torch.float64, self.device, "wE", (nb,))
+        n = theta.shape[0] if theta.dim() == 2 else -1
+        _need(theta, torch.float64, self.device, "theta", (n, 8))
+        arr, nw = self._windows(windows)
+        return arr, nw, nb, n
+
+    def loglik(self, windows, dA, dE, wA, wE, theta, prec="fp64", out=None):
+        """logL, <d|h>, <h|h> per candidate (Eq. 2 over each window)."""
+        arr, nw, nb, n = self._data_args(windows, dA, dE, wA, wE, theta)
+        if out is None:
+            out = tuple(torch.zeros(n, dtype=torch.float64, device=self.device) for _ in range(3))
+        logL, dh, hh = out
+        for t, name in ((logL, "logL"), (dh, "dh"), (hh, "hh")):
+            if t is not None:
+                _need(t, torch.float64, self.device, name, (n,))
+        self._check(lib().gb_loglik(self._h, PRECISIONS[prec], arr, nw, _ptr(dA), _ptr(dE), _ptr(wA), _ptr(wE),
+                                    nb, _ptr(theta), n, _ptr(logL), _ptr(dh), _ptr(hh), _stream(self.device)))
+        return logL, dh, hh
+
+    def loglik_grad(self, windows, dA, dE, wA, wE, theta, prec="fp64", out=None):
+        """logL and d logL / d theta (n, 8) by the adjoint kernel."""
+        arr, nw, nb, n = self._data_args(windows, dA, dE, wA, wE, theta)
+        if out is None:
+            out = (torch.zeros(n, dtype=torch.float64, device=self.device),
+                   torch.zeros((n, 8), dtype=torch.float64, device=self.device))
+        logL, grad = out
+        if logL is not None:
+            _need(logL, torch.float64, self.device, "logL", (n,))
+        _need(grad, torch.float64, self.device, "grad", (n, 8))
+        self._check(lib().gb_loglik_grad(self._h, PRECISIONS[prec], arr, nw, _ptr(dA), _ptr(dE), _ptr(wA),
+                                         _ptr(wE), nb, _ptr(theta), n, _ptr(logL), _ptr(grad),
+                                         _stream(self.device)))
+        return logL, grad
+
+    def mh_independence(self, logL, log_g, log_u, temperature, literal=False, out=None):
+        """Chains (n_chains, n) int32 and accept counts from (n_chains, n) float64 inputs (Alg. 4)."""
+        if logL.dim() != 2:
+            raise ValueError("logL must be (n_chains, n)")
+        nc, n = logL.shape
+        for t, name in ((logL, "logL"), (log_g, "log_g"), (log_u, "log_u")):
+            _need(t, torch.float64, self.device, name, (nc, n))
+        _need(temperature, torch.float64, self.device, "temperature", (nc,))
+        if out is None:
+            out = (torch.empty((nc, n), dtype=torch.int32, device=self.device),
+                   torch.empty(nc, dtype=torch.int32, device=self.device))
+        chain, acc = out
+        _need(chain, torch.int32, self.device, "chain", (nc, n))
+        _need(acc, torch.int32, self.device, "n_accept", (nc,))
+        self._check(lib().gb_mh_independence(self._h, nc, n, _ptr(logL), _ptr(log_g), _ptr(log_u),
+                                             _ptr(temperature), 1 if literal else 0, _ptr(chain), _ptr(acc),
+                                             _stream(self.device)))
+        return chain, acc

@@ -1,0 +1,105 @@
+// api.cu -- host entry points: argument checks, launch plans, dispatch by precision.
+#include <string>
+
+#include "gb_internal.cuh"
+
+using namespace gb;
+
+namespace {
+
+int check_windows(gb_ctx* ctx, const char* fn, const gb_window_t* win, int32_t n_win, int64_t n_bins,
+                  int64_t n_rows, int64_t* total) {
+    *total = 0;
+    if (n_win < 0) return set_error(ctx, GB_EINVAL, std::string(fn) + ": n_win < 0");
+    if (n_win > 0 && !win) return set_error(ctx, GB_EINVAL, std::string(fn) + ": null window array");
+    if (n_bins < 0 || n_rows < 0) return set_error(ctx, GB_EINVAL, std::string(fn) + ": negative extent");
+    for (int i = 0; i < n_win; ++i) {
+        const gb_window_t& w = win[i];
+        const std::string at = std::string(fn) + ": window " + std::to_string(i) + ": ";
+        if (!valid_size(w.N)) return set_error(ctx, GB_EINVAL, at + "N must be a power of two in [32, 1024]");
+        if (w.W < 0 || w.n_cand < 0 || w.data_off < 0 || w.cand_off < 0)
+            return set_error(ctx, GB_EINVAL, at + "negative size or offset");
+        if (w.data_off + (int64_t)w.W > n_bins) return set_error(ctx, GB_EINVAL, at + "data_off + W > n_bins");
+        if (w.cand_off + (int64_t)w.n_cand > n_rows) return set_error(ctx, GB_EINVAL, at + "cand_off + n_cand > n_rows");
+        *total += w.n_cand;
+    }
+    return GB_OK;
+}
+
+int sm_count(gb_ctx* ctx) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || n <= 0) n = 152;
+    return n;
+}
+
+// candidates per tile: at most 32 per warp; fewer when the batch is small so
+// that every SM gets work
+int tile_size(gb_ctx* ctx, int64_t total, int warps) {
+    const int64_t target = (int64_t)sm_count(ctx) * 2;
+    int64_t t = (total + target - 1) / target;
+    if (t > 32 * warps) t = 32 * warps;
+    if (t < warps) t = warps;
+    return (int)t;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gb_loglik(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win, const double* dA,
+              const double* dE, const double* wA, const double* wE, int64_t n_bins, const double* theta,
+              int64_t n_rows, double* logL, double* dh, double* hh, void* stream) {
+    if (!ctx) return GB_EINVAL;
+    if (prec != GB_FP64 && prec != GB_MIXED) return set_error(ctx, GB_EINVAL, "gb_loglik: unknown precision");
+    int64_t total = 0;
+    int rc = check_windows(ctx, "gb_loglik", win, n_win, n_bins, n_rows, &total);
+    if (rc != GB_OK) return rc;
+    if (total == 0) return GB_OK;
+    if (!dA || !dE || !wA || !wE || !theta || !logL) return set_error(ctx, GB_EINVAL, "gb_loglik: null pointer");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_loglik: cudaSetDevice");
+    const Plan* plan = nullptr;
+    const int warps = 4;
+    rc = get_plan(ctx, prec, win, n_win, tile_size(ctx, total, warps), &plan);
+    if (rc != GB_OK) return rc;
+    if (prec == GB_FP64)
+        return launch_loglik_fp64(ctx, *plan, dA, dE, wA, wE, theta, logL, dh, hh, (cudaStream_t)stream);
+    return launch_loglik_mixed(ctx, *plan, dA, dE, wA, wE, theta, logL, dh, hh, (cudaStream_t)stream);
+}
+
+int gb_loglik_grad(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win, const double* dA,
+                   const double* dE, const double* wA, const double* wE, int64_t n_bins, const double* theta,
+                   int64_t n_rows, double* logL, double* grad, void* stream) {
+    if (!ctx) return GB_EINVAL;
+    if (prec != GB_FP64 && prec != GB_MIXED) return set_error(ctx, GB_EINVAL, "gb_loglik_grad: unknown precision");
+    int64_t total = 0;
+    int rc = check_windows(ctx, "gb_loglik_grad", win, n_win, n_bins, n_rows, &total);
+    if (rc != GB_OK) return rc;
+    if (total == 0) return GB_OK;
+    if (!dA || !dE || !wA || !wE || !theta || !grad) return set_error(ctx, GB_EINVAL, "gb_loglik_grad: null pointer");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_loglik_grad: cudaSetDevice");
+    const Plan* plan = nullptr;
+    // distinct plan keys for the gradient kernels (their CTAs have two warps)
+    rc = get_plan(ctx, prec + 16, win, n_win, tile_size(ctx, total, 2), &plan);
+    if (rc != GB_OK) return rc;
+    if (prec == GB_FP64)
+        return launch_grad_fp64(ctx, *plan, dA, dE, wA, wE, theta, logL, grad, (cudaStream_t)stream);
+    return launch_grad_mixed(ctx, *plan, dA, dE, wA, wE, theta, logL, grad, (cudaStream_t)stream);
+}
+
+int gb_waveform(gb_ctx_t* ctx, int prec, const double* theta, int64_t B, int32_t N, double* hA, double* hE,
+                int64_t* q, void* stream) {
+    if (!ctx) return GB_EINVAL;
+    if (prec != GB_FP64 && prec != GB_MIXED) return set_error(ctx, GB_EINVAL, "gb_waveform: unknown precision");
+    if (B < 0) return set_error(ctx, GB_EINVAL, "gb_waveform: B < 0");
+    if (!valid_size(N)) return set_error(ctx, GB_EINVAL, "gb_waveform: N must be a power of two in [32, 1024]");
+    if (B == 0) return GB_OK;
+    if (!theta || !hA || !hE || !q) return set_error(ctx, GB_EINVAL, "gb_waveform: null pointer");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_waveform: cudaSetDevice");
+    if (prec == GB_FP64) return launch_waveform_fp64(ctx, theta, B, N, hA, hE, q, (cudaStream_t)stream);
+    return launch_waveform_mixed(ctx, theta, B, N, hA, hE, q, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,287 @@
+// ctx.cu -- context, geometry and twiddle tables, launch plans, error state.
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+
+#include "gb_internal.cuh"
+
+namespace gb {
+
+int set_error(gb_ctx* ctx, int code, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int cuda_error(gb_ctx* ctx, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return set_error(ctx, e == cudaErrorMemoryAllocation ? GB_ENOMEM : GB_ECUDA, m);
+}
+
+// ---------------------------------------------------------------------------
+// geometry tables: rigid equal-arm triangle on the first-order orbit
+//   x_i = AU cos a + AU e/2 (cos(2a - b_i) - 3 cos b_i)
+//   y_i = AU sin a + AU e/2 (sin(2a - b_i) - 3 sin b_i)
+//   z_i = -sqrt3 AU e cos(a - b_i),   e = L / (2 sqrt3 AU), a = 2 pi t / yr
+// sampled at t_n = n T/N.
+// ---------------------------------------------------------------------------
+__global__ void build_tables_kernel(int N, double T, double L, double* tab64, float* tab32) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const double ecc = L / (2.0 * sqrt(3.0) * kAU);
+    const double t = (double)n * (T / (double)N);
+    const double a = 2.0 * kPi * t / kYear;
+    double sa, ca;
+    sincos(a, &sa, &ca);
+    double x[3][3];
+    for (int i = 0; i < 3; ++i) {
+        const double b = 2.0 * kPi * i / 3.0;
+        x[i][0] = kAU * ca + 0.5 * kAU * ecc * (cos(2.0 * a - b) - 3.0 * cos(b));
+        x[i][1] = kAU * sa + 0.5 * kAU * ecc * (sin(2.0 * a - b) - 3.0 * sin(b));
+        x[i][2] = -sqrt(3.0) * kAU * ecc * cos(a - b);
+    }
+    double* X64 = tab64;
+    double* A64 = tab64 + 9 * N;
+    float* R32 = tab32;
+    float* A32 = tab32 + 9 * N;
+    float* CA = tab32 + 18 * N;
+    float* SA = tab32 + 20 * N;
+    const double centre[3] = {kAU * ca, kAU * sa, 0.0};
+    for (int i = 0; i < 3; ++i)
+        for (int c = 0; c < 3; ++c) {
+            X64[(i * 3 + c) * N + n] = x[i][c];
+            R32[(i * 3 + c) * N + n] = (float)((x[i][c] - centre[c]) / kC);
+        }
+    const int em[3] = {0, 1, 2}, rc[3] = {1, 2, 0};
+    for (int a_ = 0; a_ < 3; ++a_) {
+        double d[3], nn = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            d[c] = x[rc[a_]][c] - x[em[a_]][c];
+            nn += d[c] * d[c];
+        }
+        nn = sqrt(nn);
+        for (int c = 0; c < 3; ++c) {
+            A64[(a_ * 3 + c) * N + n] = d[c] / nn;
+            A32[(a_ * 3 + c) * N + n] = (float)(d[c] / nn);
+        }
+    }
+    const float chi = (float)ca, shi = (float)sa;
+    CA[n] = chi;
+    CA[N + n] = (float)(ca - (double)chi);
+    SA[n] = shi;
+    SA[N + n] = (float)(sa - (double)shi);
+}
+
+__global__ void build_twiddles_kernel(double* tw64, float* tw32) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= kTwiddles) return;
+    double s, c;
+    sincospi((double)k / 512.0, &s, &c);   // exp(-2 pi i k / 1024)
+    tw64[2 * k] = c;
+    tw64[2 * k + 1] = -s;
+    tw32[2 * k] = (float)c;
+    tw32[2 * k + 1] = (float)(-s);
+}
+
+constexpr int kTab64PerN = 18;   // doubles per sample
+constexpr int kTab32PerN = 22;   // floats per sample
+
+OrbitTables64 tables64(const gb_ctx* ctx, int N) {
+    const double* t = ctx->d_tab64[size_index(N)];
+    return OrbitTables64{t, t + 9 * N};
+}
+
+OrbitTables32 tables32(const gb_ctx* ctx, int N) {
+    const float* t = ctx->d_tab32[size_index(N)];
+    return OrbitTables32{t, t + 9 * N, t + 18 * N, t + 20 * N};
+}
+
+TabSet64 tabset64(const gb_ctx* ctx) {
+    TabSet64 s;
+    for (int i = 0; i < kNumSizes; ++i) s.t[i] = tables64(ctx, 32 << i);
+    return s;
+}
+
+TabSet32 tabset32(const gb_ctx* ctx) {
+    TabSet32 s;
+    for (int i = 0; i < kNumSizes; ++i) s.t[i] = tables32(ctx, 32 << i);
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// launch plans
+// ---------------------------------------------------------------------------
+static uint64_t fnv1a(const void* p, size_t n, uint64_t h) {
+    const unsigned char* b = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+static void free_plan(Plan& p) {
+    if (p.d_win) cudaFree(p.d_win);
+    if (p.d_tiles) cudaFree(p.d_tiles);
+    p.d_win = nullptr;
+    p.d_tiles = nullptr;
+}
+
+int get_plan(gb_ctx* ctx, int prec, const gb_window_t* win, int32_t n_win, int tile_cands,
+             const Plan** out) {
+    uint64_t key = 1469598103934665603ull;
+    key = fnv1a(&prec, sizeof prec, key);
+    key = fnv1a(&tile_cands, sizeof tile_cands, key);
+    key = fnv1a(&n_win, sizeof n_win, key);
+    key = fnv1a(win, sizeof(gb_window_t) * (size_t)n_win, key);
+    ctx->clock++;
+    for (auto& p : ctx->plans)
+        if (p.key == key && p.prec == prec && p.n_win == n_win) {
+            p.last_use = ctx->clock;
+            *out = &p;
+            return GB_OK;
+        }
+    // build the tile list: every window split into chunks of tile_cands,
+    // most expensive tiles first so that the tail of the grid is short
+    std::vector<Tile> tiles;
+    std::vector<double> cost;
+    int n_max = 0, w_max = 0;
+    for (int w = 0; w < n_win; ++w) {
+        const gb_window_t& g = win[w];
+        n_max = std::max(n_max, g.N);
+        w_max = std::max(w_max, g.W);
+        for (int64_t c = 0; c < g.n_cand; c += tile_cands) {
+            Tile t;
+            t.win = w;
+            t.pad = 0;
+            t.c_begin = g.cand_off + c;
+            t.c_end = g.cand_off + std::min<int64_t>(g.n_cand, c + tile_cands);
+            tiles.push_back(t);
+            cost.push_back((double)(t.c_end - t.c_begin) * g.N * (log2_size(g.N) + 12));
+        }
+    }
+    std::vector<int> order(tiles.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<Tile> sorted(tiles.size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = tiles[order[i]];
+
+    Plan p;
+    p.key = key;
+    p.prec = prec;
+    p.n_win = n_win;
+    p.n_tiles = (int)sorted.size();
+    p.n_max = n_max;
+    p.w_max = w_max;
+    p.last_use = ctx->clock;
+    cudaError_t e;
+    if (n_win > 0) {
+        e = cudaMalloc(&p.d_win, sizeof(gb_window_t) * n_win);
+        if (e != cudaSuccess) return cuda_error(ctx, e, "plan: cudaMalloc windows");
+        e = cudaMemcpy(p.d_win, win, sizeof(gb_window_t) * n_win, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            free_plan(p);
+            return cuda_error(ctx, e, "plan: copy windows");
+        }
+    }
+    if (!sorted.empty()) {
+        e = cudaMalloc(&p.d_tiles, sizeof(Tile) * sorted.size());
+        if (e != cudaSuccess) {
+            free_plan(p);
+            return cuda_error(ctx, e, "plan: cudaMalloc tiles");
+        }
+        e = cudaMemcpy(p.d_tiles, sorted.data(), sizeof(Tile) * sorted.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            free_plan(p);
+            return cuda_error(ctx, e, "plan: copy tiles");
+        }
+    }
+    const size_t kMaxPlans = 16;
+    if (ctx->plans.size() >= kMaxPlans) {
+        auto lru = std::min_element(ctx->plans.begin(), ctx->plans.end(),
+                                    [](const Plan& a, const Plan& b) { return a.last_use < b.last_use; });
+        // a kernel still running may read the evicted plan: wait for the device
+        cudaDeviceSynchronize();
+        free_plan(*lru);
+        ctx->plans.erase(lru);
+    }
+    ctx->plans.push_back(p);
+    *out = &ctx->plans.back();
+    return GB_OK;
+}
+
+}  // namespace gb
+
+using namespace gb;
+
+extern "C" {
+
+int gb_ctx_create(gb_ctx_t** out, const gb_obs_t* obs, int device) {
+    if (!out) return GB_EINVAL;
+    *out = nullptr;
+    if (!obs || !(obs->T_obs > 0.0) || !(obs->arm_L > 0.0) || obs->orbit_model != 0) return GB_EINVAL;
+    gb_ctx* ctx = new gb_ctx();
+    ctx->device = device;
+    ctx->obs = *obs;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return GB_ECUDA;
+    }
+    e = cudaMalloc(&ctx->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_tw64, sizeof(double) * 2 * kTwiddles);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_tw32, sizeof(float) * 2 * kTwiddles);
+    for (int i = 0; i < kNumSizes && e == cudaSuccess; ++i) {
+        const int N = 32 << i;
+        e = cudaMalloc(&ctx->d_tab64[i], sizeof(double) * kTab64PerN * N);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->d_tab32[i], sizeof(float) * kTab32PerN * N);
+        if (e == cudaSuccess) {
+            build_tables_kernel<<<(N + 127) / 128, 128>>>(N, obs->T_obs, obs->arm_L, ctx->d_tab64[i],
+                                                         ctx->d_tab32[i]);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) {
+        build_twiddles_kernel<<<(kTwiddles + 127) / 128, 128>>>(ctx->d_tw64, ctx->d_tw32);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        gb_ctx_destroy(ctx);
+        return e == cudaErrorMemoryAllocation ? GB_ENOMEM : GB_ECUDA;
+    }
+    *out = ctx;
+    return GB_OK;
+}
+
+int gb_ctx_destroy(gb_ctx_t* ctx) {
+    if (!ctx) return GB_OK;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto& p : ctx->plans) free_plan(p);
+    for (int i = 0; i < kNumSizes; ++i) {
+        if (ctx->d_tab64[i]) cudaFree(ctx->d_tab64[i]);
+        if (ctx->d_tab32[i]) cudaFree(ctx->d_tab32[i]);
+    }
+    if (ctx->d_tw64) cudaFree(ctx->d_tw64);
+    if (ctx->d_tw32) cudaFree(ctx->d_tw32);
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    delete ctx;
+    return GB_OK;
+}
+
+const char* gb_last_error(const gb_ctx_t* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int gb_ctx_check(gb_ctx_t* ctx) {
+    if (!ctx) return GB_EINVAL;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int status = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_ctx_check");
+    if (status != 0) return set_error(ctx, GB_EINVAL, "a kernel met a non-finite parameter");
+    return GB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,130 @@
+// gb_internal.cuh -- types and helpers shared by the libgb translation units.
+//
+// Physical model (the paper cites, but does not print, the waveform and the
+// detector response; Sec. III first paragraph and Sec. III.G):
+//   * rigid equal-arm triangle of arm L on the first-order heliocentric orbit,
+//     spacecraft i at beta_i = 2 pi i / 3, alpha = 2 pi t / yr;
+//   * plane wave h_ab = Re[H_ab exp(i Phi(t - k.x/c))], H = A+ E+ - i Ax Ex,
+//     Phi = 2 pi f0 xi + pi fdot xi^2 + phi0;
+//   * link i -> j:  z_ij = -i (f/2f*) sinc(X) exp(-iX) (n.H.n) exp(i Psi_j),
+//     X = (f/2f*)(1 - k.n), Psi_j the receiver's phase heterodyned by q;
+//   * first-generation equal-arm TDI X, Y, Z with D = exp(-i f/f*), then
+//     A = (Z - X)/sqrt2, E = (X - 2Y + Z)/sqrt6 (Eq. 5).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gb.h"
+
+namespace gb {
+
+constexpr double kC = 299792458.0;           // m/s
+constexpr double kAU = 1.495978707e11;       // m
+constexpr double kYear = 31557600.0;         // s (Julian year)
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kNumSizes = 6;                 // N = 32 .. 1024
+constexpr int kTwiddles = 512;               // exp(-2 pi i k / 1024), k < 512
+
+inline int log2_size(int N) {
+    int l = 0;
+    while ((1 << l) < N) ++l;
+    return l;
+}
+inline bool valid_size(int N) {
+    return N >= GB_N_MIN && N <= GB_N_MAX && (N & (N - 1)) == 0;
+}
+inline int size_index(int N) { return log2_size(N) - 5; }
+
+// Per-N geometry tables (device).  Layout: component-major, N entries each.
+struct OrbitTables64 {
+    const double* x;     // [3 craft][3 xyz][N]    positions, m
+    const double* arm;   // [3 arms][3 xyz][N]     unit vectors of arms 0->1, 1->2, 2->0
+};
+struct OrbitTables32 {
+    const float* rho;    // [3 craft][3 xyz][N]    (x_j - x_guiding_centre) / c, s
+    const float* arm;    // [3 arms][3 xyz][N]     arm unit vectors
+    const float* calpha; // [2][N]                 cos(alpha_n) as float hi, lo
+    const float* salpha; // [2][N]                 sin(alpha_n) as float hi, lo
+};
+
+// Tables of every size, passed by value as a kernel argument.
+struct TabSet64 {
+    OrbitTables64 t[kNumSizes];
+};
+struct TabSet32 {
+    OrbitTables32 t[kNumSizes];
+};
+
+// Work item: candidates [c_begin, c_end) of window `win`.
+struct Tile {
+    int32_t win;
+    int32_t pad;
+    int64_t c_begin;
+    int64_t c_end;
+};
+
+struct Plan {
+    uint64_t key = 0;
+    int prec = -1;
+    int n_win = 0;
+    int n_tiles = 0;
+    int n_max = 0;
+    int w_max = 0;
+    gb_window_t* d_win = nullptr;
+    Tile* d_tiles = nullptr;
+    uint64_t last_use = 0;
+};
+
+}  // namespace gb
+
+struct gb_ctx {
+    int device = 0;
+    gb_obs_t obs{};
+    std::string err;
+    // tables, one allocation per N
+    double* d_tab64[gb::kNumSizes] = {};
+    float* d_tab32[gb::kNumSizes] = {};
+    double* d_tw64 = nullptr;   // kTwiddles complex
+    float* d_tw32 = nullptr;
+    int* d_status = nullptr;    // device status word (GB_OK or GB_EINVAL)
+    std::vector<gb::Plan> plans;
+    uint64_t clock = 0;
+};
+
+namespace gb {
+
+int set_error(gb_ctx* ctx, int code, const std::string& msg);
+int cuda_error(gb_ctx* ctx, cudaError_t e, const char* what);
+
+OrbitTables64 tables64(const gb_ctx* ctx, int N);
+OrbitTables32 tables32(const gb_ctx* ctx, int N);
+TabSet64 tabset64(const gb_ctx* ctx);
+TabSet32 tabset32(const gb_ctx* ctx);
+inline double transfer_frequency(const gb_ctx* ctx) { return kC / (2.0 * kPi * ctx->obs.arm_L); }
+
+// Validate windows and return (creating and uploading if needed) the launch
+// plan for this layout; tiles hold at most `tile_cands` candidates.
+int get_plan(gb_ctx* ctx, int prec, const gb_window_t* win, int32_t n_win, int tile_cands,
+             const Plan** out);
+
+// launchers implemented per precision
+int launch_loglik_fp64(gb_ctx* ctx, const Plan& plan, const double* dA, const double* dE,
+                       const double* wA, const double* wE, const double* theta, double* logL,
+                       double* dh, double* hh, cudaStream_t s);
+int launch_waveform_fp64(gb_ctx* ctx, const double* theta, int64_t B, int N, double* hA,
+                         double* hE, int64_t* q, cudaStream_t s);
+int launch_loglik_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const double* dE,
+                        const double* wA, const double* wE, const double* theta, double* logL,
+                        double* dh, double* hh, cudaStream_t s);
+int launch_waveform_mixed(gb_ctx* ctx, const double* theta, int64_t B, int N, double* hA,
+                          double* hE, int64_t* q, cudaStream_t s);
+int launch_grad_fp64(gb_ctx* ctx, const Plan& plan, const double* dA, const double* dE, const double* wA,
+                     const double* wE, const double* theta, double* logL, double* grad, cudaStream_t s);
+int launch_grad_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const double* dE, const double* wA,
+                      const double* wE, const double* theta, double* logL, double* grad, cudaStream_t s);
+
+}  // namespace gb

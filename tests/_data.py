@@ -42,3 +42,25 @@ def unit_snr(src, window, wA, wE, T):
     hA, hE = template_on_window(src, k0, W, N, T)
     hh = (4.0 / T) * (np.sum(wA[doff:doff + W] * np.abs(hA) ** 2) + np.sum(wE[doff:doff + W] * np.abs(hE) ** 2))
     return float(np.sqrt(hh))
+
+
+def fisher_sigma(src, window, wA, wE, T, rel=1e-4):
+    """sqrt(diag F^-1) of F_ij = <d_i h|d_j h> on the window (oracle, central differences)."""
+    k0, W, N, doff, _, _ = window
+    wa, we = wA[doff:doff + W], wE[doff:doff + W]
+    scales = np.array([1.0 / T, 1.0 / T ** 2, 1.0, 1.0, src[4], 1.0, 1.0, 1.0])
+    J = []
+    for i in range(8):
+        h = rel * scales[i]
+        tp, tm = src.copy(), src.copy()
+        tp[i] += h
+        tm[i] -= h
+        ap, ep = template_on_window(tp, k0, W, N, T)
+        am, em = template_on_window(tm, k0, W, N, T)
+        J.append(((ap - am) / (2 * h), (ep - em) / (2 * h)))
+    F = np.empty((8, 8))
+    for i in range(8):
+        for j in range(8):
+            F[i, j] = (4.0 / T) * (np.sum(wa * (J[i][0] * J[j][0].conj()).real)
+                                   + np.sum(we * (J[i][1] * J[j][1].conj()).real))
+    return np.sqrt(np.abs(np.diag(np.linalg.pinv(F))))

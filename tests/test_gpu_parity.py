@@ -1,0 +1,314 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
+
+Bars: the plain-double path matches the oracle to 1e-10 relative (templates
+norm-wise; logL, <d|h>, <h|h> per candidate); the mixed path to
+|dlogL| <= 1e-3 at SNR ~ 50; chain indices bit-exact; the double gradient
+to 1e-9 of the gradient norm (natural parameter units).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import gb as ogb
+from oracle import mh as omh
+from paper_2307_03763_gb300 import workloads as wk
+from tests import _data
+
+pytestmark = pytest.mark.gpu
+
+YEAR = wk.YEAR
+T2 = 2 * YEAR
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="session")
+def api():
+    from paper_2307_03763_gb300 import api, build
+    build.build()
+    return api
+
+
+@pytest.fixture(scope="session")
+def ctx(api):
+    return api.Context(T2)
+
+
+@pytest.fixture(scope="session")
+def ctx1(api):
+    return api.Context(YEAR)
+
+
+def _cuda(x, dtype):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(device=DEV, dtype=dtype)
+
+
+def _thetas(rng, n, f0, T, fd_scale=1.0):
+    out = np.stack([wk.source(f0 * (1 + 0.01 * rng.uniform(-1, 1)), 0.0, 1e-22, rng) for _ in range(n)])
+    out[:, 1] = fd_scale * wk.chirp_fdot(out[:, 0], rng.uniform(0.2, 1.0, n))
+    out[:, 4] = np.exp(rng.uniform(np.log(1e-23), np.log(1e-21), n))
+    return out
+
+
+# --------------------------------------------------------------------------
+# templates
+# --------------------------------------------------------------------------
+
+BANDS = [(32, 0.8e-3), (64, 2.5e-3), (128, 5e-3), (256, 9e-3), (512, 14e-3), (1024, 19e-3)]
+
+
+@pytest.mark.parametrize("N,f0", BANDS)
+def test_waveform_fp64_matches_oracle(ctx1, N, f0):
+    rng = np.random.default_rng(100 + N)
+    th = _thetas(rng, 37, f0, YEAR)
+    hA, hE, q = ctx1.waveform(_cuda(th, torch.float64), N, "fp64")
+    qo, oA, oE = ogb.template(torch.tensor(th), N, YEAR)
+    assert torch.equal(q.cpu(), qo)
+    for g, o in ((hA, oA), (hE, oE)):
+        g = g.cpu()
+        err = (g - o).abs().amax(1) / o.abs().amax(1)
+        assert err.max() < 1e-10, err.max()
+
+
+@pytest.mark.parametrize("N,f0", BANDS)
+def test_waveform_mixed_close_to_oracle(ctx1, N, f0):
+    rng = np.random.default_rng(200 + N)
+    th = _thetas(rng, 37, f0, YEAR)
+    hA, hE, q = ctx1.waveform(_cuda(th, torch.float64), N, "mixed")
+    qo, oA, oE = ogb.template(torch.tensor(th), N, YEAR)
+    assert torch.equal(q.cpu(), qo)
+    for g, o in ((hA, oA), (hE, oE)):
+        err = (g.cpu() - o).abs().amax(1) / o.abs().amax(1)
+        assert err.max() < 2e-6, err.max()
+
+
+def test_waveform_empty_batch(ctx):
+    hA, hE, q = ctx.waveform(torch.zeros((0, 8), dtype=torch.float64, device=DEV), 64)
+    assert hA.shape == (0, 64) and q.shape == (0,)
+
+
+# --------------------------------------------------------------------------
+# log-likelihood
+# --------------------------------------------------------------------------
+
+def _run_both(ctx, wins, dA, dE, wA, wE, th, T, prec):
+    args = (_cuda(dA, torch.complex128), _cuda(dE, torch.complex128), _cuda(wA, torch.float64),
+            _cuda(wE, torch.float64), _cuda(th, torch.float64))
+    g = [x.cpu() for x in ctx.loglik(wins, *args, prec=prec)]
+    o = ogb.loglik(wins, dA, dE, wA, wE, th, T)
+    return g, o
+
+
+def _assert_close_fp64(g, o, rows=None):
+    gl, gdh, ghh = g
+    ol, odh, ohh = o
+    if rows is not None:
+        gl, gdh, ghh, ol, odh, ohh = (x[rows] for x in (gl, gdh, ghh, ol, odh, ohh))
+    scale = max(1.0, float(ohh.abs().max()))
+    assert ((gl - ol).abs() <= 1e-10 * torch.clamp(ol.abs(), min=1.0)).all(), (gl - ol).abs().max()
+    assert ((gdh - odh).abs() <= 1e-10 * scale).all(), (gdh - odh).abs().max()
+    assert ((ghh - ohh).abs() <= 1e-10 * scale).all(), (ghh - ohh).abs().max()
+
+
+def test_loglik_fp64_tiny_window_full(ctx):
+    # one window of N = 128 at 1.5 mHz, 1,000 candidates (every output checked)
+    wl = wk.tiny_window()
+    dA, dE = _data.inject(wl)
+    g, o = _run_both(ctx, wl.windows, dA, dE, wl.w_A, wl.w_E, wl.theta, wl.T, "fp64")
+    _assert_close_fp64(g, o)
+    assert float(g[2].max()) > 100.0       # the injected source is seen (SNR^2 scale)
+
+
+def test_loglik_fp64_ragged_windows(ctx):
+    # several windows in one launch: different N, W != N, templates partly or
+    # wholly outside, an empty window, W = 0, ragged candidate counts
+    rng = np.random.default_rng(7)
+    T = T2
+    specs = []
+    th_all, counts = [], []
+    for (N, f0, W, shift, nc) in [(32, 0.6e-3, 32, 0, 1), (64, 1.1e-3, 80, -20, 33), (128, 2.0e-3, 128, 45, 129),
+                                  (256, 3.9e-3, 200, 0, 257), (128, 2.4e-3, 128, 0, 0), (64, 1.5e-3, 0, 0, 5),
+                                  (512, 4.5e-3, 512, -300, 40), (1024, 5.0e-3, 1024, 0, 19),
+                                  (128, 1.7e-3, 128, 10 ** 6, 7)]:
+        src = wk.source(f0, float(wk.chirp_fdot(f0, 0.6)), 3e-22, rng)
+        kc = int(math.floor((src[0] + 0.5 * src[1] * T) * T + 0.5))
+        specs.append((kc - W // 2 + shift, W, N))
+        half = np.array([3.0 / T, abs(src[1]), 0.3, 0.3, 0.5 * src[4], 0.3, 0.3, 0.3])
+        th_all.append(wk.uniform_box(src, half, nc, rng))
+        counts.append(nc)
+    wins, nb, nt = wk.layout(specs, counts)
+    nA, nE, wA, wE = wk.noise_and_weights(wins, T, rng)
+    th = np.concatenate(th_all)
+    srcs = [[th_all[i][0]] if counts[i] else [] for i in range(len(specs))]
+    wl = wk.Workload("ragged", T, wins, nA, nE, wA, wE, srcs, th)
+    dA, dE = _data.inject(wl)
+    g, o = _run_both(ctx, wins, dA, dE, wA, wE, th, T, "fp64")
+    _assert_close_fp64(g, o)
+
+
+def test_loglik_mixed_tolerance_at_snr50(ctx):
+    wl = wk.tiny_window(seed=wk.SEED_BASE + 11)
+    src = wl.sources[0][0].copy()
+    rho1 = _data.unit_snr(src, wl.windows[0], wl.w_A, wl.w_E, wl.T)
+    scale = 50.0 / rho1
+    src[4] *= scale
+    wl.theta[:, 4] *= scale
+    dA, dE = _data.inject(wl, [[src]])
+    g, o = _run_both(ctx, wl.windows, dA, dE, wl.w_A, wl.w_E, wl.theta, wl.T, "mixed")
+    dl = (g[0] - o[0]).abs()
+    assert float(o[2].max()) > 1000.0
+    assert float(dl.max()) <= 1e-3, float(dl.max())
+
+
+def test_loglik_mixed_multiband(ctx1):
+    # every N / band of the 0.3-20 mHz workload, a few windows each
+    wl = wk.band_windows(n_win=12, cand_range=(50, 90))
+    dA, dE = _data.inject(wl)
+    g, o = _run_both(ctx1, wl.windows, dA, dE, wl.w_A, wl.w_E, wl.theta, wl.T, "mixed")
+    rel = (g[0] - o[0]).abs() / torch.clamp(o[2].abs(), min=1.0)
+    assert float(rel.max()) < 1e-5, float(rel.max())
+    gf, of = _run_both(ctx1, wl.windows, dA, dE, wl.w_A, wl.w_E, wl.theta, wl.T, "fp64")
+    _assert_close_fp64(gf, of)
+
+
+def test_loglik_posterior_workload_sampled(ctx):
+    # the 16-window, 10,000-proposal workload at full size in one launch, in
+    # both precisions; outputs sampled for the oracle (first, last and 40
+    # random rows per window)
+    wl = wk.posterior_windows()
+    rng = np.random.default_rng(5)
+    srcs = []
+    th = np.empty((wl.n_cand, 8))
+    for w, (k0, W, N, doff, coff, nc) in enumerate(wl.windows):
+        s = wl.sources[w][0].copy()
+        s[4] = wl.meta["snr"][w] / _data.unit_snr(s, wl.windows[w], wl.w_A, wl.w_E, wl.T)
+        srcs.append([s])
+        sig = _data.fisher_sigma(s, wl.windows[w], wl.w_A, wl.w_E, wl.T)
+        th[coff:coff + nc], _ = wk.gaussian_proposals(s, 10 * sig, nc, rng)
+    dA, dE = _data.inject(wl, srcs)
+    args = (_cuda(dA, torch.complex128), _cuda(dE, torch.complex128), _cuda(wl.w_A, torch.float64),
+            _cuda(wl.w_E, torch.float64), _cuda(th, torch.float64))
+    g64 = [x.cpu() for x in ctx.loglik(wl.windows, *args, prec="fp64")]
+    gmx = [x.cpu() for x in ctx.loglik(wl.windows, *args, prec="mixed")]
+    rows = []
+    for (k0, W, N, doff, coff, nc) in wl.windows:
+        rows += [coff, coff + nc - 1] + list(coff + rng.choice(nc, 40, replace=False))
+    rows = np.array(sorted(set(rows)))
+    sub_wins, sub_th = [], []
+    for (k0, W, N, doff, coff, nc) in wl.windows:
+        sel = rows[(rows >= coff) & (rows < coff + nc)]
+        sub_wins.append((k0, W, N, doff, len(sub_th), len(sel)))
+        sub_th += list(th[sel])
+    o = ogb.loglik(sub_wins, dA, dE, wl.w_A, wl.w_E, np.array(sub_th), wl.T)
+    idx = torch.tensor(rows)
+    _assert_close_fp64([x[idx] for x in g64], o)
+    assert float((gmx[0][idx] - o[0]).abs().max()) <= 2e-3 * max(1.0, float(o[2].max()) / 2500.0)
+
+
+def test_loglik_outputs_optional(ctx):
+    wl = wk.tiny_window(n_cand=40)
+    dA, dE = _data.inject(wl)
+    args = (_cuda(dA, torch.complex128), _cuda(dE, torch.complex128), _cuda(wl.w_A, torch.float64),
+            _cuda(wl.w_E, torch.float64), _cuda(wl.theta, torch.float64))
+    logL = torch.zeros(40, dtype=torch.float64, device=DEV)
+    for prec in ("fp64", "mixed"):
+        l1, _, _ = ctx.loglik(wl.windows, *args, prec=prec)
+        ctx.loglik(wl.windows, *args, prec=prec, out=(logL, None, None))
+        assert torch.equal(l1, logL)
+
+
+def test_nonfinite_parameter_gives_nan_and_status(ctx, api):
+    wl = wk.tiny_window(n_cand=8)
+    th = wl.theta.copy()
+    th[3, 2] = np.nan
+    th[5, 0] = np.inf
+    args = (_cuda(wl.noise_A, torch.complex128), _cuda(wl.noise_E, torch.complex128),
+            _cuda(wl.w_A, torch.float64), _cuda(wl.w_E, torch.float64), _cuda(th, torch.float64))
+    for prec in ("fp64", "mixed"):
+        l, _, _ = ctx.loglik(wl.windows, *args, prec=prec)
+        l = l.cpu()
+        assert math.isnan(l[3]) and math.isnan(l[5]) and torch.isfinite(l[[0, 1, 2, 4, 6, 7]]).all()
+        with pytest.raises(api.GBError):
+            ctx.check()
+        ctx.check()     # cleared
+
+
+def test_argument_errors_raise(ctx, api):
+    wl = wk.tiny_window(n_cand=8)
+    args = [_cuda(wl.noise_A, torch.complex128), _cuda(wl.noise_E, torch.complex128),
+            _cuda(wl.w_A, torch.float64), _cuda(wl.w_E, torch.float64), _cuda(wl.theta, torch.float64)]
+    k0, W, N, doff, coff, nc = wl.windows[0]
+    for bad in ([(k0, W, 100, doff, coff, nc)], [(k0, W, 2048, doff, coff, nc)],
+                [(k0, W + 1, N, doff, coff, nc)], [(k0, W, N, doff, coff + 1, nc)],
+                [(k0, -1, N, doff, coff, nc)]):
+        with pytest.raises(api.GBError):
+            ctx.loglik(bad, *args)
+    with pytest.raises(api.GBError):
+        ctx.waveform(args[4], 48)
+
+
+# --------------------------------------------------------------------------
+# Metropolis-Hastings chains
+# --------------------------------------------------------------------------
+
+def _mh_both(ctx, L, G, U, T, literal):
+    chain, acc = ctx.mh_independence(_cuda(L, torch.float64), _cuda(G, torch.float64), _cuda(U, torch.float64),
+                                     _cuda(T, torch.float64), literal=literal)
+    oc, oa = omh.mh_independence_batch(L, G, U, T, literal)
+    return chain.cpu().numpy(), acc.cpu().numpy(), np.array(oc), np.array(oa)
+
+
+@pytest.mark.parametrize("literal", [False, True])
+def test_mh_matches_oracle_full_size(ctx, literal):
+    rng = np.random.default_rng(11)
+    nch, n = 16, 10000
+    L = rng.normal(-50, 4, (nch, n))
+    G = rng.normal(0, 2, (nch, n))
+    U = np.log(rng.uniform(0, 1, (nch, n)))
+    T = np.array([1.0, 2.0, 3.0, 5.0, 10.0, 15.0] * 3)[:nch]
+    c, a, oc, oa = _mh_both(ctx, L, G, U, T, literal)
+    assert np.array_equal(c, oc)
+    assert np.array_equal(a, oa)
+
+
+def test_mh_golden_and_edge_cases(ctx):
+    path = os.path.join(os.path.dirname(__file__), "golden", "mh_alg4_worked.txt")
+    g = {}
+    for line in open(path):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.strip().split("=")
+            g[k] = [float(x) for x in v.split(",")]
+    c, a, _, _ = _mh_both(ctx, np.array([g["logL"]]), np.array([g["log_g"]]), np.array([g["log_u"]]),
+                          np.array(g["temperature"]), False)
+    assert c[0].tolist() == [int(x) for x in g["chain"]] and a[0] == int(g["n_accept"][0])
+    # ragged lengths not multiple of the prefetch depth, n = 1, -inf entries
+    for n in (1, 2, 9, 17):
+        rng = np.random.default_rng(n)
+        L = rng.normal(0, 1, (3, n))
+        L[:, n // 2] = -np.inf
+        c, a, oc, oa = _mh_both(ctx, L, rng.normal(0, 1, (3, n)), np.log(rng.uniform(0, 1, (3, n))),
+                                np.ones(3), False)
+        assert np.array_equal(c, oc) and np.array_equal(a, oa)
+
+
+# --------------------------------------------------------------------------
+# gradient
+# --------------------------------------------------------------------------
+
+def test_grad_fp64_matches_oracle(ctx):
+    wl = wk.tiny_window(n_cand=24)
+    dA, dE = _data.inject(wl)
+    th = wl.theta.copy()
+    args = (_cuda(dA, torch.complex128), _cuda(dE, torch.complex128), _cuda(wl.w_A, torch.float64),
+            _cuda(wl.w_E, torch.float64), _cuda(th, torch.float64))
+    lg, gg = (x.cpu() for x in ctx.loglik_grad(wl.windows, *args, prec="fp64"))
+    lo, go = ogb.loglik_grad(wl.windows, dA, dE, wl.w_A, wl.w_E, th, wl.T)
+    s = torch.tensor([1 / wl.T, 1 / wl.T ** 2, 1, 1, 1, 1, 1, 1], dtype=torch.float64)
+    for b in range(th.shape[0]):
+        sb = s.clone()
+        sb[4] = th[b, 4]
+        gn, on = gg[b] * sb, go[b] * sb
+        assert float((gn - on).abs().max()) <= 1e-9 * float(on.abs().sum()), (b, gn, on)
+    assert ((lg - lo).abs() <= 1e-10 * lo.abs()).all()
