@@ -14,7 +14,10 @@ M1  Temperature: by default the exponent 1/T acts on the likelihood ratio only,
     which is the Metropolis-Hastings rule for the tempered target L^(1/T).
     ``literal=True`` applies 1/T to the whole bracket as printed in Eq. 13,
         Delta = ((l_i - l_c) + (log g_c - log g_i))/T.
-    The two agree bit for bit at T = 1.
+    Both are evaluated through one weight per proposal, in this rounding order:
+        default   w_i = l_i/T - log g_i,   Delta = w_i - w_c
+        literal   v_i = l_i - log g_i,     Delta = (v_i - v_c)/T
+    (mathematically the same quantities).  The two agree bit for bit at T = 1.
 M2  "With probability alpha" is decided by a uniform variate u_i in (0, 1)
     passed in as its logarithm: accept iff log u_i < min(0, Delta).  Working
     in logs needs only +, -, / and a comparison, so two IEEE implementations
@@ -40,10 +43,12 @@ def mh_independence(logL, log_g, log_u, temperature, literal=False):
     chain = [0]
     n_accept = 0
     T = float(temperature)
+    if literal:
+        w = [float(logL[i]) - float(log_g[i]) for i in range(n)]
+    else:
+        w = [float(logL[i]) / T - float(log_g[i]) for i in range(n)]
     for i in range(1, n):
-        dl = float(logL[i]) - float(logL[c])
-        dg = float(log_g[c]) - float(log_g[i])
-        delta = (dl + dg) / T if literal else dl / T + dg
+        delta = (w[i] - w[c]) / T if literal else w[i] - w[c]
         if math.isnan(delta):
             accept = False
         else:
