@@ -257,8 +257,8 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=None, help="timed steps of the FP64 path (default: steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -337,12 +337,14 @@ def main():
     dl = (lmx - l64).abs()
     ctx.check()
 
+    # clocks sampled over both timed regions (each alone can be shorter than
+    # the sampling interval)
     clocks = ClockSampler(dev.index)
     clocks.start()
     tot_mx, kern_mx, steps_mx = timed("mixed", args.steps)
-    clk = clocks.stop()
-    fp64_steps = args.fp64_steps or args.steps
+    fp64_steps = args.fp64_steps or max(3, args.steps // 10)
     tot_64, kern_64, _ = timed("fp64", fp64_steps)
+    clk = clocks.stop()
     tot_mx, tot_64 = max_over_ranks(tot_mx), max_over_ranks(tot_64)
 
     # end to end through the public API with host buffers: proposals and their
@@ -409,7 +411,9 @@ def main():
         "e2e": {"value": evals * args.steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "clocks": clk,
-        "gpu_launches": 2 * args.steps,
+        # per step: window preparation, the persistent likelihood kernel (one
+        # per N class present: N <= 256 only here) and the chain kernel
+        "gpu_launches": 3 * args.steps,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, dA_h, dE_h, th_h)

@@ -163,6 +163,9 @@ int gb_loglik_grad(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_wi
  *     Delta = (logL_i - logL_c)/T + (log_g_c - log_g_i)      (literal = 0)
  *     Delta = ((logL_i - logL_c) + (log_g_c - log_g_i))/T    (literal = 1)
  *     accept iff log_u_i < min(0, Delta)   (a NaN Delta rejects)
+ * evaluated in IEEE double in this rounding order: w_i = logL_i/T - log_g_i,
+ * Delta = w_i - w_c (literal = 0); v_i = logL_i - log_g_i,
+ * Delta = (v_i - v_c)/T (literal = 1).
  * chain_idx (n_chains x n int32, device, written): chain[0] = 0 and
  * chain[i] = state after step i.  n_accept (n_chains int32, written). */
 int gb_mh_independence(gb_ctx_t* ctx, int32_t n_chains, int32_t n,

@@ -1,4 +1,5 @@
 // api.cu -- host entry points: argument checks, launch plans, dispatch by precision.
+#include <algorithm>
 #include <string>
 
 #include "gb_internal.cuh"
@@ -60,7 +61,10 @@ int gb_loglik(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win, co
     if (e != cudaSuccess) return cuda_error(ctx, e, "gb_loglik: cudaSetDevice");
     const Plan* plan = nullptr;
     const int warps = 4;
-    rc = get_plan(ctx, prec, win, n_win, tile_size(ctx, total, warps), &plan);
+    // mixed: work items of at most 32 candidates (one warp each), fewer when
+    // the batch would not give every resident warp of the GPU one item
+    int item = (int)std::min<int64_t>(32, std::max<int64_t>(1, (total + sm_count(ctx) * 16 - 1) / (sm_count(ctx) * 16)));
+    rc = get_plan(ctx, prec, win, n_win, prec == GB_MIXED ? item : tile_size(ctx, total, warps), &plan);
     if (rc != GB_OK) return rc;
     if (prec == GB_FP64)
         return launch_loglik_fp64(ctx, *plan, dA, dE, wA, wE, theta, logL, dh, hh, (cudaStream_t)stream);

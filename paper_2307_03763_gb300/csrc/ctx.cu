@@ -41,17 +41,11 @@ __global__ void build_tables_kernel(int N, double T, double L, double* tab64, fl
     }
     double* X64 = tab64;
     double* A64 = tab64 + 9 * N;
-    float* R32 = tab32;
-    float* A32 = tab32 + 9 * N;
-    float* CA = tab32 + 18 * N;
-    float* SA = tab32 + 20 * N;
     const double centre[3] = {kAU * ca, kAU * sa, 0.0};
     for (int i = 0; i < 3; ++i)
-        for (int c = 0; c < 3; ++c) {
-            X64[(i * 3 + c) * N + n] = x[i][c];
-            R32[(i * 3 + c) * N + n] = (float)((x[i][c] - centre[c]) / kC);
-        }
+        for (int c = 0; c < 3; ++c) X64[(i * 3 + c) * N + n] = x[i][c];
     const int em[3] = {0, 1, 2}, rc[3] = {1, 2, 0};
+    double arm[3][3];
     for (int a_ = 0; a_ < 3; ++a_) {
         double d[3], nn = 0.0;
         for (int c = 0; c < 3; ++c) {
@@ -60,15 +54,29 @@ __global__ void build_tables_kernel(int N, double T, double L, double* tab64, fl
         }
         nn = sqrt(nn);
         for (int c = 0; c < 3; ++c) {
-            A64[(a_ * 3 + c) * N + n] = d[c] / nn;
-            A32[(a_ * 3 + c) * N + n] = (float)(d[c] / nn);
+            arm[a_][c] = d[c] / nn;
+            A64[(a_ * 3 + c) * N + n] = arm[a_][c];
         }
     }
+    // float tables, lane-permuted: sample n sits at p = (n mod R)*32 + brev5(n / R)
+    const int R = N / 32;
+    const int p = (n % R) * 32 + brev5(n / R);
+    float rho[2][3];
+    for (int i = 0; i < 2; ++i)
+        for (int c = 0; c < 3; ++c) rho[i][c] = (float)((x[i][c] - centre[c]) / kC);
+    float4* G4 = (float4*)tab32;
+    G4[p] = make_float4(rho[0][0], rho[0][1], rho[0][2], rho[1][0]);
+    G4[N + p] = make_float4(rho[1][1], rho[1][2], (float)arm[0][0], (float)arm[0][1]);
+    G4[2 * N + p] = make_float4((float)arm[0][2], (float)arm[1][0], (float)arm[1][1], (float)arm[1][2]);
     const float chi = (float)ca, shi = (float)sa;
-    CA[n] = chi;
-    CA[N + n] = (float)(ca - (double)chi);
-    SA[n] = shi;
-    SA[N + n] = (float)(sa - (double)shi);
+    G4[3 * N + p] = make_float4(chi, (float)(ca - (double)chi), shi, (float)(sa - (double)shi));
+    // lane twiddle exp(-2 pi i r l / N) at entry n = r*32 + l
+    float* LT = tab32 + 16 * N;
+    const int r = n / 32, l = n % 32;
+    double s, co;
+    sincospi(2.0 * (double)(r * l) / (double)N, &s, &co);
+    LT[2 * n] = (float)co;
+    LT[2 * n + 1] = (float)(-s);
 }
 
 __global__ void build_twiddles_kernel(double* tw64, float* tw32) {
@@ -83,7 +91,7 @@ __global__ void build_twiddles_kernel(double* tw64, float* tw32) {
 }
 
 constexpr int kTab64PerN = 18;   // doubles per sample
-constexpr int kTab32PerN = 22;   // floats per sample
+constexpr int kTab32PerN = 18;   // floats per sample: 4 float4 + lane twiddles
 
 OrbitTables64 tables64(const gb_ctx* ctx, int N) {
     const double* t = ctx->d_tab64[size_index(N)];
@@ -92,7 +100,7 @@ OrbitTables64 tables64(const gb_ctx* ctx, int N) {
 
 OrbitTables32 tables32(const gb_ctx* ctx, int N) {
     const float* t = ctx->d_tab32[size_index(N)];
-    return OrbitTables32{t, t + 9 * N, t + 18 * N, t + 20 * N};
+    return OrbitTables32{(const float4*)t, (const float2*)(t + 16 * N)};
 }
 
 TabSet64 tabset64(const gb_ctx* ctx) {
@@ -122,8 +130,34 @@ static uint64_t fnv1a(const void* p, size_t n, uint64_t h) {
 static void free_plan(Plan& p) {
     if (p.d_win) cudaFree(p.d_win);
     if (p.d_tiles) cudaFree(p.d_tiles);
+    if (p.d_meta) cudaFree(p.d_meta);
+    if (p.d_prep) cudaFree(p.d_prep);
+    if (p.d_head) cudaFree(p.d_head);
     p.d_win = nullptr;
     p.d_tiles = nullptr;
+    p.d_meta = nullptr;
+    p.d_prep = nullptr;
+    p.d_head = nullptr;
+}
+
+// scratch of the mixed-precision kernels: per-window meta (with the offsets
+// of each window's float copy), the float copies, the work-queue head
+static cudaError_t alloc_mixed_scratch(Plan& p, const gb_window_t* win, int n_win) {
+    std::vector<WinMeta> meta(n_win > 0 ? n_win : 1);
+    long long off = 0;
+    for (int w = 0; w < n_win; ++w) {
+        meta[w].dd = 0.0;
+        meta[w].sig = 1.0;
+        meta[w].prep_off = off;
+        off += win[w].W;
+    }
+    p.n_prep = off;
+    cudaError_t e = cudaMalloc(&p.d_meta, sizeof(WinMeta) * meta.size());
+    if (e == cudaSuccess) e = cudaMemcpy(p.d_meta, meta.data(), sizeof(WinMeta) * meta.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_prep, sizeof(Win32) * (size_t)(off > 0 ? off : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_head, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p.d_head, 0, 2 * sizeof(int));
+    return e;
 }
 
 int get_plan(gb_ctx* ctx, int prec, const gb_window_t* win, int32_t n_win, int tile_cands,
@@ -162,6 +196,12 @@ int get_plan(gb_ctx* ctx, int prec, const gb_window_t* win, int32_t n_win, int t
     std::vector<int> order(tiles.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    // mixed plans: items of windows with N >= 512 first (their own kernel)
+    int n_large = 0;
+    if ((prec & 15) == GB_MIXED) {
+        std::stable_partition(order.begin(), order.end(), [&](int a) { return win[tiles[a].win].N >= 512; });
+        for (const Tile& t : tiles) n_large += win[t.win].N >= 512 ? 1 : 0;
+    }
     std::vector<Tile> sorted(tiles.size());
     for (size_t i = 0; i < order.size(); ++i) sorted[i] = tiles[order[i]];
 
@@ -172,6 +212,7 @@ int get_plan(gb_ctx* ctx, int prec, const gb_window_t* win, int32_t n_win, int t
     p.n_tiles = (int)sorted.size();
     p.n_max = n_max;
     p.w_max = w_max;
+    p.n_large = n_large;
     p.last_use = ctx->clock;
     cudaError_t e;
     if (n_win > 0) {
@@ -193,6 +234,13 @@ int get_plan(gb_ctx* ctx, int prec, const gb_window_t* win, int32_t n_win, int t
         if (e != cudaSuccess) {
             free_plan(p);
             return cuda_error(ctx, e, "plan: copy tiles");
+        }
+    }
+    if ((prec & 15) == GB_MIXED) {
+        e = alloc_mixed_scratch(p, win, n_win);
+        if (e != cudaSuccess) {
+            free_plan(p);
+            return cuda_error(ctx, e, "plan: mixed-precision scratch");
         }
     }
     const size_t kMaxPlans = 16;

@@ -44,12 +44,24 @@ struct OrbitTables64 {
     const double* x;     // [3 craft][3 xyz][N]    positions, m
     const double* arm;   // [3 arms][3 xyz][N]     unit vectors of arms 0->1, 1->2, 2->0
 };
+// Float tables are stored lane-permuted: with R = N/32, entry p = r*32 + l
+// holds sample n = R*brev5(l) + r, which is the sample lane l evaluates in its
+// r-th step (the bit reversal feeds the across-lane FFT stage).
+// Four float4 per sample (group-major, [4][N]); with rho_j = (x_j - x_centre)/c
+// and n_01, n_12 the unit vectors of arms 0->1 and 1->2:
+//   g[0] = (rho_0.xyz, rho_1.x)   g[1] = (rho_1.yz, n_01.xy)
+//   g[2] = (n_01.z, n_12.xyz)     g[3] = (cos a hi, cos a lo, sin a hi, sin a lo)
+// The third spacecraft and arm follow exactly from the rigid triangle:
+// rho_2 = -rho_0 - rho_1 (the centroid is the guiding centre) and
+// n_20 = -n_01 - n_12 (the arms close).
 struct OrbitTables32 {
-    const float* rho;    // [3 craft][3 xyz][N]    (x_j - x_guiding_centre) / c, s
-    const float* arm;    // [3 arms][3 xyz][N]     arm unit vectors
-    const float* calpha; // [2][N]                 cos(alpha_n) as float hi, lo
-    const float* salpha; // [2][N]                 sin(alpha_n) as float hi, lo
+    const float4* g;     // [4][N]
+    const float2* ltw;   // [R][32]                exp(-2 pi i r l / N), lane twiddles
 };
+
+__host__ __device__ inline int brev5(int l) {
+    return ((l & 1) << 4) | ((l & 2) << 2) | (l & 4) | ((l & 8) >> 2) | ((l & 16) >> 4);
+}
 
 // Tables of every size, passed by value as a kernel argument.
 struct TabSet64 {
@@ -67,6 +79,21 @@ struct Tile {
     int64_t c_end;
 };
 
+// Per-window values the mixed-precision kernels derive once per launch:
+// <d|d>, the scale sigma = sqrt(max w) of the float copy of the window, and
+// where that copy starts in the plan's scratch buffer.
+struct WinMeta {
+    double dd;
+    double sig;
+    long long prep_off;
+};
+
+// Float copy of one window bin: data times sigma, weights over sigma^2.
+struct Win32 {
+    float2 dA, dE;
+    float wA, wE;
+};
+
 struct Plan {
     uint64_t key = 0;
     int prec = -1;
@@ -74,8 +101,14 @@ struct Plan {
     int n_tiles = 0;
     int n_max = 0;
     int w_max = 0;
+    long long n_prep = 0;           // total window bins (scratch entries)
+    int n_large = 0;                // mixed plans: items with N >= 512 come first
     gb_window_t* d_win = nullptr;
     Tile* d_tiles = nullptr;
+    // scratch of the mixed-precision path (owned by the plan)
+    WinMeta* d_meta = nullptr;
+    Win32* d_prep = nullptr;
+    int* d_head = nullptr;          // work-queue head
     uint64_t last_use = 0;
 };
 

@@ -16,12 +16,22 @@
 // The first four terms can reach hundreds of cycles and are formed in
 // double-word arithmetic, each product reduced modulo one exactly; the rest
 // are below 0.1 cycle and are float.  exp(2 pi i P_j) is the common factor
-// exp(2 pi i P_c) (one accurate sincospi) times exp(2 pi i dP_j) for the
-// small per-spacecraft remainder (short Taylor series).
+// exp(2 pi i P_c) (one accurate sincospi, applied once per sample to A and E)
+// times exp(2 pi i dP_j) for the small per-spacecraft remainder.
 //
-// Link transfer a sinc(X) exp(-iX) = a sum_k (-2iX)^k/(k+1)! is evaluated as
-// two Horner polynomials in y = -4X^2 (even and odd k), with the number of
-// terms chosen per candidate from the largest X = f/f* it can reach.
+// Link transfer sinc(X) exp(-iX) = sum_k (-2iX)^k/(k+1)! is evaluated as two
+// Horner polynomials in y = -4X^2 (even and odd k), with the number of terms
+// chosen per candidate from the largest X = f/f* it can reach.
+//
+// Execution: a persistent kernel whose warps take work items (a window and up
+// to 32 of its candidates) from a global queue, most expensive first.  Per
+// item the warp sets the candidates up one per lane, then evaluates them one
+// after the other: lane l computes samples n = R brev5(l) + r (R = N/32), the
+// 32-point FFT stage runs across lanes with shuffles (bit-reversed input,
+// natural output), a lane twiddle and an R-point FFT in registers finish the
+// transform, and lane l then holds bins l + 32 k1, so the window reads are
+// coalesced.  A preparation kernel forms <d|d>, the scale sigma and the float
+// copy of every window once per launch.
 #include <cmath>
 
 #include "gb_internal.cuh"
@@ -52,9 +62,9 @@ struct CandMix {
     double A;
 };
 
-struct Win32 {
-    float2 dA, dE;   // data scaled by sigma
-    float wA, wE;    // 1/S scaled by 1/sigma^2
+// per-candidate sums left by the warp for the lane-parallel epilogue
+struct Epi {
+    float dh_hi, dh_lo, hh_hi, hh_lo;
 };
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
@@ -137,7 +147,7 @@ __device__ void setup_mixed(const double* th, double T, double fstar, CandMix& c
     c.J = xmax <= 0.489 ? 4 : xmax <= 1.34 ? 7 : xmax <= 2.35 ? 10 : 0;
 }
 
-// a-free link transfer sinc(X) exp(-iX), J+1 terms of each series
+// sinc(X) exp(-iX), J+1 terms of each series (J = 0: direct evaluation)
 template <int J>
 __device__ __forceinline__ float2 link_transfer(float X) {
     if (J == 0) {
@@ -178,16 +188,22 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = (a - (s - bb)) + (b - bb);
 }
 
+// Slow part of one candidate: lane l, step r computes sample n = R brev5(l) + r
+// and writes A, E to buf{A,E}[r*32 + l] (conflict-free).
 template <int J>
-__device__ void slow_part_mixed(const CandMix& c, const OrbitTables32& tab, int N, int logN, float2* bufA,
-                                float2* bufE, int lane) {
+__device__ void slow_part_mixed(const CandMix& c, const OrbitTables32& tab, int N, float2* bufA, float2* bufE,
+                                int lane) {
+    const int R = N >> 5;
     const float invN = 1.0f / (float)N;
     const float r2 = 0.70710678118654752f, r6 = 0.40824829046386302f;
-    for (int n = lane; n < N; n += 32) {
-        const float u = (float)n * invN;
+    const int nb = R * brev5(lane);
+    for (int r = 0; r < R; ++r) {
+        const int p = r * 32 + lane;
+        const float u = (float)(nb + r) * invN;
         const float uu = u * u;
-        const float cah = __ldg(tab.calpha + n), cal = __ldg(tab.calpha + N + n);
-        const float sah = __ldg(tab.salpha + n), sal = __ldg(tab.salpha + N + n);
+        const float4 g0 = __ldg(tab.g + p), g1 = __ldg(tab.g + N + p);
+        const float4 g2 = __ldg(tab.g + 2 * N + p), g3 = __ldg(tab.g + 3 * N + p);
+        const float cah = g3.x, cal = g3.y, sah = g3.z, sal = g3.w;
         // double-word products, reduced modulo one
         float p1 = c.c1h * u;
         const float e1 = fmaf(c.c1h, u, -p1) + c.c1l * u;
@@ -218,26 +234,34 @@ __device__ void slow_part_mixed(const CandMix& c, const OrbitTables32& tab, int 
         const float tl = 6.2831853071795865f * Pl;
         const float2 ePc = make_float2(fmaf(-tl, sPc, cPc), fmaf(tl, cPc, sPc));
         const float f = fmaf(c.fdT, u, c.f0);
+        // k.rho_j: the third from the other two (the centroid is the guiding centre)
+        float krho[3];
+        krho[0] = fmaf(c.k0, g0.x, fmaf(c.k1, g0.y, c.k2 * g0.z));
+        krho[1] = fmaf(c.k0, g0.w, fmaf(c.k1, g1.x, c.k2 * g1.y));
+        krho[2] = -krho[0] - krho[1];
         float2 rx[3];
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            const float rho = fmaf(c.k0, __ldg(tab.rho + (j * 3 + 0) * N + n),
-                                   fmaf(c.k1, __ldg(tab.rho + (j * 3 + 1) * N + n),
-                                        c.k2 * __ldg(tab.rho + (j * 3 + 2) * N + n)));
-            const float kap = K + rho;
-            const float dP = fmaf(-f, rho, c.fdh * kap * kap);
+            const float kap = K + krho[j];
+            const float dP = fmaf(-f, krho[j], c.fdh * kap * kap);
             rx[j] = cis_small(dP);   // the common factor exp(2 pi i P_c) is applied once, below
         }
         const float a = fmaf(c.a1, u, c.a0);
+        // projections of the arms on k, u, v; arm 2->0 closes the triangle
+        float kn_[3], nu_[3], nv_[3];
+        kn_[0] = fmaf(c.k0, g1.z, fmaf(c.k1, g1.w, c.k2 * g2.x));
+        nu_[0] = fmaf(c.u0, g1.z, fmaf(c.u1, g1.w, c.u2 * g2.x));
+        nv_[0] = fmaf(c.v0, g1.z, fmaf(c.v1, g1.w, c.v2 * g2.x));
+        kn_[1] = fmaf(c.k0, g2.y, fmaf(c.k1, g2.z, c.k2 * g2.w));
+        nu_[1] = fmaf(c.u0, g2.y, fmaf(c.u1, g2.z, c.u2 * g2.w));
+        nv_[1] = fmaf(c.v0, g2.y, fmaf(c.v1, g2.z, c.v2 * g2.w));
+        kn_[2] = -kn_[0] - kn_[1];
+        nu_[2] = -nu_[0] - nu_[1];
+        nv_[2] = -nv_[0] - nv_[1];
         float2 zp[3], zm[3];   // arm a: link along +n (receiver rc[a]) and -n (receiver em[a])
 #pragma unroll
         for (int arm = 0; arm < 3; ++arm) {
-            const float nx = __ldg(tab.arm + (arm * 3 + 0) * N + n);
-            const float ny = __ldg(tab.arm + (arm * 3 + 1) * N + n);
-            const float nz = __ldg(tab.arm + (arm * 3 + 2) * N + n);
-            const float kn = fmaf(c.k0, nx, fmaf(c.k1, ny, c.k2 * nz));
-            const float nu = fmaf(c.u0, nx, fmaf(c.u1, ny, c.u2 * nz));
-            const float nv = fmaf(c.v0, nx, fmaf(c.v1, ny, c.v2 * nz));
+            const float kn = kn_[arm], nu = nu_[arm], nv = nv_[arm];
             const float Fp = (nu - nv) * (nu + nv);
             const float Fx = 2.0f * nu * nv;
             const float2 G = make_float2(fmaf(c.gpr, Fp, c.gxr * Fx), fmaf(c.gpi, Fp, c.gxi * Fx));
@@ -253,53 +277,100 @@ __device__ void slow_part_mixed(const CandMix& c, const OrbitTables32& tab, int 
         const float2 Xp = caddf(csubf(zm[0], zp[2]), cmulf(D, csubf(zp[0], zm[2])));
         const float2 Yp = caddf(csubf(zm[1], zp[0]), cmulf(D, csubf(zp[1], zm[0])));
         const float2 Zp = caddf(csubf(zm[2], zp[1]), cmulf(D, csubf(zp[2], zm[1])));
-        // F = -i a (1 - D^2) = 2 a sin(f/f*) D with sin(f/f*) = -Im D: no
-        // cancellation in 1 - D^2 at low frequency
+        // -i a (1 - D^2) = 2 a sin(f/f*) D with sin(f/f*) = -Im D (no
+        // cancellation at low frequency), times the common phase factor
         const float sa2 = -2.0f * a * D.y;
         const float2 F = cmulf(make_float2(sa2 * D.x, sa2 * D.y), ePc);
         const float2 Ap = make_float2((Zp.x - Xp.x) * r2, (Zp.y - Xp.y) * r2);
         const float2 Ep = make_float2((Xp.x - 2.0f * Yp.x + Zp.x) * r6, (Xp.y - 2.0f * Yp.y + Zp.y) * r6);
-        const int br = (int)(__brev((unsigned)n) >> (32 - logN));
-        bufA[br] = cmulf(F, Ap);
-        bufE[br] = cmulf(F, Ep);
+        bufA[p] = cmulf(F, Ap);
+        bufE[p] = cmulf(F, Ep);
     }
 }
 
-__device__ void fft_mixed(int N, int logN, const float2* tw, float2* bufA, float2* bufE, int lane) {
-    __syncwarp();
-    for (int s = 0; s < logN; ++s) {
-        const int h = 1 << s;
-        const int tstride = kTwiddles >> s;
-        for (int b = lane; b < N / 2; b += 32) {
-            const int j = b & (h - 1);
-            const int i0 = ((b >> s) << (s + 1)) + j;
-            const int i1 = i0 + h;
-            const float2 w = tw[j * tstride];
-            const float2 ua = bufA[i0], va = cmulf(w, bufA[i1]);
-            bufA[i0] = caddf(ua, va);
-            bufA[i1] = csubf(ua, va);
-            const float2 ue = bufE[i0], ve = cmulf(w, bufE[i1]);
-            bufE[i0] = caddf(ue, ve);
-            bufE[i1] = csubf(ue, ve);
-        }
-        __syncwarp();
-    }
-}
-
-__device__ void template_mixed(const CandMix& c, const OrbitTables32& tab, int N, int logN, const float2* tw,
-                               float2* bufA, float2* bufE, int lane) {
+__device__ void slow_part_dispatch(const CandMix& c, const OrbitTables32& tab, int N, float2* bufA, float2* bufE,
+                                   int lane) {
     switch (c.J) {
-        case 4: slow_part_mixed<4>(c, tab, N, logN, bufA, bufE, lane); break;
-        case 7: slow_part_mixed<7>(c, tab, N, logN, bufA, bufE, lane); break;
-        case 10: slow_part_mixed<10>(c, tab, N, logN, bufA, bufE, lane); break;
-        default: slow_part_mixed<0>(c, tab, N, logN, bufA, bufE, lane); break;
+        case 4: slow_part_mixed<4>(c, tab, N, bufA, bufE, lane); break;
+        case 7: slow_part_mixed<7>(c, tab, N, bufA, bufE, lane); break;
+        case 10: slow_part_mixed<10>(c, tab, N, bufA, bufE, lane); break;
+        default: slow_part_mixed<0>(c, tab, N, bufA, bufE, lane); break;
     }
-    fft_mixed(N, logN, tw, bufA, bufE, lane);
 }
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+// Per-lane twiddles of the across-lane radix-2 stages (half size h = 2^s):
+// the upper lane of a pair multiplies its value by exp(-i pi (l mod h)/h).
+struct LaneTw {
+    float2 w[4];   // stages h = 2, 4, 8, 16 (h = 1 has twiddle 1)
+};
+
+__device__ __forceinline__ LaneTw lane_twiddles(int lane) {
+    LaneTw t;
+#pragma unroll
+    for (int s = 1; s < 5; ++s) {
+        const int h = 1 << s;
+        if (lane & h) {
+            float sn, cs;
+            sincospif((float)(lane & (h - 1)) / (float)h, &sn, &cs);
+            t.w[s - 1] = make_float2(cs, -sn);
+        } else {
+            t.w[s - 1] = make_float2(1.0f, 0.0f);
+        }
+    }
+    return t;
+}
+
+// 32-point DFT across the lanes: lane l holds element brev5(l) of the
+// sequence on entry and element l of its transform on exit (radix-2 DIT).
+__device__ __forceinline__ float2 lane_fft(float2 x, const LaneTw& tw, int lane) {
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int h = 1 << s;
+        const float2 u = s == 0 ? x : cmulf(x, tw.w[s - 1]);
+        const float2 v = make_float2(__shfl_xor_sync(0xffffffffu, u.x, h), __shfl_xor_sync(0xffffffffu, u.y, h));
+        x = (lane & h) ? csubf(v, u) : caddf(u, v);
+    }
+    return x;
+}
+
+// R-point DFT in registers, natural order in and out (radix-2 DIT with a
+// compile-time bit reversal); twiddles exp(-2 pi i j / R) from the table of
+// exp(-2 pi i k / 1024), k < 512.
+template <int R>
+__device__ __forceinline__ void reg_fft(float2 (&x)[R], const float2* __restrict__ tw1024) {
+    if constexpr (R > 1) {
+        constexpr int LR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : R == 16 ? 4 : 5;
+        float2 y[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            int b = 0;
+#pragma unroll
+            for (int k = 0; k < LR; ++k) b |= ((i >> k) & 1) << (LR - 1 - k);
+            y[b] = x[i];
+        }
+#pragma unroll
+        for (int s = 0; s < LR; ++s) {
+            const int h = 1 << s;
+#pragma unroll
+            for (int b = 0; b < R / 2; ++b) {
+                const int j = b & (h - 1);
+                const int i0 = ((b >> s) << (s + 1)) + j;
+                const int i1 = i0 + h;
+                float2 t;
+                if (j == 0) {
+                    t = y[i1];
+                } else if (4 * j == 2 * h) {   // exp(-i pi/2) = -i
+                    t = make_float2(y[i1].y, -y[i1].x);
+                } else {
+                    t = cmulf(__ldg(tw1024 + j * (512 / h)), y[i1]);
+                }
+                y[i1] = csubf(y[i0], t);
+                y[i0] = caddf(y[i0], t);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) x[i] = y[i];
+    }
 }
 
 __device__ __forceinline__ void kahan_add(float& sum, float& comp, float x) {
@@ -309,25 +380,67 @@ __device__ __forceinline__ void kahan_add(float& sum, float& comp, float x) {
     sum = t;
 }
 
-__global__ void __launch_bounds__(kWarpsMx * 32) loglik_mixed_kernel(
-    const gb_window_t* __restrict__ wins, const Tile* __restrict__ tiles, TabSet32 tabs,
-    const float2* __restrict__ tw_g, double T, double fstar, const double2* __restrict__ dA,
-    const double2* __restrict__ dE, const double* __restrict__ wA, const double* __restrict__ wE,
-    const double* __restrict__ theta, double* __restrict__ logL, double* __restrict__ dh_out,
-    double* __restrict__ hh_out, int* status, int n_max, int w_max) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* tw = (float2*)smem_raw;                               // kTwiddles
-    double* red = (double*)(tw + kTwiddles);                      // 2 * kWarpsMx
-    CandMix* cands = (CandMix*)(red + 2 * kWarpsMx);              // kWarpsMx * 32
-    Win32* ws = (Win32*)(cands + kWarpsMx * 32);                  // w_max
-    float2* bufs = (float2*)(ws + w_max);                         // kWarpsMx * 2 * n_max
+// Transform one channel (R values per lane in buf[r*32 + lane]) into bins
+// l + 32 k1 held in x[k1].
+template <int R>
+__device__ __forceinline__ void channel_fft(const float2* buf, const OrbitTables32& tab, const float2* tw1024,
+                                            const LaneTw& ltw, int lane, float2 (&x)[R]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = lane_fft(buf[r * 32 + lane], ltw, lane);
+#pragma unroll
+    for (int r = 1; r < R; ++r) x[r] = cmulf(x[r], __ldg(tab.ltw + r * 32 + lane));
+    reg_fft<R>(x, tw1024);
+}
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const Tile tile = tiles[blockIdx.x];
-    const gb_window_t win = wins[tile.win];
-    for (int i = threadIdx.x; i < kTwiddles; i += blockDim.x) tw[i] = tw_g[i];
+// FFT of both channels and the window inner products of one candidate.
+template <int R>
+__device__ void fft_inner(const float2* bufA, const float2* bufE, const OrbitTables32& tab, const float2* tw1024,
+                          const LaneTw& ltw, int lane, int off, int W, const Win32* __restrict__ pw, float& sdh,
+                          float& cdh, float& shh, float& chh) {
+    constexpr int N = 32 * R;
+    float2 x[R];
+#pragma unroll
+    for (int ch = 0; ch < 2; ++ch) {
+        channel_fft<R>(ch == 0 ? bufA : bufE, tab, tw1024, ltw, lane, x);
+#pragma unroll
+        for (int k1 = 0; k1 < R; ++k1) {
+            const int k = lane + 32 * k1;
+            const int m = k < N / 2 ? k : k - N;
+            const int kk = off + m;
+            if (kk >= 0 && kk < W) {
+                const Win32 v = pw[kk];
+                const float2 d = ch == 0 ? v.dA : v.dE;
+                const float w = ch == 0 ? v.wA : v.wE;
+                kahan_add(sdh, cdh, w * fmaf(d.x, x[k1].x, d.y * x[k1].y));
+                kahan_add(shh, chh, w * fmaf(x[k1].x, x[k1].x, x[k1].y * x[k1].y));
+            }
+        }
+    }
+}
 
-    // <d|d> and the window scale sigma^2 = max w (block-wide, fixed order)
+// Compensated warp sum of Kahan pairs: returns hi + lo on every lane.
+__device__ __forceinline__ void warp_sum2(float sum, float comp, float& hi, float& lo) {
+    hi = sum;
+    lo = -comp;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        float s, e;
+        two_sum(hi, h2, s, e);
+        hi = s;
+        lo = lo + l2 + e;
+    }
+}
+
+__global__ void prep_mixed_kernel(const gb_window_t* __restrict__ wins, WinMeta* __restrict__ meta,
+                                  Win32* __restrict__ prep, const double2* __restrict__ dA,
+                                  const double2* __restrict__ dE, const double* __restrict__ wA,
+                                  const double* __restrict__ wE, double T, int* head) {
+    __shared__ double s_acc[32], s_max[32];
+    const int w = blockIdx.x;
+    if (w == 0 && threadIdx.x < 2) head[threadIdx.x] = 0;   // both work queues
+    const gb_window_t win = wins[w];
     double acc = 0.0, wmax = 0.0;
     for (int i = threadIdx.x; i < win.W; i += blockDim.x) {
         const double2 a = dA[win.data_off + i], e = dE[win.data_off + i];
@@ -335,21 +448,28 @@ __global__ void __launch_bounds__(kWarpsMx * 32) loglik_mixed_kernel(
         acc += wa * (a.x * a.x + a.y * a.y) + we * (e.x * e.x + e.y * e.y);
         wmax = fmax(wmax, fmax(wa, we));
     }
-    acc = warp_sum_d(acc);
-    for (int o = 16; o > 0; o >>= 1) wmax = fmax(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        wmax = fmax(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     if (lane == 0) {
-        red[warp] = acc;
-        red[kWarpsMx + warp] = wmax;
+        s_acc[warp] = acc;
+        s_max[warp] = wmax;
     }
     __syncthreads();
     double dd = 0.0, sig2 = 0.0;
-    for (int w = 0; w < kWarpsMx; ++w) {
-        dd += red[w];
-        sig2 = fmax(sig2, red[kWarpsMx + w]);
+    for (int i = 0; i < nw; ++i) {
+        dd += s_acc[i];
+        sig2 = fmax(sig2, s_max[i]);
     }
-    dd *= 4.0 / T;
     if (!(sig2 > 0.0) || !isfinite(sig2)) sig2 = 1.0;
     const double sig = sqrt(sig2), isig2 = 1.0 / sig2;
+    const long long po = meta[w].prep_off;
+    if (threadIdx.x == 0) {
+        meta[w].dd = dd * (4.0 / T);
+        meta[w].sig = sig;
+    }
     for (int i = threadIdx.x; i < win.W; i += blockDim.x) {
         const double2 a = dA[win.data_off + i], e = dE[win.data_off + i];
         Win32 v;
@@ -357,90 +477,113 @@ __global__ void __launch_bounds__(kWarpsMx * 32) loglik_mixed_kernel(
         v.dE = make_float2((float)(e.x * sig), (float)(e.y * sig));
         v.wA = (float)(wA[win.data_off + i] * isig2);
         v.wE = (float)(wE[win.data_off + i] * isig2);
-        ws[i] = v;
+        prep[po + i] = v;
     }
-    __syncthreads();
+}
 
-    const int N = win.N;
-    const int logN = 31 - __clz(N);
-    const OrbitTables32 tab = tabs.t[logN - 5];
-    float2* bufA = bufs + (size_t)warp * 2 * n_max;
+// RMAX: largest R = N/32 this instantiation handles (8: N <= 256; 32: N = 512, 1024)
+template <int RMAX>
+__global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? 4 : 2) loglik_mixed_kernel(
+    const gb_window_t* __restrict__ wins, const WinMeta* __restrict__ meta, const Win32* __restrict__ prep,
+    const Tile* __restrict__ items, int n_items, int* head, TabSet32 tabs, const float2* __restrict__ tw1024,
+    double T, double fstar, const double* __restrict__ theta, double* __restrict__ logL,
+    double* __restrict__ dh_out, double* __restrict__ hh_out, int* status, int n_max) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    CandMix* cands = (CandMix*)smem_raw + warp * 32;
+    Epi* epi = (Epi*)((CandMix*)smem_raw + kWarpsMx * 32) + warp * 32;
+    float2* bufA = (float2*)((Epi*)((CandMix*)smem_raw + kWarpsMx * 32) + kWarpsMx * 32) + (size_t)warp * 2 * n_max;
     float2* bufE = bufA + n_max;
-    CandMix* mycand = cands + warp * 32;
-    const int64_t tlen = tile.c_end - tile.c_begin;
-    const int64_t grp = (tlen + kWarpsMx - 1) / kWarpsMx;
-    const int64_t c_lo = tile.c_begin + (int64_t)warp * grp;
-    const int64_t c_hi = min(tile.c_end, c_lo + grp);
-    if (c_lo >= c_hi) return;
-    if (c_lo + lane < c_hi) setup_mixed(theta + 8 * (c_lo + lane), T, fstar, mycand[lane]);
-    __syncwarp();
-    const double s_dh = 2.0 * sig / (double)N;
-    const double s_hh = T * sig2 / ((double)N * (double)N);
-    for (int64_t cidx = c_lo; cidx < c_hi; ++cidx) {
-        const CandMix& c = mycand[cidx - c_lo];
-        if (c.bad) {
-            if (lane == 0) {
+    const LaneTw ltw = lane_twiddles(lane);
+
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(head, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_items) break;
+        const Tile t = items[item];
+        const gb_window_t win = wins[t.win];
+        const WinMeta wm = meta[t.win];
+        const Win32* pw = prep + wm.prep_off;
+        const int N = win.N;
+        const OrbitTables32 tab = tabs.t[__ffs(N) - 6];
+        const int cnt = (int)(t.c_end - t.c_begin);
+        if (lane < cnt) setup_mixed(theta + 8 * (t.c_begin + lane), T, fstar, cands[lane]);
+        __syncwarp();
+        for (int i = 0; i < cnt; ++i) {
+            const CandMix& c = cands[i];
+            float sdh = 0.0f, cdh = 0.0f, shh = 0.0f, chh = 0.0f;
+            if (!c.bad) {
+                slow_part_dispatch(c, tab, N, bufA, bufE, lane);
+                __syncwarp();
+                const long long off64 = c.q - win.k0;
+                if (off64 > -(long long)N && off64 < (long long)win.W + N) {
+                    const int off = (int)off64;
+                    if constexpr (RMAX <= 8) {
+                        switch (N) {
+                            case 32: fft_inner<1>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh); break;
+                            case 64: fft_inner<2>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh); break;
+                            case 128: fft_inner<4>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh); break;
+                            default: fft_inner<8>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh); break;
+                        }
+                    } else {
+                        if (N == 512)
+                            fft_inner<16>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh);
+                        else
+                            fft_inner<32>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh);
+                    }
+                }
+                __syncwarp();
+            }
+            float dhh, dhl, hhh, hhl;
+            warp_sum2(sdh, cdh, dhh, dhl);
+            warp_sum2(shh, chh, hhh, hhl);
+            if (lane == 0) epi[i] = Epi{dhh, dhl, hhh, hhl};
+        }
+        __syncwarp();
+        // lane-parallel epilogue in double, coalesced stores
+        if (lane < cnt) {
+            const CandMix& c = cands[lane];
+            const int64_t cidx = t.c_begin + lane;
+            if (c.bad) {
                 logL[cidx] = nan("");
                 if (dh_out) dh_out[cidx] = nan("");
                 if (hh_out) hh_out[cidx] = nan("");
                 atomicOr(status, 1);
+            } else {
+                const Epi s = epi[lane];
+                const double Sdh = (double)s.dh_hi + (double)s.dh_lo;
+                const double Shh = (double)s.hh_hi + (double)s.hh_lo;
+                const double dh = c.A * (2.0 * wm.sig / (double)N) * Sdh;
+                const double hh = (c.A * c.A) * (T * wm.sig * wm.sig / ((double)N * (double)N)) * Shh;
+                logL[cidx] = dh - 0.5 * hh - 0.5 * wm.dd;
+                if (dh_out) dh_out[cidx] = dh;
+                if (hh_out) hh_out[cidx] = hh;
             }
-            continue;
-        }
-        template_mixed(c, tab, N, logN, tw, bufA, bufE, lane);
-        const int64_t off64 = c.q - N / 2 - win.k0;
-        float sdh = 0.0f, cdh = 0.0f, shh = 0.0f, chh = 0.0f;
-        if (off64 > -(int64_t)N && off64 < (int64_t)win.W) {
-            const int off = (int)off64;
-            for (int m = lane; m < N; m += 32) {
-                const int kk = off + m;
-                if (kk >= 0 && kk < win.W) {
-                    const int idx = (m + N / 2) & (N - 1);
-                    const float2 hA = bufA[idx], hE = bufE[idx];
-                    const Win32 v = ws[kk];
-                    kahan_add(sdh, cdh, fmaf(v.wA, fmaf(v.dA.x, hA.x, v.dA.y * hA.y),
-                                             v.wE * fmaf(v.dE.x, hE.x, v.dE.y * hE.y)));
-                    kahan_add(shh, chh, fmaf(v.wA, fmaf(hA.x, hA.x, hA.y * hA.y),
-                                             v.wE * fmaf(hE.x, hE.x, hE.y * hE.y)));
-                }
-            }
-        }
-        const double Sdh = warp_sum_d((double)sdh - (double)cdh);
-        const double Shh = warp_sum_d((double)shh - (double)chh);
-        if (lane == 0) {
-            const double dh = c.A * s_dh * Sdh;
-            const double hh = c.A * c.A * s_hh * Shh;
-            logL[cidx] = dh - 0.5 * hh - 0.5 * dd;
-            if (dh_out) dh_out[cidx] = dh;
-            if (hh_out) hh_out[cidx] = hh;
         }
         __syncwarp();
     }
 }
 
 __global__ void __launch_bounds__(kWarpsMx * 32) waveform_mixed_kernel(
-    OrbitTables32 tab, const float2* __restrict__ tw_g, double T, double fstar, int N,
-    const double* __restrict__ theta, int64_t B, int group, double2* __restrict__ hA,
-    double2* __restrict__ hE, int64_t* __restrict__ q_out, int* status) {
+    OrbitTables32 tab, const float2* __restrict__ tw1024, double T, double fstar, int N,
+    const double* __restrict__ theta, int64_t B, int group, double2* __restrict__ hA, double2* __restrict__ hE,
+    int64_t* __restrict__ q_out, int* status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* tw = (float2*)smem_raw;
-    CandMix* cands = (CandMix*)(tw + kTwiddles);
-    float2* bufs = (float2*)(cands + kWarpsMx * 32);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < kTwiddles; i += blockDim.x) tw[i] = tw_g[i];
-    __syncthreads();
-    const int logN = 31 - __clz(N);
-    float2* bufA = bufs + (size_t)warp * 2 * N;
+    CandMix* cands = (CandMix*)smem_raw + warp * 32;
+    float2* bufA = (float2*)((CandMix*)smem_raw + kWarpsMx * 32) + (size_t)warp * 2 * N;
     float2* bufE = bufA + N;
-    CandMix* mycand = cands + warp * 32;
+    const LaneTw ltw = lane_twiddles(lane);
     const int64_t c_lo = ((int64_t)blockIdx.x * kWarpsMx + warp) * group;
     const int64_t c_hi = min(B, c_lo + group);
     if (c_lo >= c_hi) return;
-    if (c_lo + lane < c_hi) setup_mixed(theta + 8 * (c_lo + lane), T, fstar, mycand[lane]);
+    if (c_lo + lane < c_hi) setup_mixed(theta + 8 * (c_lo + lane), T, fstar, cands[lane]);
     __syncwarp();
+    const int R = N / 32;
     const double scale = T / (2.0 * (double)N);
     for (int64_t b = c_lo; b < c_hi; ++b) {
-        const CandMix& c = mycand[b - c_lo];
+        const CandMix& c = cands[b - c_lo];
         double2* outA = hA + b * N;
         double2* outE = hE + b * N;
         if (c.bad) {
@@ -451,17 +594,36 @@ __global__ void __launch_bounds__(kWarpsMx * 32) waveform_mixed_kernel(
             }
             continue;
         }
-        template_mixed(c, tab, N, logN, tw, bufA, bufE, lane);
+        slow_part_dispatch(c, tab, N, bufA, bufE, lane);
+        __syncwarp();
         const double s = scale * c.A;
-        for (int m = lane; m < N; m += 32) {
-            const int idx = (m + N / 2) & (N - 1);
-            const float2 a = bufA[idx], e = bufE[idx];
-            outA[m] = make_double2(s * a.x, s * a.y);
-            outE[m] = make_double2(s * e.x, s * e.y);
+        for (int ch = 0; ch < 2; ++ch) {
+            float2 x[32];
+            const float2* buf = ch == 0 ? bufA : bufE;
+            double2* out = ch == 0 ? outA : outE;
+            switch (R) {
+                case 1: channel_fft<1>(buf, tab, tw1024, ltw, lane, *(float2(*)[1])x); break;
+                case 2: channel_fft<2>(buf, tab, tw1024, ltw, lane, *(float2(*)[2])x); break;
+                case 4: channel_fft<4>(buf, tab, tw1024, ltw, lane, *(float2(*)[4])x); break;
+                case 8: channel_fft<8>(buf, tab, tw1024, ltw, lane, *(float2(*)[8])x); break;
+                case 16: channel_fft<16>(buf, tab, tw1024, ltw, lane, *(float2(*)[16])x); break;
+                default: channel_fft<32>(buf, tab, tw1024, ltw, lane, *(float2(*)[32])x); break;
+            }
+            for (int k1 = 0; k1 < R; ++k1) {
+                const int k = lane + 32 * k1;
+                const int m = (k + N / 2) & (N - 1);   // entry m stands for bin q - N/2 + m
+                out[m] = make_double2(s * x[k1].x, s * x[k1].y);
+            }
         }
         if (lane == 0) q_out[b] = c.q;
         __syncwarp();
     }
+}
+
+int resident_blocks(const void* kernel, int threads, size_t smem) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) n = 1;
+    return n;
 }
 
 }  // namespace
@@ -470,25 +632,47 @@ int launch_loglik_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const d
                         const double* wE, const double* theta, double* logL, double* dh, double* hh,
                         cudaStream_t s) {
     if (plan.n_tiles == 0) return GB_OK;
-    const size_t smem = sizeof(float2) * kTwiddles + sizeof(double) * 2 * kWarpsMx +
-                        sizeof(CandMix) * kWarpsMx * 32 + sizeof(Win32) * (size_t)plan.w_max +
-                        sizeof(float2) * kWarpsMx * 2 * (size_t)plan.n_max;
-    cudaError_t e = cudaFuncSetAttribute(loglik_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_error(ctx, e, "loglik_mixed: smem attribute");
-    loglik_mixed_kernel<<<plan.n_tiles, kWarpsMx * 32, smem, s>>>(
-        plan.d_win, plan.d_tiles, tabset32(ctx), (const float2*)ctx->d_tw32, ctx->obs.T_obs,
-        transfer_frequency(ctx), (const double2*)dA, (const double2*)dE, wA, wE, theta, logL, dh, hh,
-        ctx->d_status, plan.n_max, plan.w_max);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_error(ctx, e, "loglik_mixed launch");
+    prep_mixed_kernel<<<plan.n_win, 256, 0, s>>>(plan.d_win, plan.d_meta, plan.d_prep, (const double2*)dA,
+                                                 (const double2*)dE, wA, wE, ctx->obs.T_obs, plan.d_head);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(ctx, e, "prep_mixed launch");
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    // two persistent launches drain the two queues: N >= 512 items, then N <= 256
+    const int n_small = plan.n_tiles - plan.n_large;
+    for (int part = 0; part < 2; ++part) {
+        const int n_items = part == 0 ? plan.n_large : n_small;
+        if (n_items == 0) continue;
+        const int nmax = part == 0 ? 1024 : (plan.n_max < 256 ? plan.n_max : 256);
+        const size_t smem = (sizeof(CandMix) + sizeof(Epi)) * kWarpsMx * 32 + sizeof(float2) * kWarpsMx * 2 * (size_t)nmax;
+        const void* kfn = part == 0 ? (const void*)loglik_mixed_kernel<32> : (const void*)loglik_mixed_kernel<8>;
+        e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_error(ctx, e, "loglik_mixed: smem attribute");
+        int grid = sms * resident_blocks(kfn, kWarpsMx * 32, smem);
+        const int need = (n_items + kWarpsMx - 1) / kWarpsMx;
+        if (grid > need) grid = need;
+        const Tile* items = plan.d_tiles + (part == 0 ? 0 : plan.n_large);
+        int* head = plan.d_head + (part == 0 ? 1 : 0);
+        if (part == 0)
+            loglik_mixed_kernel<32><<<grid, kWarpsMx * 32, smem, s>>>(
+                plan.d_win, plan.d_meta, plan.d_prep, items, n_items, head, tabset32(ctx),
+                (const float2*)ctx->d_tw32, ctx->obs.T_obs, transfer_frequency(ctx), theta, logL, dh, hh,
+                ctx->d_status, nmax);
+        else
+            loglik_mixed_kernel<8><<<grid, kWarpsMx * 32, smem, s>>>(
+                plan.d_win, plan.d_meta, plan.d_prep, items, n_items, head, tabset32(ctx),
+                (const float2*)ctx->d_tw32, ctx->obs.T_obs, transfer_frequency(ctx), theta, logL, dh, hh,
+                ctx->d_status, nmax);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_error(ctx, e, "loglik_mixed launch");
+    }
     return GB_OK;
 }
 
 int launch_waveform_mixed(gb_ctx* ctx, const double* theta, int64_t B, int N, double* hA, double* hE,
                           int64_t* q, cudaStream_t s) {
     if (B == 0) return GB_OK;
-    const size_t smem =
-        sizeof(float2) * kTwiddles + sizeof(CandMix) * kWarpsMx * 32 + sizeof(float2) * kWarpsMx * 2 * (size_t)N;
+    const size_t smem = sizeof(CandMix) * kWarpsMx * 32 + sizeof(float2) * kWarpsMx * 2 * (size_t)N;
     cudaError_t e = cudaFuncSetAttribute(waveform_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_error(ctx, e, "waveform_mixed: smem attribute");
     int sms = 152;

@@ -273,6 +273,28 @@ def test_mh_matches_oracle_full_size(ctx, literal):
     assert np.array_equal(a, oa)
 
 
+@pytest.mark.parametrize("T,literal", [(1.0, False), (3.0, False), (3.0, True)])
+def test_mh_near_ties_match_oracle(ctx, T, literal):
+    # log u placed exactly on, or one ulp below, the acceptance boundary
+    # Delta of the current state, so that the decision needs the full double
+    # expression; the oracle run on the same inputs fixes the expected chain
+    rng = np.random.default_rng(21)
+    n = 4000
+    L = rng.normal(-40.0, 5.0, n)
+    G = rng.normal(0.0, 1.0, n)
+    w = (L - G) if literal else (L / T - G)
+    U = np.log(rng.uniform(0, 1, n))
+    c = 0
+    for i in range(1, n):
+        d = (w[i] - w[c]) / T if literal else w[i] - w[c]
+        if d < 0 and rng.uniform() < 0.5:
+            U[i] = d if rng.uniform() < 0.5 else np.nextafter(d, -np.inf)
+        if U[i] < min(0.0, d):
+            c = i
+    cg, ag, co, ao = _mh_both(ctx, L[None], G[None], U[None], np.array([T]), literal)
+    assert np.array_equal(cg, co) and np.array_equal(ag, ao)
+
+
 def test_mh_golden_and_edge_cases(ctx):
     path = os.path.join(os.path.dirname(__file__), "golden", "mh_alg4_worked.txt")
     g = {}
