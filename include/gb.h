@@ -173,6 +173,38 @@ int gb_mh_independence(gb_ctx_t* ctx, int32_t n_chains, int32_t n,
                        const double* temperature, int32_t literal,
                        int32_t* chain_idx, int32_t* n_accept, void* stream);
 
+/* Allocation-free variant of gb_loglik with prec = GB_MIXED.
+ *
+ * The paper has no counterpart to this entry point.  It serves callers that
+ * must not allocate device memory while they run: a plugin inside a host
+ * application that hands out all device memory through its own pool, or a
+ * latency-critical loop that cannot accept the device-wide synchronisation
+ * that cudaMalloc and cudaFree imply.  It needs no context.
+ *
+ * Windows, data, candidates and outputs are those of gb_loglik (device
+ * pointers, host window array), and so are the results.  All scratch memory
+ * (geometry tables and twiddles, window descriptors and work items,
+ * per-window values, float copies of the windows, work-queue heads) lives in
+ * one static device array of about 8.6 MB, which every GPU that loads the
+ * library holds until the process exits.  Limits: n_win <= 4096, the windows'
+ * W add up to at most 262144 bins, at most 65536 work items (about two
+ * million candidates); beyond them the call returns GB_EINVAL with a message.
+ *
+ * The call runs on the current CUDA device.  Its first call on a device, and
+ * any call with a different T_obs or arm_L, also sets the device up: it takes
+ * the device address of the static array and builds the tables into it.
+ * Make that first call before any stream capture.  Every call shares the one
+ * array and leaves its contents behind; what must start at zero is reset by
+ * the call itself.  Calls that overlap on the GPU (other streams, other host
+ * threads) race on the array: the caller must serialise them.  Non-finite
+ * parameters give NaN outputs.  err (may be NULL) receives a message of at
+ * most err_len bytes when the call fails. */
+int gb_loglik_mixed_noalloc(const gb_obs_t* obs, const gb_window_t* win, int32_t n_win,
+                            const double* dA, const double* dE, const double* wA, const double* wE,
+                            int64_t n_bins, const double* theta, int64_t n_rows,
+                            double* logL, double* dh, double* hh, void* stream,
+                            char* err, int32_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -52,6 +52,8 @@ _SIGNATURES = {
     "gb_loglik_grad": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _I64, _P,
                                       _I64, _P, _P, _P]),
     "gb_mh_independence": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, _I32, _P, _P, _P]),
+    "gb_loglik_mixed_noalloc": (ctypes.c_int, [ctypes.POINTER(Obs), ctypes.POINTER(Window), _I32, _P, _P, _P, _P,
+                                               _I64, _P, _I64, _P, _P, _P, _P, ctypes.c_char_p, _I32]),
 }
 
 

@@ -90,6 +90,18 @@ __global__ void build_twiddles_kernel(double* tw64, float* tw32) {
     tw32[2 * k + 1] = (float)(-s);
 }
 
+// Build the geometry tables of every size and the twiddles into memory the
+// caller provides (laid out like a context's), asynchronously on `s`.
+cudaError_t build_tables_into(double T, double L, double* const tab64[kNumSizes], float* const tab32[kNumSizes],
+                              double* tw64, float* tw32, cudaStream_t s) {
+    for (int i = 0; i < kNumSizes; ++i) {
+        const int N = 32 << i;
+        build_tables_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, T, L, tab64[i], tab32[i]);
+    }
+    build_twiddles_kernel<<<(kTwiddles + 127) / 128, 128, 0, s>>>(tw64, tw32);
+    return cudaGetLastError();
+}
+
 constexpr int kTab64PerN = 18;   // doubles per sample
 constexpr int kTab32PerN = 18;   // floats per sample: 4 float4 + lane twiddles
 

@@ -133,6 +133,8 @@ namespace gb {
 int set_error(gb_ctx* ctx, int code, const std::string& msg);
 int cuda_error(gb_ctx* ctx, cudaError_t e, const char* what);
 
+cudaError_t build_tables_into(double T, double L, double* const tab64[kNumSizes], float* const tab32[kNumSizes],
+                              double* tw64, float* tw32, cudaStream_t s);
 OrbitTables64 tables64(const gb_ctx* ctx, int N);
 OrbitTables32 tables32(const gb_ctx* ctx, int N);
 TabSet64 tabset64(const gb_ctx* ctx);

@@ -689,3 +689,191 @@ int launch_waveform_mixed(gb_ctx* ctx, const double* theta, int64_t B, int N, do
 }
 
 }  // namespace gb
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the mixed-precision likelihood.
+//
+// Everything the kernels above need beyond the caller's inputs and outputs --
+// geometry tables and twiddles, the window descriptors and work items, the
+// per-window values and float copies, the work-queue heads -- lives in one
+// file-scope device array, so a call allocates no memory at all.
+// ---------------------------------------------------------------------------
+#include <cstring>
+#include <mutex>
+
+namespace gb {
+namespace {
+
+constexpr int kNaMaxWindows = 4096;
+constexpr long long kNaMaxBins = 262144;
+constexpr int kNaMaxItems = 65536;
+constexpr size_t kNaAlign = 256;
+constexpr size_t na_round(size_t x) { return (x + kNaAlign - 1) / kNaAlign * kNaAlign; }
+constexpr size_t kNaSamples = 32 + 64 + 128 + 256 + 512 + 1024;
+constexpr size_t kNaOffTab64 = 0;
+constexpr size_t kNaOffTab32 = na_round(kNaOffTab64 + sizeof(double) * 18 * kNaSamples);
+constexpr size_t kNaOffTw64 = na_round(kNaOffTab32 + sizeof(float) * 18 * kNaSamples);
+constexpr size_t kNaOffTw32 = na_round(kNaOffTw64 + sizeof(double) * 2 * kTwiddles);
+constexpr size_t kNaOffWin = na_round(kNaOffTw32 + sizeof(float) * 2 * kTwiddles);
+constexpr size_t kNaOffItems = na_round(kNaOffWin + sizeof(gb_window_t) * kNaMaxWindows);
+constexpr size_t kNaOffMeta = na_round(kNaOffItems + sizeof(Tile) * kNaMaxItems);
+constexpr size_t kNaOffPrep = na_round(kNaOffMeta + sizeof(WinMeta) * kNaMaxWindows);
+constexpr size_t kNaOffHead = na_round(kNaOffPrep + sizeof(Win32) * kNaMaxBins);
+constexpr size_t kNaBytes = na_round(kNaOffHead + 4 * sizeof(int));   // two queue heads, status
+
+// 8.6 MB per device, kept until the process exits
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+struct NaDevice {
+    unsigned char* base = nullptr;   // device address of g_noalloc_scratch
+    double T = 0.0, L = 0.0;         // observation the tables were built for
+};
+constexpr int kNaMaxDevices = 64;
+NaDevice g_na_dev[kNaMaxDevices];
+std::mutex g_na_mutex;
+Tile g_na_items[kNaMaxItems];          // host staging of the work items
+WinMeta g_na_meta[kNaMaxWindows];
+
+int na_fail(char* err, int err_len, int code, const char* msg) {
+    if (err && err_len > 0) {
+        std::strncpy(err, msg, (size_t)err_len - 1);
+        err[err_len - 1] = '\0';
+    }
+    return code;
+}
+
+}  // namespace
+}  // namespace gb
+
+using namespace gb;
+
+extern "C" int gb_loglik_mixed_noalloc(const gb_obs_t* obs, const gb_window_t* win, int32_t n_win,
+                                       const double* dA, const double* dE, const double* wA, const double* wE,
+                                       int64_t n_bins, const double* theta, int64_t n_rows, double* logL,
+                                       double* dh, double* hh, void* stream, char* err, int32_t err_len) {
+    if (err && err_len > 0) err[0] = '\0';
+    if (!obs || !(obs->T_obs > 0.0) || !(obs->arm_L > 0.0) || obs->orbit_model != 0)
+        return na_fail(err, err_len, GB_EINVAL, "gb_loglik_mixed_noalloc: bad observation");
+    if (n_win < 0 || n_bins < 0 || n_rows < 0 || (n_win > 0 && !win))
+        return na_fail(err, err_len, GB_EINVAL, "gb_loglik_mixed_noalloc: bad sizes");
+    if (n_win > kNaMaxWindows)
+        return na_fail(err, err_len, GB_EINVAL, "gb_loglik_mixed_noalloc: more than 4096 windows");
+    long long total = 0, bins = 0, items = 0;
+    int n_max = 0;
+    for (int i = 0; i < n_win; ++i) {
+        const gb_window_t& w = win[i];
+        if (!valid_size(w.N) || w.W < 0 || w.n_cand < 0 || w.data_off < 0 || w.cand_off < 0 ||
+            w.data_off + (int64_t)w.W > n_bins || w.cand_off + (int64_t)w.n_cand > n_rows)
+            return na_fail(err, err_len, GB_EINVAL, "gb_loglik_mixed_noalloc: invalid window descriptor");
+        total += w.n_cand;
+        bins += w.W;
+        n_max = w.N > n_max ? w.N : n_max;
+    }
+    if (bins > kNaMaxBins)
+        return na_fail(err, err_len, GB_EINVAL, "gb_loglik_mixed_noalloc: more than 262144 window bins in total");
+    if (total == 0) return GB_OK;
+    if (!dA || !dE || !wA || !wE || !theta || !logL)
+        return na_fail(err, err_len, GB_EINVAL, "gb_loglik_mixed_noalloc: null pointer");
+    int dev = 0, sms = 152;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kNaMaxDevices)
+        return na_fail(err, err_len, GB_ECUDA, "gb_loglik_mixed_noalloc: no current device");
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int per = (int)std::min<long long>(32, std::max<long long>(1, (total + sms * 16 - 1) / (sms * 16)));
+    for (int i = 0; i < n_win; ++i) items += (win[i].n_cand + per - 1) / per;
+    if (items > kNaMaxItems)
+        return na_fail(err, err_len, GB_EINVAL, "gb_loglik_mixed_noalloc: more than 65536 work items "
+                                                "(about 2 million candidates)");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    NaDevice& d = g_na_dev[dev];
+    if (!d.base) {
+        e = cudaGetSymbolAddress((void**)&d.base, g_noalloc_scratch);
+        if (e != cudaSuccess) {
+            d.base = nullptr;
+            return na_fail(err, err_len, GB_ECUDA, "gb_loglik_mixed_noalloc: cudaGetSymbolAddress failed");
+        }
+    }
+    unsigned char* b = d.base;
+    double* t64[kNumSizes];
+    float* t32[kNumSizes];
+    TabSet32 tabs;
+    size_t o64 = kNaOffTab64, o32 = kNaOffTab32;
+    for (int i = 0; i < kNumSizes; ++i) {
+        const int N = 32 << i;
+        t64[i] = (double*)(b + o64);
+        t32[i] = (float*)(b + o32);
+        tabs.t[i] = OrbitTables32{(const float4*)t32[i], (const float2*)(t32[i] + 16 * N)};
+        o64 += sizeof(double) * 18 * N;
+        o32 += sizeof(float) * 18 * N;
+    }
+    double* tw64 = (double*)(b + kNaOffTw64);
+    float* tw32 = (float*)(b + kNaOffTw32);
+    if (d.T != obs->T_obs || d.L != obs->arm_L) {
+        e = build_tables_into(obs->T_obs, obs->arm_L, t64, t32, tw64, tw32, s);
+        if (e != cudaSuccess) return na_fail(err, err_len, GB_ECUDA, "gb_loglik_mixed_noalloc: table build failed");
+        d.T = obs->T_obs;
+        d.L = obs->arm_L;
+    }
+    // work items (windows with N >= 512 first) and window offsets, staged on the host
+    int n_large = 0, k = 0;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int i = 0; i < n_win; ++i) {
+            if ((win[i].N >= 512) != (pass == 0)) continue;
+            for (int64_t c = 0; c < win[i].n_cand; c += per) {
+                Tile t;
+                t.win = i;
+                t.pad = 0;
+                t.c_begin = win[i].cand_off + c;
+                t.c_end = win[i].cand_off + std::min<int64_t>(win[i].n_cand, c + per);
+                g_na_items[k++] = t;
+                if (pass == 0) ++n_large;
+            }
+        }
+    long long off = 0;
+    for (int i = 0; i < n_win; ++i) {
+        g_na_meta[i].dd = 0.0;
+        g_na_meta[i].sig = 1.0;
+        g_na_meta[i].prep_off = off;
+        off += win[i].W;
+    }
+    gb_window_t* d_win = (gb_window_t*)(b + kNaOffWin);
+    Tile* d_items = (Tile*)(b + kNaOffItems);
+    WinMeta* d_meta = (WinMeta*)(b + kNaOffMeta);
+    Win32* d_prep = (Win32*)(b + kNaOffPrep);
+    int* d_head = (int*)(b + kNaOffHead);
+    int* d_status = d_head + 2;
+    e = cudaMemcpyAsync(d_win, win, sizeof(gb_window_t) * (size_t)n_win, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_items, g_na_items, sizeof(Tile) * (size_t)k, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_meta, g_na_meta, sizeof(WinMeta) * (size_t)n_win, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return na_fail(err, err_len, GB_ECUDA, "gb_loglik_mixed_noalloc: upload failed");
+    // the queue heads start at zero: the preparation kernel resets them
+    prep_mixed_kernel<<<n_win, 256, 0, s>>>(d_win, d_meta, d_prep, (const double2*)dA, (const double2*)dE, wA, wE,
+                                            obs->T_obs, d_head);
+    const double fstar = kC / (2.0 * kPi * obs->arm_L);
+    for (int part = 0; part < 2 && cudaGetLastError() == cudaSuccess; ++part) {
+        const int n_items = part == 0 ? n_large : k - n_large;
+        if (n_items == 0) continue;
+        const int nmax = part == 0 ? 1024 : (n_max < 256 ? n_max : 256);
+        const size_t smem = (sizeof(CandMix) + sizeof(Epi)) * kWarpsMx * 32 + sizeof(float2) * kWarpsMx * 2 * (size_t)nmax;
+        const void* kfn = part == 0 ? (const void*)loglik_mixed_kernel<32> : (const void*)loglik_mixed_kernel<8>;
+        if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) break;
+        int grid = sms * resident_blocks(kfn, kWarpsMx * 32, smem);
+        const int need = (n_items + kWarpsMx - 1) / kWarpsMx;
+        if (grid > need) grid = need;
+        const Tile* it = d_items + (part == 0 ? 0 : n_large);
+        int* head = d_head + (part == 0 ? 1 : 0);
+        if (part == 0)
+            loglik_mixed_kernel<32><<<grid, kWarpsMx * 32, smem, s>>>(d_win, d_meta, d_prep, it, n_items, head, tabs,
+                                                                      (const float2*)tw32, obs->T_obs, fstar, theta,
+                                                                      logL, dh, hh, d_status, nmax);
+        else
+            loglik_mixed_kernel<8><<<grid, kWarpsMx * 32, smem, s>>>(d_win, d_meta, d_prep, it, n_items, head, tabs,
+                                                                     (const float2*)tw32, obs->T_obs, fstar, theta,
+                                                                     logL, dh, hh, d_status, nmax);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return na_fail(err, err_len, GB_ECUDA, cudaGetErrorString(e));
+    return GB_OK;
+}
