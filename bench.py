@@ -175,6 +175,25 @@ def flops_per_eval(N, f_hz, T):
     return N * per_sample + 2 * 5 * N * math.log2(N) + 26 * N
 
 
+def profiled_traffic():
+    """DRAM bytes per launch of the likelihood kernel from the committed ncu
+    summary, or None when the kernel source changed since that capture."""
+    import hashlib
+    import re
+    try:
+        prof = open(os.path.join(ROOT, "profiles", "loglik_mixed_posterior.md")).read()
+        src = open(os.path.join(ROOT, "paper_2307_03763_gb300", "csrc", "mixed.cu")).read()
+    except OSError:
+        return None
+    region = src.split("// ---------------------------------------------------------------------------\n"
+                       "// Allocation-free variant")[0].rstrip()
+    sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", prof)
+    nbytes = re.search(r"traffic_bytes_per_launch:\s*(\d+)", prof)
+    if not sha or not nbytes or sha.group(1) != hashlib.sha256(region.encode()).hexdigest():
+        return None
+    return int(nbytes.group(1))
+
+
 # ---------------------------------------------------------------------------
 
 def cpu_baseline(wl, dA, dE, theta, seconds=12.0):
@@ -386,12 +405,7 @@ def main():
     flops = sum(n * flops_per_eval(w[2], f, wl.T) for w, f in zip(wl.windows, f_mid))
     fp32_peak = 152 * 128 * 2 * 2070e6 / 1e12
     achieved = flops / (kern_mx / 1e3) / 1e12
-    traffic = None
-    try:
-        prof = json.load(open(os.path.join(ROOT, "profiles", "loglik_mixed_traffic.json")))
-        traffic = prof.get("bytes_per_launch")
-    except Exception:
-        pass
+    traffic = profiled_traffic()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

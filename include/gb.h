@@ -173,6 +173,57 @@ int gb_mh_independence(gb_ctx_t* ctx, int32_t n_chains, int32_t n,
                        const double* temperature, int32_t literal,
                        int32_t* chain_idx, int32_t* n_accept, void* stream);
 
+/* Prior box of one window: lower and upper bounds of the eight parameters in
+ * theta order (Table 1 of the paper gives its prior; the box is the
+ * caller's). */
+typedef struct {
+    double lo[8];
+    double hi[8];
+} gb_box_t;
+
+/* Genetic-search settings: tournament size (>= 1), probability of a blend
+ * crossover, per-parameter mutation probability, mutation standard deviation
+ * as a fraction of the box width. */
+typedef struct {
+    int32_t tournament;
+    int32_t reserved;
+    double p_cross;
+    double p_mut;
+    double mut_scale;
+} gb_ga_params_t;
+
+/* One generation of the genetic search of every window's population.  The
+ * paper maximises the SNR of Eq. 6 over the parameters other than A with
+ * differential evolution and sets A from Eq. 7 (Alg. 2, Sec. III.D); this is a
+ * genetic algorithm with that objective.
+ *   theta      n_win x pop x 8 population (device), pop individuals per window
+ *   dh, hh     <d|h>, <h|h> of every individual (device, from gb_loglik)
+ *   box        n_win prior boxes (device)
+ *   seed       key of the Philox-4x32-10 draws
+ *   generation_in, generation_out   one uint64 each (device): the draws
+ *              are counted by *generation_in; the call writes
+ *              *generation_out = *generation_in + 1, so two alternating slots
+ *              advance the search when the same launches are replayed
+ *   params     settings (host)
+ *   grad       n_win x 8 gradient of logL at each window's best individual of
+ *              the previous call (device, may be NULL): slots 1..4 then take
+ *              steps of radius 0.3, 0.1, 0.03, 0.01 along it in natural units
+ *   theta_out  next population (device, must not alias theta): slot 0 is the
+ *              best individual with A set to A_max = A <d|h>/<h|h> (Eq. 7),
+ *              the rest are tournament children with blend crossover and
+ *              Gaussian mutation, folded back into the box
+ *   best       n_win x 8 best individuals (device, written; may be NULL) */
+int gb_ga_step(gb_ctx_t* ctx, int32_t n_win, int32_t pop, const double* theta, const double* dh,
+               const double* hh, const gb_box_t* box, uint64_t seed, const uint64_t* generation_in,
+               uint64_t* generation_out, const gb_ga_params_t* params, const double* grad,
+               double* theta_out, double* best, void* stream);
+
+/* n blocks of Philox-4x32-10 (Salmon et al., SC 2011) with key = seed and
+ * counter (i, 0, 0, 0), i < n, written as 4 words per block (device).  The
+ * generator the genetic search draws from; exported so that it can be
+ * checked against its published definition. */
+int gb_philox4x32(gb_ctx_t* ctx, uint64_t seed, uint32_t n, uint32_t* out, void* stream);
+
 /* Allocation-free variant of gb_loglik with prec = GB_MIXED.
  *
  * The paper has no counterpart to this entry point.  It serves callers that

@@ -37,6 +37,11 @@ class Obs(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class GAParams(ctypes.Structure):
+    _fields_ = [("tournament", ctypes.c_int32), ("reserved", ctypes.c_int32), ("p_cross", ctypes.c_double),
+                ("p_mut", ctypes.c_double), ("mut_scale", ctypes.c_double)]
+
+
 _LIB = None
 _P = ctypes.c_void_p
 _I32, _I64 = ctypes.c_int32, ctypes.c_int64
@@ -54,6 +59,9 @@ _SIGNATURES = {
     "gb_mh_independence": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, _I32, _P, _P, _P]),
     "gb_loglik_mixed_noalloc": (ctypes.c_int, [ctypes.POINTER(Obs), ctypes.POINTER(Window), _I32, _P, _P, _P, _P,
                                                _I64, _P, _I64, _P, _P, _P, _P, ctypes.c_char_p, _I32]),
+    "gb_ga_step": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, ctypes.c_uint64, _P, _P,
+                                  ctypes.POINTER(GAParams), _P, _P, _P, _P]),
+    "gb_philox4x32": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint32, _P, _P]),
 }
 
 
@@ -201,6 +209,37 @@ class Context:
                                          _ptr(wE), nb, _ptr(theta), n, _ptr(logL), _ptr(grad),
                                          _stream(self.device)))
         return logL, grad
+
+    def ga_step(self, n_win, pop, theta, dh, hh, box, seed, gen_in, gen_out, params, grad=None, out=None,
+                best=None):
+        """One generation of the genetic search (see gb_ga_step); returns (out, best)."""
+        n = n_win * pop
+        _need(theta, torch.float64, self.device, "theta", (n, 8))
+        _need(dh, torch.float64, self.device, "dh", (n,))
+        _need(hh, torch.float64, self.device, "hh", (n,))
+        _need(box, torch.float64, self.device, "box", (n_win, 16))
+        _need(gen_in, torch.int64, self.device, "gen_in", (1,))
+        _need(gen_out, torch.int64, self.device, "gen_out", (1,))
+        if grad is not None:
+            _need(grad, torch.float64, self.device, "grad", (n_win, 8))
+        if out is None:
+            out = torch.empty_like(theta)
+        if best is None:
+            best = torch.empty((n_win, 8), dtype=torch.float64, device=self.device)
+        _need(out, torch.float64, self.device, "out", (n, 8))
+        _need(best, torch.float64, self.device, "best", (n_win, 8))
+        self._check(lib().gb_ga_step(self._h, n_win, pop, _ptr(theta), _ptr(dh), _ptr(hh), _ptr(box),
+                                     int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(gen_in), _ptr(gen_out),
+                                     ctypes.byref(params), _ptr(grad), _ptr(out), _ptr(best),
+                                     _stream(self.device)))
+        return out, best
+
+    def philox(self, seed, n):
+        """n blocks of Philox-4x32-10 with key = seed, counter (i, 0, 0, 0): (n, 4) int64 of uint32 values."""
+        out = torch.empty(4 * n, dtype=torch.int32, device=self.device)
+        self._check(lib().gb_philox4x32(self._h, int(seed) & 0xFFFFFFFFFFFFFFFF, int(n), _ptr(out),
+                                        _stream(self.device)))
+        return (out.to(torch.int64) & 0xFFFFFFFF).view(n, 4)
 
     def mh_independence(self, logL, log_g, log_u, temperature, literal=False, out=None):
         """Chains (n_chains, n) int32 and accept counts from (n_chains, n) float64 inputs (Alg. 4)."""

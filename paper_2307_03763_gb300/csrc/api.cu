@@ -84,8 +84,10 @@ int gb_loglik_grad(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_wi
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_error(ctx, e, "gb_loglik_grad: cudaSetDevice");
     const Plan* plan = nullptr;
-    // distinct plan keys for the gradient kernels (their CTAs have two warps)
-    rc = get_plan(ctx, prec + 16, win, n_win, tile_size(ctx, total, 2), &plan);
+    // distinct plan keys for the gradient kernels; FP64: CTAs of two warps;
+    // mixed: warp work items of at most 32 candidates
+    int item = (int)std::min<int64_t>(32, std::max<int64_t>(1, (total + sm_count(ctx) * 8 - 1) / (sm_count(ctx) * 8)));
+    rc = get_plan(ctx, prec + 16, win, n_win, prec == GB_MIXED ? item : tile_size(ctx, total, 2), &plan);
     if (rc != GB_OK) return rc;
     if (prec == GB_FP64)
         return launch_grad_fp64(ctx, *plan, dA, dE, wA, wE, theta, logL, grad, (cudaStream_t)stream);

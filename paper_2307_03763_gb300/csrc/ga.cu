@@ -1,0 +1,265 @@
+// ga.cu -- one generation of the genetic search over every window's population.
+//
+// The paper's local search (Alg. 2, Sec. III.D) maximises the SNR of Eq. 6 over
+// the seven parameters other than A with differential evolution and then sets
+// A to the analytic best amplitude of Eq. 7.  The search here is a genetic
+// algorithm with the same objective, run on the device so that a whole
+// generation (likelihood launch + this kernel) can be replayed from a CUDA
+// graph.  Per window (one CTA):
+//   * fitness rho = <d|h>/sqrt(<h|h>) of every individual (Eq. 6);
+//   * the best individual, with A replaced by A_max = A <d|h>/<h|h> (Eq. 7),
+//     goes to slot 0 and to `best`;
+//   * with a gradient at the best individual, slots 1..4 take steps of
+//     radius 0.3, 0.1, 0.03, 0.01 along the gradient direction in natural
+//     units (a line search left to the next generation's selection);
+//   * every other slot is a child: two size-k tournaments, blend crossover,
+//     Gaussian mutation of each parameter with probability p_mut and scale
+//     mut_scale times the box width, then wrapped (longitude, phase,
+//     polarisation) or reflected (latitude, inclination, f0, fdot, A) into the
+//     window's prior box.
+// Random numbers come from Philox-4x32-10 (Salmon, Moraes, Dror and Shaw,
+// "Parallel random numbers: as easy as 1, 2, 3", SC 2011), keyed by the seed
+// and counted by (generation, window, individual, draw).
+#include <cmath>
+
+#include "gb_internal.cuh"
+
+namespace gb {
+namespace {
+
+constexpr int kGaThreads = 256;
+
+struct Philox {
+    uint32_t c[4];
+    uint32_t k[2];
+};
+
+__device__ __forceinline__ void philox_round(uint32_t (&c)[4], const uint32_t (&k)[2]) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
+    const uint32_t hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
+    const uint32_t n0 = hi1 ^ c[1] ^ k[0], n2 = hi0 ^ c[3] ^ k[1];
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+}
+
+// four 32-bit outputs for counter (a, b, cc, d) under key (k0, k1)
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t a, uint32_t b, uint32_t cc, uint32_t d, uint32_t k0,
+                                               uint32_t k1) {
+    uint32_t c[4] = {a, b, cc, d};
+    uint32_t k[2] = {k0, k1};
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        philox_round(c, k);
+        k[0] += 0x9E3779B9u;
+        k[1] += 0xBB67AE85u;
+    }
+    return make_uint4(c[0], c[1], c[2], c[3]);
+}
+
+// uniform in (0, 1) from 32 bits
+__device__ __forceinline__ double u01(uint32_t x) { return ((double)x + 0.5) * 2.3283064365386963e-10; }
+
+struct Rng {
+    uint32_t k0, k1, gen, win, ind, draw;
+    uint4 buf;
+    int left = 0;
+    __device__ uint32_t next() {
+        if (left == 0) {
+            buf = philox4x32_10(gen, win, ind, draw++, k0, k1);
+            left = 4;
+        }
+        --left;
+        return left == 3 ? buf.x : left == 2 ? buf.y : left == 1 ? buf.z : buf.w;
+    }
+    __device__ double uniform() { return u01(next()); }
+    __device__ double normal() {   // Box-Muller
+        const double a = uniform(), b = uniform();
+        return sqrt(-2.0 * log(a)) * cospi(2.0 * b);
+    }
+};
+
+__device__ __forceinline__ double wrap(double x, double lo, double hi) {
+    const double w = hi - lo;
+    if (!(w > 0.0)) return lo;
+    double y = fmod(x - lo, w);
+    if (y < 0.0) y += w;
+    return lo + y;
+}
+
+__device__ __forceinline__ double reflect(double x, double lo, double hi) {
+    const double w = hi - lo;
+    if (!(w > 0.0)) return lo;
+    double y = fmod(x - lo, 2.0 * w);
+    if (y < 0.0) y += 2.0 * w;
+    return lo + (y > w ? 2.0 * w - y : y);
+}
+
+__device__ __forceinline__ double fitness(double dh, double hh) {
+    return (hh > 0.0 && isfinite(dh) && isfinite(hh)) ? dh / sqrt(hh) : -INFINITY;
+}
+
+__global__ void __launch_bounds__(kGaThreads) ga_step_kernel(int pop, const double* __restrict__ theta,
+                                                             const double* __restrict__ dh,
+                                                             const double* __restrict__ hh,
+                                                             const gb_box_t* __restrict__ box, uint64_t seed,
+                                                             const uint64_t* __restrict__ gen_in,
+                                                             uint64_t* __restrict__ gen_out, gb_ga_params_t prm,
+                                                             const double* __restrict__ grad, double T,
+                                                             double* __restrict__ out, double* __restrict__ best) {
+    __shared__ double s_fit[kGaThreads];
+    __shared__ int s_idx[kGaThreads];
+    __shared__ double s_best[8];
+    const int w = blockIdx.x;
+    const uint64_t generation = *gen_in;
+    if (w == 0 && threadIdx.x == 0) *gen_out = generation + 1;
+    const size_t base = (size_t)w * (size_t)pop;
+    const double* th = theta + 8 * base;
+    double* to = out + 8 * base;
+    const gb_box_t bx = box[w];
+    // best individual of the window
+    double bf = -INFINITY;
+    int bi = 0;
+    for (int i = threadIdx.x; i < pop; i += blockDim.x) {
+        const double f = fitness(dh[base + i], hh[base + i]);
+        if (f > bf || (f == bf && i < bi)) {
+            bf = f;
+            bi = i;
+        }
+    }
+    s_fit[threadIdx.x] = bf;
+    s_idx[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            const double f2 = s_fit[threadIdx.x + s];
+            const int i2 = s_idx[threadIdx.x + s];
+            if (f2 > s_fit[threadIdx.x] || (f2 == s_fit[threadIdx.x] && i2 < s_idx[threadIdx.x])) {
+                s_fit[threadIdx.x] = f2;
+                s_idx[threadIdx.x] = i2;
+            }
+        }
+        __syncthreads();
+    }
+    const int ib = s_idx[0];
+    if (threadIdx.x < 8) {
+        double v = th[8 * ib + threadIdx.x];
+        if (threadIdx.x == 4) {   // A_max = A <d|h>/<h|h> (Eq. 7), kept inside the box
+            const double d = dh[base + ib], h = hh[base + ib];
+            if (h > 0.0 && d > 0.0) v = fmin(fmax(v * d / h, bx.lo[4]), bx.hi[4]);
+        }
+        s_best[threadIdx.x] = v;
+        if (best) best[8 * (size_t)w + threadIdx.x] = v;
+    }
+    __syncthreads();
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const double scale[8] = {1.0 / T, 1.0 / (T * T), 1.0, 1.0, s_best[4], 1.0, 1.0, 1.0};
+    double gnorm = 0.0;
+    if (grad) {
+        for (int j = 0; j < 8; ++j) {
+            const double g = grad[8 * (size_t)w + j] * scale[j];
+            gnorm += g * g;
+        }
+        gnorm = sqrt(gnorm);
+    }
+    const double radii[4] = {0.3, 0.1, 0.03, 0.01};
+    for (int i = threadIdx.x; i < pop; i += blockDim.x) {
+        double c[8];
+        if (i == 0) {
+            for (int j = 0; j < 8; ++j) c[j] = s_best[j];
+        } else if (i <= 4 && grad && gnorm > 0.0 && isfinite(gnorm)) {
+            for (int j = 0; j < 8; ++j) {
+                const double dj = grad[8 * (size_t)w + j] * scale[j] / gnorm;
+                c[j] = s_best[j] + radii[i - 1] * scale[j] * dj;
+            }
+        } else {
+            Rng rng{k0, k1, (uint32_t)generation, (uint32_t)w, (uint32_t)i, 0u};
+            int par[2];
+            for (int p = 0; p < 2; ++p) {
+                int win_i = (int)(rng.next() % (uint32_t)pop);
+                double win_f = fitness(dh[base + win_i], hh[base + win_i]);
+                for (int t = 1; t < prm.tournament; ++t) {
+                    const int j = (int)(rng.next() % (uint32_t)pop);
+                    const double f = fitness(dh[base + j], hh[base + j]);
+                    if (f > win_f) {
+                        win_f = f;
+                        win_i = j;
+                    }
+                }
+                par[p] = win_i;
+            }
+            for (int j = 0; j < 8; ++j) {
+                const double a = th[8 * par[0] + j], b = th[8 * par[1] + j];
+                const double t = rng.uniform();
+                double x = (rng.uniform() < prm.p_cross) ? a + t * (b - a) : a;
+                if (rng.uniform() < prm.p_mut) x += prm.mut_scale * (bx.hi[j] - bx.lo[j]) * rng.normal();
+                c[j] = x;
+            }
+        }
+        // back into the prior box
+        c[0] = reflect(c[0], bx.lo[0], bx.hi[0]);
+        c[1] = reflect(c[1], bx.lo[1], bx.hi[1]);
+        c[2] = reflect(c[2], bx.lo[2], bx.hi[2]);
+        c[3] = wrap(c[3], bx.lo[3], bx.hi[3]);
+        c[4] = reflect(c[4], bx.lo[4], bx.hi[4]);
+        c[5] = reflect(c[5], bx.lo[5], bx.hi[5]);
+        c[6] = wrap(c[6], bx.lo[6], bx.hi[6]);
+        c[7] = wrap(c[7], bx.lo[7], bx.hi[7]);
+        for (int j = 0; j < 8; ++j) to[8 * i + j] = c[j];
+    }
+}
+
+// raw Philox outputs, for tests of the generator against its published definition
+__global__ void philox_kernel(uint64_t seed, uint32_t n, uint32_t* out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 r = philox4x32_10(i, 0u, 0u, 0u, (uint32_t)seed, (uint32_t)(seed >> 32));
+    out[4 * i + 0] = r.x;
+    out[4 * i + 1] = r.y;
+    out[4 * i + 2] = r.z;
+    out[4 * i + 3] = r.w;
+}
+
+}  // namespace
+}  // namespace gb
+
+using namespace gb;
+
+extern "C" int gb_ga_step(gb_ctx_t* ctx, int32_t n_win, int32_t pop, const double* theta, const double* dh,
+                          const double* hh, const gb_box_t* box, uint64_t seed, const uint64_t* generation_in,
+                          uint64_t* generation_out, const gb_ga_params_t* params, const double* grad,
+                          double* theta_out, double* best, void* stream) {
+    if (!ctx) return GB_EINVAL;
+    if (n_win < 0 || pop < 0) return set_error(ctx, GB_EINVAL, "gb_ga_step: negative size");
+    if (n_win == 0 || pop == 0) return GB_OK;
+    if (!theta || !dh || !hh || !box || !params || !theta_out || !generation_in || !generation_out)
+        return set_error(ctx, GB_EINVAL, "gb_ga_step: null pointer");
+    if (theta == theta_out) return set_error(ctx, GB_EINVAL, "gb_ga_step: theta_out must not alias theta");
+    if (generation_in == generation_out)
+        return set_error(ctx, GB_EINVAL, "gb_ga_step: generation_out must not alias generation_in");
+    if (params->tournament < 1 || !(params->p_cross >= 0.0 && params->p_cross <= 1.0) ||
+        !(params->p_mut >= 0.0 && params->p_mut <= 1.0) || !(params->mut_scale >= 0.0))
+        return set_error(ctx, GB_EINVAL, "gb_ga_step: bad parameters");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_ga_step: cudaSetDevice");
+    ga_step_kernel<<<n_win, kGaThreads, 0, (cudaStream_t)stream>>>(pop, theta, dh, hh, box, seed, generation_in,
+                                                                   generation_out, *params, grad, ctx->obs.T_obs,
+                                                                   theta_out, best);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_ga_step launch");
+    return GB_OK;
+}
+
+extern "C" int gb_philox4x32(gb_ctx_t* ctx, uint64_t seed, uint32_t n, uint32_t* out, void* stream) {
+    if (!ctx) return GB_EINVAL;
+    if (n == 0) return GB_OK;
+    if (!out) return set_error(ctx, GB_EINVAL, "gb_philox4x32: null pointer");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_philox4x32: cudaSetDevice");
+    philox_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(seed, n, out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_philox4x32 launch");
+    return GB_OK;
+}

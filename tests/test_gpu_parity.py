@@ -319,6 +319,30 @@ def test_mh_golden_and_edge_cases(ctx):
 # gradient
 # --------------------------------------------------------------------------
 
+@pytest.mark.parametrize("which", ["tiny", "band"])
+def test_grad_mixed_matches_oracle(ctx, ctx1, which):
+    # mixed-precision adjoint against the oracle's gradient, per candidate, in
+    # natural parameter units, relative to the gradient norm
+    if which == "tiny":
+        wl, c = wk.tiny_window(n_cand=40), ctx
+    else:
+        wl, c = wk.band_windows(n_win=10, cand_range=(6, 9)), ctx1
+    dA, dE = _data.inject(wl)
+    th = wl.theta.copy()
+    args = (_cuda(dA, torch.complex128), _cuda(dE, torch.complex128), _cuda(wl.w_A, torch.float64),
+            _cuda(wl.w_E, torch.float64), _cuda(th, torch.float64))
+    lg, gg = (x.cpu() for x in c.loglik_grad(wl.windows, *args, prec="mixed"))
+    lo, go = ogb.loglik_grad(wl.windows, dA, dE, wl.w_A, wl.w_E, th, wl.T)
+    worst = 0.0
+    for b in range(th.shape[0]):
+        s = torch.tensor([1 / wl.T, 1 / wl.T ** 2, 1, 1, th[b, 4], 1, 1, 1], dtype=torch.float64)
+        gn, on = gg[b] * s, go[b] * s
+        worst = max(worst, float((gn - on).abs().max()) / float(on.abs().sum()))
+    assert worst <= 1e-4, worst
+    lm, _, _ = c.loglik(wl.windows, *args, prec="mixed")
+    assert torch.allclose(lg, lm.cpu(), rtol=0, atol=1e-9 * float(lo.abs().max()))
+
+
 def test_grad_fp64_matches_oracle(ctx):
     wl = wk.tiny_window(n_cand=24)
     dA, dE = _data.inject(wl)
