@@ -348,6 +348,9 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         return float(t.item())
 
+    # launch shapes for this batch from the library's autotuner (untimed)
+    tuning = {p: ctx.autotune(wl.windows, dA, dE, wA, wE, theta, prec=p, reps=3) for p in ("mixed", "fp64")}
+
     # accuracy of the mixed path against the FP64 path on this workload
     l64 = torch.empty_like(logL)
     ctx.loglik(wl.windows, dA, dE, wA, wE, theta, prec="fp64", out=(l64, None, None))
@@ -418,6 +421,7 @@ def main():
         "mixed_vs_fp64": {"max_abs_dlogL": float(dl.max()), "p99_abs_dlogL": float(dl.quantile(0.99)),
                           "median_abs_dlogL": float(dl.median()), "snr_range": [20, 200]},
         "loglik_ms": kern_mx, "mh_ms": ms_step - kern_mx,
+        "autotune": tuning,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": traffic,
                      "kernel": "loglik_mixed_kernel",

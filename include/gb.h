@@ -173,6 +173,32 @@ int gb_mh_independence(gb_ctx_t* ctx, int32_t n_chains, int32_t n,
                        const double* temperature, int32_t literal,
                        int32_t* chain_idx, int32_t* n_accept, void* stream);
 
+/* Launch shapes chosen by gb_autotune: candidates per work item and resident
+ * CTAs per SM of the persistent mixed-precision kernels (0 = built-in
+ * heuristic), candidates per CTA tile of the FP64 kernel, and the measured
+ * milliseconds per call with the choice and with the heuristics. */
+typedef struct {
+    int32_t item;
+    int32_t blocks_per_sm;
+    int32_t tile;
+    int32_t reserved;
+    double ms;
+    double ms_default;
+} gb_tuning_t;
+
+/* Launch-shape autotuner (the paper has no counterpart; it times the
+ * batched evaluation of Sec. III.G on the caller's own batch).  Runs
+ * gb_loglik with prec on the given inputs for a set of launch shapes (mixed:
+ * 2, 4, 8, 16 or 32 candidates per work item x 1, 2, 3 or all resident CTAs
+ * per SM; FP64: 16 to 128 candidates per CTA tile), reps timed calls each,
+ * keeps the fastest in the context for later calls and reports it in chosen
+ * (may be NULL).  logL (n_rows doubles, device) is overwritten.  Synchronous;
+ * allocates launch plans for the trial shapes. */
+int gb_autotune(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win,
+                const double* dA, const double* dE, const double* wA, const double* wE,
+                int64_t n_bins, const double* theta, int64_t n_rows, double* logL, int32_t reps,
+                gb_tuning_t* chosen, void* stream);
+
 /* Prior box of one window: lower and upper bounds of the eight parameters in
  * theta order (Table 1 of the paper gives its prior; the box is the
  * caller's). */

@@ -42,6 +42,11 @@ class GAParams(ctypes.Structure):
                 ("p_mut", ctypes.c_double), ("mut_scale", ctypes.c_double)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("item", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("ms", ctypes.c_double), ("ms_default", ctypes.c_double)]
+
+
 _LIB = None
 _P = ctypes.c_void_p
 _I32, _I64 = ctypes.c_int32, ctypes.c_int64
@@ -62,6 +67,8 @@ _SIGNATURES = {
     "gb_ga_step": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, ctypes.c_uint64, _P, _P,
                                   ctypes.POINTER(GAParams), _P, _P, _P, _P]),
     "gb_philox4x32": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint32, _P, _P]),
+    "gb_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _I64, _P, _I64,
+                                   _P, _I32, ctypes.POINTER(Tuning), _P]),
 }
 
 
@@ -209,6 +216,17 @@ class Context:
                                          _ptr(wE), nb, _ptr(theta), n, _ptr(logL), _ptr(grad),
                                          _stream(self.device)))
         return logL, grad
+
+    def autotune(self, windows, dA, dE, wA, wE, theta, prec="mixed", reps=3):
+        """Pick the fastest launch shape for this batch (see gb_autotune); returns a dict."""
+        arr, nw, nb, n = self._data_args(windows, dA, dE, wA, wE, theta)
+        logL = torch.empty(n, dtype=torch.float64, device=self.device)
+        t = Tuning()
+        self._check(lib().gb_autotune(self._h, PRECISIONS[prec], arr, nw, _ptr(dA), _ptr(dE), _ptr(wA), _ptr(wE),
+                                      nb, _ptr(theta), n, _ptr(logL), int(reps), ctypes.byref(t),
+                                      _stream(self.device)))
+        return {"item": t.item, "blocks_per_sm": t.blocks_per_sm, "tile": t.tile, "ms": t.ms,
+                "ms_default": t.ms_default}
 
     def ga_step(self, n_win, pop, theta, dh, hh, box, seed, gen_in, gen_out, params, grad=None, out=None,
                 best=None):

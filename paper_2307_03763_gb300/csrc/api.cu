@@ -64,7 +64,10 @@ int gb_loglik(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win, co
     // mixed: work items of at most 32 candidates (one warp each), fewer when
     // the batch would not give every resident warp of the GPU one item
     int item = (int)std::min<int64_t>(32, std::max<int64_t>(1, (total + sm_count(ctx) * 16 - 1) / (sm_count(ctx) * 16)));
-    rc = get_plan(ctx, prec, win, n_win, prec == GB_MIXED ? item : tile_size(ctx, total, warps), &plan);
+    if (ctx->tune_item > 0) item = std::min(ctx->tune_item, 32);
+    int tile = tile_size(ctx, total, warps);
+    if (ctx->tune_tile64 > 0) tile = std::min(ctx->tune_tile64, 32 * warps);
+    rc = get_plan(ctx, prec, win, n_win, prec == GB_MIXED ? item : tile, &plan);
     if (rc != GB_OK) return rc;
     if (prec == GB_FP64)
         return launch_loglik_fp64(ctx, *plan, dA, dE, wA, wE, theta, logL, dh, hh, (cudaStream_t)stream);
@@ -92,6 +95,78 @@ int gb_loglik_grad(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_wi
     if (prec == GB_FP64)
         return launch_grad_fp64(ctx, *plan, dA, dE, wA, wE, theta, logL, grad, (cudaStream_t)stream);
     return launch_grad_mixed(ctx, *plan, dA, dE, wA, wE, theta, logL, grad, (cudaStream_t)stream);
+}
+
+int gb_autotune(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win, const double* dA,
+                const double* dE, const double* wA, const double* wE, int64_t n_bins, const double* theta,
+                int64_t n_rows, double* logL, int32_t reps, gb_tuning_t* chosen, void* stream) {
+    if (!ctx) return GB_EINVAL;
+    if (prec != GB_FP64 && prec != GB_MIXED) return set_error(ctx, GB_EINVAL, "gb_autotune: unknown precision");
+    int64_t total = 0;
+    int rc = check_windows(ctx, "gb_autotune", win, n_win, n_bins, n_rows, &total);
+    if (rc != GB_OK) return rc;
+    if (!dA || !dE || !wA || !wE || !theta || !logL) return set_error(ctx, GB_EINVAL, "gb_autotune: null pointer");
+    if (reps < 1) reps = 3;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_autotune: cudaSetDevice");
+    struct Cfg {
+        int item, bpsm, tile;
+    };
+    std::vector<Cfg> cfgs;
+    cfgs.push_back({0, 0, 0});   // built-in heuristics first
+    if (prec == GB_MIXED) {
+        for (int item : {2, 4, 8, 16, 32})
+            for (int bpsm : {0, 1, 2, 3}) cfgs.push_back({item, bpsm, 0});
+    } else {
+        for (int tile : {16, 32, 64, 128}) cfgs.push_back({0, 0, tile});
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_autotune: events");
+    double best = 1e300, first = 0.0;
+    Cfg pick = cfgs[0];
+    for (size_t i = 0; i < cfgs.size() && rc == GB_OK; ++i) {
+        ctx->tune_item = cfgs[i].item;
+        ctx->tune_bpsm = cfgs[i].bpsm;
+        ctx->tune_tile64 = cfgs[i].tile;
+        rc = gb_loglik(ctx, prec, win, n_win, dA, dE, wA, wE, n_bins, theta, n_rows, logL, nullptr, nullptr, stream);
+        if (rc != GB_OK) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && rc == GB_OK; ++r)
+            rc = gb_loglik(ctx, prec, win, n_win, dA, dE, wA, wE, n_bins, theta, n_rows, logL, nullptr, nullptr,
+                           stream);
+        cudaEventRecord(e1, s);
+        e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            rc = cuda_error(ctx, e, "gb_autotune: timing");
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = ms / reps;
+        if (i == 0) first = per;
+        if (per < best) {
+            best = per;
+            pick = cfgs[i];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tune_item = pick.item;
+    ctx->tune_bpsm = pick.bpsm;
+    ctx->tune_tile64 = pick.tile;
+    if (rc != GB_OK) return rc;
+    if (chosen) {
+        chosen->item = pick.item;
+        chosen->blocks_per_sm = pick.bpsm;
+        chosen->tile = pick.tile;
+        chosen->reserved = 0;
+        chosen->ms = best;
+        chosen->ms_default = first;
+    }
+    return GB_OK;
 }
 
 int gb_waveform(gb_ctx_t* ctx, int prec, const double* theta, int64_t B, int32_t N, double* hA, double* hE,

@@ -126,6 +126,10 @@ struct gb_ctx {
     int* d_status = nullptr;    // device status word (GB_OK or GB_EINVAL)
     std::vector<gb::Plan> plans;
     uint64_t clock = 0;
+    // launch shapes chosen by gb_autotune (0: built-in heuristics)
+    int tune_item = 0;        // mixed: candidates per work item
+    int tune_bpsm = 0;        // mixed: resident CTAs per SM of the persistent kernels
+    int tune_tile64 = 0;      // FP64: candidates per CTA tile
 };
 
 namespace gb {

@@ -481,9 +481,14 @@ __global__ void prep_mixed_kernel(const gb_window_t* __restrict__ wins, WinMeta*
     }
 }
 
+// resident CTAs per SM the small-N instantiation is compiled for (register cap)
+#ifndef GB_MIXED_MINB
+#define GB_MIXED_MINB 4
+#endif
+
 // RMAX: largest R = N/32 this instantiation handles (8: N <= 256; 32: N = 512, 1024)
 template <int RMAX>
-__global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? 4 : 2) loglik_mixed_kernel(
+__global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) loglik_mixed_kernel(
     const gb_window_t* __restrict__ wins, const WinMeta* __restrict__ meta, const Win32* __restrict__ prep,
     const Tile* __restrict__ items, int n_items, int* head, TabSet32 tabs, const float2* __restrict__ tw1024,
     double T, double fstar, const double* __restrict__ theta, double* __restrict__ logL,
@@ -648,7 +653,9 @@ int launch_loglik_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const d
         const void* kfn = part == 0 ? (const void*)loglik_mixed_kernel<32> : (const void*)loglik_mixed_kernel<8>;
         e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_error(ctx, e, "loglik_mixed: smem attribute");
-        int grid = sms * resident_blocks(kfn, kWarpsMx * 32, smem);
+        int bpsm = resident_blocks(kfn, kWarpsMx * 32, smem);
+        if (ctx->tune_bpsm > 0 && ctx->tune_bpsm < bpsm) bpsm = ctx->tune_bpsm;
+        int grid = sms * bpsm;
         const int need = (n_items + kWarpsMx - 1) / kWarpsMx;
         if (grid > need) grid = need;
         const Tile* items = plan.d_tiles + (part == 0 ? 0 : plan.n_large);

@@ -343,6 +343,25 @@ def test_grad_mixed_matches_oracle(ctx, ctx1, which):
     assert torch.allclose(lg, lm.cpu(), rtol=0, atol=1e-9 * float(lo.abs().max()))
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_autotune_keeps_results(api, prec):
+    # the tuner changes launch shapes only: outputs stay bit-identical
+    wl = wk.band_windows(n_win=16, cand_range=(200, 600))
+    c = api.Context(wl.T)
+    args = (_cuda(wl.noise_A, torch.complex128), _cuda(wl.noise_E, torch.complex128), _cuda(wl.w_A, torch.float64),
+            _cuda(wl.w_E, torch.float64), _cuda(wl.theta, torch.float64))
+    before = [x.clone() for x in c.loglik(wl.windows, *args, prec=prec)]
+    t = c.autotune(wl.windows, *args, prec=prec, reps=2)
+    after = c.loglik(wl.windows, *args, prec=prec)
+    for x, y in zip(before, after):
+        assert torch.equal(x, y)
+    assert t["ms"] <= t["ms_default"] + 1e-9
+    if prec == "mixed":
+        assert t["item"] in (0, 2, 4, 8, 16, 32) and t["blocks_per_sm"] in (0, 1, 2, 3)
+    else:
+        assert t["tile"] in (0, 16, 32, 64, 128)
+
+
 def test_grad_fp64_matches_oracle(ctx):
     wl = wk.tiny_window(n_cand=24)
     dA, dE = _data.inject(wl)
