@@ -244,6 +244,24 @@ int gb_ga_step(gb_ctx_t* ctx, int32_t n_win, int32_t pop, const double* theta, c
                uint64_t* generation_out, const gb_ga_params_t* params, const double* grad,
                double* theta_out, double* best, void* stream);
 
+/* Gaussian proposals of the independence sampler (Alg. 4 draws n samples per
+ * round from the current proposal distribution; Sec. III.G).  For window w
+ * and proposal i, with counter-based Philox-4x32-10 draws keyed by seed and
+ * counted by (*round_in, w, i, block):
+ *   z_j  eight Box-Muller normals from the first two blocks
+ *        (z_2m = r cos 2 pi v, z_2m+1 = r sin 2 pi v, r = sqrt(-2 log u),
+ *         u, v = (x + 1/2) 2^-32 of consecutive 32-bit words)
+ *   theta = mu_w + L_w z               (L_w lower triangular, row-major 8x8)
+ *   log_g = -|z|^2/2 - sum_j log L_w,jj - 4 log(2 pi)
+ *   log_u = log of a uniform from the first word of the third block
+ * mu: n_win x 8, chol: n_win x 64 (device); theta n_win x n x 8, log_g and
+ * log_u n_win x n (device, written).  round_in/round_out: one uint64 each
+ * (device), *round_out = *round_in + 1, so replayed launches draw new
+ * samples.  n_win <= 65535. */
+int gb_draw_gaussian(gb_ctx_t* ctx, int32_t n_win, int32_t n, const double* mu, const double* chol,
+                     uint64_t seed, const uint64_t* round_in, uint64_t* round_out, double* theta,
+                     double* log_g, double* log_u, void* stream);
+
 /* n blocks of Philox-4x32-10 (Salmon et al., SC 2011) with key = seed and
  * counter (i, 0, 0, 0), i < n, written as 4 words per block (device).  The
  * generator the genetic search draws from; exported so that it can be

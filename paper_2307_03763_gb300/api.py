@@ -69,6 +69,7 @@ _SIGNATURES = {
     "gb_philox4x32": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint32, _P, _P]),
     "gb_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _I64, _P, _I64,
                                    _P, _I32, ctypes.POINTER(Tuning), _P]),
+    "gb_draw_gaussian": (ctypes.c_int, [_P, _I32, _I32, _P, _P, ctypes.c_uint64, _P, _P, _P, _P, _P, _P]),
 }
 
 
@@ -251,6 +252,26 @@ class Context:
                                      ctypes.byref(params), _ptr(grad), _ptr(out), _ptr(best),
                                      _stream(self.device)))
         return out, best
+
+    def draw_gaussian(self, mu, chol, n, seed, round_in, round_out, out=None):
+        """Gaussian proposals per window (see gb_draw_gaussian): theta (n_win*n, 8), log_g, log_u (n_win, n)."""
+        n_win = mu.shape[0]
+        _need(mu, torch.float64, self.device, "mu", (n_win, 8))
+        _need(chol, torch.float64, self.device, "chol", (n_win, 8, 8))
+        _need(round_in, torch.int64, self.device, "round_in", (1,))
+        _need(round_out, torch.int64, self.device, "round_out", (1,))
+        if out is None:
+            out = (torch.empty((n_win * n, 8), dtype=torch.float64, device=self.device),
+                   torch.empty((n_win, n), dtype=torch.float64, device=self.device),
+                   torch.empty((n_win, n), dtype=torch.float64, device=self.device))
+        th, lg, lu = out
+        _need(th, torch.float64, self.device, "theta", (n_win * n, 8))
+        _need(lg, torch.float64, self.device, "log_g", (n_win, n))
+        _need(lu, torch.float64, self.device, "log_u", (n_win, n))
+        self._check(lib().gb_draw_gaussian(self._h, n_win, int(n), _ptr(mu), _ptr(chol),
+                                           int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(round_in), _ptr(round_out),
+                                           _ptr(th), _ptr(lg), _ptr(lu), _stream(self.device)))
+        return th, lg, lu
 
     def philox(self, seed, n):
         """n blocks of Philox-4x32-10 with key = seed, counter (i, 0, 0, 0): (n, 4) int64 of uint32 values."""

@@ -211,6 +211,47 @@ __global__ void __launch_bounds__(kGaThreads) ga_step_kernel(int pop, const doub
     }
 }
 
+// Proposals of an independence sampler (Alg. 4: "n samples randomly drawn"),
+// one thread per proposal: z_j = Box-Muller normals from Philox counter
+// (round, window, proposal, block), theta = mu + L z (L lower triangular),
+// log g = -|z|^2/2 - sum_j log L_jj - 4 log(2 pi), log u from one more draw.
+__global__ void draw_gaussian_kernel(int n, const double* __restrict__ mu, const double* __restrict__ chol,
+                                     uint64_t seed, const uint64_t* __restrict__ round_in,
+                                     uint64_t* __restrict__ round_out, double* __restrict__ theta,
+                                     double* __restrict__ log_g, double* __restrict__ log_u) {
+    const int w = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t rnd = *round_in;
+    if (w == 0 && blockIdx.x == 0 && threadIdx.x == 0) *round_out = rnd + 1;
+    if (i >= n) return;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const uint4 a = philox4x32_10((uint32_t)rnd, (uint32_t)w, (uint32_t)i, 0u, k0, k1);
+    const uint4 b = philox4x32_10((uint32_t)rnd, (uint32_t)w, (uint32_t)i, 1u, k0, k1);
+    const uint4 c = philox4x32_10((uint32_t)rnd, (uint32_t)w, (uint32_t)i, 2u, k0, k1);
+    const uint32_t words[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    double z[8];
+    for (int j = 0; j < 4; ++j) {
+        const double r = sqrt(-2.0 * log(u01(words[2 * j])));
+        double s, co;
+        sincospi(2.0 * u01(words[2 * j + 1]), &s, &co);
+        z[2 * j] = r * co;
+        z[2 * j + 1] = r * s;
+    }
+    const double* m = mu + 8 * w;
+    const double* L = chol + 64 * w;
+    const size_t row = (size_t)w * n + i;
+    double zz = 0.0, ld = 0.0;
+    for (int r = 0; r < 8; ++r) {
+        double v = m[r];
+        for (int k = 0; k <= r; ++k) v += L[8 * r + k] * z[k];
+        theta[8 * row + r] = v;
+        zz += z[r] * z[r];
+        ld += log(L[8 * r + r]);
+    }
+    log_g[row] = -0.5 * zz - ld - 4.0 * log(2.0 * kPi);
+    log_u[row] = log(u01(c.x));
+}
+
 // raw Philox outputs, for tests of the generator against its published definition
 __global__ void philox_kernel(uint64_t seed, uint32_t n, uint32_t* out) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -249,6 +290,26 @@ extern "C" int gb_ga_step(gb_ctx_t* ctx, int32_t n_win, int32_t pop, const doubl
                                                                    theta_out, best);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "gb_ga_step launch");
+    return GB_OK;
+}
+
+extern "C" int gb_draw_gaussian(gb_ctx_t* ctx, int32_t n_win, int32_t n, const double* mu, const double* chol,
+                                uint64_t seed, const uint64_t* round_in, uint64_t* round_out, double* theta,
+                                double* log_g, double* log_u, void* stream) {
+    if (!ctx) return GB_EINVAL;
+    if (n_win < 0 || n < 0) return set_error(ctx, GB_EINVAL, "gb_draw_gaussian: negative size");
+    if (n_win == 0 || n == 0) return GB_OK;
+    if (n_win > 65535) return set_error(ctx, GB_EINVAL, "gb_draw_gaussian: more than 65535 windows");
+    if (!mu || !chol || !round_in || !round_out || !theta || !log_g || !log_u)
+        return set_error(ctx, GB_EINVAL, "gb_draw_gaussian: null pointer");
+    if (round_in == round_out) return set_error(ctx, GB_EINVAL, "gb_draw_gaussian: round_out must not alias round_in");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_draw_gaussian: cudaSetDevice");
+    dim3 grid((unsigned)((n + 255) / 256), (unsigned)n_win);
+    draw_gaussian_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(n, mu, chol, seed, round_in, round_out, theta, log_g,
+                                                                 log_u);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_draw_gaussian launch");
     return GB_OK;
 }
 

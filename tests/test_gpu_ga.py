@@ -81,3 +81,67 @@ def test_ga_graph_replay_equals_eager(api):
     bb = b.run(21, graph=True)
     assert np.array_equal(ba, bb)
     assert torch.equal(a.th[a.cur], b.th[b.cur])
+
+
+def _draws_reference(mu, L, seed, rnd, w, i):
+    """Proposal i of window w, round rnd, re-derived from the generator's definition."""
+    k = [seed & 0xFFFFFFFF, seed >> 32]
+    words = philox4x32_10([rnd, w, i, 0], k) + philox4x32_10([rnd, w, i, 1], k)
+    u01 = lambda x: (x + 0.5) * 2.0 ** -32
+    z = []
+    for j in range(4):
+        r = math.sqrt(-2.0 * math.log(u01(words[2 * j])))
+        a = 2.0 * math.pi * u01(words[2 * j + 1])
+        z += [r * math.cos(a), r * math.sin(a)]
+    z = np.array(z)
+    th = mu + L @ z
+    lg = -0.5 * z @ z - np.log(np.diag(L)).sum() - 4 * math.log(2 * math.pi)
+    lu = math.log(u01(philox4x32_10([rnd, w, i, 2], k)[0]))
+    return th, lg, lu
+
+
+def test_gaussian_draws_match_definition(api):
+    ctx = api.Context(wk.YEAR)
+    rng = np.random.default_rng(8)
+    nw, n = 3, 300
+    mu = rng.normal(size=(nw, 8))
+    A = rng.normal(size=(nw, 8, 8)) * 0.1
+    cov = A @ A.transpose(0, 2, 1) + np.eye(8)[None] * 0.5
+    L = np.linalg.cholesky(cov)
+    r = torch.tensor([5, 0], dtype=torch.int64, device=DEV)
+    th, lg, lu = ctx.draw_gaussian(_cuda(mu, torch.float64), _cuda(L, torch.float64), n, 0x1234ABCD5678, r[0:1], r[1:2])
+    assert int(r[1]) == 6
+    th, lg, lu = th.cpu().numpy().reshape(nw, n, 8), lg.cpu().numpy(), lu.cpu().numpy()
+    for w in range(nw):
+        for i in (0, 1, 77, n - 1):
+            rt, rg, ru = _draws_reference(mu[w], L[w], 0x1234ABCD5678, 5, w, i)
+            assert np.allclose(th[w, i], rt, rtol=1e-13, atol=1e-13)
+            assert abs(lg[w, i] - rg) < 1e-12 and abs(lu[w, i] - ru) < 1e-13
+    # the draws have the requested mean and covariance
+    big = ctx.draw_gaussian(_cuda(mu[:1], torch.float64), _cuda(L[:1], torch.float64), 200000, 9, r[0:1], r[1:2])[0]
+    x = big.cpu().numpy()
+    assert np.abs(x.mean(0) - mu[0]).max() < 6 * np.sqrt(np.diag(cov[0]).max() / 200000)
+    assert np.abs(np.cov(x.T) - cov[0]).max() < 0.02 * np.abs(cov[0]).max()
+
+
+def test_posterior_rounds_graph_equals_eager_and_chains_are_valid(api):
+    from paper_2307_03763_gb300.posterior import PosteriorRounds
+    wl, src, dA, dE, box = _single_source_problem(seed=wk.SEED_BASE + 42)
+    ctx = api.Context(wl.T)
+    args = (_cuda(dA, torch.complex128), _cuda(dE, torch.complex128), _cuda(wl.w_A, torch.float64),
+            _cuda(wl.w_E, torch.float64))
+    sig = _data.fisher_sigma(src, wl.windows[0], wl.w_A, wl.w_E, wl.T)
+    cov = np.diag((3 * sig) ** 2)[None]
+    a = PosteriorRounds(ctx, wl.windows, *args, src[None], cov, n=10000, seed=11).run(7, graph=False)
+    b = PosteriorRounds(ctx, wl.windows, *args, src[None], cov, n=10000, seed=11).run(7, graph=True)
+    assert torch.equal(a.chain, b.chain) and torch.equal(a.theta, b.theta)
+    ch = b.chain[0].cpu().numpy()
+    L, G, U = (x.cpu().numpy().reshape(-1) for x in (b.logL, b.log_g[0], b.log_u[0]))
+    assert ch[0] == 0
+    c = 0
+    for i in range(1, len(ch)):
+        d = (L[i] - G[i]) - (L[c] - G[c])
+        if U[i] < min(0.0, d):
+            c = i
+        assert ch[i] == c
+    assert 0 < int(b.accepted[0]) < 10000

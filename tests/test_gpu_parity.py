@@ -377,3 +377,33 @@ def test_grad_fp64_matches_oracle(ctx):
         gn, on = gg[b] * sb, go[b] * sb
         assert float((gn - on).abs().max()) <= 1e-9 * float(on.abs().sum()), (b, gn, on)
     assert ((lg - lo).abs() <= 1e-10 * lo.abs()).all()
+
+
+def test_autograd_function_uses_the_adjoint(ctx):
+    from paper_2307_03763_gb300 import autograd as ag
+    wl = wk.tiny_window(n_cand=12)
+    dA, dE = _data.inject(wl)
+    data = (_cuda(dA, torch.complex128), _cuda(dE, torch.complex128), _cuda(wl.w_A, torch.float64),
+            _cuda(wl.w_E, torch.float64))
+    th = _cuda(wl.theta, torch.float64).requires_grad_(True)
+    for prec in ("fp64", "mixed"):
+        l = ag.loglik(ctx, wl.windows, *data, th, prec=prec)
+        wts = torch.linspace(0.5, 2.0, 12, dtype=torch.float64, device=DEV)
+        (g,) = torch.autograd.grad((l * wts).sum(), th)
+        _, gd = ctx.loglik_grad(wl.windows, *data, th.detach(), prec=prec)
+        assert torch.allclose(g, gd * wts[:, None], rtol=1e-12, atol=0)
+
+
+def test_observed_fisher_matches_oracle_fisher(ctx):
+    # noise-free data at the truth: -d2 logL = J^T W J exactly
+    from paper_2307_03763_gb300 import autograd as ag
+    wl = wk.tiny_window(seed=wk.SEED_BASE + 50, n_cand=1)
+    src = wl.sources[0][0].copy()
+    src[4] *= 50.0 / _data.unit_snr(src, wl.windows[0], wl.w_A, wl.w_E, wl.T)
+    hA, hE = _data.template_on_window(src, *wl.windows[0][:3], wl.T)
+    data = (_cuda(hA, torch.complex128), _cuda(hE, torch.complex128), _cuda(wl.w_A, torch.float64),
+            _cuda(wl.w_E, torch.float64))
+    F = ag.observed_fisher(ctx, wl.windows, *data, _cuda(src[None], torch.float64), prec="fp64")[0].cpu().numpy()
+    sig = np.sqrt(np.diag(np.linalg.pinv(F)))
+    ref = _data.fisher_sigma(src, wl.windows[0], wl.w_A, wl.w_E, wl.T)
+    assert np.allclose(sig, ref, rtol=2e-3), (sig, ref)
