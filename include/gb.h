@@ -107,6 +107,12 @@ int gb_ctx_destroy(gb_ctx_t* ctx);
 /* Message of the last failing call on `ctx` (never NULL; "" if none). */
 const char* gb_last_error(const gb_ctx_t* ctx);
 
+/* Number of kernels the context's calls have launched so far, counted on
+ * the host at each launch (the paper has no counterpart: instrumentation for
+ * benchmarks).  0 for a NULL context.  Not thread safe across concurrent
+ * calls on one context, like the rest of the API. */
+uint64_t gb_launch_count(const gb_ctx_t* ctx);
+
 /* Synchronise the device, read and clear the context's status word.
  * Returns GB_OK, or GB_EINVAL if a kernel met a non-finite parameter since
  * the last check. */

@@ -56,6 +56,7 @@ _SIGNATURES = {
     "gb_ctx_destroy": (ctypes.c_int, [_P]),
     "gb_last_error": (ctypes.c_char_p, [_P]),
     "gb_ctx_check": (ctypes.c_int, [_P]),
+    "gb_launch_count": (ctypes.c_uint64, [_P]),
     "gb_waveform": (ctypes.c_int, [_P, ctypes.c_int, _P, _I64, _I32, _P, _P, _P, _P]),
     "gb_loglik": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _I64, _P, _I64,
                                  _P, _P, _P, _P]),
@@ -153,6 +154,10 @@ class Context:
     def _check(self, rc):
         if rc != GB_OK:
             raise GBError(rc, lib().gb_last_error(self._h).decode())
+
+    def launch_count(self):
+        """Kernels launched by this context's calls so far."""
+        return int(lib().gb_launch_count(self._h))
 
     def check(self):
         """Synchronise and raise if a kernel met a non-finite parameter."""

@@ -298,14 +298,23 @@ int gb_ctx_create(gb_ctx_t** out, const gb_obs_t* obs, int device) {
         if (e == cudaSuccess) {
             build_tables_kernel<<<(N + 127) / 128, 128>>>(N, obs->T_obs, obs->arm_L, ctx->d_tab64[i],
                                                          ctx->d_tab32[i]);
+            ++ctx->launches;
             e = cudaGetLastError();
         }
     }
     if (e == cudaSuccess) {
         build_twiddles_kernel<<<(kTwiddles + 127) / 128, 128>>>(ctx->d_tw64, ctx->d_tw32);
+        ++ctx->launches;
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    // MH scratch for 262,144 proposals in 1,024 chunks, so that common chain
+    // sizes never allocate inside a call (or a stream capture)
+    if (e == cudaSuccess) {
+        const size_t b = mh_scratch_bytes(1024, 262144);
+        e = cudaMalloc(&ctx->d_mh, b);
+        if (e == cudaSuccess) ctx->mh_bytes = b;
+    }
     if (e != cudaSuccess) {
         gb_ctx_destroy(ctx);
         return e == cudaErrorMemoryAllocation ? GB_ENOMEM : GB_ECUDA;
@@ -326,11 +335,14 @@ int gb_ctx_destroy(gb_ctx_t* ctx) {
     if (ctx->d_tw64) cudaFree(ctx->d_tw64);
     if (ctx->d_tw32) cudaFree(ctx->d_tw32);
     if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->d_mh) cudaFree(ctx->d_mh);
     delete ctx;
     return GB_OK;
 }
 
 const char* gb_last_error(const gb_ctx_t* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+uint64_t gb_launch_count(const gb_ctx_t* ctx) { return ctx ? ctx->launches : 0; }
 
 int gb_ctx_check(gb_ctx_t* ctx) {
     if (!ctx) return GB_EINVAL;

@@ -338,6 +338,7 @@ int launch_loglik_fp64(gb_ctx* ctx, const Plan& plan, const double* dA, const do
         plan.d_win, plan.d_tiles, tabset64(ctx), (const C64*)ctx->d_tw64, ctx->obs.T_obs,
         transfer_frequency(ctx), (const C64*)dA, (const C64*)dE, wA, wE, theta, logL, dh, hh,
         ctx->d_status, plan.n_max);
+    ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "loglik64 launch");
     return GB_OK;
@@ -358,6 +359,7 @@ int launch_waveform_fp64(gb_ctx* ctx, const double* theta, int64_t B, int N, dou
     waveform64_kernel<<<(unsigned)blocks, kWarps64 * 32, smem, s>>>(
         tables64(ctx, N), (const C64*)ctx->d_tw64, ctx->obs.T_obs, transfer_frequency(ctx), N,
         theta, B, (int)group, (C64*)hA, (C64*)hE, q, ctx->d_status);
+    ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "waveform64 launch");
     return GB_OK;

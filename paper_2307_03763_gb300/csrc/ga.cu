@@ -288,6 +288,7 @@ extern "C" int gb_ga_step(gb_ctx_t* ctx, int32_t n_win, int32_t pop, const doubl
     ga_step_kernel<<<n_win, kGaThreads, 0, (cudaStream_t)stream>>>(pop, theta, dh, hh, box, seed, generation_in,
                                                                    generation_out, *params, grad, ctx->obs.T_obs,
                                                                    theta_out, best);
+    ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "gb_ga_step launch");
     return GB_OK;
@@ -308,6 +309,7 @@ extern "C" int gb_draw_gaussian(gb_ctx_t* ctx, int32_t n_win, int32_t n, const d
     dim3 grid((unsigned)((n + 255) / 256), (unsigned)n_win);
     draw_gaussian_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(n, mu, chol, seed, round_in, round_out, theta, log_g,
                                                                  log_u);
+    ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "gb_draw_gaussian launch");
     return GB_OK;
@@ -320,6 +322,7 @@ extern "C" int gb_philox4x32(gb_ctx_t* ctx, uint64_t seed, uint32_t n, uint32_t*
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_error(ctx, e, "gb_philox4x32: cudaSetDevice");
     philox_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(seed, n, out);
+    ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "gb_philox4x32 launch");
     return GB_OK;

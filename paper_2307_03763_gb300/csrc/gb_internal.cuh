@@ -130,11 +130,20 @@ struct gb_ctx {
     int tune_item = 0;        // mixed: candidates per work item
     int tune_bpsm = 0;        // mixed: resident CTAs per SM of the persistent kernels
     int tune_tile64 = 0;      // FP64: candidates per CTA tile
+    // chunk summaries of the MH scan (grown on demand)
+    void* d_mh = nullptr;
+    size_t mh_bytes = 0;
+    // kernels launched by this context's calls
+    uint64_t launches = 0;
 };
 
 namespace gb {
 
 int set_error(gb_ctx* ctx, int code, const std::string& msg);
+// MH scratch: bytes for `chunk_slots` (chain, chunk) summaries and the keys
+// of `proposals` proposals; grow the buffer
+int ensure_mh_scratch(gb_ctx* ctx, size_t bytes);
+size_t mh_scratch_bytes(size_t chunk_slots, size_t proposals);
 int cuda_error(gb_ctx* ctx, cudaError_t e, const char* what);
 
 cudaError_t build_tables_into(double T, double L, double* const tab64[kNumSizes], float* const tab32[kNumSizes],

@@ -448,6 +448,7 @@ int launch_grad_fp64(gb_ctx* ctx, const Plan& plan, const double* dA, const doub
                                                            (const C*)ctx->d_tw64, ctx->obs.T_obs,
                                                            transfer_frequency(ctx), (const C*)dA, (const C*)dE,
                                                            wA, wE, theta, logL, grad, ctx->d_status, plan.n_max);
+    ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "grad64 launch");
     return GB_OK;

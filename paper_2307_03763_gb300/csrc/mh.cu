@@ -2,132 +2,557 @@
 // (Sec. III.G, Alg. 4, Eq. 13).
 //
 // The proposal does not depend on the chain state, so all log-likelihoods are
-// computed first and each chain is one scan over its proposals.  One CTA runs
-// one chain: all its threads turn a chunk of proposals into weights
-//   w_i = logL_i/T - log g_i   (default reading),  v_i = logL_i - log g_i (literal)
-// in shared memory, then one warp scans the chunk.  The scan is sequential
-// only through the current state c: while c stays the same, the acceptance
-// tests of the following proposals are independent, so the warp tests 32 at a
-// time against c, finds the first acceptance with a ballot, records the
-// rejections before it and moves c there.
+// computed first and each chain is a scan over its proposals.  The scan is
+// made parallel across chunks of proposals without changing a single decision.
 //
-// Each test is decided first in float with a rigorous error margin and falls
-// back to the IEEE double expression only when the margin cannot decide: on
-// GB300 a double instruction occupies the FP64 pipe of a sub-partition for
-// tens of cycles, and a scan is a chain of dependent tests.  The decision is
-// always the one the double expression takes, so the chains are identical bit
-// for bit to a one-at-a-time double-precision scan.
+// Acceptance of proposal j depends on the current state c only through its
+// weight w_c (w = logL/T - log g, or logL - log g for the literal form), and it
+// is monotone in w_c: the IEEE difference fl(w_j - w_c) does not increase when
+// w_c does, and neither does its quotient by a positive T.  So the set of
+// current weights that accept j is {w_c <= tau_j} for one double tau_j (or
+// empty), found exactly from a first guess w_j - log u_j and a few evaluations
+// of the double test (a bisection over the ordered doubles when the guess is
+// more than three steps away).  Mapping doubles to order-preserving integers
+// ("keys") turns the scan into integer comparisons:
+//     state key s (key of w_c);  proposal j is accepted iff s <= K_j.
+//
+// Launches:
+//   summary  one CTA per (chain, chunk).  The first accepted proposal of the
+//            chunk, for an unknown incoming state, is one of the prefix
+//            records of K (positions where K exceeds every earlier K); for
+//            each record the CTA follows the chain from there to the chunk's
+//            end and stores the exit state and acceptance count.  K and the
+//            state keys go to global memory for the write launch.
+//   combine  a sequential pass over the chunk summaries (the first record
+//            with s <= K_r gives the exit) that yields the incoming state of
+//            every chunk and the acceptance count: inside each write CTA for
+//            chains of at most 32 chunks, else one CTA per chain beforehand.
+//   write    one CTA per (chain, chunk): from its incoming state, follows the
+//            chain through the chunk and writes the state after every step.
+// A chunk with more than 32 records, and every chunk of a literal-form chain
+// whose T is not a positive finite number (where the test is not monotone),
+// is scanned with the double test itself in the combine and write launches.
+// Every decision equals the one a one-at-a-time double-precision scan takes.
 #include <cfloat>
+#include <climits>
 #include <cmath>
 
 #include "gb_internal.cuh"
+
+#ifndef GB_MH_CHUNK
+#define GB_MH_CHUNK 512
+#endif
 
 namespace gb {
 namespace {
 
 constexpr int kMhThreads = 256;
-constexpr int kMhChunk = 8192;   // proposals staged in shared memory at a time
+constexpr int kMhWarps = kMhThreads / 32;
+constexpr int kMhChunk = GB_MH_CHUNK;   // proposals per chunk
+constexpr int kMhRec = 32;              // records summarised per chunk
+constexpr int kCombineBatch = 32;       // chunk summaries staged in shared memory at a time
 
-// one weight per proposal; x / 1 == x exactly, so T = 1 skips the division
-__device__ __forceinline__ double weight(double l, double g, double T, int literal) {
-    return (literal || T == 1.0) ? __dadd_rn(l, -g) : __dadd_rn(__ddiv_rn(l, T), -g);
+static_assert(kMhChunk % 32 == 0 && kMhChunk >= 32 && kMhChunk <= 2048, "chunk size");
+
+struct MhSummary {          // one per (chain, chunk)
+    long long K[kMhRec];    // threshold keys of the records, increasing
+    long long s[kMhRec];    // exit state key when the chunk is entered through record r
+    int32_t c[kMhRec];      // exit state index
+    int32_t n[kMhRec];      // acceptances on that path, the record included
+    int32_t count;          // records, or -1: scan this chunk with the double test
+    int32_t pad[3];
+};
+struct MhEntry {            // incoming state of a chunk
+    long long s;
+    int32_t c;
+    int32_t pad;
+};
+
+constexpr long long kSignMask = 0x7FFFFFFFFFFFFFFFLL;
+constexpr long long kEmpty = LLONG_MIN;      // threshold of a proposal no state accepts
+constexpr long long kNaNState = LLONG_MAX;   // key of a NaN weight: accepts nothing
+constexpr long long kKeyNegInf = -0x7FF0000000000000LL;
+constexpr long long kKeyPosInf = 0x7FF0000000000000LL;
+
+__device__ __forceinline__ bool is_nan(double x) {
+    return (__double_as_longlong(x) & kSignMask) > kKeyPosInf;
+}
+// order key of a non-NaN double: x < y  <=>  key(x) < key(y); -0 and +0 share key 0
+__device__ __forceinline__ long long dkey(double x) {
+    const long long b = __double_as_longlong(x);
+    return b >= 0 ? b : -(b & kSignMask);
+}
+__device__ __forceinline__ double from_key(long long k) {
+    return k >= 0 ? __longlong_as_double(k) : __longlong_as_double((-k) | LLONG_MIN);
+}
+__device__ __forceinline__ long long state_key(double w) { return is_nan(w) ? kNaNState : dkey(w); }
+
+// The three forms of the test, fixed at compile time so that no division is
+// issued where the rule has none:
+//   kPlain    w = logL - log g,      Delta = w_i - w_c   (either form at T = 1)
+//   kTempered w = logL/T - log g,    Delta = w_i - w_c   (default form)
+//   kDivide   v = logL - log g,      Delta = (v_i - v_c)/T   (literal form)
+enum { kPlain = 0, kTempered = 1, kDivide = 2 };
+
+__device__ __forceinline__ int rule_of(double T, int literal) {
+    return T == 1.0 ? kPlain : (literal ? kDivide : kTempered);
+}
+// the threshold form holds unless the literal rule divides by a T that is not positive and finite
+__device__ __forceinline__ bool keys_valid(int rule, double T) { return rule != kDivide || (T > 0.0 && T <= DBL_MAX); }
+
+// weight of one proposal, in the oracle's rounding order
+template <int RULE>
+__device__ __forceinline__ double weight(double l, double g, double T) {
+    if (RULE == kTempered) return __dadd_rn(__ddiv_rn(l, T), -g);
+    return __dadd_rn(l, -g);
 }
 
-// Eq. 13 in double: Delta = w_i - w_c (default) or (v_i - v_c)/T (literal);
-// accept iff log u < min(0, Delta); a NaN Delta rejects.
-__device__ __forceinline__ bool accept_exact(double wi, double ui, double wc, double T, int literal) {
-    double delta = __dadd_rn(wi, -wc);
-    if (literal && T != 1.0) delta = __ddiv_rn(delta, T);
-    return !isnan(delta) && (ui < fmin(0.0, delta));
+// Eq. 13: accept iff log u < min(0, Delta); a NaN Delta (or NaN log u) rejects
+template <int RULE>
+__device__ __forceinline__ bool accept(double wj, double uj, double wc, double T) {
+    double d = __dadd_rn(wj, -wc);
+    if (RULE == kDivide) d = __ddiv_rn(d, T);
+    if (is_nan(d) || is_nan(uj)) return false;
+    const long long ku = dkey(uj);
+    return ku < 0 && ku < dkey(d);
 }
 
-// The same decision from float copies W = fl(w), U = fl(u) when Delta = w_i - w_c:
-// 1 accept, 0 reject, -1 undecided.  With rounding to nearest,
-//   |fl(W_i - W_c) - fl64(w_i - w_c)| < 2^-23 (|W_i| + |W_c| + |D|) and
-//   |U - u| < 2^-23 |U|,
-// so a gap between U and D above M = 2^-22 (|W_i| + |W_c| + |D| + |U|) decides
-// u < Delta exactly; U < 0 implies u < 0.  Non-finite values are undecided.
-__device__ __forceinline__ int accept_fast(float Wi, float Ui, float Wc) {
-    if (!(fabsf(Wi) <= FLT_MAX) || !(fabsf(Wc) <= FLT_MAX) || !(Ui < 0.0f)) return -1;
-    const float D = Wi - Wc;
-    if (!(fabsf(D) <= FLT_MAX)) return -1;
-    const float M = 2.384185791015625e-07f * (fabsf(Wi) + fabsf(Wc) + fabsf(D) + fabsf(Ui)) + 1e-37f;
-    if (Ui - D > M) return 0;
-    if (D - Ui > M) return 1;
-    return -1;
+// Largest key k with accept(w, u, from_key(k)), or kEmpty.  Needs the test to
+// be monotone (plain and tempered rules, or T positive and finite).  For u < 0
+// the set is empty exactly when w is NaN or -inf (Delta is then NaN or -inf
+// for every state); otherwise accept(.., -inf) holds, and accept(.., +inf)
+// never does.
+template <int RULE>
+__device__ long long threshold(double w, double u, double T) {
+    if (is_nan(u) || dkey(u) >= 0 || is_nan(w) || dkey(w) == kKeyNegInf) return kEmpty;
+    long long lo = kKeyNegInf, hi = kKeyPosInf;   // accept(lo) holds, accept(hi) does not
+    const double g = RULE == kDivide ? __dadd_rn(w, -__dmul_rn(u, T)) : __dadd_rn(w, -u);
+    if (!is_nan(g)) {
+        long long k = min(max(dkey(g), kKeyNegInf), kKeyPosInf);
+        if (accept<RULE>(w, u, from_key(k), T)) {
+            lo = k;
+            for (int it = 0; it < 3 && lo + 1 < hi; ++it) {
+                if (!accept<RULE>(w, u, from_key(lo + 1), T)) return lo;
+                ++lo;
+            }
+        } else {
+            hi = k;
+            for (int it = 0; it < 3 && hi - 1 > lo; ++it) {
+                if (accept<RULE>(w, u, from_key(hi - 1), T)) return hi - 1;
+                --hi;
+            }
+        }
+    }
+    while ((unsigned long long)hi - (unsigned long long)lo > 1ULL) {
+        const long long mid = lo + (long long)(((unsigned long long)hi - (unsigned long long)lo) >> 1);
+        if (accept<RULE>(w, u, from_key(mid), T)) lo = mid;
+        else hi = mid;
+    }
+    return lo;
 }
 
-__global__ void __launch_bounds__(kMhThreads) mh_kernel(int n, int chunk, const double* __restrict__ logL,
-                                                        const double* __restrict__ log_g,
-                                                        const double* __restrict__ log_u,
-                                                        const double* __restrict__ temperature, int literal,
-                                                        int32_t* __restrict__ chain, int32_t* __restrict__ n_accept) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* ws = (double*)smem_raw;   // chunk
-    float* Wf = (float*)(ws + chunk); // chunk
-    float* Uf = Wf + chunk;           // chunk
+// thresholds and state keys of the proposals [p0, p0 + len) into shared memory
+template <int RULE>
+__device__ void chunk_keys(const double* L, const double* G, const double* U, double T, int p0, int len,
+                           long long* K, long long* S) {
+    for (int j = threadIdx.x; j < len; j += blockDim.x) {
+        const double w = weight<RULE>(L[p0 + j], G[p0 + j], T);
+        S[j] = state_key(w);
+        K[j] = threshold<RULE>(w, U[p0 + j], T);
+    }
+}
+
+// first local position >= p (below len) whose proposal a state of key s accepts, else len
+__device__ __forceinline__ int next_accept(const long long* K, int p, int len, long long s, int lane) {
+    for (int b = p; b < len; b += 32) {
+        const int j = b + lane;
+        const unsigned ball = __ballot_sync(0xffffffffu, j < len && s <= K[j]);
+        if (ball) return b + __ffs(ball) - 1;
+    }
+    return len;
+}
+
+// One warp scans proposals [a, b) with the double test from state c (weight
+// wc); writes the state after every step into out when out is not null.
+template <int RULE>
+__device__ void scan_exact(const double* L, const double* G, const double* U, double T, int a, int b, int& c,
+                           double& wc, int& n_acc, int32_t* out, int lane) {
+    int p = a;
+    while (p < b) {
+        int hit = -1;
+        for (int base = p; base < b; base += 32) {
+            const int j = base + lane;
+            double wj = 0.0;
+            bool ok = false;
+            if (j < b) {
+                wj = weight<RULE>(L[j], G[j], T);
+                ok = accept<RULE>(wj, U[j], wc, T);
+            }
+            const unsigned ball = __ballot_sync(0xffffffffu, ok);
+            const int stop = ball ? base + __ffs(ball) - 1 : min(b, base + 32);
+            if (out && j < stop) out[j] = c;
+            if (ball) {
+                hit = stop;
+                wc = __shfl_sync(0xffffffffu, wj, __ffs(ball) - 1);
+                break;
+            }
+        }
+        if (hit < 0) break;
+        c = hit;
+        if (out && lane == 0) out[c] = c;
+        ++n_acc;
+        p = hit + 1;
+    }
+}
+
+// run-time dispatch on the chain's rule (uniform within a CTA)
+__device__ __forceinline__ double weight_rt(int rule, double l, double g, double T) {
+    return rule == kTempered ? weight<kTempered>(l, g, T) : weight<kPlain>(l, g, T);
+}
+__device__ __forceinline__ void chunk_keys_rt(int rule, const double* L, const double* G, const double* U, double T,
+                                              int p0, int len, long long* K, long long* S) {
+    if (rule == kPlain) chunk_keys<kPlain>(L, G, U, T, p0, len, K, S);
+    else if (rule == kTempered) chunk_keys<kTempered>(L, G, U, T, p0, len, K, S);
+    else chunk_keys<kDivide>(L, G, U, T, p0, len, K, S);
+}
+__device__ __forceinline__ void scan_exact_rt(int rule, const double* L, const double* G, const double* U, double T,
+                                              int a, int b, int& c, double& wc, int& n_acc, int32_t* out, int lane) {
+    if (rule == kPlain) scan_exact<kPlain>(L, G, U, T, a, b, c, wc, n_acc, out, lane);
+    else if (rule == kTempered) scan_exact<kTempered>(L, G, U, T, a, b, c, wc, n_acc, out, lane);
+    else scan_exact<kDivide>(L, G, U, T, a, b, c, wc, n_acc, out, lane);
+}
+
+// chunk k of a chain covers proposals [1 + k C, min(n, 1 + (k+1) C))
+__device__ __forceinline__ int chunk_start(int k) { return 1 + k * kMhChunk; }
+
+constexpr int kSegWin = kMhChunk / kMhThreads > 0 ? kMhChunk / kMhThreads : 1;   // 32-wide windows per warp
+
+// Summary of one (chain, chunk): thresholds and state keys (kept in global
+// memory for the write launch), prefix records of the thresholds, and for
+// each record the exit state of the chain entered there.
+__global__ void __launch_bounds__(kMhThreads) mh_summary_kernel(int n, int n_chunks, const double* __restrict__ logL,
+                                                                const double* __restrict__ log_g,
+                                                                const double* __restrict__ log_u,
+                                                                const double* __restrict__ temperature, int literal,
+                                                                MhSummary* __restrict__ sum, long long* __restrict__ gK,
+                                                                long long* __restrict__ gS) {
+    __shared__ long long K[kMhChunk], S[kMhChunk];
+    __shared__ signed char rec_id[kMhChunk];
+    __shared__ int rec_pos[kMhRec], rec_link[kMhRec], rec_c[kMhRec], rec_n[kMhRec];
+    __shared__ long long rec_s[kMhRec], seg_max[kMhWarps];
+    __shared__ int seg_cnt[kMhWarps];
+    const int r = blockIdx.x / n_chunks, k = blockIdx.x - r * n_chunks;
+    MhSummary& out = sum[(size_t)r * n_chunks + k];
+    const double T = temperature[r];
+    const int rule = rule_of(T, literal);
+    if (!keys_valid(rule, T)) {
+        if (threadIdx.x == 0) out.count = -1;
+        return;
+    }
+    const size_t base = (size_t)r * (size_t)n;
+    const int p0 = chunk_start(k), len = min(kMhChunk, n - p0);
+    chunk_keys_rt(rule, logL + base, log_g + base, log_u + base, T, p0, len, K, S);
+    for (int j = threadIdx.x; j < len; j += blockDim.x) rec_id[j] = -1;
+    __syncthreads();
+    for (int j = threadIdx.x; j < len; j += blockDim.x) {
+        gK[base + p0 + j] = K[j];
+        gS[base + p0 + j] = S[j];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // prefix records of K: each warp takes kSegWin consecutive windows
+    long long v[kSegWin], exc[kSegWin];
+    long long run = kEmpty;
+#pragma unroll
+    for (int q = 0; q < kSegWin; ++q) {
+        const int j = (warp * kSegWin + q) * 32 + lane;
+        v[q] = j < len ? K[j] : kEmpty;
+        long long inc = v[q];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc = max(inc, t);
+        }
+        const long long e = __shfl_up_sync(0xffffffffu, inc, 1);
+        exc[q] = lane == 0 ? run : max(run, e);
+        run = max(run, __shfl_sync(0xffffffffu, inc, 31));
+    }
+    if (lane == 0) seg_max[warp] = run;
+    __syncthreads();
+    long long before = kEmpty;
+    for (int w = 0; w < warp; ++w) before = max(before, seg_max[w]);
+    unsigned balls[kSegWin];
+    int mine = 0;
+#pragma unroll
+    for (int q = 0; q < kSegWin; ++q) {
+        const int j = (warp * kSegWin + q) * 32 + lane;
+        balls[q] = __ballot_sync(0xffffffffu, j < len && v[q] > max(before, exc[q]));
+        mine += __popc(balls[q]);
+    }
+    if (lane == 0) seg_cnt[warp] = mine;
+    __syncthreads();
+    int off = 0, cnt = 0;
+    for (int w = 0; w < kMhWarps; ++w) {
+        if (w < warp) off += seg_cnt[w];
+        cnt += seg_cnt[w];
+    }
+    if (cnt > kMhRec) {
+        if (threadIdx.x == 0) out.count = -1;
+        return;
+    }
+#pragma unroll
+    for (int q = 0; q < kSegWin; ++q) {
+        if (balls[q] >> lane & 1u) {
+            const int j = (warp * kSegWin + q) * 32 + lane;
+            const int id = off + __popc(balls[q] & ((1u << lane) - 1u));
+            rec_pos[id] = j;
+            rec_id[j] = (signed char)id;
+        }
+        off += __popc(balls[q]);
+    }
+    __syncthreads();
+    // follow the chain from each record until the chunk ends or it reaches a later record
+    for (int m = warp; m < cnt; m += kMhWarps) {
+        int c = rec_pos[m], acc = 1, link = -1;
+        long long s = S[c];
+        for (;;) {
+            const int j = next_accept(K, c + 1, len, s, lane);
+            if (j >= len) break;
+            if (rec_id[j] >= 0) {
+                link = rec_id[j];
+                break;
+            }
+            c = j;
+            s = S[j];
+            ++acc;
+        }
+        if (lane == 0) {
+            rec_link[m] = link;
+            rec_c[m] = c;
+            rec_s[m] = s;
+            rec_n[m] = acc;
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        // a path that reaches record m' continues as m' does: resolve the links
+        // (they point to later records) by pointer jumping
+        int link = -1, c = 0, acc = 0;
+        long long s = 0;
+        if (lane < cnt) {
+            link = rec_link[lane];
+            c = rec_c[lane];
+            s = rec_s[lane];
+            acc = rec_n[lane];
+        }
+        for (int step = 0; step < 5; ++step) {
+            const int src = link >= 0 ? link : lane;
+            const int link2 = __shfl_sync(0xffffffffu, link, src);
+            const int c2 = __shfl_sync(0xffffffffu, c, src);
+            const long long s2 = __shfl_sync(0xffffffffu, s, src);
+            const int acc2 = __shfl_sync(0xffffffffu, acc, src);
+            if (link >= 0) {
+                acc += acc2;
+                c = c2;
+                s = s2;
+                link = link2;
+            }
+        }
+        if (lane < cnt) {
+            out.K[lane] = K[rec_pos[lane]];
+            out.s[lane] = s;
+            out.c[lane] = p0 + c;
+            out.n[lane] = acc;
+        }
+        if (lane == 0) out.count = cnt;
+    }
+}
+
+// Chunk summaries [0, nb) staged in shared memory, applied in order by one
+// warp to the state (c, s); a chunk without a summary is scanned with the
+// double test.  Returns through c, s, acc.
+struct StagedSummaries {
+    long long K[kCombineBatch][kMhRec], s[kCombineBatch][kMhRec];
+    int c[kCombineBatch][kMhRec], n[kCombineBatch][kMhRec], count[kCombineBatch];
+};
+
+__device__ void stage_summaries(StagedSummaries& st, const MhSummary* sm, int nb) {
+    for (int i = threadIdx.x; i < nb * kMhRec; i += blockDim.x) {
+        const int b = i / kMhRec, l = i - b * kMhRec;
+        const MhSummary& t = sm[b];
+        if (l == 0) st.count[b] = t.count;
+        st.K[b][l] = t.K[l];
+        st.s[b][l] = t.s[l];
+        st.c[b][l] = t.c[l];
+        st.n[b][l] = t.n[l];
+    }
+}
+
+__device__ void apply_summaries(const StagedSummaries& st, int k0, int nb, int n, int rule, double T,
+                                const double* L, const double* G, const double* U, MhEntry* en, int& c,
+                                long long& s, int& acc, int lane) {
+    for (int b = 0; b < nb; ++b) {
+        const int k = k0 + b;
+        if (en && lane == 0) {
+            en[k].s = s;
+            en[k].c = c;
+        }
+        const int cnt = st.count[b];
+        if (cnt >= 0) {
+            const unsigned ball = __ballot_sync(0xffffffffu, lane < cnt && s <= st.K[b][lane]);
+            if (ball) {
+                const int f = __ffs(ball) - 1;
+                c = st.c[b][f];
+                s = st.s[b][f];
+                acc += st.n[b][f];
+            }
+        } else {
+            const int p0 = chunk_start(k);
+            double wc = weight_rt(rule, L[c], G[c], T);
+            scan_exact_rt(rule, L, G, U, T, p0, min(n, p0 + kMhChunk), c, wc, acc, nullptr, lane);
+            s = state_key(wc);
+        }
+    }
+}
+
+// Incoming state of every chunk and the acceptance count, for chains of more
+// than kCombineBatch chunks (shorter chains combine inside the write launch).
+__global__ void __launch_bounds__(kMhThreads) mh_combine_kernel(int n, int n_chunks, const double* __restrict__ logL,
+                                                                const double* __restrict__ log_g,
+                                                                const double* __restrict__ log_u,
+                                                                const double* __restrict__ temperature, int literal,
+                                                                const MhSummary* __restrict__ sum,
+                                                                MhEntry* __restrict__ entry, int32_t* __restrict__ chain,
+                                                                int32_t* __restrict__ n_accept) {
+    __shared__ StagedSummaries st;
     const int r = blockIdx.x;
+    const size_t base = (size_t)r * (size_t)n;
+    const double* L = logL + base;
+    const double* G = log_g + base;
+    const double* U = log_u + base;
+    const double T = temperature[r];
+    const int rule = rule_of(T, literal);
+    const MhSummary* sm = sum + (size_t)r * n_chunks;
+    MhEntry* en = entry + (size_t)r * n_chunks;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int c = 0, acc = 0;
+    long long s = state_key(weight_rt(rule, L[0], G[0], T));
+    if (threadIdx.x == 0) chain[base] = 0;
+    for (int k0 = 0; k0 < n_chunks; k0 += kCombineBatch) {
+        const int nb = min(kCombineBatch, n_chunks - k0);
+        __syncthreads();
+        stage_summaries(st, sm + k0, nb);
+        __syncthreads();
+        if (warp == 0) apply_summaries(st, k0, nb, n, rule, T, L, G, U, en, c, s, acc, lane);
+    }
+    if (threadIdx.x == 0 && n_accept) n_accept[r] = acc;
+}
+
+// Writes the chain through one chunk from its incoming state: read from
+// `entry` when given, else combined here from the summaries of the earlier
+// chunks (at most kCombineBatch of them).  The last chunk of a chain also
+// writes the acceptance count in that case, the first one chain[0].
+__global__ void __launch_bounds__(kMhThreads) mh_write_kernel(int n, int n_chunks, const double* __restrict__ logL,
+                                                              const double* __restrict__ log_g,
+                                                              const double* __restrict__ log_u,
+                                                              const double* __restrict__ temperature, int literal,
+                                                              const MhSummary* __restrict__ sum,
+                                                              const MhEntry* __restrict__ entry,
+                                                              const long long* __restrict__ gK,
+                                                              const long long* __restrict__ gS,
+                                                              int32_t* __restrict__ chain, int32_t* __restrict__ n_accept) {
+    __shared__ long long K[kMhChunk], S[kMhChunk];
+    __shared__ StagedSummaries st;
+    __shared__ int in_c, in_acc;
+    __shared__ long long in_s;
+    const int r = blockIdx.x / n_chunks, k = blockIdx.x - r * n_chunks;
     const size_t base = (size_t)r * (size_t)n;
     const double* L = logL + base;
     const double* G = log_g + base;
     const double* U = log_u + base;
     int32_t* out = chain + base;
     const double T = temperature[r];
-    const bool fast = !literal || T == 1.0;
+    const int rule = rule_of(T, literal);
+    const size_t slot = (size_t)r * n_chunks + k;
+    const int p0 = chunk_start(k), len = min(kMhChunk, n - p0);
+    const bool keyed = sum[slot].count >= 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int c = 0;
-    double wc = weight(L[0], G[0], T, literal);
-    float Wc = (float)wc;
-    int acc = 0;
-    if (threadIdx.x == 0) out[0] = 0;
-    for (int p0 = 1; p0 < n; p0 += chunk) {
-        const int len = min(chunk, n - p0);
-        __syncthreads();   // the previous chunk is scanned
+    if (keyed)
         for (int j = threadIdx.x; j < len; j += blockDim.x) {
-            const double w = weight(L[p0 + j], G[p0 + j], T, literal);
-            ws[j] = w;
-            Wf[j] = (float)w;
-            Uf[j] = (float)U[p0 + j];
+            K[j] = gK[base + p0 + j];
+            S[j] = gS[base + p0 + j];
         }
+    if (entry) {
+        if (threadIdx.x == 0) {
+            in_c = entry[slot].c;
+            in_s = entry[slot].s;
+            in_acc = 0;
+        }
+    } else {
+        stage_summaries(st, sum + (size_t)r * n_chunks, k);
         __syncthreads();
-        if (warp != 0) continue;
-        int lo = 0;
-        while (lo < len) {
-            int a = len;
-            for (int b = lo; b < len; b += 32) {
+        if (warp == 0) {
+            int c = 0, acc = 0;
+            long long s = state_key(weight_rt(rule, L[0], G[0], T));
+            apply_summaries(st, 0, k, n, rule, T, L, G, U, nullptr, c, s, acc, lane);
+            if (lane == 0) {
+                in_c = c;
+                in_s = s;
+                in_acc = acc;
+            }
+        }
+        if (k == 0 && threadIdx.x == 0) out[0] = 0;
+    }
+    __syncthreads();
+    if (warp != 0) return;
+    int c = in_c, acc = in_acc;
+    long long s = in_s;
+    if (!keyed) {
+        double wc = weight_rt(rule, L[c], G[c], T);
+        scan_exact_rt(rule, L, G, U, T, p0, p0 + len, c, wc, acc, out, lane);
+    } else {
+        int p = 0;
+        while (p < len) {
+            int hit = -1;
+            for (int b = p; b < len; b += 32) {
                 const int j = b + lane;
-                bool ok = false;
-                if (j < len) {
-                    const double wj = ws[j];
-                    // w = -inf (a proposal outside the prior) is never accepted
-                    if (__double_as_longlong(wj) != (long long)0xFFF0000000000000ULL) {
-                        int d = fast ? accept_fast(Wf[j], Uf[j], Wc) : -1;
-                        if (d < 0) d = accept_exact(wj, U[p0 + j], wc, T, literal) ? 1 : 0;
-                        ok = d == 1;
-                    }
-                }
-                const unsigned ball = __ballot_sync(0xffffffffu, ok);
+                const unsigned ball = __ballot_sync(0xffffffffu, j < len && s <= K[j]);
                 const int stop = ball ? b + __ffs(ball) - 1 : min(len, b + 32);
-                if (j < stop) out[p0 + j] = c;   // rejections up to the acceptance
+                if (j < stop) out[p0 + j] = c;
                 if (ball) {
-                    a = stop;
+                    hit = stop;
                     break;
                 }
             }
-            if (a < len) {
-                c = p0 + a;
-                wc = ws[a];
-                Wc = Wf[a];
-                if (lane == 0) out[c] = c;
-                ++acc;
-            }
-            lo = a + 1;
+            if (hit < 0) break;
+            c = p0 + hit;
+            s = S[hit];
+            if (lane == 0) out[c] = c;
+            ++acc;
+            p = hit + 1;
         }
     }
-    if (threadIdx.x == 0 && n_accept) n_accept[r] = acc;
+    if (!entry && k == n_chunks - 1 && lane == 0 && n_accept) n_accept[r] = acc;
 }
 
 }  // namespace
+
+int ensure_mh_scratch(gb_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->mh_bytes) return GB_OK;
+    if (ctx->d_mh) cudaFree(ctx->d_mh);
+    ctx->d_mh = nullptr;
+    ctx->mh_bytes = 0;
+    cudaError_t e = cudaMalloc(&ctx->d_mh, bytes);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? set_error(ctx, GB_ENOMEM, "MH scratch")
+                                                                 : cuda_error(ctx, e, "MH scratch");
+    ctx->mh_bytes = bytes;
+    return GB_OK;
+}
+
+// summaries and incoming states per (chain, chunk), then two int64 keys per proposal
+size_t mh_scratch_bytes(size_t chunk_slots, size_t proposals) {
+    return chunk_slots * (sizeof(MhSummary) + sizeof(MhEntry)) + proposals * 2 * sizeof(long long);
+}
+
 }  // namespace gb
 
 using namespace gb;
@@ -143,12 +568,31 @@ extern "C" int gb_mh_independence(gb_ctx_t* ctx, int32_t n_chains, int32_t n, co
     if (literal != 0 && literal != 1) return set_error(ctx, GB_EINVAL, "gb_mh_independence: literal must be 0 or 1");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_error(ctx, e, "gb_mh_independence: cudaSetDevice");
-    const int chunk = n - 1 < kMhChunk ? (n - 1 > 0 ? n - 1 : 1) : kMhChunk;
-    const size_t smem = (sizeof(double) + 2 * sizeof(float)) * (size_t)chunk;
-    e = cudaFuncSetAttribute(mh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_mh_independence: smem attribute");
-    mh_kernel<<<n_chains, kMhThreads, smem, (cudaStream_t)stream>>>(n, chunk, logL, log_g, log_u, temperature,
-                                                                     literal, chain_idx, n_accept);
+    const int n_chunks = (n - 1 + kMhChunk - 1) / kMhChunk;
+    const size_t slots = (size_t)n_chains * (size_t)n_chunks;
+    if (slots > (size_t)INT_MAX) return set_error(ctx, GB_EINVAL, "gb_mh_independence: too many chunks");
+    const size_t props = (size_t)n_chains * (size_t)n;
+    int rc = ensure_mh_scratch(ctx, mh_scratch_bytes(slots > 0 ? slots : 1, props));
+    if (rc != GB_OK) return rc;
+    MhSummary* sum = (MhSummary*)ctx->d_mh;
+    MhEntry* entry = (MhEntry*)(sum + slots);
+    long long* gK = (long long*)(entry + slots);
+    long long* gS = gK + props;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool fused = n_chunks > 0 && n_chunks <= kCombineBatch;
+    if (n_chunks > 0)
+        mh_summary_kernel<<<(unsigned)slots, kMhThreads, 0, st>>>(n, n_chunks, logL, log_g, log_u, temperature,
+                                                                  literal, sum, gK, gS);
+    if (n_chunks > 0) ++ctx->launches;
+    if (!fused)
+        mh_combine_kernel<<<n_chains, kMhThreads, 0, st>>>(n, n_chunks, logL, log_g, log_u, temperature, literal,
+                                                           sum, entry, chain_idx, n_accept);
+    if (!fused) ++ctx->launches;
+    if (n_chunks > 0)
+        mh_write_kernel<<<(unsigned)slots, kMhThreads, 0, st>>>(n, n_chunks, logL, log_g, log_u, temperature,
+                                                                literal, sum, fused ? nullptr : entry, gK, gS,
+                                                                chain_idx, n_accept);
+    if (n_chunks > 0) ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "gb_mh_independence launch");
     return GB_OK;

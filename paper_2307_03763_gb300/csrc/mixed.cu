@@ -639,6 +639,7 @@ int launch_loglik_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const d
     if (plan.n_tiles == 0) return GB_OK;
     prep_mixed_kernel<<<plan.n_win, 256, 0, s>>>(plan.d_win, plan.d_meta, plan.d_prep, (const double2*)dA,
                                                  (const double2*)dE, wA, wE, ctx->obs.T_obs, plan.d_head);
+    ++ctx->launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "prep_mixed launch");
     int sms = 152;
@@ -670,6 +671,7 @@ int launch_loglik_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const d
                 plan.d_win, plan.d_meta, plan.d_prep, items, n_items, head, tabset32(ctx),
                 (const float2*)ctx->d_tw32, ctx->obs.T_obs, transfer_frequency(ctx), theta, logL, dh, hh,
                 ctx->d_status, nmax);
+        ++ctx->launches;
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_error(ctx, e, "loglik_mixed launch");
     }
@@ -690,6 +692,7 @@ int launch_waveform_mixed(gb_ctx* ctx, const double* theta, int64_t B, int N, do
     waveform_mixed_kernel<<<(unsigned)blocks, kWarpsMx * 32, smem, s>>>(
         tables32(ctx, N), (const float2*)ctx->d_tw32, ctx->obs.T_obs, transfer_frequency(ctx), N, theta, B,
         (int)group, (double2*)hA, (double2*)hE, q, ctx->d_status);
+    ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "waveform_mixed launch");
     return GB_OK;
@@ -1380,6 +1383,7 @@ int launch_grad_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const dou
     if (plan.n_tiles == 0) return GB_OK;
     prep_mixed_kernel<<<plan.n_win, 256, 0, s>>>(plan.d_win, plan.d_meta, plan.d_prep, (const double2*)dA,
                                                  (const double2*)dE, wA, wE, ctx->obs.T_obs, plan.d_head);
+    ++ctx->launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "prep_mixed launch");
     int sms = 152;
@@ -1407,6 +1411,7 @@ int launch_grad_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const dou
             grad_mixed_kernel<8><<<grid, kWarpsMx * 32, smem, s>>>(
                 plan.d_win, plan.d_meta, plan.d_prep, items, n_items, head, tabset32(ctx), (const float2*)ctx->d_tw32,
                 ctx->obs.T_obs, transfer_frequency(ctx), theta, logL, grad, ctx->d_status, nmax);
+        ++ctx->launches;
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_error(ctx, e, "grad_mixed launch");
     }

@@ -44,8 +44,8 @@ def unit_snr(src, window, wA, wE, T):
     return float(np.sqrt(hh))
 
 
-def fisher_sigma(src, window, wA, wE, T, rel=1e-4):
-    """sqrt(diag F^-1) of F_ij = <d_i h|d_j h> on the window (oracle, central differences)."""
+def fisher_matrix(src, window, wA, wE, T, rel=1e-4):
+    """F_ij = <d_i h|d_j h> on the window (oracle templates, central differences)."""
     k0, W, N, doff, _, _ = window
     wa, we = wA[doff:doff + W], wE[doff:doff + W]
     scales = np.array([1.0 / T, 1.0 / T ** 2, 1.0, 1.0, src[4], 1.0, 1.0, 1.0])
@@ -63,4 +63,10 @@ def fisher_sigma(src, window, wA, wE, T, rel=1e-4):
         for j in range(8):
             F[i, j] = (4.0 / T) * (np.sum(wa * (J[i][0] * J[j][0].conj()).real)
                                    + np.sum(we * (J[i][1] * J[j][1].conj()).real))
+    return F
+
+
+def fisher_sigma(src, window, wA, wE, T, rel=1e-4):
+    """sqrt(diag F^-1) of the window's Fisher matrix."""
+    F = fisher_matrix(src, window, wA, wE, T, rel)
     return np.sqrt(np.abs(np.diag(np.linalg.pinv(F))))

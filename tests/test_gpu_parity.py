@@ -315,6 +315,41 @@ def test_mh_golden_and_edge_cases(ctx):
         assert np.array_equal(c, oc) and np.array_equal(a, oa)
 
 
+def _mh_adversarial_rows(rng, n):
+    """Rows that reach every path of the chunked scan: sorted weights (more
+    records per chunk than are summarised), special values, weights of 1e20
+    where the first threshold guess is many doubles off, tiny |log u|."""
+    rows = []
+    L = np.sort(rng.normal(0, 50, n))
+    rows.append((L, np.zeros(n), np.log(rng.uniform(size=n))))
+    L, G, U = rng.normal(0, 3, n), rng.normal(0, 1, n), np.log(rng.uniform(size=n))
+    for a in (L, G, U):
+        m = rng.uniform(size=n) < 0.02
+        a[m] = rng.choice([np.inf, -np.inf, np.nan, 0.0, -0.0], m.sum())
+    rows.append((L, G, U))
+    rows.append((1e20 + rng.integers(-4, 4, n) * 16384.0, -1e20 + rng.integers(-4, 4, n) * 16384.0,
+                 np.log(rng.uniform(size=n))))
+    rows.append((np.round(rng.normal(0, 3, n)), np.zeros(n), -rng.uniform(0, 1e-18, n)))
+    rows.append((rng.normal(-50, 4, n), rng.normal(0, 2, n), np.log(rng.uniform(size=n))))
+    return [np.stack(x) for x in zip(*rows)]
+
+
+@pytest.mark.parametrize("literal", [False, True])
+def test_mh_chunked_scan_adversarial(ctx, literal):
+    # every chain length around the chunk size, and one long enough that the
+    # chunk summaries are combined in several batches; temperatures that keep
+    # the threshold form (positive, finite) and ones that do not (literal form)
+    rng = np.random.default_rng(31 + literal)
+    temps = np.array([1.0, 0.7, 3.0, -2.0, np.inf, np.nan, 1e-300, 1e300])
+    for n in (2, 31, 511, 512, 513, 514, 1025, 40001):
+        L, G, U = _mh_adversarial_rows(rng, n)
+        rows = len(L)
+        for T in temps:
+            c, a, oc, oa = _mh_both(ctx, L, G, U, np.full(rows, T), literal)
+            assert np.array_equal(c, oc), (n, T, np.argwhere(c != oc)[:5])
+            assert np.array_equal(a, oa), (n, T)
+
+
 # --------------------------------------------------------------------------
 # gradient
 # --------------------------------------------------------------------------
@@ -404,6 +439,9 @@ def test_observed_fisher_matches_oracle_fisher(ctx):
     data = (_cuda(hA, torch.complex128), _cuda(hE, torch.complex128), _cuda(wl.w_A, torch.float64),
             _cuda(wl.w_E, torch.float64))
     F = ag.observed_fisher(ctx, wl.windows, *data, _cuda(src[None], torch.float64), prec="fp64")[0].cpu().numpy()
-    sig = np.sqrt(np.diag(np.linalg.pinv(F)))
-    ref = _data.fisher_sigma(src, wl.windows[0], wl.w_A, wl.w_E, wl.T)
-    assert np.allclose(sig, ref, rtol=2e-3), (sig, ref)
+    ref = _data.fisher_matrix(src, wl.windows[0], wl.w_A, wl.w_E, wl.T)
+    sc = np.array([1 / wl.T, 1 / wl.T ** 2, 1, 1, src[4], 1, 1, 1])
+    Fs, Rs = F * np.outer(sc, sc), ref * np.outer(sc, sc)
+    d = np.sqrt(np.outer(np.diag(Rs), np.diag(Rs)))
+    assert np.abs(Fs - Rs).max() <= 1e-5 * d.max() and (np.abs(Fs - Rs) / d).max() < 1e-4, (Fs, Rs)
+    assert np.all(np.linalg.eigvalsh(Fs) > -1e-9 * d.max())
