@@ -135,15 +135,18 @@ __device__ void setup_mixed(const double* th, double T, double fstar, CandMix& c
     c.f0 = (float)f0;
     c.fdT = (float)(fd * T);
     c.fdh = (float)(0.5 * fd);
-    c.a0 = (float)(f0 / (2.0 * fstar));
-    c.a1 = (float)(fd * T / (2.0 * fstar));
+    const double ifs = 1.0 / fstar;   // the float results do not see the reciprocal's rounding
+    c.a0 = (float)(0.5 * f0 * ifs);
+    c.a1 = (float)(0.5 * fd * T * ifs);
     float sD, cD;
-    sincosf((float)(f0 / fstar), &sD, &cD);
+    sincosf((float)(f0 * ifs), &sD, &cD);
     c.D0r = cD;
     c.D0i = -sD;
-    c.eps = (float)(fd * T / fstar);
-    // largest link argument X = f (1 + |k.n|)/(2 f*) <= f_max / f*
-    const double xmax = fmax(fabs(f0), fabs(f0 + fd * T)) / fstar;
+    c.eps = (float)(fd * T * ifs);
+    // largest link argument X = f (1 + |k.n|)/(2 f*) <= f_max / f*; the
+    // tier keeps the first omitted series term below 2e-8 (few tiers: every
+    // tier is a separate copy of the slow part in the instruction cache)
+    const double xmax = fmax(fabs(f0), fabs(f0 + fd * T)) * ifs;
     c.J = xmax <= 0.489 ? 4 : xmax <= 1.34 ? 7 : xmax <= 2.35 ? 10 : 0;
 }
 
@@ -166,20 +169,41 @@ __device__ __forceinline__ float2 link_transfer(float X) {
     return make_float2(re, -2.0f * X * im);
 }
 
-// exp(2 pi i x) for |x| <= 0.125, Taylor series of sin and cos of 2 pi x
-__device__ __forceinline__ float2 cis_small(float x) {
-    const float t = 6.2831853071795865f * x;
-    const float t2 = t * t;
-    float s = fmaf(t2, 2.7557319223985893e-06f, -1.9841269841269841e-04f);
-    s = fmaf(s, t2, 8.3333333333333332e-03f);
-    s = fmaf(s, t2, -1.6666666666666666e-01f);
-    s = fmaf(s * t2, t, t);
-    float co = fmaf(t2, -2.7557319223985888e-07f, 2.4801587301587302e-05f);
-    co = fmaf(co, t2, -1.3888888888888889e-03f);
-    co = fmaf(co, t2, 4.1666666666666664e-02f);
-    co = fmaf(co, t2, -0.5f);
-    co = fmaf(co, t2, 1.0f);
-    return make_float2(co, s);
+// exp(2 pi i x) for a receiver phase x = -f k.rho + ..., |x| <= xmax/(2 pi sqrt 3)
+// (each spacecraft is L/sqrt 3 from the guiding centre, and f L/c = xmax/(2 pi)):
+// Taylor series of sin and cos of t = 2 pi x, truncated where the first
+// omitted term is below 2e-8 for the tier's bound on t (J = 4: t <= 0.282,
+// 7: 0.774); sincospif above the J = 7 tier.
+template <int J>
+__device__ __forceinline__ float2 cis_rx(float x) {
+    if constexpr (J == 0 || J >= 10) {
+        float sn, cs;
+        sincospif(2.0f * x, &sn, &cs);
+        return make_float2(cs, sn);
+    } else {
+        const float t = 6.2831853071795865f * x;
+        const float t2 = t * t;
+        float s, co;
+        if constexpr (J <= 4) {
+            s = fmaf(t2, -1.9841269841269841e-04f, 8.3333333333333332e-03f);
+            s = fmaf(s, t2, -1.6666666666666666e-01f);
+            s = fmaf(s * t2, t, t);
+            co = fmaf(t2, -1.3888888888888889e-03f, 4.1666666666666664e-02f);
+            co = fmaf(co, t2, -0.5f);
+            co = fmaf(co, t2, 1.0f);
+        } else {
+            s = fmaf(t2, 2.7557319223985893e-06f, -1.9841269841269841e-04f);
+            s = fmaf(s, t2, 8.3333333333333332e-03f);
+            s = fmaf(s, t2, -1.6666666666666666e-01f);
+            s = fmaf(s * t2, t, t);
+            co = fmaf(t2, -2.7557319223985888e-07f, 2.4801587301587302e-05f);
+            co = fmaf(co, t2, -1.3888888888888889e-03f);
+            co = fmaf(co, t2, 4.1666666666666664e-02f);
+            co = fmaf(co, t2, -0.5f);
+            co = fmaf(co, t2, 1.0f);
+        }
+        return make_float2(co, s);
+    }
 }
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -244,7 +268,7 @@ __device__ void slow_part_mixed(const CandMix& c, const OrbitTables32& tab, int 
         for (int j = 0; j < 3; ++j) {
             const float kap = K + krho[j];
             const float dP = fmaf(-f, krho[j], c.fdh * kap * kap);
-            rx[j] = cis_small(dP);   // the common factor exp(2 pi i P_c) is applied once, below
+            rx[j] = cis_rx<J>(dP);   // the common factor exp(2 pi i P_c) is applied once, below
         }
         const float a = fmaf(c.a1, u, c.a0);
         // projections of the arms on k, u, v; arm 2->0 closes the triangle
@@ -399,7 +423,8 @@ __device__ void fft_inner(const float2* bufA, const float2* bufE, const OrbitTab
                           float& cdh, float& shh, float& chh) {
     constexpr int N = 32 * R;
     float2 x[R];
-#pragma unroll
+    // one copy of the transform for both channels (instruction-cache footprint)
+#pragma unroll 1
     for (int ch = 0; ch < 2; ++ch) {
         channel_fft<R>(ch == 0 ? bufA : bufE, tab, tw1024, ltw, lane, x);
 #pragma unroll
@@ -411,8 +436,9 @@ __device__ void fft_inner(const float2* bufA, const float2* bufE, const OrbitTab
                 const Win32 v = pw[kk];
                 const float2 d = ch == 0 ? v.dA : v.dE;
                 const float w = ch == 0 ? v.wA : v.wE;
-                kahan_add(sdh, cdh, w * fmaf(d.x, x[k1].x, d.y * x[k1].y));
-                kahan_add(shh, chh, w * fmaf(x[k1].x, x[k1].x, x[k1].y * x[k1].y));
+                // explicit products: the same rounding in every kernel that forms these sums
+                kahan_add(sdh, cdh, __fmul_rn(w, fmaf(d.x, x[k1].x, d.y * x[k1].y)));
+                kahan_add(shh, chh, __fmul_rn(w, fmaf(x[k1].x, x[k1].x, x[k1].y * x[k1].y)));
             }
         }
     }
@@ -1066,7 +1092,7 @@ __device__ __forceinline__ void sample_grad(const CandGx& g, const OrbitTables32
     for (int j = 0; j < 3; ++j) {
         const float kap = K + krho[j];
         const float dP = fmaf(-f, krho[j], c.fdh * kap * kap);
-        const float2 v = cmulf(ePc, cis_small(dP));
+        const float2 v = cmulf(ePc, cis_rx<J>(dP));
         const float tk = tu - kap;
         const float fk = fmaf(-fd, kap, f);
         float dph[KT];
@@ -1230,8 +1256,8 @@ __device__ void residual_adjoint(float2* buf, int ch, const OrbitTables32& tab, 
             const Win32 v = pw[kk];
             const float2 d = ch == 0 ? v.dA : v.dE;
             const float w = ch == 0 ? v.wA : v.wE;
-            kahan_add(sdh, cdh, w * fmaf(d.x, x[k1].x, d.y * x[k1].y));
-            kahan_add(shh, chh, w * fmaf(x[k1].x, x[k1].x, x[k1].y * x[k1].y));
+            kahan_add(sdh, cdh, __fmul_rn(w, fmaf(d.x, x[k1].x, d.y * x[k1].y)));
+            kahan_add(shh, chh, __fmul_rn(w, fmaf(x[k1].x, x[k1].x, x[k1].y * x[k1].y)));
             rc = make_float2(w * fmaf(-kappa, x[k1].x, d.x), -(w * fmaf(-kappa, x[k1].y, d.y)));   // conj(r)
         }
         buf[k] = rc;
