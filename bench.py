@@ -12,6 +12,8 @@ precision path (headline) and the plain FP64 path, with |dlogL| of the mixed
 path against FP64 stated, and seconds per 10k-sample posterior round.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --workload tiny|band|population   (the other configurations:
+      one JSON line each with their own figures; not the headline line)
 
 Under torchrun each rank runs its own replica of the workload (different
 seed) on its own GPU with no collective on the data path (weak scaling); only
@@ -273,6 +275,92 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# the other configurations (one GPU): their own figures, one JSON line each
+# ---------------------------------------------------------------------------
+
+def run_workload(args):
+    """tiny: one N = 128 window, 1,000 candidates (FP64 and mixed logL);
+    band: 512 windows over 0.3-20 mHz, N = 32..1024, 2k-20k candidates each,
+    one persistent launch; population: 64 windows x 4,096 (N = 256), logL,
+    adjoint gradient in both precisions, and 200 GA generations."""
+    from paper_2307_03763_gb300 import api, build
+    from paper_2307_03763_gb300.ga import GASearch
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn, reps, warm=3, flush_l2=True):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize(dev)
+        ms = []
+        for _ in range(reps):
+            if flush_l2:
+                flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            ms.append((a, b))
+        torch.cuda.synchronize(dev)
+        return float(np.mean([a.elapsed_time(b) for a, b in ms]))
+
+    wl = {"tiny": wk.tiny_window, "band": wk.band_windows, "population": wk.population_windows}[args.workload]()
+    ctx = api.Context(wl.T)
+    T_ = lambda x, dt: torch.as_tensor(np.ascontiguousarray(x)).to(dev, dt)
+    data = (T_(wl.noise_A, torch.complex128), T_(wl.noise_E, torch.complex128), T_(wl.w_A, torch.float64),
+            T_(wl.w_E, torch.float64))
+    theta = T_(wl.theta, torch.float64)
+    n = wl.n_cand
+    reps = max(3, min(args.steps, 20))
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    tune = ctx.autotune(wl.windows, *data, theta, prec="mixed", reps=3)
+    ms_mx = timed(lambda: ctx.loglik(wl.windows, *data, theta, prec="mixed"), reps)
+    ms_64 = timed(lambda: ctx.loglik(wl.windows, *data, theta, prec="fp64"), 1 if n > 10 ** 6 else 3)
+    l64 = ctx.loglik(wl.windows, *data, theta, prec="fp64")[0]
+    lmx = ctx.loglik(wl.windows, *data, theta, prec="mixed")[0]
+    dl = (lmx - l64).abs()
+    line = {"metric": METRIC, "workload": args.workload, "n_gpus": 1, "unit": UNIT, "higher_is_better": True,
+            "data": "synthetic noise windows (timing; injected sources do not change the work)",
+            "windows": len(wl.windows), "evals_per_launch": n,
+            "mixed": {"value": n / ms_mx * 1e3, "ms": ms_mx, "autotune": tune},
+            "fp64": {"value": n / ms_64 * 1e3, "ms": ms_64},
+            "mixed_vs_fp64": {"max_abs_dlogL": float(dl.max()), "median_abs_dlogL": float(dl.median())},
+            "l2": "flushed between timed launches"}
+    if args.workload == "band":
+        Ns = np.array([w[2] for w in wl.windows])
+        per = {}
+        for N in np.unique(Ns):
+            sub = [w for w in wl.windows if w[2] == N]
+            cnt = sum(w[5] for w in sub)
+            ms = timed(lambda: ctx.loglik(sub, *data, theta, prec="mixed"), 3)
+            per[int(N)] = {"evals": int(cnt), "ms": ms, "evals_per_s": cnt / ms * 1e3}
+        line["mixed_by_N"] = per
+    if args.workload == "population":
+        ms_g = timed(lambda: ctx.loglik_grad(wl.windows, *data, theta, prec="mixed"), reps)
+        sub = [(k0, W, N, doff, coff, 512) for (k0, W, N, doff, coff, nc) in wl.windows]
+        ms_g64 = timed(lambda: ctx.loglik_grad(sub, *data, theta, prec="fp64"), 1)
+        line["grad_mixed"] = {"value": n / ms_g * 1e3, "unit": "gradients/s", "ms": ms_g}
+        line["grad_fp64"] = {"value": 512 * len(sub) / ms_g64 * 1e3, "unit": "gradients/s", "ms": ms_g64,
+                             "sample": "512 candidates per window"}
+        boxes = np.array([np.concatenate([wl.theta[c:c + m].min(0), wl.theta[c:c + m].max(0)])
+                          for (_, _, _, _, c, m) in wl.windows])
+        ga_ms = {}
+        for graph in (False, True):
+            ga = GASearch(ctx, wl.windows, *data, boxes, pop=4096, seed=5)
+            ga.run(4, graph=graph)
+            ga_ms["graph" if graph else "eager"] = timed(lambda: ga.run(200, graph=graph), 1, warm=0,
+                                                         flush_l2=False) / 200
+        line["ga_generation_ms"] = ga_ms
+        line["ga"] = "64 windows x 4,096, gradient-polished elites, 200 generations per timed call"
+    line["clocks"] = clocks.stop()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -281,12 +369,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=None, help="timed steps of the FP64 path (default: steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="posterior", choices=["posterior", "tiny", "band", "population"],
+                    help="posterior: the headline step; the others print their own figures")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload != "posterior":
+        return run_workload(args)
 
     from paper_2307_03763_gb300 import api, build
     if world > 1:
