@@ -54,7 +54,7 @@ extern "C" {
 #define GB_OK        0
 #define GB_EINVAL   -1   /* bad argument (host check) or non-finite theta (device) */
 #define GB_ECUDA    -2   /* a CUDA runtime call failed */
-#define GB_ETIMEOUT -3   /* reserved: no entry point waits on another agent */
+#define GB_ETIMEOUT -3   /* a persistent kernel stopped at the context's time budget */
 #define GB_ENOMEM   -4   /* device allocation failed */
 
 #define GB_FP64   0      /* every step in IEEE double */
@@ -107,6 +107,17 @@ int gb_ctx_destroy(gb_ctx_t* ctx);
 /* Message of the last failing call on `ctx` (never NULL; "" if none). */
 const char* gb_last_error(const gb_ctx_t* ctx);
 
+/* Work budget of the persistent mixed-precision kernels (gb_loglik and
+ * gb_loglik_grad with GB_MIXED), in seconds; 0 (the default) means none.
+ * Each warp of such a launch stops taking work items once `seconds` have
+ * passed since it started, by the GPU's global timer, and flags the stop in
+ * the status word, so the next gb_ctx_check returns GB_ETIMEOUT.  The rows of
+ * the items not taken are not written.  The FP64 kernels and the other entry
+ * points ignore the budget.  A bounded launch time for batches whose cost the
+ * caller cannot predict (the paper has no counterpart).  GB_EINVAL unless
+ * 0 <= seconds <= 1e9. */
+int gb_ctx_set_time_budget(gb_ctx_t* ctx, double seconds);
+
 /* Number of kernels the context's calls have launched so far, counted on
  * the host at each launch (the paper has no counterpart: instrumentation for
  * benchmarks).  0 for a NULL context.  Not thread safe across concurrent
@@ -114,8 +125,9 @@ const char* gb_last_error(const gb_ctx_t* ctx);
 uint64_t gb_launch_count(const gb_ctx_t* ctx);
 
 /* Synchronise the device, read and clear the context's status word.
- * Returns GB_OK, or GB_EINVAL if a kernel met a non-finite parameter since
- * the last check. */
+ * Returns GB_OK; GB_ETIMEOUT if a persistent kernel stopped at the time
+ * budget (gb_ctx_set_time_budget) since the last check; else GB_EINVAL if a
+ * kernel met a non-finite parameter since the last check. */
 int gb_ctx_check(gb_ctx_t* ctx);
 
 /* Frequency-domain A/E templates (the signal model s(theta) of Sec. III,

@@ -57,6 +57,7 @@ _SIGNATURES = {
     "gb_last_error": (ctypes.c_char_p, [_P]),
     "gb_ctx_check": (ctypes.c_int, [_P]),
     "gb_launch_count": (ctypes.c_uint64, [_P]),
+    "gb_ctx_set_time_budget": (ctypes.c_int, [_P, ctypes.c_double]),
     "gb_waveform": (ctypes.c_int, [_P, ctypes.c_int, _P, _I64, _I32, _P, _P, _P, _P]),
     "gb_loglik": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _I64, _P, _I64,
                                  _P, _P, _P, _P]),
@@ -154,6 +155,10 @@ class Context:
     def _check(self, rc):
         if rc != GB_OK:
             raise GBError(rc, lib().gb_last_error(self._h).decode())
+
+    def set_time_budget(self, seconds):
+        """Work budget of the persistent mixed-precision kernels (0: none)."""
+        self._check(lib().gb_ctx_set_time_budget(self._h, float(seconds)))
 
     def launch_count(self):
         """Kernels launched by this context's calls so far."""

@@ -352,7 +352,21 @@ int gb_ctx_check(gb_ctx_t* ctx) {
     if (e == cudaSuccess) e = cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
     if (e != cudaSuccess) return cuda_error(ctx, e, "gb_ctx_check");
+    if (status & kStatusBudget)
+        return set_error(ctx, GB_ETIMEOUT,
+                         std::string("a persistent kernel stopped at the context's time budget; rows of the items "
+                                     "it did not take were not written") +
+                             (status & kStatusNonFinite ? "; a kernel also met a non-finite parameter" : ""));
     if (status != 0) return set_error(ctx, GB_EINVAL, "a kernel met a non-finite parameter");
+    return GB_OK;
+}
+
+int gb_ctx_set_time_budget(gb_ctx_t* ctx, double seconds) {
+    if (!ctx) return GB_EINVAL;
+    if (!(seconds >= 0.0) || seconds > 1.0e9)
+        return set_error(ctx, GB_EINVAL, "gb_ctx_set_time_budget: seconds must be in [0, 1e9]");
+    ctx->budget_ns = (unsigned long long)(seconds * 1.0e9);
+    if (seconds > 0.0 && ctx->budget_ns == 0ULL) ctx->budget_ns = 1ULL;
     return GB_OK;
 }
 

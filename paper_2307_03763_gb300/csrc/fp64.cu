@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kWarps64 * 32) loglik64_kernel(
                 logL[cidx] = nan("");
                 if (dh_out) dh_out[cidx] = nan("");
                 if (hh_out) hh_out[cidx] = nan("");
-                atomicOr(status, 1);
+                atomicOr(status, kStatusNonFinite);
             }
             continue;
         }
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(kWarps64 * 32) waveform64_kernel(
             for (int m = lane; m < N; m += 32) outA[m] = outE[m] = C64{nan(""), nan("")};
             if (lane == 0) {
                 q_out[b] = 0;
-                atomicOr(status, 1);
+                atomicOr(status, kStatusNonFinite);
             }
             continue;
         }

@@ -135,9 +135,22 @@ struct gb_ctx {
     size_t mh_bytes = 0;
     // kernels launched by this context's calls
     uint64_t launches = 0;
+    // work budget of the persistent kernels, nanoseconds per warp (0: none)
+    unsigned long long budget_ns = 0;
 };
 
 namespace gb {
+
+// bits of the device status word
+constexpr int kStatusNonFinite = 1;   // a candidate had a non-finite parameter
+constexpr int kStatusBudget = 2;      // a persistent kernel stopped at its time budget
+
+// Nanoseconds since an arbitrary origin, from the GPU's global timer.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 int set_error(gb_ctx* ctx, int code, const std::string& msg);
 // MH scratch: bytes for `chunk_slots` (chain, chunk) summaries and the keys

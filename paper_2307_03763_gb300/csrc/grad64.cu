@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(kWarpsG * 32) grad64_kernel(
             if (lane == 0) {
                 if (logL_out) logL_out[cidx] = nan("");
                 for (int k = 0; k < K; ++k) grad_out[8 * cidx + k] = nan("");
-                atomicOr(status, 1);
+                atomicOr(status, kStatusNonFinite);
             }
             continue;
         }

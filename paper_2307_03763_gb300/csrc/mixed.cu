@@ -518,7 +518,8 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) 
     const gb_window_t* __restrict__ wins, const WinMeta* __restrict__ meta, const Win32* __restrict__ prep,
     const Tile* __restrict__ items, int n_items, int* head, TabSet32 tabs, const float2* __restrict__ tw1024,
     double T, double fstar, const double* __restrict__ theta, double* __restrict__ logL,
-    double* __restrict__ dh_out, double* __restrict__ hh_out, int* status, int n_max) {
+    double* __restrict__ dh_out, double* __restrict__ hh_out, int* status, int n_max,
+    unsigned long long budget_ns) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     CandMix* cands = (CandMix*)smem_raw + warp * 32;
@@ -527,9 +528,18 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) 
     float2* bufE = bufA + n_max;
     const LaneTw ltw = lane_twiddles(lane);
 
+    const unsigned long long t0 = global_ns();
     for (;;) {
+        // a warp past the time budget takes no further item and flags it
         int item = 0;
-        if (lane == 0) item = atomicAdd(head, 1);
+        if (lane == 0) {
+            if (budget_ns != 0ULL && global_ns() - t0 > budget_ns) {
+                atomicOr(status, kStatusBudget);
+                item = n_items;
+            } else {
+                item = atomicAdd(head, 1);
+            }
+        }
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
         const Tile t = items[item];
@@ -580,7 +590,7 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) 
                 logL[cidx] = nan("");
                 if (dh_out) dh_out[cidx] = nan("");
                 if (hh_out) hh_out[cidx] = nan("");
-                atomicOr(status, 1);
+                atomicOr(status, kStatusNonFinite);
             } else {
                 const Epi s = epi[lane];
                 const double Sdh = (double)s.dh_hi + (double)s.dh_lo;
@@ -621,7 +631,7 @@ __global__ void __launch_bounds__(kWarpsMx * 32) waveform_mixed_kernel(
             for (int m = lane; m < N; m += 32) outA[m] = outE[m] = make_double2(nan(""), nan(""));
             if (lane == 0) {
                 q_out[b] = 0;
-                atomicOr(status, 1);
+                atomicOr(status, kStatusNonFinite);
             }
             continue;
         }
@@ -691,12 +701,12 @@ int launch_loglik_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const d
             loglik_mixed_kernel<32><<<grid, kWarpsMx * 32, smem, s>>>(
                 plan.d_win, plan.d_meta, plan.d_prep, items, n_items, head, tabset32(ctx),
                 (const float2*)ctx->d_tw32, ctx->obs.T_obs, transfer_frequency(ctx), theta, logL, dh, hh,
-                ctx->d_status, nmax);
+                ctx->d_status, nmax, ctx->budget_ns);
         else
             loglik_mixed_kernel<8><<<grid, kWarpsMx * 32, smem, s>>>(
                 plan.d_win, plan.d_meta, plan.d_prep, items, n_items, head, tabset32(ctx),
                 (const float2*)ctx->d_tw32, ctx->obs.T_obs, transfer_frequency(ctx), theta, logL, dh, hh,
-                ctx->d_status, nmax);
+                ctx->d_status, nmax, ctx->budget_ns);
         ++ctx->launches;
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_error(ctx, e, "loglik_mixed launch");
@@ -903,11 +913,11 @@ extern "C" int gb_loglik_mixed_noalloc(const gb_obs_t* obs, const gb_window_t* w
         if (part == 0)
             loglik_mixed_kernel<32><<<grid, kWarpsMx * 32, smem, s>>>(d_win, d_meta, d_prep, it, n_items, head, tabs,
                                                                       (const float2*)tw32, obs->T_obs, fstar, theta,
-                                                                      logL, dh, hh, d_status, nmax);
+                                                                      logL, dh, hh, d_status, nmax, 0ULL);
         else
             loglik_mixed_kernel<8><<<grid, kWarpsMx * 32, smem, s>>>(d_win, d_meta, d_prep, it, n_items, head, tabs,
                                                                      (const float2*)tw32, obs->T_obs, fstar, theta,
-                                                                     logL, dh, hh, d_status, nmax);
+                                                                     logL, dh, hh, d_status, nmax, 0ULL);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return na_fail(err, err_len, GB_ECUDA, cudaGetErrorString(e));
@@ -1299,7 +1309,7 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? 2 : 1) grad_mixed_k
     const gb_window_t* __restrict__ wins, const WinMeta* __restrict__ meta, const Win32* __restrict__ prep,
     const Tile* __restrict__ items, int n_items, int* head, TabSet32 tabs, const float2* __restrict__ tw1024,
     double T, double fstar, const double* __restrict__ theta, double* __restrict__ logL,
-    double* __restrict__ grad, int* status, int n_max) {
+    double* __restrict__ grad, int* status, int n_max, unsigned long long budget_ns) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     CandGx* cands = (CandGx*)smem_raw + warp * 32;
@@ -1308,9 +1318,18 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? 2 : 1) grad_mixed_k
     float2* bufE = bufA + n_max;
     const LaneTw ltw = lane_twiddles(lane);
     const float Tf = (float)T, inv_fstar = (float)(1.0 / fstar);
+    const unsigned long long t0 = global_ns();
     for (;;) {
+        // a warp past the time budget takes no further item and flags it
         int item = 0;
-        if (lane == 0) item = atomicAdd(head, 1);
+        if (lane == 0) {
+            if (budget_ns != 0ULL && global_ns() - t0 > budget_ns) {
+                atomicOr(status, kStatusBudget);
+                item = n_items;
+            } else {
+                item = atomicAdd(head, 1);
+            }
+        }
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
         const Tile t = items[item];
@@ -1376,7 +1395,7 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? 2 : 1) grad_mixed_k
             if (g.m.bad) {
                 if (logL) logL[cidx] = nan("");
                 for (int k = 0; k < 8; ++k) grad[8 * cidx + k] = nan("");
-                atomicOr(status, 1);
+                atomicOr(status, kStatusNonFinite);
             } else {
                 const EpiG& s = epi[lane];
                 const double A = g.m.A, sig = wm.sig;
@@ -1432,11 +1451,11 @@ int launch_grad_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const dou
         if (part == 0)
             grad_mixed_kernel<32><<<grid, kWarpsMx * 32, smem, s>>>(
                 plan.d_win, plan.d_meta, plan.d_prep, items, n_items, head, tabset32(ctx), (const float2*)ctx->d_tw32,
-                ctx->obs.T_obs, transfer_frequency(ctx), theta, logL, grad, ctx->d_status, nmax);
+                ctx->obs.T_obs, transfer_frequency(ctx), theta, logL, grad, ctx->d_status, nmax, ctx->budget_ns);
         else
             grad_mixed_kernel<8><<<grid, kWarpsMx * 32, smem, s>>>(
                 plan.d_win, plan.d_meta, plan.d_prep, items, n_items, head, tabset32(ctx), (const float2*)ctx->d_tw32,
-                ctx->obs.T_obs, transfer_frequency(ctx), theta, logL, grad, ctx->d_status, nmax);
+                ctx->obs.T_obs, transfer_frequency(ctx), theta, logL, grad, ctx->d_status, nmax, ctx->budget_ns);
         ++ctx->launches;
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_error(ctx, e, "grad_mixed launch");

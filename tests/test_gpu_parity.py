@@ -56,7 +56,9 @@ def _thetas(rng, n, f0, T, fd_scale=1.0):
 # templates
 # --------------------------------------------------------------------------
 
-BANDS = [(32, 0.8e-3), (64, 2.5e-3), (128, 5e-3), (256, 9e-3), (512, 14e-3), (1024, 19e-3)]
+# the last two reach the J = 10 and direct link-transfer tiers (f/f* = 1.6, 2.6)
+BANDS = [(32, 0.8e-3), (64, 2.5e-3), (128, 5e-3), (256, 9e-3), (512, 14e-3), (1024, 19e-3), (1024, 30e-3),
+         (1024, 50e-3)]
 
 
 @pytest.mark.parametrize("N,f0", BANDS)
@@ -445,3 +447,49 @@ def test_observed_fisher_matches_oracle_fisher(ctx):
     d = np.sqrt(np.outer(np.diag(Rs), np.diag(Rs)))
     assert np.abs(Fs - Rs).max() <= 1e-5 * d.max() and (np.abs(Fs - Rs) / d).max() < 1e-4, (Fs, Rs)
     assert np.all(np.linalg.eigvalsh(Fs) > -1e-9 * d.max())
+
+
+def test_time_budget_stops_persistent_kernels(api):
+    # 1 ns: no warp takes an item; a fifth of the launch time: some do.  The
+    # rows of the items not taken stay as they were and the check reports it.
+    # many small items per warp (one N = 128 window, 200,000 candidates)
+    wl = wk.tiny_window(n_cand=200000)
+    ctx = api.Context(wl.T)
+    data = (_cuda(wl.noise_A, torch.complex128), _cuda(wl.noise_E, torch.complex128), _cuda(wl.w_A, torch.float64),
+            _cuda(wl.w_E, torch.float64))
+    th = _cuda(wl.theta, torch.float64)
+    n = wl.n_cand
+    g = torch.empty((n, 8), dtype=torch.float64, device=DEV)
+    logL = torch.empty(n, dtype=torch.float64, device=DEV)
+
+    def run(grad):
+        if grad:
+            ctx.loglik_grad(wl.windows, *data, th, prec="mixed", out=(logL, g))
+        else:
+            ctx.loglik(wl.windows, *data, th, prec="mixed", out=(logL, None, None))
+
+    for grad in (False, True):
+        run(grad)
+        ctx.check()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        run(grad)
+        b.record()
+        torch.cuda.synchronize()
+        full_s = a.elapsed_time(b) * 1e-3
+        for budget, partial in ((1e-9, False), (0.2 * full_s, True)):
+            logL.fill_(float("nan"))
+            ctx.set_time_budget(budget)
+            run(grad)
+            with pytest.raises(api.GBError) as err:
+                ctx.check()
+            assert err.value.code == api.GB_ETIMEOUT
+            left = int(torch.isnan(logL).sum())
+            assert (0 < left < n) if partial else (left > 0), (grad, budget, left, n)
+        ctx.set_time_budget(0.0)
+        logL.fill_(float("nan"))
+        run(grad)
+        ctx.check()
+        assert not bool(torch.isnan(logL).any())
+    with pytest.raises(api.GBError):
+        ctx.set_time_budget(-1.0)
