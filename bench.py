@@ -12,8 +12,9 @@ precision path (headline) and the plain FP64 path, with |dlogL| of the mixed
 path against FP64 stated, and seconds per 10k-sample posterior round.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-  python bench.py --workload tiny|band|population   (the other configurations:
-      one JSON line each with their own figures; not the headline line)
+  python bench.py --workload tiny|band|population|fullband   (the other
+      configurations: one JSON line each with their own figures; not the
+      headline line)
 
 Under torchrun each rank runs its own replica of the workload (different
 seed) on its own GPU with no collective on the data path (weak scaling); only
@@ -361,6 +362,30 @@ def run_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def run_fullband(args):
+    """Config 5: 0.3-15 mHz at T = 2 yr with the requested number of injected
+    binaries, windows from Alg. 1, GA search-and-subtract rounds in every
+    window, a 10,000-proposal posterior for every recovered source."""
+    from paper_2307_03763_gb300 import api, build, fullband
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ctx = api.Context(2 * wk.YEAR)
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    st = fullband.run(ctx, n_src=args.fb_sources, rounds=args.fb_rounds, pop=args.fb_pop, generations=args.fb_gens)
+    line = {"metric": "total wall time, s per posterior (full-band search)", "workload": "fullband",
+            "n_gpus": 1, "unit": "s", "higher_is_better": False, "data": "synthetic",
+            "value": st["wall_s"], "s_per_posterior": st["s_per_posterior"],
+            "s_per_posterior_6_temperatures": 6 * st["s_per_posterior"] if st["s_per_posterior"] else None,
+            "config": {"workload": "fullband: 0.3-15 mHz, T=2 yr, dt=15 s, %d binaries, Alg. 1 windows" %
+                       args.fb_sources}, "stats": st,
+            # kernels launched from the host; the GA generations replayed from CUDA graphs are not counted
+            "host_kernel_launches": ctx.launch_count(),
+            "clocks": clocks.stop()}
+    print(json.dumps(line, default=float), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -369,14 +394,20 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=None, help="timed steps of the FP64 path (default: steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="posterior", choices=["posterior", "tiny", "band", "population"],
+    ap.add_argument("--workload", default="posterior", choices=["posterior", "tiny", "band", "population", "fullband"],
                     help="posterior: the headline step; the others print their own figures")
+    ap.add_argument("--fb-sources", type=int, default=200000, help="fullband: injected binaries")
+    ap.add_argument("--fb-rounds", type=int, default=3, help="fullband: search-and-subtract rounds")
+    ap.add_argument("--fb-pop", type=int, default=1024, help="fullband: GA population per window")
+    ap.add_argument("--fb-gens", type=int, default=100, help="fullband: GA generations per round")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "fullband":
+        return run_fullband(args)
     if args.workload != "posterior":
         return run_workload(args)
 

@@ -181,6 +181,45 @@ def log_uniforms(n, rng):
 # the five workloads
 # ----------------------------------------------------------------------------
 
+def fullband_sources(n_src=200000, f_lo=0.3e-3, f_hi=15e-3, seed=SEED_BASE + 5):
+    """The full-band population: f0 log-uniform in [f_lo, f_hi], fdot from
+    Eq. 8 with Mc ~ U[0.2, 1] M_sun, A log-uniform in [1e-23, 1e-21], angles
+    on the Table 1 ranges; (n_src, 8), sorted by f0."""
+    rng = np.random.default_rng(seed)
+    f0 = np.sort(np.exp(rng.uniform(np.log(f_lo), np.log(f_hi), n_src)))
+    fdot = chirp_fdot(f0, rng.uniform(0.2, 1.0, n_src))
+    A = np.exp(rng.uniform(np.log(1e-23), np.log(1e-21), n_src))
+    beta, lam, iota, psi, phi0 = random_angles(rng, n_src)
+    return np.stack([f0, fdot, beta, lam, A, iota, psi, phi0], 1)
+
+
+def fullband_layout(f_lo=0.3e-3, f_hi=15e-3, T=2 * YEAR, n_cap=1024):
+    """Search windows from the segments of Alg. 1: [(k0, N, ka, kb)], the
+    segment's bins [ka, kb) (the frequency range searched there) and a window
+    of N bins centred on it, N the smallest power of two (>= 32) that holds
+    the segment.  A segment wider than n_cap bins is split into equal parts."""
+    out = []
+    for fa, fb in segments(f_lo, f_hi, T):
+        ka, kb = int(math.floor(fa * T)), int(math.ceil(fb * T))
+        parts = max(1, int(math.ceil((kb - ka) / n_cap)))
+        edges = np.linspace(ka, kb, parts + 1).round().astype(np.int64)
+        for a, b in zip(edges[:-1], edges[1:]):
+            N = 1 << max(5, int(math.ceil(math.log2(max(int(b - a), 1)))))
+            c = (int(a) + int(b)) // 2
+            out.append((c - N // 2, N, int(a), int(b)))
+    return out
+
+
+def band_noise(k_lo, k_hi, T, rng):
+    """Noise on the contiguous bins [k_lo, k_hi): Re, Im ~ N(0, T S / 4), and w = 1/S."""
+    f = np.arange(k_lo, k_hi, dtype=np.float64) / T
+    S = psd_AE(f)
+    sd = np.sqrt(T * S / 4.0)
+    n = k_hi - k_lo
+    nA = sd * (rng.standard_normal(n) + 1j * rng.standard_normal(n))
+    nE = sd * (rng.standard_normal(n) + 1j * rng.standard_normal(n))
+    return nA, nE, 1.0 / S
+
 def tiny_window(seed=SEED_BASE + 1, n_cand=1000, N=128, T=2 * YEAR):
     """One window of N = W = 128 bins at f0 = 1.5 mHz, T = 2 yr; 1,000 candidates
     uniform in a box around the injected source (f0 +- 5/T, fdot in [0, 2 fdot],
