@@ -241,6 +241,7 @@ typedef struct {
  * differential evolution and sets A from Eq. 7 (Alg. 2, Sec. III.D); this is a
  * genetic algorithm with that objective.
  *   theta      n_win x pop x 8 population (device), pop individuals per window
+ *              (pop <= 32768: the population's fitness is held in shared memory)
  *   dh, hh     <d|h>, <h|h> of every individual (device, from gb_loglik)
  *   box        n_win prior boxes (device)
  *   seed       key of the Philox-4x32-10 draws

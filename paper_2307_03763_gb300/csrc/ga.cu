@@ -28,6 +28,7 @@ namespace gb {
 namespace {
 
 constexpr int kGaThreads = 256;
+constexpr int kGaMaxPop = 32768;   // fitness of the population in shared memory
 
 struct Philox {
     uint32_t c[4];
@@ -62,6 +63,9 @@ __device__ __forceinline__ uint4 philox4x32_10(uint32_t a, uint32_t b, uint32_t 
 // uniform in (0, 1) from 32 bits
 __device__ __forceinline__ double u01(uint32_t x) { return ((double)x + 0.5) * 2.3283064365386963e-10; }
 
+// Draws of the genetic search.  They only steer a heuristic, so they are taken
+// in float where that saves double-precision work: indices by multiply-shift,
+// Bernoulli tests as integer thresholds, normals by float Box-Muller.
 struct Rng {
     uint32_t k0, k1, gen, win, ind, draw;
     uint4 buf;
@@ -74,31 +78,51 @@ struct Rng {
         --left;
         return left == 3 ? buf.x : left == 2 ? buf.y : left == 1 ? buf.z : buf.w;
     }
-    __device__ double uniform() { return u01(next()); }
-    __device__ double normal() {   // Box-Muller
-        const double a = uniform(), b = uniform();
-        return sqrt(-2.0 * log(a)) * cospi(2.0 * b);
+    __device__ int index(int n) { return (int)(((uint64_t)next() * (uint64_t)n) >> 32); }
+    __device__ float uniform_f() { return ((float)(next() >> 8) + 0.5f) * 5.9604644775390625e-08f; }   // 2^-24
+    __device__ bool bernoulli(uint32_t thr, bool always) { return always || next() < thr; }
+    __device__ float normal_f() {   // Box-Muller
+        const float a = uniform_f(), b = uniform_f();
+        return sqrtf(-2.0f * logf(a)) * cospif(2.0f * b);
     }
 };
 
-__device__ __forceinline__ double wrap(double x, double lo, double hi) {
-    const double w = hi - lo;
-    if (!(w > 0.0)) return lo;
-    double y = fmod(x - lo, w);
-    if (y < 0.0) y += w;
-    return lo + y;
+// probability p as a threshold on 32 random bits (p >= 1: always)
+__device__ __forceinline__ uint32_t prob_threshold(double p, bool& always) {
+    always = p >= 1.0;
+    return always ? 0u : (uint32_t)(p * 4294967296.0);
 }
 
+// reflect / wrap into [lo, hi]; one fold covers a step of up to a box width,
+// the remainder form handles any other value
 __device__ __forceinline__ double reflect(double x, double lo, double hi) {
+    if (x >= lo && x <= hi) return x;
     const double w = hi - lo;
     if (!(w > 0.0)) return lo;
+    if (x < lo && x >= lo - w) return 2.0 * lo - x;
+    if (x > hi && x <= hi + w) return 2.0 * hi - x;
     double y = fmod(x - lo, 2.0 * w);
     if (y < 0.0) y += 2.0 * w;
     return lo + (y > w ? 2.0 * w - y : y);
 }
 
-__device__ __forceinline__ double fitness(double dh, double hh) {
-    return (hh > 0.0 && isfinite(dh) && isfinite(hh)) ? dh / sqrt(hh) : -INFINITY;
+__device__ __forceinline__ double wrap(double x, double lo, double hi) {
+    if (x >= lo && x < hi) return x;
+    const double w = hi - lo;
+    if (!(w > 0.0)) return lo;
+    if (x < lo && x >= lo - w) return x + w;
+    if (x >= hi && x < hi + w) return x - w;
+    double y = fmod(x - lo, w);
+    if (y < 0.0) y += w;
+    return lo + y;
+}
+
+// rho = <d|h>/sqrt(<h|h>) (Eq. 6), in float: it only ranks individuals
+__device__ __forceinline__ float fitness(double dh, double hh) {
+    if (!(hh > 0.0) || !isfinite(dh) || !isfinite(hh)) return -INFINITY;
+    const float h = (float)hh;
+    if (h >= 1e-30f && h <= 1e30f && fabs(dh) < 1e30) return (float)dh * rsqrtf(h);
+    return (float)(dh / sqrt(hh));
 }
 
 __global__ void __launch_bounds__(kGaThreads) ga_step_kernel(int pop, const double* __restrict__ theta,
@@ -109,7 +133,8 @@ __global__ void __launch_bounds__(kGaThreads) ga_step_kernel(int pop, const doub
                                                              uint64_t* __restrict__ gen_out, gb_ga_params_t prm,
                                                              const double* __restrict__ grad, double T,
                                                              double* __restrict__ out, double* __restrict__ best) {
-    __shared__ double s_fit[kGaThreads];
+    extern __shared__ float s_pop_fit[];   // pop
+    __shared__ float s_fit[kGaThreads];
     __shared__ int s_idx[kGaThreads];
     __shared__ double s_best[8];
     const int w = blockIdx.x;
@@ -119,12 +144,13 @@ __global__ void __launch_bounds__(kGaThreads) ga_step_kernel(int pop, const doub
     const double* th = theta + 8 * base;
     double* to = out + 8 * base;
     const gb_box_t bx = box[w];
-    // best individual of the window
-    double bf = -INFINITY;
+    // fitness of every individual, and the best one (lowest index among equals)
+    float bf = -INFINITY;
     int bi = 0;
     for (int i = threadIdx.x; i < pop; i += blockDim.x) {
-        const double f = fitness(dh[base + i], hh[base + i]);
-        if (f > bf || (f == bf && i < bi)) {
+        const float f = fitness(dh[base + i], hh[base + i]);
+        s_pop_fit[i] = f;
+        if (f > bf) {
             bf = f;
             bi = i;
         }
@@ -134,7 +160,7 @@ __global__ void __launch_bounds__(kGaThreads) ga_step_kernel(int pop, const doub
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) {
-            const double f2 = s_fit[threadIdx.x + s];
+            const float f2 = s_fit[threadIdx.x + s];
             const int i2 = s_idx[threadIdx.x + s];
             if (f2 > s_fit[threadIdx.x] || (f2 == s_fit[threadIdx.x] && i2 < s_idx[threadIdx.x])) {
                 s_fit[threadIdx.x] = f2;
@@ -164,6 +190,10 @@ __global__ void __launch_bounds__(kGaThreads) ga_step_kernel(int pop, const doub
         }
         gnorm = sqrt(gnorm);
     }
+    bool all_c, all_m;
+    const uint32_t thr_c = prob_threshold(prm.p_cross, all_c), thr_m = prob_threshold(prm.p_mut, all_m);
+    double sigma[8];
+    for (int j = 0; j < 8; ++j) sigma[j] = prm.mut_scale * (bx.hi[j] - bx.lo[j]);
     const double radii[4] = {0.3, 0.1, 0.03, 0.01};
     for (int i = threadIdx.x; i < pop; i += blockDim.x) {
         double c[8];
@@ -178,11 +208,11 @@ __global__ void __launch_bounds__(kGaThreads) ga_step_kernel(int pop, const doub
             Rng rng{k0, k1, (uint32_t)generation, (uint32_t)w, (uint32_t)i, 0u};
             int par[2];
             for (int p = 0; p < 2; ++p) {
-                int win_i = (int)(rng.next() % (uint32_t)pop);
-                double win_f = fitness(dh[base + win_i], hh[base + win_i]);
+                int win_i = rng.index(pop);
+                float win_f = s_pop_fit[win_i];
                 for (int t = 1; t < prm.tournament; ++t) {
-                    const int j = (int)(rng.next() % (uint32_t)pop);
-                    const double f = fitness(dh[base + j], hh[base + j]);
+                    const int j = rng.index(pop);
+                    const float f = s_pop_fit[j];
                     if (f > win_f) {
                         win_f = f;
                         win_i = j;
@@ -192,9 +222,9 @@ __global__ void __launch_bounds__(kGaThreads) ga_step_kernel(int pop, const doub
             }
             for (int j = 0; j < 8; ++j) {
                 const double a = th[8 * par[0] + j], b = th[8 * par[1] + j];
-                const double t = rng.uniform();
-                double x = (rng.uniform() < prm.p_cross) ? a + t * (b - a) : a;
-                if (rng.uniform() < prm.p_mut) x += prm.mut_scale * (bx.hi[j] - bx.lo[j]) * rng.normal();
+                const double t = (double)rng.uniform_f();
+                double x = rng.bernoulli(thr_c, all_c) ? fma(t, b - a, a) : a;
+                if (rng.bernoulli(thr_m, all_m)) x = fma(sigma[j], (double)rng.normal_f(), x);
                 c[j] = x;
             }
         }
@@ -283,11 +313,17 @@ extern "C" int gb_ga_step(gb_ctx_t* ctx, int32_t n_win, int32_t pop, const doubl
     if (params->tournament < 1 || !(params->p_cross >= 0.0 && params->p_cross <= 1.0) ||
         !(params->p_mut >= 0.0 && params->p_mut <= 1.0) || !(params->mut_scale >= 0.0))
         return set_error(ctx, GB_EINVAL, "gb_ga_step: bad parameters");
+    if (pop > kGaMaxPop) return set_error(ctx, GB_EINVAL, "gb_ga_step: pop above 32768");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_error(ctx, e, "gb_ga_step: cudaSetDevice");
-    ga_step_kernel<<<n_win, kGaThreads, 0, (cudaStream_t)stream>>>(pop, theta, dh, hh, box, seed, generation_in,
-                                                                   generation_out, *params, grad, ctx->obs.T_obs,
-                                                                   theta_out, best);
+    const size_t smem = sizeof(float) * (size_t)pop;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(ga_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_error(ctx, e, "gb_ga_step: smem attribute");
+    }
+    ga_step_kernel<<<n_win, kGaThreads, smem, (cudaStream_t)stream>>>(pop, theta, dh, hh, box, seed, generation_in,
+                                                                      generation_out, *params, grad, ctx->obs.T_obs,
+                                                                      theta_out, best);
     ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "gb_ga_step launch");
