@@ -299,7 +299,7 @@ int gb_philox4x32(gb_ctx_t* ctx, uint64_t seed, uint32_t n, uint32_t* out, void*
  * pointers, host window array), and so are the results.  All scratch memory
  * (geometry tables and twiddles, window descriptors and work items,
  * per-window values, float copies of the windows, work-queue heads) lives in
- * one static device array of about 8.6 MB, which every GPU that loads the
+ * one static device array of about 8.7 MB, which every GPU that loads the
  * library holds until the process exits.  Limits: n_win <= 4096, the windows'
  * W add up to at most 262144 bins, at most 65536 work items (about two
  * million candidates); beyond them the call returns GB_EINVAL with a message.

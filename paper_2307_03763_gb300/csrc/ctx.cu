@@ -64,12 +64,22 @@ __global__ void build_tables_kernel(int N, double T, double L, double* tab64, fl
     float rho[2][3];
     for (int i = 0; i < 2; ++i)
         for (int c = 0; c < 3; ++c) rho[i][c] = (float)((x[i][c] - centre[c]) / kC);
-    float4* G4 = (float4*)tab32;
-    G4[p] = make_float4(rho[0][0], rho[0][1], rho[0][2], rho[1][0]);
-    G4[N + p] = make_float4(rho[1][1], rho[1][2], (float)arm[0][0], (float)arm[0][1]);
-    G4[2 * N + p] = make_float4((float)arm[0][2], (float)arm[1][0], (float)arm[1][1], (float)arm[1][2]);
     const float chi = (float)ca, shi = (float)sa;
-    G4[3 * N + p] = make_float4(chi, (float)(ca - (double)chi), shi, (float)(sa - (double)shi));
+    const float4 g0 = make_float4(rho[0][0], rho[0][1], rho[0][2], rho[1][0]);
+    const float4 g1 = make_float4(rho[1][1], rho[1][2], (float)arm[0][0], (float)arm[0][1]);
+    const float4 g2 = make_float4((float)arm[0][2], (float)arm[1][0], (float)arm[1][1], (float)arm[1][2]);
+    const float4 g3 = make_float4(chi, (float)(ca - (double)chi), shi, (float)(sa - (double)shi));
+    float4* G4 = (float4*)tab32;
+    G4[p] = g0;
+    G4[N + p] = g1;
+    G4[2 * N + p] = g2;
+    G4[3 * N + p] = g3;
+    // the same in natural order (sample n at n), after the lane twiddles
+    float4* G4n = (float4*)(tab32 + 18 * N);
+    G4n[n] = g0;
+    G4n[N + n] = g1;
+    G4n[2 * N + n] = g2;
+    G4n[3 * N + n] = g3;
     // lane twiddle exp(-2 pi i r l / N) at entry n = r*32 + l
     float* LT = tab32 + 16 * N;
     const int r = n / 32, l = n % 32;
@@ -102,8 +112,6 @@ cudaError_t build_tables_into(double T, double L, double* const tab64[kNumSizes]
     return cudaGetLastError();
 }
 
-constexpr int kTab64PerN = 18;   // doubles per sample
-constexpr int kTab32PerN = 18;   // floats per sample: 4 float4 + lane twiddles
 
 OrbitTables64 tables64(const gb_ctx* ctx, int N) {
     const double* t = ctx->d_tab64[size_index(N)];
@@ -112,7 +120,7 @@ OrbitTables64 tables64(const gb_ctx* ctx, int N) {
 
 OrbitTables32 tables32(const gb_ctx* ctx, int N) {
     const float* t = ctx->d_tab32[size_index(N)];
-    return OrbitTables32{(const float4*)t, (const float2*)(t + 16 * N)};
+    return OrbitTables32{(const float4*)t, (const float2*)(t + 16 * N), (const float4*)(t + 18 * N)};
 }
 
 TabSet64 tabset64(const gb_ctx* ctx) {

@@ -55,9 +55,13 @@ struct OrbitTables64 {
 // rho_2 = -rho_0 - rho_1 (the centroid is the guiding centre) and
 // n_20 = -n_01 - n_12 (the arms close).
 struct OrbitTables32 {
-    const float4* g;     // [4][N]
+    const float4* g;     // [4][N], lane-permuted order (see the table kernel)
     const float2* ltw;   // [R][32]                exp(-2 pi i r l / N), lane twiddles
+    const float4* gn;    // [4][N], the same values in natural sample order
 };
+
+constexpr int kTab64PerN = 18;   // doubles per sample
+constexpr int kTab32PerN = 34;   // floats per sample: 4 float4 (permuted) + lane twiddles + 4 float4 (natural)
 
 __host__ __device__ inline int brev5(int l) {
     return ((l & 1) << 4) | ((l & 2) << 2) | (l & 4) | ((l & 8) >> 2) | ((l & 16) >> 4);

@@ -212,21 +212,24 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = (a - (s - bb)) + (b - bb);
 }
 
-// Slow part of one candidate: lane l, step r computes sample n = R brev5(l) + r
-// and writes A, E to buf{A,E}[r*32 + l] (conflict-free).
-template <int J>
+// Slow part of one candidate: lane l, step r computes sample n and writes A, E
+// to buf{A,E}[r*32 + l] (conflict-free), with n = l + 32 r (NAT: natural
+// order, for the transform of the likelihood kernel) or n = R brev5(l) + r
+// (for the across-lane transform of the waveform and gradient kernels).
+template <int J, bool NAT>
 __device__ void slow_part_mixed(const CandMix& c, const OrbitTables32& tab, int N, float2* bufA, float2* bufE,
                                 int lane) {
     const int R = N >> 5;
     const float invN = 1.0f / (float)N;
     const float r2 = 0.70710678118654752f, r6 = 0.40824829046386302f;
-    const int nb = R * brev5(lane);
+    const int nb = NAT ? lane : R * brev5(lane);
+    const float4* tg = NAT ? tab.gn : tab.g;
     for (int r = 0; r < R; ++r) {
         const int p = r * 32 + lane;
-        const float u = (float)(nb + r) * invN;
+        const float u = (float)(NAT ? nb + 32 * r : nb + r) * invN;
         const float uu = u * u;
-        const float4 g0 = __ldg(tab.g + p), g1 = __ldg(tab.g + N + p);
-        const float4 g2 = __ldg(tab.g + 2 * N + p), g3 = __ldg(tab.g + 3 * N + p);
+        const float4 g0 = __ldg(tg + p), g1 = __ldg(tg + N + p);
+        const float4 g2 = __ldg(tg + 2 * N + p), g3 = __ldg(tg + 3 * N + p);
         const float cah = g3.x, cal = g3.y, sah = g3.z, sal = g3.w;
         // double-word products, reduced modulo one
         float p1 = c.c1h * u;
@@ -312,13 +315,14 @@ __device__ void slow_part_mixed(const CandMix& c, const OrbitTables32& tab, int 
     }
 }
 
+template <bool NAT>
 __device__ void slow_part_dispatch(const CandMix& c, const OrbitTables32& tab, int N, float2* bufA, float2* bufE,
                                    int lane) {
     switch (c.J) {
-        case 4: slow_part_mixed<4>(c, tab, N, bufA, bufE, lane); break;
-        case 7: slow_part_mixed<7>(c, tab, N, bufA, bufE, lane); break;
-        case 10: slow_part_mixed<10>(c, tab, N, bufA, bufE, lane); break;
-        default: slow_part_mixed<0>(c, tab, N, bufA, bufE, lane); break;
+        case 4: slow_part_mixed<4, NAT>(c, tab, N, bufA, bufE, lane); break;
+        case 7: slow_part_mixed<7, NAT>(c, tab, N, bufA, bufE, lane); break;
+        case 10: slow_part_mixed<10, NAT>(c, tab, N, bufA, bufE, lane); break;
+        default: slow_part_mixed<0, NAT>(c, tab, N, bufA, bufE, lane); break;
     }
 }
 
@@ -416,29 +420,171 @@ __device__ __forceinline__ void channel_fft(const float2* buf, const OrbitTables
     reg_fft<R>(x, tw1024);
 }
 
-// FFT of both channels and the window inner products of one candidate.
+// ---------------------------------------------------------------------------
+// Transform of the likelihood kernel.  Input: lane l holds samples
+// n = l + 32 r, r < R (R = N/32).  With n = l + 32 r and bin K = k1 + R k2,
+//   S[K] = sum_l w32^(l k2) [ wN^(l k1) sum_r s[l + 32 r] wR^(r k1) ],
+// so each lane first takes an R-point DFT of its own samples and a twiddle;
+// a transpose through shared memory then gives each group of G = 32/R lanes
+// one of the R 32-point DFTs, factored as 32 = R x G over l = j + G m:
+//   sum_l y_l w32^(l k2) = sum_j w32^(j ka) wG^(j kb) sum_m y_(j+Gm) wR^(m ka),
+//   k2 = ka + R kb:
+// an R-point DFT in registers, a twiddle, and a G-point DFT across the
+// group's lanes -- by a second transpose and register DFTs when R >= G, by
+// radix-2 decimation-in-frequency shuffles otherwise.  Both transposes are
+// skewed so that every half-warp access touches 16 distinct banks.
+// ---------------------------------------------------------------------------
+
+// element (k1, l) of the first transpose: row k1 of 32, rotated by G k1
 template <int R>
-__device__ void fft_inner(const float2* bufA, const float2* bufE, const OrbitTables32& tab, const float2* tw1024,
-                          const LaneTw& ltw, int lane, int off, int W, const Win32* __restrict__ pw, float& sdh,
-                          float& cdh, float& shh, float& chh) {
-    constexpr int N = 32 * R;
-    float2 x[R];
+__device__ __forceinline__ int t1_addr(int k1, int l) {
+    return 32 * k1 + ((l + (32 / R) * k1) & 31);
+}
+
+// element (group g, ka, u, v) of the second transpose for R = 4 (G = 8):
+// lane j = u + 2v of group g holds ka; lane 2 ka + u collects v = 0..3
+__device__ __forceinline__ int t2_addr4(int g, int ka, int u, int v) {
+    const int h = g >> 1, gp = g & 1;
+    return 64 * h + 16 * ka + ((8 * gp + 4 * u + v + ka) & 15);
+}
+
+// element (group g, lane j of the group, ka) of the second transpose (R >= 8)
+template <int R>
+__device__ __forceinline__ int t2_addr(int g, int j, int ka) {
+    constexpr int G = 32 / R, GPH = 16 / G;   // groups per half-warp
+    const int h = g / GPH, gp = g - h * GPH;
+    return 16 * R * h + 16 * ka + ((gp + GPH * j + (16 / R) * ka) & 15);
+}
+
+// G-point DFT of v[0..G) in registers, natural order in and out (G = 1, 2, 4)
+template <int G>
+__device__ __forceinline__ void dft_small(float2* v) {
+    if constexpr (G == 2) {
+        const float2 a = v[0], b = v[1];
+        v[0] = caddf(a, b);
+        v[1] = csubf(a, b);
+    } else if constexpr (G == 4) {
+        const float2 s02 = caddf(v[0], v[2]), d02 = csubf(v[0], v[2]);
+        const float2 s13 = caddf(v[1], v[3]), d13 = csubf(v[1], v[3]);
+        v[0] = caddf(s02, s13);
+        v[2] = csubf(s02, s13);
+        v[1] = make_float2(d02.x + d13.y, d02.y - d13.x);   // d02 - i d13
+        v[3] = make_float2(d02.x - d13.y, d02.y + d13.x);   // d02 + i d13
+    }
+}
+
+// bit reversal of the low b bits
+__device__ __forceinline__ int brev_bits(int x, int b) { return b == 0 ? 0 : (int)(__brev((unsigned)x) >> (32 - b)); }
+
+// Both channels of one candidate: transform, then the window inner products.
+template <int R>
+__device__ void fft_inner_nat(float2* bufA, float2* bufE, const OrbitTables32& tab, const float2* tw1024,
+                              const LaneTw& ltw, int lane, int off, int W, const Win32* __restrict__ pw, float& sdh,
+                              float& cdh, float& shh, float& chh) {
+    constexpr int N = 32 * R, G = 32 / R;
+    constexpr int LG = G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 8 ? 3 : G == 16 ? 4 : 5;
+    const int g = lane / G, j = lane % G;
     // one copy of the transform for both channels (instruction-cache footprint)
 #pragma unroll 1
     for (int ch = 0; ch < 2; ++ch) {
-        channel_fft<R>(ch == 0 ? bufA : bufE, tab, tw1024, ltw, lane, x);
+        float2* buf = ch == 0 ? bufA : bufE;
+        float2 x[R];
 #pragma unroll
-        for (int k1 = 0; k1 < R; ++k1) {
-            const int k = lane + 32 * k1;
-            const int m = k < N / 2 ? k : k - N;
+        for (int r = 0; r < R; ++r) x[r] = buf[r * 32 + lane];
+        reg_fft<R>(x, tw1024);
+#pragma unroll
+        for (int k1 = 1; k1 < R; ++k1) x[k1] = cmulf(x[k1], __ldg(tab.ltw + k1 * 32 + lane));
+        if constexpr (R > 1) {
+            __syncwarp();
+#pragma unroll
+            for (int k1 = 0; k1 < R; ++k1) buf[t1_addr<R>(k1, lane)] = x[k1];
+            __syncwarp();
+#pragma unroll
+            for (int m = 0; m < R; ++m) x[m] = buf[t1_addr<R>(g, j + G * m)];
+            reg_fft<R>(x, tw1024);
+            if constexpr (G > 1) {
+                // exp(-2 pi i j ka / 32) = exp(-2 pi i (R j) ka / N): the lane-twiddle table
+#pragma unroll
+                for (int ka = 1; ka < R; ++ka) x[ka] = cmulf(x[ka], __ldg(tab.ltw + ka * 32 + R * j));
+            }
+        }
+        // x[q] is the value of bin K(q): the G-point stage, then the bin map
+        int kbase;   // K(q) = g + R*(ka(q) + R*kb(q)) with ka, kb per branch below
+        if constexpr (R == 4) {
+            // 8 = 4 x 2 over j = u + 2v: lane 2 ka + u gathers v = 0..3, a 4-point
+            // DFT over v, twiddle exp(-2 pi i u kv / 8), a 2-point DFT over u
+            // across the lane pair; it then holds kb = kv + 4 u, kv = 0..3
+            const int u = j & 1, ka = j >> 1;
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < 4; ++q) buf[t2_addr4(g, q, j & 1, j >> 1)] = x[q];
+            __syncwarp();
+#pragma unroll
+            for (int v = 0; v < 4; ++v) x[v] = buf[t2_addr4(g, ka, u, v)];
+            dft_small<4>(x);
+            if (u) {
+                const float r = 0.70710678118654752f;
+                x[1] = make_float2(r * (x[1].x + x[1].y), r * (x[1].y - x[1].x));    // * exp(-i pi/4)
+                x[2] = make_float2(x[2].y, -x[2].x);                                 // * -i
+                x[3] = make_float2(r * (x[3].y - x[3].x), -r * (x[3].x + x[3].y));   // * exp(-3 i pi/4)
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 v = make_float2(__shfl_xor_sync(0xffffffffu, x[q].x, 1),
+                                             __shfl_xor_sync(0xffffffffu, x[q].y, 1));
+                x[q] = u ? csubf(v, x[q]) : caddf(x[q], v);
+            }
+            kbase = g + 4 * ka + 64 * u;   // + 16 kv for x[kv]: K = g + 4 (ka + 4 (kv + 4 u))
+        } else if constexpr (R >= G && G > 1) {
+            __syncwarp();
+#pragma unroll
+            for (int ka = 0; ka < R; ++ka) buf[t2_addr<R>(g, j, ka)] = x[ka];
+            __syncwarp();
+            // lane j now takes ka = (R/G) j + t for t < R/G, all G lanes of the group
+#pragma unroll
+            for (int t = 0; t < R / G; ++t) {
+#pragma unroll
+                for (int j2 = 0; j2 < G; ++j2) x[t * G + j2] = buf[t2_addr<R>(g, j2, (R / G) * j + t)];
+                dft_small<G>(x + t * G);
+            }
+            kbase = g + R * (R / G) * j;   // + R t + R^2 kb for x[t G + kb]
+        } else if constexpr (G > 1) {
+            // radix-2 decimation in frequency across the group's lanes
+#pragma unroll
+            for (int s = LG - 1; s >= 0; --s) {
+                const int h = 1 << s;
+                const bool upper = (lane & h) != 0;
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const float2 v = make_float2(__shfl_xor_sync(0xffffffffu, x[q].x, h),
+                                                 __shfl_xor_sync(0xffffffffu, x[q].y, h));
+                    if (!upper) {
+                        x[q] = caddf(x[q], v);
+                    } else {
+                        const float2 d = csubf(v, x[q]);
+                        x[q] = s == 0 ? d : cmulf(d, ltw.w[s - 1]);
+                    }
+                }
+            }
+            kbase = g + R * R * brev_bits(j, LG);   // + R ka for x[ka]
+        } else {
+            kbase = g;   // G = 1: + R ka for x[ka]
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            int K;
+            if constexpr (R == 4) K = kbase + 16 * q;
+            else if constexpr (R >= G && G > 1) K = kbase + R * (q / G) + R * R * (q % G);
+            else K = kbase + R * q;
+            const int m = K < N / 2 ? K : K - N;
             const int kk = off + m;
             if (kk >= 0 && kk < W) {
                 const Win32 v = pw[kk];
                 const float2 d = ch == 0 ? v.dA : v.dE;
                 const float w = ch == 0 ? v.wA : v.wE;
                 // explicit products: the same rounding in every kernel that forms these sums
-                kahan_add(sdh, cdh, __fmul_rn(w, fmaf(d.x, x[k1].x, d.y * x[k1].y)));
-                kahan_add(shh, chh, __fmul_rn(w, fmaf(x[k1].x, x[k1].x, x[k1].y * x[k1].y)));
+                kahan_add(sdh, cdh, __fmul_rn(w, fmaf(d.x, x[q].x, d.y * x[q].y)));
+                kahan_add(shh, chh, __fmul_rn(w, fmaf(x[q].x, x[q].x, x[q].y * x[q].y)));
             }
         }
     }
@@ -555,23 +701,23 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) 
             const CandMix& c = cands[i];
             float sdh = 0.0f, cdh = 0.0f, shh = 0.0f, chh = 0.0f;
             if (!c.bad) {
-                slow_part_dispatch(c, tab, N, bufA, bufE, lane);
+                slow_part_dispatch<true>(c, tab, N, bufA, bufE, lane);
                 __syncwarp();
                 const long long off64 = c.q - win.k0;
                 if (off64 > -(long long)N && off64 < (long long)win.W + N) {
                     const int off = (int)off64;
                     if constexpr (RMAX <= 8) {
                         switch (N) {
-                            case 32: fft_inner<1>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh); break;
-                            case 64: fft_inner<2>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh); break;
-                            case 128: fft_inner<4>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh); break;
-                            default: fft_inner<8>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh); break;
+                            case 32: fft_inner_nat<1>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh); break;
+                            case 64: fft_inner_nat<2>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh); break;
+                            case 128: fft_inner_nat<4>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh); break;
+                            default: fft_inner_nat<8>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh); break;
                         }
                     } else {
                         if (N == 512)
-                            fft_inner<16>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh);
+                            fft_inner_nat<16>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh);
                         else
-                            fft_inner<32>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh);
+                            fft_inner_nat<32>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh);
                     }
                 }
                 __syncwarp();
@@ -635,7 +781,7 @@ __global__ void __launch_bounds__(kWarpsMx * 32) waveform_mixed_kernel(
             }
             continue;
         }
-        slow_part_dispatch(c, tab, N, bufA, bufE, lane);
+        slow_part_dispatch<false>(c, tab, N, bufA, bufE, lane);
         __syncwarp();
         const double s = scale * c.A;
         for (int ch = 0; ch < 2; ++ch) {
@@ -757,8 +903,8 @@ constexpr size_t kNaAlign = 256;
 constexpr size_t na_round(size_t x) { return (x + kNaAlign - 1) / kNaAlign * kNaAlign; }
 constexpr size_t kNaSamples = 32 + 64 + 128 + 256 + 512 + 1024;
 constexpr size_t kNaOffTab64 = 0;
-constexpr size_t kNaOffTab32 = na_round(kNaOffTab64 + sizeof(double) * 18 * kNaSamples);
-constexpr size_t kNaOffTw64 = na_round(kNaOffTab32 + sizeof(float) * 18 * kNaSamples);
+constexpr size_t kNaOffTab32 = na_round(kNaOffTab64 + sizeof(double) * kTab64PerN * kNaSamples);
+constexpr size_t kNaOffTw64 = na_round(kNaOffTab32 + sizeof(float) * kTab32PerN * kNaSamples);
 constexpr size_t kNaOffTw32 = na_round(kNaOffTw64 + sizeof(double) * 2 * kTwiddles);
 constexpr size_t kNaOffWin = na_round(kNaOffTw32 + sizeof(float) * 2 * kTwiddles);
 constexpr size_t kNaOffItems = na_round(kNaOffWin + sizeof(gb_window_t) * kNaMaxWindows);
@@ -767,7 +913,7 @@ constexpr size_t kNaOffPrep = na_round(kNaOffMeta + sizeof(WinMeta) * kNaMaxWind
 constexpr size_t kNaOffHead = na_round(kNaOffPrep + sizeof(Win32) * kNaMaxBins);
 constexpr size_t kNaBytes = na_round(kNaOffHead + 4 * sizeof(int));   // two queue heads, status
 
-// 8.6 MB per device, kept until the process exits
+// 8.7 MB per device, kept until the process exits
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
 struct NaDevice {
@@ -849,9 +995,10 @@ extern "C" int gb_loglik_mixed_noalloc(const gb_obs_t* obs, const gb_window_t* w
         const int N = 32 << i;
         t64[i] = (double*)(b + o64);
         t32[i] = (float*)(b + o32);
-        tabs.t[i] = OrbitTables32{(const float4*)t32[i], (const float2*)(t32[i] + 16 * N)};
-        o64 += sizeof(double) * 18 * N;
-        o32 += sizeof(float) * 18 * N;
+        tabs.t[i] = OrbitTables32{(const float4*)t32[i], (const float2*)(t32[i] + 16 * N),
+                                  (const float4*)(t32[i] + 18 * N)};
+        o64 += sizeof(double) * kTab64PerN * N;
+        o32 += sizeof(float) * kTab32PerN * N;
     }
     double* tw64 = (double*)(b + kNaOffTw64);
     float* tw32 = (float*)(b + kNaOffTw32);
@@ -1346,7 +1493,7 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? 2 : 1) grad_mixed_k
             float sdh = 0.0f, cdh = 0.0f, shh = 0.0f, chh = 0.0f;
             float tacc[KT][2] = {}, vp[2][2] = {}, vq[2][2] = {};
             if (!g.m.bad) {
-                slow_part_dispatch(g.m, tab, N, bufA, bufE, lane);
+                slow_part_dispatch<false>(g.m, tab, N, bufA, bufE, lane);
                 __syncwarp();
                 const long long off64 = g.m.q - win.k0;
                 const int off = (off64 > -(long long)N && off64 < (long long)win.W + N) ? (int)off64 : -4 * N;

@@ -376,8 +376,10 @@ def test_grad_mixed_matches_oracle(ctx, ctx1, which):
         gn, on = gg[b] * s, go[b] * s
         worst = max(worst, float((gn - on).abs().max()) / float(on.abs().sum()))
     assert worst <= 1e-4, worst
+    # the likelihood kernel's logL: the same float arithmetic up to the order of
+    # the transform's operations (the two kernels factor the DFT differently)
     lm, _, _ = c.loglik(wl.windows, *args, prec="mixed")
-    assert torch.allclose(lg, lm.cpu(), rtol=0, atol=1e-9 * float(lo.abs().max()))
+    assert torch.allclose(lg, lm.cpu(), rtol=0, atol=1e-6 * float(lo.abs().max()))
 
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
