@@ -78,6 +78,18 @@ __device__ __forceinline__ void split(double x, float& h, float& l) {
     l = (float)(x - (double)h);
 }
 
+// exp(-2 pi i m / 32), m < 16: the twiddles of the register DFTs (R <= 32),
+// read with compile-time indices as constant operands
+__constant__ float2 kW32[16] = {
+    {1.000000000e+00f, 0.0f}, {9.807852804e-01f, -1.950903220e-01f},
+    {9.238795325e-01f, -3.826834324e-01f}, {8.314696123e-01f, -5.555702330e-01f},
+    {7.071067812e-01f, -7.071067812e-01f}, {5.555702330e-01f, -8.314696123e-01f},
+    {3.826834324e-01f, -9.238795325e-01f}, {1.950903220e-01f, -9.807852804e-01f},
+    {0.0f, -1.000000000e+00f}, {-1.950903220e-01f, -9.807852804e-01f},
+    {-3.826834324e-01f, -9.238795325e-01f}, {-5.555702330e-01f, -8.314696123e-01f},
+    {-7.071067812e-01f, -7.071067812e-01f}, {-8.314696123e-01f, -5.555702330e-01f},
+    {-9.238795325e-01f, -3.826834324e-01f}, {-9.807852804e-01f, -1.950903220e-01f}};
+
 // 1/k! for the link transfer series (Taylor coefficients of (e^w - 1)/w)
 __constant__ float kInvFact[24] = {
     1.0f, 1.0f, 0.5f, 1.6666666666666666e-01f, 4.1666666666666664e-02f, 8.3333333333333332e-03f,
@@ -390,7 +402,7 @@ __device__ __forceinline__ void reg_fft(float2 (&x)[R], const float2* __restrict
                 } else if (4 * j == 2 * h) {   // exp(-i pi/2) = -i
                     t = make_float2(y[i1].y, -y[i1].x);
                 } else {
-                    t = cmulf(__ldg(tw1024 + j * (512 / h)), y[i1]);
+                    t = cmulf(kW32[j * (16 / h)], y[i1]);
                 }
                 y[i1] = csubf(y[i0], t);
                 y[i0] = caddf(y[i0], t);
