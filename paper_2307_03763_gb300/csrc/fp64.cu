@@ -28,22 +28,37 @@ __device__ __forceinline__ C64 cscale(C64 a, double s) { return {a.x * s, a.y * 
 // Per-candidate constants.
 struct Cand64 {
     double k[3];          // propagation direction
-    double Hr[6], Hi[6];  // H_xx, H_yy, H_zz, H_xy, H_xz, H_yz
-    double f0, fd, delta, phi0, A;
+    double u[3], v[3];    // polarisation basis (psi = 0)
+    double gpr, gxr, gpi, gxi;   // n.H.n = (gpr Fp + gxr Fx) + i (gpi Fp + gxi Fx), Fp = (n.u)^2 - (n.v)^2, Fx = 2 (n.u)(n.v)
+    double f0, fd, delta, phi0c, A;   // phi0c = phi0 / (2 pi)
+    double D0r, D0i;      // exp(-i f0 / f*)
+    double eps;           // fdot / f*
     long long q;
     int bad;
-    int pad;
+    int J;                // degree of the link-transfer series (0: direct evaluation)
 };
 
 struct Geo64 {
-    double T, T_over_N, fstar, scale;   // scale = T / (2N)
+    double T, T_over_N, inv_fstar, scale;   // scale = T / (2N)
     int N, logN;
 };
+
+// 1/k!, k < 35: the link-transfer series
+__constant__ double kInvFact64[35] = {
+    1.00000000000000000e+00, 1.00000000000000000e+00, 5.00000000000000000e-01, 1.66666666666666657e-01,
+    4.16666666666666644e-02, 8.33333333333333322e-03, 1.38888888888888894e-03, 1.98412698412698413e-04,
+    2.48015873015873016e-05, 2.75573192239858925e-06, 2.75573192239858883e-07, 2.50521083854417202e-08,
+    2.08767569878681002e-09, 1.60590438368216133e-10, 1.14707455977297245e-11, 7.64716373181981641e-13,
+    4.77947733238738525e-14, 2.81145725434552060e-15, 1.56192069685862253e-16, 8.22063524662432950e-18,
+    4.11031762331216484e-19, 1.95729410633912626e-20, 8.89679139245057408e-22, 3.86817017063068413e-23,
+    1.61173757109611839e-24, 6.44695028438447359e-26, 2.47959626322479759e-27, 9.18368986379554601e-29,
+    3.27988923706983776e-30, 1.13099628864477159e-31, 3.76998762881590539e-33, 1.21612504155351789e-34,
+    3.80039075485474342e-36, 1.15163356207719509e-37, 3.38715753552116180e-39};
 
 // Candidate setup (one lane, one candidate).  The carrier bin uses explicit
 // round-to-nearest operations so that q is bit-identical to any IEEE
 // evaluation of ((f0*T) + ((0.5*fdot)*T)*T) + 0.5.
-__device__ void setup64(const double* th, double T, Cand64& c) {
+__device__ void setup64(const double* th, double T, double inv_fstar, Cand64& c) {
     const double f0 = th[0], fd = th[1], beta = th[2], lam = th[3];
     const double A = th[4], iota = th[5], psi = th[6], phi0 = th[7];
     bool bad = false;
@@ -56,7 +71,7 @@ __device__ void setup64(const double* th, double T, Cand64& c) {
     c.delta = __dadd_rn(f0T, -qd);
     c.f0 = f0;
     c.fd = fd;
-    c.phi0 = phi0;
+    c.phi0c = phi0 * 0.15915494309189535;   // 1 / (2 pi)
     c.A = A;
     double sb, cb, sl, cl, s2, c2;
     sincos(beta, &sb, &cb);
@@ -66,96 +81,139 @@ __device__ void setup64(const double* th, double T, Cand64& c) {
     c.k[0] = -(cb * cl);
     c.k[1] = -(cb * sl);
     c.k[2] = -sb;
-    const double u[3] = {sb * cl, sb * sl, -cb};
-    const double v[3] = {sl, -cl, 0.0};
-    const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+    c.u[0] = sb * cl;
+    c.u[1] = sb * sl;
+    c.u[2] = -cb;
+    c.v[0] = sl;
+    c.v[1] = -cl;
+    c.v[2] = 0.0;
+    // H = A+ E+(psi) - i Ax Ex(psi) with E+ = u u - v v and Ex = u v + v u rotated
+    // by 2 psi: n.H.n = A+ (c2 Fp - s2 Fx) - i Ax (s2 Fp + c2 Fx)
     const double Ap = A * (1.0 + ci * ci);
     const double Ax = -2.0 * A * ci;
-    for (int m = 0; m < 6; ++m) {
-        const int a = ia[m], b = ib[m];
-        const double ep = u[a] * u[b] - v[a] * v[b];
-        const double ex = u[a] * v[b] + v[a] * u[b];
-        const double Ep = c2 * ep - s2 * ex;
-        const double Ex = s2 * ep + c2 * ex;
-        c.Hr[m] = Ap * Ep;
-        c.Hi[m] = -(Ax * Ex);
+    c.gpr = Ap * c2;
+    c.gxr = -(Ap * s2);
+    c.gpi = -(Ax * s2);
+    c.gxi = -(Ax * c2);
+    // link-transfer series degree: first omitted term below 1e-17 for the
+    // largest argument X = f (1 + |k.n|)/(2 f*) <= f_max / f*
+    const double xmax = fmax(fabs(f0), fabs(f0 + fd * T)) * inv_fstar;
+    c.J = xmax <= 0.22 ? 6 : xmax <= 0.5 ? 8 : xmax <= 1.3 ? 12 : xmax <= 2.35 ? 16 : 0;
+    double sD, cD;
+    sincos(f0 * inv_fstar, &sD, &cD);
+    c.D0r = cD;
+    c.D0i = -sD;
+    c.eps = fd * inv_fstar;
+}
+
+// n.H.n for a unit arm vector n
+__device__ __forceinline__ C64 nHn(const Cand64& c, double nx, double ny, double nz) {
+    const double nu = c.u[0] * nx + c.u[1] * ny + c.u[2] * nz;
+    const double nv = c.v[0] * nx + c.v[1] * ny;
+    const double Fp = (nu - nv) * (nu + nv), Fx = 2.0 * nu * nv;
+    return {c.gpr * Fp + c.gxr * Fx, c.gpi * Fp + c.gxi * Fx};
+}
+
+// sinc(X) exp(-iX): J+1 terms of the series of (1 - e^{-2iX})/(2iX) split into
+// real and imaginary parts (Horner in y = -4X^2); J = 0: direct evaluation
+template <int J>
+__device__ __forceinline__ C64 transfer64(double X) {
+    if constexpr (J == 0) {
+        double sX, cX;
+        sincos(X, &sX, &cX);
+        const double sinc = (X != 0.0) ? sX / X : 1.0;
+        return {sinc * cX, -(sinc * sX)};
+    } else {
+        const double y = -4.0 * X * X;
+        double re = kInvFact64[2 * J + 1], im = kInvFact64[2 * J + 2];
+#pragma unroll
+        for (int j = J - 1; j >= 0; --j) {
+            re = fma(re, y, kInvFact64[2 * j + 1]);
+            im = fma(im, y, kInvFact64[2 * j + 2]);
+        }
+        return {re, -2.0 * X * im};
     }
 }
 
-// n.H.n for a unit vector n and the symmetric complex H.
-__device__ __forceinline__ C64 nHn(const Cand64& c, double nx, double ny, double nz) {
-    const double m0 = nx * nx, m1 = ny * ny, m2 = nz * nz;
-    const double m3 = 2.0 * nx * ny, m4 = 2.0 * nx * nz, m5 = 2.0 * ny * nz;
-    C64 g;
-    g.x = c.Hr[0] * m0 + c.Hr[1] * m1 + c.Hr[2] * m2 + c.Hr[3] * m3 + c.Hr[4] * m4 + c.Hr[5] * m5;
-    g.y = c.Hi[0] * m0 + c.Hi[1] * m1 + c.Hi[2] * m2 + c.Hi[3] * m3 + c.Hi[4] * m4 + c.Hi[5] * m5;
-    return g;
-}
-
 // -i a sinc(X) exp(-iX) G exp(i Psi)
+template <int J>
 __device__ __forceinline__ C64 link64(double a, double X, C64 G, C64 rx) {
-    double sX, cX;
-    sincos(X, &sX, &cX);
-    const double sinc = (X != 0.0) ? sX / X : 1.0;
-    const C64 tr = {a * sinc * cX, -(a * sinc * sX)};   // a sinc(X) e^{-iX}
+    const C64 t = transfer64<J>(X);
+    const C64 tr = {a * t.x, a * t.y};
     const C64 z = cmul(cmul(tr, G), rx);
     return {z.y, -z.x};                                    // times -i
 }
 
 // Slow part of one candidate into buf{A,E} at bit-reversed positions, then
-// an in-place radix-2 FFT -> natural-order DFT S_k, k = 0..N-1.
+// an in-place radix-2 FFT -> natural-order DFT S_k, k = 0..N-1.  The receiver
+// phases reach ~1e6 rad; taken in cycles and reduced modulo one first, their
+// sines come from a short argument.
+template <int J>
 __device__ void template64(const Cand64& c, const Geo64& g, const OrbitTables64& tab, const C64* tw,
                            C64* bufA, C64* bufE, int lane) {
     const int N = g.N;
+    const double inv_c = 1.0 / kC;
+    const double u_step = 1.0 / (double)N;   // t/T = n/N exactly
     for (int n = lane; n < N; n += 32) {
         const double t = (double)n * g.T_over_N;
         C64 rx[3];
         for (int j = 0; j < 3; ++j) {
             const double kap = (c.k[0] * tab.x[(j * 3 + 0) * N + n] + c.k[1] * tab.x[(j * 3 + 1) * N + n] +
-                                c.k[2] * tab.x[(j * 3 + 2) * N + n]) / kC;
-            const double ph = 2.0 * kPi *
-                                  (c.delta * t / g.T + 0.5 * c.fd * (t * t) - c.f0 * kap - c.fd * t * kap +
-                                   0.5 * c.fd * (kap * kap)) +
-                              c.phi0;
+                                c.k[2] * tab.x[(j * 3 + 2) * N + n]) * inv_c;
+            // receiver phase in cycles, reduced modulo one before the sine and cosine
+            double cyc = c.delta * ((double)n * u_step) + 0.5 * c.fd * (t * t) - c.f0 * kap - c.fd * t * kap +
+                         0.5 * c.fd * (kap * kap) + c.phi0c;
+            cyc -= rint(cyc);
             double s, co;
-            sincos(ph, &s, &co);
+            sincospi(2.0 * cyc, &s, &co);
             rx[j] = {co, s};
         }
         const double f = c.f0 + c.fd * t;
-        const double a = f / (2.0 * g.fstar);
+        const double a = f * (0.5 * g.inv_fstar);
         C64 z01, z10, z12, z21, z20, z02;
         {
             const double nx = tab.arm[0 * N + n], ny = tab.arm[1 * N + n], nz = tab.arm[2 * N + n];
             const double kn = c.k[0] * nx + c.k[1] * ny + c.k[2] * nz;
             const C64 G = nHn(c, nx, ny, nz);
-            z01 = link64(a, a * (1.0 - kn), G, rx[1]);
-            z10 = link64(a, a * (1.0 + kn), G, rx[0]);
+            z01 = link64<J>(a, a * (1.0 - kn), G, rx[1]);
+            z10 = link64<J>(a, a * (1.0 + kn), G, rx[0]);
         }
         {
             const double nx = tab.arm[3 * N + n], ny = tab.arm[4 * N + n], nz = tab.arm[5 * N + n];
             const double kn = c.k[0] * nx + c.k[1] * ny + c.k[2] * nz;
             const C64 G = nHn(c, nx, ny, nz);
-            z12 = link64(a, a * (1.0 - kn), G, rx[2]);
-            z21 = link64(a, a * (1.0 + kn), G, rx[1]);
+            z12 = link64<J>(a, a * (1.0 - kn), G, rx[2]);
+            z21 = link64<J>(a, a * (1.0 + kn), G, rx[1]);
         }
         {
             const double nx = tab.arm[6 * N + n], ny = tab.arm[7 * N + n], nz = tab.arm[8 * N + n];
             const double kn = c.k[0] * nx + c.k[1] * ny + c.k[2] * nz;
             const C64 G = nHn(c, nx, ny, nz);
-            z20 = link64(a, a * (1.0 - kn), G, rx[0]);
-            z02 = link64(a, a * (1.0 + kn), G, rx[2]);
+            z20 = link64<J>(a, a * (1.0 - kn), G, rx[0]);
+            z02 = link64<J>(a, a * (1.0 + kn), G, rx[2]);
         }
-        double sD, cD;
-        sincos(f / g.fstar, &sD, &cD);
-        const C64 D = {cD, -sD};
+        // D = exp(-i f/f*) = exp(-i f0/f*) exp(-i th), th = fdot t / f*: a short
+        // series while |th| <= 1/64 (terms to th^7, first omitted below 1e-19)
+        C64 D;
+        const double th = c.eps * t;
+        if (fabs(th) <= 0.015625) {
+            const double t2 = th * th;
+            const double cs = fma(fma(fma(t2, -1.0 / 720.0, 1.0 / 24.0), t2, -0.5), t2, 1.0);
+            const double sn = th * fma(fma(fma(t2, -1.0 / 5040.0, 1.0 / 120.0), t2, -1.0 / 6.0), t2, 1.0);
+            D = cmul({c.D0r, c.D0i}, {cs, -sn});
+        } else {
+            double sD, cD;
+            sincos(f * g.inv_fstar, &sD, &cD);
+            D = {cD, -sD};
+        }
         const C64 D2 = cmul(D, D);
         const C64 omd = {1.0 - D2.x, -D2.y};
         const C64 X = cmul(omd, csub(cadd(z10, cmul(D, z01)), cadd(z20, cmul(D, z02))));
         const C64 Y = cmul(omd, csub(cadd(z21, cmul(D, z12)), cadd(z01, cmul(D, z10))));
         const C64 Z = cmul(omd, csub(cadd(z02, cmul(D, z20)), cadd(z12, cmul(D, z21))));
-        const double r2 = sqrt(2.0), r6 = sqrt(6.0);
-        const C64 sA = {(Z.x - X.x) / r2, (Z.y - X.y) / r2};
-        const C64 sE = {(X.x - 2.0 * Y.x + Z.x) / r6, (X.y - 2.0 * Y.y + Z.y) / r6};
+        const double r2 = 0.70710678118654752, r6 = 0.40824829046386302;   // 1/sqrt(2), 1/sqrt(6)
+        const C64 sA = {(Z.x - X.x) * r2, (Z.y - X.y) * r2};
+        const C64 sE = {(X.x - 2.0 * Y.x + Z.x) * r6, (X.y - 2.0 * Y.y + Z.y) * r6};
         const int br = (int)(__brev((unsigned)n) >> (32 - g.logN));
         bufA[br] = sA;
         bufE[br] = sE;
@@ -178,6 +236,17 @@ __device__ void template64(const Cand64& c, const Geo64& g, const OrbitTables64&
             bufE[i1] = csub(ue, ve);
         }
         __syncwarp();
+    }
+}
+
+__device__ void template64_dispatch(const Cand64& c, const Geo64& g, const OrbitTables64& tab, const C64* tw,
+                                    C64* bufA, C64* bufE, int lane) {
+    switch (c.J) {
+        case 6: template64<6>(c, g, tab, tw, bufA, bufE, lane); break;
+        case 8: template64<8>(c, g, tab, tw, bufA, bufE, lane); break;
+        case 12: template64<12>(c, g, tab, tw, bufA, bufE, lane); break;
+        case 16: template64<16>(c, g, tab, tw, bufA, bufE, lane); break;
+        default: template64<0>(c, g, tab, tw, bufA, bufE, lane); break;
     }
 }
 
@@ -221,7 +290,7 @@ __global__ void __launch_bounds__(kWarps64 * 32) loglik64_kernel(
     g.logN = 31 - __clz(win.N);
     g.T = T;
     g.T_over_N = T / (double)win.N;
-    g.fstar = fstar;
+    g.inv_fstar = 1.0 / fstar;
     g.scale = T / (2.0 * (double)win.N);
     const OrbitTables64 tab = tabs.t[g.logN - 5];
     C64* bufA = bufs + (size_t)warp * 2 * n_max;
@@ -233,7 +302,7 @@ __global__ void __launch_bounds__(kWarps64 * 32) loglik64_kernel(
     const int64_t c_lo = tile.c_begin + (int64_t)warp * grp;
     const int64_t c_hi = min(tile.c_end, c_lo + grp);
     if (c_lo >= c_hi) return;
-    if (c_lo + lane < c_hi) setup64(theta + 8 * (c_lo + lane), T, mycand[lane]);
+    if (c_lo + lane < c_hi) setup64(theta + 8 * (c_lo + lane), T, g.inv_fstar, mycand[lane]);
     __syncwarp();
     const int64_t half = win.N / 2;
     for (int64_t cidx = c_lo; cidx < c_hi; ++cidx) {
@@ -247,7 +316,7 @@ __global__ void __launch_bounds__(kWarps64 * 32) loglik64_kernel(
             }
             continue;
         }
-        template64(c, g, tab, tw, bufA, bufE, lane);
+        template64_dispatch(c, g, tab, tw, bufA, bufE, lane);
         double sdh = 0.0, shh = 0.0;
         for (int m = lane; m < win.N; m += 32) {
             const int64_t kk = c.q - half + m - win.k0;
@@ -287,7 +356,7 @@ __global__ void __launch_bounds__(kWarps64 * 32) waveform64_kernel(
     g.logN = 31 - __clz(N);
     g.T = T;
     g.T_over_N = T / (double)N;
-    g.fstar = fstar;
+    g.inv_fstar = 1.0 / fstar;
     g.scale = T / (2.0 * (double)N);
     C64* bufA = bufs + (size_t)warp * 2 * N;
     C64* bufE = bufA + N;
@@ -295,7 +364,7 @@ __global__ void __launch_bounds__(kWarps64 * 32) waveform64_kernel(
     const int64_t c_lo = ((int64_t)blockIdx.x * kWarps64 + warp) * group;
     const int64_t c_hi = min(B, c_lo + group);
     if (c_lo >= c_hi) return;
-    if (c_lo + lane < c_hi) setup64(theta + 8 * (c_lo + lane), T, mycand[lane]);
+    if (c_lo + lane < c_hi) setup64(theta + 8 * (c_lo + lane), T, g.inv_fstar, mycand[lane]);
     __syncwarp();
     for (int64_t b = c_lo; b < c_hi; ++b) {
         const Cand64& c = mycand[b - c_lo];
@@ -309,7 +378,7 @@ __global__ void __launch_bounds__(kWarps64 * 32) waveform64_kernel(
             }
             continue;
         }
-        template64(c, g, tab, tw, bufA, bufE, lane);
+        template64_dispatch(c, g, tab, tw, bufA, bufE, lane);
         for (int m = lane; m < N; m += 32) {
             const int idx = (m + N / 2) & (N - 1);
             outA[m] = cscale(bufA[idx], g.scale);
