@@ -34,6 +34,8 @@ def observed_fisher(lib_ctx, windows, dA, dE, wA, wE, theta, prec="fp64", rel=1e
 
     windows: (k0, W, N, data_off, _, _) per window; theta: (n_win, 8) device.
     Step per parameter: rel times its natural scale (1/T, 1/T^2, 1 rad, A).
+    The entries span ~70 decades in these units: invert S F S with
+    S = diag(1/T, 1/T^2, 1, 1, A, 1, 1, 1), not F itself.
     """
     n_win = theta.shape[0]
     T = lib_ctx.T_obs

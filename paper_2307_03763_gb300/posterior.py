@@ -73,3 +73,62 @@ class PosteriorRounds:
             if left:
                 self._round()
         return self
+
+
+class AnnealedPosterior:
+    """Alg. 4 with a temperature ladder: one round of n proposals per
+    temperature (15, 10, 5, 3, 2, 1 by default), every window's proposal
+    refitted between rounds to the states its chain visited.
+
+    The paper refits paired two-dimensional kernel density estimates; here the
+    refit is a Gaussian: the mean and covariance of the visited states
+    (weighted by the steps spent in each), the covariance scaled by the ratio
+    of the next temperature to this one (the tempered target's variance
+    scales with T) and widened by ``inflate``.  The rounds run in the
+    library (draws, likelihood, chains); the refit statistics are
+    8-dimensional means and covariances formed with torch on the device.
+    """
+
+    def __init__(self, ctx, windows, dA, dE, wA, wE, mean, cov, n, seed=1, temperatures=(15, 10, 5, 3, 2, 1),
+                 prec="mixed", inflate=1.44, floor=1e-4):
+        self.rounds = PosteriorRounds(ctx, windows, dA, dE, wA, wE, mean, cov, n, seed=seed, prec=prec)
+        self.temperatures = [float(t) for t in temperatures]
+        self.inflate = float(inflate)
+        self.cov0 = torch.as_tensor(cov, dtype=torch.float64, device=ctx.device).reshape(self.rounds.nw, 8, 8)
+        self.floor = float(floor)
+
+    def _refit(self, ratio):
+        r = self.rounds
+        th = r.theta.view(r.nw, r.n, 8)
+        idx = r.chain.long()                                          # state after every step
+        states = torch.gather(th, 1, idx[:, :, None].expand(-1, -1, 8))   # (nw, n, 8), steps weigh the states
+        mu = states.mean(1)
+        dev = states - mu[:, None, :]
+        cov = dev.transpose(1, 2) @ dev / max(1, r.n - 1)
+        # the next target is narrower by T_next/T in variance
+        cov = ratio * self.inflate * 0.5 * (cov + cov.transpose(1, 2))
+        # floor: eigenvalues of the refit in the first round's metric
+        L0 = torch.linalg.cholesky(self.cov0)
+        Li = torch.linalg.inv(L0)
+        M = Li @ cov @ Li.transpose(1, 2)
+        ev, V = torch.linalg.eigh(0.5 * (M + M.transpose(1, 2)))
+        ev = torch.clamp(torch.nan_to_num(ev, nan=1.0), min=self.floor, max=1.0 / self.floor)
+        # a square root S (S S^T = L0 M L0^T) and, from the QR factors of S^T,
+        # the lower-triangular factor with a positive diagonal (no squaring of
+        # the condition number; natural units span ~20 decades)
+        S = L0 @ (V * torch.sqrt(ev)[:, None, :])
+        _, Rq = torch.linalg.qr(S.transpose(1, 2))
+        L = Rq.transpose(1, 2)
+        L = L * torch.sign(torch.diagonal(L, dim1=1, dim2=2))[:, None, :]
+        r.mean.copy_(torch.nan_to_num(mu))
+        r.chol.copy_(L)
+
+    def run(self):
+        """All temperatures; the buffers of ``self.rounds`` hold the last (T = 1) round."""
+        r = self.rounds
+        for k, T in enumerate(self.temperatures):
+            r.temperature.fill_(T)
+            r.run(1, graph=False)
+            if k + 1 < len(self.temperatures):
+                self._refit(self.temperatures[k + 1] / T)
+        return self

@@ -67,6 +67,9 @@ def fisher_matrix(src, window, wA, wE, T, rel=1e-4):
 
 
 def fisher_sigma(src, window, wA, wE, T, rel=1e-4):
-    """sqrt(diag F^-1) of the window's Fisher matrix."""
+    """sqrt(diag F^-1) of the window's Fisher matrix, inverted in natural units
+    (1/T, 1/T^2, rad, A): in SI units its entries span ~70 decades, beyond the
+    reach of a pseudo-inverse's relative cut-off."""
     F = fisher_matrix(src, window, wA, wE, T, rel)
-    return np.sqrt(np.abs(np.diag(np.linalg.pinv(F))))
+    sc = np.array([1.0 / T, 1.0 / T ** 2, 1.0, 1.0, src[4], 1.0, 1.0, 1.0])
+    return np.sqrt(np.abs(np.diag(np.linalg.pinv(F * np.outer(sc, sc))))) * sc

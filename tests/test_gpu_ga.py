@@ -145,3 +145,24 @@ def test_posterior_rounds_graph_equals_eager_and_chains_are_valid(api):
             c = i
         assert ch[i] == c
     assert 0 < int(b.accepted[0]) < 10000
+
+
+def test_annealed_posterior_concentrates_on_the_source(api):
+    # six temperatures from a proposal 10 Fisher widths wide and 2 widths off:
+    # the T = 1 chain sits on the source and has about the Fisher width
+    from paper_2307_03763_gb300.posterior import AnnealedPosterior
+    wl, src, dA, dE, box = _single_source_problem(snr=60.0, seed=wk.SEED_BASE + 43)
+    ctx = api.Context(wl.T)
+    args = (_cuda(dA, torch.complex128), _cuda(dE, torch.complex128), _cuda(wl.w_A, torch.float64),
+            _cuda(wl.w_E, torch.float64))
+    sig = _data.fisher_sigma(src, wl.windows[0], wl.w_A, wl.w_E, wl.T)
+    start = src + 2.0 * sig * np.array([1, -1, 1, -1, 0.5, 1, -1, 1])
+    ap = AnnealedPosterior(ctx, wl.windows, *args, start[None], np.diag((10 * sig) ** 2)[None], n=10000,
+                           seed=5).run()
+    r = ap.rounds
+    th = r.theta.view(1, r.n, 8)[0].cpu().numpy()
+    states = th[r.chain[0].long().cpu().numpy()]
+    mean, sd = states.mean(0), states.std(0)
+    assert abs(mean[0] - src[0]) < 3 * sig[0], (mean[0], src[0], sig[0])
+    assert 0.2 * sig[0] < sd[0] < 3 * sig[0], (sd[0], sig[0])
+    assert int(r.accepted[0]) > 100
