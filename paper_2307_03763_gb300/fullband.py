@@ -147,12 +147,14 @@ class FullBand:
         s[:, 0] = 1.0 / self.T
         s[:, 1] = 1.0 / self.T ** 2
         s[:, 4] = theta[:, 4].abs()
-        Fs = F * s[:, :, None] * s[:, None, :]
-        ev, V = torch.linalg.eigh(0.5 * (Fs + Fs.transpose(1, 2)))
-        ev = torch.clamp(ev, min=1e-8 * torch.clamp(ev[:, -1:], min=1e-300))
-        C = (V / ev[:, None, :]) @ V.transpose(1, 2) * width ** 2
-        cap = torch.tensor([4.0, 4.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0], dtype=theta.dtype, device=self.dev) ** 2
-        d = torch.sqrt(torch.clamp(torch.diagonal(C, dim1=1, dim2=2) / cap, min=1.0))
+        # 8x8 algebra on the host (no device linear-algebra library needed)
+        s = s.cpu().numpy()
+        Fs = F.cpu().numpy() * s[:, :, None] * s[:, None, :]
+        ev, V = np.linalg.eigh(0.5 * (Fs + Fs.transpose(0, 2, 1)))
+        ev = np.maximum(ev, 1e-8 * np.maximum(ev[:, -1:], 1e-300))
+        C = (V / ev[:, None, :]) @ V.transpose(0, 2, 1) * width ** 2
+        cap = np.array([4.0, 4.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0]) ** 2
+        d = np.sqrt(np.maximum(np.diagonal(C, axis1=1, axis2=2) / cap, 1.0))
         C = C / d[:, :, None] / d[:, None, :]
         return C * s[:, :, None] * s[:, None, :]
 

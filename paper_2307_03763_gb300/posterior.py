@@ -9,6 +9,7 @@ N(mean_w, cov_w) per window; the paper anneals and refits it with a 2-D KDE
 between rounds, which is not part of this driver.  The module orders calls,
 owns buffers and factors the 8x8 proposal covariances once at set-up.
 """
+import numpy as np
 import torch
 
 
@@ -25,8 +26,9 @@ class PosteriorRounds:
         self.windows = [(k0, W, N, doff, w * self.n, self.n) for w, (k0, W, N, doff, _, _) in enumerate(windows)]
         self.data = (dA, dE, wA, wE)
         self.mean = torch.as_tensor(mean, dtype=torch.float64, device=dev).reshape(self.nw, 8).contiguous()
-        cov = torch.as_tensor(cov, dtype=torch.float64, device=dev).reshape(self.nw, 8, 8)
-        self.chol = torch.linalg.cholesky(cov).contiguous()
+        # 8x8 factors on the host (no device linear-algebra library needed)
+        cov = np.asarray(torch.as_tensor(cov).detach().cpu(), dtype=np.float64).reshape(self.nw, 8, 8)
+        self.chol = torch.as_tensor(np.linalg.cholesky(cov), device=dev).contiguous()
         self.temperature = (torch.ones(self.nw, dtype=torch.float64, device=dev) if temperature is None else
                             torch.as_tensor(temperature, dtype=torch.float64, device=dev).contiguous())
         m = self.nw * self.n
@@ -84,9 +86,11 @@ class AnnealedPosterior:
     refit is a Gaussian: the mean and covariance of the visited states
     (weighted by the steps spent in each), the covariance scaled by the ratio
     of the next temperature to this one (the tempered target's variance
-    scales with T) and widened by ``inflate``.  The rounds run in the
-    library (draws, likelihood, chains); the refit statistics are
-    8-dimensional means and covariances formed with torch on the device.
+    scales with T), widened by ``inflate``, and floored and capped at
+    ``floor`` and 1/``floor`` times the first round's in every direction.  The
+    rounds run in the library (draws, likelihood, chains); the refit's
+    8-dimensional means and covariances are formed with torch on the device
+    and factored on the host.
     """
 
     def __init__(self, ctx, windows, dA, dE, wA, wE, mean, cov, n, seed=1, temperatures=(15, 10, 5, 3, 2, 1),
@@ -94,34 +98,34 @@ class AnnealedPosterior:
         self.rounds = PosteriorRounds(ctx, windows, dA, dE, wA, wE, mean, cov, n, seed=seed, prec=prec)
         self.temperatures = [float(t) for t in temperatures]
         self.inflate = float(inflate)
-        self.cov0 = torch.as_tensor(cov, dtype=torch.float64, device=ctx.device).reshape(self.rounds.nw, 8, 8)
         self.floor = float(floor)
+        self.L0 = self.rounds.chol.cpu().numpy()
 
     def _refit(self, ratio):
         r = self.rounds
         th = r.theta.view(r.nw, r.n, 8)
-        idx = r.chain.long()                                          # state after every step
-        states = torch.gather(th, 1, idx[:, :, None].expand(-1, -1, 8))   # (nw, n, 8), steps weigh the states
+        idx = r.chain.long()                                              # state after every step
+        states = torch.gather(th, 1, idx[:, :, None].expand(-1, -1, 8))   # (nw, n, 8): steps weigh the states
         mu = states.mean(1)
         dev = states - mu[:, None, :]
-        cov = dev.transpose(1, 2) @ dev / max(1, r.n - 1)
+        cov = (dev.transpose(1, 2) @ dev / max(1, r.n - 1)).cpu().numpy()
+        mu = np.nan_to_num(mu.cpu().numpy())
         # the next target is narrower by T_next/T in variance
-        cov = ratio * self.inflate * 0.5 * (cov + cov.transpose(1, 2))
-        # floor: eigenvalues of the refit in the first round's metric
-        L0 = torch.linalg.cholesky(self.cov0)
-        Li = torch.linalg.inv(L0)
-        M = Li @ cov @ Li.transpose(1, 2)
-        ev, V = torch.linalg.eigh(0.5 * (M + M.transpose(1, 2)))
-        ev = torch.clamp(torch.nan_to_num(ev, nan=1.0), min=self.floor, max=1.0 / self.floor)
-        # a square root S (S S^T = L0 M L0^T) and, from the QR factors of S^T,
-        # the lower-triangular factor with a positive diagonal (no squaring of
-        # the condition number; natural units span ~20 decades)
-        S = L0 @ (V * torch.sqrt(ev)[:, None, :])
-        _, Rq = torch.linalg.qr(S.transpose(1, 2))
-        L = Rq.transpose(1, 2)
-        L = L * torch.sign(torch.diagonal(L, dim1=1, dim2=2))[:, None, :]
-        r.mean.copy_(torch.nan_to_num(mu))
-        r.chol.copy_(L)
+        cov = ratio * self.inflate * 0.5 * (cov + cov.transpose(0, 2, 1))
+        # floor and cap the eigenvalues in the first round's metric, then take
+        # the lower-triangular factor with a positive diagonal from the QR
+        # factors of a square root (no squaring of the condition number; the
+        # natural units span ~20 decades)
+        Li = np.linalg.inv(self.L0)
+        M = Li @ cov @ Li.transpose(0, 2, 1)
+        ev, V = np.linalg.eigh(0.5 * (M + M.transpose(0, 2, 1)))
+        ev = np.clip(np.nan_to_num(ev, nan=1.0), self.floor, 1.0 / self.floor)
+        S = self.L0 @ (V * np.sqrt(ev)[:, None, :])
+        _, Rq = np.linalg.qr(S.transpose(0, 2, 1))
+        L = Rq.transpose(0, 2, 1)
+        L = L * np.sign(np.diagonal(L, axis1=1, axis2=2))[:, None, :]
+        r.mean.copy_(torch.as_tensor(mu))
+        r.chol.copy_(torch.as_tensor(L))
 
     def run(self):
         """All temperatures; the buffers of ``self.rounds`` hold the last (T = 1) round."""
