@@ -281,6 +281,29 @@ int gb_draw_gaussian(gb_ctx_t* ctx, int32_t n_win, int32_t n, const double* mu, 
                      uint64_t seed, const uint64_t* round_in, uint64_t* round_out, double* theta,
                      double* log_g, double* log_u, void* stream);
 
+/* Gaussian refit of the independence proposal between the temperatures of
+ * Alg. 4 (the paper refits paired 2-D kernel density estimates; this is the
+ * Gaussian counterpart).  For window w, over the n states theta[w][chain[w][i]]
+ * (device; chain as written by gb_mh_independence, so a state weighs the
+ * steps spent in it), with u the number of accepted moves (i >= 1 with
+ * chain[i] = i) and P = chol[w] chol[w]^T the current proposal:
+ *   mean  mu_w = sample mean
+ *   C     = ratio (g inflate S + (1 - g) P),  S the sample covariance
+ *           (divisor n - 1), g = u / (u + kappa)
+ *   M     = L0^-1 C L0^-T            (L0 = chol0[w], lower triangular)
+ *   M_jk /= d_j d_k, d_j = max(1, sqrt(M_jj var_floor))   (variances <= 1/var_floor)
+ *   M_jj += var_floor;  chol[w] = L0 chol(M)   (overwritten)
+ * ratio is the next temperature over this one (the tempered target's
+ * variance scales with T); kappa is a pseudo-count that keeps a round with
+ * few acceptances close to the current proposal.  A non-finite M is replaced
+ * by the identity.  theta n_win x n x 8, chain n_win x n int32, chol0 and
+ * chol n_win x 64 (row-major, lower triangular; chol must not alias chol0),
+ * mu n_win x 8 (device).  n >= 2, ratio > 0, inflate > 0, kappa >= 0,
+ * 0 < var_floor < 1. */
+int gb_gauss_refit(gb_ctx_t* ctx, int32_t n_win, int32_t n, const double* theta, const int32_t* chain,
+                   const double* chol0, double ratio, double inflate, double kappa, double var_floor,
+                   double* mu, double* chol, void* stream);
+
 /* n blocks of Philox-4x32-10 (Salmon et al., SC 2011) with key = seed and
  * counter (i, 0, 0, 0), i < n, written as 4 words per block (device).  The
  * generator the genetic search draws from; exported so that it can be

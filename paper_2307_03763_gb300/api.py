@@ -68,6 +68,8 @@ _SIGNATURES = {
                                                _I64, _P, _I64, _P, _P, _P, _P, ctypes.c_char_p, _I32]),
     "gb_ga_step": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, ctypes.c_uint64, _P, _P,
                                   ctypes.POINTER(GAParams), _P, _P, _P, _P]),
+    "gb_gauss_refit": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, _P, _P, _P]),
     "gb_philox4x32": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint32, _P, _P]),
     "gb_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _I64, _P, _I64,
                                    _P, _I32, ctypes.POINTER(Tuning), _P]),
@@ -282,6 +284,21 @@ class Context:
                                            int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(round_in), _ptr(round_out),
                                            _ptr(th), _ptr(lg), _ptr(lu), _stream(self.device)))
         return th, lg, lu
+
+    def gauss_refit(self, theta, chain, chol0, ratio, inflate, kappa, floor, out):
+        """Gaussian refit of each window's proposal to its chain (see gb_gauss_refit).
+        out = (mu, chol): chol holds the current proposal's factor on entry."""
+        nw, n = chain.shape
+        _need(theta, torch.float64, self.device, "theta", (nw * n, 8))
+        _need(chain, torch.int32, self.device, "chain", (nw, n))
+        _need(chol0, torch.float64, self.device, "chol0", (nw, 8, 8))
+        mu, chol = out
+        _need(mu, torch.float64, self.device, "mu", (nw, 8))
+        _need(chol, torch.float64, self.device, "chol", (nw, 8, 8))
+        self._check(lib().gb_gauss_refit(self._h, nw, n, _ptr(theta), _ptr(chain), _ptr(chol0), float(ratio),
+                                         float(inflate), float(kappa), float(floor), _ptr(mu), _ptr(chol),
+                                         _stream(self.device)))
+        return mu, chol
 
     def philox(self, seed, n):
         """n blocks of Philox-4x32-10 with key = seed, counter (i, 0, 0, 0): (n, 4) int64 of uint32 values."""

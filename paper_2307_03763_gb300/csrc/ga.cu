@@ -351,6 +351,169 @@ extern "C" int gb_draw_gaussian(gb_ctx_t* ctx, int32_t n_win, int32_t n, const d
     return GB_OK;
 }
 
+namespace gb {
+namespace {
+
+// Gaussian refit of an independence proposal to the states its chain visited
+// (Alg. 4 refits the proposal between temperatures).  One CTA per window:
+// moments of theta[chain[i]] over all n steps (a state weighs the steps spent
+// in it), shifted by the first state, and the number u of accepted moves;
+// then one thread blends the sample covariance with the current proposal's
+// (weight u/(u + kappa) on the sample), scales it, whitens it with the first
+// proposal's factor L0, caps every whitened variance at 1/floor, adds floor
+// to the diagonal, factors it and writes L0 L_M.
+constexpr int kRefitThreads = 256;
+
+__global__ void __launch_bounds__(kRefitThreads) gauss_refit_kernel(int n, const double* __restrict__ theta,
+                                                                    const int32_t* __restrict__ chain,
+                                                                    const double* __restrict__ chol0, double ratio,
+                                                                    double inflate, double kappa, double floor_,
+                                                                    double* __restrict__ mu_out,
+                                                                    double* chol_io) {
+    __shared__ double x0[8];
+    __shared__ double part[kRefitThreads / 32][45];
+    const int w = blockIdx.x;
+    const double* th = theta + (size_t)w * (size_t)n * 8;
+    const int32_t* ch = chain + (size_t)w * (size_t)n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < 8) {
+        const int c0 = min(max(ch[0], 0), n - 1);
+        x0[threadIdx.x] = th[8 * (size_t)c0 + threadIdx.x];
+    }
+    __syncthreads();
+    double s[45];   // 8 first moments, 36 second moments (upper triangle), accepted moves
+#pragma unroll
+    for (int q = 0; q < 45; ++q) s[q] = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int c = min(max(ch[i], 0), n - 1);
+        if (i > 0 && ch[i] == i) s[44] += 1.0;
+        double d[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) d[j] = th[8 * (size_t)c + j] - x0[j];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s[j] += d[j];
+        int q = 8;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int k = j; k < 8; ++k) {
+                s[q] = fma(d[j], d[k], s[q]);
+                ++q;
+            }
+    }
+#pragma unroll
+    for (int q = 0; q < 45; ++q) {
+        double v = s[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) part[warp][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double t[45];
+    for (int q = 0; q < 45; ++q) {
+        t[q] = 0.0;
+        for (int k = 0; k < kRefitThreads / 32; ++k) t[q] += part[k][q];
+    }
+    const double inv_n = 1.0 / (double)n;
+    // the current proposal's covariance P = L L^T (read before chol_io is written)
+    double* Lio = chol_io + 64 * (size_t)w;
+    double P[8][8];
+    for (int j = 0; j < 8; ++j)
+        for (int k = 0; k <= j; ++k) {
+            double v = 0.0;
+            for (int m = 0; m <= k; ++m) v += Lio[8 * j + m] * Lio[8 * k + m];
+            P[j][k] = v;
+            P[k][j] = v;
+        }
+    const double wgt = t[44] / (t[44] + kappa);
+    double C[8][8];
+    int q = 8;
+    for (int j = 0; j < 8; ++j)
+        for (int k = j; k < 8; ++k) {
+            const double sc = (t[q] - t[j] * t[k] * inv_n) / (double)(n - 1);
+            ++q;
+            const double c = ratio * (wgt * inflate * sc + (1.0 - wgt) * P[j][k]);
+            C[j][k] = c;
+            C[k][j] = c;
+        }
+    const double* L0 = chol0 + 64 * (size_t)w;
+    // Y = L0^-1 C, then M = L0^-1 Y^T (= L0^-1 C L0^-T)
+    double Y[8][8], M[8][8];
+    for (int col = 0; col < 8; ++col)
+        for (int r = 0; r < 8; ++r) {
+            double v = C[r][col];
+            for (int k = 0; k < r; ++k) v -= L0[8 * r + k] * Y[k][col];
+            Y[r][col] = v / L0[8 * r + r];
+        }
+    for (int col = 0; col < 8; ++col)
+        for (int r = 0; r < 8; ++r) {
+            double v = Y[col][r];
+            for (int k = 0; k < r; ++k) v -= L0[8 * r + k] * M[k][col];
+            M[r][col] = v / L0[8 * r + r];
+        }
+    bool ok = true;
+    double dcap[8];
+    for (int j = 0; j < 8; ++j) {
+        ok = ok && isfinite(M[j][j]);
+        dcap[j] = fmax(1.0, sqrt(fmax(M[j][j], 0.0) * floor_));
+    }
+    for (int j = 0; j < 8; ++j)
+        for (int k = 0; k < 8; ++k) {
+            ok = ok && isfinite(M[j][k]);
+            M[j][k] = 0.5 * (M[j][k] + M[k][j]) / (dcap[j] * dcap[k]);
+        }
+    if (!ok)
+        for (int j = 0; j < 8; ++j)
+            for (int k = 0; k < 8; ++k) M[j][k] = j == k ? 1.0 : 0.0;
+    for (int j = 0; j < 8; ++j) M[j][j] += floor_;
+    // Cholesky of M (positive definite: a covariance plus floor on the diagonal)
+    double Lm[8][8];
+    for (int j = 0; j < 8; ++j) {
+        double dj = M[j][j];
+        for (int k = 0; k < j; ++k) dj -= Lm[j][k] * Lm[j][k];
+        dj = sqrt(fmax(dj, floor_ * 1e-6));
+        Lm[j][j] = dj;
+        for (int r = j + 1; r < 8; ++r) {
+            double v = M[r][j];
+            for (int k = 0; k < j; ++k) v -= Lm[r][k] * Lm[j][k];
+            Lm[r][j] = v / dj;
+        }
+        for (int r = 0; r < j; ++r) Lm[r][j] = 0.0;
+    }
+    for (int r = 0; r < 8; ++r)
+        for (int c = 0; c < 8; ++c) {
+            double v = 0.0;
+            for (int k = c; k <= r; ++k) v += L0[8 * r + k] * Lm[k][c];
+            Lio[8 * r + c] = c <= r ? v : 0.0;
+        }
+    for (int j = 0; j < 8; ++j) mu_out[8 * (size_t)w + j] = ok ? x0[j] + t[j] * inv_n : x0[j];
+}
+
+}  // namespace
+}  // namespace gb
+
+extern "C" int gb_gauss_refit(gb_ctx_t* ctx, int32_t n_win, int32_t n, const double* theta, const int32_t* chain,
+                              const double* chol0, double ratio, double inflate, double kappa, double floor_,
+                              double* mu, double* chol, void* stream) {
+    if (!ctx) return GB_EINVAL;
+    if (n_win < 0 || n < 0) return set_error(ctx, GB_EINVAL, "gb_gauss_refit: negative size");
+    if (n_win == 0) return GB_OK;
+    if (n < 2) return set_error(ctx, GB_EINVAL, "gb_gauss_refit: at least two steps per chain");
+    if (!theta || !chain || !chol0 || !mu || !chol) return set_error(ctx, GB_EINVAL, "gb_gauss_refit: null pointer");
+    if (!(ratio > 0.0) || !(ratio < 1e300) || !(inflate > 0.0) || !(inflate < 1e300) || !(kappa >= 0.0) ||
+        !(kappa < 1e300) || !(floor_ > 0.0) || !(floor_ < 1.0))
+        return set_error(ctx, GB_EINVAL, "gb_gauss_refit: ratio, inflate > 0, kappa >= 0, 0 < floor < 1");
+    if (chol == chol0) return set_error(ctx, GB_EINVAL, "gb_gauss_refit: chol must not alias chol0");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_gauss_refit: cudaSetDevice");
+    gauss_refit_kernel<<<n_win, kRefitThreads, 0, (cudaStream_t)stream>>>(n, theta, chain, chol0, ratio, inflate,
+                                                                          kappa, floor_, mu, chol);
+    ++ctx->launches;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_gauss_refit launch");
+    return GB_OK;
+}
+
 extern "C" int gb_philox4x32(gb_ctx_t* ctx, uint64_t seed, uint32_t n, uint32_t* out, void* stream) {
     if (!ctx) return GB_EINVAL;
     if (n == 0) return GB_OK;

@@ -83,56 +83,55 @@ class AnnealedPosterior:
     refitted between rounds to the states its chain visited.
 
     The paper refits paired two-dimensional kernel density estimates; here the
-    refit is a Gaussian: the mean and covariance of the visited states
-    (weighted by the steps spent in each), the covariance scaled by the ratio
-    of the next temperature to this one (the tempered target's variance
-    scales with T), widened by ``inflate``, and floored and capped at
-    ``floor`` and 1/``floor`` times the first round's in every direction.  The
-    rounds run in the library (draws, likelihood, chains); the refit's
-    8-dimensional means and covariances are formed with torch on the device
-    and factored on the host.
+    refit is a Gaussian (``gb_gauss_refit``): the mean and covariance of the
+    visited states (weighted by the steps spent in each), the sample
+    covariance widened by ``inflate`` and blended with the current proposal's
+    by the number of accepted moves against the pseudo-count ``kappa``, all
+    scaled by the ratio of the next temperature to this one (the tempered
+    target's variance scales with T), regularised in the first round's
+    whitened metric.  Every step runs on the device, so
+    the whole ladder is captured once in a CUDA graph and replayed; each
+    replay starts again from the initial proposal with new draws.  A good
+    initial proposal is the Fisher covariance times the first temperature
+    (the tempered target's width), slightly widened.
     """
 
     def __init__(self, ctx, windows, dA, dE, wA, wE, mean, cov, n, seed=1, temperatures=(15, 10, 5, 3, 2, 1),
-                 prec="mixed", inflate=1.44, floor=1e-4):
+                 prec="mixed", inflate=1.44, kappa=16.0, floor=1e-4):
+        self.ctx = ctx
+        self.kappa = float(kappa)
         self.rounds = PosteriorRounds(ctx, windows, dA, dE, wA, wE, mean, cov, n, seed=seed, prec=prec)
         self.temperatures = [float(t) for t in temperatures]
         self.inflate = float(inflate)
         self.floor = float(floor)
-        self.L0 = self.rounds.chol.cpu().numpy()
+        self.mean0 = self.rounds.mean.clone()
+        self.chol0 = self.rounds.chol.clone()
+        self.graph = None
 
-    def _refit(self, ratio):
+    def _ladder(self):
         r = self.rounds
-        th = r.theta.view(r.nw, r.n, 8)
-        idx = r.chain.long()                                              # state after every step
-        states = torch.gather(th, 1, idx[:, :, None].expand(-1, -1, 8))   # (nw, n, 8): steps weigh the states
-        mu = states.mean(1)
-        dev = states - mu[:, None, :]
-        cov = (dev.transpose(1, 2) @ dev / max(1, r.n - 1)).cpu().numpy()
-        mu = np.nan_to_num(mu.cpu().numpy())
-        # the next target is narrower by T_next/T in variance
-        cov = ratio * self.inflate * 0.5 * (cov + cov.transpose(0, 2, 1))
-        # floor and cap the eigenvalues in the first round's metric, then take
-        # the lower-triangular factor with a positive diagonal from the QR
-        # factors of a square root (no squaring of the condition number; the
-        # natural units span ~20 decades)
-        Li = np.linalg.inv(self.L0)
-        M = Li @ cov @ Li.transpose(0, 2, 1)
-        ev, V = np.linalg.eigh(0.5 * (M + M.transpose(0, 2, 1)))
-        ev = np.clip(np.nan_to_num(ev, nan=1.0), self.floor, 1.0 / self.floor)
-        S = self.L0 @ (V * np.sqrt(ev)[:, None, :])
-        _, Rq = np.linalg.qr(S.transpose(0, 2, 1))
-        L = Rq.transpose(0, 2, 1)
-        L = L * np.sign(np.diagonal(L, axis1=1, axis2=2))[:, None, :]
-        r.mean.copy_(torch.as_tensor(mu))
-        r.chol.copy_(torch.as_tensor(L))
-
-    def run(self):
-        """All temperatures; the buffers of ``self.rounds`` hold the last (T = 1) round."""
-        r = self.rounds
+        r.mean.copy_(self.mean0)
+        r.chol.copy_(self.chol0)
         for k, T in enumerate(self.temperatures):
             r.temperature.fill_(T)
-            r.run(1, graph=False)
+            r._round()
             if k + 1 < len(self.temperatures):
-                self._refit(self.temperatures[k + 1] / T)
+                self.ctx.gauss_refit(r.theta, r.chain, self.chol0, self.temperatures[k + 1] / T, self.inflate,
+                                     self.kappa, self.floor, out=(r.mean, r.chol))
+
+    def run(self, graph=False):
+        """One posterior: all temperatures from the initial proposal; the
+        buffers of ``self.rounds`` hold the last (T = 1) round.  With graph,
+        the first call runs the ladder eagerly and captures it; later calls
+        replay the capture."""
+        if not graph:
+            self._ladder()
+            return self
+        if self.graph is None:
+            self._ladder()
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph):
+                self._ladder()
+            return self
+        self.graph.replay()
         return self

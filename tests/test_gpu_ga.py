@@ -148,8 +148,8 @@ def test_posterior_rounds_graph_equals_eager_and_chains_are_valid(api):
 
 
 def test_annealed_posterior_concentrates_on_the_source(api):
-    # six temperatures from a proposal 10 Fisher widths wide and 2 widths off:
-    # the T = 1 chain sits on the source and has about the Fisher width
+    # six temperatures from the T = 15 Fisher width (x 1.2), started 2 widths
+    # off: the T = 1 chain sits on the source and has about the Fisher width
     from paper_2307_03763_gb300.posterior import AnnealedPosterior
     wl, src, dA, dE, box = _single_source_problem(snr=60.0, seed=wk.SEED_BASE + 43)
     ctx = api.Context(wl.T)
@@ -157,8 +157,8 @@ def test_annealed_posterior_concentrates_on_the_source(api):
             _cuda(wl.w_E, torch.float64))
     sig = _data.fisher_sigma(src, wl.windows[0], wl.w_A, wl.w_E, wl.T)
     start = src + 2.0 * sig * np.array([1, -1, 1, -1, 0.5, 1, -1, 1])
-    ap = AnnealedPosterior(ctx, wl.windows, *args, start[None], np.diag((10 * sig) ** 2)[None], n=10000,
-                           seed=5).run()
+    ap = AnnealedPosterior(ctx, wl.windows, *args, start[None], np.diag(15 * (1.2 * sig) ** 2)[None], n=10000,
+                           seed=5).run(graph=True)
     r = ap.rounds
     th = r.theta.view(1, r.n, 8)[0].cpu().numpy()
     states = th[r.chain[0].long().cpu().numpy()]
@@ -166,3 +166,63 @@ def test_annealed_posterior_concentrates_on_the_source(api):
     assert abs(mean[0] - src[0]) < 3 * sig[0], (mean[0], src[0], sig[0])
     assert 0.2 * sig[0] < sd[0] < 3 * sig[0], (sd[0], sig[0])
     assert int(r.accepted[0]) > 100
+
+
+def test_gauss_refit_matches_its_definition(api):
+    ctx = api.Context(wk.YEAR)
+    rng = np.random.default_rng(17)
+    nw, n = 3, 700
+    scale, floor = 1.7, 1e-3
+    th = rng.normal(size=(nw, n, 8)) * np.array([1e-9, 1e-17, 0.1, 0.2, 1e-23, 0.3, 0.1, 0.5]) \
+        + np.array([3e-3, 1e-16, 0.2, 1.0, 1e-22, 1.0, 0.5, 2.0])
+    ch = np.zeros((nw, n), np.int32)
+    for w in range(nw):
+        c = 0
+        for i in range(1, n):
+            if rng.uniform() < 0.3:
+                c = i
+            ch[w, i] = c
+    A = rng.normal(size=(nw, 8, 8)) * 0.3
+    L0 = np.linalg.cholesky(A @ A.transpose(0, 2, 1) + np.eye(8)) * np.array([1e-8, 1e-16, 1, 1, 1e-22, 1, 1, 1])[:, None]
+    L0 = np.tril(L0)
+    mu = torch.empty((nw, 8), dtype=torch.float64, device=DEV)
+    chol = torch.empty((nw, 8, 8), dtype=torch.float64, device=DEV)
+    B = rng.normal(size=(nw, 8, 8)) * 0.2
+    Lp = np.tril(np.linalg.cholesky(B @ B.transpose(0, 2, 1) + np.eye(8))) * np.array(
+        [1e-8, 1e-16, 1, 1, 1e-22, 1, 1, 1])[:, None]
+    chol.copy_(_cuda(Lp, torch.float64))
+    inflate, kappa = 1.3, 40.0
+    ctx.gauss_refit(_cuda(th.reshape(-1, 8), torch.float64), _cuda(ch, torch.int32), _cuda(L0, torch.float64),
+                    scale, inflate, kappa, floor, out=(mu, chol))
+    mu, chol = mu.cpu().numpy(), chol.cpu().numpy()
+    for w in range(nw):
+        st = th[w][ch[w]]
+        m = st.mean(0)
+        u = np.sum(ch[w][1:] == np.arange(1, n))
+        g = u / (u + kappa)
+        C = scale * (g * inflate * np.cov(st.T, ddof=1) + (1 - g) * Lp[w] @ Lp[w].T)
+        Li = np.linalg.inv(L0[w])
+        M = Li @ C @ Li.T
+        d = np.maximum(1.0, np.sqrt(np.diag(M) * floor))
+        M = M / np.outer(d, d) + floor * np.eye(8)
+        ref = L0[w] @ np.linalg.cholesky(M)
+        assert np.allclose(mu[w], m, rtol=1e-12, atol=0)
+        assert np.allclose(chol[w], ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max(axis=1, keepdims=True).max())
+        assert np.all(np.triu(chol[w], 1) == 0)
+
+
+def test_annealed_ladder_graph_replay_equals_eager(api):
+    from paper_2307_03763_gb300.posterior import AnnealedPosterior
+    wl, src, dA, dE, box = _single_source_problem(snr=40.0, seed=wk.SEED_BASE + 44)
+    ctx = api.Context(wl.T)
+    args = (_cuda(dA, torch.complex128), _cuda(dE, torch.complex128), _cuda(wl.w_A, torch.float64),
+            _cuda(wl.w_E, torch.float64))
+    sig = _data.fisher_sigma(src, wl.windows[0], wl.w_A, wl.w_E, wl.T)
+    a = AnnealedPosterior(ctx, wl.windows, *args, src[None], np.diag((10 * sig) ** 2)[None], n=4000, seed=9)
+    b = AnnealedPosterior(ctx, wl.windows, *args, src[None], np.diag((10 * sig) ** 2)[None], n=4000, seed=9)
+    a.run()
+    a.run()                  # the second ladder
+    b.run(graph=True)        # eager ladder + capture
+    b.run(graph=True)        # replay: the second ladder
+    assert torch.equal(a.rounds.chain, b.rounds.chain) and torch.equal(a.rounds.theta, b.rounds.theta)
+    assert torch.equal(a.rounds.chol, b.rounds.chol)
