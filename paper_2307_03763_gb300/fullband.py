@@ -14,10 +14,10 @@ library's kernels, batched over all windows at once:
              elites, generations replayed from a CUDA graph); a window's best
              individual counts as recovered when its SNR (Eq. 6) passes the
              threshold;
-  posterior  for the round's recovered sources, proposal covariances from the
-             observed Fisher matrix of the adjoint gradient (10x its width, as
-             in the posterior workload) and one 10,000-proposal round of
-             ``PosteriorRounds``;
+  posterior  for the round's recovered sources, Alg. 4: the six-temperature
+             ladder of ``AnnealedPosterior`` (10,000 proposals per
+             temperature), started from the observed Fisher matrix of the
+             adjoint gradient at the first temperature's width;
   subtract   the recovered templates (``gb_waveform``) leave the window data
              before the next round.
 
@@ -35,7 +35,7 @@ import torch
 from . import autograd as gbag
 from . import workloads as wk
 from .ga import GASearch
-from .posterior import PosteriorRounds
+from .posterior import AnnealedPosterior
 
 # fixed parts of every window's search box (the f0 range is the segment's)
 _LO = np.array([0.0, 0.0, -np.pi / 2, -np.pi, 1e-24, 0.0, 0.0, 0.0])
@@ -138,10 +138,11 @@ class FullBand:
             b[w] = np.concatenate([lo, hi])
         return b
 
-    def _proposal_cov(self, win, theta, width=10.0):
+    def _proposal_cov(self, win, theta, width=1.2 * math.sqrt(15.0)):
         """(n, 8, 8) covariances width^2 F^-1 from the observed Fisher matrix of
-        the adjoint gradient, in natural units with eigenvalues floored and
-        variances capped at the search box."""
+        the adjoint gradient (default: the T = 15 tempered width, widened by
+        1.2), in natural units with eigenvalues floored and variances capped
+        at the search box."""
         F = gbag.observed_fisher(self.ctx, win, self.dA, self.dE, self.wA, self.wE, theta, prec=self.prec)
         s = torch.ones_like(theta)
         s[:, 0] = 1.0 / self.T
@@ -191,11 +192,11 @@ class FullBand:
                        for w in sub]
                 mu = torch.as_tensor(best[sub], device=self.dev).contiguous()
                 cov = self._proposal_cov(win, mu)
-                pr = PosteriorRounds(self.ctx, win, self.dA, self.dE, self.wA, self.wE, mu, cov, n=n_post,
-                                     seed=self.seed + 1000 * r + i, prec=self.prec).run(1, graph=False)
-                acc = pr.accepted.cpu().numpy()
+                ap = AnnealedPosterior(self.ctx, win, self.dA, self.dE, self.wA, self.wE, mu, cov, n=n_post,
+                                       seed=self.seed + 1000 * r + i, prec=self.prec).run()
+                acc = ap.rounds.accepted.cpu().numpy()
                 post.extend(int(a) for a in acc)
-                del pr
+                del ap
             t2 = _sync(self.dev)
             t_post += t2 - t1
             # subtract the recovered templates from their windows
