@@ -51,3 +51,43 @@ def observed_fisher(lib_ctx, windows, dA, dE, wA, wE, theta, prec="fp64", rel=1e
     H = (g[:, 0] - g[:, 1]) / (2 * step[:, :, None])        # H[w, i, j] = d g_j / d theta_i
     F = -0.5 * (H + H.transpose(1, 2))
     return F
+
+
+def newton_polish(lib_ctx, windows, dA, dE, wA, wE, theta, iters=6, prec="mixed", lam0=1e-3):
+    """Local maximisation of logL from one point per window (the gradient
+    polish that stands in for Alg. 2's SLSQP step): Levenberg-Marquardt
+    steps (F + lam diag F) d = g with the adjoint gradient g and the observed
+    Fisher matrix F, solved in natural units (1/T, 1/T^2, rad, A); a step is
+    taken only where it raises logL, else lam grows tenfold.  Returns the
+    polished theta (n_win, 8) and its logL.  The likelihood, gradient and
+    Fisher matrices come from the library; the 8x8 solves run on the host."""
+    import numpy as np
+    T = lib_ctx.T_obs
+    th = theta.clone()
+    n = th.shape[0]
+    wins = [(k0, W, N, doff, w, 1) for w, (k0, W, N, doff, _, _) in enumerate(windows)]
+    logL, g = lib_ctx.loglik_grad(wins, dA, dE, wA, wE, th, prec=prec)
+    lam = np.full(n, lam0)
+    for _ in range(int(iters)):
+        F = observed_fisher(lib_ctx, windows, dA, dE, wA, wE, th, prec=prec).cpu().numpy()
+        s = np.ones((n, 8))
+        s[:, 0], s[:, 1], s[:, 4] = 1.0 / T, 1.0 / T ** 2, np.abs(th[:, 4].cpu().numpy())
+        Fs = F * s[:, :, None] * s[:, None, :]
+        gs = g.cpu().numpy() * s
+        A = Fs + lam[:, None, None] * np.eye(8)[None] * np.maximum(np.abs(np.diagonal(Fs, axis1=1, axis2=2)),
+                                                                     1e-12)[:, :, None]
+        ok = np.all(np.isfinite(A), axis=(1, 2)) & np.all(np.isfinite(gs), axis=1)
+        d = np.zeros((n, 8))
+        if ok.any():
+            d[ok] = np.linalg.solve(A[ok], gs[ok][:, :, None])[:, :, 0]
+        d = np.where(np.isfinite(d), d, 0.0)
+        step = torch.as_tensor(d * s, device=th.device)
+        trial = th + step
+        lt, gt = lib_ctx.loglik_grad(wins, dA, dE, wA, wE, trial, prec=prec)
+        better = (lt > logL) & torch.isfinite(lt)
+        th = torch.where(better[:, None], trial, th)
+        g = torch.where(better[:, None], gt, g)
+        logL = torch.where(better, lt, logL)
+        b = better.cpu().numpy()
+        lam = np.where(b, np.maximum(lam / 10.0, 1e-6), lam * 10.0)
+    return th, logL

@@ -11,9 +11,10 @@ library's kernels, batched over all windows at once:
              scattered into the contiguous band on top of the noise, then
              copied into the windows;
   search     per round, one ``GASearch`` over all windows (gradient-polished
-             elites, generations replayed from a CUDA graph); a window's best
-             individual counts as recovered when its SNR (Eq. 6) passes the
-             threshold;
+             elites, generations replayed from a CUDA graph), then
+             Levenberg-Marquardt steps from each window's best individual
+             (adjoint gradient, observed Fisher matrix); the result counts as
+             recovered when its SNR (Eq. 6) passes the threshold;
   posterior  for the round's recovered sources, Alg. 4: the six-temperature
              ladder of ``AnnealedPosterior`` (10,000 proposals per
              temperature), started from the observed Fisher matrix of the
@@ -178,11 +179,19 @@ class FullBand:
                           prec=self.prec)
             best = ga.run(generations, graph=True)
             snr = ga.best_snr()
+            del ga
+            # gradient polish of every window's best (stands in for Alg. 2's SLSQP)
+            allw = [(k0, N, N, int(self.doff[w]), 0, 0) for w, (k0, N, _, _) in enumerate(self.layout)]
+            th_b, _ = gbag.newton_polish(self.ctx, allw, self.dA, self.dE, self.wA, self.wE,
+                                         torch.as_tensor(best, device=self.dev).contiguous(), prec=self.prec)
+            _, dh, hh = self.ctx.loglik([(k0, W, N, doff, w, 1) for w, (k0, W, N, doff, _, _) in enumerate(allw)],
+                                        self.dA, self.dE, self.wA, self.wE, th_b.contiguous(), prec=self.prec)
+            best = th_b.cpu().numpy()
+            snr = (dh / torch.sqrt(torch.clamp(hh, min=1e-300))).cpu().numpy()
             t1 = _sync(self.dev)
             t_ga += t1 - t0
             evals += pop * self.n_win * generations
             rec = np.nonzero(snr > snr_min)[0]
-            del ga
             if rec.size == 0:
                 break
             # posterior rounds for this round's recoveries, in batches
