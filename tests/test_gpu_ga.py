@@ -226,3 +226,23 @@ def test_annealed_ladder_graph_replay_equals_eager(api):
     b.run(graph=True)        # replay: the second ladder
     assert torch.equal(a.rounds.chain, b.rounds.chain) and torch.equal(a.rounds.theta, b.rounds.theta)
     assert torch.equal(a.rounds.chol, b.rounds.chol)
+
+
+def test_newton_polish_reaches_the_maximum(api):
+    # noise-free data: the likelihood peaks at the source; start one Fisher
+    # width away in every parameter
+    from paper_2307_03763_gb300.autograd import newton_polish
+    wl, src, _, _, _ = _single_source_problem(snr=50.0, seed=wk.SEED_BASE + 45)
+    ctx = api.Context(wl.T)
+    hA, hE = _data.template_on_window(src, *wl.windows[0][:3], wl.T)
+    args = (_cuda(hA, torch.complex128), _cuda(hE, torch.complex128), _cuda(wl.w_A, torch.float64),
+            _cuda(wl.w_E, torch.float64))
+    sig = _data.fisher_sigma(src, wl.windows[0], wl.w_A, wl.w_E, wl.T)
+    start = src + sig * np.array([1, -1, 1, -1, 0.5, 1, -1, 1])
+    l0 = ctx.loglik(wl.windows[:1], *args, _cuda(start[None], torch.float64), prec="fp64")[0]
+    th, L = newton_polish(ctx, wl.windows, *args, _cuda(start[None], torch.float64), iters=10, prec="fp64")
+    th = th.cpu().numpy()[0]
+    # the maximum is logL = 0; f0, fdot and the sky position converge, while
+    # (A, iota, psi, phi0) move along their curved degeneracy valley
+    assert float(L[0]) > max(float(l0[0]), -0.1), (float(l0[0]), float(L[0]))
+    assert np.all(np.abs(th[:4] - src[:4]) < 0.05 * sig[:4]), (th - src) / sig
