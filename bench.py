@@ -194,7 +194,10 @@ def profiled_traffic():
     except OSError:
         return None
     region = src.split("// ---------------------------------------------------------------------------\n"
-                       "// Allocation-free variant")[0].rstrip()
+                       "// Allocation-free variant")[0]
+    # code only: // comments and blank space do not change the kernel
+    region = "\n".join(ln.split("//")[0].rstrip() for ln in region.splitlines())
+    region = "\n".join(ln for ln in region.splitlines() if ln.strip())
     sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", prof)
     nbytes = re.search(r"traffic_bytes_per_launch:\s*(\d+)", prof)
     if not sha or not nbytes or sha.group(1) != hashlib.sha256(region.encode()).hexdigest():

@@ -26,11 +26,13 @@
 // Execution: a persistent kernel whose warps take work items (a window and up
 // to 32 of its candidates) from a global queue, most expensive first.  Per
 // item the warp sets the candidates up one per lane, then evaluates them one
-// after the other: lane l computes samples n = R brev5(l) + r (R = N/32), the
-// 32-point FFT stage runs across lanes with shuffles (bit-reversed input,
-// natural output), a lane twiddle and an R-point FFT in registers finish the
-// transform, and lane l then holds bins l + 32 k1, so the window reads are
-// coalesced.  A preparation kernel forms <d|d>, the scale sigma and the float
+// after the other.  In the likelihood kernel lane l computes samples
+// n = l + 32 r (R = N/32) and the transform is R-point register DFTs around
+// skewed shared-memory transposes (see fft_inner_nat).  The waveform and
+// gradient kernels keep the earlier order n = R brev5(l) + r with a 32-point
+// stage across lanes (shuffles, bit-reversed input, natural output), a lane
+// twiddle and an R-point register FFT, after which lane l holds bins
+// l + 32 k1.  A preparation kernel forms <d|d>, the scale sigma and the float
 // copy of every window once per launch.
 #include <cmath>
 
