@@ -381,7 +381,8 @@ def run_fullband(args):
     ctx = api.Context(2 * wk.YEAR)
     clocks = ClockSampler(dev.index)
     clocks.start()
-    st = fullband.run(ctx, n_src=args.fb_sources, rounds=args.fb_rounds, pop=args.fb_pop, generations=args.fb_gens)
+    st = fullband.run(ctx, n_src=args.fb_sources, rounds=args.fb_rounds, pop=args.fb_pop, generations=args.fb_gens,
+                      phase=not args.fb_no_phase)
     line = {"metric": "total wall time, s per posterior (full-band search)", "workload": "fullband",
             "n_gpus": 1, "unit": "s", "higher_is_better": False, "data": "synthetic",
             "value": st["wall_s"], "s_per_posterior": st["s_per_posterior"],
@@ -408,6 +409,8 @@ def main():
     ap.add_argument("--fb-rounds", type=int, default=3, help="fullband: search-and-subtract rounds")
     ap.add_argument("--fb-pop", type=int, default=1024, help="fullband: GA population per window")
     ap.add_argument("--fb-gens", type=int, default=100, help="fullband: GA generations per round")
+    ap.add_argument("--fb-no-phase", action="store_true",
+                    help="fullband: rank GA individuals by the plain SNR instead of the SNR maximised over phi0")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

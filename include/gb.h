@@ -163,6 +163,19 @@ int gb_loglik(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win,
               int64_t n_bins, const double* theta, int64_t n_rows,
               double* logL, double* dh, double* hh, void* stream);
 
+/* gb_loglik plus the imaginary part of the data-template product,
+ *   dh_im = (4/T) Im sum_k w_k d_k h_k*    (device, n_rows, written; not NULL)
+ * per candidate.  The template depends on phi0 only through the common
+ * factor exp(i phi0) of Sec. III's signal model, so
+ *   <d|h(phi0 + delta)> = cos(delta) dh + sin(delta) dh_im,
+ * dh_im is <d|h> at phi0 + pi/2, and the phase-maximised <d|h> is
+ * sqrt(dh^2 + dh_im^2) at delta = atan2(dh_im, dh).  Same inputs, outputs,
+ * layout rules and errors as gb_loglik; GB_EINVAL when dh_im is NULL. */
+int gb_loglik_phase(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win,
+                    const double* dA, const double* dE, const double* wA, const double* wE,
+                    int64_t n_bins, const double* theta, int64_t n_rows,
+                    double* logL, double* dh, double* dh_im, double* hh, void* stream);
+
 /* Gradient of the log-likelihood, d logL / d theta, for every candidate, by
  * the adjoint (reverse-mode) method: the template is recomputed, never
  * stored.  Same inputs as gb_loglik; grad is n x 8 (device, written), in the
@@ -243,6 +256,11 @@ typedef struct {
  *   theta      n_win x pop x 8 population (device), pop individuals per window
  *              (pop <= 32768: the population's fitness is held in shared memory)
  *   dh, hh     <d|h>, <h|h> of every individual (device, from gb_loglik)
+ *   dh_im      imaginary parts from gb_loglik_phase (device, may be NULL):
+ *              in a window whose phi0 range spans 2 pi the fitness is then
+ *              maximised over phi0, rho = sqrt(dh^2 + dh_im^2)/sqrt(hh), and
+ *              the best individual is rotated to phi0 + atan2(dh_im, dh)
+ *              (wrapped into the box) with A_max = A sqrt(dh^2 + dh_im^2)/hh
  *   box        n_win prior boxes (device)
  *   seed       key of the Philox-4x32-10 draws
  *   generation_in, generation_out   one uint64 each (device): the draws
@@ -259,7 +277,7 @@ typedef struct {
  *              Gaussian mutation, folded back into the box
  *   best       n_win x 8 best individuals (device, written; may be NULL) */
 int gb_ga_step(gb_ctx_t* ctx, int32_t n_win, int32_t pop, const double* theta, const double* dh,
-               const double* hh, const gb_box_t* box, uint64_t seed, const uint64_t* generation_in,
+               const double* hh, const double* dh_im, const gb_box_t* box, uint64_t seed, const uint64_t* generation_in,
                uint64_t* generation_out, const gb_ga_params_t* params, const double* grad,
                double* theta_out, double* best, void* stream);
 

@@ -61,12 +61,14 @@ _SIGNATURES = {
     "gb_waveform": (ctypes.c_int, [_P, ctypes.c_int, _P, _I64, _I32, _P, _P, _P, _P]),
     "gb_loglik": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _I64, _P, _I64,
                                  _P, _P, _P, _P]),
+    "gb_loglik_phase": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _I64, _P,
+                                       _I64, _P, _P, _P, _P, _P]),
     "gb_loglik_grad": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _I64, _P,
                                       _I64, _P, _P, _P]),
     "gb_mh_independence": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, _I32, _P, _P, _P]),
     "gb_loglik_mixed_noalloc": (ctypes.c_int, [ctypes.POINTER(Obs), ctypes.POINTER(Window), _I32, _P, _P, _P, _P,
                                                _I64, _P, _I64, _P, _P, _P, _P, ctypes.c_char_p, _I32]),
-    "gb_ga_step": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, ctypes.c_uint64, _P, _P,
+    "gb_ga_step": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, _P, ctypes.c_uint64, _P, _P,
                                   ctypes.POINTER(GAParams), _P, _P, _P, _P]),
     "gb_gauss_refit": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_double, _P, _P, _P]),
@@ -215,6 +217,21 @@ class Context:
                                     nb, _ptr(theta), n, _ptr(logL), _ptr(dh), _ptr(hh), _stream(self.device)))
         return logL, dh, hh
 
+    def loglik_phase(self, windows, dA, dE, wA, wE, theta, prec="fp64", out=None):
+        """logL, <d|h>, <d|h>_im, <h|h> per candidate (see gb_loglik_phase)."""
+        arr, nw, nb, n = self._data_args(windows, dA, dE, wA, wE, theta)
+        if out is None:
+            out = tuple(torch.zeros(n, dtype=torch.float64, device=self.device) for _ in range(4))
+        logL, dh, dh_im, hh = out
+        _need(dh_im, torch.float64, self.device, "dh_im", (n,))
+        for t, name in ((logL, "logL"), (dh, "dh"), (hh, "hh")):
+            if t is not None:
+                _need(t, torch.float64, self.device, name, (n,))
+        self._check(lib().gb_loglik_phase(self._h, PRECISIONS[prec], arr, nw, _ptr(dA), _ptr(dE), _ptr(wA),
+                                          _ptr(wE), nb, _ptr(theta), n, _ptr(logL), _ptr(dh), _ptr(dh_im),
+                                          _ptr(hh), _stream(self.device)))
+        return logL, dh, dh_im, hh
+
     def loglik_grad(self, windows, dA, dE, wA, wE, theta, prec="fp64", out=None):
         """logL and d logL / d theta (n, 8) by the adjoint kernel."""
         arr, nw, nb, n = self._data_args(windows, dA, dE, wA, wE, theta)
@@ -242,12 +259,16 @@ class Context:
                 "ms_default": t.ms_default}
 
     def ga_step(self, n_win, pop, theta, dh, hh, box, seed, gen_in, gen_out, params, grad=None, out=None,
-                best=None):
-        """One generation of the genetic search (see gb_ga_step); returns (out, best)."""
+                best=None, dh_im=None):
+        """One generation of the genetic search (see gb_ga_step); returns (out, best).
+
+        With dh_im (from loglik_phase) the fitness is maximised over phi0."""
         n = n_win * pop
         _need(theta, torch.float64, self.device, "theta", (n, 8))
         _need(dh, torch.float64, self.device, "dh", (n,))
         _need(hh, torch.float64, self.device, "hh", (n,))
+        if dh_im is not None:
+            _need(dh_im, torch.float64, self.device, "dh_im", (n,))
         _need(box, torch.float64, self.device, "box", (n_win, 16))
         _need(gen_in, torch.int64, self.device, "gen_in", (1,))
         _need(gen_out, torch.int64, self.device, "gen_out", (1,))
@@ -259,7 +280,7 @@ class Context:
             best = torch.empty((n_win, 8), dtype=torch.float64, device=self.device)
         _need(out, torch.float64, self.device, "out", (n, 8))
         _need(best, torch.float64, self.device, "best", (n_win, 8))
-        self._check(lib().gb_ga_step(self._h, n_win, pop, _ptr(theta), _ptr(dh), _ptr(hh), _ptr(box),
+        self._check(lib().gb_ga_step(self._h, n_win, pop, _ptr(theta), _ptr(dh), _ptr(hh), _ptr(dh_im), _ptr(box),
                                      int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(gen_in), _ptr(gen_out),
                                      ctypes.byref(params), _ptr(grad), _ptr(out), _ptr(best),
                                      _stream(self.device)))

@@ -43,22 +43,18 @@ int tile_size(gb_ctx* ctx, int64_t total, int warps) {
     return (int)t;
 }
 
-}  // namespace
-
-extern "C" {
-
-int gb_loglik(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win, const double* dA,
-              const double* dE, const double* wA, const double* wE, int64_t n_bins, const double* theta,
-              int64_t n_rows, double* logL, double* dh, double* hh, void* stream) {
+int loglik_impl(gb_ctx_t* ctx, const char* name, int prec, const gb_window_t* win, int32_t n_win, const double* dA,
+                const double* dE, const double* wA, const double* wE, int64_t n_bins, const double* theta,
+                int64_t n_rows, double* logL, double* dh, double* dh_im, double* hh, void* stream) {
     if (!ctx) return GB_EINVAL;
-    if (prec != GB_FP64 && prec != GB_MIXED) return set_error(ctx, GB_EINVAL, "gb_loglik: unknown precision");
+    if (prec != GB_FP64 && prec != GB_MIXED) return set_error(ctx, GB_EINVAL, std::string(name) + ": unknown precision");
     int64_t total = 0;
-    int rc = check_windows(ctx, "gb_loglik", win, n_win, n_bins, n_rows, &total);
+    int rc = check_windows(ctx, name, win, n_win, n_bins, n_rows, &total);
     if (rc != GB_OK) return rc;
     if (total == 0) return GB_OK;
-    if (!dA || !dE || !wA || !wE || !theta || !logL) return set_error(ctx, GB_EINVAL, "gb_loglik: null pointer");
+    if (!dA || !dE || !wA || !wE || !theta || !logL) return set_error(ctx, GB_EINVAL, std::string(name) + ": null pointer");
     cudaError_t e = cudaSetDevice(ctx->device);
-    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_loglik: cudaSetDevice");
+    if (e != cudaSuccess) return cuda_error(ctx, e, "loglik: cudaSetDevice");
     const Plan* plan = nullptr;
     const int warps = 4;
     // mixed: work items of at most 32 candidates (one warp each), fewer when
@@ -70,8 +66,27 @@ int gb_loglik(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win, co
     rc = get_plan(ctx, prec, win, n_win, prec == GB_MIXED ? item : tile, &plan);
     if (rc != GB_OK) return rc;
     if (prec == GB_FP64)
-        return launch_loglik_fp64(ctx, *plan, dA, dE, wA, wE, theta, logL, dh, hh, (cudaStream_t)stream);
-    return launch_loglik_mixed(ctx, *plan, dA, dE, wA, wE, theta, logL, dh, hh, (cudaStream_t)stream);
+        return launch_loglik_fp64(ctx, *plan, dA, dE, wA, wE, theta, logL, dh, hh, dh_im, (cudaStream_t)stream);
+    return launch_loglik_mixed(ctx, *plan, dA, dE, wA, wE, theta, logL, dh, hh, dh_im, (cudaStream_t)stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+int gb_loglik(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win, const double* dA,
+              const double* dE, const double* wA, const double* wE, int64_t n_bins, const double* theta,
+              int64_t n_rows, double* logL, double* dh, double* hh, void* stream) {
+    return loglik_impl(ctx, "gb_loglik", prec, win, n_win, dA, dE, wA, wE, n_bins, theta, n_rows, logL, dh, nullptr,
+                       hh, stream);
+}
+
+int gb_loglik_phase(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win, const double* dA,
+                    const double* dE, const double* wA, const double* wE, int64_t n_bins, const double* theta,
+                    int64_t n_rows, double* logL, double* dh, double* dh_im, double* hh, void* stream) {
+    if (ctx && !dh_im) return set_error(ctx, GB_EINVAL, "gb_loglik_phase: dh_im is null");
+    return loglik_impl(ctx, "gb_loglik_phase", prec, win, n_win, dA, dE, wA, wE, n_bins, theta, n_rows, logL, dh,
+                       dh_im, hh, stream);
 }
 
 int gb_loglik_grad(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win, const double* dA,

@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(kWarps64 * 32) loglik64_kernel(
     const C64* __restrict__ tw_g, double T, double fstar, const C64* __restrict__ dA,
     const C64* __restrict__ dE, const double* __restrict__ wA, const double* __restrict__ wE,
     const double* __restrict__ theta, double* __restrict__ logL, double* __restrict__ dh_out,
-    double* __restrict__ hh_out, int* status, int n_max) {
+    double* __restrict__ hh_out, double* __restrict__ dhi_out, int* status, int n_max) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C64* tw = (C64*)smem_raw;                                   // kTwiddles
     double* red = (double*)(tw + kTwiddles);                    // kWarps64
@@ -312,12 +312,13 @@ __global__ void __launch_bounds__(kWarps64 * 32) loglik64_kernel(
                 logL[cidx] = nan("");
                 if (dh_out) dh_out[cidx] = nan("");
                 if (hh_out) hh_out[cidx] = nan("");
+                if (dhi_out) dhi_out[cidx] = nan("");
                 atomicOr(status, kStatusNonFinite);
             }
             continue;
         }
         template64_dispatch(c, g, tab, tw, bufA, bufE, lane);
-        double sdh = 0.0, shh = 0.0;
+        double sdh = 0.0, shh = 0.0, sdhi = 0.0;
         for (int m = lane; m < win.N; m += 32) {
             const int64_t kk = c.q - half + m - win.k0;
             if (kk >= 0 && kk < win.W) {
@@ -327,14 +328,17 @@ __global__ void __launch_bounds__(kWarps64 * 32) loglik64_kernel(
                 const double wa = wA[win.data_off + kk], we = wE[win.data_off + kk];
                 sdh += wa * (a.x * hA.x + a.y * hA.y) + we * (e.x * hE.x + e.y * hE.y);
                 shh += wa * (hA.x * hA.x + hA.y * hA.y) + we * (hE.x * hE.x + hE.y * hE.y);
+                if (dhi_out) sdhi += wa * (a.y * hA.x - a.x * hA.y) + we * (e.y * hE.x - e.x * hE.y);
             }
         }
         sdh = warp_sum(sdh) * (4.0 / T);
         shh = warp_sum(shh) * (4.0 / T);
+        if (dhi_out) sdhi = warp_sum(sdhi) * (4.0 / T);
         if (lane == 0) {
             logL[cidx] = sdh - 0.5 * shh - 0.5 * dd;
             if (dh_out) dh_out[cidx] = sdh;
             if (hh_out) hh_out[cidx] = shh;
+            if (dhi_out) dhi_out[cidx] = sdhi;
         }
         __syncwarp();
     }
@@ -398,7 +402,7 @@ static size_t smem64_loglik(int n_max) {
 
 int launch_loglik_fp64(gb_ctx* ctx, const Plan& plan, const double* dA, const double* dE,
                        const double* wA, const double* wE, const double* theta, double* logL,
-                       double* dh, double* hh, cudaStream_t s) {
+                       double* dh, double* hh, double* dh_im, cudaStream_t s) {
     if (plan.n_tiles == 0) return GB_OK;
     const size_t smem = smem64_loglik(plan.n_max);
     cudaError_t e = cudaFuncSetAttribute(loglik64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -406,7 +410,7 @@ int launch_loglik_fp64(gb_ctx* ctx, const Plan& plan, const double* dA, const do
     loglik64_kernel<<<plan.n_tiles, kWarps64 * 32, smem, s>>>(
         plan.d_win, plan.d_tiles, tabset64(ctx), (const C64*)ctx->d_tw64, ctx->obs.T_obs,
         transfer_frequency(ctx), (const C64*)dA, (const C64*)dE, wA, wE, theta, logL, dh, hh,
-        ctx->d_status, plan.n_max);
+        dh_im, ctx->d_status, plan.n_max);
     ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "loglik64 launch");

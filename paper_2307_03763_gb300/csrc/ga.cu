@@ -9,6 +9,12 @@
 //   * fitness rho = <d|h>/sqrt(<h|h>) of every individual (Eq. 6);
 //   * the best individual, with A replaced by A_max = A <d|h>/<h|h> (Eq. 7),
 //     goes to slot 0 and to `best`;
+//   * optionally the fitness is also maximised over phi0 in closed form: the
+//     template carries phi0 only as the common factor exp(i phi0), so with
+//     Z = <d|h> + i <d|h>_im (the second the same sum over Im(d conj h)),
+//     <d|h(phi0 + delta)> = Re(exp(-i delta) Z); the maximum over delta is |Z|
+//     at delta = arg Z, rho = |Z|/sqrt(<h|h>), and the best individual is
+//     rotated to phi0 + arg Z with A_max = A |Z|/<h|h>;
 //   * with a gradient at the best individual, slots 1..4 take steps of
 //     radius 0.3, 0.1, 0.03, 0.01 along the gradient direction in natural
 //     units (a line search left to the next generation's selection);
@@ -128,6 +134,7 @@ __device__ __forceinline__ float fitness(double dh, double hh) {
 __global__ void __launch_bounds__(kGaThreads) ga_step_kernel(int pop, const double* __restrict__ theta,
                                                              const double* __restrict__ dh,
                                                              const double* __restrict__ hh,
+                                                             const double* __restrict__ dh_im,
                                                              const gb_box_t* __restrict__ box, uint64_t seed,
                                                              const uint64_t* __restrict__ gen_in,
                                                              uint64_t* __restrict__ gen_out, gb_ga_params_t prm,
@@ -144,11 +151,14 @@ __global__ void __launch_bounds__(kGaThreads) ga_step_kernel(int pop, const doub
     const double* th = theta + 8 * base;
     double* to = out + 8 * base;
     const gb_box_t bx = box[w];
+    // phase maximisation needs the whole circle of phi0 inside the box
+    const bool pmax = dh_im != nullptr && bx.hi[7] - bx.lo[7] >= 2.0 * kPi * (1.0 - 1e-12);
     // fitness of every individual, and the best one (lowest index among equals)
     float bf = -INFINITY;
     int bi = 0;
     for (int i = threadIdx.x; i < pop; i += blockDim.x) {
-        const float f = fitness(dh[base + i], hh[base + i]);
+        const float f = pmax ? fitness(hypot(dh[base + i], dh_im[base + i]), hh[base + i])
+                             : fitness(dh[base + i], hh[base + i]);
         s_pop_fit[i] = f;
         if (f > bf) {
             bf = f;
@@ -172,9 +182,14 @@ __global__ void __launch_bounds__(kGaThreads) ga_step_kernel(int pop, const doub
     const int ib = s_idx[0];
     if (threadIdx.x < 8) {
         double v = th[8 * ib + threadIdx.x];
+        const double di = pmax ? dh_im[base + ib] : 0.0;
         if (threadIdx.x == 4) {   // A_max = A <d|h>/<h|h> (Eq. 7), kept inside the box
-            const double d = dh[base + ib], h = hh[base + ib];
-            if (h > 0.0 && d > 0.0) v = fmin(fmax(v * d / h, bx.lo[4]), bx.hi[4]);
+            const double d = pmax ? hypot(dh[base + ib], di) : dh[base + ib], h = hh[base + ib];
+            if (h > 0.0 && d > 0.0 && isfinite(d)) v = fmin(fmax(v * d / h, bx.lo[4]), bx.hi[4]);
+        }
+        if (threadIdx.x == 7 && pmax) {   // phi0 + arg Z, back onto the circle of the box
+            const double d = dh[base + ib];
+            if (isfinite(d) && isfinite(di) && (d != 0.0 || di != 0.0)) v = wrap(v + atan2(di, d), bx.lo[7], bx.hi[7]);
         }
         s_best[threadIdx.x] = v;
         if (best) best[8 * (size_t)w + threadIdx.x] = v;
@@ -299,7 +314,7 @@ __global__ void philox_kernel(uint64_t seed, uint32_t n, uint32_t* out) {
 using namespace gb;
 
 extern "C" int gb_ga_step(gb_ctx_t* ctx, int32_t n_win, int32_t pop, const double* theta, const double* dh,
-                          const double* hh, const gb_box_t* box, uint64_t seed, const uint64_t* generation_in,
+                          const double* hh, const double* dh_im, const gb_box_t* box, uint64_t seed, const uint64_t* generation_in,
                           uint64_t* generation_out, const gb_ga_params_t* params, const double* grad,
                           double* theta_out, double* best, void* stream) {
     if (!ctx) return GB_EINVAL;
@@ -321,7 +336,7 @@ extern "C" int gb_ga_step(gb_ctx_t* ctx, int32_t n_win, int32_t pop, const doubl
         e = cudaFuncSetAttribute(ga_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_error(ctx, e, "gb_ga_step: smem attribute");
     }
-    ga_step_kernel<<<n_win, kGaThreads, smem, (cudaStream_t)stream>>>(pop, theta, dh, hh, box, seed, generation_in,
+    ga_step_kernel<<<n_win, kGaThreads, smem, (cudaStream_t)stream>>>(pop, theta, dh, hh, dh_im, box, seed, generation_in,
                                                                       generation_out, *params, grad, ctx->obs.T_obs,
                                                                       theta_out, best);
     ++ctx->launches;

@@ -65,8 +65,13 @@ struct CandMix {
 };
 
 // per-candidate sums left by the warp for the lane-parallel epilogue
+template <bool IM>
 struct Epi {
     float dh_hi, dh_lo, hh_hi, hh_lo;
+};
+template <>
+struct Epi<true> {
+    float dh_hi, dh_lo, hh_hi, hh_lo, im_hi, im_lo;
 };
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
@@ -490,11 +495,12 @@ __device__ __forceinline__ void dft_small(float2* v) {
 // bit reversal of the low b bits
 __device__ __forceinline__ int brev_bits(int x, int b) { return b == 0 ? 0 : (int)(__brev((unsigned)x) >> (32 - b)); }
 
-// Both channels of one candidate: transform, then the window inner products.
-template <int R>
+// Both channels of one candidate: transform, then the window inner products
+// (with IM also the imaginary part of sum w d conj(h)).
+template <int R, bool IM>
 __device__ void fft_inner_nat(float2* bufA, float2* bufE, const OrbitTables32& tab, const float2* tw1024,
                               const LaneTw& ltw, int lane, int off, int W, const Win32* __restrict__ pw, float& sdh,
-                              float& cdh, float& shh, float& chh) {
+                              float& cdh, float& shh, float& chh, float& sim, float& cim) {
     constexpr int N = 32 * R, G = 32 / R;
     constexpr int LG = G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 8 ? 3 : G == 16 ? 4 : 5;
     const int g = lane / G, j = lane % G;
@@ -599,6 +605,7 @@ __device__ void fft_inner_nat(float2* bufA, float2* bufE, const OrbitTables32& t
                 // explicit products: the same rounding in every kernel that forms these sums
                 kahan_add(sdh, cdh, __fmul_rn(w, fmaf(d.x, x[q].x, d.y * x[q].y)));
                 kahan_add(shh, chh, __fmul_rn(w, fmaf(x[q].x, x[q].x, x[q].y * x[q].y)));
+                if constexpr (IM) kahan_add(sim, cim, __fmul_rn(w, fmaf(d.y, x[q].x, -(d.x * x[q].y))));
             }
         }
     }
@@ -673,18 +680,19 @@ __global__ void prep_mixed_kernel(const gb_window_t* __restrict__ wins, WinMeta*
 #endif
 
 // RMAX: largest R = N/32 this instantiation handles (8: N <= 256; 32: N = 512, 1024)
-template <int RMAX>
+template <int RMAX, bool IM>
 __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) loglik_mixed_kernel(
     const gb_window_t* __restrict__ wins, const WinMeta* __restrict__ meta, const Win32* __restrict__ prep,
     const Tile* __restrict__ items, int n_items, int* head, TabSet32 tabs, const float2* __restrict__ tw1024,
     double T, double fstar, const double* __restrict__ theta, double* __restrict__ logL,
-    double* __restrict__ dh_out, double* __restrict__ hh_out, int* status, int n_max,
+    double* __restrict__ dh_out, double* __restrict__ hh_out, double* __restrict__ dhi_out, int* status, int n_max,
     unsigned long long budget_ns) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     CandMix* cands = (CandMix*)smem_raw + warp * 32;
-    Epi* epi = (Epi*)((CandMix*)smem_raw + kWarpsMx * 32) + warp * 32;
-    float2* bufA = (float2*)((Epi*)((CandMix*)smem_raw + kWarpsMx * 32) + kWarpsMx * 32) + (size_t)warp * 2 * n_max;
+    Epi<IM>* epi = (Epi<IM>*)((CandMix*)smem_raw + kWarpsMx * 32) + warp * 32;
+    float2* bufA =
+        (float2*)((Epi<IM>*)((CandMix*)smem_raw + kWarpsMx * 32) + kWarpsMx * 32) + (size_t)warp * 2 * n_max;
     float2* bufE = bufA + n_max;
     const LaneTw ltw = lane_twiddles(lane);
 
@@ -713,33 +721,42 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) 
         __syncwarp();
         for (int i = 0; i < cnt; ++i) {
             const CandMix& c = cands[i];
-            float sdh = 0.0f, cdh = 0.0f, shh = 0.0f, chh = 0.0f;
+            float sdh = 0.0f, cdh = 0.0f, shh = 0.0f, chh = 0.0f, sim = 0.0f, cim = 0.0f;
             if (!c.bad) {
                 slow_part_dispatch<true>(c, tab, N, bufA, bufE, lane);
                 __syncwarp();
                 const long long off64 = c.q - win.k0;
                 if (off64 > -(long long)N && off64 < (long long)win.W + N) {
                     const int off = (int)off64;
+#define GB_FFT_INNER(R) \
+    fft_inner_nat<R, IM>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh, sim, cim)
                     if constexpr (RMAX <= 8) {
                         switch (N) {
-                            case 32: fft_inner_nat<1>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh); break;
-                            case 64: fft_inner_nat<2>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh); break;
-                            case 128: fft_inner_nat<4>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh); break;
-                            default: fft_inner_nat<8>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh); break;
+                            case 32: GB_FFT_INNER(1); break;
+                            case 64: GB_FFT_INNER(2); break;
+                            case 128: GB_FFT_INNER(4); break;
+                            default: GB_FFT_INNER(8); break;
                         }
                     } else {
                         if (N == 512)
-                            fft_inner_nat<16>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh);
+                            GB_FFT_INNER(16);
                         else
-                            fft_inner_nat<32>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh);
+                            GB_FFT_INNER(32);
                     }
+#undef GB_FFT_INNER
                 }
                 __syncwarp();
             }
-            float dhh, dhl, hhh, hhl;
+            float dhh, dhl, hhh, hhl, imh = 0.0f, iml = 0.0f;
             warp_sum2(sdh, cdh, dhh, dhl);
             warp_sum2(shh, chh, hhh, hhl);
-            if (lane == 0) epi[i] = Epi{dhh, dhl, hhh, hhl};
+            if constexpr (IM) warp_sum2(sim, cim, imh, iml);
+            if (lane == 0) {
+                if constexpr (IM)
+                    epi[i] = Epi<IM>{dhh, dhl, hhh, hhl, imh, iml};
+                else
+                    epi[i] = Epi<IM>{dhh, dhl, hhh, hhl};
+            }
         }
         __syncwarp();
         // lane-parallel epilogue in double, coalesced stores
@@ -750,9 +767,10 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) 
                 logL[cidx] = nan("");
                 if (dh_out) dh_out[cidx] = nan("");
                 if (hh_out) hh_out[cidx] = nan("");
+                if (IM && dhi_out) dhi_out[cidx] = nan("");
                 atomicOr(status, kStatusNonFinite);
             } else {
-                const Epi s = epi[lane];
+                const Epi<IM> s = epi[lane];
                 const double Sdh = (double)s.dh_hi + (double)s.dh_lo;
                 const double Shh = (double)s.hh_hi + (double)s.hh_lo;
                 const double dh = c.A * (2.0 * wm.sig / (double)N) * Sdh;
@@ -760,6 +778,9 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) 
                 logL[cidx] = dh - 0.5 * hh - 0.5 * wm.dd;
                 if (dh_out) dh_out[cidx] = dh;
                 if (hh_out) hh_out[cidx] = hh;
+                if constexpr (IM) {
+                    if (dhi_out) dhi_out[cidx] = c.A * (2.0 * wm.sig / (double)N) * ((double)s.im_hi + (double)s.im_lo);
+                }
             }
         }
         __syncwarp();
@@ -827,11 +848,27 @@ int resident_blocks(const void* kernel, int threads, size_t smem) {
     return n;
 }
 
+// Part 0 drains the N >= 512 queue, part 1 the N <= 256 queue.
+const void* mixed_kernel_fn(int part, bool im) {
+    if (im) return part == 0 ? (const void*)loglik_mixed_kernel<32, true> : (const void*)loglik_mixed_kernel<8, true>;
+    return part == 0 ? (const void*)loglik_mixed_kernel<32, false> : (const void*)loglik_mixed_kernel<8, false>;
+}
+
+cudaError_t launch_mixed_part(const void* kfn, int grid, size_t smem, cudaStream_t s, const gb_window_t* wins,
+                              const WinMeta* meta, const Win32* prep, const Tile* items, int n_items, int* head,
+                              TabSet32 tabs, const float2* tw1024, double T, double fstar, const double* theta,
+                              double* logL, double* dh, double* hh, double* dhi, int* status, int n_max,
+                              unsigned long long budget_ns) {
+    void* args[] = {&wins, &meta, &prep,  &items, &n_items, &head, &tabs, &tw1024, &T,      &fstar,    &theta,
+                    &logL, &dh,   &hh,    &dhi,   &status,  &n_max, &budget_ns};
+    return cudaLaunchKernel(kfn, dim3(grid), dim3(kWarpsMx * 32), args, smem, s);
+}
+
 }  // namespace
 
 int launch_loglik_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const double* dE, const double* wA,
                         const double* wE, const double* theta, double* logL, double* dh, double* hh,
-                        cudaStream_t s) {
+                        double* dh_im, cudaStream_t s) {
     if (plan.n_tiles == 0) return GB_OK;
     prep_mixed_kernel<<<plan.n_win, 256, 0, s>>>(plan.d_win, plan.d_meta, plan.d_prep, (const double2*)dA,
                                                  (const double2*)dE, wA, wE, ctx->obs.T_obs, plan.d_head);
@@ -846,8 +883,9 @@ int launch_loglik_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const d
         const int n_items = part == 0 ? plan.n_large : n_small;
         if (n_items == 0) continue;
         const int nmax = part == 0 ? 1024 : (plan.n_max < 256 ? plan.n_max : 256);
-        const size_t smem = (sizeof(CandMix) + sizeof(Epi)) * kWarpsMx * 32 + sizeof(float2) * kWarpsMx * 2 * (size_t)nmax;
-        const void* kfn = part == 0 ? (const void*)loglik_mixed_kernel<32> : (const void*)loglik_mixed_kernel<8>;
+        const size_t epi_bytes = dh_im ? sizeof(Epi<true>) : sizeof(Epi<false>);
+        const size_t smem = (sizeof(CandMix) + epi_bytes) * kWarpsMx * 32 + sizeof(float2) * kWarpsMx * 2 * (size_t)nmax;
+        const void* kfn = mixed_kernel_fn(part, dh_im != nullptr);
         e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_error(ctx, e, "loglik_mixed: smem attribute");
         int bpsm = resident_blocks(kfn, kWarpsMx * 32, smem);
@@ -857,18 +895,11 @@ int launch_loglik_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const d
         if (grid > need) grid = need;
         const Tile* items = plan.d_tiles + (part == 0 ? 0 : plan.n_large);
         int* head = plan.d_head + (part == 0 ? 1 : 0);
-        if (part == 0)
-            loglik_mixed_kernel<32><<<grid, kWarpsMx * 32, smem, s>>>(
-                plan.d_win, plan.d_meta, plan.d_prep, items, n_items, head, tabset32(ctx),
-                (const float2*)ctx->d_tw32, ctx->obs.T_obs, transfer_frequency(ctx), theta, logL, dh, hh,
-                ctx->d_status, nmax, ctx->budget_ns);
-        else
-            loglik_mixed_kernel<8><<<grid, kWarpsMx * 32, smem, s>>>(
-                plan.d_win, plan.d_meta, plan.d_prep, items, n_items, head, tabset32(ctx),
-                (const float2*)ctx->d_tw32, ctx->obs.T_obs, transfer_frequency(ctx), theta, logL, dh, hh,
-                ctx->d_status, nmax, ctx->budget_ns);
+        e = launch_mixed_part(kfn, grid, smem, s, plan.d_win, plan.d_meta, plan.d_prep, items, n_items, head,
+                              tabset32(ctx), (const float2*)ctx->d_tw32, ctx->obs.T_obs, transfer_frequency(ctx),
+                              theta, logL, dh, hh, dh_im, ctx->d_status, nmax, ctx->budget_ns);
         ++ctx->launches;
-        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_error(ctx, e, "loglik_mixed launch");
     }
     return GB_OK;
@@ -1063,22 +1094,18 @@ extern "C" int gb_loglik_mixed_noalloc(const gb_obs_t* obs, const gb_window_t* w
         const int n_items = part == 0 ? n_large : k - n_large;
         if (n_items == 0) continue;
         const int nmax = part == 0 ? 1024 : (n_max < 256 ? n_max : 256);
-        const size_t smem = (sizeof(CandMix) + sizeof(Epi)) * kWarpsMx * 32 + sizeof(float2) * kWarpsMx * 2 * (size_t)nmax;
-        const void* kfn = part == 0 ? (const void*)loglik_mixed_kernel<32> : (const void*)loglik_mixed_kernel<8>;
+        const size_t smem =
+            (sizeof(CandMix) + sizeof(Epi<false>)) * kWarpsMx * 32 + sizeof(float2) * kWarpsMx * 2 * (size_t)nmax;
+        const void* kfn = mixed_kernel_fn(part, false);
         if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) break;
         int grid = sms * resident_blocks(kfn, kWarpsMx * 32, smem);
         const int need = (n_items + kWarpsMx - 1) / kWarpsMx;
         if (grid > need) grid = need;
         const Tile* it = d_items + (part == 0 ? 0 : n_large);
         int* head = d_head + (part == 0 ? 1 : 0);
-        if (part == 0)
-            loglik_mixed_kernel<32><<<grid, kWarpsMx * 32, smem, s>>>(d_win, d_meta, d_prep, it, n_items, head, tabs,
-                                                                      (const float2*)tw32, obs->T_obs, fstar, theta,
-                                                                      logL, dh, hh, d_status, nmax, 0ULL);
-        else
-            loglik_mixed_kernel<8><<<grid, kWarpsMx * 32, smem, s>>>(d_win, d_meta, d_prep, it, n_items, head, tabs,
-                                                                     (const float2*)tw32, obs->T_obs, fstar, theta,
-                                                                     logL, dh, hh, d_status, nmax, 0ULL);
+        if (launch_mixed_part(kfn, grid, smem, s, d_win, d_meta, d_prep, it, n_items, head, tabs, (const float2*)tw32,
+                              obs->T_obs, fstar, theta, logL, dh, hh, nullptr, d_status, nmax, 0ULL) != cudaSuccess)
+            break;
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return na_fail(err, err_len, GB_ECUDA, cudaGetErrorString(e));

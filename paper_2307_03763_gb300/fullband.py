@@ -160,11 +160,11 @@ class FullBand:
         C = C / d[:, :, None] / d[:, None, :]
         return C * s[:, :, None] * s[:, None, :]
 
-    def search(self, rounds=3, pop=1024, generations=100, snr_min=10.0, n_post=10000, post_batch=4096):
+    def search(self, rounds=3, pop=1024, generations=100, snr_min=10.0, n_post=10000, post_batch=4096, phase=True):
         wins = self.windows([pop] * self.n_win)
         boxes = self.boxes()
         self.stats.update({"rounds": rounds, "pop": pop, "generations": generations, "snr_min": snr_min,
-                           "proposals_per_posterior": n_post})
+                           "proposals_per_posterior": n_post, "phase_maximised_fitness": phase})
         th0 = torch.as_tensor(np.repeat(boxes[:, None, :8], pop, 1).reshape(-1, 8)
                               + np.repeat((boxes[:, None, 8:] - boxes[:, None, :8]) * 0.5, pop, 1).reshape(-1, 8),
                               device=self.dev).contiguous()
@@ -176,7 +176,7 @@ class FullBand:
         for r in range(rounds):
             t0 = _sync(self.dev)
             ga = GASearch(self.ctx, wins, self.dA, self.dE, self.wA, self.wE, boxes, pop, seed=self.seed + 17 * r,
-                          prec=self.prec)
+                          prec=self.prec, phase=phase)
             best = ga.run(generations, graph=True)
             snr = ga.best_snr()
             del ga
@@ -256,7 +256,7 @@ class FullBand:
 
 
 def run(ctx, n_src=200000, f_lo=0.3e-3, f_hi=15e-3, T=2 * wk.YEAR, rounds=3, pop=1024, generations=100,
-        snr_min=10.0, n_post=10000, seed=wk.SEED_BASE + 5, warm=True):
+        snr_min=10.0, n_post=10000, seed=wk.SEED_BASE + 5, warm=True, phase=True):
     """Config 5 end to end; returns the statistics (wall times in seconds).
     warm: run a small instance first, so that one-time library initialisation
     (kernel modules, solver handles) is not in the times."""
@@ -269,7 +269,7 @@ def run(ctx, n_src=200000, f_lo=0.3e-3, f_hi=15e-3, T=2 * wk.YEAR, rounds=3, pop
     fb = FullBand(ctx, wk.fullband_sources(n_src, f_lo, f_hi, seed), wk.fullband_layout(f_lo, f_hi, T), T,
                   seed=seed).synthesize()
     snr_inj, owner = fb.injected_snr()
-    fb.search(rounds=rounds, pop=pop, generations=generations, snr_min=snr_min, n_post=n_post)
+    fb.search(rounds=rounds, pop=pop, generations=generations, snr_min=snr_min, n_post=n_post, phase=phase)
     st = dict(fb.stats)
     st.update(fb.match(snr_inj, owner))
     st["wall_s"] = _sync(ctx.device) - t0

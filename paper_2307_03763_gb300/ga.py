@@ -1,7 +1,8 @@
 """Genetic search of every window on the device: a thin driver over libgb.
 
 One generation is three library calls on the current stream: the batched
-likelihood of the whole population (``gb_loglik``), the gradient at each
+likelihood of the whole population (``gb_loglik``, or ``gb_loglik_phase``
+when the fitness is maximised over phi0 in closed form), the gradient at each
 window's best individual (``gb_loglik_grad``, the polish step) and
 ``gb_ga_step`` (selection, crossover, mutation, the best individual with its
 analytic amplitude, and steps along the gradient).  Two generations
@@ -22,15 +23,19 @@ class GASearch:
     windows: (k0, W, N, data_off, _, _) per window; data tensors as for
     ``Context.loglik``; boxes: (n_win, 16) prior boxes (lo[8], hi[8]);
     pop: individuals per window.  The initial population is drawn uniformly
-    in each box from ``seed`` (an input of the search).
+    in each box from ``seed`` (an input of the search).  phase=True ranks
+    individuals by their SNR maximised over phi0 (the template carries phi0
+    as a common factor exp(i phi0)) and rotates the best one to that phase.
     """
 
-    def __init__(self, ctx, windows, dA, dE, wA, wE, boxes, pop, seed=1, prec="mixed", params=None, polish=True):
+    def __init__(self, ctx, windows, dA, dE, wA, wE, boxes, pop, seed=1, prec="mixed", params=None, polish=True,
+                 phase=True):
         self.ctx = ctx
         self.nw = len(windows)
         self.pop = int(pop)
         self.prec = prec
         self.polish = polish
+        self.phase = phase
         self.seed = int(seed)
         self.windows = [(k0, W, N, doff, w * self.pop, self.pop) for w, (k0, W, N, doff, _, _) in enumerate(windows)]
         self.best_windows = [(k0, W, N, doff, w, 1) for w, (k0, W, N, doff, _, _) in enumerate(windows)]
@@ -47,6 +52,7 @@ class GASearch:
         self.logL = torch.zeros(n, dtype=torch.float64, device=dev)
         self.dh = torch.zeros(n, dtype=torch.float64, device=dev)
         self.hh = torch.zeros(n, dtype=torch.float64, device=dev)
+        self.dh_im = torch.zeros(n, dtype=torch.float64, device=dev) if phase else None
         self.best = torch.zeros((self.nw, 8), dtype=torch.float64, device=dev)
         self.grad = torch.zeros((self.nw, 8), dtype=torch.float64, device=dev)
         self.gen = torch.zeros(2, dtype=torch.int64, device=dev)
@@ -59,14 +65,18 @@ class GASearch:
         src, dst = self.cur, 1 - self.cur
         slot = self.done % 2
         ctx = self.ctx
-        ctx.loglik(self.windows, *self.data, self.th[src], prec=self.prec, out=(self.logL, self.dh, self.hh))
+        if self.phase:
+            ctx.loglik_phase(self.windows, *self.data, self.th[src], prec=self.prec,
+                             out=(self.logL, self.dh, self.dh_im, self.hh))
+        else:
+            ctx.loglik(self.windows, *self.data, self.th[src], prec=self.prec, out=(self.logL, self.dh, self.hh))
         grad = None
         if polish:
             ctx.loglik_grad(self.best_windows, *self.data, self.best, prec=self.prec, out=(None, self.grad))
             grad = self.grad
         ctx.ga_step(self.nw, self.pop, self.th[src], self.dh, self.hh, self.box, self.seed,
                     self.gen[slot:slot + 1], self.gen[1 - slot:2 - slot], self.params, grad,
-                    out=self.th[dst], best=self.best)
+                    out=self.th[dst], best=self.best, dh_im=self.dh_im)
         self.cur = dst
         self.done += 1
 

@@ -69,6 +69,46 @@ def test_ga_recovers_an_injected_source(api):
     assert rho > 0.8 * 60.0
 
 
+def test_ga_step_phase_maximised_best(api):
+    # gb_ga_step with dh_im on made-up inner products: window 0 (phi0 box of
+    # 2 pi) ranks by sqrt(dh^2 + dh_im^2)/sqrt(hh) and rotates the best to
+    # phi0 + atan2(dh_im, dh) with A_max = A |Z|/hh; window 1 (phi0 box of
+    # pi) ranks by dh/sqrt(hh) and keeps phi0
+    ctx = api.Context(wk.YEAR)
+    rng = np.random.default_rng(5)
+    pop = 300
+    lo = np.array([1e-3, 0.0, -1.5, -3.0, 1e-23, 0.0, 0.0, 0.0])
+    hi = np.array([1.001e-3, 1e-17, 1.5, 3.0, 1e-21, np.pi, np.pi, 2 * np.pi])
+    hi1 = hi.copy()
+    hi1[7] = np.pi
+    box = np.stack([np.concatenate([lo, hi]), np.concatenate([lo, hi1])])
+    th = lo + (np.stack([hi, hi1])[:, None, :] - lo) * rng.uniform(size=(2, pop, 8))
+    th[:, :, 4] = 1e-22
+    hh = rng.uniform(50.0, 200.0, size=(2, pop))
+    dh = rng.uniform(-40.0, 40.0, size=(2, pop))
+    dhi = rng.uniform(-40.0, 40.0, size=(2, pop))
+    ib0 = int(np.argmax(np.hypot(dh[0], dhi[0]) / np.sqrt(hh[0])))
+    ib1 = int(np.argmax(dh[1] / np.sqrt(hh[1])))
+    # a clear winner in each window (no float ties in the ranking)
+    dh[0, ib0], dhi[0, ib0] = -55.0, 60.0
+    dh[1, ib1] = 70.0
+    gen = torch.zeros(2, dtype=torch.int64, device=DEV)
+    out, best = ctx.ga_step(2, pop, _cuda(th.reshape(-1, 8), torch.float64), _cuda(dh.ravel(), torch.float64),
+                            _cuda(hh.ravel(), torch.float64), _cuda(box, torch.float64), 11, gen[0:1], gen[1:2],
+                            api.GAParams(3, 0, 0.9, 0.15, 0.02), dh_im=_cuda(dhi.ravel(), torch.float64))
+    best = best.cpu().numpy()
+    z0 = np.hypot(dh[0, ib0], dhi[0, ib0])
+    e0 = th[0, ib0].copy()
+    e0[4] = min(max(e0[4] * z0 / hh[0, ib0], lo[4]), hi[4])
+    e0[7] = (e0[7] + np.arctan2(dhi[0, ib0], dh[0, ib0])) % (2 * np.pi)
+    e1 = th[1, ib1].copy()
+    e1[4] = min(max(e1[4] * dh[1, ib1] / hh[1, ib1], lo[4]), hi[4])
+    assert np.allclose(best[0], e0, rtol=1e-13, atol=1e-13 * np.abs(e0)), (best[0], e0)
+    assert np.array_equal(best[1], e1), (best[1], e1)
+    o = out.cpu().numpy().reshape(2, pop, 8)
+    assert np.array_equal(o[:, 0], best)
+
+
 def test_ga_graph_replay_equals_eager(api):
     from paper_2307_03763_gb300.ga import GASearch
     wl, src, dA, dE, box = _single_source_problem(seed=wk.SEED_BASE + 41)

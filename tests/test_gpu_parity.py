@@ -175,6 +175,47 @@ def test_loglik_mixed_multiband(ctx1):
     _assert_close_fp64(gf, of)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_loglik_phase_is_dh_at_a_quarter_turn(ctx1, prec):
+    # gb_loglik_phase: dh_im(theta) = <d|h> at phi0 + pi/2 (oracle), every N
+    # of the band workload; logL, dh, hh are those of gb_loglik
+    wl = wk.band_windows(seed=wk.SEED_BASE + 21, n_win=12, cand_range=(40, 70))
+    dA, dE = _data.inject(wl)
+    args = (_cuda(dA, torch.complex128), _cuda(dE, torch.complex128), _cuda(wl.w_A, torch.float64),
+            _cuda(wl.w_E, torch.float64), _cuda(wl.theta, torch.float64))
+    lp, dp, dip, hp = (x.cpu() for x in ctx1.loglik_phase(wl.windows, *args, prec=prec))
+    lg, dg, hg = (x.cpu() for x in ctx1.loglik(wl.windows, *args, prec=prec))
+    tq = wl.theta.copy()
+    tq[:, 7] += np.pi / 2
+    _, oq, ohh = ogb.loglik(wl.windows, dA, dE, wl.w_A, wl.w_E, tq, wl.T)
+    if prec == "fp64":
+        assert torch.equal(lp, lg) and torch.equal(dp, dg) and torch.equal(hp, hg)
+        scale = max(1.0, float(ohh.abs().max()))
+        assert float((dip - oq).abs().max()) <= 1e-10 * scale
+    else:
+        assert float((lp - lg).abs().max()) <= 1e-9 * max(1.0, float(hg.abs().max()))
+        rel = (dip - oq).abs() / torch.clamp(ohh.abs(), min=1.0)
+        assert float(rel.max()) < 1e-5, float(rel.max())
+
+
+def test_loglik_phase_mixed_at_snr50(ctx):
+    # the imaginary part meets the mixed path's bar at SNR ~ 50
+    wl = wk.tiny_window(seed=wk.SEED_BASE + 11)
+    src = wl.sources[0][0].copy()
+    scale = 50.0 / _data.unit_snr(src, wl.windows[0], wl.w_A, wl.w_E, wl.T)
+    src[4] *= scale
+    wl.theta[:, 4] *= scale
+    dA, dE = _data.inject(wl, [[src]])
+    args = (_cuda(dA, torch.complex128), _cuda(dE, torch.complex128), _cuda(wl.w_A, torch.float64),
+            _cuda(wl.w_E, torch.float64), _cuda(wl.theta, torch.float64))
+    _, _, dip, _ = (x.cpu() for x in ctx.loglik_phase(wl.windows, *args, prec="mixed"))
+    tq = wl.theta.copy()
+    tq[:, 7] += np.pi / 2
+    _, oq, _ = ogb.loglik(wl.windows, dA, dE, wl.w_A, wl.w_E, tq, wl.T)
+    assert float(oq.abs().max()) > 1000.0
+    assert float((dip - oq).abs().max()) <= 1e-3
+
+
 def test_loglik_posterior_workload_sampled(ctx):
     # the 16-window, 10,000-proposal workload at full size in one launch, in
     # both precisions; outputs sampled for the oracle (first, last and 40

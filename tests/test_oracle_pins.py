@@ -292,6 +292,35 @@ def test_amplitude_max_maximises_loglik():
         assert (l3 <= l2).all()
 
 
+def test_phase_maximised_inner_product_matches_brute_force():
+    # phi0 enters as the common factor exp(i phi0), so <d|h(phi0 + delta)> =
+    # cos(delta) <d|h> + sin(delta) <d|h(phi0 + pi/2)>; its maximum over delta
+    # is the modulus, reached at delta = atan2 -- checked on a 720-point grid
+    wl, dA, dE = _one_window()
+    th = wl.theta[:4].copy()
+    win = [(wl.windows[0][0], wl.windows[0][1], wl.windows[0][2], 0, 0, 4)]
+    _, dh, _ = gb.loglik(win, dA, dE, wl.w_A, wl.w_E, th, wl.T)
+    tq = th.copy()
+    tq[:, 7] += np.pi / 2
+    _, dhq, _ = gb.loglik(win, dA, dE, wl.w_A, wl.w_E, tq, wl.T)
+    grid = np.linspace(0.0, 2 * np.pi, 720, endpoint=False)
+    vals = []
+    for d in grid:
+        t = th.copy()
+        t[:, 7] += d
+        vals.append(gb.loglik(win, dA, dE, wl.w_A, wl.w_E, t, wl.T)[1].numpy())
+    vals = np.array(vals)                                   # (grid, 4)
+    mod = np.hypot(dh.numpy(), dhq.numpy())
+    best = np.arctan2(dhq.numpy(), dh.numpy()) % (2 * np.pi)
+    assert np.allclose(vals, np.cos(grid)[:, None] * dh.numpy() + np.sin(grid)[:, None] * dhq.numpy(),
+                       rtol=0, atol=1e-10 * mod.max())
+    assert (vals.max(axis=0) <= mod * (1 + 1e-12)).all()
+    assert (vals.max(axis=0) >= mod * np.cos(np.pi / 720)).all()
+    step = grid[1] - grid[0]
+    diff = np.abs((grid[vals.argmax(axis=0)] - best + np.pi) % (2 * np.pi) - np.pi)
+    assert (diff <= step).all()
+
+
 def test_empty_window_and_disjoint_template():
     wl, dA, dE = _one_window()
     k0, W, N, doff, coff, nc = wl.windows[0]
