@@ -57,9 +57,10 @@ int loglik_impl(gb_ctx_t* ctx, const char* name, int prec, const gb_window_t* wi
     if (e != cudaSuccess) return cuda_error(ctx, e, "loglik: cudaSetDevice");
     const Plan* plan = nullptr;
     const int warps = 4;
-    // mixed: work items of at most 32 candidates (one warp each), fewer when
-    // the batch would not give every resident warp of the GPU one item
-    int item = (int)std::min<int64_t>(32, std::max<int64_t>(1, (total + sm_count(ctx) * 16 - 1) / (sm_count(ctx) * 16)));
+    // mixed: work items of at most 16 candidates (one warp each; smaller
+    // items balance the persistent warps' tails), fewer when the batch would
+    // not give every resident warp of the GPU one item
+    int item = (int)std::min<int64_t>(16, std::max<int64_t>(1, (total + sm_count(ctx) * 16 - 1) / (sm_count(ctx) * 16)));
     if (ctx->tune_item > 0) item = std::min(ctx->tune_item, 32);
     int tile = tile_size(ctx, total, warps);
     if (ctx->tune_tile64 > 0) tile = std::min(ctx->tune_tile64, 32 * warps);

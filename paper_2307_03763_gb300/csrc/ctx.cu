@@ -80,9 +80,24 @@ __global__ void build_tables_kernel(int N, double T, double L, double* tab64, fl
     G4n[N + n] = g1;
     G4n[2 * N + n] = g2;
     G4n[3 * N + n] = g3;
+    // the same as component pairs of the sample pair (n, n + 32) that lane
+    // n mod 32 takes in one step (N >= 64): float4 f of pair step h holds
+    // components 2f and 2f + 1 of both samples, (c_2f(n), c_2f(n+32),
+    // c_2f+1(n), c_2f+1(n+32)), at f N/2 + 32 h + lane
+    const int r = n / 32, l = n % 32;
+    if (N >= 64) {
+        const float comp[16] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w,
+                                g2.x, g2.y, g2.z, g2.w, g3.x, g3.y, g3.z, g3.w};
+        float* GP = tab32 + 34 * N;
+        const int odd = r & 1;
+        for (int f = 0; f < 8; ++f) {
+            float* e = GP + 4 * ((size_t)f * (N / 2) + 32 * (r / 2) + l);
+            e[odd] = comp[2 * f];
+            e[2 + odd] = comp[2 * f + 1];
+        }
+    }
     // lane twiddle exp(-2 pi i r l / N) at entry n = r*32 + l
     float* LT = tab32 + 16 * N;
-    const int r = n / 32, l = n % 32;
     double s, co;
     sincospi(2.0 * (double)(r * l) / (double)N, &s, &co);
     LT[2 * n] = (float)co;
@@ -120,7 +135,8 @@ OrbitTables64 tables64(const gb_ctx* ctx, int N) {
 
 OrbitTables32 tables32(const gb_ctx* ctx, int N) {
     const float* t = ctx->d_tab32[size_index(N)];
-    return OrbitTables32{(const float4*)t, (const float2*)(t + 16 * N), (const float4*)(t + 18 * N)};
+    return OrbitTables32{(const float4*)t, (const float2*)(t + 16 * N), (const float4*)(t + 18 * N),
+                         (const float4*)(t + 34 * N)};
 }
 
 TabSet64 tabset64(const gb_ctx* ctx) {

@@ -58,10 +58,12 @@ struct OrbitTables32 {
     const float4* g;     // [4][N], lane-permuted order (see the table kernel)
     const float2* ltw;   // [R][32]                exp(-2 pi i r l / N), lane twiddles
     const float4* gn;    // [4][N], the same values in natural sample order
+    const float4* gp;    // [8][N/2], sample pairs (n, n + 32) of each lane, component pairs
 };
 
 constexpr int kTab64PerN = 18;   // doubles per sample
-constexpr int kTab32PerN = 34;   // floats per sample: 4 float4 (permuted) + lane twiddles + 4 float4 (natural)
+// floats per sample: 4 float4 (permuted) + lane twiddles + 4 float4 (natural) + 4 float4 (pairs)
+constexpr int kTab32PerN = 50;
 
 __host__ __device__ inline int brev5(int l) {
     return ((l & 1) << 4) | ((l & 2) << 2) | (l & 4) | ((l & 8) >> 2) | ((l & 16) >> 4);

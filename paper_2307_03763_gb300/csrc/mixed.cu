@@ -24,16 +24,19 @@
 // chosen per candidate from the largest X = f/f* it can reach.
 //
 // Execution: a persistent kernel whose warps take work items (a window and up
-// to 32 of its candidates) from a global queue, most expensive first.  Per
-// item the warp sets the candidates up one per lane, then evaluates them one
-// after the other.  In the likelihood kernel lane l computes samples
-// n = l + 32 r (R = N/32) and the transform is R-point register DFTs around
-// skewed shared-memory transposes (see fft_inner_nat).  The waveform and
-// gradient kernels keep the earlier order n = R brev5(l) + r with a 32-point
-// stage across lanes (shuffles, bit-reversed input, natural output), a lane
-// twiddle and an R-point register FFT, after which lane l holds bins
-// l + 32 k1.  A preparation kernel forms <d|d>, the scale sigma and the float
-// copy of every window once per launch.
+// to 32 of its candidates, 16 by default) from a global queue, most expensive
+// first.  Per item the warp sets the candidates up one per lane, then
+// evaluates them one after the other.  In the likelihood kernel lane l
+// computes samples n = l + 32 r (R = N/32), for N >= 64 two at a time (n and
+// n + 32) with packed two-wide FP32 instructions (sm_100 and later: one FFMA2
+// does the FMAs of both samples), reading the orbit tables in a layout that
+// gives both samples' values as one register pair; the transform is R-point
+// register DFTs around skewed shared-memory transposes (see fft_inner_nat).
+// The waveform and gradient kernels keep the earlier order n = R brev5(l) + r
+// with a 32-point stage across lanes (shuffles, bit-reversed input, natural
+// output), a lane twiddle and an R-point register FFT, after which lane l
+// holds bins l + 32 k1.  A preparation kernel forms <d|d>, the scale sigma
+// and the float copy of every window once per launch.
 #include <cmath>
 
 #include "gb_internal.cuh"
@@ -106,7 +109,8 @@ __constant__ float kInvFact[24] = {
     1.5619206968586225e-16f, 8.2206352466243295e-18f, 4.1103176233121648e-19f, 1.9572941063391263e-20f,
     8.8967913924505741e-22f, 3.8681701706306835e-23f};
 
-__device__ void setup_mixed(const double* th, double T, double fstar, CandMix& c) {
+// ifs = 1/f*, formed once per thread by the caller
+__device__ void setup_mixed(const double* th, double T, double ifs, CandMix& c) {
     const double f0 = th[0], fd = th[1], beta = th[2], lam = th[3];
     const double A = th[4], iota = th[5], psi = th[6], phi0 = th[7];
     bool bad = false;
@@ -154,7 +158,6 @@ __device__ void setup_mixed(const double* th, double T, double fstar, CandMix& c
     c.f0 = (float)f0;
     c.fdT = (float)(fd * T);
     c.fdh = (float)(0.5 * fd);
-    const double ifs = 1.0 / fstar;   // the float results do not see the reciprocal's rounding
     c.a0 = (float)(0.5 * f0 * ifs);
     c.a1 = (float)(0.5 * fd * T * ifs);
     float sD, cD;
@@ -334,9 +337,227 @@ __device__ void slow_part_mixed(const CandMix& c, const OrbitTables32& tab, int 
     }
 }
 
+// ---------------------------------------------------------------------------
+// The slow part two samples at a time.  Lane l takes the samples n = l + 32 r
+// and n + 32 of one step together; every float operation acts on the pair
+// (x = sample n, y = sample n + 32) as one packed FP32 instruction, and a
+// complex value of the pair is kept as two pairs (real parts, imaginary
+// parts).  The arithmetic is that of slow_part_mixed, operation by operation.
+// ---------------------------------------------------------------------------
+using f2 = float2;
+__device__ __forceinline__ f2 bc(float x) { return make_float2(x, x); }
+__device__ __forceinline__ f2 padd(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 pmul(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 pfma(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 pneg(f2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ f2 psub(f2 a, f2 b) { return __fadd2_rn(a, pneg(b)); }
+__device__ __forceinline__ f2 print(f2 a) { return make_float2(rintf(a.x), rintf(a.y)); }
+
+__device__ __forceinline__ void ptwo_sum(f2 a, f2 b, f2& s, f2& e) {
+    s = padd(a, b);
+    const f2 bb = psub(s, a);
+    e = padd(psub(a, psub(s, bb)), psub(b, bb));
+}
+
+struct cpair {   // two complex numbers: re = (re_x, re_y), im = (im_x, im_y)
+    f2 re, im;
+};
+__device__ __forceinline__ cpair pcmul(cpair a, cpair b) {
+    return cpair{pfma(a.re, b.re, pneg(pmul(a.im, b.im))), pfma(a.re, b.im, pmul(a.im, b.re))};
+}
+__device__ __forceinline__ cpair pcadd(cpair a, cpair b) { return cpair{padd(a.re, b.re), padd(a.im, b.im)}; }
+__device__ __forceinline__ cpair pcsub(cpair a, cpair b) { return cpair{psub(a.re, b.re), psub(a.im, b.im)}; }
+
+// coefficient pairs (1/(2j+1)!, 1/(2j+2)!) of the link series, each value
+// duplicated for the two samples
+__constant__ float4 kLinkPair[11] = {
+    {1.0f, 1.0f, 0.5f, 0.5f},
+    {1.6666666666666666e-01f, 1.6666666666666666e-01f, 4.1666666666666664e-02f, 4.1666666666666664e-02f},
+    {8.3333333333333332e-03f, 8.3333333333333332e-03f, 1.3888888888888889e-03f, 1.3888888888888889e-03f},
+    {1.9841269841269841e-04f, 1.9841269841269841e-04f, 2.4801587301587302e-05f, 2.4801587301587302e-05f},
+    {2.7557319223985893e-06f, 2.7557319223985893e-06f, 2.7557319223985888e-07f, 2.7557319223985888e-07f},
+    {2.5052108385441720e-08f, 2.5052108385441720e-08f, 2.0876756987868100e-09f, 2.0876756987868100e-09f},
+    {1.6059043836821613e-10f, 1.6059043836821613e-10f, 1.1470745597729725e-11f, 1.1470745597729725e-11f},
+    {7.6471637318198164e-13f, 7.6471637318198164e-13f, 4.7794773323873853e-14f, 4.7794773323873853e-14f},
+    {2.8114572543455206e-15f, 2.8114572543455206e-15f, 1.5619206968586225e-16f, 1.5619206968586225e-16f},
+    {8.2206352466243295e-18f, 8.2206352466243295e-18f, 4.1103176233121648e-19f, 4.1103176233121648e-19f},
+    {1.9572941063391263e-20f, 1.9572941063391263e-20f, 8.8967913924505741e-22f, 8.8967913924505741e-22f}};
+
+// link_transfer<J> of a pair
+template <int J>
+__device__ __forceinline__ cpair plink_transfer(f2 X) {
+    if constexpr (J == 0) {
+        const float2 a = link_transfer<0>(X.x), b = link_transfer<0>(X.y);
+        return cpair{make_float2(a.x, b.x), make_float2(a.y, b.y)};
+    } else {
+        const f2 y = pmul(bc(-4.0f), pmul(X, X));
+        const float4 cJ = kLinkPair[J];
+        f2 re = make_float2(cJ.x, cJ.y), im = make_float2(cJ.z, cJ.w);
+#pragma unroll
+        for (int j = J - 1; j >= 0; --j) {
+            const float4 cj = kLinkPair[j];
+            re = pfma(re, y, make_float2(cj.x, cj.y));
+            im = pfma(im, y, make_float2(cj.z, cj.w));
+        }
+        return cpair{re, pmul(pmul(bc(-2.0f), X), im)};
+    }
+}
+
+// cis_rx<J> of a pair
+template <int J>
+__device__ __forceinline__ cpair pcis_rx(f2 x) {
+    if constexpr (J == 0 || J >= 10) {
+        const float2 a = cis_rx<J>(x.x), b = cis_rx<J>(x.y);
+        return cpair{make_float2(a.x, b.x), make_float2(a.y, b.y)};
+    } else {
+        const f2 t = pmul(bc(6.2831853071795865f), x);
+        const f2 t2 = pmul(t, t);
+        f2 s, co;
+        if constexpr (J <= 4) {
+            s = pfma(t2, bc(-1.9841269841269841e-04f), bc(8.3333333333333332e-03f));
+            s = pfma(s, t2, bc(-1.6666666666666666e-01f));
+            s = pfma(pmul(s, t2), t, t);
+            co = pfma(t2, bc(-1.3888888888888889e-03f), bc(4.1666666666666664e-02f));
+            co = pfma(co, t2, bc(-0.5f));
+            co = pfma(co, t2, bc(1.0f));
+        } else {
+            s = pfma(t2, bc(2.7557319223985893e-06f), bc(-1.9841269841269841e-04f));
+            s = pfma(s, t2, bc(8.3333333333333332e-03f));
+            s = pfma(s, t2, bc(-1.6666666666666666e-01f));
+            s = pfma(pmul(s, t2), t, t);
+            co = pfma(t2, bc(-2.7557319223985888e-07f), bc(2.4801587301587302e-05f));
+            co = pfma(co, t2, bc(-1.3888888888888889e-03f));
+            co = pfma(co, t2, bc(4.1666666666666664e-02f));
+            co = pfma(co, t2, bc(-0.5f));
+            co = pfma(co, t2, bc(1.0f));
+        }
+        return cpair{co, s};
+    }
+}
+
+// natural sample order (the likelihood kernel's transform), N >= 64
+template <int J>
+__device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N, float2* bufA, float2* bufE,
+                               int lane) {
+    const int R = N >> 5, H = N >> 1;
+    const float invN = 1.0f / (float)N;
+    const f2 r2 = bc(0.70710678118654752f), r6 = bc(0.40824829046386302f);
+    for (int r = 0; r < R; r += 2) {
+        const int m = (r >> 1) * 32 + lane;
+        float4 t[8];
+#pragma unroll
+        for (int f = 0; f < 8; ++f) t[f] = __ldg(tab.gp + f * H + m);
+        const f2 rho0x = make_float2(t[0].x, t[0].y), rho0y = make_float2(t[0].z, t[0].w);
+        const f2 rho0z = make_float2(t[1].x, t[1].y), rho1x = make_float2(t[1].z, t[1].w);
+        const f2 rho1y = make_float2(t[2].x, t[2].y), rho1z = make_float2(t[2].z, t[2].w);
+        const f2 n0x = make_float2(t[3].x, t[3].y), n0y = make_float2(t[3].z, t[3].w);
+        const f2 n0z = make_float2(t[4].x, t[4].y), n1x = make_float2(t[4].z, t[4].w);
+        const f2 n1y = make_float2(t[5].x, t[5].y), n1z = make_float2(t[5].z, t[5].w);
+        const f2 cah = make_float2(t[6].x, t[6].y), cal = make_float2(t[6].z, t[6].w);
+        const f2 sah = make_float2(t[7].x, t[7].y), sal = make_float2(t[7].z, t[7].w);
+        const int n = lane + 32 * r;
+        const f2 u = pmul(make_float2((float)n, (float)(n + 32)), bc(invN));
+        const f2 uu = pmul(u, u);
+        // double-word products, reduced modulo one
+        f2 p1 = pmul(bc(c.c1h), u);
+        const f2 e1 = pfma(bc(c.c1l), u, pfma(bc(c.c1h), u, pneg(p1)));
+        f2 p2 = pmul(bc(c.c2h), uu);
+        const f2 e2 = pfma(bc(c.c2l), uu, pfma(bc(c.c2h), uu, pneg(p2)));
+        f2 p3 = pmul(bc(c.Fch), cah);
+        const f2 e3 = padd(pfma(bc(c.Fch), cah, pneg(p3)), pfma(bc(c.Fch), cal, pmul(bc(c.Fcl), cah)));
+        f2 p4 = pmul(bc(c.Fsh), sah);
+        const f2 e4 = padd(pfma(bc(c.Fsh), sah, pneg(p4)), pfma(bc(c.Fsh), sal, pmul(bc(c.Fsl), sah)));
+        p1 = psub(p1, print(p1));
+        p2 = psub(p2, print(p2));
+        p3 = psub(p3, print(p3));
+        p4 = psub(p4, print(p4));
+        f2 s, e, ea, eb, ec;
+        ptwo_sum(bc(c.c0h), p1, s, ea);
+        ptwo_sum(s, p2, s, eb);
+        ptwo_sum(s, pneg(p3), s, ec);
+        ptwo_sum(s, pneg(p4), s, e);
+        s = psub(s, print(s));
+        const f2 K = pfma(bc(c.Kc), cah, pmul(bc(c.Ks), sah));
+        const f2 lo = padd(psub(psub(padd(padd(bc(c.c0l), e1), e2), e3), e4), padd(padd(padd(ea, eb), ec), e));
+        const f2 small = pfma(pneg(pmul(bc(c.fdT), u)), K, lo);
+        f2 Pc, Pl;
+        ptwo_sum(s, small, Pc, Pl);
+        Pc = psub(Pc, print(Pc));
+        float sx, cx, sy, cy;
+        sincospif(2.0f * Pc.x, &sx, &cx);
+        sincospif(2.0f * Pc.y, &sy, &cy);
+        const f2 sP = make_float2(sx, sy), cP = make_float2(cx, cy);
+        const f2 tl = pmul(bc(6.2831853071795865f), Pl);
+        const cpair ePc{pfma(pneg(tl), sP, cP), pfma(tl, cP, sP)};
+        const f2 fr = pfma(bc(c.fdT), u, bc(c.f0));
+        f2 krho[3];
+        krho[0] = pfma(bc(c.k0), rho0x, pfma(bc(c.k1), rho0y, pmul(bc(c.k2), rho0z)));
+        krho[1] = pfma(bc(c.k0), rho1x, pfma(bc(c.k1), rho1y, pmul(bc(c.k2), rho1z)));
+        krho[2] = psub(pneg(krho[0]), krho[1]);
+        cpair rx[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const f2 kap = padd(K, krho[j]);
+            const f2 dP = pfma(pneg(fr), krho[j], pmul(pmul(bc(c.fdh), kap), kap));
+            rx[j] = pcis_rx<J>(dP);
+        }
+        const f2 a = pfma(bc(c.a1), u, bc(c.a0));
+        f2 kn_[3], nu_[3], nv_[3];
+        kn_[0] = pfma(bc(c.k0), n0x, pfma(bc(c.k1), n0y, pmul(bc(c.k2), n0z)));
+        nu_[0] = pfma(bc(c.u0), n0x, pfma(bc(c.u1), n0y, pmul(bc(c.u2), n0z)));
+        nv_[0] = pfma(bc(c.v0), n0x, pfma(bc(c.v1), n0y, pmul(bc(c.v2), n0z)));
+        kn_[1] = pfma(bc(c.k0), n1x, pfma(bc(c.k1), n1y, pmul(bc(c.k2), n1z)));
+        nu_[1] = pfma(bc(c.u0), n1x, pfma(bc(c.u1), n1y, pmul(bc(c.u2), n1z)));
+        nv_[1] = pfma(bc(c.v0), n1x, pfma(bc(c.v1), n1y, pmul(bc(c.v2), n1z)));
+        kn_[2] = psub(pneg(kn_[0]), kn_[1]);
+        nu_[2] = psub(pneg(nu_[0]), nu_[1]);
+        nv_[2] = psub(pneg(nv_[0]), nv_[1]);
+        cpair zp[3], zm[3];
+#pragma unroll
+        for (int arm = 0; arm < 3; ++arm) {
+            const f2 kn = kn_[arm], nu = nu_[arm], nv = nv_[arm];
+            const f2 Fp = pmul(psub(nu, nv), padd(nu, nv));
+            const f2 Fx = pmul(pmul(bc(2.0f), nu), nv);
+            const cpair G{pfma(bc(c.gpr), Fp, pmul(bc(c.gxr), Fx)), pfma(bc(c.gpi), Fp, pmul(bc(c.gxi), Fx))};
+            const int rp = arm == 2 ? 0 : arm + 1;
+            const int rm = arm;
+            zp[arm] = pcmul(pcmul(plink_transfer<J>(pmul(a, psub(bc(1.0f), kn))), G), rx[rp]);
+            zm[arm] = pcmul(pcmul(plink_transfer<J>(pmul(a, padd(bc(1.0f), kn))), G), rx[rm]);
+        }
+        const f2 du = pmul(bc(c.eps), u);
+        const cpair Dc{pfma(pmul(bc(-0.5f), du), du, bc(1.0f)), pneg(du)};
+        const cpair D = pcmul(cpair{bc(c.D0r), bc(c.D0i)}, Dc);
+        const cpair Xp = pcadd(pcsub(zm[0], zp[2]), pcmul(D, pcsub(zp[0], zm[2])));
+        const cpair Yp = pcadd(pcsub(zm[1], zp[0]), pcmul(D, pcsub(zp[1], zm[0])));
+        const cpair Zp = pcadd(pcsub(zm[2], zp[1]), pcmul(D, pcsub(zp[2], zm[1])));
+        const f2 sa2 = pmul(pmul(bc(-2.0f), a), D.im);
+        const cpair F = pcmul(cpair{pmul(sa2, D.re), pmul(sa2, D.im)}, ePc);
+        const cpair Ap{pmul(psub(Zp.re, Xp.re), r2), pmul(psub(Zp.im, Xp.im), r2)};
+        const cpair Ep{pmul(padd(psub(Xp.re, pmul(bc(2.0f), Yp.re)), Zp.re), r6),
+                       pmul(padd(psub(Xp.im, pmul(bc(2.0f), Yp.im)), Zp.im), r6)};
+        const cpair oA = pcmul(F, Ap), oE = pcmul(F, Ep);
+        const int p = r * 32 + lane;
+        bufA[p] = make_float2(oA.re.x, oA.im.x);
+        bufA[p + 32] = make_float2(oA.re.y, oA.im.y);
+        bufE[p] = make_float2(oE.re.x, oE.im.x);
+        bufE[p + 32] = make_float2(oE.re.y, oE.im.y);
+    }
+}
+
 template <bool NAT>
 __device__ void slow_part_dispatch(const CandMix& c, const OrbitTables32& tab, int N, float2* bufA, float2* bufE,
                                    int lane) {
+    if constexpr (NAT) {
+        if (N >= 64) {
+            switch (c.J) {
+                case 4: slow_part_pair<4>(c, tab, N, bufA, bufE, lane); break;
+                case 7: slow_part_pair<7>(c, tab, N, bufA, bufE, lane); break;
+                case 10: slow_part_pair<10>(c, tab, N, bufA, bufE, lane); break;
+                default: slow_part_pair<0>(c, tab, N, bufA, bufE, lane); break;
+            }
+            return;
+        }
+    }
     switch (c.J) {
         case 4: slow_part_mixed<4, NAT>(c, tab, N, bufA, bufE, lane); break;
         case 7: slow_part_mixed<7, NAT>(c, tab, N, bufA, bufE, lane); break;
@@ -695,6 +916,7 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) 
         (float2*)((Epi<IM>*)((CandMix*)smem_raw + kWarpsMx * 32) + kWarpsMx * 32) + (size_t)warp * 2 * n_max;
     float2* bufE = bufA + n_max;
     const LaneTw ltw = lane_twiddles(lane);
+    const double ifs = 1.0 / fstar;   // the float results do not see the reciprocal's rounding
 
     const unsigned long long t0 = global_ns();
     for (;;) {
@@ -717,7 +939,7 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) 
         const int N = win.N;
         const OrbitTables32 tab = tabs.t[__ffs(N) - 6];
         const int cnt = (int)(t.c_end - t.c_begin);
-        if (lane < cnt) setup_mixed(theta + 8 * (t.c_begin + lane), T, fstar, cands[lane]);
+        if (lane < cnt) setup_mixed(theta + 8 * (t.c_begin + lane), T, ifs, cands[lane]);
         __syncwarp();
         for (int i = 0; i < cnt; ++i) {
             const CandMix& c = cands[i];
@@ -800,7 +1022,7 @@ __global__ void __launch_bounds__(kWarpsMx * 32) waveform_mixed_kernel(
     const int64_t c_lo = ((int64_t)blockIdx.x * kWarpsMx + warp) * group;
     const int64_t c_hi = min(B, c_lo + group);
     if (c_lo >= c_hi) return;
-    if (c_lo + lane < c_hi) setup_mixed(theta + 8 * (c_lo + lane), T, fstar, cands[lane]);
+    if (c_lo + lane < c_hi) setup_mixed(theta + 8 * (c_lo + lane), T, 1.0 / fstar, cands[lane]);
     __syncwarp();
     const int R = N / 32;
     const double scale = T / (2.0 * (double)N);
@@ -1041,7 +1263,7 @@ extern "C" int gb_loglik_mixed_noalloc(const gb_obs_t* obs, const gb_window_t* w
         t64[i] = (double*)(b + o64);
         t32[i] = (float*)(b + o32);
         tabs.t[i] = OrbitTables32{(const float4*)t32[i], (const float2*)(t32[i] + 16 * N),
-                                  (const float4*)(t32[i] + 18 * N)};
+                                  (const float4*)(t32[i] + 18 * N), (const float4*)(t32[i] + 34 * N)};
         o64 += sizeof(double) * kTab64PerN * N;
         o32 += sizeof(float) * kTab32PerN * N;
     }
@@ -1177,7 +1399,7 @@ struct CandGx {
 };
 
 __device__ void setup_grad_mixed(const double* th, double T, double fstar, CandGx& g) {
-    setup_mixed(th, T, fstar, g.m);
+    setup_mixed(th, T, 1.0 / fstar, g.m);
     const float beta = (float)th[2], lam = (float)th[3], iota = (float)th[5], psi = (float)th[6];
     float sb, cb, sl, cl, si, ci, s2, c2;
     sincosf(beta, &sb, &cb);
