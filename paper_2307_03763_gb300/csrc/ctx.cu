@@ -102,6 +102,7 @@ __global__ void build_tables_kernel(int N, double T, double L, double* tab64, fl
     sincospi(2.0 * (double)(r * l) / (double)N, &s, &co);
     LT[2 * n] = (float)co;
     LT[2 * n + 1] = (float)(-s);
+    ((float4*)(tab32 + 50 * N))[n] = make_float4((float)co, (float)co, (float)(-s), (float)(-s));
 }
 
 __global__ void build_twiddles_kernel(double* tw64, float* tw32) {
@@ -136,7 +137,7 @@ OrbitTables64 tables64(const gb_ctx* ctx, int N) {
 OrbitTables32 tables32(const gb_ctx* ctx, int N) {
     const float* t = ctx->d_tab32[size_index(N)];
     return OrbitTables32{(const float4*)t, (const float2*)(t + 16 * N), (const float4*)(t + 18 * N),
-                         (const float4*)(t + 34 * N)};
+                         (const float4*)(t + 34 * N), (const float4*)(t + 50 * N)};
 }
 
 TabSet64 tabset64(const gb_ctx* ctx) {

@@ -59,11 +59,13 @@ struct OrbitTables32 {
     const float2* ltw;   // [R][32]                exp(-2 pi i r l / N), lane twiddles
     const float4* gn;    // [4][N], the same values in natural sample order
     const float4* gp;    // [8][N/2], sample pairs (n, n + 32) of each lane, component pairs
+    const float4* ltw4;  // [R][32]                the lane twiddles as (re, re, im, im)
 };
 
 constexpr int kTab64PerN = 18;   // doubles per sample
 // floats per sample: 4 float4 (permuted) + lane twiddles + 4 float4 (natural) + 4 float4 (pairs)
-constexpr int kTab32PerN = 50;
+// + duplicated lane twiddles
+constexpr int kTab32PerN = 54;
 
 __host__ __device__ inline int brev5(int l) {
     return ((l & 1) << 4) | ((l & 2) << 2) | (l & 4) | ((l & 8) >> 2) | ((l & 16) >> 4);
@@ -96,8 +98,9 @@ struct WinMeta {
 
 // Float copy of one window bin: data times sigma, weights over sigma^2.
 struct Win32 {
-    float2 dA, dE;
-    float wA, wE;
+    float2 dre;   // (Re dA, Re dE)
+    float2 dim;   // (Im dA, Im dE)
+    float2 w;     // (wA, wE)
 };
 
 struct Plan {

@@ -31,7 +31,8 @@
 // n + 32) with packed two-wide FP32 instructions (sm_100 and later: one FFMA2
 // does the FMAs of both samples), reading the orbit tables in a layout that
 // gives both samples' values as one register pair; the transform is R-point
-// register DFTs around skewed shared-memory transposes (see fft_inner_nat).
+// register DFTs around skewed shared-memory transposes, both channels packed
+// together (see fft_inner_ch).
 // The waveform and gradient kernels keep the earlier order n = R brev5(l) + r
 // with a 32-point stage across lanes (shuffles, bit-reversed input, natural
 // output), a lane twiddle and an R-point register FFT, after which lane l
@@ -332,8 +333,13 @@ __device__ void slow_part_mixed(const CandMix& c, const OrbitTables32& tab, int 
         const float2 F = cmulf(make_float2(sa2 * D.x, sa2 * D.y), ePc);
         const float2 Ap = make_float2((Zp.x - Xp.x) * r2, (Zp.y - Xp.y) * r2);
         const float2 Ep = make_float2((Xp.x - 2.0f * Yp.x + Zp.x) * r6, (Xp.y - 2.0f * Yp.y + Zp.y) * r6);
-        bufA[p] = cmulf(F, Ap);
-        bufE[p] = cmulf(F, Ep);
+        const float2 oA = cmulf(F, Ap), oE = cmulf(F, Ep);
+        if constexpr (NAT) {   // channel-pair elements for the likelihood transform
+            ((float4*)bufA)[p] = make_float4(oA.x, oE.x, oA.y, oE.y);
+        } else {
+            bufA[p] = oA;
+            bufE[p] = oE;
+        }
     }
 }
 
@@ -536,11 +542,11 @@ __device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N
         const cpair Ep{pmul(padd(psub(Xp.re, pmul(bc(2.0f), Yp.re)), Zp.re), r6),
                        pmul(padd(psub(Xp.im, pmul(bc(2.0f), Yp.im)), Zp.im), r6)};
         const cpair oA = pcmul(F, Ap), oE = pcmul(F, Ep);
+        // channel-pair elements (A re, E re, A im, E im) for the transform
         const int p = r * 32 + lane;
-        bufA[p] = make_float2(oA.re.x, oA.im.x);
-        bufA[p + 32] = make_float2(oA.re.y, oA.im.y);
-        bufE[p] = make_float2(oE.re.x, oE.im.x);
-        bufE[p + 32] = make_float2(oE.re.y, oE.im.y);
+        float4* buf = (float4*)bufA;
+        buf[p] = make_float4(oA.re.x, oE.re.x, oA.im.x, oE.im.x);
+        buf[p + 32] = make_float4(oA.re.y, oE.re.y, oA.im.y, oE.im.y);
     }
 }
 
@@ -688,148 +694,239 @@ __device__ __forceinline__ int t2_addr4(int g, int ka, int u, int v) {
     return 64 * h + 16 * ka + ((8 * gp + 4 * u + v + ka) & 15);
 }
 
-// element (group g, lane j of the group, ka) of the second transpose (R >= 8)
+// element (group g, lane j of the group, ka) of the second transpose (R >= 8),
+// in 16-byte elements: row g G + j of R elements, the low three index bits
+// rotated so that every quarter-warp access touches 8 distinct 16-byte bank
+// groups (rotation constants found by checking all accesses of each R)
 template <int R>
 __device__ __forceinline__ int t2_addr(int g, int j, int ka) {
-    constexpr int G = 32 / R, GPH = 16 / G;   // groups per half-warp
-    const int h = g / GPH, gp = g - h * GPH;
-    return 16 * R * h + 16 * ka + ((gp + GPH * j + (16 / R) * ka) & 15);
-}
-
-// G-point DFT of v[0..G) in registers, natural order in and out (G = 1, 2, 4)
-template <int G>
-__device__ __forceinline__ void dft_small(float2* v) {
-    if constexpr (G == 2) {
-        const float2 a = v[0], b = v[1];
-        v[0] = caddf(a, b);
-        v[1] = csubf(a, b);
-    } else if constexpr (G == 4) {
-        const float2 s02 = caddf(v[0], v[2]), d02 = csubf(v[0], v[2]);
-        const float2 s13 = caddf(v[1], v[3]), d13 = csubf(v[1], v[3]);
-        v[0] = caddf(s02, s13);
-        v[2] = csubf(s02, s13);
-        v[1] = make_float2(d02.x + d13.y, d02.y - d13.x);   // d02 - i d13
-        v[3] = make_float2(d02.x - d13.y, d02.y + d13.x);   // d02 + i d13
-    }
+    constexpr int G = 32 / R;
+    constexpr int a = R == 8 ? 2 : R == 16 ? 1 : 0, b = R == 16 ? 2 : 1, c = R == 16 ? 1 : 0;
+    return (g * G + j) * R + (ka & ~7) + ((ka + a * j + b * g + c * (ka >> 3)) & 7);
 }
 
 // bit reversal of the low b bits
 __device__ __forceinline__ int brev_bits(int x, int b) { return b == 0 ? 0 : (int)(__brev((unsigned)x) >> (32 - b)); }
 
-// Both channels of one candidate: transform, then the window inner products
-// (with IM also the imaginary part of sum w d conj(h)).
+// The transform works on both channels at once: a value is a cpair with
+// channel A in .x and channel E in .y of its real and imaginary pairs, kept in
+// shared memory as one 16-byte element (A re, E re, A im, E im).
+__device__ __forceinline__ cpair ld4(const float4* p) {
+    const float4 v = *p;
+    return cpair{make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ cpair ldg4(const float4* p) {
+    const float4 v = __ldg(p);
+    return cpair{make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ void st4(float4* p, cpair v) { *p = make_float4(v.re.x, v.re.y, v.im.x, v.im.y); }
+__device__ __forceinline__ cpair pmul_mi(cpair v) { return cpair{v.im, pneg(v.re)}; }   // times -i
+
+// exp(-2 pi i m / 32), m < 16, each part duplicated for the two channels
+__constant__ float4 kW32d[16] = {
+    {1.000000000e+00f, 1.000000000e+00f, 0.0f, 0.0f},
+    {9.807852804e-01f, 9.807852804e-01f, -1.950903220e-01f, -1.950903220e-01f},
+    {9.238795325e-01f, 9.238795325e-01f, -3.826834324e-01f, -3.826834324e-01f},
+    {8.314696123e-01f, 8.314696123e-01f, -5.555702330e-01f, -5.555702330e-01f},
+    {7.071067812e-01f, 7.071067812e-01f, -7.071067812e-01f, -7.071067812e-01f},
+    {5.555702330e-01f, 5.555702330e-01f, -8.314696123e-01f, -8.314696123e-01f},
+    {3.826834324e-01f, 3.826834324e-01f, -9.238795325e-01f, -9.238795325e-01f},
+    {1.950903220e-01f, 1.950903220e-01f, -9.807852804e-01f, -9.807852804e-01f},
+    {0.0f, 0.0f, -1.000000000e+00f, -1.000000000e+00f},
+    {-1.950903220e-01f, -1.950903220e-01f, -9.807852804e-01f, -9.807852804e-01f},
+    {-3.826834324e-01f, -3.826834324e-01f, -9.238795325e-01f, -9.238795325e-01f},
+    {-5.555702330e-01f, -5.555702330e-01f, -8.314696123e-01f, -8.314696123e-01f},
+    {-7.071067812e-01f, -7.071067812e-01f, -7.071067812e-01f, -7.071067812e-01f},
+    {-8.314696123e-01f, -8.314696123e-01f, -5.555702330e-01f, -5.555702330e-01f},
+    {-9.238795325e-01f, -9.238795325e-01f, -3.826834324e-01f, -3.826834324e-01f},
+    {-9.807852804e-01f, -9.807852804e-01f, -1.950903220e-01f, -1.950903220e-01f}};
+
+// reg_fft<R> on channel pairs
+template <int R>
+__device__ __forceinline__ void reg_fft2(cpair (&x)[R]) {
+    if constexpr (R > 1) {
+        constexpr int LR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : R == 16 ? 4 : 5;
+        cpair y[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            int b = 0;
+#pragma unroll
+            for (int k = 0; k < LR; ++k) b |= ((i >> k) & 1) << (LR - 1 - k);
+            y[b] = x[i];
+        }
+#pragma unroll
+        for (int s = 0; s < LR; ++s) {
+            const int h = 1 << s;
+#pragma unroll
+            for (int b = 0; b < R / 2; ++b) {
+                const int j = b & (h - 1);
+                const int i0 = ((b >> s) << (s + 1)) + j;
+                const int i1 = i0 + h;
+                cpair t;
+                if (j == 0) {
+                    t = y[i1];
+                } else if (4 * j == 2 * h) {   // exp(-i pi/2) = -i
+                    t = pmul_mi(y[i1]);
+                } else {
+                    const float4 w = kW32d[j * (16 / h)];
+                    t = pcmul(cpair{make_float2(w.x, w.y), make_float2(w.z, w.w)}, y[i1]);
+                }
+                y[i1] = pcsub(y[i0], t);
+                y[i0] = pcadd(y[i0], t);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) x[i] = y[i];
+    }
+}
+
+// G-point DFT of v[0..G) in registers, natural order in and out (G = 1, 2, 4)
+template <int G>
+__device__ __forceinline__ void dft_small2(cpair* v) {
+    if constexpr (G == 2) {
+        const cpair a = v[0], b = v[1];
+        v[0] = pcadd(a, b);
+        v[1] = pcsub(a, b);
+    } else if constexpr (G == 4) {
+        const cpair s02 = pcadd(v[0], v[2]), d02 = pcsub(v[0], v[2]);
+        const cpair s13 = pcadd(v[1], v[3]), d13 = pcsub(v[1], v[3]);
+        v[0] = pcadd(s02, s13);
+        v[2] = pcsub(s02, s13);
+        v[1] = cpair{padd(d02.re, d13.im), psub(d02.im, d13.re)};   // d02 - i d13
+        v[3] = cpair{psub(d02.re, d13.im), padd(d02.im, d13.re)};   // d02 + i d13
+    }
+}
+
+__device__ __forceinline__ cpair shfl_xor4(cpair v, int m) {
+    return cpair{make_float2(__shfl_xor_sync(0xffffffffu, v.re.x, m), __shfl_xor_sync(0xffffffffu, v.re.y, m)),
+                 make_float2(__shfl_xor_sync(0xffffffffu, v.im.x, m), __shfl_xor_sync(0xffffffffu, v.im.y, m))};
+}
+
+__device__ __forceinline__ void kahan_add2(f2& sum, f2& comp, f2 x) {
+    const f2 y = psub(x, comp);
+    const f2 t = padd(sum, y);
+    comp = psub(psub(t, sum), y);
+    sum = t;
+}
+
+// the two channels' Kahan pairs as one: the sum is s - c
+__device__ __forceinline__ void kahan_merge(f2 sum, f2 comp, float& s, float& c) {
+    float e;
+    two_sum(sum.x, sum.y, s, e);
+    c = (comp.x + comp.y) - e;
+}
+
+// Both channels of one candidate (buf: N channel-pair elements, sample n at
+// n): transform, then the window inner products (with IM also the imaginary
+// part of sum w d conj(h)); each sum is returned as s - c.
 template <int R, bool IM>
-__device__ void fft_inner_nat(float2* bufA, float2* bufE, const OrbitTables32& tab, const float2* tw1024,
-                              const LaneTw& ltw, int lane, int off, int W, const Win32* __restrict__ pw, float& sdh,
-                              float& cdh, float& shh, float& chh, float& sim, float& cim) {
+__device__ void fft_inner_ch(float4* buf, const OrbitTables32& tab, const LaneTw& ltw, int lane, int off, int W,
+                             const Win32* __restrict__ pw, float& sdh, float& cdh, float& shh, float& chh, float& sim,
+                             float& cim) {
     constexpr int N = 32 * R, G = 32 / R;
     constexpr int LG = G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 8 ? 3 : G == 16 ? 4 : 5;
     const int g = lane / G, j = lane % G;
-    // one copy of the transform for both channels (instruction-cache footprint)
-#pragma unroll 1
-    for (int ch = 0; ch < 2; ++ch) {
-        float2* buf = ch == 0 ? bufA : bufE;
-        float2 x[R];
+    cpair x[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) x[r] = buf[r * 32 + lane];
-        reg_fft<R>(x, tw1024);
+    for (int r = 0; r < R; ++r) x[r] = ld4(buf + r * 32 + lane);
+    reg_fft2<R>(x);
 #pragma unroll
-        for (int k1 = 1; k1 < R; ++k1) x[k1] = cmulf(x[k1], __ldg(tab.ltw + k1 * 32 + lane));
-        if constexpr (R > 1) {
-            __syncwarp();
+    for (int k1 = 1; k1 < R; ++k1) x[k1] = pcmul(x[k1], ldg4(tab.ltw4 + k1 * 32 + lane));
+    if constexpr (R > 1) {
+        __syncwarp();
 #pragma unroll
-            for (int k1 = 0; k1 < R; ++k1) buf[t1_addr<R>(k1, lane)] = x[k1];
-            __syncwarp();
+        for (int k1 = 0; k1 < R; ++k1) st4(buf + t1_addr<R>(k1, lane), x[k1]);
+        __syncwarp();
 #pragma unroll
-            for (int m = 0; m < R; ++m) x[m] = buf[t1_addr<R>(g, j + G * m)];
-            reg_fft<R>(x, tw1024);
-            if constexpr (G > 1) {
-                // exp(-2 pi i j ka / 32) = exp(-2 pi i (R j) ka / N): the lane-twiddle table
+        for (int m = 0; m < R; ++m) x[m] = ld4(buf + t1_addr<R>(g, j + G * m));
+        reg_fft2<R>(x);
+        if constexpr (G > 1) {
+            // exp(-2 pi i j ka / 32) = exp(-2 pi i (R j) ka / N): the lane-twiddle table
 #pragma unroll
-                for (int ka = 1; ka < R; ++ka) x[ka] = cmulf(x[ka], __ldg(tab.ltw + ka * 32 + R * j));
-            }
-        }
-        // x[q] is the value of bin K(q): the G-point stage, then the bin map
-        int kbase;   // K(q) = g + R*(ka(q) + R*kb(q)) with ka, kb per branch below
-        if constexpr (R == 4) {
-            // 8 = 4 x 2 over j = u + 2v: lane 2 ka + u gathers v = 0..3, a 4-point
-            // DFT over v, twiddle exp(-2 pi i u kv / 8), a 2-point DFT over u
-            // across the lane pair; it then holds kb = kv + 4 u, kv = 0..3
-            const int u = j & 1, ka = j >> 1;
-            __syncwarp();
-#pragma unroll
-            for (int q = 0; q < 4; ++q) buf[t2_addr4(g, q, j & 1, j >> 1)] = x[q];
-            __syncwarp();
-#pragma unroll
-            for (int v = 0; v < 4; ++v) x[v] = buf[t2_addr4(g, ka, u, v)];
-            dft_small<4>(x);
-            if (u) {
-                const float r = 0.70710678118654752f;
-                x[1] = make_float2(r * (x[1].x + x[1].y), r * (x[1].y - x[1].x));    // * exp(-i pi/4)
-                x[2] = make_float2(x[2].y, -x[2].x);                                 // * -i
-                x[3] = make_float2(r * (x[3].y - x[3].x), -r * (x[3].x + x[3].y));   // * exp(-3 i pi/4)
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float2 v = make_float2(__shfl_xor_sync(0xffffffffu, x[q].x, 1),
-                                             __shfl_xor_sync(0xffffffffu, x[q].y, 1));
-                x[q] = u ? csubf(v, x[q]) : caddf(x[q], v);
-            }
-            kbase = g + 4 * ka + 64 * u;   // + 16 kv for x[kv]: K = g + 4 (ka + 4 (kv + 4 u))
-        } else if constexpr (R >= G && G > 1) {
-            __syncwarp();
-#pragma unroll
-            for (int ka = 0; ka < R; ++ka) buf[t2_addr<R>(g, j, ka)] = x[ka];
-            __syncwarp();
-            // lane j now takes ka = (R/G) j + t for t < R/G, all G lanes of the group
-#pragma unroll
-            for (int t = 0; t < R / G; ++t) {
-#pragma unroll
-                for (int j2 = 0; j2 < G; ++j2) x[t * G + j2] = buf[t2_addr<R>(g, j2, (R / G) * j + t)];
-                dft_small<G>(x + t * G);
-            }
-            kbase = g + R * (R / G) * j;   // + R t + R^2 kb for x[t G + kb]
-        } else if constexpr (G > 1) {
-            // radix-2 decimation in frequency across the group's lanes
-#pragma unroll
-            for (int s = LG - 1; s >= 0; --s) {
-                const int h = 1 << s;
-                const bool upper = (lane & h) != 0;
-#pragma unroll
-                for (int q = 0; q < R; ++q) {
-                    const float2 v = make_float2(__shfl_xor_sync(0xffffffffu, x[q].x, h),
-                                                 __shfl_xor_sync(0xffffffffu, x[q].y, h));
-                    if (!upper) {
-                        x[q] = caddf(x[q], v);
-                    } else {
-                        const float2 d = csubf(v, x[q]);
-                        x[q] = s == 0 ? d : cmulf(d, ltw.w[s - 1]);
-                    }
-                }
-            }
-            kbase = g + R * R * brev_bits(j, LG);   // + R ka for x[ka]
-        } else {
-            kbase = g;   // G = 1: + R ka for x[ka]
-        }
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-            int K;
-            if constexpr (R == 4) K = kbase + 16 * q;
-            else if constexpr (R >= G && G > 1) K = kbase + R * (q / G) + R * R * (q % G);
-            else K = kbase + R * q;
-            const int m = K < N / 2 ? K : K - N;
-            const int kk = off + m;
-            if (kk >= 0 && kk < W) {
-                const Win32 v = pw[kk];
-                const float2 d = ch == 0 ? v.dA : v.dE;
-                const float w = ch == 0 ? v.wA : v.wE;
-                // explicit products: the same rounding in every kernel that forms these sums
-                kahan_add(sdh, cdh, __fmul_rn(w, fmaf(d.x, x[q].x, d.y * x[q].y)));
-                kahan_add(shh, chh, __fmul_rn(w, fmaf(x[q].x, x[q].x, x[q].y * x[q].y)));
-                if constexpr (IM) kahan_add(sim, cim, __fmul_rn(w, fmaf(d.y, x[q].x, -(d.x * x[q].y))));
-            }
+            for (int ka = 1; ka < R; ++ka) x[ka] = pcmul(x[ka], ldg4(tab.ltw4 + ka * 32 + R * j));
         }
     }
+    // x[q] is the value of bin K(q): the G-point stage, then the bin map
+    int kbase;   // K(q) = g + R*(ka(q) + R*kb(q)) with ka, kb per branch below
+    if constexpr (R == 4) {
+        // 8 = 4 x 2 over j = u + 2v: lane 2 ka + u gathers v = 0..3, a 4-point
+        // DFT over v, twiddle exp(-2 pi i u kv / 8), a 2-point DFT over u
+        // across the lane pair; it then holds kb = kv + 4 u, kv = 0..3
+        const int u = j & 1, ka = j >> 1;
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) st4(buf + t2_addr4(g, q, j & 1, j >> 1), x[q]);
+        __syncwarp();
+#pragma unroll
+        for (int v = 0; v < 4; ++v) x[v] = ld4(buf + t2_addr4(g, ka, u, v));
+        dft_small2<4>(x);
+        if (u) {
+            const f2 r = bc(0.70710678118654752f);
+            x[1] = cpair{pmul(r, padd(x[1].re, x[1].im)), pmul(r, psub(x[1].im, x[1].re))};     // * exp(-i pi/4)
+            x[2] = pmul_mi(x[2]);                                                                  // * -i
+            x[3] = cpair{pmul(r, psub(x[3].im, x[3].re)), pneg(pmul(r, padd(x[3].re, x[3].im)))};  // * exp(-3 i pi/4)
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const cpair v = shfl_xor4(x[q], 1);
+            x[q] = u ? pcsub(v, x[q]) : pcadd(x[q], v);
+        }
+        kbase = g + 4 * ka + 64 * u;   // + 16 kv for x[kv]: K = g + 4 (ka + 4 (kv + 4 u))
+    } else if constexpr (R >= G && G > 1) {
+        __syncwarp();
+#pragma unroll
+        for (int ka = 0; ka < R; ++ka) st4(buf + t2_addr<R>(g, j, ka), x[ka]);
+        __syncwarp();
+        // lane j now takes ka = (R/G) j + t for t < R/G, all G lanes of the group
+#pragma unroll
+        for (int t = 0; t < R / G; ++t) {
+#pragma unroll
+            for (int j2 = 0; j2 < G; ++j2) x[t * G + j2] = ld4(buf + t2_addr<R>(g, j2, (R / G) * j + t));
+            dft_small2<G>(x + t * G);
+        }
+        kbase = g + R * (R / G) * j;   // + R t + R^2 kb for x[t G + kb]
+    } else if constexpr (G > 1) {
+        // radix-2 decimation in frequency across the group's lanes
+#pragma unroll
+        for (int s = LG - 1; s >= 0; --s) {
+            const int h = 1 << s;
+            const bool upper = (lane & h) != 0;
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const cpair v = shfl_xor4(x[q], h);
+                if (!upper) {
+                    x[q] = pcadd(x[q], v);
+                } else {
+                    const cpair d = pcsub(v, x[q]);
+                    x[q] = s == 0 ? d : pcmul(d, cpair{bc(ltw.w[s - 1].x), bc(ltw.w[s - 1].y)});
+                }
+            }
+        }
+        kbase = g + R * R * brev_bits(j, LG);   // + R ka for x[ka]
+    } else {
+        kbase = g;   // G = 1: + R ka for x[ka]
+    }
+    const f2 z = bc(0.0f);
+    f2 s_dh = z, c_dh = z, s_hh = z, c_hh = z, s_im = z, c_im = z;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        int K;
+        if constexpr (R == 4) K = kbase + 16 * q;
+        else if constexpr (R >= G && G > 1) K = kbase + R * (q / G) + R * R * (q % G);
+        else K = kbase + R * q;
+        const int m = K < N / 2 ? K : K - N;
+        const int kk = off + m;
+        if (kk >= 0 && kk < W) {
+            const Win32 v = pw[kk];
+            // explicit products: the same rounding in every kernel that forms these sums
+            kahan_add2(s_dh, c_dh, pmul(v.w, pfma(v.dre, x[q].re, pmul(v.dim, x[q].im))));
+            kahan_add2(s_hh, c_hh, pmul(v.w, pfma(x[q].re, x[q].re, pmul(x[q].im, x[q].im))));
+            if constexpr (IM) kahan_add2(s_im, c_im, pmul(v.w, pfma(v.dim, x[q].re, pneg(pmul(v.dre, x[q].im)))));
+        }
+    }
+    kahan_merge(s_dh, c_dh, sdh, cdh);
+    kahan_merge(s_hh, c_hh, shh, chh);
+    if constexpr (IM) kahan_merge(s_im, c_im, sim, cim);
 }
 
 // Compensated warp sum of Kahan pairs: returns hi + lo on every lane.
@@ -887,10 +984,9 @@ __global__ void prep_mixed_kernel(const gb_window_t* __restrict__ wins, WinMeta*
     for (int i = threadIdx.x; i < win.W; i += blockDim.x) {
         const double2 a = dA[win.data_off + i], e = dE[win.data_off + i];
         Win32 v;
-        v.dA = make_float2((float)(a.x * sig), (float)(a.y * sig));
-        v.dE = make_float2((float)(e.x * sig), (float)(e.y * sig));
-        v.wA = (float)(wA[win.data_off + i] * isig2);
-        v.wE = (float)(wE[win.data_off + i] * isig2);
+        v.dre = make_float2((float)(a.x * sig), (float)(e.x * sig));
+        v.dim = make_float2((float)(a.y * sig), (float)(e.y * sig));
+        v.w = make_float2((float)(wA[win.data_off + i] * isig2), (float)(wE[win.data_off + i] * isig2));
         prep[po + i] = v;
     }
 }
@@ -951,7 +1047,7 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) 
                 if (off64 > -(long long)N && off64 < (long long)win.W + N) {
                     const int off = (int)off64;
 #define GB_FFT_INNER(R) \
-    fft_inner_nat<R, IM>(bufA, bufE, tab, tw1024, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh, sim, cim)
+    fft_inner_ch<R, IM>((float4*)bufA, tab, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh, sim, cim)
                     if constexpr (RMAX <= 8) {
                         switch (N) {
                             case 32: GB_FFT_INNER(1); break;
@@ -1263,7 +1359,8 @@ extern "C" int gb_loglik_mixed_noalloc(const gb_obs_t* obs, const gb_window_t* w
         t64[i] = (double*)(b + o64);
         t32[i] = (float*)(b + o32);
         tabs.t[i] = OrbitTables32{(const float4*)t32[i], (const float2*)(t32[i] + 16 * N),
-                                  (const float4*)(t32[i] + 18 * N), (const float4*)(t32[i] + 34 * N)};
+                                  (const float4*)(t32[i] + 18 * N), (const float4*)(t32[i] + 34 * N),
+                                  (const float4*)(t32[i] + 50 * N)};
         o64 += sizeof(double) * kTab64PerN * N;
         o32 += sizeof(float) * kTab32PerN * N;
     }
@@ -1674,8 +1771,8 @@ __device__ void residual_adjoint(float2* buf, int ch, const OrbitTables32& tab, 
         float2 rc = make_float2(0.0f, 0.0f);
         if (kk >= 0 && kk < W) {
             const Win32 v = pw[kk];
-            const float2 d = ch == 0 ? v.dA : v.dE;
-            const float w = ch == 0 ? v.wA : v.wE;
+            const float2 d = ch == 0 ? make_float2(v.dre.x, v.dim.x) : make_float2(v.dre.y, v.dim.y);
+            const float w = ch == 0 ? v.w.x : v.w.y;
             kahan_add(sdh, cdh, __fmul_rn(w, fmaf(d.x, x[k1].x, d.y * x[k1].y)));
             kahan_add(shh, chh, __fmul_rn(w, fmaf(x[k1].x, x[k1].x, x[k1].y * x[k1].y)));
             rc = make_float2(w * fmaf(-kappa, x[k1].x, d.x), -(w * fmaf(-kappa, x[k1].y, d.y)));   // conj(r)
