@@ -36,39 +36,6 @@ namespace {
 constexpr int kGaThreads = 256;
 constexpr int kGaMaxPop = 32768;   // fitness of the population in shared memory
 
-struct Philox {
-    uint32_t c[4];
-    uint32_t k[2];
-};
-
-__device__ __forceinline__ void philox_round(uint32_t (&c)[4], const uint32_t (&k)[2]) {
-    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
-    const uint32_t hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
-    const uint32_t hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
-    const uint32_t n0 = hi1 ^ c[1] ^ k[0], n2 = hi0 ^ c[3] ^ k[1];
-    c[0] = n0;
-    c[1] = lo1;
-    c[2] = n2;
-    c[3] = lo0;
-}
-
-// four 32-bit outputs for counter (a, b, cc, d) under key (k0, k1)
-__device__ __forceinline__ uint4 philox4x32_10(uint32_t a, uint32_t b, uint32_t cc, uint32_t d, uint32_t k0,
-                                               uint32_t k1) {
-    uint32_t c[4] = {a, b, cc, d};
-    uint32_t k[2] = {k0, k1};
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        philox_round(c, k);
-        k[0] += 0x9E3779B9u;
-        k[1] += 0xBB67AE85u;
-    }
-    return make_uint4(c[0], c[1], c[2], c[3]);
-}
-
-// uniform in (0, 1) from 32 bits
-__device__ __forceinline__ double u01(uint32_t x) { return ((double)x + 0.5) * 2.3283064365386963e-10; }
-
 // Draws of the genetic search.  They only steer a heuristic, so they are taken
 // in float where that saves double-precision work: indices by multiply-shift,
 // Bernoulli tests as integer thresholds, normals by float Box-Muller.

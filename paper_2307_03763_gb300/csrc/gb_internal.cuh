@@ -161,6 +161,37 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
+// Philox-4x32-10 (Salmon, Moraes, Dror and Shaw, "Parallel random numbers:
+// as easy as 1, 2, 3", SC 2011): ten rounds of two 32x32 -> 64-bit products
+// with the Weyl key schedule.
+__device__ __forceinline__ void philox_round(uint32_t (&c)[4], const uint32_t (&k)[2]) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
+    const uint32_t hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
+    const uint32_t n0 = hi1 ^ c[1] ^ k[0], n2 = hi0 ^ c[3] ^ k[1];
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+}
+
+// four 32-bit outputs for counter (a, b, cc, d) under key (k0, k1)
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t a, uint32_t b, uint32_t cc, uint32_t d, uint32_t k0,
+                                               uint32_t k1) {
+    uint32_t c[4] = {a, b, cc, d};
+    uint32_t k[2] = {k0, k1};
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        philox_round(c, k);
+        k[0] += 0x9E3779B9u;
+        k[1] += 0xBB67AE85u;
+    }
+    return make_uint4(c[0], c[1], c[2], c[3]);
+}
+
+// uniform in (0, 1) from 32 bits
+__device__ __forceinline__ double u01(uint32_t x) { return ((double)x + 0.5) * 2.3283064365386963e-10; }
+
 int set_error(gb_ctx* ctx, int code, const std::string& msg);
 // MH scratch: bytes for `chunk_slots` (chain, chunk) summaries and the keys
 // of `proposals` proposals; grow the buffer

@@ -5,10 +5,14 @@ proposals per window (``gb_draw_gaussian``), evaluate them all
 (``gb_loglik``), and build one chain per window (``gb_mh_independence``).
 The draws are counted on the device, so two rounds captured once in a CUDA
 graph can be replayed to run many rounds.  The proposal of a round is
-N(mean_w, cov_w) per window; the paper anneals and refits it with a 2-D KDE
-between rounds, which is not part of this driver.  The module orders calls,
+N(mean_w, cov_w) per window (``PosteriorRounds``, ``AnnealedPosterior``) or,
+as the paper describes Alg. 4, uniform over a reduced box at the first
+temperature and paired 2-D kernel-density estimates of the previous
+temperature's chain afterwards (``KDEPosterior``).  The module orders calls,
 owns buffers and factors the 8x8 proposal covariances once at set-up.
 """
+import math
+
 import numpy as np
 import torch
 
@@ -124,6 +128,106 @@ class AnnealedPosterior:
         buffers of ``self.rounds`` hold the last (T = 1) round.  With graph,
         the first call runs the ladder eagerly and captures it; later calls
         replay the capture."""
+        if not graph:
+            self._ladder()
+            return self
+        if self.graph is None:
+            self._ladder()
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph):
+                self._ladder()
+            return self
+        self.graph.replay()
+        return self
+
+
+def reduced_box(mle, sigma, prior_lo, prior_hi):
+    """The reduced parameter space of Sec. III.G for each window: theta_MLE
+    +- 4 sigma, f0 +- sigma_f, fdot over its whole prior range, psi +- pi/1000,
+    phi0 +- 2 pi/1000, the non-periodic ranges cut to the prior box.
+    mle, sigma: (n_win, 8); prior_lo, prior_hi: (n_win, 8) or (8,).
+    Returns (n_win, 16) boxes lo[8], hi[8]."""
+    mle = np.atleast_2d(np.asarray(mle, dtype=np.float64))
+    sigma = np.atleast_2d(np.asarray(sigma, dtype=np.float64))
+    plo = np.broadcast_to(np.asarray(prior_lo, dtype=np.float64), mle.shape)
+    phi = np.broadcast_to(np.asarray(prior_hi, dtype=np.float64), mle.shape)
+    half = 4.0 * sigma
+    half[:, 0] = sigma[:, 0]
+    half[:, 6] = math.pi / 1000
+    half[:, 7] = 2 * math.pi / 1000
+    lo, hi = mle - half, mle + half
+    lo[:, 1], hi[:, 1] = plo[:, 1], phi[:, 1]
+    lo[:, :6] = np.maximum(lo[:, :6], plo[:, :6])
+    hi[:, :6] = np.minimum(hi[:, :6], phi[:, :6])
+    return np.concatenate([lo, hi], axis=1)
+
+
+class KDEPosterior:
+    """Alg. 4 as the paper describes it (Sec. III.G): a temperature ladder
+    (15, 10, 5, 3, 2, 1 by default) of n proposals per window and
+    temperature.  The first temperature draws uniformly from each window's
+    reduced box; after each temperature the chain's states are smoothed into
+    paired two-dimensional kernel-density estimates, (f0, fdot),
+    (lambda, beta), (A, iota), which are the next temperature's proposal
+    (``gb_kde_build`` / ``gb_kde_draw``), psi and phi0 staying uniform over
+    their narrow ranges.  Each estimate is a grid x grid table over the pair's
+    box, mixed with a uniform floor so that no cell is left out.
+
+    Every step runs on the device; with graph=True the ladder is captured
+    once and replayed, each replay a new posterior from the uniform start.
+    box: (n_win, 16) reduced boxes (``reduced_box``)."""
+
+    def __init__(self, ctx, windows, dA, dE, wA, wE, box, n, seed=1, temperatures=(15, 10, 5, 3, 2, 1),
+                 prec="mixed", grid=64, floor=0.01, literal=False):
+        self.ctx = ctx
+        dev = ctx.device
+        self.nw = len(windows)
+        self.n = int(n)
+        self.seed = int(seed)
+        self.prec = prec
+        self.literal = literal
+        self.grid = int(grid)
+        self.floor = float(floor)
+        self.temperatures = [float(t) for t in temperatures]
+        self.windows = [(k0, W, N, doff, w * self.n, self.n) for w, (k0, W, N, doff, _, _) in enumerate(windows)]
+        self.data = (dA, dE, wA, wE)
+        self.box = torch.as_tensor(np.asarray(box, dtype=np.float64).reshape(self.nw, 16), device=dev).contiguous()
+        GG = self.grid * self.grid
+        flat = torch.arange(1, GG + 1, dtype=torch.float64, device=dev) / GG   # uniform over the box
+        self.flat = flat.expand(self.nw, 3, GG).contiguous()
+        self.cdf = self.flat.clone()
+        m = self.nw * self.n
+        self.theta = torch.empty((m, 8), dtype=torch.float64, device=dev)
+        self.log_g = torch.empty((self.nw, self.n), dtype=torch.float64, device=dev)
+        self.log_u = torch.empty((self.nw, self.n), dtype=torch.float64, device=dev)
+        self.logL = torch.empty(m, dtype=torch.float64, device=dev)
+        self.chain = torch.empty((self.nw, self.n), dtype=torch.int32, device=dev)
+        self.accepted = torch.empty(self.nw, dtype=torch.int32, device=dev)
+        self.temperature = torch.empty(self.nw, dtype=torch.float64, device=dev)
+        self.rounds = torch.zeros(2, dtype=torch.int64, device=dev)
+        self.graph = None
+
+    def _ladder(self):
+        c = self.ctx
+        self.cdf.copy_(self.flat)
+        K = len(self.temperatures)
+        for k, T in enumerate(self.temperatures):
+            s = k % 2
+            self.temperature.fill_(T)
+            c.kde_draw(self.box, self.grid, self.cdf, self.n, self.seed, self.rounds[s:s + 1],
+                       self.rounds[1 - s:2 - s], out=(self.theta, self.log_g, self.log_u))
+            c.loglik(self.windows, *self.data, self.theta, prec=self.prec, out=(self.logL, None, None))
+            c.mh_independence(self.logL.view(self.nw, self.n), self.log_g, self.log_u, self.temperature,
+                              literal=self.literal, out=(self.chain, self.accepted))
+            if k + 1 < K:
+                c.kde_build(self.theta, self.chain, self.box, self.grid, self.floor, out=self.cdf)
+        if K % 2:   # the next ladder reads the draw counter from slot 0
+            self.rounds[0:1].copy_(self.rounds[1:2])
+
+    def run(self, graph=False):
+        """One posterior: all temperatures from the uniform start; theta,
+        chain and accepted hold the last (T = 1) round.  With graph, the first
+        call runs the ladder eagerly and captures it; later calls replay it."""
         if not graph:
             self._ladder()
             return self

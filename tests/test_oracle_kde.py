@@ -144,3 +144,17 @@ def test_build_window_uses_the_chain_states():
         if a != b:
             assert P[a] == pytest.approx(P[b], rel=1e-9)     # 200 steps each
         assert P.sum() == pytest.approx(1.0)
+
+
+def test_product_reduced_box_matches_the_oracle():
+    # the driver's host-side reduced box (no GPU needed) against the oracle's
+    from paper_2307_03763_gb300.posterior import reduced_box
+    rng = np.random.default_rng(8)
+    plo = np.array([2.9e-3, 0.0, -np.pi / 2, -np.pi, 1e-24, 0.0, 0.0, 0.0])
+    phi = np.array([3.1e-3, 5e-16, np.pi / 2, np.pi, 1e-20, np.pi, np.pi, 2 * np.pi])
+    mle = plo + (phi - plo) * rng.uniform(size=(20, 8))
+    sig = (phi - plo) * rng.uniform(0.001, 0.3, size=(20, 8))
+    got = reduced_box(mle, sig, plo, phi)
+    for w in range(20):
+        lo, hi = kde.reduced_box(mle[w], sig[w], plo, phi)
+        assert np.array_equal(got[w, :8], lo) and np.array_equal(got[w, 8:], hi)
