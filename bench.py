@@ -382,11 +382,12 @@ def run_fullband(args):
     clocks = ClockSampler(dev.index)
     clocks.start()
     st = fullband.run(ctx, n_src=args.fb_sources, rounds=args.fb_rounds, pop=args.fb_pop, generations=args.fb_gens,
-                      phase=not args.fb_no_phase)
+                      phase=not args.fb_no_phase, posterior=args.fb_posterior)
     line = {"metric": "total wall time, s per posterior (full-band search)", "workload": "fullband",
             "n_gpus": 1, "unit": "s", "higher_is_better": False, "data": "synthetic",
             "value": st["wall_s"], "s_per_posterior": st["s_per_posterior"],
-            "posterior": "Alg. 4: six temperatures (15..1) x 10,000 proposals per recovered source",
+            "posterior": "Alg. 4: six temperatures (15..1) x 10,000 proposals per recovered source (%s)" % (
+                "uniform reduced box, then paired 2-D KDEs" if args.fb_posterior == "kde" else "Gaussian refits"),
             "config": {"workload": "fullband: 0.3-15 mHz, T=2 yr, dt=15 s, %d binaries, Alg. 1 windows" %
                        args.fb_sources}, "stats": st,
             # kernels launched from the host; the GA generations replayed from CUDA graphs are not counted
@@ -409,6 +410,8 @@ def main():
     ap.add_argument("--fb-rounds", type=int, default=3, help="fullband: search-and-subtract rounds")
     ap.add_argument("--fb-pop", type=int, default=1024, help="fullband: GA population per window")
     ap.add_argument("--fb-gens", type=int, default=100, help="fullband: GA generations per round")
+    ap.add_argument("--fb-posterior", default="gauss", choices=["gauss", "kde"],
+                    help="fullband: Alg. 4 proposals, Gaussian refits or the paper's paired KDEs")
     ap.add_argument("--fb-no-phase", action="store_true",
                     help="fullband: rank GA individuals by the plain SNR instead of the SNR maximised over phi0")
     args = ap.parse_args()

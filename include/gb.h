@@ -327,34 +327,40 @@ int gb_gauss_refit(gb_ctx_t* ctx, int32_t n_win, int32_t n, const double* theta,
  * (f0, fdot), (lambda, beta), (A, iota), is the proposal of the next; psi and
  * phi0 stay uniform over their narrow reduced ranges).  Window w's reduced
  * box is box[w] = lo[8], hi[8] (device, n_win x 16, hi > lo).  Each pair's
- * estimate is a grid x grid table of cumulative cell probabilities over the
- * pair's box, cdf[w][p][c] for the flattened cell c = i grid + j (i the
- * first parameter's cell: (f0, fdot), (lambda, beta), (A, iota) for
- * p = 0, 1, 2), device, n_win x 3 x grid^2 doubles.  A table with
- * cdf[c] = (c + 1)/grid^2 is uniform over the box (the first temperature).
+ * estimate is a grid x grid table of cumulative cell probabilities,
+ * cdf[w][p][c] for the flattened cell c = i grid + j (i the first
+ * parameter's cell: (f0, fdot), (lambda, beta), (A, iota) for p = 0, 1, 2;
+ * device, n_win x 3 x grid^2 doubles), over the extent
+ * ext[w][p] = (x0, x1, y0, y1) (device, n_win x 3 x 4 doubles).  A table with
+ * cdf[c] = (c + 1)/grid^2 over the box's extents is uniform over the box
+ * (the first temperature).
  *
  * gb_kde_build: from the chain (n_win x n int32, as written by
- * gb_mh_independence) over theta (n_win x n x 8): the n entries theta[chain[i]]
- * are counted per cell (floor((x - lo)/(hi - lo) grid), clamped), smoothed per
- * axis by a Gaussian kernel of h = s (u + 1)^(-1/6) (s the standard deviation
- * of the entries, u the accepted moves; weights exp(-d^2/2 sigma^2) in cells,
- * |d| <= min(ceil(3 sigma), grid - 1), normalised; mass past the box edge
- * dropped), normalised, mixed with a uniform floor_mass (0..1) and summed.
+ * gb_mh_independence) over theta (n_win x n x 8).  Per axis, with the n
+ * entries theta[chain[i]] in [a, b], h = s (u + 1)^(-1/6) (s their standard
+ * deviation, u the accepted moves) and c0 = (hi - lo)/grid, the extent is
+ * [max(lo, a - 3h - c0), min(hi, b + 3h + c0)] (written to ext).  The
+ * entries are counted per cell (floor((x - x0)/(x1 - x0) grid), clamped),
+ * smoothed per axis by the Gaussian of width h (weights exp(-d^2/2 sigma^2),
+ * sigma = h/cell, |d| <= min(ceil(3 sigma), grid - 1), normalised; mass past
+ * the grid edge dropped), normalised, mixed with a uniform floor_mass (0..1)
+ * and summed into cdf.
  *
  * gb_kde_draw: n proposals per window.  With Philox-4x32-10 words
  * w_0..w_11 from key seed and counters (*round_in, w, i, 0..2), u_k =
  * (w_k + 1/2) 2^-32: pair p takes the first cell c with cdf[c] > u_3p (the
- * last if none) and the point lo + (cell + u_3p+1 or u_3p+2) (hi - lo)/grid;
+ * last if none) and the point x0 + (cell + u_3p+1) (x1 - x0)/grid (y alike with
+ * u_3p+2);
  * psi = lo + u_9 (hi - lo), phi0 with u_10;
  *   log_g = sum_p log((cdf[c] - cdf[c-1]) / cell area) - log(psi width)
  *           - log(phi0 width),   log_u = log u_11.
  * theta n_win x n x 8, log_g, log_u n_win x n (device, written);
  * *round_out = *round_in + 1.  grid in [2, 128], n_win <= 65535. */
 int gb_kde_build(gb_ctx_t* ctx, int32_t n_win, int32_t n, const double* theta, const int32_t* chain,
-                 const double* box, int32_t grid, double floor_mass, double* cdf, void* stream);
+                 const double* box, int32_t grid, double floor_mass, double* cdf, double* ext, void* stream);
 int gb_kde_draw(gb_ctx_t* ctx, int32_t n_win, int32_t n, const double* box, int32_t grid, const double* cdf,
-                uint64_t seed, const uint64_t* round_in, uint64_t* round_out, double* theta, double* log_g,
-                double* log_u, void* stream);
+                const double* ext, uint64_t seed, const uint64_t* round_in, uint64_t* round_out, double* theta,
+                double* log_g, double* log_u, void* stream);
 
 /* n blocks of Philox-4x32-10 (Salmon et al., SC 2011) with key = seed and
  * counter (i, 0, 0, 0), i < n, written as 4 words per block (device).  The

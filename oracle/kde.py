@@ -22,28 +22,35 @@ K1  Pairs (theta indices): (f0, fdot) = (0, 1), (lambda, beta) = (3, 2),
 K2  Reduced space (the box of Sec. III.G): theta_MLE +- 4 sigma, f0 +- sigma_f,
     fdot over its whole prior range, psi +- pi/1000, phi0 +- 2 pi/1000, every
     range cut to the prior box; sigma = sqrt(diag F^-1).
-K3  Grid estimate of one pair over its reduced box [lo_x, hi_x] x [lo_y, hi_y]
-    with G x G cells (cell (i, j) covers x in lo_x + [i, i+1) c_x, c_x =
-    (hi_x - lo_x)/G, and likewise y):
+K3  Grid estimate of one pair.  The grid spans the chain's own range on each
+    axis, as kernel-density grids do: [max(lo, a - 3h - c0), min(hi,
+    b + 3h + c0)] for entries in [a, b], bandwidth h and the box cell
+    c0 = (hi - lo)/G, so that its resolution follows the posterior (fdot's
+    reduced range is its whole prior, thousands of posterior widths at high
+    frequency); the first temperature's grids span the box.  On that extent
+    [lo', hi'] with G x G cells (cell (i, j) covers x in lo' + [i, i+1) c,
+    c = (hi' - lo')/G, and likewise y):
       * the chain's n entries (each step counts the state it is in, so a
         state weighs the steps spent in it) are counted per cell, cell index
-        floor((x - lo_x) / (hi_x - lo_x) * G) clamped to [0, G-1];
+        floor((x - lo') / (hi' - lo') * G) clamped to [0, G-1];
       * the counts are smoothed by a Gaussian kernel per axis with Scott's
         bandwidth for two dimensions, h = s n_eff^(-1/6), s the standard
         deviation of the n entries (divisor n) and n_eff the number of
         distinct visits, accepted moves + 1; in cells sigma = h / c, the
         weights exp(-d^2 / (2 sigma^2)) for |d| <= r = min(ceil(3 sigma), G-1)
         normalised to sum one (sigma = 0: no smoothing); mass pushed past the
-        box edge is dropped;
+        grid edge is dropped;
       * the result is normalised to one and mixed with a uniform floor:
         P = (1 - eps) S / sum S + eps / G^2, so every cell keeps a chance.
-K4  The density is constant on a cell.  A draw picks cell c (flattened
-    c = i G + j) with probability P_c through the cumulative sums
+K4  The density is constant on a cell of the pair's grid.  A draw picks
+    cell c (flattened c = i G + j) with probability P_c through the
+    cumulative sums
     C_c = P_0 + ... + P_c: the first c with C_c > u (the last cell if none),
     then a uniform point in it.  P_c is taken as C_c - C_(c-1) (C_(-1) = 0),
     the probability the draw actually has, and
     log g = sum_pairs log(P_c / (c_x c_y)) - log(width psi) - log(width phi0).
-K5  The first temperature uses flat grids, P_c = 1/G^2: uniform in the box.
+K5  The first temperature uses flat grids over the box, P_c = 1/G^2:
+    uniform in the box.
 K6  Between temperatures the estimate is used as it is, without rescaling
     for the next temperature (the paper uses the obtained posterior as the
     next proposal).
@@ -104,21 +111,29 @@ def cell_index(v, lo, hi, G):
     return min(max(i, 0), G - 1)
 
 
+def grid_extent(v, h, lo, hi, G):
+    """[lo', hi'] of one axis (reading K3)."""
+    c0 = (hi - lo) / G
+    return max(lo, float(np.min(v)) - 3.0 * h - c0), min(hi, float(np.max(v)) + 3.0 * h + c0)
+
+
 def pair_grid(x, y, n_eff, box_x, box_y, G, eps):
-    """Cell probabilities P (G x G, x index first) of one pair (reading K3).
+    """Cell probabilities P (G x G, x index first) of one pair and the grid's
+    extents ((lo'_x, hi'_x), (lo'_y, hi'_y)) (reading K3).
 
     x, y: the n chain entries of the pair's two parameters."""
     x, y = np.asarray(x, float), np.asarray(y, float)
     n = len(x)
+    bw = n_eff ** (-1.0 / 6.0)
+    hx, hy = x.std() * bw, y.std() * bw
+    ex, ey = grid_extent(x, hx, box_x[0], box_x[1], G), grid_extent(y, hy, box_y[0], box_y[1], G)
     H = np.zeros((G, G))
     for a, b in zip(x, y):
-        H[cell_index(a, box_x[0], box_x[1], G), cell_index(b, box_y[0], box_y[1], G)] += 1.0
-    sx, sy = x.std(), y.std()
-    bw = n_eff ** (-1.0 / 6.0)
-    cx, cy = (box_x[1] - box_x[0]) / G, (box_y[1] - box_y[0]) / G
-    S = smoothing_matrix(sx * bw / cx, G) @ H @ smoothing_matrix(sy * bw / cy, G).T
+        H[cell_index(a, ex[0], ex[1], G), cell_index(b, ey[0], ey[1], G)] += 1.0
+    cx, cy = (ex[1] - ex[0]) / G, (ey[1] - ey[0]) / G
+    S = smoothing_matrix(hx / cx, G) @ H @ smoothing_matrix(hy / cy, G).T
     assert n > 0 and S.sum() > 0
-    return (1.0 - eps) * S / S.sum() + eps / (G * G)
+    return (1.0 - eps) * S / S.sum() + eps / (G * G), (ex, ey)
 
 
 def flat_grid(G):
@@ -132,21 +147,32 @@ def cumulative(P):
 
 
 def build_window(theta, chain, lo, hi, G, eps):
-    """Cumulative sums of the three pair grids of one window from its chain:
-    theta (n, 8) proposals, chain (n) state index after each step."""
+    """Cumulative sums of the three pair grids of one window from its chain,
+    and their extents: theta (n, 8) proposals, chain (n) state index after
+    each step.  Returns (C (3, G^2), E (3, 4) = lo'_x, hi'_x, lo'_y, hi'_y)."""
     theta = np.asarray(theta, float)
     states = theta[np.asarray(chain, int)]
     n_eff = accepted_moves(chain) + 1
-    return np.stack([cumulative(pair_grid(states[:, dx], states[:, dy], n_eff, (lo[dx], hi[dx]),
-                                          (lo[dy], hi[dy]), G, eps)) for dx, dy in PAIRS])
+    C, E = [], []
+    for dx, dy in PAIRS:
+        P, (ex, ey) = pair_grid(states[:, dx], states[:, dy], n_eff, (lo[dx], hi[dx]), (lo[dy], hi[dy]), G, eps)
+        C.append(cumulative(P))
+        E.append([ex[0], ex[1], ey[0], ey[1]])
+    return np.stack(C), np.array(E)
+
+
+def box_extents(lo, hi):
+    """The pairs' extents of the first temperature: the box (reading K5)."""
+    return np.array([[lo[dx], hi[dx], lo[dy], hi[dy]] for dx, dy in PAIRS])
 
 
 def u01(word):
     return (int(word) + 0.5) * 2.0 ** -32
 
 
-def draw(cdfs, lo, hi, G, words):
-    """One proposal from the three pairs' cumulative sums (reading K4, K7).
+def draw(cdfs, exts, lo, hi, G, words):
+    """One proposal from the three pairs' cumulative sums over their extents
+    (reading K4, K7); lo, hi: the box (psi and phi0).
 
     Returns (theta[8], log_g, log_u)."""
     theta = np.zeros(8)
@@ -159,9 +185,10 @@ def draw(cdfs, lo, hi, G, words):
             c += 1
         Pc = C[c] - (C[c - 1] if c > 0 else 0.0)
         i, j = divmod(c, G)
-        cx, cy = (hi[dx] - lo[dx]) / G, (hi[dy] - lo[dy]) / G
-        theta[dx] = lo[dx] + (i + u01(words[3 * p + 1])) * cx
-        theta[dy] = lo[dy] + (j + u01(words[3 * p + 2])) * cy
+        x0, x1, y0, y1 = exts[p]
+        cx, cy = (x1 - x0) / G, (y1 - y0) / G
+        theta[dx] = x0 + (i + u01(words[3 * p + 1])) * cx
+        theta[dy] = y0 + (j + u01(words[3 * p + 2])) * cy
         log_g += math.log(Pc) - math.log(cx * cy)
     for d, w in ((6, 9), (7, 10)):
         theta[d] = lo[d] + u01(words[w]) * (hi[d] - lo[d])

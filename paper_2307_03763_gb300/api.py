@@ -72,8 +72,8 @@ _SIGNATURES = {
                                   ctypes.POINTER(GAParams), _P, _P, _P, _P]),
     "gb_gauss_refit": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_double, _P, _P, _P]),
-    "gb_kde_build": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _I32, ctypes.c_double, _P, _P]),
-    "gb_kde_draw": (ctypes.c_int, [_P, _I32, _I32, _P, _I32, _P, ctypes.c_uint64, _P, _P, _P, _P, _P, _P]),
+    "gb_kde_build": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _I32, ctypes.c_double, _P, _P, _P]),
+    "gb_kde_draw": (ctypes.c_int, [_P, _I32, _I32, _P, _I32, _P, _P, ctypes.c_uint64, _P, _P, _P, _P, _P, _P]),
     "gb_philox4x32": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint32, _P, _P]),
     "gb_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _I64, _P, _I64,
                                    _P, _I32, ctypes.POINTER(Tuning), _P]),
@@ -309,21 +309,25 @@ class Context:
         return th, lg, lu
 
     def kde_build(self, theta, chain, box, grid, floor, out):
-        """Paired KDE proposal tables from each window's chain (see gb_kde_build); out (n_win, 3, grid^2)."""
+        """Paired KDE proposal tables from each window's chain (see gb_kde_build);
+        out = (cdf (n_win, 3, grid^2), ext (n_win, 3, 4))."""
         nw, n = chain.shape
+        cdf, ext = out
         _need(theta, torch.float64, self.device, "theta", (nw * n, 8))
         _need(chain, torch.int32, self.device, "chain", (nw, n))
         _need(box, torch.float64, self.device, "box", (nw, 16))
-        _need(out, torch.float64, self.device, "cdf", (nw, 3, grid * grid))
+        _need(cdf, torch.float64, self.device, "cdf", (nw, 3, grid * grid))
+        _need(ext, torch.float64, self.device, "ext", (nw, 3, 4))
         self._check(lib().gb_kde_build(self._h, nw, n, _ptr(theta), _ptr(chain), _ptr(box), int(grid), float(floor),
-                                       _ptr(out), _stream(self.device)))
-        return out
+                                       _ptr(cdf), _ptr(ext), _stream(self.device)))
+        return cdf, ext
 
-    def kde_draw(self, box, grid, cdf, n, seed, round_in, round_out, out=None):
+    def kde_draw(self, box, grid, cdf, ext, n, seed, round_in, round_out, out=None):
         """n proposals per window from the paired KDE tables (see gb_kde_draw): theta (n_win*n, 8), log_g, log_u."""
         nw = box.shape[0]
         _need(box, torch.float64, self.device, "box", (nw, 16))
         _need(cdf, torch.float64, self.device, "cdf", (nw, 3, grid * grid))
+        _need(ext, torch.float64, self.device, "ext", (nw, 3, 4))
         _need(round_in, torch.int64, self.device, "round_in", (1,))
         _need(round_out, torch.int64, self.device, "round_out", (1,))
         if out is None:
@@ -334,7 +338,7 @@ class Context:
         _need(th, torch.float64, self.device, "theta", (nw * n, 8))
         _need(lg, torch.float64, self.device, "log_g", (nw, n))
         _need(lu, torch.float64, self.device, "log_u", (nw, n))
-        self._check(lib().gb_kde_draw(self._h, nw, int(n), _ptr(box), int(grid), _ptr(cdf),
+        self._check(lib().gb_kde_draw(self._h, nw, int(n), _ptr(box), int(grid), _ptr(cdf), _ptr(ext),
                                       int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(round_in), _ptr(round_out), _ptr(th),
                                       _ptr(lg), _ptr(lu), _stream(self.device)))
         return th, lg, lu

@@ -16,9 +16,13 @@ library's kernels, batched over all windows at once:
              (adjoint gradient, observed Fisher matrix); the result counts as
              recovered when its SNR (Eq. 6) passes the threshold;
   posterior  for the round's recovered sources, Alg. 4: the six-temperature
-             ladder of ``AnnealedPosterior`` (10,000 proposals per
-             temperature), started from the observed Fisher matrix of the
-             adjoint gradient at the first temperature's width;
+             ladder (10,000 proposals per temperature) of
+             ``AnnealedPosterior`` (default: Gaussian proposals from the
+             observed Fisher matrix of the adjoint gradient, refitted between
+             temperatures) or of ``KDEPosterior`` (posterior="kde": uniform
+             over the reduced box, then paired 2-D KDEs, as the paper
+             describes it; from search optima its final-round acceptance is
+             far lower);
   subtract   the recovered templates (``gb_waveform``) leave the window data
              before the next round.
 
@@ -36,7 +40,7 @@ import torch
 from . import autograd as gbag
 from . import workloads as wk
 from .ga import GASearch
-from .posterior import AnnealedPosterior
+from .posterior import AnnealedPosterior, KDEPosterior, reduced_box
 
 # fixed parts of every window's search box (the f0 range is the segment's)
 _LO = np.array([0.0, 0.0, -np.pi / 2, -np.pi, 1e-24, 0.0, 0.0, 0.0])
@@ -160,11 +164,13 @@ class FullBand:
         C = C / d[:, :, None] / d[:, None, :]
         return C * s[:, :, None] * s[:, None, :]
 
-    def search(self, rounds=3, pop=1024, generations=100, snr_min=10.0, n_post=10000, post_batch=4096, phase=True):
+    def search(self, rounds=3, pop=1024, generations=100, snr_min=10.0, n_post=10000, post_batch=4096, phase=True,
+               posterior="gauss"):
         wins = self.windows([pop] * self.n_win)
         boxes = self.boxes()
         self.stats.update({"rounds": rounds, "pop": pop, "generations": generations, "snr_min": snr_min,
-                           "proposals_per_posterior": n_post, "phase_maximised_fitness": phase})
+                           "proposals_per_posterior": n_post, "phase_maximised_fitness": phase,
+                           "posterior_proposals": posterior})
         th0 = torch.as_tensor(np.repeat(boxes[:, None, :8], pop, 1).reshape(-1, 8)
                               + np.repeat((boxes[:, None, 8:] - boxes[:, None, :8]) * 0.5, pop, 1).reshape(-1, 8),
                               device=self.dev).contiguous()
@@ -200,10 +206,18 @@ class FullBand:
                 win = [(self.layout[w][0], self.layout[w][1], self.layout[w][1], int(self.doff[w]), 0, 0)
                        for w in sub]
                 mu = torch.as_tensor(best[sub], device=self.dev).contiguous()
-                cov = self._proposal_cov(win, mu)
-                ap = AnnealedPosterior(self.ctx, win, self.dA, self.dE, self.wA, self.wE, mu, cov, n=n_post,
-                                       seed=self.seed + 1000 * r + i, prec=self.prec).run()
-                acc = ap.rounds.accepted.cpu().numpy()
+                if posterior == "kde":
+                    # the paper's proposals: uniform over the reduced box, then paired KDEs
+                    sig = np.sqrt(np.diagonal(self._proposal_cov(win, mu, width=1.0), axis1=1, axis2=2))
+                    box = reduced_box(best[sub], sig, boxes[sub, :8], boxes[sub, 8:])
+                    ap = KDEPosterior(self.ctx, win, self.dA, self.dE, self.wA, self.wE, box, n=n_post,
+                                      seed=self.seed + 1000 * r + i, prec=self.prec).run()
+                    acc = ap.accepted.cpu().numpy()
+                else:
+                    cov = self._proposal_cov(win, mu)
+                    ap = AnnealedPosterior(self.ctx, win, self.dA, self.dE, self.wA, self.wE, mu, cov, n=n_post,
+                                           seed=self.seed + 1000 * r + i, prec=self.prec).run()
+                    acc = ap.rounds.accepted.cpu().numpy()
                 post.extend(int(a) for a in acc)
                 del ap
             t2 = _sync(self.dev)
@@ -256,7 +270,7 @@ class FullBand:
 
 
 def run(ctx, n_src=200000, f_lo=0.3e-3, f_hi=15e-3, T=2 * wk.YEAR, rounds=3, pop=1024, generations=100,
-        snr_min=10.0, n_post=10000, seed=wk.SEED_BASE + 5, warm=True, phase=True):
+        snr_min=10.0, n_post=10000, seed=wk.SEED_BASE + 5, warm=True, phase=True, posterior="gauss"):
     """Config 5 end to end; returns the statistics (wall times in seconds).
     warm: run a small instance first, so that one-time library initialisation
     (kernel modules, solver handles) is not in the times."""
@@ -264,12 +278,13 @@ def run(ctx, n_src=200000, f_lo=0.3e-3, f_hi=15e-3, T=2 * wk.YEAR, rounds=3, pop
         small = FullBand(ctx, wk.fullband_sources(200, 2e-3, 2.1e-3, seed + 1), wk.fullband_layout(2e-3, 2.1e-3, T),
                          T, seed=seed + 1).synthesize()
         small.injected_snr()
-        small.search(rounds=1, pop=64, generations=4, snr_min=snr_min, n_post=256)
+        small.search(rounds=1, pop=64, generations=4, snr_min=snr_min, n_post=256, posterior=posterior)
     t0 = _sync(ctx.device)
     fb = FullBand(ctx, wk.fullband_sources(n_src, f_lo, f_hi, seed), wk.fullband_layout(f_lo, f_hi, T), T,
                   seed=seed).synthesize()
     snr_inj, owner = fb.injected_snr()
-    fb.search(rounds=rounds, pop=pop, generations=generations, snr_min=snr_min, n_post=n_post, phase=phase)
+    fb.search(rounds=rounds, pop=pop, generations=generations, snr_min=snr_min, n_post=n_post, phase=phase,
+              posterior=posterior)
     st = dict(fb.stats)
     st.update(fb.match(snr_inj, owner))
     st["wall_s"] = _sync(ctx.device) - t0

@@ -170,8 +170,9 @@ class KDEPosterior:
     paired two-dimensional kernel-density estimates, (f0, fdot),
     (lambda, beta), (A, iota), which are the next temperature's proposal
     (``gb_kde_build`` / ``gb_kde_draw``), psi and phi0 staying uniform over
-    their narrow ranges.  Each estimate is a grid x grid table over the pair's
-    box, mixed with a uniform floor so that no cell is left out.
+    their narrow ranges.  Each estimate is a grid x grid table over the
+    chain's range on each axis (widened by three bandwidths, inside the box),
+    mixed with a uniform floor so that no cell is left out.
 
     Every step runs on the device; with graph=True the ladder is captured
     once and replayed, each replay a new posterior from the uniform start.
@@ -196,6 +197,10 @@ class KDEPosterior:
         flat = torch.arange(1, GG + 1, dtype=torch.float64, device=dev) / GG   # uniform over the box
         self.flat = flat.expand(self.nw, 3, GG).contiguous()
         self.cdf = self.flat.clone()
+        b = self.box
+        self.box_ext = torch.stack([torch.stack([b[:, dx], b[:, 8 + dx], b[:, dy], b[:, 8 + dy]], dim=1)
+                                    for dx, dy in ((0, 1), (3, 2), (4, 5))], dim=1).contiguous()
+        self.ext = self.box_ext.clone()
         m = self.nw * self.n
         self.theta = torch.empty((m, 8), dtype=torch.float64, device=dev)
         self.log_g = torch.empty((self.nw, self.n), dtype=torch.float64, device=dev)
@@ -210,17 +215,18 @@ class KDEPosterior:
     def _ladder(self):
         c = self.ctx
         self.cdf.copy_(self.flat)
+        self.ext.copy_(self.box_ext)
         K = len(self.temperatures)
         for k, T in enumerate(self.temperatures):
             s = k % 2
             self.temperature.fill_(T)
-            c.kde_draw(self.box, self.grid, self.cdf, self.n, self.seed, self.rounds[s:s + 1],
+            c.kde_draw(self.box, self.grid, self.cdf, self.ext, self.n, self.seed, self.rounds[s:s + 1],
                        self.rounds[1 - s:2 - s], out=(self.theta, self.log_g, self.log_u))
             c.loglik(self.windows, *self.data, self.theta, prec=self.prec, out=(self.logL, None, None))
             c.mh_independence(self.logL.view(self.nw, self.n), self.log_g, self.log_u, self.temperature,
                               literal=self.literal, out=(self.chain, self.accepted))
             if k + 1 < K:
-                c.kde_build(self.theta, self.chain, self.box, self.grid, self.floor, out=self.cdf)
+                c.kde_build(self.theta, self.chain, self.box, self.grid, self.floor, out=(self.cdf, self.ext))
         if K % 2:   # the next ladder reads the draw counter from slot 0
             self.rounds[0:1].copy_(self.rounds[1:2])
 

@@ -61,11 +61,13 @@ def test_kde_build_matches_oracle(api, grid):
     th = centre[:, None, :] + width[:, None, :] * rng.normal(0.0, 0.25, size=(nw, n, 8))
     ch = _chains(rng, nw, n, [0.4, 0.02, 0.0])
     cdf = torch.empty((nw, 3, grid * grid), dtype=torch.float64, device=DEV)
+    ext = torch.empty((nw, 3, 4), dtype=torch.float64, device=DEV)
     ctx.kde_build(_cuda(th.reshape(-1, 8), torch.float64), _cuda(ch, torch.int32), _cuda(box, torch.float64), grid,
-                  0.01, out=cdf)
-    got = cdf.cpu().numpy()
+                  0.01, out=(cdf, ext))
+    got, gext = cdf.cpu().numpy(), ext.cpu().numpy()
     for w in range(nw):
-        ref = okde.build_window(th[w], ch[w], lo[w], hi[w], grid, 0.01)
+        ref, rext = okde.build_window(th[w], ch[w], lo[w], hi[w], grid, 0.01)
+        assert np.allclose(gext[w], rext, rtol=1e-12, atol=0), (w, gext[w], rext)
         assert np.abs(got[w] - ref).max() < 2e-6, (w, np.abs(got[w] - ref).max())
         assert np.all(np.diff(got[w], axis=1) > 0) and np.allclose(got[w][:, -1], 1.0, atol=1e-12)
 
@@ -80,18 +82,22 @@ def test_kde_draw_matches_oracle(api):
     lo, hi = box[:, :8], box[:, 8:]
     th = (lo + hi)[:, None, :] / 2 + (hi - lo)[:, None, :] * rng.normal(0.0, 0.2, size=(nw, n, 8))
     ch = _chains(rng, nw, n, [0.3, 0.01])
-    C = np.stack([okde.build_window(th[w], ch[w], lo[w], hi[w], G, 0.02) for w in range(nw)])
+    built = [okde.build_window(th[w], ch[w], lo[w], hi[w], G, 0.02) for w in range(nw)]
+    C = np.stack([b[0] for b in built])
+    E = np.stack([b[1] for b in built])
     C[1, 1] = okde.cumulative(okde.flat_grid(G))
+    E[1, 1] = okde.box_extents(lo[1], hi[1])[1]
     seed = 0x5EED0000C0FFEE
     r = torch.tensor([41, 0], dtype=torch.int64, device=DEV)
-    t, lg, lu = ctx.kde_draw(_cuda(box, torch.float64), G, _cuda(C, torch.float64), n, seed, r[0:1], r[1:2])
+    t, lg, lu = ctx.kde_draw(_cuda(box, torch.float64), G, _cuda(C, torch.float64), _cuda(E, torch.float64), n, seed,
+                             r[0:1], r[1:2])
     assert int(r[1]) == 42
     t, lg, lu = t.cpu().numpy().reshape(nw, n, 8), lg.cpu().numpy(), lu.cpu().numpy()
     key = [seed & 0xFFFFFFFF, seed >> 32]
     for w in range(nw):
         for i in list(range(0, n, 97)) + [n - 1]:
             words = sum((philox4x32_10([41, w, i, b], key) for b in range(3)), [])
-            rt, rg, ru = okde.draw(C[w], lo[w], hi[w], G, words)
+            rt, rg, ru = okde.draw(C[w], E[w], lo[w], hi[w], G, words)
             assert np.allclose(t[w, i], rt, rtol=1e-15, atol=0), (w, i, t[w, i], rt)
             assert abs(lg[w, i] - rg) <= 1e-12 * abs(rg) and abs(lu[w, i] - ru) <= 1e-13
     # every draw inside its box
@@ -103,8 +109,10 @@ def test_kde_draw_flat_table_is_uniform(api):
     G = 8
     box = np.concatenate([np.zeros(8), np.arange(1, 9, dtype=float)])[None]
     C = np.stack([okde.cumulative(okde.flat_grid(G))] * 3)[None]
+    E = okde.box_extents(box[0, :8], box[0, 8:])[None]
     r = torch.tensor([0, 0], dtype=torch.int64, device=DEV)
-    t, lg, _ = ctx.kde_draw(_cuda(box, torch.float64), G, _cuda(C, torch.float64), 100000, 3, r[0:1], r[1:2])
+    t, lg, _ = ctx.kde_draw(_cuda(box, torch.float64), G, _cuda(C, torch.float64), _cuda(E, torch.float64), 100000, 3,
+                            r[0:1], r[1:2])
     u = t.cpu().numpy() / np.arange(1, 9)
     assert np.allclose(lg.cpu().numpy(), -math.log(math.factorial(8)), rtol=1e-12)
     assert np.abs(u.mean(0) - 0.5).max() < 0.005 and np.abs(u.var(0) - 1 / 12).max() < 0.002

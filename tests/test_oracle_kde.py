@@ -39,7 +39,7 @@ def test_flat_grid_is_uniform_in_the_box():
     rng = np.random.default_rng(3)
     pts = []
     for _ in range(4000):
-        th, lg, lu = kde.draw(C, lo, hi, G, rng.integers(0, 2 ** 32, 12))
+        th, lg, lu = kde.draw(C, kde.box_extents(lo, hi), lo, hi, G, rng.integers(0, 2 ** 32, 12))
         assert lg == pytest.approx(-math.log(vol), rel=1e-12)
         assert lu < 0
         pts.append(th)
@@ -50,13 +50,18 @@ def test_flat_grid_is_uniform_in_the_box():
 
 
 def test_single_state_puts_the_kde_mass_in_its_cell():
-    # zero spread: no smoothing, every entry in one cell, plus the floor
-    G, eps = 8, 0.05
+    # zero spread: no smoothing, a grid of one box cell either side of the
+    # state (the state in its middle cell), every entry in that cell, plus the floor
+    G, eps = 7, 0.05
     x, y = np.full(50, 0.33), np.full(50, 0.71)
-    P = kde.pair_grid(x, y, 1, (0.0, 1.0), (0.0, 1.0), G, eps)
+    P, (ex, ey) = kde.pair_grid(x, y, 1, (0.0, 1.0), (0.0, 2.0), G, eps)
+    assert ex == pytest.approx((0.33 - 1 / 7, 0.33 + 1 / 7)) and ey == pytest.approx((0.71 - 2 / 7, 0.71 + 2 / 7))
     expect = np.full((G, G), eps / G ** 2)
-    expect[2, 5] += 1 - eps
+    expect[3, 3] += 1 - eps
     assert np.allclose(P, expect, rtol=0, atol=1e-15)
+    # at the box edge the grid is cut to the box
+    _, (ex, _) = kde.pair_grid(np.full(5, 0.01), np.full(5, 0.5), 1, (0.0, 1.0), (0.0, 1.0), G, eps)
+    assert ex == pytest.approx((0.0, 0.01 + 1 / 7))
 
 
 def test_kernel_smoothing_of_one_entry_is_the_discrete_gaussian():
@@ -84,11 +89,14 @@ def test_grid_of_a_gaussian_sample_matches_the_smoothed_gaussian():
     x = rng.normal(0.2, 0.05, n)
     y = rng.normal(-0.1, 0.2, n)
     bx, by = (0.0, 0.4), (-0.9, 0.7)
-    P = kde.pair_grid(x, y, n, bx, by, G, 0.0)
+    P, (gx, gy) = kde.pair_grid(x, y, n, bx, by, G, 0.0)
     h = n ** (-1 / 6)
-    ex = np.linspace(bx[0], bx[1], G + 1)
-    ey = np.linspace(by[0], by[1], G + 1)
-    cx, cy = (bx[1] - bx[0]) / G, (by[1] - by[0]) / G
+    # the grid spans the sample's range +- 3h (and a box cell), inside the box
+    assert gx[0] == pytest.approx(max(bx[0], x.min() - 3 * 0.05 * h - 0.4 / G), rel=1e-6)
+    assert gy[1] == pytest.approx(min(by[1], y.max() + 3 * 0.2 * h + 1.6 / G), rel=1e-6)
+    ex = np.linspace(gx[0], gx[1], G + 1)
+    ey = np.linspace(gy[0], gy[1], G + 1)
+    cx, cy = (gx[1] - gx[0]) / G, (gy[1] - gy[0]) / G
     # histogram binning adds a cell^2/12 variance, the discrete kernel its own
     sx = math.sqrt(0.05 ** 2 * (1 + h ** 2) + cx ** 2 / 12)
     sy = math.sqrt(0.2 ** 2 * (1 + h ** 2) + cy ** 2 / 12)
@@ -118,7 +126,7 @@ def test_draws_follow_the_cell_probabilities():
     counts = np.zeros(G * G)
     m = 40000
     for _ in range(m):
-        th, lg, _ = kde.draw(C, lo, hi, G, rng.integers(0, 2 ** 32, 12))
+        th, lg, _ = kde.draw(C, kde.box_extents(lo, hi), lo, hi, G, rng.integers(0, 2 ** 32, 12))
         i, j = int(th[0] / 2.0 * G), int(th[1] / 4.0 * G)
         counts[i * G + j] += 1
         # log g: the drawn cell's probability over its area, the rest flat
@@ -136,11 +144,13 @@ def test_build_window_uses_the_chain_states():
     chain = np.zeros(n, int)
     chain[200:] = 200                     # two states: proposal 0, then 200
     lo, hi = np.zeros(8), np.ones(8)
-    C = kde.build_window(theta, chain, lo, hi, G, 0.0)
+    C, E = kde.build_window(theta, chain, lo, hi, G, 0.0)
     for p, (dx, dy) in enumerate(kde.PAIRS):
         P = np.diff(np.concatenate([[0.0], C[p]])).reshape(G, G)
-        a = (kde.cell_index(theta[0, dx], 0, 1, G), kde.cell_index(theta[0, dy], 0, 1, G))
-        b = (kde.cell_index(theta[200, dx], 0, 1, G), kde.cell_index(theta[200, dy], 0, 1, G))
+        x0, x1, y0, y1 = E[p]
+        assert x0 <= min(theta[0, dx], theta[200, dx]) and x1 >= max(theta[0, dx], theta[200, dx])
+        a = (kde.cell_index(theta[0, dx], x0, x1, G), kde.cell_index(theta[0, dy], y0, y1, G))
+        b = (kde.cell_index(theta[200, dx], x0, x1, G), kde.cell_index(theta[200, dy], y0, y1, G))
         if a != b:
             assert P[a] == pytest.approx(P[b], rel=1e-9)     # 200 steps each
         assert P.sum() == pytest.approx(1.0)
