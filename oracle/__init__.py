@@ -19,6 +19,7 @@ gb      fast/slow template, naive DFT, window inner products, logL, gradient
 mh      independence Metropolis-Hastings chain (Alg. 4, Eq. 13)
 kde     reduced box and paired 2-D kernel-density proposals of the annealed
         posterior (Sec. III.G, Alg. 4)
+noise   median-periodogram noise estimate of a segment (Sec. III.C)
 brute   brute-force time-domain simulation of the same physics (no fast/slow
         split, exact delays), used only to pin ``gb`` against the physics
 """
