@@ -382,7 +382,8 @@ def run_fullband(args):
     clocks = ClockSampler(dev.index)
     clocks.start()
     st = fullband.run(ctx, n_src=args.fb_sources, rounds=args.fb_rounds, pop=args.fb_pop, generations=args.fb_gens,
-                      phase=not args.fb_no_phase, posterior=args.fb_posterior)
+                      phase=not args.fb_no_phase, posterior=args.fb_posterior, scheme=args.fb_scheme,
+                      noise=args.fb_noise)
     line = {"metric": "total wall time, s per posterior (full-band search)", "workload": "fullband",
             "n_gpus": 1, "unit": "s", "higher_is_better": False, "data": "synthetic",
             "value": st["wall_s"], "s_per_posterior": st["s_per_posterior"],
@@ -410,6 +411,10 @@ def main():
     ap.add_argument("--fb-rounds", type=int, default=3, help="fullband: search-and-subtract rounds")
     ap.add_argument("--fb-pop", type=int, default=1024, help="fullband: GA population per window")
     ap.add_argument("--fb-gens", type=int, default=100, help="fullband: GA generations per round")
+    ap.add_argument("--fb-scheme", default="all", choices=["all", "evenodd"],
+                    help="fullband: all windows at once, or the paper's even/odd runs (Table 2)")
+    ap.add_argument("--fb-noise", default="true", choices=["true", "median"],
+                    help="fullband: weights from the true PSD, or each segment's median periodogram")
     ap.add_argument("--fb-posterior", default="gauss", choices=["gauss", "kde"],
                     help="fullband: Alg. 4 proposals, Gaussian refits or the paper's paired KDEs")
     ap.add_argument("--fb-no-phase", action="store_true",

@@ -356,6 +356,22 @@ int gb_gauss_refit(gb_ctx_t* ctx, int32_t n_win, int32_t n, const double* theta,
  *           - log(phi0 width),   log_u = log u_11.
  * theta n_win x n x 8, log_g, log_u n_win x n (device, written);
  * *round_out = *round_in + 1.  grid in [2, 128], n_win <= 65535. */
+/* Noise estimate within a frequency segment (Sec. III.C): for window w and
+ * channel c (0 = A, 1 = E) the median over the window's W bins of the
+ * periodogram 2 (Re d_k^2 + Im d_k^2) / T_obs (the data are continuous-FT
+ * samples, so this is the paper's 2 |DFT|^2 / (N f_sample)); for even W the
+ * mean of the two middle values.  debias != 0 divides by ln 2 (the median of
+ * an exponential variate is ln 2 times its mean), else the median as printed.
+ *   win        n_win descriptors (HOST array; W <= 4096, data_off + W <= n_bins)
+ *   dA, dE     complex data (device, interleaved, n_bins entries)
+ *   S          n_win x 2 estimates (device, written; NaN for W = 0)
+ *   wA, wE     weights (device, may both be NULL): the window's bins are set
+ *              to 1/S, the segment's constant noise weight
+ * The estimate is re-run after signals are subtracted (the paper's dynamic
+ * noise estimate). */
+int gb_noise_median(gb_ctx_t* ctx, const gb_window_t* win, int32_t n_win, const double* dA, const double* dE,
+                    int64_t n_bins, int32_t debias, double* S, double* wA, double* wE, void* stream);
+
 int gb_kde_build(gb_ctx_t* ctx, int32_t n_win, int32_t n, const double* theta, const int32_t* chain,
                  const double* box, int32_t grid, double floor_mass, double* cdf, double* ext, void* stream);
 int gb_kde_draw(gb_ctx_t* ctx, int32_t n_win, int32_t n, const double* box, int32_t grid, const double* cdf,

@@ -72,6 +72,7 @@ _SIGNATURES = {
                                   ctypes.POINTER(GAParams), _P, _P, _P, _P]),
     "gb_gauss_refit": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_double, _P, _P, _P]),
+    "gb_noise_median": (ctypes.c_int, [_P, ctypes.POINTER(Window), _I32, _P, _P, _I64, _I32, _P, _P, _P, _P]),
     "gb_kde_build": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _I32, ctypes.c_double, _P, _P, _P]),
     "gb_kde_draw": (ctypes.c_int, [_P, _I32, _I32, _P, _I32, _P, _P, ctypes.c_uint64, _P, _P, _P, _P, _P, _P]),
     "gb_philox4x32": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint32, _P, _P]),
@@ -307,6 +308,23 @@ class Context:
                                            int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(round_in), _ptr(round_out),
                                            _ptr(th), _ptr(lg), _ptr(lu), _stream(self.device)))
         return th, lg, lu
+
+    def noise_median(self, windows, dA, dE, debias=False, weights=None):
+        """Median-periodogram noise of every window (see gb_noise_median): S (n_win, 2).
+        weights = (wA, wE) are set to 1/S over each window's bins."""
+        nb = dA.shape[0]
+        _need(dA, torch.complex128, self.device, "dA", (nb,))
+        _need(dE, torch.complex128, self.device, "dE", (nb,))
+        arr, nw = self._windows(windows)
+        S = torch.empty((nw, 2), dtype=torch.float64, device=self.device)
+        wA = wE = None
+        if weights is not None:
+            wA, wE = weights
+            _need(wA, torch.float64, self.device, "wA", (nb,))
+            _need(wE, torch.float64, self.device, "wE", (nb,))
+        self._check(lib().gb_noise_median(self._h, arr, nw, _ptr(dA), _ptr(dE), nb, int(bool(debias)), _ptr(S),
+                                          _ptr(wA), _ptr(wE), _stream(self.device)))
+        return S
 
     def kde_build(self, theta, chain, box, grid, floor, out):
         """Paired KDE proposal tables from each window's chain (see gb_kde_build);

@@ -26,9 +26,12 @@ library's kernels, batched over all windows at once:
   subtract   the recovered templates (``gb_waveform``) leave the window data
              before the next round.
 
-Windows keep their own copies of the data, so a recovered source is removed
-from its window only (the paper's even/odd alternation of neighbouring
-segments is not reproduced).  The module orders calls, moves data and keeps
+Windows keep their own copies of the data; within a run a recovered source is
+removed from its window only.  scheme="evenodd" runs the paper's three runs
+over even and odd segments (Table 2): between runs the other parity's
+signals are subtracted from the whole band and the window copies refreshed.
+noise="median" replaces each searched window's weights by its median
+periodogram (Sec. III.C) before every round.  The module orders calls, moves data and keeps
 statistics; the arithmetic runs in the library.
 """
 import math
@@ -101,6 +104,8 @@ class FullBand:
         # window copies
         gidx = torch.cat([torch.arange(k0 - self.k_lo, k0 - self.k_lo + N, device=self.dev)
                           for k0, N, _, _ in self.layout])
+        self._gidx = gidx
+        self._band0 = (bandA, bandE)
         self.dA = bandA[gidx].contiguous()
         self.dE = bandE[gidx].contiguous()
         self.wA = bandW[gidx].contiguous()
@@ -164,88 +169,175 @@ class FullBand:
         C = C / d[:, :, None] / d[:, None, :]
         return C * s[:, :, None] * s[:, None, :]
 
+    def _wins(self, active, counts=None):
+        """Descriptors of the windows `active` (counts[i] candidates for the i-th, default 0)."""
+        out, coff = [], 0
+        for i, w in enumerate(active):
+            k0, N, _, _ = self.layout[w]
+            c = 0 if counts is None else int(counts[i])
+            out.append((k0, N, N, int(self.doff[w]), coff, c))
+            coff += c
+        return out
+
+    def _refresh(self, active, bandA, bandE):
+        """Window copies of the windows `active` from band arrays."""
+        pos = torch.cat([torch.arange(int(self.doff[w]), int(self.doff[w]) + self.layout[w][1], device=self.dev)
+                         for w in active])
+        self.dA[pos] = bandA[self._gidx[pos]]
+        self.dE[pos] = bandE[self._gidx[pos]]
+
+    def _subtract_windows(self, ws, theta):
+        """Remove templates theta[i] from window ws[i]'s own copy."""
+        for N in sorted({self.layout[w][1] for w in ws}):
+            sel = [i for i, w in enumerate(ws) if self.layout[w][1] == N]
+            th = torch.as_tensor(theta[sel], device=self.dev).contiguous()
+            for j0 in range(0, len(sel), 8192):
+                part = [ws[i] for i in sel[j0:j0 + 8192]]
+                hA, hE, q = self.ctx.waveform(th[j0:j0 + len(part)], N, "fp64")
+                k0 = torch.as_tensor([self.layout[w][0] for w in part], device=self.dev)
+                off = torch.as_tensor([int(self.doff[w]) for w in part], device=self.dev)
+                loc = q[:, None] - N // 2 + torch.arange(N, device=self.dev)[None, :] - k0[:, None]
+                ok = (loc >= 0) & (loc < N)
+                idx = (loc + off[:, None])[ok]
+                for tgt, h in ((self.dA, hA), (self.dE, hE)):
+                    torch.view_as_real(tgt).index_add_(0, idx, -torch.view_as_real(h)[ok])
+
+    def _subtract_band(self, bandA, bandE, found):
+        """band -= templates of found (window, theta) pairs, each at its window's N."""
+        for N in sorted({self.layout[w][1] for w, _ in found}):
+            th = torch.as_tensor(np.array([t for w, t in found if self.layout[w][1] == N]), device=self.dev)
+            self._scatter((bandA, bandE), self.k_lo, th.contiguous(), int(N), -1.0)
+
+    def _posteriors(self, ws, best, boxes, n_post, post_batch, posterior, seed):
+        acc_all = []
+        for i in range(0, len(ws), post_batch):
+            sub = list(ws[i:i + post_batch])
+            win = self._wins(sub)
+            mu = torch.as_tensor(best[i:i + len(sub)], device=self.dev).contiguous()
+            if posterior == "kde":
+                # the paper's proposals: uniform over the reduced box, then paired KDEs
+                sig = np.sqrt(np.diagonal(self._proposal_cov(win, mu, width=1.0), axis1=1, axis2=2))
+                box = reduced_box(best[i:i + len(sub)], sig, boxes[sub, :8], boxes[sub, 8:])
+                ap = KDEPosterior(self.ctx, win, self.dA, self.dE, self.wA, self.wE, box, n=n_post,
+                                  seed=seed + i, prec=self.prec).run()
+                acc = ap.accepted.cpu().numpy()
+            else:
+                cov = self._proposal_cov(win, mu)
+                ap = AnnealedPosterior(self.ctx, win, self.dA, self.dE, self.wA, self.wE, mu, cov, n=n_post,
+                                       seed=seed + i, prec=self.prec).run()
+                acc = ap.rounds.accepted.cpu().numpy()
+            acc_all.extend(int(a) for a in acc)
+            del ap
+        return acc_all
+
+    def _search_windows(self, active, n_rounds, tag, acc, boxes, pop, generations, snr_min, n_post, post_batch,
+                        phase, posterior, noise):
+        """Search-and-subtract in the windows `active` (Alg. 2-3 per window):
+        each round a genetic search in every active window, the polish, and
+        for the windows whose optimum passes the SNR threshold a posterior
+        and the subtraction of its template from the window's copy; a window
+        leaves the active set when a round finds nothing in it.
+        Returns [(window, theta, snr, accepted moves of its posterior)]."""
+        active = np.asarray(active, dtype=int)
+        found = []
+        for r in range(n_rounds):
+            if active.size == 0:
+                break
+            t0 = _sync(self.dev)
+            wins = self._wins(active, [pop] * active.size)
+            if noise == "median":   # the segment noise, updated after every subtraction
+                self.ctx.noise_median(self._wins(active), self.dA, self.dE, debias=True, weights=(self.wA, self.wE))
+            ga = GASearch(self.ctx, wins, self.dA, self.dE, self.wA, self.wE, boxes[active], pop,
+                          seed=self.seed + 17 * (r + 100 * tag), prec=self.prec, phase=phase)
+            best = ga.run(generations, graph=True)
+            del ga
+            # gradient polish of every window's best (stands in for Alg. 2's SLSQP)
+            allw = self._wins(active)
+            th_b, _ = gbag.newton_polish(self.ctx, allw, self.dA, self.dE, self.wA, self.wE,
+                                         torch.as_tensor(best, device=self.dev).contiguous(), prec=self.prec)
+            _, dh, hh = self.ctx.loglik(self._wins(active, [1] * active.size), self.dA, self.dE, self.wA, self.wE,
+                                        th_b.contiguous(), prec=self.prec)
+            best = th_b.cpu().numpy()
+            snr = (dh / torch.sqrt(torch.clamp(hh, min=1e-300))).cpu().numpy()
+            t1 = _sync(self.dev)
+            acc["ga"] += t1 - t0
+            acc["evals"] += pop * active.size * generations
+            hit = np.nonzero(snr > snr_min)[0]
+            if hit.size:
+                ws = active[hit]
+                pa = self._posteriors(ws, best[hit], boxes, n_post, post_batch, posterior,
+                                      self.seed + 1000 * (r + 100 * tag))
+                acc["n_post"] += len(pa)
+                t2 = _sync(self.dev)
+                acc["post_s"] += t2 - t1
+                self._subtract_windows(list(ws), best[hit])
+                acc["sub"] += _sync(self.dev) - t2
+                found.extend((int(w), best[i].copy(), float(snr[i]), a) for w, i, a in zip(ws, hit, pa))
+            active = active[hit]
+        return found
+
     def search(self, rounds=3, pop=1024, generations=100, snr_min=10.0, n_post=10000, post_batch=4096, phase=True,
-               posterior="gauss"):
-        wins = self.windows([pop] * self.n_win)
+               posterior="gauss", scheme="all", noise="true"):
+        """Search every window for up to `rounds` signals.
+
+        scheme="all": all windows at once on their own copies of the data.
+        scheme="evenodd": the paper's three runs (Table 2, Alg. 3): the even
+        segments for up to 3 signals on the data; the odd segments for up to
+        `rounds` signals on the data minus the even runs' signals; the even
+        segments again for up to `rounds` on the data minus the odd
+        segments' signals, except those whose odd neighbours found nothing
+        and that found fewer than 3 (their first-run signals are kept).
+        noise="median": the weights of each searched window are its median
+        periodogram (Sec. III.C), updated after every subtraction."""
         boxes = self.boxes()
         self.stats.update({"rounds": rounds, "pop": pop, "generations": generations, "snr_min": snr_min,
                            "proposals_per_posterior": n_post, "phase_maximised_fitness": phase,
-                           "posterior_proposals": posterior})
+                           "posterior_proposals": posterior, "scheme": scheme, "noise": noise})
+        wins = self.windows([pop] * self.n_win)
         th0 = torch.as_tensor(np.repeat(boxes[:, None, :8], pop, 1).reshape(-1, 8)
                               + np.repeat((boxes[:, None, 8:] - boxes[:, None, :8]) * 0.5, pop, 1).reshape(-1, 8),
                               device=self.dev).contiguous()
         self.stats["autotune"] = self.ctx.autotune(wins, self.dA, self.dE, self.wA, self.wE, th0, prec=self.prec,
                                                    reps=2)
-        found, post = [], []
-        t_ga = t_post = t_sub = 0.0
-        evals = 0
-        for r in range(rounds):
-            t0 = _sync(self.dev)
-            ga = GASearch(self.ctx, wins, self.dA, self.dE, self.wA, self.wE, boxes, pop, seed=self.seed + 17 * r,
-                          prec=self.prec, phase=phase)
-            best = ga.run(generations, graph=True)
-            snr = ga.best_snr()
-            del ga
-            # gradient polish of every window's best (stands in for Alg. 2's SLSQP)
-            allw = [(k0, N, N, int(self.doff[w]), 0, 0) for w, (k0, N, _, _) in enumerate(self.layout)]
-            th_b, _ = gbag.newton_polish(self.ctx, allw, self.dA, self.dE, self.wA, self.wE,
-                                         torch.as_tensor(best, device=self.dev).contiguous(), prec=self.prec)
-            _, dh, hh = self.ctx.loglik([(k0, W, N, doff, w, 1) for w, (k0, W, N, doff, _, _) in enumerate(allw)],
-                                        self.dA, self.dE, self.wA, self.wE, th_b.contiguous(), prec=self.prec)
-            best = th_b.cpu().numpy()
-            snr = (dh / torch.sqrt(torch.clamp(hh, min=1e-300))).cpu().numpy()
-            t1 = _sync(self.dev)
-            t_ga += t1 - t0
-            evals += pop * self.n_win * generations
-            rec = np.nonzero(snr > snr_min)[0]
-            if rec.size == 0:
-                break
-            # posterior rounds for this round's recoveries, in batches
-            for i in range(0, rec.size, post_batch):
-                sub = rec[i:i + post_batch]
-                win = [(self.layout[w][0], self.layout[w][1], self.layout[w][1], int(self.doff[w]), 0, 0)
-                       for w in sub]
-                mu = torch.as_tensor(best[sub], device=self.dev).contiguous()
-                if posterior == "kde":
-                    # the paper's proposals: uniform over the reduced box, then paired KDEs
-                    sig = np.sqrt(np.diagonal(self._proposal_cov(win, mu, width=1.0), axis1=1, axis2=2))
-                    box = reduced_box(best[sub], sig, boxes[sub, :8], boxes[sub, 8:])
-                    ap = KDEPosterior(self.ctx, win, self.dA, self.dE, self.wA, self.wE, box, n=n_post,
-                                      seed=self.seed + 1000 * r + i, prec=self.prec).run()
-                    acc = ap.accepted.cpu().numpy()
-                else:
-                    cov = self._proposal_cov(win, mu)
-                    ap = AnnealedPosterior(self.ctx, win, self.dA, self.dE, self.wA, self.wE, mu, cov, n=n_post,
-                                           seed=self.seed + 1000 * r + i, prec=self.prec).run()
-                    acc = ap.rounds.accepted.cpu().numpy()
-                post.extend(int(a) for a in acc)
-                del ap
-            t2 = _sync(self.dev)
-            t_post += t2 - t1
-            # subtract the recovered templates from their windows
-            for N in sorted({self.layout[w][1] for w in rec}):
-                sel = [w for w in rec if self.layout[w][1] == N]
-                th = torch.as_tensor(best[sel], device=self.dev).contiguous()
-                for j0 in range(0, len(sel), 8192):
-                    part = sel[j0:j0 + 8192]
-                    hA, hE, q = self.ctx.waveform(th[j0:j0 + len(part)], N, "fp64")
-                    k0 = torch.as_tensor([self.layout[w][0] for w in part], device=self.dev)
-                    off = torch.as_tensor([int(self.doff[w]) for w in part], device=self.dev)
-                    loc = q[:, None] - N // 2 + torch.arange(N, device=self.dev)[None, :] - k0[:, None]
-                    ok = (loc >= 0) & (loc < N)
-                    idx = (loc + off[:, None])[ok]
-                    for tgt, h in ((self.dA, hA), (self.dE, hE)):
-                        torch.view_as_real(tgt).index_add_(0, idx, -torch.view_as_real(h)[ok])
-            t_sub += _sync(self.dev) - t2
-            found.extend((r, int(w), best[w].copy(), float(snr[w])) for w in rec)
-        self.found = found
-        self.stats.update({"ga_s": t_ga, "posterior_s": t_post, "subtract_s": t_sub, "ga_evals": evals,
+        acc = {"ga": 0.0, "post_s": 0.0, "sub": 0.0, "evals": 0, "n_post": 0}
+        kw = dict(boxes=boxes, pop=pop, generations=generations, snr_min=snr_min, n_post=n_post,
+                  post_batch=post_batch, phase=phase, posterior=posterior, noise=noise)
+        if scheme == "all":
+            found = self._search_windows(np.arange(self.n_win), rounds, 0, acc, **kw)
+        elif scheme == "evenodd":
+            even, odd = np.arange(0, self.n_win, 2), np.arange(1, self.n_win, 2)
+            run1 = self._search_windows(even, 3, 1, acc, **kw)
+            t = _sync(self.dev)
+            bA, bE = self._band0[0].clone(), self._band0[1].clone()
+            self._subtract_band(bA, bE, [(f[0], f[1]) for f in run1])
+            self._refresh(odd, bA, bE)
+            acc["sub"] += _sync(self.dev) - t
+            run2 = self._search_windows(odd, rounds, 2, acc, **kw)
+            t = _sync(self.dev)
+            n1 = np.bincount([f[0] for f in run1], minlength=self.n_win)
+            n2 = np.bincount([f[0] for f in run2], minlength=self.n_win)
+            redo = np.array([w for w in even if n1[w] >= 3 or (w > 0 and n2[w - 1] > 0) or
+                             (w + 1 < self.n_win and n2[w + 1] > 0)], dtype=int)
+            bA, bE = self._band0[0].clone(), self._band0[1].clone()
+            self._subtract_band(bA, bE, [(f[0], f[1]) for f in run2])
+            if redo.size:
+                self._refresh(redo, bA, bE)
+            acc["sub"] += _sync(self.dev) - t
+            run3 = self._search_windows(redo, rounds, 3, acc, **kw)
+            keep = set(int(w) for w in even) - set(int(w) for w in redo)
+            found = run2 + run3 + [f for f in run1 if f[0] in keep]
+            self.stats.update({"run_signals": [len(run1), len(run2), len(run3)], "even_searched_again": int(redo.size)})
+        else:
+            raise ValueError("scheme must be 'all' or 'evenodd'")
+        self.found = [(0, w, th, s) for w, th, s, _ in found]
+        post = [a for _, _, _, a in found]   # the catalogue's posteriors
+        t_ga, evals = acc["ga"], acc["evals"]
+        self.stats.update({"ga_s": t_ga, "posterior_s": acc["post_s"], "subtract_s": acc["sub"], "ga_evals": evals,
                            "ga_evals_per_s": evals / t_ga if t_ga > 0 else None, "recovered": len(found),
-                           "recovered_per_round": [sum(1 for f in found if f[0] == r) for r in range(rounds)],
-                           "posteriors": len(post),
-                           "s_per_posterior": t_post / len(post) if post else None,
+                           "posteriors": len(post), "posteriors_run": acc["n_post"],
+                           "s_per_posterior": acc["post_s"] / acc["n_post"] if acc["n_post"] else None,
                            "median_accept_rate": float(np.median(post) / n_post) if post else None})
-        return found
+        return self.found
 
     def match(self, snr_inj, owner):
         """How the recoveries sit on the injections: the fractions of recovered
@@ -270,7 +362,8 @@ class FullBand:
 
 
 def run(ctx, n_src=200000, f_lo=0.3e-3, f_hi=15e-3, T=2 * wk.YEAR, rounds=3, pop=1024, generations=100,
-        snr_min=10.0, n_post=10000, seed=wk.SEED_BASE + 5, warm=True, phase=True, posterior="gauss"):
+        snr_min=10.0, n_post=10000, seed=wk.SEED_BASE + 5, warm=True, phase=True, posterior="gauss", scheme="all",
+        noise="true"):
     """Config 5 end to end; returns the statistics (wall times in seconds).
     warm: run a small instance first, so that one-time library initialisation
     (kernel modules, solver handles) is not in the times."""
@@ -278,13 +371,14 @@ def run(ctx, n_src=200000, f_lo=0.3e-3, f_hi=15e-3, T=2 * wk.YEAR, rounds=3, pop
         small = FullBand(ctx, wk.fullband_sources(200, 2e-3, 2.1e-3, seed + 1), wk.fullband_layout(2e-3, 2.1e-3, T),
                          T, seed=seed + 1).synthesize()
         small.injected_snr()
-        small.search(rounds=1, pop=64, generations=4, snr_min=snr_min, n_post=256, posterior=posterior)
+        small.search(rounds=1, pop=64, generations=4, snr_min=snr_min, n_post=256, posterior=posterior,
+                     scheme=scheme, noise=noise)
     t0 = _sync(ctx.device)
     fb = FullBand(ctx, wk.fullband_sources(n_src, f_lo, f_hi, seed), wk.fullband_layout(f_lo, f_hi, T), T,
                   seed=seed).synthesize()
     snr_inj, owner = fb.injected_snr()
     fb.search(rounds=rounds, pop=pop, generations=generations, snr_min=snr_min, n_post=n_post, phase=phase,
-              posterior=posterior)
+              posterior=posterior, scheme=scheme, noise=noise)
     st = dict(fb.stats)
     st.update(fb.match(snr_inj, owner))
     st["wall_s"] = _sync(ctx.device) - t0

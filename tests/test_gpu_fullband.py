@@ -19,9 +19,9 @@ def test_fullband_narrow_band(api):
     # within a bin of an injected source about 2% of the time
     from paper_2307_03763_gb300 import fullband
     ctx = api.Context(2 * wk.YEAR)
-    for post in ("gauss", "kde"):
+    for post, scheme, noise in (("gauss", "all", "true"), ("kde", "all", "true"), ("gauss", "evenodd", "median")):
         st = fullband.run(ctx, n_src=400, f_lo=2e-3, f_hi=2.6e-3, rounds=2, pop=1024, generations=200, n_post=2000,
-                          posterior=post, warm=post == "gauss")
+                          posterior=post, warm=post == "gauss" and scheme == "all", scheme=scheme, noise=noise)
         assert st["windows"] == len(wk.fullband_layout(2e-3, 2.6e-3, 2 * wk.YEAR))
         assert st["recovered"] > 100, st
         assert st["within_1_bin"] >= 0.15 and st["within_3_bins"] >= 0.3, st
