@@ -31,8 +31,8 @@ removed from its window only.  scheme="evenodd" runs the paper's three runs
 over even and odd segments (Table 2): between runs the other parity's
 signals are subtracted from the whole band and the window copies refreshed.
 noise="median" replaces each searched window's weights by its median
-periodogram (Sec. III.C) before every round.  The module orders calls, moves data and keeps
-statistics; the arithmetic runs in the library.
+periodogram (Sec. III.C) before every round.  The module orders calls,
+moves data and keeps statistics; the arithmetic runs in the library.
 """
 import math
 import time
