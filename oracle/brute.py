@@ -61,6 +61,12 @@ def _source(theta):
 
 def tdi_AE_series(theta, t, L):
     """Real TDI A(t), E(t) at the sample times t (1-D array), exact delays."""
+    A, E, _ = tdi_AET_series(theta, t, L)
+    return A, E
+
+
+def tdi_AET_series(theta, t, L):
+    """Real TDI A(t), E(t), T(t) = (X + Y + Z)/sqrt3 at the sample times t."""
     f0, fdot, phi0, khat, H = _source(theta)
     tau = L / C_LIGHT
     # events m = 0..4: time t - m tau, every spacecraft at its position then
@@ -87,7 +93,19 @@ def tdi_AE_series(theta, t, L):
     X = michelson(0, 1, 2)
     Y = michelson(1, 2, 0)
     Z = michelson(2, 0, 1)
-    return (Z - X) / math.sqrt(2.0), (X - 2.0 * Y + Z) / math.sqrt(6.0)
+    return (Z - X) / math.sqrt(2.0), (X - 2.0 * Y + Z) / math.sqrt(6.0), (X + Y + Z) / math.sqrt(3.0)
+
+
+def brute_force_spectrum_aet(theta, T, dt, bins, L=2.5e9, chunk=1 << 16):
+    """brute_force_spectrum() with T: (A~, E~, T~) at the given bins."""
+    n_tot = int(round(T / dt))
+    out = np.empty((3, n_tot))
+    for s in range(0, n_tot, chunk):
+        e = min(n_tot, s + chunk)
+        t = np.arange(s, e, dtype=np.float64) * dt
+        out[:, s:e] = tdi_AET_series(theta, t, L)
+    bins = np.asarray(bins)
+    return tuple(np.fft.rfft(x)[bins] * dt for x in out)
 
 
 def brute_force_spectrum(theta, T, dt, bins, L=2.5e9, chunk=1 << 16):

@@ -52,6 +52,10 @@ R9  Discrete inner product over window bins k in [k0, k0+W):
     template contribute only to <d|d>.
 R10 logL = <d|h> - <h|h>/2 - <d|d>/2 (Eq. 2 expanded; all three restricted
     to the window).
+R11 T = (X + Y + Z)/sqrt3 (Eq. 5).  The paper drops T below f*/2 = c/(4 pi L)
+    because its response is suppressed there (Sec. II); a window uses T when
+    its lowest frequency k0/T is at least f*/2, and its <.|.> then sums A, E
+    and T.
 """
 import math
 
@@ -136,6 +140,14 @@ def slow_part(theta, N, T, L=ARM_L, static=False):
 
     theta: (B, 8) float64 in the order of R1.  Returns q (B,), sA (B, N), sE (B, N).
     """
+    q, sA, sE, _ = slow_part_aet(theta, N, T, L, static)
+    return q, sA, sE
+
+
+def slow_part_aet(theta, N, T, L=ARM_L, static=False):
+    """Heterodyned TDI A, E and T at t_n = n T/N (R5, R6, R8, R11; Eqs. 4-5).
+
+    Returns q (B,), sA, sE, sT (B, N)."""
     theta = torch.as_tensor(theta, dtype=F64)
     f0, fdot, beta, lam, A, iota, psi, phi0 = theta.unbind(-1)
     q, delta = carrier_bin(f0, fdot, T)
@@ -178,7 +190,8 @@ def slow_part(theta, N, T, L=ARM_L, static=False):
     Zc = michelson(2, 0, 1)
     sA = (Zc - Xc) / math.sqrt(2.0)
     sE = (Xc - 2.0 * Yc + Zc) / math.sqrt(6.0)
-    return q, sA, sE
+    sT = (Xc + Yc + Zc) / math.sqrt(3.0)
+    return q, sA, sE, sT
 
 
 def dft_centered(s):
@@ -204,6 +217,18 @@ def template(theta, N, T, L=ARM_L, static=False):
     q, sA, sE = slow_part(theta, N, T, L, static)
     scale = T / (2.0 * N)
     return q, scale * dft_centered(sA), scale * dft_centered(sE)
+
+
+def template_aet(theta, N, T, L=ARM_L, static=False):
+    """template() with the T channel: q, hA, hE, hT (R8, R11)."""
+    q, sA, sE, sT = slow_part_aet(theta, N, T, L, static)
+    scale = T / (2.0 * N)
+    return q, scale * dft_centered(sA), scale * dft_centered(sE), scale * dft_centered(sT)
+
+
+def uses_t(k0, T, L=ARM_L):
+    """R11: the window's lowest frequency k0/T is at least f*/2."""
+    return k0 / T >= 0.5 * transfer_frequency(L)
 
 
 def window_inner_products(k0, dA, dE, wA, wE, q, hA, hE, T):
@@ -258,6 +283,32 @@ def loglik(windows, dA, dE, wA, wE, theta, T, L=ARM_L, chunk=2048):
         logL = logL.index_put((idx,), torch.cat([p[2] for p in parts.values()]))
         DH = DH.index_put((idx,), torch.cat([p[3] for p in parts.values()]))
         HH = HH.index_put((idx,), torch.cat([p[4] for p in parts.values()]))
+    return logL, DH, HH
+
+
+def loglik_aet(windows, dA, dE, dT, wA, wE, wT, theta, T, L=ARM_L, chunk=2048):
+    """loglik() with the T channel in the windows above f*/2 (R11); dT, wT
+    alongside dA, wA.  Returns logL, dh, hh."""
+    theta = torch.as_tensor(theta, dtype=F64)
+    dA, dE, dT = (torch.as_tensor(x, dtype=C128) for x in (dA, dE, dT))
+    wA, wE, wT = (torch.as_tensor(x, dtype=F64) for x in (wA, wE, wT))
+    n_total = theta.shape[0]
+    logL = torch.zeros(n_total, dtype=F64)
+    DH = torch.zeros(n_total, dtype=F64)
+    HH = torch.zeros(n_total, dtype=F64)
+    for (k0, W, N, doff, coff, nc) in windows:
+        sl = slice(doff, doff + W)
+        for c0 in range(coff, coff + nc, chunk):
+            c1 = min(c0 + chunk, coff + nc)
+            q, hA, hE, hT = template_aet(theta[c0:c1], N, T, L)
+            dh, hh, dd = window_inner_products(k0, dA[sl], dE[sl], wA[sl], wE[sl], q, hA, hE, T)
+            if uses_t(k0, T, L):
+                dht, hht, ddt = window_inner_products(k0, dT[sl], dT[sl] * 0, wT[sl], wT[sl] * 0, q, hT,
+                                                      hT * 0, T)
+                dh, hh, dd = dh + dht, hh + hht, dd + ddt
+            logL[c0:c1] = dh - 0.5 * hh - 0.5 * dd
+            DH[c0:c1] = dh
+            HH[c0:c1] = hh
     return logL, DH, HH
 
 

@@ -413,3 +413,99 @@ def test_gradient_closed_forms_for_amplitude_and_phase():
         hA, hE = _data.template_on_window(th[b], k0, W, N, wl.T)
         ref = (4 / wl.T) * (np.sum(wl.w_A * (dA * hA.conj()).imag) + np.sum(wl.w_E * (dE * hE.conj()).imag))
         assert abs(float(g[b, 7]) - ref) <= 1e-10 * abs(ref)
+
+
+# --------------------------------------------------------------------------
+# the T channel (Eq. 5, reading R11)
+# --------------------------------------------------------------------------
+
+@pytest.mark.slow
+def test_t_channel_matches_brute_force():
+    # 14 mHz, on a bin, T = 1 yr: T is about 1% of A there; the oracle's T
+    # agrees with the exact-delay simulation to the fast/slow split's
+    # O(1e-4) of the A scale (0.6% of T's own); a sign slip in X + Y + Z
+    # (e.g. X - Y + Z) fails by O(1)
+    T = YEAR
+    N, dt = 256, 15.0
+    q = round(14e-3 * T)
+    th = np.array([q / T, 0.0, 0.4, 1.3, 1e-22, 0.9, 0.3, 1.7])
+    qq, hA, hE, hT = gb.template_aet(torch.tensor(th[None]), N, T)
+    qq = int(qq[0])
+    bA, bE, bT = brute.brute_force_spectrum_aet(th, T, dt, np.arange(qq - N // 2, qq + N // 2))
+    sA, sT = np.abs(bA).max(), np.abs(bT).max()
+    assert 0.005 < sT / sA < 0.03
+    err = np.abs(hT[0].numpy() - bT).max()
+    assert err < 3e-4 * sA and err < 0.02 * sT, (err / sA, err / sT)
+
+
+def test_t_channel_is_suppressed_below_half_the_transfer_frequency():
+    # the paper's reason for dropping T below f*/2 (Sec. II): its response
+    # grows steeply with f and stays below 1% of A's below f*/2
+    rng = np.random.default_rng(21)
+    th = torch.tensor(_theta(rng, f0=1e-3)[None])
+    ratio = []
+    for f in (1e-3, 2e-3, 4e-3, 0.5 * gb.transfer_frequency()):
+        th[0, 0] = f
+        _, hA, _, hT = gb.template_aet(th, 256, YEAR)
+        ratio.append(float(hT.abs().max() / hA.abs().max()))
+    assert all(b > 4 * a for a, b in zip(ratio, ratio[1:])), ratio
+    assert ratio[-1] < 0.01, ratio
+
+
+def test_t_channel_carries_the_global_phase_and_is_linear_in_amplitude():
+    rng = np.random.default_rng(22)
+    th = torch.tensor(_theta(rng, f0=12e-3)[None])
+    _, _, _, hT = gb.template_aet(th, 256, YEAR)
+    th2 = th.clone()
+    th2[0, 7] += 0.6
+    th2[0, 4] *= 3.0
+    _, _, _, hT2 = gb.template_aet(th2, 256, YEAR)
+    assert (hT2 - 3.0 * np.exp(0.6j) * hT).abs().max() < 1e-12 * hT.abs().max()
+
+
+def _t_window(seed, f0):
+    rng = np.random.default_rng(seed)
+    T, N = YEAR, 256
+    src = _theta(rng, f0=f0)
+    q = int(gb.carrier_bin(torch.tensor([src[0]]), torch.tensor([src[1]]), T)[0][0])
+    k0, W = q - N // 2 + 7, N
+    th = np.stack([src] + [src + rng.normal(0, 1, 8) * np.array([0.2 / T, 0, 0.01, 0.01, 1e-24, 0.01, 0.01, 0.05])
+                           for _ in range(5)])
+    _, hA, hE, hT = gb.template_aet(torch.tensor(src[None]), N, T)
+    w = [np.full(W, 1e42), np.full(W, 2e42), np.full(W, 5e41)]
+    d = []
+    for h, wt in zip((hA, hE, hT), w):
+        x = np.zeros(W, np.complex128)
+        x[:N - 7] = h[0].numpy()[7:]
+        sd = np.sqrt(T / (4 * wt[0]))      # Re, Im ~ N(0, T S / 4), S = 1/w
+        d.append(x + (rng.normal(size=W) + 1j * rng.normal(size=W)) * sd)
+    return T, N, [(k0, W, N, 0, 0, len(th))], th, d, w
+
+
+def test_loglik_with_t_is_the_three_channel_residual_norm():
+    T, N, win, th, d, w = _t_window(31, 12e-3)
+    assert gb.uses_t(win[0][0], T)
+    logL, dh, hh = gb.loglik_aet(win, *d, *w, th, T)
+    k0 = win[0][0]
+    for b in range(len(th)):
+        _, hA, hE, hT = gb.template_aet(torch.tensor(th[b:b + 1]), N, T)
+        q = int(gb.carrier_bin(torch.tensor([th[b, 0]]), torch.tensor([th[b, 1]]), T)[0][0])
+        ref = 0.0
+        for x, wt, h in zip(d, w, (hA, hE, hT)):
+            hw = np.zeros(N, np.complex128)
+            j = q - N // 2 + np.arange(N) - k0
+            ok = (j >= 0) & (j < N)
+            hw[j[ok]] = h[0].numpy()[ok]
+            ref += -0.5 * (4 / T) * np.sum(wt * np.abs(x - hw) ** 2)
+        assert abs(float(logL[b]) - ref) <= 1e-10 * abs(ref)
+    # the T channel adds to <h|h>
+    _, _, hh_ae = gb.loglik(win, d[0], d[1], w[0], w[1], th, T)
+    assert (hh > hh_ae).all()
+
+
+def test_loglik_with_t_reduces_to_a_and_e_below_half_the_transfer_frequency():
+    T, N, win, th, d, w = _t_window(32, 6e-3)
+    assert not gb.uses_t(win[0][0], T)
+    a = gb.loglik_aet(win, *d, *w, th, T)
+    b = gb.loglik(win, d[0], d[1], w[0], w[1], th, T)
+    assert all(torch.equal(x, y) for x, y in zip(a, b))
