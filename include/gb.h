@@ -142,6 +142,11 @@ int gb_ctx_check(gb_ctx_t* ctx);
 int gb_waveform(gb_ctx_t* ctx, int prec, const double* theta, int64_t B, int32_t N,
                 double* hA, double* hE, int64_t* q, void* stream);
 
+/* gb_waveform with the T channel, hT laid out like hA (B x N complex,
+ * device, written).  prec must be GB_FP64 (else GB_EINVAL). */
+int gb_waveform_aet(gb_ctx_t* ctx, int prec, const double* theta, int64_t B, int32_t N,
+                    double* hA, double* hE, double* hT, int64_t* q, void* stream);
+
 /* Batched log-likelihood over windows (Eq. 2 restricted to each window,
  * Sec. III.D):  logL = <d|h> - <h|h>/2 - <d|d>/2.
  *   win        n_win descriptors (HOST array, read during the call)
@@ -162,6 +167,19 @@ int gb_loglik(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win,
               const double* dA, const double* dE, const double* wA, const double* wE,
               int64_t n_bins, const double* theta, int64_t n_rows,
               double* logL, double* dh, double* hh, void* stream);
+
+/* gb_loglik with the T channel T = (X + Y + Z)/sqrt3 (Eq. 5).  The paper
+ * keeps T only above half the transfer frequency, f* / 2 = c/(4 pi L), where
+ * its response is not suppressed (Sec. II): a window whose lowest frequency
+ * k0/T_obs is at least f* / 2 sums A, E and T in every inner product
+ * (including <d|d>); the others use A and E only.  dT (complex, interleaved)
+ * and wT (1/S_T) are laid out like dA and wA (device, n_bins entries, not
+ * NULL).  Everything else as gb_loglik.  The mixed path transforms T
+ * through the same packed kernel, paired with zero. */
+int gb_loglik_aet(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win,
+                  const double* dA, const double* dE, const double* dT, const double* wA, const double* wE,
+                  const double* wT, int64_t n_bins, const double* theta, int64_t n_rows,
+                  double* logL, double* dh, double* hh, void* stream);
 
 /* gb_loglik plus the imaginary part of the data-template product,
  *   dh_im = (4/T) Im sum_k w_k d_k h_k*    (device, n_rows, written; not NULL)

@@ -61,6 +61,9 @@ _SIGNATURES = {
     "gb_waveform": (ctypes.c_int, [_P, ctypes.c_int, _P, _I64, _I32, _P, _P, _P, _P]),
     "gb_loglik": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _I64, _P, _I64,
                                  _P, _P, _P, _P]),
+    "gb_loglik_aet": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _P, _P, _I64,
+                                     _P, _I64, _P, _P, _P, _P]),
+    "gb_waveform_aet": (ctypes.c_int, [_P, ctypes.c_int, _P, _I64, _I32, _P, _P, _P, _P, _P]),
     "gb_loglik_phase": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _I64, _P,
                                        _I64, _P, _P, _P, _P, _P]),
     "gb_loglik_grad": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _I64, _P,
@@ -219,6 +222,33 @@ class Context:
         self._check(lib().gb_loglik(self._h, PRECISIONS[prec], arr, nw, _ptr(dA), _ptr(dE), _ptr(wA), _ptr(wE),
                                     nb, _ptr(theta), n, _ptr(logL), _ptr(dh), _ptr(hh), _stream(self.device)))
         return logL, dh, hh
+
+    def loglik_aet(self, windows, dA, dE, dT, wA, wE, wT, theta, prec="fp64", out=None):
+        """logL, <d|h>, <h|h> with the T channel in the windows above f*/2 (see gb_loglik_aet)."""
+        arr, nw, nb, n = self._data_args(windows, dA, dE, wA, wE, theta)
+        _need(dT, torch.complex128, self.device, "dT", (nb,))
+        _need(wT, torch.float64, self.device, "wT", (nb,))
+        if out is None:
+            out = tuple(torch.zeros(n, dtype=torch.float64, device=self.device) for _ in range(3))
+        logL, dh, hh = out
+        for t, name in ((logL, "logL"), (dh, "dh"), (hh, "hh")):
+            if t is not None:
+                _need(t, torch.float64, self.device, name, (n,))
+        self._check(lib().gb_loglik_aet(self._h, PRECISIONS[prec], arr, nw, _ptr(dA), _ptr(dE), _ptr(dT), _ptr(wA),
+                                        _ptr(wE), _ptr(wT), nb, _ptr(theta), n, _ptr(logL), _ptr(dh), _ptr(hh),
+                                        _stream(self.device)))
+        return logL, dh, hh
+
+    def waveform_aet(self, theta, N):
+        """A/E/T templates (FP64): hA, hE, hT (B, N) complex128, q (B,) int64."""
+        B = theta.shape[0] if theta.dim() == 2 else -1
+        _need(theta, torch.float64, self.device, "theta", (B, 8))
+        hA = torch.empty((B, N), dtype=torch.complex128, device=self.device)
+        hE, hT = torch.empty_like(hA), torch.empty_like(hA)
+        q = torch.empty(B, dtype=torch.int64, device=self.device)
+        self._check(lib().gb_waveform_aet(self._h, PRECISIONS["fp64"], _ptr(theta), B, int(N), _ptr(hA), _ptr(hE),
+                                          _ptr(hT), _ptr(q), _stream(self.device)))
+        return hA, hE, hT, q
 
     def loglik_phase(self, windows, dA, dE, wA, wE, theta, prec="fp64", out=None):
         """logL, <d|h>, <d|h>_im, <h|h> per candidate (see gb_loglik_phase)."""

@@ -45,7 +45,8 @@ int tile_size(gb_ctx* ctx, int64_t total, int warps) {
 
 int loglik_impl(gb_ctx_t* ctx, const char* name, int prec, const gb_window_t* win, int32_t n_win, const double* dA,
                 const double* dE, const double* wA, const double* wE, int64_t n_bins, const double* theta,
-                int64_t n_rows, double* logL, double* dh, double* dh_im, double* hh, void* stream) {
+                int64_t n_rows, double* logL, double* dh, double* dh_im, double* hh, void* stream,
+                const double* dT = nullptr, const double* wT = nullptr) {
     if (!ctx) return GB_EINVAL;
     if (prec != GB_FP64 && prec != GB_MIXED) return set_error(ctx, GB_EINVAL, std::string(name) + ": unknown precision");
     int64_t total = 0;
@@ -67,8 +68,9 @@ int loglik_impl(gb_ctx_t* ctx, const char* name, int prec, const gb_window_t* wi
     rc = get_plan(ctx, prec, win, n_win, prec == GB_MIXED ? item : tile, &plan);
     if (rc != GB_OK) return rc;
     if (prec == GB_FP64)
-        return launch_loglik_fp64(ctx, *plan, dA, dE, wA, wE, theta, logL, dh, hh, dh_im, (cudaStream_t)stream);
-    return launch_loglik_mixed(ctx, *plan, dA, dE, wA, wE, theta, logL, dh, hh, dh_im, (cudaStream_t)stream);
+        return launch_loglik_fp64(ctx, *plan, dA, dE, wA, wE, theta, logL, dh, hh, dh_im, dT, wT,
+                                  (cudaStream_t)stream);
+    return launch_loglik_mixed(ctx, *plan, dA, dE, wA, wE, theta, logL, dh, hh, dh_im, dT, wT, (cudaStream_t)stream);
 }
 
 }  // namespace
@@ -80,6 +82,15 @@ int gb_loglik(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win, co
               int64_t n_rows, double* logL, double* dh, double* hh, void* stream) {
     return loglik_impl(ctx, "gb_loglik", prec, win, n_win, dA, dE, wA, wE, n_bins, theta, n_rows, logL, dh, nullptr,
                        hh, stream);
+}
+
+int gb_loglik_aet(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win, const double* dA,
+                  const double* dE, const double* dT, const double* wA, const double* wE, const double* wT,
+                  int64_t n_bins, const double* theta, int64_t n_rows, double* logL, double* dh, double* hh,
+                  void* stream) {
+    if (ctx && (!dT || !wT)) return set_error(ctx, GB_EINVAL, "gb_loglik_aet: dT and wT are required");
+    return loglik_impl(ctx, "gb_loglik_aet", prec, win, n_win, dA, dE, wA, wE, n_bins, theta, n_rows, logL, dh,
+                       nullptr, hh, stream, dT, wT);
 }
 
 int gb_loglik_phase(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win, const double* dA,
@@ -185,6 +196,19 @@ int gb_autotune(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win, 
     return GB_OK;
 }
 
+int gb_waveform_aet(gb_ctx_t* ctx, int prec, const double* theta, int64_t B, int32_t N, double* hA, double* hE,
+                    double* hT, int64_t* q, void* stream) {
+    if (!ctx) return GB_EINVAL;
+    if (prec != GB_FP64) return set_error(ctx, GB_EINVAL, "gb_waveform_aet: the T channel template is FP64 only");
+    if (B < 0) return set_error(ctx, GB_EINVAL, "gb_waveform_aet: B < 0");
+    if (!valid_size(N)) return set_error(ctx, GB_EINVAL, "gb_waveform_aet: N must be a power of two in [32, 1024]");
+    if (B == 0) return GB_OK;
+    if (!theta || !hA || !hE || !hT || !q) return set_error(ctx, GB_EINVAL, "gb_waveform_aet: null pointer");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_waveform_aet: cudaSetDevice");
+    return launch_waveform_fp64(ctx, theta, B, N, hA, hE, hT, q, (cudaStream_t)stream);
+}
+
 int gb_waveform(gb_ctx_t* ctx, int prec, const double* theta, int64_t B, int32_t N, double* hA, double* hE,
                 int64_t* q, void* stream) {
     if (!ctx) return GB_EINVAL;
@@ -195,7 +219,7 @@ int gb_waveform(gb_ctx_t* ctx, int prec, const double* theta, int64_t B, int32_t
     if (!theta || !hA || !hE || !q) return set_error(ctx, GB_EINVAL, "gb_waveform: null pointer");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_error(ctx, e, "gb_waveform: cudaSetDevice");
-    if (prec == GB_FP64) return launch_waveform_fp64(ctx, theta, B, N, hA, hE, q, (cudaStream_t)stream);
+    if (prec == GB_FP64) return launch_waveform_fp64(ctx, theta, B, N, hA, hE, nullptr, q, (cudaStream_t)stream);
     return launch_waveform_mixed(ctx, theta, B, N, hA, hE, q, (cudaStream_t)stream);
 }
 

@@ -186,12 +186,15 @@ static cudaError_t alloc_mixed_scratch(Plan& p, const gb_window_t* win, int n_wi
         meta[w].dd = 0.0;
         meta[w].sig = 1.0;
         meta[w].prep_off = off;
+        meta[w].use_t = 0;
+        meta[w].pad = 0;
         off += win[w].W;
     }
     p.n_prep = off;
     cudaError_t e = cudaMalloc(&p.d_meta, sizeof(WinMeta) * meta.size());
     if (e == cudaSuccess) e = cudaMemcpy(p.d_meta, meta.data(), sizeof(WinMeta) * meta.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&p.d_prep, sizeof(Win32) * (size_t)(off > 0 ? off : 1));
+    // float window copies: A and E, then T (filled only when the T channel is given)
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_prep, 2 * sizeof(Win32) * (size_t)(off > 0 ? off : 1));
     if (e == cudaSuccess) e = cudaMalloc(&p.d_head, 2 * sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p.d_head, 0, 2 * sizeof(int));
     return e;

@@ -148,9 +148,10 @@ __device__ __forceinline__ C64 link64(double a, double X, C64 G, C64 rx) {
 // an in-place radix-2 FFT -> natural-order DFT S_k, k = 0..N-1.  The receiver
 // phases reach ~1e6 rad; taken in cycles and reduced modulo one first, their
 // sines come from a short argument.
+// bufT (may be null): also T = (X + Y + Z)/sqrt3
 template <int J>
 __device__ void template64(const Cand64& c, const Geo64& g, const OrbitTables64& tab, const C64* tw,
-                           C64* bufA, C64* bufE, int lane) {
+                           C64* bufA, C64* bufE, C64* bufT, int lane) {
     const int N = g.N;
     const double inv_c = 1.0 / kC;
     const double u_step = 1.0 / (double)N;   // t/T = n/N exactly
@@ -217,6 +218,10 @@ __device__ void template64(const Cand64& c, const Geo64& g, const OrbitTables64&
         const int br = (int)(__brev((unsigned)n) >> (32 - g.logN));
         bufA[br] = sA;
         bufE[br] = sE;
+        if (bufT) {
+            const double r3 = 0.57735026918962576;   // 1/sqrt(3)
+            bufT[br] = {(X.x + Y.x + Z.x) * r3, (X.y + Y.y + Z.y) * r3};
+        }
     }
     __syncwarp();
     // radix-2 decimation in time, bit-reversed input, natural-order output
@@ -234,19 +239,24 @@ __device__ void template64(const Cand64& c, const Geo64& g, const OrbitTables64&
             const C64 ue = bufE[i0], ve = cmul(w, bufE[i1]);
             bufE[i0] = cadd(ue, ve);
             bufE[i1] = csub(ue, ve);
+            if (bufT) {
+                const C64 ut = bufT[i0], vt = cmul(w, bufT[i1]);
+                bufT[i0] = cadd(ut, vt);
+                bufT[i1] = csub(ut, vt);
+            }
         }
         __syncwarp();
     }
 }
 
 __device__ void template64_dispatch(const Cand64& c, const Geo64& g, const OrbitTables64& tab, const C64* tw,
-                                    C64* bufA, C64* bufE, int lane) {
+                                    C64* bufA, C64* bufE, C64* bufT, int lane) {
     switch (c.J) {
-        case 6: template64<6>(c, g, tab, tw, bufA, bufE, lane); break;
-        case 8: template64<8>(c, g, tab, tw, bufA, bufE, lane); break;
-        case 12: template64<12>(c, g, tab, tw, bufA, bufE, lane); break;
-        case 16: template64<16>(c, g, tab, tw, bufA, bufE, lane); break;
-        default: template64<0>(c, g, tab, tw, bufA, bufE, lane); break;
+        case 6: template64<6>(c, g, tab, tw, bufA, bufE, bufT, lane); break;
+        case 8: template64<8>(c, g, tab, tw, bufA, bufE, bufT, lane); break;
+        case 12: template64<12>(c, g, tab, tw, bufA, bufE, bufT, lane); break;
+        case 16: template64<16>(c, g, tab, tw, bufA, bufE, bufT, lane); break;
+        default: template64<0>(c, g, tab, tw, bufA, bufE, bufT, lane); break;
     }
 }
 
@@ -260,23 +270,31 @@ __global__ void __launch_bounds__(kWarps64 * 32) loglik64_kernel(
     const C64* __restrict__ tw_g, double T, double fstar, const C64* __restrict__ dA,
     const C64* __restrict__ dE, const double* __restrict__ wA, const double* __restrict__ wE,
     const double* __restrict__ theta, double* __restrict__ logL, double* __restrict__ dh_out,
-    double* __restrict__ hh_out, double* __restrict__ dhi_out, int* status, int n_max) {
+    double* __restrict__ hh_out, double* __restrict__ dhi_out, const C64* __restrict__ dT,
+    const double* __restrict__ wT, int* status, int n_max) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C64* tw = (C64*)smem_raw;                                   // kTwiddles
     double* red = (double*)(tw + kTwiddles);                    // kWarps64
     Cand64* cands = (Cand64*)(red + kWarps64);                  // kWarps64 * 32
-    C64* bufs = (C64*)(cands + kWarps64 * 32);                  // kWarps64 * 2 * n_max
+    C64* bufs = (C64*)(cands + kWarps64 * 32);                  // kWarps64 * (2 or 3) * n_max
+    const int nch = dT ? 3 : 2;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Tile tile = tiles[blockIdx.x];
     const gb_window_t win = wins[tile.win];
     for (int i = threadIdx.x; i < kTwiddles; i += blockDim.x) tw[i] = tw_g[i];
 
+    // T enters windows whose lowest frequency is at least f*/2
+    const bool useT = dT != nullptr && (double)win.k0 / T >= 0.5 * fstar;
     // <d|d> over the window, block-wide (fixed order -> deterministic)
     double acc = 0.0;
     for (int i = threadIdx.x; i < win.W; i += blockDim.x) {
         const C64 a = dA[win.data_off + i], e = dE[win.data_off + i];
         acc += wA[win.data_off + i] * (a.x * a.x + a.y * a.y) + wE[win.data_off + i] * (e.x * e.x + e.y * e.y);
+        if (useT) {
+            const C64 t = dT[win.data_off + i];
+            acc += wT[win.data_off + i] * (t.x * t.x + t.y * t.y);
+        }
     }
     acc = warp_sum(acc);
     if (lane == 0) red[warp] = acc;
@@ -293,8 +311,9 @@ __global__ void __launch_bounds__(kWarps64 * 32) loglik64_kernel(
     g.inv_fstar = 1.0 / fstar;
     g.scale = T / (2.0 * (double)win.N);
     const OrbitTables64 tab = tabs.t[g.logN - 5];
-    C64* bufA = bufs + (size_t)warp * 2 * n_max;
+    C64* bufA = bufs + (size_t)warp * nch * n_max;
     C64* bufE = bufA + n_max;
+    C64* bufT = useT ? bufE + n_max : nullptr;
     Cand64* mycand = cands + warp * 32;
 
     const int64_t tlen = tile.c_end - tile.c_begin;
@@ -317,7 +336,7 @@ __global__ void __launch_bounds__(kWarps64 * 32) loglik64_kernel(
             }
             continue;
         }
-        template64_dispatch(c, g, tab, tw, bufA, bufE, lane);
+        template64_dispatch(c, g, tab, tw, bufA, bufE, bufT, lane);
         double sdh = 0.0, shh = 0.0, sdhi = 0.0;
         for (int m = lane; m < win.N; m += 32) {
             const int64_t kk = c.q - half + m - win.k0;
@@ -329,6 +348,13 @@ __global__ void __launch_bounds__(kWarps64 * 32) loglik64_kernel(
                 sdh += wa * (a.x * hA.x + a.y * hA.y) + we * (e.x * hE.x + e.y * hE.y);
                 shh += wa * (hA.x * hA.x + hA.y * hA.y) + we * (hE.x * hE.x + hE.y * hE.y);
                 if (dhi_out) sdhi += wa * (a.y * hA.x - a.x * hA.y) + we * (e.y * hE.x - e.x * hE.y);
+                if (useT) {
+                    const C64 hT = cscale(bufT[idx], g.scale), t = dT[win.data_off + kk];
+                    const double wt = wT[win.data_off + kk];
+                    sdh += wt * (t.x * hT.x + t.y * hT.y);
+                    shh += wt * (hT.x * hT.x + hT.y * hT.y);
+                    if (dhi_out) sdhi += wt * (t.y * hT.x - t.x * hT.y);
+                }
             }
         }
         sdh = warp_sum(sdh) * (4.0 / T);
@@ -347,7 +373,7 @@ __global__ void __launch_bounds__(kWarps64 * 32) loglik64_kernel(
 __global__ void __launch_bounds__(kWarps64 * 32) waveform64_kernel(
     OrbitTables64 tab, const C64* __restrict__ tw_g, double T, double fstar, int N,
     const double* __restrict__ theta, int64_t B, int group, C64* __restrict__ hA, C64* __restrict__ hE,
-    int64_t* __restrict__ q_out, int* status) {
+    C64* __restrict__ hT, int64_t* __restrict__ q_out, int* status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C64* tw = (C64*)smem_raw;
     Cand64* cands = (Cand64*)(tw + kTwiddles);
@@ -362,8 +388,9 @@ __global__ void __launch_bounds__(kWarps64 * 32) waveform64_kernel(
     g.T_over_N = T / (double)N;
     g.inv_fstar = 1.0 / fstar;
     g.scale = T / (2.0 * (double)N);
-    C64* bufA = bufs + (size_t)warp * 2 * N;
+    C64* bufA = bufs + (size_t)warp * (hT ? 3 : 2) * N;
     C64* bufE = bufA + N;
+    C64* bufT = hT ? bufE + N : nullptr;
     Cand64* mycand = cands + warp * 32;
     const int64_t c_lo = ((int64_t)blockIdx.x * kWarps64 + warp) * group;
     const int64_t c_hi = min(B, c_lo + group);
@@ -375,18 +402,22 @@ __global__ void __launch_bounds__(kWarps64 * 32) waveform64_kernel(
         C64* outA = hA + b * N;
         C64* outE = hE + b * N;
         if (c.bad) {
-            for (int m = lane; m < N; m += 32) outA[m] = outE[m] = C64{nan(""), nan("")};
+            for (int m = lane; m < N; m += 32) {
+                outA[m] = outE[m] = C64{nan(""), nan("")};
+                if (hT) hT[b * N + m] = C64{nan(""), nan("")};
+            }
             if (lane == 0) {
                 q_out[b] = 0;
                 atomicOr(status, kStatusNonFinite);
             }
             continue;
         }
-        template64_dispatch(c, g, tab, tw, bufA, bufE, lane);
+        template64_dispatch(c, g, tab, tw, bufA, bufE, bufT, lane);
         for (int m = lane; m < N; m += 32) {
             const int idx = (m + N / 2) & (N - 1);
             outA[m] = cscale(bufA[idx], g.scale);
             outE[m] = cscale(bufE[idx], g.scale);
+            if (hT) hT[b * N + m] = cscale(bufT[idx], g.scale);
         }
         if (lane == 0) q_out[b] = c.q;
         __syncwarp();
@@ -395,22 +426,23 @@ __global__ void __launch_bounds__(kWarps64 * 32) waveform64_kernel(
 
 }  // namespace
 
-static size_t smem64_loglik(int n_max) {
+static size_t smem64_loglik(int n_max, int nch) {
     return sizeof(C64) * kTwiddles + sizeof(double) * kWarps64 + sizeof(Cand64) * kWarps64 * 32 +
-           sizeof(C64) * kWarps64 * 2 * (size_t)n_max;
+           sizeof(C64) * kWarps64 * nch * (size_t)n_max;
 }
 
 int launch_loglik_fp64(gb_ctx* ctx, const Plan& plan, const double* dA, const double* dE,
                        const double* wA, const double* wE, const double* theta, double* logL,
-                       double* dh, double* hh, double* dh_im, cudaStream_t s) {
+                       double* dh, double* hh, double* dh_im, const double* dT, const double* wT,
+                       cudaStream_t s) {
     if (plan.n_tiles == 0) return GB_OK;
-    const size_t smem = smem64_loglik(plan.n_max);
+    const size_t smem = smem64_loglik(plan.n_max, dT ? 3 : 2);
     cudaError_t e = cudaFuncSetAttribute(loglik64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_error(ctx, e, "loglik64: smem attribute");
     loglik64_kernel<<<plan.n_tiles, kWarps64 * 32, smem, s>>>(
         plan.d_win, plan.d_tiles, tabset64(ctx), (const C64*)ctx->d_tw64, ctx->obs.T_obs,
         transfer_frequency(ctx), (const C64*)dA, (const C64*)dE, wA, wE, theta, logL, dh, hh,
-        dh_im, ctx->d_status, plan.n_max);
+        dh_im, (const C64*)dT, wT, ctx->d_status, plan.n_max);
     ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "loglik64 launch");
@@ -418,10 +450,10 @@ int launch_loglik_fp64(gb_ctx* ctx, const Plan& plan, const double* dA, const do
 }
 
 int launch_waveform_fp64(gb_ctx* ctx, const double* theta, int64_t B, int N, double* hA, double* hE,
-                         int64_t* q, cudaStream_t s) {
+                         double* hT, int64_t* q, cudaStream_t s) {
     if (B == 0) return GB_OK;
     const size_t smem = sizeof(C64) * kTwiddles + sizeof(Cand64) * kWarps64 * 32 +
-                        sizeof(C64) * kWarps64 * 2 * (size_t)N;
+                        sizeof(C64) * kWarps64 * (hT ? 3 : 2) * (size_t)N;
     cudaError_t e = cudaFuncSetAttribute(waveform64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_error(ctx, e, "waveform64: smem attribute");
     int sms = 152;
@@ -431,7 +463,7 @@ int launch_waveform_fp64(gb_ctx* ctx, const double* theta, int64_t B, int N, dou
     const int64_t blocks = (B + group * kWarps64 - 1) / (group * kWarps64);
     waveform64_kernel<<<(unsigned)blocks, kWarps64 * 32, smem, s>>>(
         tables64(ctx, N), (const C64*)ctx->d_tw64, ctx->obs.T_obs, transfer_frequency(ctx), N,
-        theta, B, (int)group, (C64*)hA, (C64*)hE, q, ctx->d_status);
+        theta, B, (int)group, (C64*)hA, (C64*)hE, (C64*)hT, q, ctx->d_status);
     ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "waveform64 launch");

@@ -94,6 +94,8 @@ struct WinMeta {
     double dd;
     double sig;
     long long prep_off;
+    int use_t;   // the window's <.|.> includes the T channel (float copy at prep_off + n_prep)
+    int pad;
 };
 
 // Float copy of one window bin: data times sigma, weights over sigma^2.
@@ -215,12 +217,14 @@ int get_plan(gb_ctx* ctx, int prec, const gb_window_t* win, int32_t n_win, int t
 // launchers implemented per precision
 int launch_loglik_fp64(gb_ctx* ctx, const Plan& plan, const double* dA, const double* dE,
                        const double* wA, const double* wE, const double* theta, double* logL,
-                       double* dh, double* hh, double* dh_im, cudaStream_t s);
+                       double* dh, double* hh, double* dh_im, const double* dT, const double* wT,
+                       cudaStream_t s);
 int launch_waveform_fp64(gb_ctx* ctx, const double* theta, int64_t B, int N, double* hA,
-                         double* hE, int64_t* q, cudaStream_t s);
+                         double* hE, double* hT, int64_t* q, cudaStream_t s);
 int launch_loglik_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const double* dE,
                         const double* wA, const double* wE, const double* theta, double* logL,
-                        double* dh, double* hh, double* dh_im, cudaStream_t s);
+                        double* dh, double* hh, double* dh_im, const double* dT, const double* wT,
+                        cudaStream_t s);
 int launch_waveform_mixed(gb_ctx* ctx, const double* theta, int64_t B, int N, double* hA,
                           double* hE, int64_t* q, cudaStream_t s);
 int launch_grad_fp64(gb_ctx* ctx, const Plan& plan, const double* dA, const double* dE, const double* wA,

@@ -241,7 +241,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // (for the across-lane transform of the waveform and gradient kernels).
 template <int J, bool NAT>
 __device__ void slow_part_mixed(const CandMix& c, const OrbitTables32& tab, int N, float2* bufA, float2* bufE,
-                                int lane) {
+                                int lane, float4* bufT) {
     const int R = N >> 5;
     const float invN = 1.0f / (float)N;
     const float r2 = 0.70710678118654752f, r6 = 0.40824829046386302f;
@@ -336,6 +336,11 @@ __device__ void slow_part_mixed(const CandMix& c, const OrbitTables32& tab, int 
         const float2 oA = cmulf(F, Ap), oE = cmulf(F, Ep);
         if constexpr (NAT) {   // channel-pair elements for the likelihood transform
             ((float4*)bufA)[p] = make_float4(oA.x, oE.x, oA.y, oE.y);
+            if (bufT) {   // T = (X + Y + Z)/sqrt3, paired with zero
+                const float r3 = 0.57735026918962576f;
+                const float2 oT = cmulf(F, make_float2((Xp.x + Yp.x + Zp.x) * r3, (Xp.y + Yp.y + Zp.y) * r3));
+                bufT[p] = make_float4(oT.x, 0.0f, oT.y, 0.0f);
+            }
         } else {
             bufA[p] = oA;
             bufE[p] = oE;
@@ -441,10 +446,11 @@ __device__ __forceinline__ cpair pcis_rx(f2 x) {
     }
 }
 
-// natural sample order (the likelihood kernel's transform), N >= 64
-template <int J>
+// natural sample order (the likelihood kernel's transform), N >= 64; with
+// T3 and bufT also T = (X + Y + Z)/sqrt3, paired with zero
+template <int J, bool T3>
 __device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N, float2* bufA, float2* bufE,
-                               int lane) {
+                               int lane, float4* bufT) {
     const int R = N >> 5, H = N >> 1;
     const float invN = 1.0f / (float)N;
     const f2 r2 = bc(0.70710678118654752f), r6 = bc(0.40824829046386302f);
@@ -547,28 +553,38 @@ __device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N
         float4* buf = (float4*)bufA;
         buf[p] = make_float4(oA.re.x, oE.re.x, oA.im.x, oE.im.x);
         buf[p + 32] = make_float4(oA.re.y, oE.re.y, oA.im.y, oE.im.y);
+        if constexpr (T3) {
+            if (bufT) {
+                const f2 r3 = bc(0.57735026918962576f);
+                const cpair Tp{pmul(padd(padd(Xp.re, Yp.re), Zp.re), r3), pmul(padd(padd(Xp.im, Yp.im), Zp.im), r3)};
+                const cpair oT = pcmul(F, Tp);
+                bufT[p] = make_float4(oT.re.x, 0.0f, oT.im.x, 0.0f);
+                bufT[p + 32] = make_float4(oT.re.y, 0.0f, oT.im.y, 0.0f);
+            }
+        }
     }
 }
 
-template <bool NAT>
+template <bool NAT, bool T3 = false>
 __device__ void slow_part_dispatch(const CandMix& c, const OrbitTables32& tab, int N, float2* bufA, float2* bufE,
-                                   int lane) {
+                                   int lane, float4* bufT = nullptr) {
     if constexpr (NAT) {
         if (N >= 64) {
             switch (c.J) {
-                case 4: slow_part_pair<4>(c, tab, N, bufA, bufE, lane); break;
-                case 7: slow_part_pair<7>(c, tab, N, bufA, bufE, lane); break;
-                case 10: slow_part_pair<10>(c, tab, N, bufA, bufE, lane); break;
-                default: slow_part_pair<0>(c, tab, N, bufA, bufE, lane); break;
+                case 4: slow_part_pair<4, T3>(c, tab, N, bufA, bufE, lane, bufT); break;
+                case 7: slow_part_pair<7, T3>(c, tab, N, bufA, bufE, lane, bufT); break;
+                case 10: slow_part_pair<10, T3>(c, tab, N, bufA, bufE, lane, bufT); break;
+                default: slow_part_pair<0, T3>(c, tab, N, bufA, bufE, lane, bufT); break;
             }
             return;
         }
     }
+    float4* bt = T3 ? bufT : nullptr;
     switch (c.J) {
-        case 4: slow_part_mixed<4, NAT>(c, tab, N, bufA, bufE, lane); break;
-        case 7: slow_part_mixed<7, NAT>(c, tab, N, bufA, bufE, lane); break;
-        case 10: slow_part_mixed<10, NAT>(c, tab, N, bufA, bufE, lane); break;
-        default: slow_part_mixed<0, NAT>(c, tab, N, bufA, bufE, lane); break;
+        case 4: slow_part_mixed<4, NAT>(c, tab, N, bufA, bufE, lane, bt); break;
+        case 7: slow_part_mixed<7, NAT>(c, tab, N, bufA, bufE, lane, bt); break;
+        case 10: slow_part_mixed<10, NAT>(c, tab, N, bufA, bufE, lane, bt); break;
+        default: slow_part_mixed<0, NAT>(c, tab, N, bufA, bufE, lane, bt); break;
     }
 }
 
@@ -944,20 +960,31 @@ __device__ __forceinline__ void warp_sum2(float sum, float comp, float& hi, floa
     }
 }
 
+// dT, wT (may be null): the T channel, used in windows whose lowest frequency
+// k0/T is at least f*/2; its float copy goes n_prep entries after A and E's.
 __global__ void prep_mixed_kernel(const gb_window_t* __restrict__ wins, WinMeta* __restrict__ meta,
                                   Win32* __restrict__ prep, const double2* __restrict__ dA,
                                   const double2* __restrict__ dE, const double* __restrict__ wA,
-                                  const double* __restrict__ wE, double T, int* head) {
+                                  const double* __restrict__ wE, const double2* __restrict__ dT,
+                                  const double* __restrict__ wT, long long n_prep, double T, double fstar,
+                                  int* head) {
     __shared__ double s_acc[32], s_max[32];
     const int w = blockIdx.x;
     if (w == 0 && threadIdx.x < 2) head[threadIdx.x] = 0;   // both work queues
     const gb_window_t win = wins[w];
+    const bool useT = dT != nullptr && (double)win.k0 / T >= 0.5 * fstar;
     double acc = 0.0, wmax = 0.0;
     for (int i = threadIdx.x; i < win.W; i += blockDim.x) {
         const double2 a = dA[win.data_off + i], e = dE[win.data_off + i];
         const double wa = wA[win.data_off + i], we = wE[win.data_off + i];
         acc += wa * (a.x * a.x + a.y * a.y) + we * (e.x * e.x + e.y * e.y);
         wmax = fmax(wmax, fmax(wa, we));
+        if (useT) {
+            const double2 t = dT[win.data_off + i];
+            const double wt = wT[win.data_off + i];
+            acc += wt * (t.x * t.x + t.y * t.y);
+            wmax = fmax(wmax, wt);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -980,6 +1007,7 @@ __global__ void prep_mixed_kernel(const gb_window_t* __restrict__ wins, WinMeta*
     if (threadIdx.x == 0) {
         meta[w].dd = dd * (4.0 / T);
         meta[w].sig = sig;
+        meta[w].use_t = useT ? 1 : 0;
     }
     for (int i = threadIdx.x; i < win.W; i += blockDim.x) {
         const double2 a = dA[win.data_off + i], e = dE[win.data_off + i];
@@ -988,6 +1016,14 @@ __global__ void prep_mixed_kernel(const gb_window_t* __restrict__ wins, WinMeta*
         v.dim = make_float2((float)(a.y * sig), (float)(e.y * sig));
         v.w = make_float2((float)(wA[win.data_off + i] * isig2), (float)(wE[win.data_off + i] * isig2));
         prep[po + i] = v;
+        if (useT) {   // T in the first slot of each pair, zero in the second
+            const double2 t = dT[win.data_off + i];
+            Win32 u;
+            u.dre = make_float2((float)(t.x * sig), 0.0f);
+            u.dim = make_float2((float)(t.y * sig), 0.0f);
+            u.w = make_float2((float)(wT[win.data_off + i] * isig2), 0.0f);
+            prep[n_prep + po + i] = u;
+        }
     }
 }
 
@@ -997,13 +1033,21 @@ __global__ void prep_mixed_kernel(const gb_window_t* __restrict__ wins, WinMeta*
 #endif
 
 // RMAX: largest R = N/32 this instantiation handles (8: N <= 256; 32: N = 512, 1024)
-template <int RMAX, bool IM>
+// the two channels' compensated sums added into one (true sums s - c)
+__device__ __forceinline__ void kahan_join(float& s, float& c, float s2, float c2) {
+    float hi, e;
+    two_sum(s, s2, hi, e);
+    s = hi;
+    c = (c + c2) - e;
+}
+
+template <int RMAX, bool IM, bool T3>
 __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) loglik_mixed_kernel(
     const gb_window_t* __restrict__ wins, const WinMeta* __restrict__ meta, const Win32* __restrict__ prep,
     const Tile* __restrict__ items, int n_items, int* head, TabSet32 tabs, const float2* __restrict__ tw1024,
     double T, double fstar, const double* __restrict__ theta, double* __restrict__ logL,
     double* __restrict__ dh_out, double* __restrict__ hh_out, double* __restrict__ dhi_out, int* status, int n_max,
-    unsigned long long budget_ns) {
+    unsigned long long budget_ns, long long n_prep) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     CandMix* cands = (CandMix*)smem_raw + warp * 32;
@@ -1011,6 +1055,10 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) 
     float2* bufA =
         (float2*)((Epi<IM>*)((CandMix*)smem_raw + kWarpsMx * 32) + kWarpsMx * 32) + (size_t)warp * 2 * n_max;
     float2* bufE = bufA + n_max;
+    // T3: a second channel-pair buffer per warp for (T, 0)
+    float4* bufT = T3 ? (float4*)((float2*)((Epi<IM>*)((CandMix*)smem_raw + kWarpsMx * 32) + kWarpsMx * 32) +
+                                  (size_t)kWarpsMx * 2 * n_max) + (size_t)warp * n_max
+                      : nullptr;
     const LaneTw ltw = lane_twiddles(lane);
     const double ifs = 1.0 / fstar;   // the float results do not see the reciprocal's rounding
 
@@ -1032,6 +1080,8 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) 
         const gb_window_t win = wins[t.win];
         const WinMeta wm = meta[t.win];
         const Win32* pw = prep + wm.prep_off;
+        const bool useT = T3 && wm.use_t;
+        const Win32* pwT = prep + n_prep + wm.prep_off;
         const int N = win.N;
         const OrbitTables32 tab = tabs.t[__ffs(N) - 6];
         const int cnt = (int)(t.c_end - t.c_begin);
@@ -1041,7 +1091,7 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) 
             const CandMix& c = cands[i];
             float sdh = 0.0f, cdh = 0.0f, shh = 0.0f, chh = 0.0f, sim = 0.0f, cim = 0.0f;
             if (!c.bad) {
-                slow_part_dispatch<true>(c, tab, N, bufA, bufE, lane);
+                slow_part_dispatch<true, T3>(c, tab, N, bufA, bufE, lane, useT ? bufT : nullptr);
                 __syncwarp();
                 const long long off64 = c.q - win.k0;
                 if (off64 > -(long long)N && off64 < (long long)win.W + N) {
@@ -1062,6 +1112,29 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) 
                             GB_FFT_INNER(32);
                     }
 #undef GB_FFT_INNER
+                    if constexpr (T3) {
+                        if (useT) {   // the T channel through the same transform, then into the sums
+                            float tdh = 0.0f, tcdh = 0.0f, thh = 0.0f, tchh = 0.0f, tim = 0.0f, tcim = 0.0f;
+#define GB_FFT_INNER_T(R) \
+    fft_inner_ch<R, false>(bufT, tab, ltw, lane, off, win.W, pwT, tdh, tcdh, thh, tchh, tim, tcim)
+                            if constexpr (RMAX <= 8) {
+                                switch (N) {
+                                    case 32: GB_FFT_INNER_T(1); break;
+                                    case 64: GB_FFT_INNER_T(2); break;
+                                    case 128: GB_FFT_INNER_T(4); break;
+                                    default: GB_FFT_INNER_T(8); break;
+                                }
+                            } else {
+                                if (N == 512)
+                                    GB_FFT_INNER_T(16);
+                                else
+                                    GB_FFT_INNER_T(32);
+                            }
+#undef GB_FFT_INNER_T
+                            kahan_join(sdh, cdh, tdh, tcdh);
+                            kahan_join(shh, chh, thh, tchh);
+                        }
+                    }
                 }
                 __syncwarp();
             }
@@ -1167,18 +1240,22 @@ int resident_blocks(const void* kernel, int threads, size_t smem) {
 }
 
 // Part 0 drains the N >= 512 queue, part 1 the N <= 256 queue.
-const void* mixed_kernel_fn(int part, bool im) {
-    if (im) return part == 0 ? (const void*)loglik_mixed_kernel<32, true> : (const void*)loglik_mixed_kernel<8, true>;
-    return part == 0 ? (const void*)loglik_mixed_kernel<32, false> : (const void*)loglik_mixed_kernel<8, false>;
+const void* mixed_kernel_fn(int part, bool im, bool t3) {
+    if (t3) return part == 0 ? (const void*)loglik_mixed_kernel<32, false, true>
+                             : (const void*)loglik_mixed_kernel<8, false, true>;
+    if (im)
+        return part == 0 ? (const void*)loglik_mixed_kernel<32, true, false>
+                         : (const void*)loglik_mixed_kernel<8, true, false>;
+    return part == 0 ? (const void*)loglik_mixed_kernel<32, false, false> : (const void*)loglik_mixed_kernel<8, false, false>;
 }
 
 cudaError_t launch_mixed_part(const void* kfn, int grid, size_t smem, cudaStream_t s, const gb_window_t* wins,
                               const WinMeta* meta, const Win32* prep, const Tile* items, int n_items, int* head,
                               TabSet32 tabs, const float2* tw1024, double T, double fstar, const double* theta,
                               double* logL, double* dh, double* hh, double* dhi, int* status, int n_max,
-                              unsigned long long budget_ns) {
-    void* args[] = {&wins, &meta, &prep,  &items, &n_items, &head, &tabs, &tw1024, &T,      &fstar,    &theta,
-                    &logL, &dh,   &hh,    &dhi,   &status,  &n_max, &budget_ns};
+                              unsigned long long budget_ns, long long n_prep) {
+    void* args[] = {&wins, &meta, &prep, &items, &n_items, &head,  &tabs,      &tw1024, &T,     &fstar,
+                    &theta, &logL, &dh,  &hh,    &dhi,     &status, &n_max,    &budget_ns, &n_prep};
     return cudaLaunchKernel(kfn, dim3(grid), dim3(kWarpsMx * 32), args, smem, s);
 }
 
@@ -1186,10 +1263,12 @@ cudaError_t launch_mixed_part(const void* kfn, int grid, size_t smem, cudaStream
 
 int launch_loglik_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const double* dE, const double* wA,
                         const double* wE, const double* theta, double* logL, double* dh, double* hh,
-                        double* dh_im, cudaStream_t s) {
+                        double* dh_im, const double* dT, const double* wT, cudaStream_t s) {
     if (plan.n_tiles == 0) return GB_OK;
+    const bool t3 = dT != nullptr;
     prep_mixed_kernel<<<plan.n_win, 256, 0, s>>>(plan.d_win, plan.d_meta, plan.d_prep, (const double2*)dA,
-                                                 (const double2*)dE, wA, wE, ctx->obs.T_obs, plan.d_head);
+                                                 (const double2*)dE, wA, wE, (const double2*)dT, wT, plan.n_prep,
+                                                 ctx->obs.T_obs, transfer_frequency(ctx), plan.d_head);
     ++ctx->launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "prep_mixed launch");
@@ -1202,8 +1281,9 @@ int launch_loglik_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const d
         if (n_items == 0) continue;
         const int nmax = part == 0 ? 1024 : (plan.n_max < 256 ? plan.n_max : 256);
         const size_t epi_bytes = dh_im ? sizeof(Epi<true>) : sizeof(Epi<false>);
-        const size_t smem = (sizeof(CandMix) + epi_bytes) * kWarpsMx * 32 + sizeof(float2) * kWarpsMx * 2 * (size_t)nmax;
-        const void* kfn = mixed_kernel_fn(part, dh_im != nullptr);
+        const size_t smem = (sizeof(CandMix) + epi_bytes) * kWarpsMx * 32 + sizeof(float2) * kWarpsMx * 2 * (size_t)nmax +
+                            (t3 ? sizeof(float4) * kWarpsMx * (size_t)nmax : 0);
+        const void* kfn = mixed_kernel_fn(part, dh_im != nullptr, t3);
         e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_error(ctx, e, "loglik_mixed: smem attribute");
         int bpsm = resident_blocks(kfn, kWarpsMx * 32, smem);
@@ -1215,7 +1295,7 @@ int launch_loglik_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const d
         int* head = plan.d_head + (part == 0 ? 1 : 0);
         e = launch_mixed_part(kfn, grid, smem, s, plan.d_win, plan.d_meta, plan.d_prep, items, n_items, head,
                               tabset32(ctx), (const float2*)ctx->d_tw32, ctx->obs.T_obs, transfer_frequency(ctx),
-                              theta, logL, dh, hh, dh_im, ctx->d_status, nmax, ctx->budget_ns);
+                              theta, logL, dh, hh, dh_im, ctx->d_status, nmax, ctx->budget_ns, plan.n_prep);
         ++ctx->launches;
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_error(ctx, e, "loglik_mixed launch");
@@ -1392,6 +1472,8 @@ extern "C" int gb_loglik_mixed_noalloc(const gb_obs_t* obs, const gb_window_t* w
         g_na_meta[i].dd = 0.0;
         g_na_meta[i].sig = 1.0;
         g_na_meta[i].prep_off = off;
+        g_na_meta[i].use_t = 0;
+        g_na_meta[i].pad = 0;
         off += win[i].W;
     }
     gb_window_t* d_win = (gb_window_t*)(b + kNaOffWin);
@@ -1406,16 +1488,16 @@ extern "C" int gb_loglik_mixed_noalloc(const gb_obs_t* obs, const gb_window_t* w
         e = cudaMemcpyAsync(d_meta, g_na_meta, sizeof(WinMeta) * (size_t)n_win, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return na_fail(err, err_len, GB_ECUDA, "gb_loglik_mixed_noalloc: upload failed");
     // the queue heads start at zero: the preparation kernel resets them
-    prep_mixed_kernel<<<n_win, 256, 0, s>>>(d_win, d_meta, d_prep, (const double2*)dA, (const double2*)dE, wA, wE,
-                                            obs->T_obs, d_head);
     const double fstar = kC / (2.0 * kPi * obs->arm_L);
+    prep_mixed_kernel<<<n_win, 256, 0, s>>>(d_win, d_meta, d_prep, (const double2*)dA, (const double2*)dE, wA, wE,
+                                            nullptr, nullptr, 0LL, obs->T_obs, fstar, d_head);
     for (int part = 0; part < 2 && cudaGetLastError() == cudaSuccess; ++part) {
         const int n_items = part == 0 ? n_large : k - n_large;
         if (n_items == 0) continue;
         const int nmax = part == 0 ? 1024 : (n_max < 256 ? n_max : 256);
         const size_t smem =
             (sizeof(CandMix) + sizeof(Epi<false>)) * kWarpsMx * 32 + sizeof(float2) * kWarpsMx * 2 * (size_t)nmax;
-        const void* kfn = mixed_kernel_fn(part, false);
+        const void* kfn = mixed_kernel_fn(part, false, false);
         if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) break;
         int grid = sms * resident_blocks(kfn, kWarpsMx * 32, smem);
         const int need = (n_items + kWarpsMx - 1) / kWarpsMx;
@@ -1423,7 +1505,7 @@ extern "C" int gb_loglik_mixed_noalloc(const gb_obs_t* obs, const gb_window_t* w
         const Tile* it = d_items + (part == 0 ? 0 : n_large);
         int* head = d_head + (part == 0 ? 1 : 0);
         if (launch_mixed_part(kfn, grid, smem, s, d_win, d_meta, d_prep, it, n_items, head, tabs, (const float2*)tw32,
-                              obs->T_obs, fstar, theta, logL, dh, hh, nullptr, d_status, nmax, 0ULL) != cudaSuccess)
+                              obs->T_obs, fstar, theta, logL, dh, hh, nullptr, d_status, nmax, 0ULL, 0LL) != cudaSuccess)
             break;
     }
     e = cudaGetLastError();
@@ -1934,7 +2016,8 @@ int launch_grad_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const dou
                       const double* wE, const double* theta, double* logL, double* grad, cudaStream_t s) {
     if (plan.n_tiles == 0) return GB_OK;
     prep_mixed_kernel<<<plan.n_win, 256, 0, s>>>(plan.d_win, plan.d_meta, plan.d_prep, (const double2*)dA,
-                                                 (const double2*)dE, wA, wE, ctx->obs.T_obs, plan.d_head);
+                                                 (const double2*)dE, wA, wE, nullptr, nullptr, plan.n_prep,
+                                                 ctx->obs.T_obs, transfer_frequency(ctx), plan.d_head);
     ++ctx->launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "prep_mixed launch");

@@ -1,0 +1,101 @@
+"""The T channel (Eq. 5; used above f*/2, Sec. II) through the C ABI against
+the oracle: FP64 templates and likelihoods to 1e-10, the mixed likelihood to
+1e-5 of <h|h>, windows below f*/2 unchanged from gb_loglik."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import gb as ogb
+from paper_2307_03763_gb300 import workloads as wk
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+T = wk.YEAR
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2307_03763_gb300 import api, build
+    build.build()
+    return api.Context(T)
+
+
+def _c(x, dt):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(DEV, dt)
+
+
+def _problem(seed, specs, n_cand):
+    """Windows (f0, N) with an injected source each, noise and weights per channel."""
+    rng = np.random.default_rng(seed)
+    wins, th_all, data, weights = [], [], [[], [], []], [[], [], []]
+    off = coff = 0
+    for f0, N in specs:
+        src = wk.source(f0, float(wk.chirp_fdot(f0, 0.5)), 1e-22, rng)
+        q = int(ogb.carrier_bin(torch.tensor([src[0]]), torch.tensor([src[1]]), T)[0][0])
+        k0, W = q - N // 2 + 3, N
+        _, hA, hE, hT = ogb.template_aet(torch.tensor(src[None]), N, T)
+        for c, (h, wv) in enumerate(zip((hA, hE, hT), (1e41, 1e41, 3e41))):
+            x = np.zeros(W, np.complex128)
+            x[:N - 3] = h[0].numpy()[3:]
+            sd = math.sqrt(T / (4 * wv))
+            data[c].append(x + (rng.normal(size=W) + 1j * rng.normal(size=W)) * sd)
+            weights[c].append(np.full(W, wv) * (1 + 0.1 * rng.uniform(size=W)))
+        half = np.array([2 / T, abs(src[1]), 0.05, 0.05, 0.1 * src[4], 0.05, 0.05, 0.2])
+        th_all.append(wk.uniform_box(src, half, n_cand, rng))
+        wins.append((k0, W, N, off, coff, n_cand))
+        off += W
+        coff += n_cand
+    d = [np.concatenate(x) for x in data]
+    w = [np.concatenate(x) for x in weights]
+    return wins, np.concatenate(th_all), d, w
+
+
+SPECS = [(6e-3, 256), (11e-3, 512), (16e-3, 1024), (9.8e-3, 256)]
+
+
+def test_waveform_aet_fp64_matches_oracle(ctx):
+    rng = np.random.default_rng(3)
+    th = np.stack([wk.source(f, 1e-16, 1e-22, rng) for f in (2e-3, 12e-3, 17e-3)])
+    for N in (256, 1024):
+        hA, hE, hT, q = ctx.waveform_aet(_c(th, torch.float64), N)
+        oq, oA, oE, oT = ogb.template_aet(torch.tensor(th), N, T)
+        assert torch.equal(q.cpu(), oq)
+        for g, o in ((hA, oA), (hE, oE), (hT, oT)):
+            g = g.cpu()
+            assert ((g - o).abs().max(dim=1).values <= 1e-10 * o.abs().max(dim=1).values + 1e-300).all()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_loglik_aet_matches_oracle(ctx, prec):
+    wins, th, d, w = _problem(7, SPECS, 24)
+    assert [ogb.uses_t(k0, T) for k0, *_ in wins] == [False, True, True, True]
+    args = [_c(x, torch.complex128) for x in d] + [_c(x, torch.float64) for x in w]
+    g = [x.cpu() for x in ctx.loglik_aet(wins, *args, _c(th, torch.float64), prec=prec)]
+    o = ogb.loglik_aet(wins, *d, *w, th, T)
+    if prec == "fp64":
+        scale = max(1.0, float(o[2].abs().max()))
+        assert float((g[0] - o[0]).abs().max()) <= 1e-10 * float(o[0].abs().max())
+        assert float((g[1] - o[1]).abs().max()) <= 1e-10 * scale
+        assert float((g[2] - o[2]).abs().max()) <= 1e-10 * scale
+    else:
+        rel = (g[0] - o[0]).abs() / torch.clamp(o[2].abs(), min=1.0)
+        assert float(rel.max()) < 1e-5, float(rel.max())
+    # the window below f*/2 is the plain A/E likelihood
+    a = [x.cpu() for x in ctx.loglik(wins[:1], args[0], args[1], args[3], args[4], _c(th, torch.float64), prec=prec)]
+    n0 = wins[0][5]
+    assert torch.equal(a[0][:n0], g[0][:n0])
+
+
+def test_t_channel_argument_errors(ctx):
+    from paper_2307_03763_gb300 import api
+    rng = np.random.default_rng(9)
+    th = _c(np.stack([wk.source(12e-3, 1e-16, 1e-22, rng)]), torch.float64)
+    with pytest.raises(api.GBError):
+        ctx.waveform_aet(th, 100)                      # N not a power of two
+    h = torch.empty((1, 256), dtype=torch.complex128, device=DEV)
+    q = torch.empty(1, dtype=torch.int64, device=DEV)
+    rc = api.lib().gb_waveform_aet(ctx._h, api.PRECISIONS["mixed"], api._ptr(th), 1, 256, api._ptr(h), api._ptr(h),
+                                   api._ptr(h), api._ptr(q), None)
+    assert rc != 0                                     # the T template is FP64 only
