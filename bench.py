@@ -349,6 +349,19 @@ def run_workload(args):
             ms = timed(lambda: ctx.loglik(sub, *data, theta, prec="mixed"), 3)
             per[int(N)] = {"evals": int(cnt), "ms": ms, "evals_per_s": cnt / ms * 1e3}
         line["mixed_by_N"] = per
+        # the paper's channel rule: T joins A and E in the windows above f*/2 (Sec. II)
+        nT, wT = wk.t_noise_and_weights(wl.windows, wl.T, np.random.default_rng(wk.SEED_BASE + 33))
+        dT, wTt = T_(nT, torch.complex128), T_(wT, torch.float64)
+        aet = lambda p: ctx.loglik_aet(wl.windows, data[0], data[1], dT, data[2], data[3], wTt, theta, prec=p)
+        ms_aet = timed(lambda: aet("mixed"), reps)
+        fstar_half = 2.99792458e8 / (4 * np.pi * 2.5e9)
+        with_t = [w for w in wl.windows if w[0] / wl.T >= fstar_half]
+        l64t = aet("fp64")[0] if n <= 10 ** 6 else None
+        line["mixed_aet"] = {"value": n / ms_aet * 1e3, "ms": ms_aet, "windows_with_T": len(with_t),
+                             "evals_with_T": int(sum(w[5] for w in with_t)),
+                             "rule": "A, E and T in windows whose lowest frequency is at least f*/2 = 9.54 mHz"}
+        if l64t is not None:
+            line["mixed_aet"]["max_abs_dlogL_vs_fp64"] = float((aet("mixed")[0] - l64t).abs().max())
     if args.workload == "population":
         ms_g = timed(lambda: ctx.loglik_grad(wl.windows, *data, theta, prec="mixed"), reps)
         sub = [(k0, W, N, doff, coff, 512) for (k0, W, N, doff, coff, nc) in wl.windows]

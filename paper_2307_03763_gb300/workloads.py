@@ -47,6 +47,29 @@ def psd_AE(f, L=ARM_L):
     return 8.0 * np.sin(x) ** 2 * ((2 + np.cos(x)) * s_oms + 2 * (3 + 2 * np.cos(x) + np.cos(2 * x)) * s_acc)
 
 
+def psd_T(f, L=ARM_L):
+    """One-sided analytic PSD of TDI T for the same two noises and the
+    first-generation T transfer, x = 2 pi f L / c:
+      S_T = 16 sin^2 x [(1 - cos x) S_oms + 2 (1 - cos x)^2 S_acc]."""
+    f = np.asarray(f, dtype=np.float64)
+    x = 2.0 * np.pi * f * L / C_LIGHT
+    s_acc = (3e-15) ** 2 * (1 + (0.4e-3 / f) ** 2) * (1 + (f / 8e-3) ** 4) / (2 * np.pi * f * C_LIGHT) ** 2
+    s_oms = (15e-12) ** 2 * (1 + (2e-3 / f) ** 4) * (2 * np.pi * f / C_LIGHT) ** 2
+    return 16.0 * np.sin(x) ** 2 * ((1 - np.cos(x)) * s_oms + 2 * (1 - np.cos(x)) ** 2 * s_acc)
+
+
+def t_noise_and_weights(windows, T, rng):
+    """T-channel noise, Re and Im ~ N(0, T S_T / 4) per bin, and w = 1/S_T."""
+    nb = sum(w[1] for w in windows)
+    nT = np.empty(nb, np.complex128)
+    wT = np.empty(nb)
+    for (k0, W, N, doff, _, _) in windows:
+        S = psd_T((k0 + np.arange(W)) / T)
+        nT[doff:doff + W] = np.sqrt(T * S / 4.0) * (rng.standard_normal(W) + 1j * rng.standard_normal(W))
+        wT[doff:doff + W] = 1.0 / S
+    return nT, wT
+
+
 def chirp_fdot(f, mchirp_msun):
     """fdot = 96/5 pi^(8/3) Mc^(5/3) f^(11/3) in geometric units (Eq. 8)."""
     mc = np.asarray(mchirp_msun, dtype=np.float64) * G_MSUN_S
