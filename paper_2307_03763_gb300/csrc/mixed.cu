@@ -1537,36 +1537,55 @@ namespace {
 
 constexpr int KT = 4;   // f0, fdot, beta, lambda
 
+// A complex value with its KT = 4 forward tangents.  The tangents are kept
+// as two pairs, k = (0, 1) and (2, 3), of real parts dr and imaginary parts
+// di, so that every tangent operation is one packed FP32 instruction per pair.
 struct DCf {
     float2 v;
-    float2 d[KT];
+    f2 dr[2], di[2];
 };
 __device__ __forceinline__ DCf dmulf(const DCf& a, const DCf& b) {
     DCf o;
     o.v = cmulf(a.v, b.v);
 #pragma unroll
-    for (int k = 0; k < KT; ++k) o.d[k] = caddf(cmulf(a.d[k], b.v), cmulf(a.v, b.d[k]));
+    for (int p = 0; p < 2; ++p) {   // a.d b.v + a.v b.d
+        const f2 re1 = pfma(a.dr[p], bc(b.v.x), pneg(pmul(a.di[p], bc(b.v.y))));
+        const f2 im1 = pfma(a.dr[p], bc(b.v.y), pmul(a.di[p], bc(b.v.x)));
+        const f2 re2 = pfma(bc(a.v.x), b.dr[p], pneg(pmul(bc(a.v.y), b.di[p])));
+        const f2 im2 = pfma(bc(a.v.x), b.di[p], pmul(bc(a.v.y), b.dr[p]));
+        o.dr[p] = padd(re1, re2);
+        o.di[p] = padd(im1, im2);
+    }
     return o;
 }
 __device__ __forceinline__ DCf daddf(const DCf& a, const DCf& b) {
     DCf o;
     o.v = caddf(a.v, b.v);
 #pragma unroll
-    for (int k = 0; k < KT; ++k) o.d[k] = caddf(a.d[k], b.d[k]);
+    for (int p = 0; p < 2; ++p) {
+        o.dr[p] = padd(a.dr[p], b.dr[p]);
+        o.di[p] = padd(a.di[p], b.di[p]);
+    }
     return o;
 }
 __device__ __forceinline__ DCf dsubf(const DCf& a, const DCf& b) {
     DCf o;
     o.v = csubf(a.v, b.v);
 #pragma unroll
-    for (int k = 0; k < KT; ++k) o.d[k] = csubf(a.d[k], b.d[k]);
+    for (int p = 0; p < 2; ++p) {
+        o.dr[p] = psub(a.dr[p], b.dr[p]);
+        o.di[p] = psub(a.di[p], b.di[p]);
+    }
     return o;
 }
 __device__ __forceinline__ DCf dscalef(const DCf& a, float s) {
     DCf o;
     o.v = make_float2(a.v.x * s, a.v.y * s);
 #pragma unroll
-    for (int k = 0; k < KT; ++k) o.d[k] = make_float2(a.d[k].x * s, a.d[k].y * s);
+    for (int p = 0; p < 2; ++p) {
+        o.dr[p] = pmul(a.dr[p], bc(s));
+        o.di[p] = pmul(a.di[p], bc(s));
+    }
     return o;
 }
 
@@ -1701,9 +1720,10 @@ __device__ __forceinline__ void sample_grad(const CandGx& g, const OrbitTables32
         dph[3] = -fk * g.cb * (vx0 + vrho[j]);
         rx[j].v = v;
 #pragma unroll
-        for (int k = 0; k < KT; ++k) {
-            const float t = 6.2831853071795865f * dph[k];
-            rx[j].d[k] = make_float2(-t * v.y, t * v.x);
+        for (int p = 0; p < 2; ++p) {
+            const f2 t = pmul(bc(6.2831853071795865f), make_float2(dph[2 * p], dph[2 * p + 1]));
+            rx[j].dr[p] = pmul(pneg(t), bc(v.y));
+            rx[j].di[p] = pmul(t, bc(v.x));
         }
     }
     const float a = fmaf(c.a1, u, c.a0);
@@ -1732,11 +1752,17 @@ __device__ __forceinline__ void sample_grad(const CandGx& g, const OrbitTables32
         const float Fp = (nu - nv) * (nu + nv), Fx = 2.0f * nu * nv;
         DCf G;
         G.v = make_float2(fmaf(g.gp.x, Fp, g.gx.x * Fx), fmaf(g.gp.y, Fp, g.gx.y * Fx));
+        float dFp[KT], dFx[KT];
 #pragma unroll
         for (int k = 0; k < KT; ++k) {
-            const float dFp = 2.0f * (nu * dnu[k] - nv * dnv[k]);
-            const float dFx = 2.0f * (dnu[k] * nv + nu * dnv[k]);
-            G.d[k] = make_float2(fmaf(g.gp.x, dFp, g.gx.x * dFx), fmaf(g.gp.y, dFp, g.gx.y * dFx));
+            dFp[k] = 2.0f * (nu * dnu[k] - nv * dnv[k]);
+            dFx[k] = 2.0f * (dnu[k] * nv + nu * dnv[k]);
+        }
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const f2 fp = make_float2(dFp[2 * p], dFp[2 * p + 1]), fx = make_float2(dFx[2 * p], dFx[2 * p + 1]);
+            G.dr[p] = pfma(bc(g.gp.x), fp, pmul(bc(g.gx.x), fx));
+            G.di[p] = pfma(bc(g.gp.y), fp, pmul(bc(g.gx.y), fx));
         }
         const int rp = arm == 2 ? 0 : arm + 1, rm = arm;
 #pragma unroll
@@ -1747,10 +1773,14 @@ __device__ __forceinline__ void sample_grad(const CandGx& g, const OrbitTables32
             link_transfer_d<J>(X, Tv, Td);
             DCf Tl;
             Tl.v = Tv;
+            float dX[KT];
 #pragma unroll
-            for (int k = 0; k < KT; ++k) {
-                const float dX = da[k] * fmaf(-sd, kn, 1.0f) - sd * a * dkn[k];
-                Tl.d[k] = make_float2(Td.x * dX, Td.y * dX);
+            for (int k = 0; k < KT; ++k) dX[k] = da[k] * fmaf(-sd, kn, 1.0f) - sd * a * dkn[k];
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                const f2 x = make_float2(dX[2 * p], dX[2 * p + 1]);
+                Tl.dr[p] = pmul(bc(Td.x), x);
+                Tl.di[p] = pmul(bc(Td.y), x);
             }
             const DCf& rr = rx[sgn == 0 ? rp : rm];
             const DCf z = dmulf(dmulf(Tl, G), rr);
@@ -1774,16 +1804,21 @@ __device__ __forceinline__ void sample_grad(const CandGx& g, const OrbitTables32
         D.v = cmulf(make_float2(c.D0r, c.D0i), make_float2(fmaf(-0.5f * du, du, 1.0f), -du));
         const float dphi[KT] = {inv_fstar, tu * inv_fstar, 0.0f, 0.0f};
 #pragma unroll
-        for (int k = 0; k < KT; ++k) D.d[k] = make_float2(D.v.y * dphi[k], -D.v.x * dphi[k]);   // -i D dphi
+        for (int p = 0; p < 2; ++p) {   // -i D dphi
+            const f2 x = make_float2(dphi[2 * p], dphi[2 * p + 1]);
+            D.dr[p] = pmul(bc(D.v.y), x);
+            D.di[p] = pmul(bc(-D.v.x), x);
+        }
     }
     DCf F;
     {
         const float sa2 = -2.0f * a * D.v.y;
         F.v = make_float2(sa2 * D.v.x, sa2 * D.v.y);
 #pragma unroll
-        for (int k = 0; k < KT; ++k) {
-            const float dsa2 = -2.0f * (da[k] * D.v.y + a * D.d[k].y);
-            F.d[k] = make_float2(dsa2 * D.v.x + sa2 * D.d[k].x, dsa2 * D.v.y + sa2 * D.d[k].y);
+        for (int p = 0; p < 2; ++p) {
+            const f2 dsa2 = pmul(bc(-2.0f), pfma(make_float2(da[2 * p], da[2 * p + 1]), bc(D.v.y), pmul(bc(a), D.di[p])));
+            F.dr[p] = pfma(dsa2, bc(D.v.x), pmul(bc(sa2), D.dr[p]));
+            F.di[p] = pfma(dsa2, bc(D.v.y), pmul(bc(sa2), D.di[p]));
         }
     }
     const float r2 = 0.70710678118654752f, r6 = 0.40824829046386302f;
@@ -1882,9 +1917,15 @@ __device__ void tangent_sweep(const CandGx& g, const OrbitTables32& tab, int N, 
         sample_grad<J>(g, tab, N, n, Tf, inv_fstar, SA, SE, PA, PE, QA, QE);
         const float2 a = cA[n], e = cE[n];
 #pragma unroll
-        for (int k = 0; k < KT; ++k)
-            kahan_add(tacc[k][0], tacc[k][1],
-                      fmaf(a.x, SA.d[k].x, fmaf(a.y, SA.d[k].y, fmaf(e.x, SE.d[k].x, e.y * SE.d[k].y))));
+        for (int p = 0; p < 2; ++p) {
+            f2 sum = make_float2(tacc[2 * p][0], tacc[2 * p + 1][0]), comp = make_float2(tacc[2 * p][1], tacc[2 * p + 1][1]);
+            kahan_add2(sum, comp, pfma(bc(a.x), SA.dr[p], pfma(bc(a.y), SA.di[p], pfma(bc(e.x), SE.dr[p],
+                                                                                       pmul(bc(e.y), SE.di[p])))));
+            tacc[2 * p][0] = sum.x;
+            tacc[2 * p + 1][0] = sum.y;
+            tacc[2 * p][1] = comp.x;
+            tacc[2 * p + 1][1] = comp.y;
+        }
         // c conj(P) = (c.x P.x + c.y P.y) + i (c.y P.x - c.x P.y)
         kahan_add(vp[0][0], vp[0][1], fmaf(a.x, PA.x, fmaf(a.y, PA.y, fmaf(e.x, PE.x, e.y * PE.y))));
         kahan_add(vp[1][0], vp[1][1], fmaf(a.y, PA.x, fmaf(-a.x, PA.y, fmaf(e.y, PE.x, -e.x * PE.y))));
