@@ -88,6 +88,25 @@ def test_loglik_aet_matches_oracle(ctx, prec):
     assert torch.equal(a[0][:n0], g[0][:n0])
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_loglik_aet_every_template_length(ctx, prec):
+    # T windows at every N (the mixed kernel's N = 32, 64, 128 branches take
+    # the other second-stage forms of the transform), ragged candidate counts
+    specs = [(10.0e-3, 32), (10.5e-3, 64), (11e-3, 128), (12e-3, 256), (13e-3, 512), (14e-3, 1024)]
+    wins, th, d, w = _problem(11, specs, 9)
+    wins = [(k0, W, N, doff, coff, nc) for (k0, W, N, doff, coff, nc) in wins]
+    assert all(ogb.uses_t(k0, T) for k0, *_ in wins)
+    args = [_c(x, torch.complex128) for x in d] + [_c(x, torch.float64) for x in w]
+    g = [x.cpu() for x in ctx.loglik_aet(wins, *args, _c(th, torch.float64), prec=prec)]
+    o = ogb.loglik_aet(wins, *d, *w, th, T)
+    if prec == "fp64":
+        assert float((g[0] - o[0]).abs().max()) <= 1e-10 * float(o[0].abs().max())
+        assert float((g[2] - o[2]).abs().max()) <= 1e-10 * max(1.0, float(o[2].abs().max()))
+    else:
+        rel = (g[0] - o[0]).abs() / torch.clamp(o[2].abs(), min=1.0)
+        assert float(rel.max()) < 1e-5, float(rel.max())
+
+
 def test_t_channel_argument_errors(ctx):
     from paper_2307_03763_gb300 import api
     rng = np.random.default_rng(9)
