@@ -143,7 +143,7 @@ int gb_waveform(gb_ctx_t* ctx, int prec, const double* theta, int64_t B, int32_t
                 double* hA, double* hE, int64_t* q, void* stream);
 
 /* gb_waveform with the T channel, hT laid out like hA (B x N complex,
- * device, written).  prec must be GB_FP64 (else GB_EINVAL). */
+ * device, written); either precision. */
 int gb_waveform_aet(gb_ctx_t* ctx, int prec, const double* theta, int64_t B, int32_t N,
                     double* hA, double* hE, double* hT, int64_t* q, void* stream);
 

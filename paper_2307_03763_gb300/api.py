@@ -239,14 +239,14 @@ class Context:
                                         _stream(self.device)))
         return logL, dh, hh
 
-    def waveform_aet(self, theta, N):
-        """A/E/T templates (FP64): hA, hE, hT (B, N) complex128, q (B,) int64."""
+    def waveform_aet(self, theta, N, prec="fp64"):
+        """A/E/T templates: hA, hE, hT (B, N) complex128, q (B,) int64."""
         B = theta.shape[0] if theta.dim() == 2 else -1
         _need(theta, torch.float64, self.device, "theta", (B, 8))
         hA = torch.empty((B, N), dtype=torch.complex128, device=self.device)
         hE, hT = torch.empty_like(hA), torch.empty_like(hA)
         q = torch.empty(B, dtype=torch.int64, device=self.device)
-        self._check(lib().gb_waveform_aet(self._h, PRECISIONS["fp64"], _ptr(theta), B, int(N), _ptr(hA), _ptr(hE),
+        self._check(lib().gb_waveform_aet(self._h, PRECISIONS[prec], _ptr(theta), B, int(N), _ptr(hA), _ptr(hE),
                                           _ptr(hT), _ptr(q), _stream(self.device)))
         return hA, hE, hT, q
 

@@ -199,14 +199,15 @@ int gb_autotune(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win, 
 int gb_waveform_aet(gb_ctx_t* ctx, int prec, const double* theta, int64_t B, int32_t N, double* hA, double* hE,
                     double* hT, int64_t* q, void* stream) {
     if (!ctx) return GB_EINVAL;
-    if (prec != GB_FP64) return set_error(ctx, GB_EINVAL, "gb_waveform_aet: the T channel template is FP64 only");
+    if (prec != GB_FP64 && prec != GB_MIXED) return set_error(ctx, GB_EINVAL, "gb_waveform_aet: unknown precision");
     if (B < 0) return set_error(ctx, GB_EINVAL, "gb_waveform_aet: B < 0");
     if (!valid_size(N)) return set_error(ctx, GB_EINVAL, "gb_waveform_aet: N must be a power of two in [32, 1024]");
     if (B == 0) return GB_OK;
     if (!theta || !hA || !hE || !hT || !q) return set_error(ctx, GB_EINVAL, "gb_waveform_aet: null pointer");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_error(ctx, e, "gb_waveform_aet: cudaSetDevice");
-    return launch_waveform_fp64(ctx, theta, B, N, hA, hE, hT, q, (cudaStream_t)stream);
+    if (prec == GB_FP64) return launch_waveform_fp64(ctx, theta, B, N, hA, hE, hT, q, (cudaStream_t)stream);
+    return launch_waveform_mixed(ctx, theta, B, N, hA, hE, hT, q, (cudaStream_t)stream);
 }
 
 int gb_waveform(gb_ctx_t* ctx, int prec, const double* theta, int64_t B, int32_t N, double* hA, double* hE,
@@ -220,7 +221,7 @@ int gb_waveform(gb_ctx_t* ctx, int prec, const double* theta, int64_t B, int32_t
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_error(ctx, e, "gb_waveform: cudaSetDevice");
     if (prec == GB_FP64) return launch_waveform_fp64(ctx, theta, B, N, hA, hE, nullptr, q, (cudaStream_t)stream);
-    return launch_waveform_mixed(ctx, theta, B, N, hA, hE, q, (cudaStream_t)stream);
+    return launch_waveform_mixed(ctx, theta, B, N, hA, hE, nullptr, q, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -226,7 +226,7 @@ int launch_loglik_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const d
                         double* dh, double* hh, double* dh_im, const double* dT, const double* wT,
                         cudaStream_t s);
 int launch_waveform_mixed(gb_ctx* ctx, const double* theta, int64_t B, int N, double* hA,
-                          double* hE, int64_t* q, cudaStream_t s);
+                          double* hE, double* hT, int64_t* q, cudaStream_t s);
 int launch_grad_fp64(gb_ctx* ctx, const Plan& plan, const double* dA, const double* dE, const double* wA,
                      const double* wE, const double* theta, double* logL, double* grad, cudaStream_t s);
 int launch_grad_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const double* dE, const double* wA,

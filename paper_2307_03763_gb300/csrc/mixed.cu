@@ -344,6 +344,10 @@ __device__ void slow_part_mixed(const CandMix& c, const OrbitTables32& tab, int 
         } else {
             bufA[p] = oA;
             bufE[p] = oE;
+            if (bufT) {   // the waveform's T, as float2 samples
+                const float r3 = 0.57735026918962576f;
+                ((float2*)bufT)[p] = cmulf(F, make_float2((Xp.x + Yp.x + Zp.x) * r3, (Xp.y + Yp.y + Zp.y) * r3));
+            }
         }
     }
 }
@@ -1181,12 +1185,14 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) 
 __global__ void __launch_bounds__(kWarpsMx * 32) waveform_mixed_kernel(
     OrbitTables32 tab, const float2* __restrict__ tw1024, double T, double fstar, int N,
     const double* __restrict__ theta, int64_t B, int group, double2* __restrict__ hA, double2* __restrict__ hE,
-    int64_t* __restrict__ q_out, int* status) {
+    double2* __restrict__ hT, int64_t* __restrict__ q_out, int* status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nch = hT ? 3 : 2;
     CandMix* cands = (CandMix*)smem_raw + warp * 32;
-    float2* bufA = (float2*)((CandMix*)smem_raw + kWarpsMx * 32) + (size_t)warp * 2 * N;
+    float2* bufA = (float2*)((CandMix*)smem_raw + kWarpsMx * 32) + (size_t)warp * nch * N;
     float2* bufE = bufA + N;
+    float2* bufT = hT ? bufE + N : nullptr;
     const LaneTw ltw = lane_twiddles(lane);
     const int64_t c_lo = ((int64_t)blockIdx.x * kWarpsMx + warp) * group;
     const int64_t c_hi = min(B, c_lo + group);
@@ -1200,20 +1206,23 @@ __global__ void __launch_bounds__(kWarpsMx * 32) waveform_mixed_kernel(
         double2* outA = hA + b * N;
         double2* outE = hE + b * N;
         if (c.bad) {
-            for (int m = lane; m < N; m += 32) outA[m] = outE[m] = make_double2(nan(""), nan(""));
+            for (int m = lane; m < N; m += 32) {
+                outA[m] = outE[m] = make_double2(nan(""), nan(""));
+                if (hT) hT[b * N + m] = make_double2(nan(""), nan(""));
+            }
             if (lane == 0) {
                 q_out[b] = 0;
                 atomicOr(status, kStatusNonFinite);
             }
             continue;
         }
-        slow_part_dispatch<false>(c, tab, N, bufA, bufE, lane);
+        slow_part_dispatch<false, true>(c, tab, N, bufA, bufE, lane, (float4*)bufT);
         __syncwarp();
         const double s = scale * c.A;
-        for (int ch = 0; ch < 2; ++ch) {
+        for (int ch = 0; ch < nch; ++ch) {
             float2 x[32];
-            const float2* buf = ch == 0 ? bufA : bufE;
-            double2* out = ch == 0 ? outA : outE;
+            const float2* buf = ch == 0 ? bufA : ch == 1 ? bufE : bufT;
+            double2* out = ch == 0 ? outA : ch == 1 ? outE : hT + b * N;
             switch (R) {
                 case 1: channel_fft<1>(buf, tab, tw1024, ltw, lane, *(float2(*)[1])x); break;
                 case 2: channel_fft<2>(buf, tab, tw1024, ltw, lane, *(float2(*)[2])x); break;
@@ -1304,9 +1313,9 @@ int launch_loglik_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const d
 }
 
 int launch_waveform_mixed(gb_ctx* ctx, const double* theta, int64_t B, int N, double* hA, double* hE,
-                          int64_t* q, cudaStream_t s) {
+                          double* hT, int64_t* q, cudaStream_t s) {
     if (B == 0) return GB_OK;
-    const size_t smem = sizeof(CandMix) * kWarpsMx * 32 + sizeof(float2) * kWarpsMx * 2 * (size_t)N;
+    const size_t smem = sizeof(CandMix) * kWarpsMx * 32 + sizeof(float2) * kWarpsMx * (hT ? 3 : 2) * (size_t)N;
     cudaError_t e = cudaFuncSetAttribute(waveform_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_error(ctx, e, "waveform_mixed: smem attribute");
     int sms = 152;
@@ -1316,7 +1325,7 @@ int launch_waveform_mixed(gb_ctx* ctx, const double* theta, int64_t B, int N, do
     const int64_t blocks = (B + group * kWarpsMx - 1) / (group * kWarpsMx);
     waveform_mixed_kernel<<<(unsigned)blocks, kWarpsMx * 32, smem, s>>>(
         tables32(ctx, N), (const float2*)ctx->d_tw32, ctx->obs.T_obs, transfer_frequency(ctx), N, theta, B,
-        (int)group, (double2*)hA, (double2*)hE, q, ctx->d_status);
+        (int)group, (double2*)hA, (double2*)hE, (double2*)hT, q, ctx->d_status);
     ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "waveform_mixed launch");
