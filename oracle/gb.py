@@ -312,6 +312,14 @@ def loglik_aet(windows, dA, dE, dT, wA, wE, wT, theta, T, L=ARM_L, chunk=2048):
     return logL, DH, HH
 
 
+def loglik_grad_aet(windows, dA, dE, dT, wA, wE, wT, theta, T, L=ARM_L, chunk=2048):
+    """loglik_grad() of loglik_aet(): the T channel in windows above f*/2 (R11)."""
+    th = torch.as_tensor(theta, dtype=F64).detach().clone().requires_grad_(True)
+    logL, _, _ = loglik_aet(windows, dA, dE, dT, wA, wE, wT, th, T, L, chunk)
+    logL.sum().backward()
+    return logL.detach(), th.grad.detach()
+
+
 def loglik_grad(windows, dA, dE, wA, wE, theta, T, L=ARM_L, chunk=2048):
     """d logL / d theta for every candidate row, by reverse-mode autodiff of ``loglik``.
 

@@ -509,3 +509,28 @@ def test_loglik_with_t_reduces_to_a_and_e_below_half_the_transfer_frequency():
     a = gb.loglik_aet(win, *d, *w, th, T)
     b = gb.loglik(win, d[0], d[1], w[0], w[1], th, T)
     assert all(torch.equal(x, y) for x, y in zip(a, b))
+
+
+def test_t_channel_gradient_matches_central_differences():
+    # the three-channel likelihood's gradient (autodiff) against Richardson
+    # central differences of loglik_aet, in a window above f*/2
+    T, N, win, th, d, w = _t_window(33, 12e-3)
+    x = th[1].copy()
+    frac = ((x[0] + 0.5 * x[1] * T) * T) % 1.0
+    assert abs(frac - 0.5) > 0.01
+    one = [(win[0][0], win[0][1], N, 0, 0, 1)]
+    _, g = gb.loglik_grad_aet(one, *d, *w, x[None], T)
+    s = _scales(T, x[4])
+    gfd = np.zeros(8)
+    for i in range(8):
+        def D(h):
+            tp, tm = x.copy(), x.copy()
+            tp[i] += h
+            tm[i] -= h
+            lp = gb.loglik_aet(one, *d, *w, tp[None], T)[0][0]
+            lm = gb.loglik_aet(one, *d, *w, tm[None], T)[0][0]
+            return float(lp - lm) / (2 * h)
+        h = 1e-3 * s[i]
+        gfd[i] = (4 * D(h / 2) - D(h)) / 3
+    gn, gfn = g[0].numpy() * s, gfd * s
+    assert np.abs(gn - gfn).max() <= 1e-7 * np.abs(gn).sum(), (gn, gfn)
