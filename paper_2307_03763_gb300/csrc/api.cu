@@ -101,10 +101,24 @@ int gb_loglik_phase(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_w
                        dh_im, hh, stream);
 }
 
+int gb_loglik_grad_aet(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win, const double* dA,
+                       const double* dE, const double* dT, const double* wA, const double* wE, const double* wT,
+                       int64_t n_bins, const double* theta, int64_t n_rows, double* logL, double* grad,
+                       void* stream);
+
 int gb_loglik_grad(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win, const double* dA,
                    const double* dE, const double* wA, const double* wE, int64_t n_bins, const double* theta,
                    int64_t n_rows, double* logL, double* grad, void* stream) {
+    return gb_loglik_grad_aet(ctx, prec, win, n_win, dA, dE, nullptr, wA, wE, nullptr, n_bins, theta, n_rows, logL,
+                              grad, stream);
+}
+
+int gb_loglik_grad_aet(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win, const double* dA,
+                       const double* dE, const double* dT, const double* wA, const double* wE, const double* wT,
+                       int64_t n_bins, const double* theta, int64_t n_rows, double* logL, double* grad,
+                       void* stream) {
     if (!ctx) return GB_EINVAL;
+    if ((dT == nullptr) != (wT == nullptr)) return set_error(ctx, GB_EINVAL, "gb_loglik_grad_aet: dT and wT together");
     if (prec != GB_FP64 && prec != GB_MIXED) return set_error(ctx, GB_EINVAL, "gb_loglik_grad: unknown precision");
     int64_t total = 0;
     int rc = check_windows(ctx, "gb_loglik_grad", win, n_win, n_bins, n_rows, &total);
@@ -120,8 +134,8 @@ int gb_loglik_grad(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_wi
     rc = get_plan(ctx, prec + 16, win, n_win, prec == GB_MIXED ? item : tile_size(ctx, total, 2), &plan);
     if (rc != GB_OK) return rc;
     if (prec == GB_FP64)
-        return launch_grad_fp64(ctx, *plan, dA, dE, wA, wE, theta, logL, grad, (cudaStream_t)stream);
-    return launch_grad_mixed(ctx, *plan, dA, dE, wA, wE, theta, logL, grad, (cudaStream_t)stream);
+        return launch_grad_fp64(ctx, *plan, dA, dE, wA, wE, theta, logL, grad, dT, wT, (cudaStream_t)stream);
+    return launch_grad_mixed(ctx, *plan, dA, dE, wA, wE, theta, logL, grad, dT, wT, (cudaStream_t)stream);
 }
 
 int gb_autotune(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win, const double* dA,

@@ -228,8 +228,10 @@ int launch_loglik_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const d
 int launch_waveform_mixed(gb_ctx* ctx, const double* theta, int64_t B, int N, double* hA,
                           double* hE, double* hT, int64_t* q, cudaStream_t s);
 int launch_grad_fp64(gb_ctx* ctx, const Plan& plan, const double* dA, const double* dE, const double* wA,
-                     const double* wE, const double* theta, double* logL, double* grad, cudaStream_t s);
+                     const double* wE, const double* theta, double* logL, double* grad, const double* dT,
+                     const double* wT, cudaStream_t s);
 int launch_grad_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const double* dE, const double* wA,
-                      const double* wE, const double* theta, double* logL, double* grad, cudaStream_t s);
+                      const double* wE, const double* theta, double* logL, double* grad, const double* dT,
+                      const double* wT, cudaStream_t s);
 
 }  // namespace gb

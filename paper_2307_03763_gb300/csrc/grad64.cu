@@ -167,8 +167,10 @@ struct Geo {
     int N, logN;
 };
 
-// Slow-part response of one sample with eight tangents: returns A and E.
-__device__ void sample_dual(const CandG& c, const Geo& g, const OrbitTables64& tab, int n, DC& Aout, DC& Eout) {
+// Slow-part response of one sample with eight tangents: returns A and E, and
+// T = (X + Y + Z)/sqrt3 when Tout is not null.
+__device__ void sample_dual(const CandG& c, const Geo& g, const OrbitTables64& tab, int n, DC& Aout, DC& Eout,
+                            DC* Tout = nullptr) {
     const int N = g.N;
     const double t = (double)n * g.T_over_N;
     const double f = c.f0 + c.fd * t;
@@ -276,23 +278,25 @@ __device__ void sample_dual(const CandG& c, const Geo& g, const OrbitTables64& t
     const DC Ep = dscale(dadd(dsub(Xp, dscale(Yp, 2.0)), Zp), 1.0 / r6);
     Aout = dmul(F, Ap);
     Eout = dmul(F, Ep);
+    if (Tout) *Tout = dmul(F, dscale(dadd(dadd(Xp, Yp), Zp), 1.0 / sqrt(3.0)));
 }
 
 // forward template (value only), used for the residual
 __device__ void template_value(const CandG& c, const Geo& g, const OrbitTables64& tab, const C* tw, C* bufA,
-                               C* bufE, int lane) {
+                               C* bufE, C* bufT, int lane) {
     const int N = g.N;
     for (int n = lane; n < N; n += 32) {
-        DC Ad, Ed;
-        sample_dual(c, g, tab, n, Ad, Ed);
+        DC Ad, Ed, Td;
+        sample_dual(c, g, tab, n, Ad, Ed, bufT ? &Td : nullptr);
         const int br = (int)(__brev((unsigned)n) >> (32 - g.logN));
         bufA[br] = Ad.v;
         bufE[br] = Ed.v;
+        if (bufT) bufT[br] = Td.v;
     }
     __syncwarp();
 }
 
-__device__ void fft_inplace(int N, int logN, const C* tw, C* bufA, C* bufE, int lane) {
+__device__ void fft_inplace(int N, int logN, const C* tw, C* bufA, C* bufE, C* bufT, int lane) {
     for (int s = 0; s < logN; ++s) {
         const int h = 1 << s;
         const int tstride = kTwiddles >> s;
@@ -307,6 +311,11 @@ __device__ void fft_inplace(int N, int logN, const C* tw, C* bufA, C* bufE, int 
             const C ue = bufE[i0], ve = cmul(w, bufE[i1]);
             bufE[i0] = cadd(ue, ve);
             bufE[i1] = csub(ue, ve);
+            if (bufT) {
+                const C ut = bufT[i0], vt = cmul(w, bufT[i1]);
+                bufT[i0] = cadd(ut, vt);
+                bufT[i1] = csub(ut, vt);
+            }
         }
         __syncwarp();
     }
@@ -321,7 +330,8 @@ __global__ void __launch_bounds__(kWarpsG * 32) grad64_kernel(
     const gb_window_t* __restrict__ wins, const Tile* __restrict__ tiles, TabSet64 tabs, const C* __restrict__ tw_g,
     double T, double fstar, const C* __restrict__ dA, const C* __restrict__ dE, const double* __restrict__ wA,
     const double* __restrict__ wE, const double* __restrict__ theta, double* __restrict__ logL_out,
-    double* __restrict__ grad_out, int* status, int n_max) {
+    double* __restrict__ grad_out, const C* __restrict__ dT, const double* __restrict__ wT, int* status,
+    int n_max) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = (C*)smem_raw;
     double* red = (double*)(tw + kTwiddles);
@@ -332,10 +342,16 @@ __global__ void __launch_bounds__(kWarpsG * 32) grad64_kernel(
     const Tile tile = tiles[blockIdx.x];
     const gb_window_t win = wins[tile.win];
     for (int i = threadIdx.x; i < kTwiddles; i += blockDim.x) tw[i] = tw_g[i];
+    // T enters windows whose lowest frequency is at least f*/2 (dT given)
+    const bool useT = dT != nullptr && (double)win.k0 / T >= 0.5 * fstar;
     double acc = 0.0;
     for (int i = threadIdx.x; i < win.W; i += blockDim.x) {
         const C a = dA[win.data_off + i], e = dE[win.data_off + i];
         acc += wA[win.data_off + i] * (a.x * a.x + a.y * a.y) + wE[win.data_off + i] * (e.x * e.x + e.y * e.y);
+        if (useT) {
+            const C t = dT[win.data_off + i];
+            acc += wT[win.data_off + i] * (t.x * t.x + t.y * t.y);
+        }
     }
     acc = wsum(acc);
     if (lane == 0) red[warp] = acc;
@@ -353,8 +369,9 @@ __global__ void __launch_bounds__(kWarpsG * 32) grad64_kernel(
     g.scale = T / (2.0 * (double)win.N);
     const OrbitTables64 tab = tabs.t[g.logN - 5];
     const int N = g.N;
-    C* bufA = bufs + (size_t)warp * 2 * n_max;
+    C* bufA = bufs + (size_t)warp * (dT ? 3 : 2) * n_max;
     C* bufE = bufA + n_max;
+    C* bufT = useT ? bufE + n_max : nullptr;
     CandG* mycand = cands + warp * 32;
     const int64_t tlen = tile.c_end - tile.c_begin;
     const int64_t grp = (tlen + kWarpsG - 1) / kWarpsG;
@@ -374,8 +391,8 @@ __global__ void __launch_bounds__(kWarpsG * 32) grad64_kernel(
             continue;
         }
         // (1) template
-        template_value(c, g, tab, tw, bufA, bufE, lane);
-        fft_inplace(N, g.logN, tw, bufA, bufE, lane);
+        template_value(c, g, tab, tw, bufA, bufE, bufT, lane);
+        fft_inplace(N, g.logN, tw, bufA, bufE, bufT, lane);
         // (2) logL and residual r_m = w (d - h) at DFT index m mod N, in place
         double sdh = 0.0, shh = 0.0;
         for (int idx = lane; idx < N; idx += 32) {
@@ -394,6 +411,18 @@ __global__ void __launch_bounds__(kWarpsG * 32) grad64_kernel(
             // conjugate for the adjoint transform: c = conj(FFT(conj(r)))
             bufA[idx] = {rA.x, -rA.y};
             bufE[idx] = {rE.x, -rE.y};
+            if (useT) {
+                const C hT = cscale(bufT[idx], g.scale);
+                C rT = {0.0, 0.0};
+                if (kk >= 0 && kk < win.W) {
+                    const C t = dT[win.data_off + kk];
+                    const double wt = wT[win.data_off + kk];
+                    sdh += wt * (t.x * hT.x + t.y * hT.y);
+                    shh += wt * (hT.x * hT.x + hT.y * hT.y);
+                    rT = {wt * (t.x - hT.x), wt * (t.y - hT.y)};
+                }
+                bufT[idx] = {rT.x, -rT.y};
+            }
         }
         sdh = wsum(sdh) * (4.0 / T);
         shh = wsum(shh) * (4.0 / T);
@@ -408,21 +437,31 @@ __global__ void __launch_bounds__(kWarpsG * 32) grad64_kernel(
                 const C te = bufE[i];
                 bufE[i] = bufE[j];
                 bufE[j] = te;
+                if (useT) {
+                    const C tt = bufT[i];
+                    bufT[i] = bufT[j];
+                    bufT[j] = tt;
+                }
             }
         }
         __syncwarp();
-        fft_inplace(N, g.logN, tw, bufA, bufE, lane);
+        fft_inplace(N, g.logN, tw, bufA, bufE, bufT, lane);
         // (4) tangent sweep: g_i += Re(c_n conj(ds_n/dtheta_i)), c_n = conj(buf[n])
         double gacc[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) gacc[k] = 0.0;
         for (int n = lane; n < N; n += 32) {
-            DC Ad, Ed;
-            sample_dual(c, g, tab, n, Ad, Ed);
+            DC Ad, Ed, Td;
+            sample_dual(c, g, tab, n, Ad, Ed, useT ? &Td : nullptr);
             const C cA = {bufA[n].x, -bufA[n].y}, cE = {bufE[n].x, -bufE[n].y};
 #pragma unroll
             for (int k = 0; k < K; ++k)
                 gacc[k] += cA.x * Ad.d[k].x + cA.y * Ad.d[k].y + cE.x * Ed.d[k].x + cE.y * Ed.d[k].y;
+            if (useT) {
+                const C cT = {bufT[n].x, -bufT[n].y};
+#pragma unroll
+                for (int k = 0; k < K; ++k) gacc[k] += cT.x * Td.d[k].x + cT.y * Td.d[k].y;
+            }
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) gacc[k] = wsum(gacc[k]) * (2.0 / (double)N);
@@ -438,16 +477,18 @@ __global__ void __launch_bounds__(kWarpsG * 32) grad64_kernel(
 }  // namespace
 
 int launch_grad_fp64(gb_ctx* ctx, const Plan& plan, const double* dA, const double* dE, const double* wA,
-                     const double* wE, const double* theta, double* logL, double* grad, cudaStream_t s) {
+                     const double* wE, const double* theta, double* logL, double* grad, const double* dT,
+                     const double* wT, cudaStream_t s) {
     if (plan.n_tiles == 0) return GB_OK;
     const size_t smem = sizeof(C) * kTwiddles + sizeof(double) * kWarpsG + sizeof(CandG) * kWarpsG * 32 +
-                        sizeof(C) * kWarpsG * 2 * (size_t)plan.n_max;
+                        sizeof(C) * kWarpsG * (dT ? 3 : 2) * (size_t)plan.n_max;
     cudaError_t e = cudaFuncSetAttribute(grad64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_error(ctx, e, "grad64: smem attribute");
     grad64_kernel<<<plan.n_tiles, kWarpsG * 32, smem, s>>>(plan.d_win, plan.d_tiles, tabset64(ctx),
                                                            (const C*)ctx->d_tw64, ctx->obs.T_obs,
                                                            transfer_frequency(ctx), (const C*)dA, (const C*)dE,
-                                                           wA, wE, theta, logL, grad, ctx->d_status, plan.n_max);
+                                                           wA, wE, theta, logL, grad, (const C*)dT, wT,
+                                                           ctx->d_status, plan.n_max);
     ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "grad64 launch");

@@ -1658,12 +1658,19 @@ __device__ __forceinline__ void link_transfer_d(float X, float2& Tv, float2& Td)
     Td = make_float2(-8.0f * X * da, -2.0f * b + 16.0f * X * X * db);
 }
 
+// the T channel's sample with its tangents and P, Q responses
+struct TOut {
+    DCf S;
+    float2 P, Q;
+};
+
 // One sample of the unit-amplitude slow part at sample n: A and E with the
-// four forward tangents, and the P and Q responses (values).
-template <int J>
+// four forward tangents, and the P and Q responses (values); with T3 also T
+// = (X + Y + Z)/sqrt3 into *to.
+template <int J, bool T3 = false>
 __device__ __forceinline__ void sample_grad(const CandGx& g, const OrbitTables32& tab, int N, int n, float Tf,
                                             float inv_fstar, DCf& SA, DCf& SE, float2& PA, float2& PE, float2& QA,
-                                            float2& QE) {
+                                            float2& QE, TOut* to = nullptr) {
     const CandMix& c = g.m;
     const int R = N >> 5;
     const int p = (n % R) * 32 + brev5(n / R);
@@ -1837,6 +1844,7 @@ __device__ __forceinline__ void sample_grad(const CandGx& g, const OrbitTables32
         const DCf Zp = daddf(dsubf(zm[2], zp[1]), dmulf(D, dsubf(zp[2], zm[1])));
         SA = dmulf(F, dscalef(dsubf(Zp, Xp), r2));
         SE = dmulf(F, dscalef(daddf(dsubf(Xp, dscalef(Yp, 2.0f)), Zp), r6));
+        if constexpr (T3) to->S = dmulf(F, dscalef(daddf(daddf(Xp, Yp), Zp), 0.57735026918962576f));
     }
 #pragma unroll
     for (int w = 0; w < 2; ++w) {
@@ -1854,6 +1862,14 @@ __device__ __forceinline__ void sample_grad(const CandGx& g, const OrbitTables32
         } else {
             QA = Av;
             QE = Ev;
+        }
+        if constexpr (T3) {
+            const float r3 = 0.57735026918962576f;
+            const float2 Tv = cmulf(F.v, make_float2((Xp.x + Yp.x + Zp.x) * r3, (Xp.y + Yp.y + Zp.y) * r3));
+            if (w == 0)
+                to->P = Tv;
+            else
+                to->Q = Tv;
         }
     }
 }
@@ -1916,14 +1932,19 @@ __device__ void residual_adjoint(float2* buf, int ch, const OrbitTables32& tab, 
     __syncwarp();
 }
 
-template <int J>
+// cT (T3, may be null): the T channel's adjoint
+template <int J, bool T3 = false>
 __device__ void tangent_sweep(const CandGx& g, const OrbitTables32& tab, int N, float Tf, float inv_fstar,
                               const float2* cA, const float2* cE, int lane, float (&tacc)[KT][2],
-                              float (&vp)[2][2], float (&vq)[2][2]) {
+                              float (&vp)[2][2], float (&vq)[2][2], const float2* cT = nullptr) {
     for (int n = lane; n < N; n += 32) {
         DCf SA, SE;
         float2 PA, PE, QA, QE;
-        sample_grad<J>(g, tab, N, n, Tf, inv_fstar, SA, SE, PA, PE, QA, QE);
+        TOut to;
+        if (T3 && cT)
+            sample_grad<J, true>(g, tab, N, n, Tf, inv_fstar, SA, SE, PA, PE, QA, QE, &to);
+        else
+            sample_grad<J, false>(g, tab, N, n, Tf, inv_fstar, SA, SE, PA, PE, QA, QE);
         const float2 a = cA[n], e = cE[n];
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
@@ -1940,21 +1961,44 @@ __device__ void tangent_sweep(const CandGx& g, const OrbitTables32& tab, int N, 
         kahan_add(vp[1][0], vp[1][1], fmaf(a.y, PA.x, fmaf(-a.x, PA.y, fmaf(e.y, PE.x, -e.x * PE.y))));
         kahan_add(vq[0][0], vq[0][1], fmaf(a.x, QA.x, fmaf(a.y, QA.y, fmaf(e.x, QE.x, e.y * QE.y))));
         kahan_add(vq[1][0], vq[1][1], fmaf(a.y, QA.x, fmaf(-a.x, QA.y, fmaf(e.y, QE.x, -e.x * QE.y))));
+        if constexpr (T3) {
+            if (cT) {
+                const float2 t = cT[n];
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    f2 sum = make_float2(tacc[2 * p][0], tacc[2 * p + 1][0]);
+                    f2 comp = make_float2(tacc[2 * p][1], tacc[2 * p + 1][1]);
+                    kahan_add2(sum, comp, pfma(bc(t.x), to.S.dr[p], pmul(bc(t.y), to.S.di[p])));
+                    tacc[2 * p][0] = sum.x;
+                    tacc[2 * p + 1][0] = sum.y;
+                    tacc[2 * p][1] = comp.x;
+                    tacc[2 * p + 1][1] = comp.y;
+                }
+                kahan_add(vp[0][0], vp[0][1], fmaf(t.x, to.P.x, t.y * to.P.y));
+                kahan_add(vp[1][0], vp[1][1], fmaf(t.y, to.P.x, -t.x * to.P.y));
+                kahan_add(vq[0][0], vq[0][1], fmaf(t.x, to.Q.x, t.y * to.Q.y));
+                kahan_add(vq[1][0], vq[1][1], fmaf(t.y, to.Q.x, -t.x * to.Q.y));
+            }
+        }
     }
 }
 
-template <int RMAX>
+template <int RMAX, bool T3>
 __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? 2 : 1) grad_mixed_kernel(
     const gb_window_t* __restrict__ wins, const WinMeta* __restrict__ meta, const Win32* __restrict__ prep,
     const Tile* __restrict__ items, int n_items, int* head, TabSet32 tabs, const float2* __restrict__ tw1024,
     double T, double fstar, const double* __restrict__ theta, double* __restrict__ logL,
-    double* __restrict__ grad, int* status, int n_max, unsigned long long budget_ns) {
+    double* __restrict__ grad, int* status, int n_max, unsigned long long budget_ns, long long n_prep) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     CandGx* cands = (CandGx*)smem_raw + warp * 32;
     EpiG* epi = (EpiG*)((CandGx*)smem_raw + kWarpsMx * 32) + warp * 32;
     float2* bufA = (float2*)((EpiG*)((CandGx*)smem_raw + kWarpsMx * 32) + kWarpsMx * 32) + (size_t)warp * 2 * n_max;
     float2* bufE = bufA + n_max;
+    // T3: one more buffer per warp, for T
+    float2* bufT = T3 ? (float2*)((EpiG*)((CandGx*)smem_raw + kWarpsMx * 32) + kWarpsMx * 32) +
+                            (size_t)kWarpsMx * 2 * n_max + (size_t)warp * n_max
+                      : nullptr;
     const LaneTw ltw = lane_twiddles(lane);
     const float Tf = (float)T, inv_fstar = (float)(1.0 / fstar);
     const unsigned long long t0 = global_ns();
@@ -1978,6 +2022,8 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? 2 : 1) grad_mixed_k
         const int N = win.N;
         const OrbitTables32 tab = tabs.t[__ffs(N) - 6];
         const int cnt = (int)(t.c_end - t.c_begin);
+        const bool useT = T3 && wm.use_t;
+        const Win32* pwT = prep + n_prep + wm.prep_off;
         if (lane < cnt) setup_grad_mixed(theta + 8 * (t.c_begin + lane), T, fstar, cands[lane]);
         __syncwarp();
         for (int i = 0; i < cnt; ++i) {
@@ -1985,7 +2031,7 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? 2 : 1) grad_mixed_k
             float sdh = 0.0f, cdh = 0.0f, shh = 0.0f, chh = 0.0f;
             float tacc[KT][2] = {}, vp[2][2] = {}, vq[2][2] = {};
             if (!g.m.bad) {
-                slow_part_dispatch<false>(g.m, tab, N, bufA, bufE, lane);
+                slow_part_dispatch<false, T3>(g.m, tab, N, bufA, bufE, lane, useT ? (float4*)bufT : nullptr);
                 __syncwarp();
                 const long long off64 = g.m.q - win.k0;
                 const int off = (off64 > -(long long)N && off64 < (long long)win.W + N) ? (int)off64 : -4 * N;
@@ -2007,11 +2053,29 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? 2 : 1) grad_mixed_k
                             residual_adjoint<32>(buf, ch, tab, tw1024, ltw, lane, off, win.W, pw, kappa, sdh, cdh, shh, chh);
                     }
                 }
+                if constexpr (T3) {
+                    if (useT) {   // T's data sit in the first slot of each pair of its float copy
+                        if constexpr (RMAX <= 8) {
+                            switch (N) {
+                                case 32: residual_adjoint<1>(bufT, 0, tab, tw1024, ltw, lane, off, win.W, pwT, kappa, sdh, cdh, shh, chh); break;
+                                case 64: residual_adjoint<2>(bufT, 0, tab, tw1024, ltw, lane, off, win.W, pwT, kappa, sdh, cdh, shh, chh); break;
+                                case 128: residual_adjoint<4>(bufT, 0, tab, tw1024, ltw, lane, off, win.W, pwT, kappa, sdh, cdh, shh, chh); break;
+                                default: residual_adjoint<8>(bufT, 0, tab, tw1024, ltw, lane, off, win.W, pwT, kappa, sdh, cdh, shh, chh); break;
+                            }
+                        } else {
+                            if (N == 512)
+                                residual_adjoint<16>(bufT, 0, tab, tw1024, ltw, lane, off, win.W, pwT, kappa, sdh, cdh, shh, chh);
+                            else
+                                residual_adjoint<32>(bufT, 0, tab, tw1024, ltw, lane, off, win.W, pwT, kappa, sdh, cdh, shh, chh);
+                        }
+                    }
+                }
+                const float2* cT = useT ? bufT : nullptr;
                 switch (g.m.J) {
-                    case 4: tangent_sweep<4>(g, tab, N, Tf, inv_fstar, bufA, bufE, lane, tacc, vp, vq); break;
-                    case 7: tangent_sweep<7>(g, tab, N, Tf, inv_fstar, bufA, bufE, lane, tacc, vp, vq); break;
-                    case 10: tangent_sweep<10>(g, tab, N, Tf, inv_fstar, bufA, bufE, lane, tacc, vp, vq); break;
-                    default: tangent_sweep<0>(g, tab, N, Tf, inv_fstar, bufA, bufE, lane, tacc, vp, vq); break;
+                    case 4: tangent_sweep<4, T3>(g, tab, N, Tf, inv_fstar, bufA, bufE, lane, tacc, vp, vq, cT); break;
+                    case 7: tangent_sweep<7, T3>(g, tab, N, Tf, inv_fstar, bufA, bufE, lane, tacc, vp, vq, cT); break;
+                    case 10: tangent_sweep<10, T3>(g, tab, N, Tf, inv_fstar, bufA, bufE, lane, tacc, vp, vq, cT); break;
+                    default: tangent_sweep<0, T3>(g, tab, N, Tf, inv_fstar, bufA, bufE, lane, tacc, vp, vq, cT); break;
                 }
                 __syncwarp();
             }
@@ -2063,10 +2127,12 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? 2 : 1) grad_mixed_k
 }  // namespace
 
 int launch_grad_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const double* dE, const double* wA,
-                      const double* wE, const double* theta, double* logL, double* grad, cudaStream_t s) {
+                      const double* wE, const double* theta, double* logL, double* grad, const double* dT,
+                      const double* wT, cudaStream_t s) {
     if (plan.n_tiles == 0) return GB_OK;
+    const bool t3 = dT != nullptr;
     prep_mixed_kernel<<<plan.n_win, 256, 0, s>>>(plan.d_win, plan.d_meta, plan.d_prep, (const double2*)dA,
-                                                 (const double2*)dE, wA, wE, nullptr, nullptr, plan.n_prep,
+                                                 (const double2*)dE, wA, wE, (const double2*)dT, wT, plan.n_prep,
                                                  ctx->obs.T_obs, transfer_frequency(ctx), plan.d_head);
     ++ctx->launches;
     cudaError_t e = cudaGetLastError();
@@ -2078,9 +2144,11 @@ int launch_grad_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const dou
         const int n_items = part == 0 ? plan.n_large : n_small;
         if (n_items == 0) continue;
         const int nmax = part == 0 ? 1024 : (plan.n_max < 256 ? plan.n_max : 256);
-        const size_t smem =
-            (sizeof(CandGx) + sizeof(EpiG)) * kWarpsMx * 32 + sizeof(float2) * kWarpsMx * 2 * (size_t)nmax;
-        const void* kfn = part == 0 ? (const void*)grad_mixed_kernel<32> : (const void*)grad_mixed_kernel<8>;
+        const size_t smem = (sizeof(CandGx) + sizeof(EpiG)) * kWarpsMx * 32 +
+                            sizeof(float2) * kWarpsMx * (t3 ? 3 : 2) * (size_t)nmax;
+        const void* kfn = t3 ? (part == 0 ? (const void*)grad_mixed_kernel<32, true> : (const void*)grad_mixed_kernel<8, true>)
+                             : (part == 0 ? (const void*)grad_mixed_kernel<32, false>
+                                          : (const void*)grad_mixed_kernel<8, false>);
         e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_error(ctx, e, "grad_mixed: smem attribute");
         int grid = sms * resident_blocks(kfn, kWarpsMx * 32, smem);
@@ -2088,16 +2156,18 @@ int launch_grad_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const dou
         if (grid > need) grid = need;
         const Tile* items = plan.d_tiles + (part == 0 ? 0 : plan.n_large);
         int* head = plan.d_head + (part == 0 ? 1 : 0);
-        if (part == 0)
-            grad_mixed_kernel<32><<<grid, kWarpsMx * 32, smem, s>>>(
-                plan.d_win, plan.d_meta, plan.d_prep, items, n_items, head, tabset32(ctx), (const float2*)ctx->d_tw32,
-                ctx->obs.T_obs, transfer_frequency(ctx), theta, logL, grad, ctx->d_status, nmax, ctx->budget_ns);
-        else
-            grad_mixed_kernel<8><<<grid, kWarpsMx * 32, smem, s>>>(
-                plan.d_win, plan.d_meta, plan.d_prep, items, n_items, head, tabset32(ctx), (const float2*)ctx->d_tw32,
-                ctx->obs.T_obs, transfer_frequency(ctx), theta, logL, grad, ctx->d_status, nmax, ctx->budget_ns);
+        TabSet32 tabs = tabset32(ctx);
+        const float2* tw = (const float2*)ctx->d_tw32;
+        double Tobs = ctx->obs.T_obs, fstar = transfer_frequency(ctx);
+        int* status = ctx->d_status;
+        unsigned long long budget = ctx->budget_ns;
+        long long n_prep = plan.n_prep;
+        int n_it = n_items, n_mx = nmax;
+        void* args[] = {(void*)&plan.d_win, (void*)&plan.d_meta, (void*)&plan.d_prep, (void*)&items, &n_it, &head,
+                        &tabs, &tw, &Tobs, &fstar, (void*)&theta, &logL, &grad, &status, &n_mx, &budget, &n_prep};
+        e = cudaLaunchKernel(kfn, dim3(grid), dim3(kWarpsMx * 32), args, smem, s);
         ++ctx->launches;
-        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_error(ctx, e, "grad_mixed launch");
     }
     return GB_OK;

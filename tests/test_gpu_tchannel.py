@@ -132,6 +132,31 @@ def test_loglik_aet_edge_windows(ctx, prec):
     assert float(g[2][na:].abs().max()) == 0.0          # no template inside: <h|h> = 0
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_loglik_grad_aet_matches_oracle(ctx, prec):
+    # the adjoint gradient with T against autodiff of the oracle's three-channel
+    # likelihood (natural units): FP64 to 1e-9, mixed to 1e-4 of the gradient's
+    # norm; windows below f*/2 and at N = 256, 512, 1,024 above it
+    specs = [(6e-3, 256), (11e-3, 512), (12e-3, 256), (16e-3, 1024)]
+    wins, th, d, w = _problem(13, specs, 3)
+    args = [_c(x, torch.complex128) for x in d] + [_c(x, torch.float64) for x in w]
+    lg, gg = (x.cpu() for x in ctx.loglik_grad_aet(wins, *args, _c(th, torch.float64), prec=prec))
+    lo, go = ogb.loglik_grad_aet(wins, *d, *w, th, T)
+    s = torch.tensor([1 / T, 1 / T ** 2, 1, 1, 1, 1, 1, 1], dtype=torch.float64)
+    tol = 1e-9 if prec == "fp64" else 1e-4
+    for b in range(th.shape[0]):
+        sb = s.clone()
+        sb[4] = th[b, 4]
+        gn, on = gg[b] * sb, go[b] * sb
+        assert float((gn - on).abs().max()) <= tol * float(on.abs().sum()), (prec, b, gn, on)
+    ltol = 1e-10 if prec == "fp64" else 1e-5
+    assert float(((lg - lo).abs() / lo.abs().clamp(min=1.0)).max()) < ltol
+    # without T data it is the A/E gradient
+    g2 = ctx.loglik_grad(wins[:1], args[0], args[1], args[3], args[4], _c(th, torch.float64), prec=prec)[1].cpu()
+    n0 = wins[0][5]
+    assert torch.equal(g2[:n0], gg[:n0])
+
+
 def test_t_channel_argument_errors(ctx):
     from paper_2307_03763_gb300 import api
     rng = np.random.default_rng(9)
