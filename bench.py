@@ -190,11 +190,14 @@ def profiled_traffic():
     import re
     try:
         prof = open(os.path.join(ROOT, "profiles", "loglik_mixed_posterior.md")).read()
-        src = open(os.path.join(ROOT, "paper_2307_03763_gb300", "csrc", "mixed.cu")).read()
+        csrc = os.path.join(ROOT, "paper_2307_03763_gb300", "csrc")
+        common = open(os.path.join(csrc, "mixed_common.cuh")).read()
+        src = open(os.path.join(csrc, "mixed.cu")).read()
     except OSError:
         return None
-    region = src.split("// ---------------------------------------------------------------------------\n"
-                       "// Allocation-free variant")[0]
+    # the kernel's source: the shared header and mixed.cu up to its allocation-free section
+    region = common + src.split("// ---------------------------------------------------------------------------\n"
+                                "// Allocation-free variant")[0]
     # code only: // comments and blank space do not change the kernel
     region = "\n".join(ln.split("//")[0].rstrip() for ln in region.splitlines())
     region = "\n".join(ln for ln in region.splitlines() if ln.strip())

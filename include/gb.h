@@ -204,6 +204,13 @@ int gb_loglik_grad(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_wi
                    int64_t n_bins, const double* theta, int64_t n_rows,
                    double* logL, double* grad, void* stream);
 
+/* gb_loglik_phase with the T channel in the windows above f* / 2 (as
+ * gb_loglik_aet): dh_im sums over A, E and T alike. */
+int gb_loglik_phase_aet(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win,
+                        const double* dA, const double* dE, const double* dT, const double* wA,
+                        const double* wE, const double* wT, int64_t n_bins, const double* theta,
+                        int64_t n_rows, double* logL, double* dh, double* dh_im, double* hh, void* stream);
+
 /* gb_loglik_grad of gb_loglik_aet's likelihood: the T channel in the windows
  * whose lowest frequency is at least f* / 2.  dT and wT as in
  * gb_loglik_aet (device, not NULL; both NULL gives gb_loglik_grad). */

@@ -63,6 +63,8 @@ _SIGNATURES = {
                                  _P, _P, _P, _P]),
     "gb_loglik_aet": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _P, _P, _I64,
                                      _P, _I64, _P, _P, _P, _P]),
+    "gb_loglik_phase_aet": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _P, _P,
+                                           _I64, _P, _I64, _P, _P, _P, _P, _P]),
     "gb_loglik_grad_aet": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _P, _P,
                                           _I64, _P, _I64, _P, _P, _P]),
     "gb_waveform_aet": (ctypes.c_int, [_P, ctypes.c_int, _P, _I64, _I32, _P, _P, _P, _P, _P]),
@@ -240,6 +242,23 @@ class Context:
                                         _ptr(wE), _ptr(wT), nb, _ptr(theta), n, _ptr(logL), _ptr(dh), _ptr(hh),
                                         _stream(self.device)))
         return logL, dh, hh
+
+    def loglik_phase_aet(self, windows, dA, dE, dT, wA, wE, wT, theta, prec="fp64", out=None):
+        """loglik_phase with the T channel above f*/2 (see gb_loglik_phase_aet)."""
+        arr, nw, nb, n = self._data_args(windows, dA, dE, wA, wE, theta)
+        _need(dT, torch.complex128, self.device, "dT", (nb,))
+        _need(wT, torch.float64, self.device, "wT", (nb,))
+        if out is None:
+            out = tuple(torch.zeros(n, dtype=torch.float64, device=self.device) for _ in range(4))
+        logL, dh, dh_im, hh = out
+        _need(dh_im, torch.float64, self.device, "dh_im", (n,))
+        for t, name in ((logL, "logL"), (dh, "dh"), (hh, "hh")):
+            if t is not None:
+                _need(t, torch.float64, self.device, name, (n,))
+        self._check(lib().gb_loglik_phase_aet(self._h, PRECISIONS[prec], arr, nw, _ptr(dA), _ptr(dE), _ptr(dT),
+                                              _ptr(wA), _ptr(wE), _ptr(wT), nb, _ptr(theta), n, _ptr(logL), _ptr(dh),
+                                              _ptr(dh_im), _ptr(hh), _stream(self.device)))
+        return logL, dh, dh_im, hh
 
     def loglik_grad_aet(self, windows, dA, dE, dT, wA, wE, wT, theta, prec="fp64", out=None):
         """logL and d logL / d theta (n, 8) with the T channel above f*/2 (see gb_loglik_grad_aet)."""

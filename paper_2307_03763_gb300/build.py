@@ -16,7 +16,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgb.so")
 
-SOURCES = ["ctx.cu", "api.cu", "fp64.cu", "mixed.cu", "grad64.cu", "mh.cu", "ga.cu", "kde.cu", "noise.cu"]
+SOURCES = ["ctx.cu", "api.cu", "fp64.cu", "mixed.cu", "mixed_variants.cu", "mixed_variants_t.cu",
+           "mixed_grad.cu", "mixed_grad_t.cu", "grad64.cu", "mh.cu", "ga.cu", "kde.cu", "noise.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

@@ -113,6 +113,16 @@ int gb_loglik_grad(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_wi
                               grad, stream);
 }
 
+int gb_loglik_phase_aet(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win, const double* dA,
+                        const double* dE, const double* dT, const double* wA, const double* wE, const double* wT,
+                        int64_t n_bins, const double* theta, int64_t n_rows, double* logL, double* dh,
+                        double* dh_im, double* hh, void* stream) {
+    if (ctx && !dh_im) return set_error(ctx, GB_EINVAL, "gb_loglik_phase_aet: dh_im is null");
+    if (ctx && (!dT || !wT)) return set_error(ctx, GB_EINVAL, "gb_loglik_phase_aet: dT and wT are required");
+    return loglik_impl(ctx, "gb_loglik_phase_aet", prec, win, n_win, dA, dE, wA, wE, n_bins, theta, n_rows, logL, dh,
+                       dh_im, hh, stream, dT, wT);
+}
+
 int gb_loglik_grad_aet(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win, const double* dA,
                        const double* dE, const double* dT, const double* wA, const double* wE, const double* wT,
                        int64_t n_bins, const double* theta, int64_t n_rows, double* logL, double* grad,

@@ -225,6 +225,11 @@ int launch_loglik_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const d
                         const double* wA, const double* wE, const double* theta, double* logL,
                         double* dh, double* hh, double* dh_im, const double* dT, const double* wT,
                         cudaStream_t s);
+// the persistent likelihood kernel with the phase output and/or the T channel
+// (part 0: N >= 512, part 1: N <= 256), compiled in mixed_variants.cu
+const void* mixed_kernel_fn_variant(int part, bool im, bool t3);
+const void* mixed_kernel_fn_t(int part, bool im);            // mixed_variants_t.cu
+const void* grad_mixed_kernel_fn_t(int part);                // mixed_grad_t.cu, the gradient with T
 int launch_waveform_mixed(gb_ctx* ctx, const double* theta, int64_t B, int N, double* hA,
                           double* hE, double* hT, int64_t* q, cudaStream_t s);
 int launch_grad_fp64(gb_ctx* ctx, const Plan& plan, const double* dA, const double* dE, const double* wA,

@@ -1,0 +1,1208 @@
+// mixed_common.cuh -- device code shared by the mixed-precision translation
+// units (likelihood, its variants, waveform, gradient): the per-candidate
+// set-up, the slow part, the transforms, the window preparation and the
+// persistent likelihood kernel template.  Every definition sits in an
+// anonymous namespace, so each translation unit instantiates what it uses.
+//
+// The mixed-precision path: the carrier phase and the bin offset keep
+// double-precision accuracy (double-word float arithmetic), while the detector
+// response, the FFT and the window inner products run in float with
+// compensated sums.  Inputs, the per-window <d|d> and every output are double.
+//
+// Why double-word instead of native double: on GB300 the FP64 pipe issues at
+// 1/64 of the FP32 rate, so a native-double phase (about ten operations per
+// sample) would cost more than the whole float response.  A double-word
+// product with an exact FMA error term costs two or three float operations.
+//
+// Phase of the receiver-j link, in cycles, at u = t/T = n/N (reading R5):
+//   P_j = phi0/2pi + delta u + (fdot T^2/2) u^2 - f0 K(n) - fdot T u K(n)
+//         - f rho_j(n) + (fdot/2) (K + rho_j)^2,
+//   K(n) = k.x_centre/c = Kc cos(alpha_n) + Ks sin(alpha_n),
+//   rho_j = k.(x_j - x_centre)/c,  f = f0 + fdot T u.
+// The first four terms can reach hundreds of cycles and are formed in
+// double-word arithmetic, each product reduced modulo one exactly; the rest
+// are below 0.1 cycle and are float.  exp(2 pi i P_j) is the common factor
+// exp(2 pi i P_c) (one accurate sincospi, applied once per sample to A and E)
+// times exp(2 pi i dP_j) for the small per-spacecraft remainder.
+//
+// Link transfer sinc(X) exp(-iX) = sum_k (-2iX)^k/(k+1)! is evaluated as two
+// Horner polynomials in y = -4X^2 (even and odd k), with the number of terms
+// chosen per candidate from the largest X = f/f* it can reach.
+//
+// Execution: a persistent kernel whose warps take work items (a window and up
+// to 32 of its candidates, 16 by default) from a global queue, most expensive
+// first.  Per item the warp sets the candidates up one per lane, then
+// evaluates them one after the other.  In the likelihood kernel lane l
+// computes samples n = l + 32 r (R = N/32), for N >= 64 two at a time (n and
+// n + 32) with packed two-wide FP32 instructions (sm_100 and later: one FFMA2
+// does the FMAs of both samples), reading the orbit tables in a layout that
+// gives both samples' values as one register pair; the transform is R-point
+// register DFTs around skewed shared-memory transposes, both channels packed
+// together (see fft_inner_ch).
+// The waveform and gradient kernels keep the earlier order n = R brev5(l) + r
+// with a 32-point stage across lanes (shuffles, bit-reversed input, natural
+// output), a lane twiddle and an R-point register FFT, after which lane l
+// holds bins l + 32 k1.  A preparation kernel forms <d|d>, the scale sigma
+// and the float copy of every window once per launch.
+#pragma once
+#include <cmath>
+
+#include "gb_internal.cuh"
+
+namespace gb {
+namespace {
+
+constexpr int kWarpsMx = 4;
+
+struct CandMix {
+    float c0h, c0l;     // phi0 / 2pi mod 1
+    float c1h, c1l;     // delta
+    float c2h, c2l;     // fdot T^2 / 2
+    float Fch, Fcl;     // f0 Kc   (cycles)
+    float Fsh, Fsl;     // f0 Ks
+    float Kc, Ks;       // s
+    float k0, k1, k2;   // propagation direction
+    float u0, u1, u2;   // polarisation basis
+    float v0, v1, v2;
+    float gpr, gxr, gpi, gxi;   // G = (gpr F+ + gxr Fx) + i (gpi F+ + gxi Fx), unit amplitude
+    float f0, fdT, fdh; // Hz, fdot T [Hz], fdot/2 [Hz/s]
+    float a0, a1;       // a = f/(2 f*) = a0 + a1 u
+    float D0r, D0i;     // exp(-i f0/f*)
+    float eps;          // fdot T / f*
+    int J;              // Horner length of the link transfer polynomial (0: direct)
+    int bad;
+    long long q;
+    double A;
+};
+
+// per-candidate sums left by the warp for the lane-parallel epilogue
+template <bool IM>
+struct Epi {
+    float dh_hi, dh_lo, hh_hi, hh_lo;
+};
+template <>
+struct Epi<true> {
+    float dh_hi, dh_lo, hh_hi, hh_lo, im_hi, im_lo;
+};
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 caddf(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csubf(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+__device__ __forceinline__ void split(double x, float& h, float& l) {
+    h = (float)x;
+    l = (float)(x - (double)h);
+}
+
+// exp(-2 pi i m / 32), m < 16: the twiddles of the register DFTs (R <= 32),
+// read with compile-time indices as constant operands
+__constant__ float2 kW32[16] = {
+    {1.000000000e+00f, 0.0f}, {9.807852804e-01f, -1.950903220e-01f},
+    {9.238795325e-01f, -3.826834324e-01f}, {8.314696123e-01f, -5.555702330e-01f},
+    {7.071067812e-01f, -7.071067812e-01f}, {5.555702330e-01f, -8.314696123e-01f},
+    {3.826834324e-01f, -9.238795325e-01f}, {1.950903220e-01f, -9.807852804e-01f},
+    {0.0f, -1.000000000e+00f}, {-1.950903220e-01f, -9.807852804e-01f},
+    {-3.826834324e-01f, -9.238795325e-01f}, {-5.555702330e-01f, -8.314696123e-01f},
+    {-7.071067812e-01f, -7.071067812e-01f}, {-8.314696123e-01f, -5.555702330e-01f},
+    {-9.238795325e-01f, -3.826834324e-01f}, {-9.807852804e-01f, -1.950903220e-01f}};
+
+// 1/k! for the link transfer series (Taylor coefficients of (e^w - 1)/w)
+__constant__ float kInvFact[24] = {
+    1.0f, 1.0f, 0.5f, 1.6666666666666666e-01f, 4.1666666666666664e-02f, 8.3333333333333332e-03f,
+    1.3888888888888889e-03f, 1.9841269841269841e-04f, 2.4801587301587302e-05f, 2.7557319223985893e-06f,
+    2.7557319223985888e-07f, 2.5052108385441720e-08f, 2.0876756987868100e-09f, 1.6059043836821613e-10f,
+    1.1470745597729725e-11f, 7.6471637318198164e-13f, 4.7794773323873853e-14f, 2.8114572543455206e-15f,
+    1.5619206968586225e-16f, 8.2206352466243295e-18f, 4.1103176233121648e-19f, 1.9572941063391263e-20f,
+    8.8967913924505741e-22f, 3.8681701706306835e-23f};
+
+// ifs = 1/f*, formed once per thread by the caller
+__device__ void setup_mixed(const double* th, double T, double ifs, CandMix& c) {
+    const double f0 = th[0], fd = th[1], beta = th[2], lam = th[3];
+    const double A = th[4], iota = th[5], psi = th[6], phi0 = th[7];
+    bool bad = false;
+    for (int i = 0; i < 8; ++i) bad |= !isfinite(th[i]);
+    c.bad = bad;
+    c.A = A;
+    const double f0T = __dmul_rn(f0, T);
+    const double xm = __dadd_rn(f0T, __dmul_rn(__dmul_rn(__dmul_rn(0.5, fd), T), T));
+    const double qd = floor(__dadd_rn(xm, 0.5));
+    c.q = bad ? 0 : (long long)qd;
+    const double delta = __dadd_rn(f0T, -qd);
+    const double inv2pi = 0.15915494309189535;
+    double p0 = phi0 * inv2pi;
+    p0 -= rint(p0);
+    split(p0, c.c0h, c.c0l);
+    split(delta, c.c1h, c.c1l);
+    split(0.5 * fd * T * T, c.c2h, c.c2l);
+    double sb, cb, sl, cl;
+    sincos(beta, &sb, &cb);
+    sincos(lam, &sl, &cl);
+    const double r = kAU / kC;
+    const double Kc = -r * cb * cl, Ks = -r * cb * sl;
+    c.Kc = (float)Kc;
+    c.Ks = (float)Ks;
+    split(f0 * Kc, c.Fch, c.Fcl);
+    split(f0 * Ks, c.Fsh, c.Fsl);
+    const float fsb = (float)sb, fcb = (float)cb, fsl = (float)sl, fcl = (float)cl;
+    c.k0 = -fcb * fcl;
+    c.k1 = -fcb * fsl;
+    c.k2 = -fsb;
+    c.u0 = fsb * fcl;
+    c.u1 = fsb * fsl;
+    c.u2 = -fcb;
+    c.v0 = fsl;
+    c.v1 = -fcl;
+    c.v2 = 0.0f;
+    float s2, c2;
+    sincosf(2.0f * (float)psi, &s2, &c2);
+    const float ci = cosf((float)iota);
+    const float Ap = 1.0f + ci * ci, Ax = -2.0f * ci;
+    c.gpr = Ap * c2;
+    c.gxr = -Ap * s2;
+    c.gpi = -Ax * s2;
+    c.gxi = -Ax * c2;
+    c.f0 = (float)f0;
+    c.fdT = (float)(fd * T);
+    c.fdh = (float)(0.5 * fd);
+    c.a0 = (float)(0.5 * f0 * ifs);
+    c.a1 = (float)(0.5 * fd * T * ifs);
+    float sD, cD;
+    sincosf((float)(f0 * ifs), &sD, &cD);
+    c.D0r = cD;
+    c.D0i = -sD;
+    c.eps = (float)(fd * T * ifs);
+    // largest link argument X = f (1 + |k.n|)/(2 f*) <= f_max / f*; the
+    // tier keeps the first omitted series term below 2e-8 (few tiers: every
+    // tier is a separate copy of the slow part in the instruction cache)
+    const double xmax = fmax(fabs(f0), fabs(f0 + fd * T)) * ifs;
+    c.J = xmax <= 0.489 ? 4 : xmax <= 1.34 ? 7 : xmax <= 2.35 ? 10 : 0;
+}
+
+// sinc(X) exp(-iX), J+1 terms of each series (J = 0: direct evaluation)
+template <int J>
+__device__ __forceinline__ float2 link_transfer(float X) {
+    if (J == 0) {
+        float s, co;
+        sincosf(X, &s, &co);
+        const float sc = X != 0.0f ? s / X : 1.0f;
+        return make_float2(sc * co, -sc * s);
+    }
+    const float y = -4.0f * X * X;
+    float re = kInvFact[2 * J + 1], im = kInvFact[2 * J + 2];
+#pragma unroll
+    for (int j = J - 1; j >= 0; --j) {
+        re = fmaf(re, y, kInvFact[2 * j + 1]);
+        im = fmaf(im, y, kInvFact[2 * j + 2]);
+    }
+    return make_float2(re, -2.0f * X * im);
+}
+
+// exp(2 pi i x) for a receiver phase x = -f k.rho + ..., |x| <= xmax/(2 pi sqrt 3)
+// (each spacecraft is L/sqrt 3 from the guiding centre, and f L/c = xmax/(2 pi)):
+// Taylor series of sin and cos of t = 2 pi x, truncated where the first
+// omitted term is below 2e-8 for the tier's bound on t (J = 4: t <= 0.282,
+// 7: 0.774); sincospif above the J = 7 tier.
+template <int J>
+__device__ __forceinline__ float2 cis_rx(float x) {
+    if constexpr (J == 0 || J >= 10) {
+        float sn, cs;
+        sincospif(2.0f * x, &sn, &cs);
+        return make_float2(cs, sn);
+    } else {
+        const float t = 6.2831853071795865f * x;
+        const float t2 = t * t;
+        float s, co;
+        if constexpr (J <= 4) {
+            s = fmaf(t2, -1.9841269841269841e-04f, 8.3333333333333332e-03f);
+            s = fmaf(s, t2, -1.6666666666666666e-01f);
+            s = fmaf(s * t2, t, t);
+            co = fmaf(t2, -1.3888888888888889e-03f, 4.1666666666666664e-02f);
+            co = fmaf(co, t2, -0.5f);
+            co = fmaf(co, t2, 1.0f);
+        } else {
+            s = fmaf(t2, 2.7557319223985893e-06f, -1.9841269841269841e-04f);
+            s = fmaf(s, t2, 8.3333333333333332e-03f);
+            s = fmaf(s, t2, -1.6666666666666666e-01f);
+            s = fmaf(s * t2, t, t);
+            co = fmaf(t2, -2.7557319223985888e-07f, 2.4801587301587302e-05f);
+            co = fmaf(co, t2, -1.3888888888888889e-03f);
+            co = fmaf(co, t2, 4.1666666666666664e-02f);
+            co = fmaf(co, t2, -0.5f);
+            co = fmaf(co, t2, 1.0f);
+        }
+        return make_float2(co, s);
+    }
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Slow part of one candidate: lane l, step r computes sample n and writes A, E
+// to buf{A,E}[r*32 + l] (conflict-free), with n = l + 32 r (NAT: natural
+// order, for the transform of the likelihood kernel) or n = R brev5(l) + r
+// (for the across-lane transform of the waveform and gradient kernels).
+template <int J, bool NAT>
+__device__ void slow_part_mixed(const CandMix& c, const OrbitTables32& tab, int N, float2* bufA, float2* bufE,
+                                int lane, float4* bufT) {
+    const int R = N >> 5;
+    const float invN = 1.0f / (float)N;
+    const float r2 = 0.70710678118654752f, r6 = 0.40824829046386302f;
+    const int nb = NAT ? lane : R * brev5(lane);
+    const float4* tg = NAT ? tab.gn : tab.g;
+    for (int r = 0; r < R; ++r) {
+        const int p = r * 32 + lane;
+        const float u = (float)(NAT ? nb + 32 * r : nb + r) * invN;
+        const float uu = u * u;
+        const float4 g0 = __ldg(tg + p), g1 = __ldg(tg + N + p);
+        const float4 g2 = __ldg(tg + 2 * N + p), g3 = __ldg(tg + 3 * N + p);
+        const float cah = g3.x, cal = g3.y, sah = g3.z, sal = g3.w;
+        // double-word products, reduced modulo one
+        float p1 = c.c1h * u;
+        const float e1 = fmaf(c.c1h, u, -p1) + c.c1l * u;
+        float p2 = c.c2h * uu;
+        const float e2 = fmaf(c.c2h, uu, -p2) + c.c2l * uu;
+        float p3 = c.Fch * cah;
+        const float e3 = fmaf(c.Fch, cah, -p3) + fmaf(c.Fch, cal, c.Fcl * cah);
+        float p4 = c.Fsh * sah;
+        const float e4 = fmaf(c.Fsh, sah, -p4) + fmaf(c.Fsh, sal, c.Fsl * sah);
+        p1 -= rintf(p1);
+        p2 -= rintf(p2);
+        p3 -= rintf(p3);
+        p4 -= rintf(p4);
+        float s, e, ea, eb, ec;
+        two_sum(c.c0h, p1, s, ea);
+        two_sum(s, p2, s, eb);
+        two_sum(s, -p3, s, ec);
+        two_sum(s, -p4, s, e);
+        s -= rintf(s);
+        const float K = fmaf(c.Kc, cah, c.Ks * sah);
+        const float small = ((c.c0l + e1 + e2 - e3 - e4) + (ea + eb + ec + e)) - c.fdT * u * K;
+        // P_c = hi + lo exactly; exp(2 pi i P_c) = exp(2 pi i hi) (1 + 2 pi i lo)
+        float Pc, Pl;
+        two_sum(s, small, Pc, Pl);
+        Pc -= rintf(Pc);
+        float sPc, cPc;
+        sincospif(2.0f * Pc, &sPc, &cPc);
+        const float tl = 6.2831853071795865f * Pl;
+        const float2 ePc = make_float2(fmaf(-tl, sPc, cPc), fmaf(tl, cPc, sPc));
+        const float f = fmaf(c.fdT, u, c.f0);
+        // k.rho_j: the third from the other two (the centroid is the guiding centre)
+        float krho[3];
+        krho[0] = fmaf(c.k0, g0.x, fmaf(c.k1, g0.y, c.k2 * g0.z));
+        krho[1] = fmaf(c.k0, g0.w, fmaf(c.k1, g1.x, c.k2 * g1.y));
+        krho[2] = -krho[0] - krho[1];
+        float2 rx[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float kap = K + krho[j];
+            const float dP = fmaf(-f, krho[j], c.fdh * kap * kap);
+            rx[j] = cis_rx<J>(dP);   // the common factor exp(2 pi i P_c) is applied once, below
+        }
+        const float a = fmaf(c.a1, u, c.a0);
+        // projections of the arms on k, u, v; arm 2->0 closes the triangle
+        float kn_[3], nu_[3], nv_[3];
+        kn_[0] = fmaf(c.k0, g1.z, fmaf(c.k1, g1.w, c.k2 * g2.x));
+        nu_[0] = fmaf(c.u0, g1.z, fmaf(c.u1, g1.w, c.u2 * g2.x));
+        nv_[0] = fmaf(c.v0, g1.z, fmaf(c.v1, g1.w, c.v2 * g2.x));
+        kn_[1] = fmaf(c.k0, g2.y, fmaf(c.k1, g2.z, c.k2 * g2.w));
+        nu_[1] = fmaf(c.u0, g2.y, fmaf(c.u1, g2.z, c.u2 * g2.w));
+        nv_[1] = fmaf(c.v0, g2.y, fmaf(c.v1, g2.z, c.v2 * g2.w));
+        kn_[2] = -kn_[0] - kn_[1];
+        nu_[2] = -nu_[0] - nu_[1];
+        nv_[2] = -nv_[0] - nv_[1];
+        float2 zp[3], zm[3];   // arm a: link along +n (receiver rc[a]) and -n (receiver em[a])
+#pragma unroll
+        for (int arm = 0; arm < 3; ++arm) {
+            const float kn = kn_[arm], nu = nu_[arm], nv = nv_[arm];
+            const float Fp = (nu - nv) * (nu + nv);
+            const float Fx = 2.0f * nu * nv;
+            const float2 G = make_float2(fmaf(c.gpr, Fp, c.gxr * Fx), fmaf(c.gpi, Fp, c.gxi * Fx));
+            const int rp = arm == 2 ? 0 : arm + 1;   // receiver of the +n link
+            const int rm = arm;                      // receiver of the -n link
+            zp[arm] = cmulf(cmulf(link_transfer<J>(a * (1.0f - kn)), G), rx[rp]);
+            zm[arm] = cmulf(cmulf(link_transfer<J>(a * (1.0f + kn)), G), rx[rm]);
+        }
+        // links: z01 = zp[0], z10 = zm[0], z12 = zp[1], z21 = zm[1], z20 = zp[2], z02 = zm[2]
+        const float du = c.eps * u;
+        const float2 Dc = make_float2(fmaf(-0.5f * du, du, 1.0f), -du);
+        const float2 D = cmulf(make_float2(c.D0r, c.D0i), Dc);
+        const float2 Xp = caddf(csubf(zm[0], zp[2]), cmulf(D, csubf(zp[0], zm[2])));
+        const float2 Yp = caddf(csubf(zm[1], zp[0]), cmulf(D, csubf(zp[1], zm[0])));
+        const float2 Zp = caddf(csubf(zm[2], zp[1]), cmulf(D, csubf(zp[2], zm[1])));
+        // -i a (1 - D^2) = 2 a sin(f/f*) D with sin(f/f*) = -Im D (no
+        // cancellation at low frequency), times the common phase factor
+        const float sa2 = -2.0f * a * D.y;
+        const float2 F = cmulf(make_float2(sa2 * D.x, sa2 * D.y), ePc);
+        const float2 Ap = make_float2((Zp.x - Xp.x) * r2, (Zp.y - Xp.y) * r2);
+        const float2 Ep = make_float2((Xp.x - 2.0f * Yp.x + Zp.x) * r6, (Xp.y - 2.0f * Yp.y + Zp.y) * r6);
+        const float2 oA = cmulf(F, Ap), oE = cmulf(F, Ep);
+        if constexpr (NAT) {   // channel-pair elements for the likelihood transform
+            ((float4*)bufA)[p] = make_float4(oA.x, oE.x, oA.y, oE.y);
+            if (bufT) {   // T = (X + Y + Z)/sqrt3, paired with zero
+                const float r3 = 0.57735026918962576f;
+                const float2 oT = cmulf(F, make_float2((Xp.x + Yp.x + Zp.x) * r3, (Xp.y + Yp.y + Zp.y) * r3));
+                bufT[p] = make_float4(oT.x, 0.0f, oT.y, 0.0f);
+            }
+        } else {
+            bufA[p] = oA;
+            bufE[p] = oE;
+            if (bufT) {   // the waveform's T, as float2 samples
+                const float r3 = 0.57735026918962576f;
+                ((float2*)bufT)[p] = cmulf(F, make_float2((Xp.x + Yp.x + Zp.x) * r3, (Xp.y + Yp.y + Zp.y) * r3));
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The slow part two samples at a time.  Lane l takes the samples n = l + 32 r
+// and n + 32 of one step together; every float operation acts on the pair
+// (x = sample n, y = sample n + 32) as one packed FP32 instruction, and a
+// complex value of the pair is kept as two pairs (real parts, imaginary
+// parts).  The arithmetic is that of slow_part_mixed, operation by operation.
+// ---------------------------------------------------------------------------
+using f2 = float2;
+__device__ __forceinline__ f2 bc(float x) { return make_float2(x, x); }
+__device__ __forceinline__ f2 padd(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 pmul(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 pfma(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 pneg(f2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ f2 psub(f2 a, f2 b) { return __fadd2_rn(a, pneg(b)); }
+__device__ __forceinline__ f2 print(f2 a) { return make_float2(rintf(a.x), rintf(a.y)); }
+
+__device__ __forceinline__ void ptwo_sum(f2 a, f2 b, f2& s, f2& e) {
+    s = padd(a, b);
+    const f2 bb = psub(s, a);
+    e = padd(psub(a, psub(s, bb)), psub(b, bb));
+}
+
+struct cpair {   // two complex numbers: re = (re_x, re_y), im = (im_x, im_y)
+    f2 re, im;
+};
+__device__ __forceinline__ cpair pcmul(cpair a, cpair b) {
+    return cpair{pfma(a.re, b.re, pneg(pmul(a.im, b.im))), pfma(a.re, b.im, pmul(a.im, b.re))};
+}
+__device__ __forceinline__ cpair pcadd(cpair a, cpair b) { return cpair{padd(a.re, b.re), padd(a.im, b.im)}; }
+__device__ __forceinline__ cpair pcsub(cpair a, cpair b) { return cpair{psub(a.re, b.re), psub(a.im, b.im)}; }
+
+// coefficient pairs (1/(2j+1)!, 1/(2j+2)!) of the link series, each value
+// duplicated for the two samples
+__constant__ float4 kLinkPair[11] = {
+    {1.0f, 1.0f, 0.5f, 0.5f},
+    {1.6666666666666666e-01f, 1.6666666666666666e-01f, 4.1666666666666664e-02f, 4.1666666666666664e-02f},
+    {8.3333333333333332e-03f, 8.3333333333333332e-03f, 1.3888888888888889e-03f, 1.3888888888888889e-03f},
+    {1.9841269841269841e-04f, 1.9841269841269841e-04f, 2.4801587301587302e-05f, 2.4801587301587302e-05f},
+    {2.7557319223985893e-06f, 2.7557319223985893e-06f, 2.7557319223985888e-07f, 2.7557319223985888e-07f},
+    {2.5052108385441720e-08f, 2.5052108385441720e-08f, 2.0876756987868100e-09f, 2.0876756987868100e-09f},
+    {1.6059043836821613e-10f, 1.6059043836821613e-10f, 1.1470745597729725e-11f, 1.1470745597729725e-11f},
+    {7.6471637318198164e-13f, 7.6471637318198164e-13f, 4.7794773323873853e-14f, 4.7794773323873853e-14f},
+    {2.8114572543455206e-15f, 2.8114572543455206e-15f, 1.5619206968586225e-16f, 1.5619206968586225e-16f},
+    {8.2206352466243295e-18f, 8.2206352466243295e-18f, 4.1103176233121648e-19f, 4.1103176233121648e-19f},
+    {1.9572941063391263e-20f, 1.9572941063391263e-20f, 8.8967913924505741e-22f, 8.8967913924505741e-22f}};
+
+// link_transfer<J> of a pair
+template <int J>
+__device__ __forceinline__ cpair plink_transfer(f2 X) {
+    if constexpr (J == 0) {
+        const float2 a = link_transfer<0>(X.x), b = link_transfer<0>(X.y);
+        return cpair{make_float2(a.x, b.x), make_float2(a.y, b.y)};
+    } else {
+        const f2 y = pmul(bc(-4.0f), pmul(X, X));
+        const float4 cJ = kLinkPair[J];
+        f2 re = make_float2(cJ.x, cJ.y), im = make_float2(cJ.z, cJ.w);
+#pragma unroll
+        for (int j = J - 1; j >= 0; --j) {
+            const float4 cj = kLinkPair[j];
+            re = pfma(re, y, make_float2(cj.x, cj.y));
+            im = pfma(im, y, make_float2(cj.z, cj.w));
+        }
+        return cpair{re, pmul(pmul(bc(-2.0f), X), im)};
+    }
+}
+
+// cis_rx<J> of a pair
+template <int J>
+__device__ __forceinline__ cpair pcis_rx(f2 x) {
+    if constexpr (J == 0 || J >= 10) {
+        const float2 a = cis_rx<J>(x.x), b = cis_rx<J>(x.y);
+        return cpair{make_float2(a.x, b.x), make_float2(a.y, b.y)};
+    } else {
+        const f2 t = pmul(bc(6.2831853071795865f), x);
+        const f2 t2 = pmul(t, t);
+        f2 s, co;
+        if constexpr (J <= 4) {
+            s = pfma(t2, bc(-1.9841269841269841e-04f), bc(8.3333333333333332e-03f));
+            s = pfma(s, t2, bc(-1.6666666666666666e-01f));
+            s = pfma(pmul(s, t2), t, t);
+            co = pfma(t2, bc(-1.3888888888888889e-03f), bc(4.1666666666666664e-02f));
+            co = pfma(co, t2, bc(-0.5f));
+            co = pfma(co, t2, bc(1.0f));
+        } else {
+            s = pfma(t2, bc(2.7557319223985893e-06f), bc(-1.9841269841269841e-04f));
+            s = pfma(s, t2, bc(8.3333333333333332e-03f));
+            s = pfma(s, t2, bc(-1.6666666666666666e-01f));
+            s = pfma(pmul(s, t2), t, t);
+            co = pfma(t2, bc(-2.7557319223985888e-07f), bc(2.4801587301587302e-05f));
+            co = pfma(co, t2, bc(-1.3888888888888889e-03f));
+            co = pfma(co, t2, bc(4.1666666666666664e-02f));
+            co = pfma(co, t2, bc(-0.5f));
+            co = pfma(co, t2, bc(1.0f));
+        }
+        return cpair{co, s};
+    }
+}
+
+// natural sample order (the likelihood kernel's transform), N >= 64; with
+// T3 and bufT also T = (X + Y + Z)/sqrt3, paired with zero
+template <int J, bool T3>
+__device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N, float2* bufA, float2* bufE,
+                               int lane, float4* bufT) {
+    const int R = N >> 5, H = N >> 1;
+    const float invN = 1.0f / (float)N;
+    const f2 r2 = bc(0.70710678118654752f), r6 = bc(0.40824829046386302f);
+    for (int r = 0; r < R; r += 2) {
+        const int m = (r >> 1) * 32 + lane;
+        float4 t[8];
+#pragma unroll
+        for (int f = 0; f < 8; ++f) t[f] = __ldg(tab.gp + f * H + m);
+        const f2 rho0x = make_float2(t[0].x, t[0].y), rho0y = make_float2(t[0].z, t[0].w);
+        const f2 rho0z = make_float2(t[1].x, t[1].y), rho1x = make_float2(t[1].z, t[1].w);
+        const f2 rho1y = make_float2(t[2].x, t[2].y), rho1z = make_float2(t[2].z, t[2].w);
+        const f2 n0x = make_float2(t[3].x, t[3].y), n0y = make_float2(t[3].z, t[3].w);
+        const f2 n0z = make_float2(t[4].x, t[4].y), n1x = make_float2(t[4].z, t[4].w);
+        const f2 n1y = make_float2(t[5].x, t[5].y), n1z = make_float2(t[5].z, t[5].w);
+        const f2 cah = make_float2(t[6].x, t[6].y), cal = make_float2(t[6].z, t[6].w);
+        const f2 sah = make_float2(t[7].x, t[7].y), sal = make_float2(t[7].z, t[7].w);
+        const int n = lane + 32 * r;
+        const f2 u = pmul(make_float2((float)n, (float)(n + 32)), bc(invN));
+        const f2 uu = pmul(u, u);
+        // double-word products, reduced modulo one
+        f2 p1 = pmul(bc(c.c1h), u);
+        const f2 e1 = pfma(bc(c.c1l), u, pfma(bc(c.c1h), u, pneg(p1)));
+        f2 p2 = pmul(bc(c.c2h), uu);
+        const f2 e2 = pfma(bc(c.c2l), uu, pfma(bc(c.c2h), uu, pneg(p2)));
+        f2 p3 = pmul(bc(c.Fch), cah);
+        const f2 e3 = padd(pfma(bc(c.Fch), cah, pneg(p3)), pfma(bc(c.Fch), cal, pmul(bc(c.Fcl), cah)));
+        f2 p4 = pmul(bc(c.Fsh), sah);
+        const f2 e4 = padd(pfma(bc(c.Fsh), sah, pneg(p4)), pfma(bc(c.Fsh), sal, pmul(bc(c.Fsl), sah)));
+        p1 = psub(p1, print(p1));
+        p2 = psub(p2, print(p2));
+        p3 = psub(p3, print(p3));
+        p4 = psub(p4, print(p4));
+        f2 s, e, ea, eb, ec;
+        ptwo_sum(bc(c.c0h), p1, s, ea);
+        ptwo_sum(s, p2, s, eb);
+        ptwo_sum(s, pneg(p3), s, ec);
+        ptwo_sum(s, pneg(p4), s, e);
+        s = psub(s, print(s));
+        const f2 K = pfma(bc(c.Kc), cah, pmul(bc(c.Ks), sah));
+        const f2 lo = padd(psub(psub(padd(padd(bc(c.c0l), e1), e2), e3), e4), padd(padd(padd(ea, eb), ec), e));
+        const f2 small = pfma(pneg(pmul(bc(c.fdT), u)), K, lo);
+        f2 Pc, Pl;
+        ptwo_sum(s, small, Pc, Pl);
+        Pc = psub(Pc, print(Pc));
+        float sx, cx, sy, cy;
+        sincospif(2.0f * Pc.x, &sx, &cx);
+        sincospif(2.0f * Pc.y, &sy, &cy);
+        const f2 sP = make_float2(sx, sy), cP = make_float2(cx, cy);
+        const f2 tl = pmul(bc(6.2831853071795865f), Pl);
+        const cpair ePc{pfma(pneg(tl), sP, cP), pfma(tl, cP, sP)};
+        const f2 fr = pfma(bc(c.fdT), u, bc(c.f0));
+        f2 krho[3];
+        krho[0] = pfma(bc(c.k0), rho0x, pfma(bc(c.k1), rho0y, pmul(bc(c.k2), rho0z)));
+        krho[1] = pfma(bc(c.k0), rho1x, pfma(bc(c.k1), rho1y, pmul(bc(c.k2), rho1z)));
+        krho[2] = psub(pneg(krho[0]), krho[1]);
+        cpair rx[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const f2 kap = padd(K, krho[j]);
+            const f2 dP = pfma(pneg(fr), krho[j], pmul(pmul(bc(c.fdh), kap), kap));
+            rx[j] = pcis_rx<J>(dP);
+        }
+        const f2 a = pfma(bc(c.a1), u, bc(c.a0));
+        f2 kn_[3], nu_[3], nv_[3];
+        kn_[0] = pfma(bc(c.k0), n0x, pfma(bc(c.k1), n0y, pmul(bc(c.k2), n0z)));
+        nu_[0] = pfma(bc(c.u0), n0x, pfma(bc(c.u1), n0y, pmul(bc(c.u2), n0z)));
+        nv_[0] = pfma(bc(c.v0), n0x, pfma(bc(c.v1), n0y, pmul(bc(c.v2), n0z)));
+        kn_[1] = pfma(bc(c.k0), n1x, pfma(bc(c.k1), n1y, pmul(bc(c.k2), n1z)));
+        nu_[1] = pfma(bc(c.u0), n1x, pfma(bc(c.u1), n1y, pmul(bc(c.u2), n1z)));
+        nv_[1] = pfma(bc(c.v0), n1x, pfma(bc(c.v1), n1y, pmul(bc(c.v2), n1z)));
+        kn_[2] = psub(pneg(kn_[0]), kn_[1]);
+        nu_[2] = psub(pneg(nu_[0]), nu_[1]);
+        nv_[2] = psub(pneg(nv_[0]), nv_[1]);
+        cpair zp[3], zm[3];
+#pragma unroll
+        for (int arm = 0; arm < 3; ++arm) {
+            const f2 kn = kn_[arm], nu = nu_[arm], nv = nv_[arm];
+            const f2 Fp = pmul(psub(nu, nv), padd(nu, nv));
+            const f2 Fx = pmul(pmul(bc(2.0f), nu), nv);
+            const cpair G{pfma(bc(c.gpr), Fp, pmul(bc(c.gxr), Fx)), pfma(bc(c.gpi), Fp, pmul(bc(c.gxi), Fx))};
+            const int rp = arm == 2 ? 0 : arm + 1;
+            const int rm = arm;
+            zp[arm] = pcmul(pcmul(plink_transfer<J>(pmul(a, psub(bc(1.0f), kn))), G), rx[rp]);
+            zm[arm] = pcmul(pcmul(plink_transfer<J>(pmul(a, padd(bc(1.0f), kn))), G), rx[rm]);
+        }
+        const f2 du = pmul(bc(c.eps), u);
+        const cpair Dc{pfma(pmul(bc(-0.5f), du), du, bc(1.0f)), pneg(du)};
+        const cpair D = pcmul(cpair{bc(c.D0r), bc(c.D0i)}, Dc);
+        const cpair Xp = pcadd(pcsub(zm[0], zp[2]), pcmul(D, pcsub(zp[0], zm[2])));
+        const cpair Yp = pcadd(pcsub(zm[1], zp[0]), pcmul(D, pcsub(zp[1], zm[0])));
+        const cpair Zp = pcadd(pcsub(zm[2], zp[1]), pcmul(D, pcsub(zp[2], zm[1])));
+        const f2 sa2 = pmul(pmul(bc(-2.0f), a), D.im);
+        const cpair F = pcmul(cpair{pmul(sa2, D.re), pmul(sa2, D.im)}, ePc);
+        const cpair Ap{pmul(psub(Zp.re, Xp.re), r2), pmul(psub(Zp.im, Xp.im), r2)};
+        const cpair Ep{pmul(padd(psub(Xp.re, pmul(bc(2.0f), Yp.re)), Zp.re), r6),
+                       pmul(padd(psub(Xp.im, pmul(bc(2.0f), Yp.im)), Zp.im), r6)};
+        const cpair oA = pcmul(F, Ap), oE = pcmul(F, Ep);
+        // channel-pair elements (A re, E re, A im, E im) for the transform
+        const int p = r * 32 + lane;
+        float4* buf = (float4*)bufA;
+        buf[p] = make_float4(oA.re.x, oE.re.x, oA.im.x, oE.im.x);
+        buf[p + 32] = make_float4(oA.re.y, oE.re.y, oA.im.y, oE.im.y);
+        if constexpr (T3) {
+            if (bufT) {
+                const f2 r3 = bc(0.57735026918962576f);
+                const cpair Tp{pmul(padd(padd(Xp.re, Yp.re), Zp.re), r3), pmul(padd(padd(Xp.im, Yp.im), Zp.im), r3)};
+                const cpair oT = pcmul(F, Tp);
+                bufT[p] = make_float4(oT.re.x, 0.0f, oT.im.x, 0.0f);
+                bufT[p + 32] = make_float4(oT.re.y, 0.0f, oT.im.y, 0.0f);
+            }
+        }
+    }
+}
+
+template <bool NAT, bool T3 = false>
+__device__ void slow_part_dispatch(const CandMix& c, const OrbitTables32& tab, int N, float2* bufA, float2* bufE,
+                                   int lane, float4* bufT = nullptr) {
+    if constexpr (NAT) {
+        if (N >= 64) {
+            switch (c.J) {
+                case 4: slow_part_pair<4, T3>(c, tab, N, bufA, bufE, lane, bufT); break;
+                case 7: slow_part_pair<7, T3>(c, tab, N, bufA, bufE, lane, bufT); break;
+                case 10: slow_part_pair<10, T3>(c, tab, N, bufA, bufE, lane, bufT); break;
+                default: slow_part_pair<0, T3>(c, tab, N, bufA, bufE, lane, bufT); break;
+            }
+            return;
+        }
+    }
+    float4* bt = T3 ? bufT : nullptr;
+    switch (c.J) {
+        case 4: slow_part_mixed<4, NAT>(c, tab, N, bufA, bufE, lane, bt); break;
+        case 7: slow_part_mixed<7, NAT>(c, tab, N, bufA, bufE, lane, bt); break;
+        case 10: slow_part_mixed<10, NAT>(c, tab, N, bufA, bufE, lane, bt); break;
+        default: slow_part_mixed<0, NAT>(c, tab, N, bufA, bufE, lane, bt); break;
+    }
+}
+
+// Per-lane twiddles of the across-lane radix-2 stages (half size h = 2^s):
+// the upper lane of a pair multiplies its value by exp(-i pi (l mod h)/h).
+struct LaneTw {
+    float2 w[4];   // stages h = 2, 4, 8, 16 (h = 1 has twiddle 1)
+};
+
+__device__ __forceinline__ LaneTw lane_twiddles(int lane) {
+    LaneTw t;
+#pragma unroll
+    for (int s = 1; s < 5; ++s) {
+        const int h = 1 << s;
+        if (lane & h) {
+            float sn, cs;
+            sincospif((float)(lane & (h - 1)) / (float)h, &sn, &cs);
+            t.w[s - 1] = make_float2(cs, -sn);
+        } else {
+            t.w[s - 1] = make_float2(1.0f, 0.0f);
+        }
+    }
+    return t;
+}
+
+// 32-point DFT across the lanes: lane l holds element brev5(l) of the
+// sequence on entry and element l of its transform on exit (radix-2 DIT).
+__device__ __forceinline__ float2 lane_fft(float2 x, const LaneTw& tw, int lane) {
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int h = 1 << s;
+        const float2 u = s == 0 ? x : cmulf(x, tw.w[s - 1]);
+        const float2 v = make_float2(__shfl_xor_sync(0xffffffffu, u.x, h), __shfl_xor_sync(0xffffffffu, u.y, h));
+        x = (lane & h) ? csubf(v, u) : caddf(u, v);
+    }
+    return x;
+}
+
+// R-point DFT in registers, natural order in and out (radix-2 DIT with a
+// compile-time bit reversal); twiddles exp(-2 pi i j / R) from the table of
+// exp(-2 pi i k / 1024), k < 512.
+template <int R>
+__device__ __forceinline__ void reg_fft(float2 (&x)[R], const float2* __restrict__ tw1024) {
+    if constexpr (R > 1) {
+        constexpr int LR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : R == 16 ? 4 : 5;
+        float2 y[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            int b = 0;
+#pragma unroll
+            for (int k = 0; k < LR; ++k) b |= ((i >> k) & 1) << (LR - 1 - k);
+            y[b] = x[i];
+        }
+#pragma unroll
+        for (int s = 0; s < LR; ++s) {
+            const int h = 1 << s;
+#pragma unroll
+            for (int b = 0; b < R / 2; ++b) {
+                const int j = b & (h - 1);
+                const int i0 = ((b >> s) << (s + 1)) + j;
+                const int i1 = i0 + h;
+                float2 t;
+                if (j == 0) {
+                    t = y[i1];
+                } else if (4 * j == 2 * h) {   // exp(-i pi/2) = -i
+                    t = make_float2(y[i1].y, -y[i1].x);
+                } else {
+                    t = cmulf(kW32[j * (16 / h)], y[i1]);
+                }
+                y[i1] = csubf(y[i0], t);
+                y[i0] = caddf(y[i0], t);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) x[i] = y[i];
+    }
+}
+
+__device__ __forceinline__ void kahan_add(float& sum, float& comp, float x) {
+    const float y = x - comp;
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+// Transform one channel (R values per lane in buf[r*32 + lane]) into bins
+// l + 32 k1 held in x[k1].
+template <int R>
+__device__ __forceinline__ void channel_fft(const float2* buf, const OrbitTables32& tab, const float2* tw1024,
+                                            const LaneTw& ltw, int lane, float2 (&x)[R]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = lane_fft(buf[r * 32 + lane], ltw, lane);
+#pragma unroll
+    for (int r = 1; r < R; ++r) x[r] = cmulf(x[r], __ldg(tab.ltw + r * 32 + lane));
+    reg_fft<R>(x, tw1024);
+}
+
+// ---------------------------------------------------------------------------
+// Transform of the likelihood kernel.  Input: lane l holds samples
+// n = l + 32 r, r < R (R = N/32).  With n = l + 32 r and bin K = k1 + R k2,
+//   S[K] = sum_l w32^(l k2) [ wN^(l k1) sum_r s[l + 32 r] wR^(r k1) ],
+// so each lane first takes an R-point DFT of its own samples and a twiddle;
+// a transpose through shared memory then gives each group of G = 32/R lanes
+// one of the R 32-point DFTs, factored as 32 = R x G over l = j + G m:
+//   sum_l y_l w32^(l k2) = sum_j w32^(j ka) wG^(j kb) sum_m y_(j+Gm) wR^(m ka),
+//   k2 = ka + R kb:
+// an R-point DFT in registers, a twiddle, and a G-point DFT across the
+// group's lanes -- by a second transpose and register DFTs when R >= G, by
+// radix-2 decimation-in-frequency shuffles otherwise.  Both transposes are
+// skewed so that every half-warp access touches 16 distinct banks.
+// ---------------------------------------------------------------------------
+
+// element (k1, l) of the first transpose: row k1 of 32, rotated by G k1
+template <int R>
+__device__ __forceinline__ int t1_addr(int k1, int l) {
+    return 32 * k1 + ((l + (32 / R) * k1) & 31);
+}
+
+// element (group g, ka, u, v) of the second transpose for R = 4 (G = 8):
+// lane j = u + 2v of group g holds ka; lane 2 ka + u collects v = 0..3
+__device__ __forceinline__ int t2_addr4(int g, int ka, int u, int v) {
+    const int h = g >> 1, gp = g & 1;
+    return 64 * h + 16 * ka + ((8 * gp + 4 * u + v + ka) & 15);
+}
+
+// element (group g, lane j of the group, ka) of the second transpose (R >= 8),
+// in 16-byte elements: row g G + j of R elements, the low three index bits
+// rotated so that every quarter-warp access touches 8 distinct 16-byte bank
+// groups (rotation constants found by checking all accesses of each R)
+template <int R>
+__device__ __forceinline__ int t2_addr(int g, int j, int ka) {
+    constexpr int G = 32 / R;
+    constexpr int a = R == 8 ? 2 : R == 16 ? 1 : 0, b = R == 16 ? 2 : 1, c = R == 16 ? 1 : 0;
+    return (g * G + j) * R + (ka & ~7) + ((ka + a * j + b * g + c * (ka >> 3)) & 7);
+}
+
+// bit reversal of the low b bits
+__device__ __forceinline__ int brev_bits(int x, int b) { return b == 0 ? 0 : (int)(__brev((unsigned)x) >> (32 - b)); }
+
+// The transform works on both channels at once: a value is a cpair with
+// channel A in .x and channel E in .y of its real and imaginary pairs, kept in
+// shared memory as one 16-byte element (A re, E re, A im, E im).
+__device__ __forceinline__ cpair ld4(const float4* p) {
+    const float4 v = *p;
+    return cpair{make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ cpair ldg4(const float4* p) {
+    const float4 v = __ldg(p);
+    return cpair{make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ void st4(float4* p, cpair v) { *p = make_float4(v.re.x, v.re.y, v.im.x, v.im.y); }
+__device__ __forceinline__ cpair pmul_mi(cpair v) { return cpair{v.im, pneg(v.re)}; }   // times -i
+
+// exp(-2 pi i m / 32), m < 16, each part duplicated for the two channels
+__constant__ float4 kW32d[16] = {
+    {1.000000000e+00f, 1.000000000e+00f, 0.0f, 0.0f},
+    {9.807852804e-01f, 9.807852804e-01f, -1.950903220e-01f, -1.950903220e-01f},
+    {9.238795325e-01f, 9.238795325e-01f, -3.826834324e-01f, -3.826834324e-01f},
+    {8.314696123e-01f, 8.314696123e-01f, -5.555702330e-01f, -5.555702330e-01f},
+    {7.071067812e-01f, 7.071067812e-01f, -7.071067812e-01f, -7.071067812e-01f},
+    {5.555702330e-01f, 5.555702330e-01f, -8.314696123e-01f, -8.314696123e-01f},
+    {3.826834324e-01f, 3.826834324e-01f, -9.238795325e-01f, -9.238795325e-01f},
+    {1.950903220e-01f, 1.950903220e-01f, -9.807852804e-01f, -9.807852804e-01f},
+    {0.0f, 0.0f, -1.000000000e+00f, -1.000000000e+00f},
+    {-1.950903220e-01f, -1.950903220e-01f, -9.807852804e-01f, -9.807852804e-01f},
+    {-3.826834324e-01f, -3.826834324e-01f, -9.238795325e-01f, -9.238795325e-01f},
+    {-5.555702330e-01f, -5.555702330e-01f, -8.314696123e-01f, -8.314696123e-01f},
+    {-7.071067812e-01f, -7.071067812e-01f, -7.071067812e-01f, -7.071067812e-01f},
+    {-8.314696123e-01f, -8.314696123e-01f, -5.555702330e-01f, -5.555702330e-01f},
+    {-9.238795325e-01f, -9.238795325e-01f, -3.826834324e-01f, -3.826834324e-01f},
+    {-9.807852804e-01f, -9.807852804e-01f, -1.950903220e-01f, -1.950903220e-01f}};
+
+// reg_fft<R> on channel pairs
+template <int R>
+__device__ __forceinline__ void reg_fft2(cpair (&x)[R]) {
+    if constexpr (R > 1) {
+        constexpr int LR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : R == 16 ? 4 : 5;
+        cpair y[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            int b = 0;
+#pragma unroll
+            for (int k = 0; k < LR; ++k) b |= ((i >> k) & 1) << (LR - 1 - k);
+            y[b] = x[i];
+        }
+#pragma unroll
+        for (int s = 0; s < LR; ++s) {
+            const int h = 1 << s;
+#pragma unroll
+            for (int b = 0; b < R / 2; ++b) {
+                const int j = b & (h - 1);
+                const int i0 = ((b >> s) << (s + 1)) + j;
+                const int i1 = i0 + h;
+                cpair t;
+                if (j == 0) {
+                    t = y[i1];
+                } else if (4 * j == 2 * h) {   // exp(-i pi/2) = -i
+                    t = pmul_mi(y[i1]);
+                } else {
+                    const float4 w = kW32d[j * (16 / h)];
+                    t = pcmul(cpair{make_float2(w.x, w.y), make_float2(w.z, w.w)}, y[i1]);
+                }
+                y[i1] = pcsub(y[i0], t);
+                y[i0] = pcadd(y[i0], t);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) x[i] = y[i];
+    }
+}
+
+// G-point DFT of v[0..G) in registers, natural order in and out (G = 1, 2, 4)
+template <int G>
+__device__ __forceinline__ void dft_small2(cpair* v) {
+    if constexpr (G == 2) {
+        const cpair a = v[0], b = v[1];
+        v[0] = pcadd(a, b);
+        v[1] = pcsub(a, b);
+    } else if constexpr (G == 4) {
+        const cpair s02 = pcadd(v[0], v[2]), d02 = pcsub(v[0], v[2]);
+        const cpair s13 = pcadd(v[1], v[3]), d13 = pcsub(v[1], v[3]);
+        v[0] = pcadd(s02, s13);
+        v[2] = pcsub(s02, s13);
+        v[1] = cpair{padd(d02.re, d13.im), psub(d02.im, d13.re)};   // d02 - i d13
+        v[3] = cpair{psub(d02.re, d13.im), padd(d02.im, d13.re)};   // d02 + i d13
+    }
+}
+
+__device__ __forceinline__ cpair shfl_xor4(cpair v, int m) {
+    return cpair{make_float2(__shfl_xor_sync(0xffffffffu, v.re.x, m), __shfl_xor_sync(0xffffffffu, v.re.y, m)),
+                 make_float2(__shfl_xor_sync(0xffffffffu, v.im.x, m), __shfl_xor_sync(0xffffffffu, v.im.y, m))};
+}
+
+__device__ __forceinline__ void kahan_add2(f2& sum, f2& comp, f2 x) {
+    const f2 y = psub(x, comp);
+    const f2 t = padd(sum, y);
+    comp = psub(psub(t, sum), y);
+    sum = t;
+}
+
+// the two channels' Kahan pairs as one: the sum is s - c
+__device__ __forceinline__ void kahan_merge(f2 sum, f2 comp, float& s, float& c) {
+    float e;
+    two_sum(sum.x, sum.y, s, e);
+    c = (comp.x + comp.y) - e;
+}
+
+// Both channels of one candidate (buf: N channel-pair elements, sample n at
+// n): transform, then the window inner products (with IM also the imaginary
+// part of sum w d conj(h)); each sum is returned as s - c.
+template <int R, bool IM>
+__device__ void fft_inner_ch(float4* buf, const OrbitTables32& tab, const LaneTw& ltw, int lane, int off, int W,
+                             const Win32* __restrict__ pw, float& sdh, float& cdh, float& shh, float& chh, float& sim,
+                             float& cim) {
+    constexpr int N = 32 * R, G = 32 / R;
+    constexpr int LG = G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 8 ? 3 : G == 16 ? 4 : 5;
+    const int g = lane / G, j = lane % G;
+    cpair x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = ld4(buf + r * 32 + lane);
+    reg_fft2<R>(x);
+#pragma unroll
+    for (int k1 = 1; k1 < R; ++k1) x[k1] = pcmul(x[k1], ldg4(tab.ltw4 + k1 * 32 + lane));
+    if constexpr (R > 1) {
+        __syncwarp();
+#pragma unroll
+        for (int k1 = 0; k1 < R; ++k1) st4(buf + t1_addr<R>(k1, lane), x[k1]);
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < R; ++m) x[m] = ld4(buf + t1_addr<R>(g, j + G * m));
+        reg_fft2<R>(x);
+        if constexpr (G > 1) {
+            // exp(-2 pi i j ka / 32) = exp(-2 pi i (R j) ka / N): the lane-twiddle table
+#pragma unroll
+            for (int ka = 1; ka < R; ++ka) x[ka] = pcmul(x[ka], ldg4(tab.ltw4 + ka * 32 + R * j));
+        }
+    }
+    // x[q] is the value of bin K(q): the G-point stage, then the bin map
+    int kbase;   // K(q) = g + R*(ka(q) + R*kb(q)) with ka, kb per branch below
+    if constexpr (R == 4) {
+        // 8 = 4 x 2 over j = u + 2v: lane 2 ka + u gathers v = 0..3, a 4-point
+        // DFT over v, twiddle exp(-2 pi i u kv / 8), a 2-point DFT over u
+        // across the lane pair; it then holds kb = kv + 4 u, kv = 0..3
+        const int u = j & 1, ka = j >> 1;
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) st4(buf + t2_addr4(g, q, j & 1, j >> 1), x[q]);
+        __syncwarp();
+#pragma unroll
+        for (int v = 0; v < 4; ++v) x[v] = ld4(buf + t2_addr4(g, ka, u, v));
+        dft_small2<4>(x);
+        if (u) {
+            const f2 r = bc(0.70710678118654752f);
+            x[1] = cpair{pmul(r, padd(x[1].re, x[1].im)), pmul(r, psub(x[1].im, x[1].re))};     // * exp(-i pi/4)
+            x[2] = pmul_mi(x[2]);                                                                  // * -i
+            x[3] = cpair{pmul(r, psub(x[3].im, x[3].re)), pneg(pmul(r, padd(x[3].re, x[3].im)))};  // * exp(-3 i pi/4)
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const cpair v = shfl_xor4(x[q], 1);
+            x[q] = u ? pcsub(v, x[q]) : pcadd(x[q], v);
+        }
+        kbase = g + 4 * ka + 64 * u;   // + 16 kv for x[kv]: K = g + 4 (ka + 4 (kv + 4 u))
+    } else if constexpr (R >= G && G > 1) {
+        __syncwarp();
+#pragma unroll
+        for (int ka = 0; ka < R; ++ka) st4(buf + t2_addr<R>(g, j, ka), x[ka]);
+        __syncwarp();
+        // lane j now takes ka = (R/G) j + t for t < R/G, all G lanes of the group
+#pragma unroll
+        for (int t = 0; t < R / G; ++t) {
+#pragma unroll
+            for (int j2 = 0; j2 < G; ++j2) x[t * G + j2] = ld4(buf + t2_addr<R>(g, j2, (R / G) * j + t));
+            dft_small2<G>(x + t * G);
+        }
+        kbase = g + R * (R / G) * j;   // + R t + R^2 kb for x[t G + kb]
+    } else if constexpr (G > 1) {
+        // radix-2 decimation in frequency across the group's lanes
+#pragma unroll
+        for (int s = LG - 1; s >= 0; --s) {
+            const int h = 1 << s;
+            const bool upper = (lane & h) != 0;
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const cpair v = shfl_xor4(x[q], h);
+                if (!upper) {
+                    x[q] = pcadd(x[q], v);
+                } else {
+                    const cpair d = pcsub(v, x[q]);
+                    x[q] = s == 0 ? d : pcmul(d, cpair{bc(ltw.w[s - 1].x), bc(ltw.w[s - 1].y)});
+                }
+            }
+        }
+        kbase = g + R * R * brev_bits(j, LG);   // + R ka for x[ka]
+    } else {
+        kbase = g;   // G = 1: + R ka for x[ka]
+    }
+    const f2 z = bc(0.0f);
+    f2 s_dh = z, c_dh = z, s_hh = z, c_hh = z, s_im = z, c_im = z;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        int K;
+        if constexpr (R == 4) K = kbase + 16 * q;
+        else if constexpr (R >= G && G > 1) K = kbase + R * (q / G) + R * R * (q % G);
+        else K = kbase + R * q;
+        const int m = K < N / 2 ? K : K - N;
+        const int kk = off + m;
+        if (kk >= 0 && kk < W) {
+            const Win32 v = pw[kk];
+            // explicit products: the same rounding in every kernel that forms these sums
+            kahan_add2(s_dh, c_dh, pmul(v.w, pfma(v.dre, x[q].re, pmul(v.dim, x[q].im))));
+            kahan_add2(s_hh, c_hh, pmul(v.w, pfma(x[q].re, x[q].re, pmul(x[q].im, x[q].im))));
+            if constexpr (IM) kahan_add2(s_im, c_im, pmul(v.w, pfma(v.dim, x[q].re, pneg(pmul(v.dre, x[q].im)))));
+        }
+    }
+    kahan_merge(s_dh, c_dh, sdh, cdh);
+    kahan_merge(s_hh, c_hh, shh, chh);
+    if constexpr (IM) kahan_merge(s_im, c_im, sim, cim);
+}
+
+// Compensated warp sum of Kahan pairs: returns hi + lo on every lane.
+__device__ __forceinline__ void warp_sum2(float sum, float comp, float& hi, float& lo) {
+    hi = sum;
+    lo = -comp;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        float s, e;
+        two_sum(hi, h2, s, e);
+        hi = s;
+        lo = lo + l2 + e;
+    }
+}
+
+// dT, wT (may be null): the T channel, used in windows whose lowest frequency
+// k0/T is at least f*/2; its float copy goes n_prep entries after A and E's.
+__global__ void prep_mixed_kernel(const gb_window_t* __restrict__ wins, WinMeta* __restrict__ meta,
+                                  Win32* __restrict__ prep, const double2* __restrict__ dA,
+                                  const double2* __restrict__ dE, const double* __restrict__ wA,
+                                  const double* __restrict__ wE, const double2* __restrict__ dT,
+                                  const double* __restrict__ wT, long long n_prep, double T, double fstar,
+                                  int* head) {
+    __shared__ double s_acc[32], s_max[32];
+    const int w = blockIdx.x;
+    if (w == 0 && threadIdx.x < 2) head[threadIdx.x] = 0;   // both work queues
+    const gb_window_t win = wins[w];
+    const bool useT = dT != nullptr && (double)win.k0 / T >= 0.5 * fstar;
+    double acc = 0.0, wmax = 0.0;
+    for (int i = threadIdx.x; i < win.W; i += blockDim.x) {
+        const double2 a = dA[win.data_off + i], e = dE[win.data_off + i];
+        const double wa = wA[win.data_off + i], we = wE[win.data_off + i];
+        acc += wa * (a.x * a.x + a.y * a.y) + we * (e.x * e.x + e.y * e.y);
+        wmax = fmax(wmax, fmax(wa, we));
+        if (useT) {
+            const double2 t = dT[win.data_off + i];
+            const double wt = wT[win.data_off + i];
+            acc += wt * (t.x * t.x + t.y * t.y);
+            wmax = fmax(wmax, wt);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        wmax = fmax(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        s_acc[warp] = acc;
+        s_max[warp] = wmax;
+    }
+    __syncthreads();
+    double dd = 0.0, sig2 = 0.0;
+    for (int i = 0; i < nw; ++i) {
+        dd += s_acc[i];
+        sig2 = fmax(sig2, s_max[i]);
+    }
+    if (!(sig2 > 0.0) || !isfinite(sig2)) sig2 = 1.0;
+    const double sig = sqrt(sig2), isig2 = 1.0 / sig2;
+    const long long po = meta[w].prep_off;
+    if (threadIdx.x == 0) {
+        meta[w].dd = dd * (4.0 / T);
+        meta[w].sig = sig;
+        meta[w].use_t = useT ? 1 : 0;
+    }
+    for (int i = threadIdx.x; i < win.W; i += blockDim.x) {
+        const double2 a = dA[win.data_off + i], e = dE[win.data_off + i];
+        Win32 v;
+        v.dre = make_float2((float)(a.x * sig), (float)(e.x * sig));
+        v.dim = make_float2((float)(a.y * sig), (float)(e.y * sig));
+        v.w = make_float2((float)(wA[win.data_off + i] * isig2), (float)(wE[win.data_off + i] * isig2));
+        prep[po + i] = v;
+        if (useT) {   // T in the first slot of each pair, zero in the second
+            const double2 t = dT[win.data_off + i];
+            Win32 u;
+            u.dre = make_float2((float)(t.x * sig), 0.0f);
+            u.dim = make_float2((float)(t.y * sig), 0.0f);
+            u.w = make_float2((float)(wT[win.data_off + i] * isig2), 0.0f);
+            prep[n_prep + po + i] = u;
+        }
+    }
+}
+
+// resident CTAs per SM the small-N instantiation is compiled for (register cap)
+#ifndef GB_MIXED_MINB
+#define GB_MIXED_MINB 4
+#endif
+
+// RMAX: largest R = N/32 this instantiation handles (8: N <= 256; 32: N = 512, 1024)
+// the two channels' compensated sums added into one (true sums s - c)
+__device__ __forceinline__ void kahan_join(float& s, float& c, float s2, float c2) {
+    float hi, e;
+    two_sum(s, s2, hi, e);
+    s = hi;
+    c = (c + c2) - e;
+}
+
+template <int RMAX, bool IM, bool T3>
+__global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) loglik_mixed_kernel(
+    const gb_window_t* __restrict__ wins, const WinMeta* __restrict__ meta, const Win32* __restrict__ prep,
+    const Tile* __restrict__ items, int n_items, int* head, TabSet32 tabs, const float2* __restrict__ tw1024,
+    double T, double fstar, const double* __restrict__ theta, double* __restrict__ logL,
+    double* __restrict__ dh_out, double* __restrict__ hh_out, double* __restrict__ dhi_out, int* status, int n_max,
+    unsigned long long budget_ns, long long n_prep) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    CandMix* cands = (CandMix*)smem_raw + warp * 32;
+    Epi<IM>* epi = (Epi<IM>*)((CandMix*)smem_raw + kWarpsMx * 32) + warp * 32;
+    float2* bufA =
+        (float2*)((Epi<IM>*)((CandMix*)smem_raw + kWarpsMx * 32) + kWarpsMx * 32) + (size_t)warp * 2 * n_max;
+    float2* bufE = bufA + n_max;
+    // T3: a second channel-pair buffer per warp for (T, 0)
+    float4* bufT = T3 ? (float4*)((float2*)((Epi<IM>*)((CandMix*)smem_raw + kWarpsMx * 32) + kWarpsMx * 32) +
+                                  (size_t)kWarpsMx * 2 * n_max) + (size_t)warp * n_max
+                      : nullptr;
+    const LaneTw ltw = lane_twiddles(lane);
+    const double ifs = 1.0 / fstar;   // the float results do not see the reciprocal's rounding
+
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        // a warp past the time budget takes no further item and flags it
+        int item = 0;
+        if (lane == 0) {
+            if (budget_ns != 0ULL && global_ns() - t0 > budget_ns) {
+                atomicOr(status, kStatusBudget);
+                item = n_items;
+            } else {
+                item = atomicAdd(head, 1);
+            }
+        }
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_items) break;
+        const Tile t = items[item];
+        const gb_window_t win = wins[t.win];
+        const WinMeta wm = meta[t.win];
+        const Win32* pw = prep + wm.prep_off;
+        const bool useT = T3 && wm.use_t;
+        const Win32* pwT = prep + n_prep + wm.prep_off;
+        const int N = win.N;
+        const OrbitTables32 tab = tabs.t[__ffs(N) - 6];
+        const int cnt = (int)(t.c_end - t.c_begin);
+        if (lane < cnt) setup_mixed(theta + 8 * (t.c_begin + lane), T, ifs, cands[lane]);
+        __syncwarp();
+        for (int i = 0; i < cnt; ++i) {
+            const CandMix& c = cands[i];
+            float sdh = 0.0f, cdh = 0.0f, shh = 0.0f, chh = 0.0f, sim = 0.0f, cim = 0.0f;
+            if (!c.bad) {
+                slow_part_dispatch<true, T3>(c, tab, N, bufA, bufE, lane, useT ? bufT : nullptr);
+                __syncwarp();
+                const long long off64 = c.q - win.k0;
+                if (off64 > -(long long)N && off64 < (long long)win.W + N) {
+                    const int off = (int)off64;
+#define GB_FFT_INNER(R) \
+    fft_inner_ch<R, IM>((float4*)bufA, tab, ltw, lane, off, win.W, pw, sdh, cdh, shh, chh, sim, cim)
+                    if constexpr (RMAX <= 8) {
+                        switch (N) {
+                            case 32: GB_FFT_INNER(1); break;
+                            case 64: GB_FFT_INNER(2); break;
+                            case 128: GB_FFT_INNER(4); break;
+                            default: GB_FFT_INNER(8); break;
+                        }
+                    } else {
+                        if (N == 512)
+                            GB_FFT_INNER(16);
+                        else
+                            GB_FFT_INNER(32);
+                    }
+#undef GB_FFT_INNER
+                    if constexpr (T3) {
+                        if (useT) {   // the T channel through the same transform, then into the sums
+                            float tdh = 0.0f, tcdh = 0.0f, thh = 0.0f, tchh = 0.0f, tim = 0.0f, tcim = 0.0f;
+#define GB_FFT_INNER_T(R) \
+    fft_inner_ch<R, IM>(bufT, tab, ltw, lane, off, win.W, pwT, tdh, tcdh, thh, tchh, tim, tcim)
+                            if constexpr (RMAX <= 8) {
+                                switch (N) {
+                                    case 32: GB_FFT_INNER_T(1); break;
+                                    case 64: GB_FFT_INNER_T(2); break;
+                                    case 128: GB_FFT_INNER_T(4); break;
+                                    default: GB_FFT_INNER_T(8); break;
+                                }
+                            } else {
+                                if (N == 512)
+                                    GB_FFT_INNER_T(16);
+                                else
+                                    GB_FFT_INNER_T(32);
+                            }
+#undef GB_FFT_INNER_T
+                            kahan_join(sdh, cdh, tdh, tcdh);
+                            kahan_join(shh, chh, thh, tchh);
+                            if constexpr (IM) kahan_join(sim, cim, tim, tcim);
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            float dhh, dhl, hhh, hhl, imh = 0.0f, iml = 0.0f;
+            warp_sum2(sdh, cdh, dhh, dhl);
+            warp_sum2(shh, chh, hhh, hhl);
+            if constexpr (IM) warp_sum2(sim, cim, imh, iml);
+            if (lane == 0) {
+                if constexpr (IM)
+                    epi[i] = Epi<IM>{dhh, dhl, hhh, hhl, imh, iml};
+                else
+                    epi[i] = Epi<IM>{dhh, dhl, hhh, hhl};
+            }
+        }
+        __syncwarp();
+        // lane-parallel epilogue in double, coalesced stores
+        if (lane < cnt) {
+            const CandMix& c = cands[lane];
+            const int64_t cidx = t.c_begin + lane;
+            if (c.bad) {
+                logL[cidx] = nan("");
+                if (dh_out) dh_out[cidx] = nan("");
+                if (hh_out) hh_out[cidx] = nan("");
+                if (IM && dhi_out) dhi_out[cidx] = nan("");
+                atomicOr(status, kStatusNonFinite);
+            } else {
+                const Epi<IM> s = epi[lane];
+                const double Sdh = (double)s.dh_hi + (double)s.dh_lo;
+                const double Shh = (double)s.hh_hi + (double)s.hh_lo;
+                const double dh = c.A * (2.0 * wm.sig / (double)N) * Sdh;
+                const double hh = (c.A * c.A) * (T * wm.sig * wm.sig / ((double)N * (double)N)) * Shh;
+                logL[cidx] = dh - 0.5 * hh - 0.5 * wm.dd;
+                if (dh_out) dh_out[cidx] = dh;
+                if (hh_out) hh_out[cidx] = hh;
+                if constexpr (IM) {
+                    if (dhi_out) dhi_out[cidx] = c.A * (2.0 * wm.sig / (double)N) * ((double)s.im_hi + (double)s.im_lo);
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+int resident_blocks(const void* kernel, int threads, size_t smem) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) n = 1;
+    return n;
+}cudaError_t launch_mixed_part(const void* kfn, int grid, size_t smem, cudaStream_t s, const gb_window_t* wins,
+                              const WinMeta* meta, const Win32* prep, const Tile* items, int n_items, int* head,
+                              TabSet32 tabs, const float2* tw1024, double T, double fstar, const double* theta,
+                              double* logL, double* dh, double* hh, double* dhi, int* status, int n_max,
+                              unsigned long long budget_ns, long long n_prep) {
+    void* args[] = {&wins, &meta, &prep, &items, &n_items, &head,  &tabs,      &tw1024, &T,     &fstar,
+                    &theta, &logL, &dh,  &hh,    &dhi,     &status, &n_max,    &budget_ns, &n_prep};
+    return cudaLaunchKernel(kfn, dim3(grid), dim3(kWarpsMx * 32), args, smem, s);
+}
+
+}  // namespace
+}  // namespace gb

@@ -157,6 +157,25 @@ def test_loglik_grad_aet_matches_oracle(ctx, prec):
     assert torch.equal(g2[:n0], gg[:n0])
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_loglik_phase_aet_is_dh_at_a_quarter_turn(ctx, prec):
+    # with T, dh_im(theta) = <d|h> over A, E and T at phi0 + pi/2
+    specs = [(6e-3, 256), (11e-3, 512), (12e-3, 256)]
+    wins, th, d, w = _problem(14, specs, 10)
+    args = [_c(x, torch.complex128) for x in d] + [_c(x, torch.float64) for x in w]
+    lp, dp, dip, hp = (x.cpu() for x in ctx.loglik_phase_aet(wins, *args, _c(th, torch.float64), prec=prec))
+    la, da, ha = (x.cpu() for x in ctx.loglik_aet(wins, *args, _c(th, torch.float64), prec=prec))
+    tq = th.copy()
+    tq[:, 7] += np.pi / 2
+    _, oq, ohh = ogb.loglik_aet(wins, *d, *w, tq, T)
+    scale = torch.clamp(ohh.abs(), min=1.0)
+    tol = 1e-10 if prec == "fp64" else 1e-5
+    assert float(((dip - oq).abs() / scale).max()) < tol
+    # the other outputs are those of loglik_aet
+    for a, b in ((lp, la), (dp, da), (hp, ha)):
+        assert float(((a - b).abs() / scale).max()) < tol
+
+
 def test_t_channel_argument_errors(ctx):
     from paper_2307_03763_gb300 import api
     rng = np.random.default_rng(9)
