@@ -63,6 +63,7 @@ int loglik_impl(gb_ctx_t* ctx, const char* name, int prec, const gb_window_t* wi
     // not give every resident warp of the GPU one item
     int item = (int)std::min<int64_t>(16, std::max<int64_t>(1, (total + sm_count(ctx) * 16 - 1) / (sm_count(ctx) * 16)));
     if (ctx->tune_item > 0) item = std::min(ctx->tune_item, 32);
+    if (dT) item = std::min(item, 16);   // the T-channel kernel's items hold at most 16 candidates
     int tile = tile_size(ctx, total, warps);
     if (ctx->tune_tile64 > 0) tile = std::min(ctx->tune_tile64, 32 * warps);
     rc = get_plan(ctx, prec, win, n_win, prec == GB_MIXED ? item : tile, &plan);

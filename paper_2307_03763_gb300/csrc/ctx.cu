@@ -253,6 +253,7 @@ int get_plan(gb_ctx* ctx, int prec, const gb_window_t* win, int32_t n_win, int t
     p.n_max = n_max;
     p.w_max = w_max;
     p.n_large = n_large;
+    p.tile_cands = tile_cands;
     p.last_use = ctx->clock;
     cudaError_t e;
     if (n_win > 0) {

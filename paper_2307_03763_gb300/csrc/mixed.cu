@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(kWarpsMx * 32) waveform_mixed_kernel(
             }
             continue;
         }
-        slow_part_dispatch<false, true>(c, tab, N, bufA, bufE, lane, (float4*)bufT);
+        slow_part_dispatch<false, true>(c, tab, N, bufA, bufE, lane, bufT);
         __syncwarp();
         const double s = scale * c.A;
         for (int ch = 0; ch < nch; ++ch) {
@@ -81,6 +81,7 @@ int launch_loglik_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const d
                         double* dh_im, const double* dT, const double* wT, cudaStream_t s) {
     if (plan.n_tiles == 0) return GB_OK;
     const bool t3 = dT != nullptr;
+    if (t3 && plan.tile_cands > kCapT) return set_error(ctx, GB_EINVAL, "loglik_mixed: T-channel items hold at most 16");
     prep_mixed_kernel<<<plan.n_win, 256, 0, s>>>(plan.d_win, plan.d_meta, plan.d_prep, (const double2*)dA,
                                                  (const double2*)dE, wA, wE, (const double2*)dT, wT, plan.n_prep,
                                                  ctx->obs.T_obs, transfer_frequency(ctx), plan.d_head);
@@ -96,8 +97,9 @@ int launch_loglik_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const d
         if (n_items == 0) continue;
         const int nmax = part == 0 ? 1024 : (plan.n_max < 256 ? plan.n_max : 256);
         const size_t epi_bytes = dh_im ? sizeof(Epi<true>) : sizeof(Epi<false>);
-        const size_t smem = (sizeof(CandMix) + epi_bytes) * kWarpsMx * 32 + sizeof(float2) * kWarpsMx * 2 * (size_t)nmax +
-                            (t3 ? sizeof(float4) * kWarpsMx * (size_t)nmax : 0);
+        const size_t cap = t3 ? kCapT : 32;
+        const size_t smem = (sizeof(CandMix) + epi_bytes) * kWarpsMx * cap + sizeof(float2) * kWarpsMx * 2 * (size_t)nmax +
+                            (t3 ? sizeof(float2) * kWarpsMx * (size_t)nmax : 0);
         const void* kfn = mixed_kernel_fn(part, dh_im != nullptr, t3);
         e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_error(ctx, e, "loglik_mixed: smem attribute");

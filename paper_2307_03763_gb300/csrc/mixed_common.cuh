@@ -53,6 +53,9 @@ namespace gb {
 namespace {
 
 constexpr int kWarpsMx = 4;
+// candidates per work item of the T-channel likelihood: a smaller candidate
+// array keeps two CTAs of the N = 1,024 instantiation resident per SM
+constexpr int kCapT = 16;
 
 struct CandMix {
     float c0h, c0l;     // phi0 / 2pi mod 1
@@ -248,7 +251,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // (for the across-lane transform of the waveform and gradient kernels).
 template <int J, bool NAT>
 __device__ void slow_part_mixed(const CandMix& c, const OrbitTables32& tab, int N, float2* bufA, float2* bufE,
-                                int lane, float4* bufT) {
+                                int lane, float2* bufT) {
     const int R = N >> 5;
     const float invN = 1.0f / (float)N;
     const float r2 = 0.70710678118654752f, r6 = 0.40824829046386302f;
@@ -343,18 +346,13 @@ __device__ void slow_part_mixed(const CandMix& c, const OrbitTables32& tab, int 
         const float2 oA = cmulf(F, Ap), oE = cmulf(F, Ep);
         if constexpr (NAT) {   // channel-pair elements for the likelihood transform
             ((float4*)bufA)[p] = make_float4(oA.x, oE.x, oA.y, oE.y);
-            if (bufT) {   // T = (X + Y + Z)/sqrt3, paired with zero
-                const float r3 = 0.57735026918962576f;
-                const float2 oT = cmulf(F, make_float2((Xp.x + Yp.x + Zp.x) * r3, (Xp.y + Yp.y + Zp.y) * r3));
-                bufT[p] = make_float4(oT.x, 0.0f, oT.y, 0.0f);
-            }
         } else {
             bufA[p] = oA;
             bufE[p] = oE;
-            if (bufT) {   // the waveform's T, as float2 samples
-                const float r3 = 0.57735026918962576f;
-                ((float2*)bufT)[p] = cmulf(F, make_float2((Xp.x + Yp.x + Zp.x) * r3, (Xp.y + Yp.y + Zp.y) * r3));
-            }
+        }
+        if (bufT) {   // T = (X + Y + Z)/sqrt3, one complex float per sample
+            const float r3 = 0.57735026918962576f;
+            bufT[p] = cmulf(F, make_float2((Xp.x + Yp.x + Zp.x) * r3, (Xp.y + Yp.y + Zp.y) * r3));
         }
     }
 }
@@ -458,10 +456,10 @@ __device__ __forceinline__ cpair pcis_rx(f2 x) {
 }
 
 // natural sample order (the likelihood kernel's transform), N >= 64; with
-// T3 and bufT also T = (X + Y + Z)/sqrt3, paired with zero
+// T3 and bufT also T = (X + Y + Z)/sqrt3, one complex float per sample
 template <int J, bool T3>
 __device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N, float2* bufA, float2* bufE,
-                               int lane, float4* bufT) {
+                               int lane, float2* bufT) {
     const int R = N >> 5, H = N >> 1;
     const float invN = 1.0f / (float)N;
     const f2 r2 = bc(0.70710678118654752f), r6 = bc(0.40824829046386302f);
@@ -569,8 +567,8 @@ __device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N
                 const f2 r3 = bc(0.57735026918962576f);
                 const cpair Tp{pmul(padd(padd(Xp.re, Yp.re), Zp.re), r3), pmul(padd(padd(Xp.im, Yp.im), Zp.im), r3)};
                 const cpair oT = pcmul(F, Tp);
-                bufT[p] = make_float4(oT.re.x, 0.0f, oT.im.x, 0.0f);
-                bufT[p + 32] = make_float4(oT.re.y, 0.0f, oT.im.y, 0.0f);
+                bufT[p] = make_float2(oT.re.x, oT.im.x);
+                bufT[p + 32] = make_float2(oT.re.y, oT.im.y);
             }
         }
     }
@@ -578,7 +576,7 @@ __device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N
 
 template <bool NAT, bool T3 = false>
 __device__ void slow_part_dispatch(const CandMix& c, const OrbitTables32& tab, int N, float2* bufA, float2* bufE,
-                                   int lane, float4* bufT = nullptr) {
+                                   int lane, float2* bufT = nullptr) {
     if constexpr (NAT) {
         if (N >= 64) {
             switch (c.J) {
@@ -590,7 +588,7 @@ __device__ void slow_part_dispatch(const CandMix& c, const OrbitTables32& tab, i
             return;
         }
     }
-    float4* bt = T3 ? bufT : nullptr;
+    float2* bt = T3 ? bufT : nullptr;
     switch (c.J) {
         case 4: slow_part_mixed<4, NAT>(c, tab, N, bufA, bufE, lane, bt); break;
         case 7: slow_part_mixed<7, NAT>(c, tab, N, bufA, bufE, lane, bt); break;
@@ -845,17 +843,26 @@ __device__ __forceinline__ void kahan_merge(f2 sum, f2 comp, float& s, float& c)
 
 // Both channels of one candidate (buf: N channel-pair elements, sample n at
 // n): transform, then the window inner products (with IM also the imaginary
-// part of sum w d conj(h)); each sum is returned as s - c.
-template <int R, bool IM>
+// part of sum w d conj(h)); each sum is returned as s - c.  With ONE, the
+// samples are read from src (one complex float each, the second channel
+// zero) and buf is only the transform's workspace.
+template <int R, bool IM, bool ONE = false>
 __device__ void fft_inner_ch(float4* buf, const OrbitTables32& tab, const LaneTw& ltw, int lane, int off, int W,
                              const Win32* __restrict__ pw, float& sdh, float& cdh, float& shh, float& chh, float& sim,
-                             float& cim) {
+                             float& cim, const float2* src = nullptr) {
     constexpr int N = 32 * R, G = 32 / R;
     constexpr int LG = G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 8 ? 3 : G == 16 ? 4 : 5;
     const int g = lane / G, j = lane % G;
     cpair x[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = ld4(buf + r * 32 + lane);
+    for (int r = 0; r < R; ++r) {
+        if constexpr (ONE) {
+            const float2 v = src[r * 32 + lane];
+            x[r] = cpair{make_float2(v.x, 0.0f), make_float2(v.y, 0.0f)};
+        } else {
+            x[r] = ld4(buf + r * 32 + lane);
+        }
+    }
     reg_fft2<R>(x);
 #pragma unroll
     for (int k1 = 1; k1 < R; ++k1) x[k1] = pcmul(x[k1], ldg4(tab.ltw4 + k1 * 32 + lane));
@@ -1061,14 +1068,16 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) 
     unsigned long long budget_ns, long long n_prep) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    CandMix* cands = (CandMix*)smem_raw + warp * 32;
-    Epi<IM>* epi = (Epi<IM>*)((CandMix*)smem_raw + kWarpsMx * 32) + warp * 32;
+    constexpr int CAP = T3 ? kCapT : 32;   // candidates of one work item
+    CandMix* cands = (CandMix*)smem_raw + warp * CAP;
+    Epi<IM>* epi = (Epi<IM>*)((CandMix*)smem_raw + kWarpsMx * CAP) + warp * CAP;
     float2* bufA =
-        (float2*)((Epi<IM>*)((CandMix*)smem_raw + kWarpsMx * 32) + kWarpsMx * 32) + (size_t)warp * 2 * n_max;
+        (float2*)((Epi<IM>*)((CandMix*)smem_raw + kWarpsMx * CAP) + kWarpsMx * CAP) + (size_t)warp * 2 * n_max;
     float2* bufE = bufA + n_max;
-    // T3: a second channel-pair buffer per warp for (T, 0)
-    float4* bufT = T3 ? (float4*)((float2*)((Epi<IM>*)((CandMix*)smem_raw + kWarpsMx * 32) + kWarpsMx * 32) +
-                                  (size_t)kWarpsMx * 2 * n_max) + (size_t)warp * n_max
+    // T3: T's samples per warp, one complex float each (the transform then
+    // runs in bufA once A and E are done)
+    float2* bufT = T3 ? (float2*)((Epi<IM>*)((CandMix*)smem_raw + kWarpsMx * CAP) + kWarpsMx * CAP) +
+                            (size_t)kWarpsMx * 2 * n_max + (size_t)warp * n_max
                       : nullptr;
     const LaneTw ltw = lane_twiddles(lane);
     const double ifs = 1.0 / fstar;   // the float results do not see the reciprocal's rounding
@@ -1126,8 +1135,10 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) 
                     if constexpr (T3) {
                         if (useT) {   // the T channel through the same transform, then into the sums
                             float tdh = 0.0f, tcdh = 0.0f, thh = 0.0f, tchh = 0.0f, tim = 0.0f, tcim = 0.0f;
-#define GB_FFT_INNER_T(R) \
-    fft_inner_ch<R, IM>(bufT, tab, ltw, lane, off, win.W, pwT, tdh, tcdh, thh, tchh, tim, tcim)
+                            __syncwarp();
+#define GB_FFT_INNER_T(R)                                                                                 \
+    fft_inner_ch<R, IM, true>((float4*)bufA, tab, ltw, lane, off, win.W, pwT, tdh, tcdh, thh, tchh, tim, tcim, \
+                              bufT)
                             if constexpr (RMAX <= 8) {
                                 switch (N) {
                                     case 32: GB_FFT_INNER_T(1); break;

@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? 2 : 1) grad_mixed_k
             float sdh = 0.0f, cdh = 0.0f, shh = 0.0f, chh = 0.0f;
             float tacc[KT][2] = {}, vp[2][2] = {}, vq[2][2] = {};
             if (!g.m.bad) {
-                slow_part_dispatch<false, T3>(g.m, tab, N, bufA, bufE, lane, useT ? (float4*)bufT : nullptr);
+                slow_part_dispatch<false, T3>(g.m, tab, N, bufA, bufE, lane, useT ? bufT : nullptr);
                 __syncwarp();
                 const long long off64 = g.m.q - win.k0;
                 const int off = (off64 > -(long long)N && off64 < (long long)win.W + N) ? (int)off64 : -4 * N;
