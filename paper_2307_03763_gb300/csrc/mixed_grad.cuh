@@ -17,8 +17,11 @@
 //   d/dA     = (2 sigma/N)   Re(conj(gp) V_P + conj(gx) V_Q)
 //   d/diota  = (2 sigma A/N) Re(conj(d_iota gp) V_P + conj(d_iota gx) V_Q), psi alike
 //   d/dphi0  = (2 sigma A/N) Im(conj(gp) V_P + conj(gx) V_Q)   (s^ ~ exp(i phi0)).
-// f0, fdot, beta, lambda are carried as forward-mode tangents through the
-// sample computation.
+// f0, fdot, beta, lambda come from the reverse mode of each sample's
+// computation (sample_adjoint): the sample's cotangent is propagated back
+// through F, the TDI combination and the six links to the receiver phases,
+// the transfer functions and the arms' polarisation responses, whose
+// parameter derivatives are closed forms.
 // ---------------------------------------------------------------------------
 #pragma once
 #include "mixed_common.cuh"
@@ -27,58 +30,6 @@ namespace gb {
 namespace {
 
 constexpr int KT = 4;   // f0, fdot, beta, lambda
-
-// A complex value with its KT = 4 forward tangents.  The tangents are kept
-// as two pairs, k = (0, 1) and (2, 3), of real parts dr and imaginary parts
-// di, so that every tangent operation is one packed FP32 instruction per pair.
-struct DCf {
-    float2 v;
-    f2 dr[2], di[2];
-};
-__device__ __forceinline__ DCf dmulf(const DCf& a, const DCf& b) {
-    DCf o;
-    o.v = cmulf(a.v, b.v);
-#pragma unroll
-    for (int p = 0; p < 2; ++p) {   // a.d b.v + a.v b.d
-        const f2 re1 = pfma(a.dr[p], bc(b.v.x), pneg(pmul(a.di[p], bc(b.v.y))));
-        const f2 im1 = pfma(a.dr[p], bc(b.v.y), pmul(a.di[p], bc(b.v.x)));
-        const f2 re2 = pfma(bc(a.v.x), b.dr[p], pneg(pmul(bc(a.v.y), b.di[p])));
-        const f2 im2 = pfma(bc(a.v.x), b.di[p], pmul(bc(a.v.y), b.dr[p]));
-        o.dr[p] = padd(re1, re2);
-        o.di[p] = padd(im1, im2);
-    }
-    return o;
-}
-__device__ __forceinline__ DCf daddf(const DCf& a, const DCf& b) {
-    DCf o;
-    o.v = caddf(a.v, b.v);
-#pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        o.dr[p] = padd(a.dr[p], b.dr[p]);
-        o.di[p] = padd(a.di[p], b.di[p]);
-    }
-    return o;
-}
-__device__ __forceinline__ DCf dsubf(const DCf& a, const DCf& b) {
-    DCf o;
-    o.v = csubf(a.v, b.v);
-#pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        o.dr[p] = psub(a.dr[p], b.dr[p]);
-        o.di[p] = psub(a.di[p], b.di[p]);
-    }
-    return o;
-}
-__device__ __forceinline__ DCf dscalef(const DCf& a, float s) {
-    DCf o;
-    o.v = make_float2(a.v.x * s, a.v.y * s);
-#pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        o.dr[p] = pmul(a.dr[p], bc(s));
-        o.di[p] = pmul(a.di[p], bc(s));
-    }
-    return o;
-}
 
 struct CandGx {
     CandMix m;
@@ -140,19 +91,27 @@ __device__ __forceinline__ void link_transfer_d(float X, float2& Tv, float2& Td)
     Td = make_float2(-8.0f * X * da, -2.0f * b + 16.0f * X * X * db);
 }
 
-// the T channel's sample with its tangents and P, Q responses
-struct TOut {
-    DCf S;
-    float2 P, Q;
-};
-
-// One sample of the unit-amplitude slow part at sample n: A and E with the
-// four forward tangents, and the P and Q responses (values); with T3 also T
-// = (X + Y + Z)/sqrt3 into *to.
+// One sample's share of the four phase-side derivatives, by reverse mode
+// through the sample computation.  With the sample's cotangents cA, cE (cT)
+// of the unit-amplitude A, E (T) values, it adds
+//   Re sum_ch conj(c_ch) dS_ch / dtheta_k,   k = f0, fdot, beta, lambda,
+// to dth[k], and U_P = sum_ch conj(c_ch) P_ch, U_Q likewise, to up, uq.
+//
+// S_ch = F sum_links mu_ch,l z_l, where z_l = T(X_l) G_arm rx_recv is one
+// link (transfer function, polarisation response of its arm, phase at its
+// receiver), F = -i a (1 - D^2) and the TDI coefficients mu hold 1, -1 and
+// the delay factor D.  So with omega_X,Y,Z = F times the channel weights of
+// X, Y, Z, the link cotangent is mu_l = D omega_a - omega_a+1 (the link
+// towards arm a+1's end) or omega_a - D omega_a+1 (the other), and
+//   d/dtheta Re(mu z) = Re(mu G rx T') dX/dtheta + Re(mu rx T dG/dtheta)
+//                       - 2 pi Im(mu z) dphase_recv/dtheta,
+// plus the derivatives of F and D themselves (f0 and fdot only).  P and Q are
+// S with G replaced by F+ and Fx: U_P = sum_arms Gamma_arm F+, with Gamma the
+// arm's sum of mu rx T.
 template <int J, bool T3 = false>
-__device__ __forceinline__ void sample_grad(const CandGx& g, const OrbitTables32& tab, int N, int n, float Tf,
-                                            float inv_fstar, DCf& SA, DCf& SE, float2& PA, float2& PE, float2& QA,
-                                            float2& QE, TOut* to = nullptr) {
+__device__ __forceinline__ void sample_adjoint(const CandGx& g, const OrbitTables32& tab, int N, int n, float Tf,
+                                               float inv_fstar, float2 cA, float2 cE, float2 cT, float (&dth)[KT],
+                                               float2& up, float2& uq) {
     const CandMix& c = g.m;
     const int R = N >> 5;
     const int p = (n % R) * 32 + brev5(n / R);
@@ -202,30 +161,16 @@ __device__ __forceinline__ void sample_grad(const CandGx& g, const OrbitTables32
     krho[2] = -krho[0] - krho[1];
     urho[2] = -urho[0] - urho[1];
     vrho[2] = -vrho[0] - vrho[1];
-    const float ux0 = fmaf(g.Uc, cah, g.Us * sah), vx0 = fmaf(g.Vc, cah, g.Vs * sah);
-    DCf rx[3];
+    // phase factor at each receiver
+    float2 rx[3];
+    float kap[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const float kap = K + krho[j];
-        const float dP = fmaf(-f, krho[j], c.fdh * kap * kap);
-        const float2 v = cmulf(ePc, cis_rx<J>(dP));
-        const float tk = tu - kap;
-        const float fk = fmaf(-fd, kap, f);
-        float dph[KT];
-        dph[0] = tk;
-        dph[1] = 0.5f * tk * tk;
-        dph[2] = -fk * (ux0 + urho[j]);
-        dph[3] = -fk * g.cb * (vx0 + vrho[j]);
-        rx[j].v = v;
-#pragma unroll
-        for (int p = 0; p < 2; ++p) {
-            const f2 t = pmul(bc(6.2831853071795865f), make_float2(dph[2 * p], dph[2 * p + 1]));
-            rx[j].dr[p] = pmul(pneg(t), bc(v.y));
-            rx[j].di[p] = pmul(t, bc(v.x));
-        }
+        kap[j] = K + krho[j];
+        const float dP = fmaf(-f, krho[j], c.fdh * kap[j] * kap[j]);
+        rx[j] = cmulf(ePc, cis_rx<J>(dP));
     }
     const float a = fmaf(c.a1, u, c.a0);
-    const float da[KT] = {0.5f * inv_fstar, 0.5f * tu * inv_fstar, 0.0f, 0.0f};
     float kn_[3], nu_[3], nv_[3], nw_[3];
     kn_[0] = fmaf(c.k0, g1.z, fmaf(c.k1, g1.w, c.k2 * g2.x));
     nu_[0] = fmaf(c.u0, g1.z, fmaf(c.u1, g1.w, c.u2 * g2.x));
@@ -239,120 +184,141 @@ __device__ __forceinline__ void sample_grad(const CandGx& g, const OrbitTables32
     nu_[2] = -nu_[0] - nu_[1];
     nv_[2] = -nv_[0] - nv_[1];
     nw_[2] = -nw_[0] - nw_[1];
-    DCf zp[3], zm[3];
-    float2 zpP[3], zmP[3], zpQ[3], zmQ[3];
+    // links: [arm][0] towards arm+1's end (+n, receiver arm+1), [arm][1] the
+    // other (-n, receiver arm); transfer value and derivative, link value
+    float2 G[3], Tv[3][2], Td[3][2], z[3][2];
 #pragma unroll
     for (int arm = 0; arm < 3; ++arm) {
-        const float kn = kn_[arm], nu = nu_[arm], nv = nv_[arm], nw = nw_[arm];
-        const float dkn[KT] = {0.0f, 0.0f, nu, g.cb * nv};
-        const float dnu[KT] = {0.0f, 0.0f, -kn, -g.sb * nv};
-        const float dnv[KT] = {0.0f, 0.0f, 0.0f, nw};
+        const float nu = nu_[arm], nv = nv_[arm];
         const float Fp = (nu - nv) * (nu + nv), Fx = 2.0f * nu * nv;
-        DCf G;
-        G.v = make_float2(fmaf(g.gp.x, Fp, g.gx.x * Fx), fmaf(g.gp.y, Fp, g.gx.y * Fx));
-        float dFp[KT], dFx[KT];
-#pragma unroll
-        for (int k = 0; k < KT; ++k) {
-            dFp[k] = 2.0f * (nu * dnu[k] - nv * dnv[k]);
-            dFx[k] = 2.0f * (dnu[k] * nv + nu * dnv[k]);
-        }
-#pragma unroll
-        for (int p = 0; p < 2; ++p) {
-            const f2 fp = make_float2(dFp[2 * p], dFp[2 * p + 1]), fx = make_float2(dFx[2 * p], dFx[2 * p + 1]);
-            G.dr[p] = pfma(bc(g.gp.x), fp, pmul(bc(g.gx.x), fx));
-            G.di[p] = pfma(bc(g.gp.y), fp, pmul(bc(g.gx.y), fx));
-        }
-        const int rp = arm == 2 ? 0 : arm + 1, rm = arm;
+        G[arm] = make_float2(fmaf(g.gp.x, Fp, g.gx.x * Fx), fmaf(g.gp.y, Fp, g.gx.y * Fx));
 #pragma unroll
         for (int sgn = 0; sgn < 2; ++sgn) {
-            const float sd = sgn == 0 ? 1.0f : -1.0f;   // +n link: X = a(1 - kn); -n link: X = a(1 + kn)
-            const float X = a * fmaf(-sd, kn, 1.0f);
-            float2 Tv, Td;
-            link_transfer_d<J>(X, Tv, Td);
-            DCf Tl;
-            Tl.v = Tv;
-            float dX[KT];
-#pragma unroll
-            for (int k = 0; k < KT; ++k) dX[k] = da[k] * fmaf(-sd, kn, 1.0f) - sd * a * dkn[k];
-#pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                const f2 x = make_float2(dX[2 * p], dX[2 * p + 1]);
-                Tl.dr[p] = pmul(bc(Td.x), x);
-                Tl.di[p] = pmul(bc(Td.y), x);
-            }
-            const DCf& rr = rx[sgn == 0 ? rp : rm];
-            const DCf z = dmulf(dmulf(Tl, G), rr);
-            const float2 Tr = cmulf(Tv, rr.v);
-            const float2 zP = make_float2(Tr.x * Fp, Tr.y * Fp), zQ = make_float2(Tr.x * Fx, Tr.y * Fx);
-            if (sgn == 0) {
-                zp[arm] = z;
-                zpP[arm] = zP;
-                zpQ[arm] = zQ;
-            } else {
-                zm[arm] = z;
-                zmP[arm] = zP;
-                zmQ[arm] = zQ;
-            }
+            const float X = a * (sgn == 0 ? 1.0f - kn_[arm] : 1.0f + kn_[arm]);
+            link_transfer_d<J>(X, Tv[arm][sgn], Td[arm][sgn]);
+            const int j = sgn == 0 ? (arm == 2 ? 0 : arm + 1) : arm;
+            z[arm][sgn] = cmulf(cmulf(Tv[arm][sgn], G[arm]), rx[j]);
         }
     }
     // delay factor D = exp(-i f/f*) and F = -i a (1 - D^2) = 2 a sin(f/f*) D
-    DCf D;
-    {
-        const float du = c.eps * u;
-        D.v = cmulf(make_float2(c.D0r, c.D0i), make_float2(fmaf(-0.5f * du, du, 1.0f), -du));
-        const float dphi[KT] = {inv_fstar, tu * inv_fstar, 0.0f, 0.0f};
+    const float du = c.eps * u;
+    const float2 D = cmulf(make_float2(c.D0r, c.D0i), make_float2(fmaf(-0.5f * du, du, 1.0f), -du));
+    const float sa2 = -2.0f * a * D.y;
+    const float2 F = make_float2(sa2 * D.x, sa2 * D.y);
+    // first-generation Michelson X, Y, Z (without F)
+    const float2 Xp = caddf(csubf(z[0][1], z[2][0]), cmulf(D, csubf(z[0][0], z[2][1])));
+    const float2 Yp = caddf(csubf(z[1][1], z[0][0]), cmulf(D, csubf(z[1][0], z[0][1])));
+    const float2 Zp = caddf(csubf(z[2][1], z[1][0]), cmulf(D, csubf(z[2][0], z[1][1])));
+    // channel weights of X, Y, Z: A = (Z - X)/sqrt2, E = (X - 2Y + Z)/sqrt6,
+    // T = (X + Y + Z)/sqrt3, each with conj(c)
+    const float r2 = 0.70710678118654752f, r6 = 0.40824829046386302f;
+    const float2 ca = make_float2(cA.x * r2, -cA.y * r2), ce = make_float2(cE.x * r6, -cE.y * r6);
+    float2 w[3] = {csubf(ce, ca), make_float2(-2.0f * ce.x, -2.0f * ce.y), caddf(ca, ce)};
+    if constexpr (T3) {
+        const float r3 = 0.57735026918962576f;
+        const float2 ct = make_float2(cT.x * r3, -cT.y * r3);
 #pragma unroll
-        for (int p = 0; p < 2; ++p) {   // -i D dphi
-            const f2 x = make_float2(dphi[2 * p], dphi[2 * p + 1]);
-            D.dr[p] = pmul(bc(D.v.y), x);
-            D.di[p] = pmul(bc(-D.v.x), x);
-        }
+        for (int q = 0; q < 3; ++q) w[q] = caddf(w[q], ct);
     }
-    DCf F;
+    // F and D depend on f0 and fdot: dD = -i D dphi, dphi = (1, t)/f*,
+    // d(sa2) = -2 (da D.y + a dD.y), da = (1, t)/(2 f*)
+    const float2 Wsum = caddf(caddf(cmulf(w[0], Xp), cmulf(w[1], Yp)), cmulf(w[2], Zp));
+    float2 om[3], Dom[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        om[q] = cmulf(F, w[q]);
+        Dom[q] = cmulf(D, om[q]);
+    }
+    const float2 Qd = caddf(caddf(cmulf(om[0], csubf(z[0][0], z[2][1])), cmulf(om[1], csubf(z[1][0], z[0][1]))),
+                            cmulf(om[2], csubf(z[2][0], z[1][1])));
     {
-        const float sa2 = -2.0f * a * D.v.y;
-        F.v = make_float2(sa2 * D.v.x, sa2 * D.v.y);
+        // per unit dphi: dD = -i D, so Re(Qd dD) = Im(Qd D); da = 1/2 and
+        // d(sa2) = -2 (D.y / 2 + a (-D.x)) = 2 a D.x - D.y
+        const float2 QD = cmulf(Qd, D);
+        const float dsa2 = fmaf(2.0f * a, D.x, -D.y);
+        const float2 dF = make_float2(fmaf(dsa2, D.x, sa2 * D.y), fmaf(dsa2, D.y, -sa2 * D.x));
+        const float fdf = fmaf(dF.x, Wsum.x, -dF.y * Wsum.y) + QD.y;   // per unit dphi
+        dth[0] = fmaf(fdf, inv_fstar, dth[0]);
+        dth[1] = fmaf(fdf, tu * inv_fstar, dth[1]);
+    }
+    float A1 = 0.0f;                           // sum of Re(mu G rx T') (1 -+ kn)
+    float Phi[3] = {0.0f, 0.0f, 0.0f};         // sum over the receiver's links of Im(mu z)
+#pragma unroll
+    for (int arm = 0; arm < 3; ++arm) {
+        const int an = arm == 2 ? 0 : arm + 1;
+        float B = 0.0f;                        // sum of -+ Re(mu G rx T')
+        float2 Gam = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int sgn = 0; sgn < 2; ++sgn) {
+            const int j = sgn == 0 ? an : arm;
+            const float2 mu = sgn == 0 ? csubf(Dom[arm], om[an]) : csubf(om[arm], Dom[an]);
+            const float2 nu_l = cmulf(mu, rx[j]);
+            const float2 nuG = cmulf(nu_l, G[arm]);
+            const float rho = fmaf(nuG.x, Td[arm][sgn].x, -nuG.y * Td[arm][sgn].y);
+            Phi[j] += fmaf(nuG.x, Tv[arm][sgn].y, nuG.y * Tv[arm][sgn].x);
+            Gam = caddf(Gam, cmulf(nu_l, Tv[arm][sgn]));
+            const float kf = sgn == 0 ? 1.0f - kn_[arm] : 1.0f + kn_[arm];
+            A1 = fmaf(rho, kf, A1);
+            B += sgn == 0 ? -rho : rho;
+        }
+        const float nu = nu_[arm], nv = nv_[arm], nw = nw_[arm], kn = kn_[arm];
+        const float Fp = (nu - nv) * (nu + nv), Fx = 2.0f * nu * nv;
+        // Re(Gamma dG) = Re(Gamma gp) dF+ + Re(Gamma gx) dFx
+        const float gpr = fmaf(Gam.x, g.gp.x, -Gam.y * g.gp.y), gxr = fmaf(Gam.x, g.gx.x, -Gam.y * g.gx.y);
+        // beta: dn.u = -k.n, dn.v = 0; lambda: dn.u = -sin(beta) n.v, dn.v = n.w;
+        // dX = -+ a dk.n with dk.n = n.u (beta), cos(beta) n.v (lambda)
+        const float dnu_l = -g.sb * nv;
+        const float dFp_b = -2.0f * nu * kn, dFx_b = -2.0f * kn * nv;
+        const float dFp_l = 2.0f * fmaf(nu, dnu_l, -nv * nw), dFx_l = 2.0f * fmaf(dnu_l, nv, nu * nw);
+        dth[2] += fmaf(gpr, dFp_b, fmaf(gxr, dFx_b, a * B * nu));
+        dth[3] += fmaf(gpr, dFp_l, fmaf(gxr, dFx_l, a * B * g.cb * nv));
+        up = caddf(up, make_float2(Gam.x * Fp, Gam.y * Fp));
+        uq = caddf(uq, make_float2(Gam.x * Fx, Gam.y * Fx));
+    }
+    // transfer functions: dX = da (1 -+ kn), da = (1, t)/(2 f*)
+    dth[0] = fmaf(A1, 0.5f * inv_fstar, dth[0]);
+    dth[1] = fmaf(A1, 0.5f * tu * inv_fstar, dth[1]);
+    // receiver phases: d phase_j = (t - kap, (t - kap)^2/2, -(f - fdot kap) u.x_j/c,
+    // -(f - fdot kap) cos(beta) v.x_j/c) cycles
+    const float ux0 = fmaf(g.Uc, cah, g.Us * sah), vx0 = fmaf(g.Vc, cah, g.Vs * sah);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float ph = -6.2831853071795865f * Phi[j];
+        const float tk = tu - kap[j];
+        const float fk = fmaf(-fd, kap[j], f);
+        dth[0] = fmaf(ph, tk, dth[0]);
+        dth[1] = fmaf(ph, 0.5f * tk * tk, dth[1]);
+        dth[2] = fmaf(ph, -fk * (ux0 + urho[j]), dth[2]);
+        dth[3] = fmaf(ph, -fk * g.cb * (vx0 + vrho[j]), dth[3]);
+    }
+}
+
+// The sample adjoints of one candidate: lane l takes samples l, l + 32, ...
+// (cA, cE, cT: the adjoint transform's output c^_n; cT may be null in the T
+// instantiation, for windows without T).  Sums are compensated per lane.
+template <int J, bool T3 = false>
+__device__ void adjoint_sweep(const CandGx& g, const OrbitTables32& tab, int N, float Tf, float inv_fstar,
+                              const float2* cA, const float2* cE, int lane, float (&tacc)[KT][2],
+                              float (&vp)[2][2], float (&vq)[2][2], const float2* cT = nullptr) {
+    for (int n = lane; n < N; n += 32) {
+        float dth[KT] = {0.0f, 0.0f, 0.0f, 0.0f};
+        float2 up = make_float2(0.0f, 0.0f), uq = make_float2(0.0f, 0.0f);
+        const float2 t = (T3 && cT) ? cT[n] : make_float2(0.0f, 0.0f);
+        sample_adjoint<J, T3>(g, tab, N, n, Tf, inv_fstar, cA[n], cE[n], t, dth, up, uq);
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
-            const f2 dsa2 = pmul(bc(-2.0f), pfma(make_float2(da[2 * p], da[2 * p + 1]), bc(D.v.y), pmul(bc(a), D.di[p])));
-            F.dr[p] = pfma(dsa2, bc(D.v.x), pmul(bc(sa2), D.dr[p]));
-            F.di[p] = pfma(dsa2, bc(D.v.y), pmul(bc(sa2), D.di[p]));
+            f2 sum = make_float2(tacc[2 * p][0], tacc[2 * p + 1][0]), comp = make_float2(tacc[2 * p][1], tacc[2 * p + 1][1]);
+            kahan_add2(sum, comp, make_float2(dth[2 * p], dth[2 * p + 1]));
+            tacc[2 * p][0] = sum.x;
+            tacc[2 * p + 1][0] = sum.y;
+            tacc[2 * p][1] = comp.x;
+            tacc[2 * p + 1][1] = comp.y;
         }
-    }
-    const float r2 = 0.70710678118654752f, r6 = 0.40824829046386302f;
-    {
-        const DCf Xp = daddf(dsubf(zm[0], zp[2]), dmulf(D, dsubf(zp[0], zm[2])));
-        const DCf Yp = daddf(dsubf(zm[1], zp[0]), dmulf(D, dsubf(zp[1], zm[0])));
-        const DCf Zp = daddf(dsubf(zm[2], zp[1]), dmulf(D, dsubf(zp[2], zm[1])));
-        SA = dmulf(F, dscalef(dsubf(Zp, Xp), r2));
-        SE = dmulf(F, dscalef(daddf(dsubf(Xp, dscalef(Yp, 2.0f)), Zp), r6));
-        if constexpr (T3) to->S = dmulf(F, dscalef(daddf(daddf(Xp, Yp), Zp), 0.57735026918962576f));
-    }
-#pragma unroll
-    for (int w = 0; w < 2; ++w) {
-        const float2* zpv = w == 0 ? zpP : zpQ;
-        const float2* zmv = w == 0 ? zmP : zmQ;
-        const float2 Xp = caddf(csubf(zmv[0], zpv[2]), cmulf(D.v, csubf(zpv[0], zmv[2])));
-        const float2 Yp = caddf(csubf(zmv[1], zpv[0]), cmulf(D.v, csubf(zpv[1], zmv[0])));
-        const float2 Zp = caddf(csubf(zmv[2], zpv[1]), cmulf(D.v, csubf(zpv[2], zmv[1])));
-        const float2 Av = cmulf(F.v, make_float2((Zp.x - Xp.x) * r2, (Zp.y - Xp.y) * r2));
-        const float2 Ev =
-            cmulf(F.v, make_float2((Xp.x - 2.0f * Yp.x + Zp.x) * r6, (Xp.y - 2.0f * Yp.y + Zp.y) * r6));
-        if (w == 0) {
-            PA = Av;
-            PE = Ev;
-        } else {
-            QA = Av;
-            QE = Ev;
-        }
-        if constexpr (T3) {
-            const float r3 = 0.57735026918962576f;
-            const float2 Tv = cmulf(F.v, make_float2((Xp.x + Yp.x + Zp.x) * r3, (Xp.y + Yp.y + Zp.y) * r3));
-            if (w == 0)
-                to->P = Tv;
-            else
-                to->Q = Tv;
-        }
+        // V = sum c conj(P) = conj(U_P)
+        kahan_add(vp[0][0], vp[0][1], up.x);
+        kahan_add(vp[1][0], vp[1][1], -up.y);
+        kahan_add(vq[0][0], vq[0][1], uq.x);
+        kahan_add(vq[1][0], vq[1][1], -uq.y);
     }
 }
 
@@ -414,59 +380,13 @@ __device__ void residual_adjoint(float2* buf, int ch, const OrbitTables32& tab, 
     __syncwarp();
 }
 
-// cT (T3, may be null): the T channel's adjoint
-template <int J, bool T3 = false>
-__device__ void tangent_sweep(const CandGx& g, const OrbitTables32& tab, int N, float Tf, float inv_fstar,
-                              const float2* cA, const float2* cE, int lane, float (&tacc)[KT][2],
-                              float (&vp)[2][2], float (&vq)[2][2], const float2* cT = nullptr) {
-    for (int n = lane; n < N; n += 32) {
-        DCf SA, SE;
-        float2 PA, PE, QA, QE;
-        TOut to;
-        if (T3 && cT)
-            sample_grad<J, true>(g, tab, N, n, Tf, inv_fstar, SA, SE, PA, PE, QA, QE, &to);
-        else
-            sample_grad<J, false>(g, tab, N, n, Tf, inv_fstar, SA, SE, PA, PE, QA, QE);
-        const float2 a = cA[n], e = cE[n];
-#pragma unroll
-        for (int p = 0; p < 2; ++p) {
-            f2 sum = make_float2(tacc[2 * p][0], tacc[2 * p + 1][0]), comp = make_float2(tacc[2 * p][1], tacc[2 * p + 1][1]);
-            kahan_add2(sum, comp, pfma(bc(a.x), SA.dr[p], pfma(bc(a.y), SA.di[p], pfma(bc(e.x), SE.dr[p],
-                                                                                       pmul(bc(e.y), SE.di[p])))));
-            tacc[2 * p][0] = sum.x;
-            tacc[2 * p + 1][0] = sum.y;
-            tacc[2 * p][1] = comp.x;
-            tacc[2 * p + 1][1] = comp.y;
-        }
-        // c conj(P) = (c.x P.x + c.y P.y) + i (c.y P.x - c.x P.y)
-        kahan_add(vp[0][0], vp[0][1], fmaf(a.x, PA.x, fmaf(a.y, PA.y, fmaf(e.x, PE.x, e.y * PE.y))));
-        kahan_add(vp[1][0], vp[1][1], fmaf(a.y, PA.x, fmaf(-a.x, PA.y, fmaf(e.y, PE.x, -e.x * PE.y))));
-        kahan_add(vq[0][0], vq[0][1], fmaf(a.x, QA.x, fmaf(a.y, QA.y, fmaf(e.x, QE.x, e.y * QE.y))));
-        kahan_add(vq[1][0], vq[1][1], fmaf(a.y, QA.x, fmaf(-a.x, QA.y, fmaf(e.y, QE.x, -e.x * QE.y))));
-        if constexpr (T3) {
-            if (cT) {
-                const float2 t = cT[n];
-#pragma unroll
-                for (int p = 0; p < 2; ++p) {
-                    f2 sum = make_float2(tacc[2 * p][0], tacc[2 * p + 1][0]);
-                    f2 comp = make_float2(tacc[2 * p][1], tacc[2 * p + 1][1]);
-                    kahan_add2(sum, comp, pfma(bc(t.x), to.S.dr[p], pmul(bc(t.y), to.S.di[p])));
-                    tacc[2 * p][0] = sum.x;
-                    tacc[2 * p + 1][0] = sum.y;
-                    tacc[2 * p][1] = comp.x;
-                    tacc[2 * p + 1][1] = comp.y;
-                }
-                kahan_add(vp[0][0], vp[0][1], fmaf(t.x, to.P.x, t.y * to.P.y));
-                kahan_add(vp[1][0], vp[1][1], fmaf(t.y, to.P.x, -t.x * to.P.y));
-                kahan_add(vq[0][0], vq[0][1], fmaf(t.x, to.Q.x, t.y * to.Q.y));
-                kahan_add(vq[1][0], vq[1][1], fmaf(t.y, to.Q.x, -t.x * to.Q.y));
-            }
-        }
-    }
-}
+// resident CTAs per SM the N <= 256 instantiation is compiled for (register cap)
+#ifndef GB_GRAD_MINB
+#define GB_GRAD_MINB 2
+#endif
 
 template <int RMAX, bool T3>
-__global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? 2 : 1) grad_mixed_kernel(
+__global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_GRAD_MINB : 1) grad_mixed_kernel(
     const gb_window_t* __restrict__ wins, const WinMeta* __restrict__ meta, const Win32* __restrict__ prep,
     const Tile* __restrict__ items, int n_items, int* head, TabSet32 tabs, const float2* __restrict__ tw1024,
     double T, double fstar, const double* __restrict__ theta, double* __restrict__ logL,
@@ -554,10 +474,10 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? 2 : 1) grad_mixed_k
                 }
                 const float2* cT = useT ? bufT : nullptr;
                 switch (g.m.J) {
-                    case 4: tangent_sweep<4, T3>(g, tab, N, Tf, inv_fstar, bufA, bufE, lane, tacc, vp, vq, cT); break;
-                    case 7: tangent_sweep<7, T3>(g, tab, N, Tf, inv_fstar, bufA, bufE, lane, tacc, vp, vq, cT); break;
-                    case 10: tangent_sweep<10, T3>(g, tab, N, Tf, inv_fstar, bufA, bufE, lane, tacc, vp, vq, cT); break;
-                    default: tangent_sweep<0, T3>(g, tab, N, Tf, inv_fstar, bufA, bufE, lane, tacc, vp, vq, cT); break;
+                    case 4: adjoint_sweep<4, T3>(g, tab, N, Tf, inv_fstar, bufA, bufE, lane, tacc, vp, vq, cT); break;
+                    case 7: adjoint_sweep<7, T3>(g, tab, N, Tf, inv_fstar, bufA, bufE, lane, tacc, vp, vq, cT); break;
+                    case 10: adjoint_sweep<10, T3>(g, tab, N, Tf, inv_fstar, bufA, bufE, lane, tacc, vp, vq, cT); break;
+                    default: adjoint_sweep<0, T3>(g, tab, N, Tf, inv_fstar, bufA, bufE, lane, tacc, vp, vq, cT); break;
                 }
                 __syncwarp();
             }
