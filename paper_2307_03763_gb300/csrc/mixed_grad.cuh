@@ -91,9 +91,44 @@ __device__ __forceinline__ void link_transfer_d(float X, float2& Tv, float2& Td)
     Td = make_float2(-8.0f * X * da, -2.0f * b + 16.0f * X * X * db);
 }
 
+// sinc(X) exp(-iX) and its X derivative for a pair (see link_transfer_d)
+template <int J>
+__device__ __forceinline__ void plink_transfer_d(f2 X, cpair& Tv, cpair& Td) {
+    if constexpr (J == 0) {
+        float2 a, da, b, db;
+        link_transfer_d<0>(X.x, a, da);
+        link_transfer_d<0>(X.y, b, db);
+        Tv = cpair{make_float2(a.x, b.x), make_float2(a.y, b.y)};
+        Td = cpair{make_float2(da.x, db.x), make_float2(da.y, db.y)};
+    } else {
+        const f2 y = pmul(bc(-4.0f), pmul(X, X));
+        const float4 cJ = kLinkPair[J];
+        f2 a = make_float2(cJ.x, cJ.y), b = make_float2(cJ.z, cJ.w), da = bc(0.0f), db = bc(0.0f);
+#pragma unroll
+        for (int j = J - 1; j >= 0; --j) {
+            const float4 cj = kLinkPair[j];
+            da = pfma(da, y, a);
+            a = pfma(a, y, make_float2(cj.x, cj.y));
+            db = pfma(db, y, b);
+            b = pfma(b, y, make_float2(cj.z, cj.w));
+        }
+        // Re T = a(y), Im T = -2X b(y); dy/dX = -8X
+        Tv = cpair{a, pmul(pmul(bc(-2.0f), X), b)};
+        Td = cpair{pmul(pmul(bc(-8.0f), X), da), pfma(pmul(bc(16.0f), pmul(X, X)), db, pmul(bc(-2.0f), b))};
+    }
+}
+
+__device__ __forceinline__ cpair pcbc(float2 v) { return cpair{bc(v.x), bc(v.y)}; }
+__device__ __forceinline__ cpair pcscale(cpair a, f2 s) { return cpair{pmul(a.re, s), pmul(a.im, s)}; }
+// Re(a b) and Im(a b) of a pair
+__device__ __forceinline__ f2 pcre(cpair a, cpair b) { return pfma(a.re, b.re, pneg(pmul(a.im, b.im))); }
+__device__ __forceinline__ f2 pcim(cpair a, cpair b) { return pfma(a.re, b.im, pmul(a.im, b.re)); }
+
 // One sample's share of the four phase-side derivatives, by reverse mode
-// through the sample computation.  With the sample's cotangents cA, cE (cT)
-// of the unit-amplitude A, E (T) values, it adds
+// through the sample computation, for the two samples n0 and n0 + 32 at once
+// (packed FP32; a second sample past N has zero cotangents).  With the
+// samples' cotangents cA, cE (cT) of the unit-amplitude A, E (T) values, it
+// adds
 //   Re sum_ch conj(c_ch) dS_ch / dtheta_k,   k = f0, fdot, beta, lambda,
 // to dth[k], and U_P = sum_ch conj(c_ch) P_ch, U_Q likewise, to up, uq.
 //
@@ -109,217 +144,238 @@ __device__ __forceinline__ void link_transfer_d(float X, float2& Tv, float2& Td)
 // S with G replaced by F+ and Fx: U_P = sum_arms Gamma_arm F+, with Gamma the
 // arm's sum of mu rx T.
 template <int J, bool T3 = false>
-__device__ __forceinline__ void sample_adjoint(const CandGx& g, const OrbitTables32& tab, int N, int n, float Tf,
-                                               float inv_fstar, float2 cA, float2 cE, float2 cT, float (&dth)[KT],
-                                               float2& up, float2& uq) {
+__device__ __forceinline__ void sample_adjoint(const CandGx& g, const OrbitTables32& tab, int N, int n0, int n1,
+                                               float Tf, float inv_fstar, cpair cA, cpair cE, cpair cT,
+                                               f2 (&dth)[KT], cpair& up, cpair& uq) {
     const CandMix& c = g.m;
     const int R = N >> 5;
-    const int p = (n % R) * 32 + brev5(n / R);
-    const float u = (float)n / (float)N;
-    const float uu = u * u;
-    const float4 g0 = __ldg(tab.g + p), g1 = __ldg(tab.g + N + p);
-    const float4 g2 = __ldg(tab.g + 2 * N + p), g3 = __ldg(tab.g + 3 * N + p);
-    const float cah = g3.x, cal = g3.y, sah = g3.z, sal = g3.w;
+    const int pa = (n0 % R) * 32 + brev5(n0 / R), pb = (n1 % R) * 32 + brev5(n1 / R);
+    const float4 a0 = __ldg(tab.g + pa), a1 = __ldg(tab.g + N + pa);
+    const float4 a2 = __ldg(tab.g + 2 * N + pa), a3 = __ldg(tab.g + 3 * N + pa);
+    const float4 b0 = __ldg(tab.g + pb), b1 = __ldg(tab.g + N + pb);
+    const float4 b2 = __ldg(tab.g + 2 * N + pb), b3 = __ldg(tab.g + 3 * N + pb);
+    const f2 u = pmul(make_float2((float)n0, (float)n1), bc(1.0f / (float)N));
+    const f2 uu = pmul(u, u);
+    const f2 cah = make_float2(a3.x, b3.x), cal = make_float2(a3.y, b3.y);
+    const f2 sah = make_float2(a3.z, b3.z), sal = make_float2(a3.w, b3.w);
     // common phase in double-word arithmetic (as in the likelihood kernel)
-    float p1 = c.c1h * u;
-    const float e1 = fmaf(c.c1h, u, -p1) + c.c1l * u;
-    float p2 = c.c2h * uu;
-    const float e2 = fmaf(c.c2h, uu, -p2) + c.c2l * uu;
-    float p3 = c.Fch * cah;
-    const float e3 = fmaf(c.Fch, cah, -p3) + fmaf(c.Fch, cal, c.Fcl * cah);
-    float p4 = c.Fsh * sah;
-    const float e4 = fmaf(c.Fsh, sah, -p4) + fmaf(c.Fsh, sal, c.Fsl * sah);
-    p1 -= rintf(p1);
-    p2 -= rintf(p2);
-    p3 -= rintf(p3);
-    p4 -= rintf(p4);
-    float s, e, ea, eb, ec;
-    two_sum(c.c0h, p1, s, ea);
-    two_sum(s, p2, s, eb);
-    two_sum(s, -p3, s, ec);
-    two_sum(s, -p4, s, e);
-    s -= rintf(s);
-    const float K = fmaf(c.Kc, cah, c.Ks * sah);
-    const float small = ((c.c0l + e1 + e2 - e3 - e4) + (ea + eb + ec + e)) - c.fdT * u * K;
-    float Pc, Pl;
-    two_sum(s, small, Pc, Pl);
-    Pc -= rintf(Pc);
-    float sPc, cPc;
-    sincospif(2.0f * Pc, &sPc, &cPc);
-    const float tl = 6.2831853071795865f * Pl;
-    const float2 ePc = make_float2(fmaf(-tl, sPc, cPc), fmaf(tl, cPc, sPc));
-    const float f = fmaf(c.fdT, u, c.f0);
-    const float fd = 2.0f * c.fdh;
-    const float tu = Tf * u;
-    float krho[3], urho[3], vrho[3];
-    krho[0] = fmaf(c.k0, g0.x, fmaf(c.k1, g0.y, c.k2 * g0.z));
-    krho[1] = fmaf(c.k0, g0.w, fmaf(c.k1, g1.x, c.k2 * g1.y));
-    urho[0] = fmaf(c.u0, g0.x, fmaf(c.u1, g0.y, c.u2 * g0.z));
-    urho[1] = fmaf(c.u0, g0.w, fmaf(c.u1, g1.x, c.u2 * g1.y));
-    vrho[0] = fmaf(c.v0, g0.x, c.v1 * g0.y);
-    vrho[1] = fmaf(c.v0, g0.w, c.v1 * g1.x);
-    krho[2] = -krho[0] - krho[1];
-    urho[2] = -urho[0] - urho[1];
-    vrho[2] = -vrho[0] - vrho[1];
+    f2 p1 = pmul(bc(c.c1h), u);
+    const f2 e1 = pfma(bc(c.c1l), u, pfma(bc(c.c1h), u, pneg(p1)));
+    f2 p2 = pmul(bc(c.c2h), uu);
+    const f2 e2 = pfma(bc(c.c2l), uu, pfma(bc(c.c2h), uu, pneg(p2)));
+    f2 p3 = pmul(bc(c.Fch), cah);
+    const f2 e3 = padd(pfma(bc(c.Fch), cah, pneg(p3)), pfma(bc(c.Fch), cal, pmul(bc(c.Fcl), cah)));
+    f2 p4 = pmul(bc(c.Fsh), sah);
+    const f2 e4 = padd(pfma(bc(c.Fsh), sah, pneg(p4)), pfma(bc(c.Fsh), sal, pmul(bc(c.Fsl), sah)));
+    p1 = psub(p1, print(p1));
+    p2 = psub(p2, print(p2));
+    p3 = psub(p3, print(p3));
+    p4 = psub(p4, print(p4));
+    f2 s, e, ea, eb, ec;
+    ptwo_sum(bc(c.c0h), p1, s, ea);
+    ptwo_sum(s, p2, s, eb);
+    ptwo_sum(s, pneg(p3), s, ec);
+    ptwo_sum(s, pneg(p4), s, e);
+    s = psub(s, print(s));
+    const f2 K = pfma(bc(c.Kc), cah, pmul(bc(c.Ks), sah));
+    const f2 lo = padd(psub(psub(padd(padd(bc(c.c0l), e1), e2), e3), e4), padd(padd(padd(ea, eb), ec), e));
+    const f2 small = pfma(pneg(pmul(bc(c.fdT), u)), K, lo);
+    f2 Pc, Pl;
+    ptwo_sum(s, small, Pc, Pl);
+    Pc = psub(Pc, print(Pc));
+    float sx, cx, sy, cy;
+    sincospif(2.0f * Pc.x, &sx, &cx);
+    sincospif(2.0f * Pc.y, &sy, &cy);
+    const f2 sP = make_float2(sx, sy), cP = make_float2(cx, cy);
+    const f2 tl = pmul(bc(6.2831853071795865f), Pl);
+    const cpair ePc{pfma(pneg(tl), sP, cP), pfma(tl, cP, sP)};
+    const f2 f = pfma(bc(c.fdT), u, bc(c.f0));
+    const f2 tu = pmul(bc(Tf), u);
+    // geometry: spacecraft offsets rho_0, rho_1 and arm vectors n_0, n_1
+    const f2 r0x = make_float2(a0.x, b0.x), r0y = make_float2(a0.y, b0.y), r0z = make_float2(a0.z, b0.z);
+    const f2 r1x = make_float2(a0.w, b0.w), r1y = make_float2(a1.x, b1.x), r1z = make_float2(a1.y, b1.y);
+    const f2 n0x = make_float2(a1.z, b1.z), n0y = make_float2(a1.w, b1.w), n0z = make_float2(a2.x, b2.x);
+    const f2 n1x = make_float2(a2.y, b2.y), n1y = make_float2(a2.z, b2.z), n1z = make_float2(a2.w, b2.w);
+    f2 krho[3], urho[3], vrho[3];
+    krho[0] = pfma(bc(c.k0), r0x, pfma(bc(c.k1), r0y, pmul(bc(c.k2), r0z)));
+    krho[1] = pfma(bc(c.k0), r1x, pfma(bc(c.k1), r1y, pmul(bc(c.k2), r1z)));
+    urho[0] = pfma(bc(c.u0), r0x, pfma(bc(c.u1), r0y, pmul(bc(c.u2), r0z)));
+    urho[1] = pfma(bc(c.u0), r1x, pfma(bc(c.u1), r1y, pmul(bc(c.u2), r1z)));
+    vrho[0] = pfma(bc(c.v0), r0x, pmul(bc(c.v1), r0y));
+    vrho[1] = pfma(bc(c.v0), r1x, pmul(bc(c.v1), r1y));
+    krho[2] = psub(pneg(krho[0]), krho[1]);
+    urho[2] = psub(pneg(urho[0]), urho[1]);
+    vrho[2] = psub(pneg(vrho[0]), vrho[1]);
     // phase factor at each receiver
-    float2 rx[3];
-    float kap[3];
+    cpair rx[3];
+    f2 kap[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        kap[j] = K + krho[j];
-        const float dP = fmaf(-f, krho[j], c.fdh * kap[j] * kap[j]);
-        rx[j] = cmulf(ePc, cis_rx<J>(dP));
+        kap[j] = padd(K, krho[j]);
+        const f2 dP = pfma(pneg(f), krho[j], pmul(pmul(bc(c.fdh), kap[j]), kap[j]));
+        rx[j] = pcmul(ePc, pcis_rx<J>(dP));
     }
-    const float a = fmaf(c.a1, u, c.a0);
-    float kn_[3], nu_[3], nv_[3], nw_[3];
-    kn_[0] = fmaf(c.k0, g1.z, fmaf(c.k1, g1.w, c.k2 * g2.x));
-    nu_[0] = fmaf(c.u0, g1.z, fmaf(c.u1, g1.w, c.u2 * g2.x));
-    nv_[0] = fmaf(c.v0, g1.z, c.v1 * g1.w);
-    nw_[0] = fmaf(g.cl, g1.z, g.sl * g1.w);
-    kn_[1] = fmaf(c.k0, g2.y, fmaf(c.k1, g2.z, c.k2 * g2.w));
-    nu_[1] = fmaf(c.u0, g2.y, fmaf(c.u1, g2.z, c.u2 * g2.w));
-    nv_[1] = fmaf(c.v0, g2.y, c.v1 * g2.z);
-    nw_[1] = fmaf(g.cl, g2.y, g.sl * g2.z);
-    kn_[2] = -kn_[0] - kn_[1];
-    nu_[2] = -nu_[0] - nu_[1];
-    nv_[2] = -nv_[0] - nv_[1];
-    nw_[2] = -nw_[0] - nw_[1];
+    const f2 a = pfma(bc(c.a1), u, bc(c.a0));
+    f2 kn_[3], nu_[3], nv_[3], nw_[3];
+    kn_[0] = pfma(bc(c.k0), n0x, pfma(bc(c.k1), n0y, pmul(bc(c.k2), n0z)));
+    nu_[0] = pfma(bc(c.u0), n0x, pfma(bc(c.u1), n0y, pmul(bc(c.u2), n0z)));
+    nv_[0] = pfma(bc(c.v0), n0x, pmul(bc(c.v1), n0y));
+    nw_[0] = pfma(bc(g.cl), n0x, pmul(bc(g.sl), n0y));
+    kn_[1] = pfma(bc(c.k0), n1x, pfma(bc(c.k1), n1y, pmul(bc(c.k2), n1z)));
+    nu_[1] = pfma(bc(c.u0), n1x, pfma(bc(c.u1), n1y, pmul(bc(c.u2), n1z)));
+    nv_[1] = pfma(bc(c.v0), n1x, pmul(bc(c.v1), n1y));
+    nw_[1] = pfma(bc(g.cl), n1x, pmul(bc(g.sl), n1y));
+    kn_[2] = psub(pneg(kn_[0]), kn_[1]);
+    nu_[2] = psub(pneg(nu_[0]), nu_[1]);
+    nv_[2] = psub(pneg(nv_[0]), nv_[1]);
+    nw_[2] = psub(pneg(nw_[0]), nw_[1]);
     // links: [arm][0] towards arm+1's end (+n, receiver arm+1), [arm][1] the
     // other (-n, receiver arm); transfer value and derivative, link value
-    float2 G[3], Tv[3][2], Td[3][2], z[3][2];
+    cpair G[3], Tv[3][2], Td[3][2], z[3][2];
 #pragma unroll
     for (int arm = 0; arm < 3; ++arm) {
-        const float nu = nu_[arm], nv = nv_[arm];
-        const float Fp = (nu - nv) * (nu + nv), Fx = 2.0f * nu * nv;
-        G[arm] = make_float2(fmaf(g.gp.x, Fp, g.gx.x * Fx), fmaf(g.gp.y, Fp, g.gx.y * Fx));
+        const f2 nu = nu_[arm], nv = nv_[arm];
+        const f2 Fp = pmul(psub(nu, nv), padd(nu, nv)), Fx = pmul(pmul(bc(2.0f), nu), nv);
+        G[arm] = cpair{pfma(bc(g.gp.x), Fp, pmul(bc(g.gx.x), Fx)), pfma(bc(g.gp.y), Fp, pmul(bc(g.gx.y), Fx))};
 #pragma unroll
         for (int sgn = 0; sgn < 2; ++sgn) {
-            const float X = a * (sgn == 0 ? 1.0f - kn_[arm] : 1.0f + kn_[arm]);
-            link_transfer_d<J>(X, Tv[arm][sgn], Td[arm][sgn]);
+            const f2 X = pmul(a, sgn == 0 ? psub(bc(1.0f), kn_[arm]) : padd(bc(1.0f), kn_[arm]));
+            plink_transfer_d<J>(X, Tv[arm][sgn], Td[arm][sgn]);
             const int j = sgn == 0 ? (arm == 2 ? 0 : arm + 1) : arm;
-            z[arm][sgn] = cmulf(cmulf(Tv[arm][sgn], G[arm]), rx[j]);
+            z[arm][sgn] = pcmul(pcmul(Tv[arm][sgn], G[arm]), rx[j]);
         }
     }
     // delay factor D = exp(-i f/f*) and F = -i a (1 - D^2) = 2 a sin(f/f*) D
-    const float du = c.eps * u;
-    const float2 D = cmulf(make_float2(c.D0r, c.D0i), make_float2(fmaf(-0.5f * du, du, 1.0f), -du));
-    const float sa2 = -2.0f * a * D.y;
-    const float2 F = make_float2(sa2 * D.x, sa2 * D.y);
+    const f2 du = pmul(bc(c.eps), u);
+    const cpair D = pcmul(cpair{bc(c.D0r), bc(c.D0i)}, cpair{pfma(pmul(bc(-0.5f), du), du, bc(1.0f)), pneg(du)});
+    const f2 sa2 = pmul(pmul(bc(-2.0f), a), D.im);
+    const cpair F = pcscale(D, sa2);
     // first-generation Michelson X, Y, Z (without F)
-    const float2 Xp = caddf(csubf(z[0][1], z[2][0]), cmulf(D, csubf(z[0][0], z[2][1])));
-    const float2 Yp = caddf(csubf(z[1][1], z[0][0]), cmulf(D, csubf(z[1][0], z[0][1])));
-    const float2 Zp = caddf(csubf(z[2][1], z[1][0]), cmulf(D, csubf(z[2][0], z[1][1])));
+    const cpair Xp = pcadd(pcsub(z[0][1], z[2][0]), pcmul(D, pcsub(z[0][0], z[2][1])));
+    const cpair Yp = pcadd(pcsub(z[1][1], z[0][0]), pcmul(D, pcsub(z[1][0], z[0][1])));
+    const cpair Zp = pcadd(pcsub(z[2][1], z[1][0]), pcmul(D, pcsub(z[2][0], z[1][1])));
     // channel weights of X, Y, Z: A = (Z - X)/sqrt2, E = (X - 2Y + Z)/sqrt6,
     // T = (X + Y + Z)/sqrt3, each with conj(c)
-    const float r2 = 0.70710678118654752f, r6 = 0.40824829046386302f;
-    const float2 ca = make_float2(cA.x * r2, -cA.y * r2), ce = make_float2(cE.x * r6, -cE.y * r6);
-    float2 w[3] = {csubf(ce, ca), make_float2(-2.0f * ce.x, -2.0f * ce.y), caddf(ca, ce)};
+    const f2 r2 = bc(0.70710678118654752f), r6 = bc(0.40824829046386302f);
+    const cpair ca{pmul(cA.re, r2), pneg(pmul(cA.im, r2))}, ce{pmul(cE.re, r6), pneg(pmul(cE.im, r6))};
+    cpair w[3] = {pcsub(ce, ca), pcscale(ce, bc(-2.0f)), pcadd(ca, ce)};
     if constexpr (T3) {
-        const float r3 = 0.57735026918962576f;
-        const float2 ct = make_float2(cT.x * r3, -cT.y * r3);
+        const f2 r3 = bc(0.57735026918962576f);
+        const cpair ct{pmul(cT.re, r3), pneg(pmul(cT.im, r3))};
 #pragma unroll
-        for (int q = 0; q < 3; ++q) w[q] = caddf(w[q], ct);
+        for (int q = 0; q < 3; ++q) w[q] = pcadd(w[q], ct);
     }
-    // F and D depend on f0 and fdot: dD = -i D dphi, dphi = (1, t)/f*,
-    // d(sa2) = -2 (da D.y + a dD.y), da = (1, t)/(2 f*)
-    const float2 Wsum = caddf(caddf(cmulf(w[0], Xp), cmulf(w[1], Yp)), cmulf(w[2], Zp));
-    float2 om[3], Dom[3];
+    const cpair Wsum = pcadd(pcadd(pcmul(w[0], Xp), pcmul(w[1], Yp)), pcmul(w[2], Zp));
+    cpair om[3], Dom[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        om[q] = cmulf(F, w[q]);
-        Dom[q] = cmulf(D, om[q]);
+        om[q] = pcmul(F, w[q]);
+        Dom[q] = pcmul(D, om[q]);
     }
-    const float2 Qd = caddf(caddf(cmulf(om[0], csubf(z[0][0], z[2][1])), cmulf(om[1], csubf(z[1][0], z[0][1]))),
-                            cmulf(om[2], csubf(z[2][0], z[1][1])));
+    const cpair Qd = pcadd(pcadd(pcmul(om[0], pcsub(z[0][0], z[2][1])), pcmul(om[1], pcsub(z[1][0], z[0][1]))),
+                           pcmul(om[2], pcsub(z[2][0], z[1][1])));
     {
-        // per unit dphi: dD = -i D, so Re(Qd dD) = Im(Qd D); da = 1/2 and
+        // F and D depend on f0 and fdot through dphi = (1, t)/f*: per unit
+        // dphi, dD = -i D, so Re(Qd dD) = Im(Qd D); da = 1/2 and
         // d(sa2) = -2 (D.y / 2 + a (-D.x)) = 2 a D.x - D.y
-        const float2 QD = cmulf(Qd, D);
-        const float dsa2 = fmaf(2.0f * a, D.x, -D.y);
-        const float2 dF = make_float2(fmaf(dsa2, D.x, sa2 * D.y), fmaf(dsa2, D.y, -sa2 * D.x));
-        const float fdf = fmaf(dF.x, Wsum.x, -dF.y * Wsum.y) + QD.y;   // per unit dphi
-        dth[0] = fmaf(fdf, inv_fstar, dth[0]);
-        dth[1] = fmaf(fdf, tu * inv_fstar, dth[1]);
+        const f2 dsa2 = pfma(pmul(bc(2.0f), a), D.re, pneg(D.im));
+        const cpair dF{pfma(dsa2, D.re, pmul(sa2, D.im)), pfma(dsa2, D.im, pneg(pmul(sa2, D.re)))};
+        const f2 fdf = padd(pcre(dF, Wsum), pcim(Qd, D));   // per unit dphi
+        dth[0] = pfma(fdf, bc(inv_fstar), dth[0]);
+        dth[1] = pfma(fdf, pmul(tu, bc(inv_fstar)), dth[1]);
     }
-    float A1 = 0.0f;                           // sum of Re(mu G rx T') (1 -+ kn)
-    float Phi[3] = {0.0f, 0.0f, 0.0f};         // sum over the receiver's links of Im(mu z)
+    f2 A1 = bc(0.0f);                          // sum of Re(mu G rx T') (1 -+ kn)
+    f2 Phi[3] = {bc(0.0f), bc(0.0f), bc(0.0f)};   // sum over the receiver's links of Im(mu z)
 #pragma unroll
     for (int arm = 0; arm < 3; ++arm) {
         const int an = arm == 2 ? 0 : arm + 1;
-        float B = 0.0f;                        // sum of -+ Re(mu G rx T')
-        float2 Gam = make_float2(0.0f, 0.0f);
+        f2 B = bc(0.0f);                       // sum of -+ Re(mu G rx T')
+        cpair Gam{bc(0.0f), bc(0.0f)};
 #pragma unroll
         for (int sgn = 0; sgn < 2; ++sgn) {
             const int j = sgn == 0 ? an : arm;
-            const float2 mu = sgn == 0 ? csubf(Dom[arm], om[an]) : csubf(om[arm], Dom[an]);
-            const float2 nu_l = cmulf(mu, rx[j]);
-            const float2 nuG = cmulf(nu_l, G[arm]);
-            const float rho = fmaf(nuG.x, Td[arm][sgn].x, -nuG.y * Td[arm][sgn].y);
-            Phi[j] += fmaf(nuG.x, Tv[arm][sgn].y, nuG.y * Tv[arm][sgn].x);
-            Gam = caddf(Gam, cmulf(nu_l, Tv[arm][sgn]));
-            const float kf = sgn == 0 ? 1.0f - kn_[arm] : 1.0f + kn_[arm];
-            A1 = fmaf(rho, kf, A1);
-            B += sgn == 0 ? -rho : rho;
+            const cpair mu = sgn == 0 ? pcsub(Dom[arm], om[an]) : pcsub(om[arm], Dom[an]);
+            const cpair nl = pcmul(mu, rx[j]);
+            const cpair nG = pcmul(nl, G[arm]);
+            const f2 rho = pcre(nG, Td[arm][sgn]);
+            Phi[j] = padd(Phi[j], pcim(nG, Tv[arm][sgn]));
+            Gam = pcadd(Gam, pcmul(nl, Tv[arm][sgn]));
+            const f2 kf = sgn == 0 ? psub(bc(1.0f), kn_[arm]) : padd(bc(1.0f), kn_[arm]);
+            A1 = pfma(rho, kf, A1);
+            B = sgn == 0 ? psub(B, rho) : padd(B, rho);
         }
-        const float nu = nu_[arm], nv = nv_[arm], nw = nw_[arm], kn = kn_[arm];
-        const float Fp = (nu - nv) * (nu + nv), Fx = 2.0f * nu * nv;
+        const f2 nu = nu_[arm], nv = nv_[arm], nw = nw_[arm], kn = kn_[arm];
+        const f2 Fp = pmul(psub(nu, nv), padd(nu, nv)), Fx = pmul(pmul(bc(2.0f), nu), nv);
         // Re(Gamma dG) = Re(Gamma gp) dF+ + Re(Gamma gx) dFx
-        const float gpr = fmaf(Gam.x, g.gp.x, -Gam.y * g.gp.y), gxr = fmaf(Gam.x, g.gx.x, -Gam.y * g.gx.y);
+        const f2 gpr = pcre(Gam, pcbc(g.gp)), gxr = pcre(Gam, pcbc(g.gx));
         // beta: dn.u = -k.n, dn.v = 0; lambda: dn.u = -sin(beta) n.v, dn.v = n.w;
         // dX = -+ a dk.n with dk.n = n.u (beta), cos(beta) n.v (lambda)
-        const float dnu_l = -g.sb * nv;
-        const float dFp_b = -2.0f * nu * kn, dFx_b = -2.0f * kn * nv;
-        const float dFp_l = 2.0f * fmaf(nu, dnu_l, -nv * nw), dFx_l = 2.0f * fmaf(dnu_l, nv, nu * nw);
-        dth[2] += fmaf(gpr, dFp_b, fmaf(gxr, dFx_b, a * B * nu));
-        dth[3] += fmaf(gpr, dFp_l, fmaf(gxr, dFx_l, a * B * g.cb * nv));
-        up = caddf(up, make_float2(Gam.x * Fp, Gam.y * Fp));
-        uq = caddf(uq, make_float2(Gam.x * Fx, Gam.y * Fx));
+        const f2 dnu_l = pmul(bc(-g.sb), nv);
+        const f2 dFp_b = pmul(pmul(bc(-2.0f), nu), kn), dFx_b = pmul(pmul(bc(-2.0f), kn), nv);
+        const f2 dFp_l = pmul(bc(2.0f), pfma(nu, dnu_l, pneg(pmul(nv, nw))));
+        const f2 dFx_l = pmul(bc(2.0f), pfma(dnu_l, nv, pmul(nu, nw)));
+        const f2 aB = pmul(a, B);
+        dth[2] = padd(dth[2], pfma(gpr, dFp_b, pfma(gxr, dFx_b, pmul(aB, nu))));
+        dth[3] = padd(dth[3], pfma(gpr, dFp_l, pfma(gxr, dFx_l, pmul(pmul(aB, bc(g.cb)), nv))));
+        up = pcadd(up, pcscale(Gam, Fp));
+        uq = pcadd(uq, pcscale(Gam, Fx));
     }
     // transfer functions: dX = da (1 -+ kn), da = (1, t)/(2 f*)
-    dth[0] = fmaf(A1, 0.5f * inv_fstar, dth[0]);
-    dth[1] = fmaf(A1, 0.5f * tu * inv_fstar, dth[1]);
+    dth[0] = pfma(A1, bc(0.5f * inv_fstar), dth[0]);
+    dth[1] = pfma(A1, pmul(tu, bc(0.5f * inv_fstar)), dth[1]);
     // receiver phases: d phase_j = (t - kap, (t - kap)^2/2, -(f - fdot kap) u.x_j/c,
     // -(f - fdot kap) cos(beta) v.x_j/c) cycles
-    const float ux0 = fmaf(g.Uc, cah, g.Us * sah), vx0 = fmaf(g.Vc, cah, g.Vs * sah);
+    const f2 ux0 = pfma(bc(g.Uc), cah, pmul(bc(g.Us), sah)), vx0 = pfma(bc(g.Vc), cah, pmul(bc(g.Vs), sah));
+    const float fd = 2.0f * c.fdh;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const float ph = -6.2831853071795865f * Phi[j];
-        const float tk = tu - kap[j];
-        const float fk = fmaf(-fd, kap[j], f);
-        dth[0] = fmaf(ph, tk, dth[0]);
-        dth[1] = fmaf(ph, 0.5f * tk * tk, dth[1]);
-        dth[2] = fmaf(ph, -fk * (ux0 + urho[j]), dth[2]);
-        dth[3] = fmaf(ph, -fk * g.cb * (vx0 + vrho[j]), dth[3]);
+        const f2 ph = pmul(bc(-6.2831853071795865f), Phi[j]);
+        const f2 tk = psub(tu, kap[j]);
+        const f2 mfk = pfma(bc(fd), kap[j], pneg(f));   // -(f - fdot kap)
+        dth[0] = pfma(ph, tk, dth[0]);
+        dth[1] = pfma(pmul(ph, bc(0.5f)), pmul(tk, tk), dth[1]);
+        dth[2] = pfma(pmul(ph, mfk), padd(ux0, urho[j]), dth[2]);
+        dth[3] = pfma(pmul(ph, mfk), pmul(bc(g.cb), padd(vx0, vrho[j])), dth[3]);
     }
 }
 
-// The sample adjoints of one candidate: lane l takes samples l, l + 32, ...
-// (cA, cE, cT: the adjoint transform's output c^_n; cT may be null in the T
-// instantiation, for windows without T).  Sums are compensated per lane.
+// The sample adjoints of one candidate: lane l takes the sample pairs
+// (l + 64 m, l + 64 m + 32) (cA, cE, cT: the adjoint transform's output c^_n;
+// cT may be null in the T instantiation, for windows without T).  Sums are
+// compensated per lane and sample slot, then merged.
 template <int J, bool T3 = false>
 __device__ void adjoint_sweep(const CandGx& g, const OrbitTables32& tab, int N, float Tf, float inv_fstar,
                               const float2* cA, const float2* cE, int lane, float (&tacc)[KT][2],
                               float (&vp)[2][2], float (&vq)[2][2], const float2* cT = nullptr) {
-    for (int n = lane; n < N; n += 32) {
-        float dth[KT] = {0.0f, 0.0f, 0.0f, 0.0f};
-        float2 up = make_float2(0.0f, 0.0f), uq = make_float2(0.0f, 0.0f);
-        const float2 t = (T3 && cT) ? cT[n] : make_float2(0.0f, 0.0f);
-        sample_adjoint<J, T3>(g, tab, N, n, Tf, inv_fstar, cA[n], cE[n], t, dth, up, uq);
+    f2 sum[KT + 4], comp[KT + 4];
 #pragma unroll
-        for (int p = 0; p < 2; ++p) {
-            f2 sum = make_float2(tacc[2 * p][0], tacc[2 * p + 1][0]), comp = make_float2(tacc[2 * p][1], tacc[2 * p + 1][1]);
-            kahan_add2(sum, comp, make_float2(dth[2 * p], dth[2 * p + 1]));
-            tacc[2 * p][0] = sum.x;
-            tacc[2 * p + 1][0] = sum.y;
-            tacc[2 * p][1] = comp.x;
-            tacc[2 * p + 1][1] = comp.y;
-        }
+    for (int k = 0; k < KT + 4; ++k) sum[k] = comp[k] = bc(0.0f);
+    for (int n0 = lane; n0 < N; n0 += 64) {
+        // N = 32: the second slot repeats sample n0 with zero cotangents
+        const bool two = n0 + 32 < N;
+        const int n1 = two ? n0 + 32 : n0;
+        auto ld = [&](const float2* b) {
+            const float2 x = b[n0], y = two ? b[n1] : make_float2(0.0f, 0.0f);
+            return cpair{make_float2(x.x, y.x), make_float2(x.y, y.y)};
+        };
+        const cpair a = ld(cA), e = ld(cE), t = (T3 && cT) ? ld(cT) : cpair{bc(0.0f), bc(0.0f)};
+        f2 dth[KT] = {bc(0.0f), bc(0.0f), bc(0.0f), bc(0.0f)};
+        cpair up{bc(0.0f), bc(0.0f)}, uq{bc(0.0f), bc(0.0f)};
+        sample_adjoint<J, T3>(g, tab, N, n0, n1, Tf, inv_fstar, a, e, t, dth, up, uq);
+#pragma unroll
+        for (int k = 0; k < KT; ++k) kahan_add2(sum[k], comp[k], dth[k]);
         // V = sum c conj(P) = conj(U_P)
-        kahan_add(vp[0][0], vp[0][1], up.x);
-        kahan_add(vp[1][0], vp[1][1], -up.y);
-        kahan_add(vq[0][0], vq[0][1], uq.x);
-        kahan_add(vq[1][0], vq[1][1], -uq.y);
+        kahan_add2(sum[KT], comp[KT], up.re);
+        kahan_add2(sum[KT + 1], comp[KT + 1], pneg(up.im));
+        kahan_add2(sum[KT + 2], comp[KT + 2], uq.re);
+        kahan_add2(sum[KT + 3], comp[KT + 3], pneg(uq.im));
     }
+#pragma unroll
+    for (int k = 0; k < KT; ++k) kahan_merge(sum[k], comp[k], tacc[k][0], tacc[k][1]);
+    kahan_merge(sum[KT], comp[KT], vp[0][0], vp[0][1]);
+    kahan_merge(sum[KT + 1], comp[KT + 1], vp[1][0], vp[1][1]);
+    kahan_merge(sum[KT + 2], comp[KT + 2], vq[0][0], vq[0][1]);
+    kahan_merge(sum[KT + 3], comp[KT + 3], vq[1][0], vq[1][1]);
 }
 
 // Forward FFT of R register values per lane: on entry lane l holds input
