@@ -183,6 +183,22 @@ def flops_per_eval(N, f_hz, T):
     return N * per_sample + 2 * 5 * N * math.log2(N) + 26 * N
 
 
+def flops_per_grad(N, f_hz, T):
+    """Floating-point operations of one mixed-precision gradient (FMA = 2).
+
+    The forward evaluation (as flops_per_eval, with 38 per window bin for the
+    inner products and the weighted residual), the adjoint transform of both
+    channels (2 x 5 N log2 N), and per sample the reverse-mode step: the
+    sample's values again, with the transfer functions' X derivatives
+    (508 + 48 J), and the adjoint arithmetic from the channel weights to the
+    four parameter sums and the P, Q sums (555).
+    """
+    xmax = f_hz / (299792458.0 / (2 * math.pi * 2.5e9))
+    J = 4 if xmax <= 0.489 else 7 if xmax <= 1.34 else 10
+    forward = N * (483 + 24 * J) + 2 * 5 * N * math.log2(N) + 38 * N
+    return forward + 2 * 5 * N * math.log2(N) + N * (508 + 48 * J + 555)
+
+
 def profiled_traffic():
     """DRAM bytes per launch of the likelihood kernel from the committed ncu
     summary, or None when the kernel source changed since that capture."""
@@ -370,6 +386,14 @@ def run_workload(args):
         sub = [(k0, W, N, doff, coff, 512) for (k0, W, N, doff, coff, nc) in wl.windows]
         ms_g64 = timed(lambda: ctx.loglik_grad(sub, *data, theta, prec="fp64"), 1)
         line["grad_mixed"] = {"value": n / ms_g * 1e3, "unit": "gradients/s", "ms": ms_g}
+        f_mid = np.array([w[0] + w[1] / 2 for w in wl.windows]) / wl.T
+        gflops = sum(w[5] * flops_per_grad(w[2], f, wl.T) for w, f in zip(wl.windows, f_mid))
+        peak = 152 * 128 * 2 * 2070e6 / 1e12
+        line["grad_mixed"]["roofline"] = {
+            "bound": "alu", "achieved": gflops / (ms_g / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "frac": gflops / (ms_g / 1e3) / 1e12 / peak, "traffic": None, "kernel": "grad_mixed_kernel",
+            "peak_note": "FP32 FMA peak from unit counts: 152 SM x 128 lanes x 2 x 2070 MHz; the timed call "
+                         "is the preparation kernel and the gradient kernel"}
         line["grad_fp64"] = {"value": 512 * len(sub) / ms_g64 * 1e3, "unit": "gradients/s", "ms": ms_g64,
                              "sample": "512 candidates per window"}
         boxes = np.array([np.concatenate([wl.theta[c:c + m].min(0), wl.theta[c:c + m].max(0)])
