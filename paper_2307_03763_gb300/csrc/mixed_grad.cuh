@@ -404,6 +404,10 @@ __device__ void residual_adjoint(float2* buf, int ch, const OrbitTables32& tab, 
                                  const LaneTw& ltw, int lane, int off, int W, const Win32* __restrict__ pw,
                                  float kappa, float& sdh, float& cdh, float& shh, float& chh) {
     constexpr int N = 32 * R;
+    // the residual is stored swizzled, entry e at e ^ ((e >> SH) & 15): both
+    // the natural-order writes and the transform's transposed reads (lane l,
+    // entries R brev5(l) + r) then touch 16 distinct bank pairs per half warp
+    constexpr int SH = (R == 1 ? 0 : R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : R == 16 ? 4 : 5) + 1;
     float2 x[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) x[r] = buf[r * 32 + lane];
@@ -423,12 +427,15 @@ __device__ void residual_adjoint(float2* buf, int ch, const OrbitTables32& tab, 
             kahan_add(shh, chh, __fmul_rn(w, fmaf(x[k1].x, x[k1].x, x[k1].y * x[k1].y)));
             rc = make_float2(w * fmaf(-kappa, x[k1].x, d.x), -(w * fmaf(-kappa, x[k1].y, d.y)));   // conj(r)
         }
-        buf[k] = rc;
+        buf[k ^ ((k >> SH) & 15)] = rc;
     }
     __syncwarp();
     const int nb = R * brev5(lane);
 #pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = buf[nb + r];
+    for (int r = 0; r < R; ++r) {
+        const int e = nb + r;
+        x[r] = buf[e ^ ((e >> SH) & 15)];
+    }
     fft_regs<R>(x, tab, tw1024, ltw, lane);
     __syncwarp();
 #pragma unroll
