@@ -359,6 +359,13 @@ def run_workload(args):
             "fp64": {"value": n / ms_64 * 1e3, "ms": ms_64},
             "mixed_vs_fp64": {"max_abs_dlogL": float(dl.max()), "median_abs_dlogL": float(dl.median())},
             "l2": "flushed between timed launches"}
+    # algorithmic rate of the mixed launch (preparation + likelihood kernels)
+    f_mid = np.array([w[0] + w[1] / 2 for w in wl.windows]) / wl.T
+    flops = sum(w[5] * flops_per_eval(w[2], f, wl.T) for w, f in zip(wl.windows, f_mid))
+    peak = 152 * 128 * 2 * 2070e6 / 1e12
+    line["mixed"]["roofline"] = {"bound": "alu", "achieved": flops / (ms_mx / 1e3) / 1e12, "peak": peak,
+                                 "unit": "TFLOP/s", "frac": flops / (ms_mx / 1e3) / 1e12 / peak,
+                                 "kernel": "loglik_mixed_kernel"}
     if args.workload == "band":
         Ns = np.array([w[2] for w in wl.windows])
         per = {}
