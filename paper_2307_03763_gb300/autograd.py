@@ -53,6 +53,33 @@ def observed_fisher(lib_ctx, windows, dA, dE, wA, wE, theta, prec="fp64", rel=1e
     return F
 
 
+def expected_fisher(lib_ctx, windows, wA, wE, theta, prec="fp64", rel=1e-5):
+    """Fisher matrix F_ij = <d_i h|d_j h> (Eq. 13, read with h in place of the
+    garbled p(d|theta)) at one parameter set per window; returns (n_win, 8, 8).
+
+    It is the observed information of noise-free data d = h(theta) on each
+    window: -d2 logL = <d_i h|d_j h> - <d - h|d_i d_j h>, and the second term
+    vanishes there.  The data are the FP64 waveforms of theta placed on the
+    windows' bins; the rest is observed_fisher.
+    """
+    dev = theta.device
+    n_bins = wA.shape[0]
+    dA = torch.zeros(n_bins, dtype=torch.complex128, device=dev)
+    dE = torch.zeros(n_bins, dtype=torch.complex128, device=dev)
+    for N in sorted({w[2] for w in windows}):
+        sel = [i for i, w in enumerate(windows) if w[2] == N]
+        hA, hE, q = lib_ctx.waveform(theta[sel].contiguous(), N, "fp64")
+        k0 = torch.as_tensor([windows[i][0] for i in sel], device=dev)
+        W = torch.as_tensor([windows[i][1] for i in sel], device=dev)
+        off = torch.as_tensor([windows[i][3] for i in sel], device=dev)
+        loc = q[:, None] - N // 2 + torch.arange(N, device=dev)[None, :] - k0[:, None]
+        ok = (loc >= 0) & (loc < W[:, None])
+        idx = (off[:, None] + loc)[ok]
+        dA[idx] = hA[ok]
+        dE[idx] = hE[ok]
+    return observed_fisher(lib_ctx, windows, dA, dE, wA, wE, theta, prec=prec, rel=rel)
+
+
 def newton_polish(lib_ctx, windows, dA, dE, wA, wE, theta, iters=6, prec="mixed", lam0=1e-3):
     """Local maximisation of logL from one point per window (the gradient
     polish that stands in for Alg. 2's SLSQP step): Levenberg-Marquardt

@@ -492,6 +492,24 @@ def test_observed_fisher_matches_oracle_fisher(ctx):
     assert np.all(np.linalg.eigvalsh(Fs) > -1e-9 * d.max())
 
 
+def test_expected_fisher_matches_oracle_fisher(ctx1):
+    # F = <d_i h|d_j h> at one source per window, every N of the band workload
+    from paper_2307_03763_gb300 import autograd as ag
+    wl = wk.band_windows(n_win=10, cand_range=(1, 2))
+    src = np.stack([wl.sources[w][0] for w in range(len(wl.windows))])
+    for w in range(len(wl.windows)):
+        src[w, 4] *= 50.0 / _data.unit_snr(src[w], wl.windows[w], wl.w_A, wl.w_E, wl.T)
+    F = ag.expected_fisher(ctx1, wl.windows, _cuda(wl.w_A, torch.float64), _cuda(wl.w_E, torch.float64),
+                           _cuda(src, torch.float64)).cpu().numpy()
+    assert sorted({w[2] for w in wl.windows}) == [32, 64, 128, 256, 512, 1024]
+    for w in range(len(wl.windows)):
+        ref = _data.fisher_matrix(src[w], wl.windows[w], wl.w_A, wl.w_E, wl.T)
+        sc = np.array([1 / wl.T, 1 / wl.T ** 2, 1, 1, src[w, 4], 1, 1, 1])
+        Fs, Rs = F[w] * np.outer(sc, sc), ref * np.outer(sc, sc)
+        d = np.sqrt(np.outer(np.diag(Rs), np.diag(Rs)))
+        assert np.abs(Fs - Rs).max() <= 1e-5 * d.max() and (np.abs(Fs - Rs) / d).max() < 1e-4, (w, Fs, Rs)
+
+
 def test_time_budget_stops_persistent_kernels(api):
     # 1 ns: no warp takes an item; a fifth of the launch time: some do.  The
     # rows of the items not taken stay as they were and the check reports it.
