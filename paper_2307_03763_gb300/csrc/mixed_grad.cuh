@@ -443,6 +443,87 @@ __device__ void residual_adjoint(float2* buf, int ch, const OrbitTables32& tab, 
     __syncwarp();
 }
 
+// lane_fft of a channel pair (packed FP32)
+__device__ __forceinline__ cpair lane_fft2(cpair x, const LaneTw& tw, int lane) {
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int h = 1 << s;
+        const cpair u = s == 0 ? x : pcmul(x, pcbc(tw.w[s - 1]));
+        const cpair v = shfl_xor4(u, h);
+        x = (lane & h) ? pcsub(v, u) : pcadd(u, v);
+    }
+    return x;
+}
+
+// fft_regs of a channel pair
+template <int R>
+__device__ __forceinline__ void fft_regs2(cpair (&x)[R], const OrbitTables32& tab, const LaneTw& ltw, int lane) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = lane_fft2(x[r], ltw, lane);
+#pragma unroll
+    for (int r = 1; r < R; ++r) x[r] = pcmul(x[r], ldg4(tab.ltw4 + r * 32 + lane));
+    reg_fft2<R>(x);
+}
+
+// residual_adjoint of both channels at once (A, E in the two halves of each
+// packed register pair), for N <= 256; the sums of both channels are added
+// into (sdh, cdh) and (shh, chh).
+template <int R>
+__device__ void residual_adjoint2(float2* bufA, float2* bufE, const OrbitTables32& tab, const LaneTw& ltw, int lane,
+                                  int off, int W, const Win32* __restrict__ pw, float kappa, float& sdh, float& cdh,
+                                  float& shh, float& chh) {
+    constexpr int N = 32 * R;
+    constexpr int SH = (R == 1 ? 0 : R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : R == 16 ? 4 : 5) + 1;
+    cpair x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const float2 a = bufA[r * 32 + lane], e = bufE[r * 32 + lane];
+        x[r] = cpair{make_float2(a.x, e.x), make_float2(a.y, e.y)};
+    }
+    fft_regs2<R>(x, tab, ltw, lane);
+    __syncwarp();
+    f2 s_dh = bc(0.0f), c_dh = bc(0.0f), s_hh = bc(0.0f), c_hh = bc(0.0f);
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) {
+        const int k = lane + 32 * k1;
+        const int m = k < N / 2 ? k : k - N;
+        const int kk = off + m;
+        cpair rc{bc(0.0f), bc(0.0f)};
+        if (kk >= 0 && kk < W) {
+            const Win32 v = pw[kk];
+            const cpair d{v.dre, v.dim};
+            kahan_add2(s_dh, c_dh, pmul(v.w, pfma(d.re, x[k1].re, pmul(d.im, x[k1].im))));
+            kahan_add2(s_hh, c_hh, pmul(v.w, pfma(x[k1].re, x[k1].re, pmul(x[k1].im, x[k1].im))));
+            rc = cpair{pmul(v.w, pfma(bc(-kappa), x[k1].re, d.re)),
+                       pneg(pmul(v.w, pfma(bc(-kappa), x[k1].im, d.im)))};   // conj(r)
+        }
+        const int ks = k ^ ((k >> SH) & 15);   // the swizzle of residual_adjoint
+        bufA[ks] = make_float2(rc.re.x, rc.im.x);
+        bufE[ks] = make_float2(rc.re.y, rc.im.y);
+    }
+    float ps, pc;
+    kahan_merge(s_dh, c_dh, ps, pc);
+    kahan_join(sdh, cdh, ps, pc);
+    kahan_merge(s_hh, c_hh, ps, pc);
+    kahan_join(shh, chh, ps, pc);
+    __syncwarp();
+    const int nb = R * brev5(lane);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = nb + r, es = e ^ ((e >> SH) & 15);
+        const float2 a = bufA[es], b = bufE[es];
+        x[r] = cpair{make_float2(a.x, b.x), make_float2(a.y, b.y)};
+    }
+    fft_regs2<R>(x, tab, ltw, lane);
+    __syncwarp();
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) {   // c^_n
+        bufA[lane + 32 * k1] = make_float2(x[k1].re.x, -x[k1].im.x);
+        bufE[lane + 32 * k1] = make_float2(x[k1].re.y, -x[k1].im.y);
+    }
+    __syncwarp();
+}
+
 // resident CTAs per SM the N <= 256 instantiation is compiled for (register cap)
 #ifndef GB_GRAD_MINB
 #define GB_GRAD_MINB 2
@@ -501,17 +582,18 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_GRAD_MINB : 1) g
                 const long long off64 = g.m.q - win.k0;
                 const int off = (off64 > -(long long)N && off64 < (long long)win.W + N) ? (int)off64 : -4 * N;
                 const float kappa = (float)(wm.sig * g.m.A * T / (2.0 * (double)N));
+                if constexpr (RMAX <= 8) {   // both channels at once
+                    switch (N) {
+                        case 32: residual_adjoint2<1>(bufA, bufE, tab, ltw, lane, off, win.W, pw, kappa, sdh, cdh, shh, chh); break;
+                        case 64: residual_adjoint2<2>(bufA, bufE, tab, ltw, lane, off, win.W, pw, kappa, sdh, cdh, shh, chh); break;
+                        case 128: residual_adjoint2<4>(bufA, bufE, tab, ltw, lane, off, win.W, pw, kappa, sdh, cdh, shh, chh); break;
+                        default: residual_adjoint2<8>(bufA, bufE, tab, ltw, lane, off, win.W, pw, kappa, sdh, cdh, shh, chh); break;
+                    }
+                }
 #pragma unroll
                 for (int ch = 0; ch < 2; ++ch) {
                     float2* buf = ch == 0 ? bufA : bufE;
-                    if constexpr (RMAX <= 8) {
-                        switch (N) {
-                            case 32: residual_adjoint<1>(buf, ch, tab, tw1024, ltw, lane, off, win.W, pw, kappa, sdh, cdh, shh, chh); break;
-                            case 64: residual_adjoint<2>(buf, ch, tab, tw1024, ltw, lane, off, win.W, pw, kappa, sdh, cdh, shh, chh); break;
-                            case 128: residual_adjoint<4>(buf, ch, tab, tw1024, ltw, lane, off, win.W, pw, kappa, sdh, cdh, shh, chh); break;
-                            default: residual_adjoint<8>(buf, ch, tab, tw1024, ltw, lane, off, win.W, pw, kappa, sdh, cdh, shh, chh); break;
-                        }
-                    } else {
+                    if constexpr (RMAX > 8) {
                         if (N == 512)
                             residual_adjoint<16>(buf, ch, tab, tw1024, ltw, lane, off, win.W, pw, kappa, sdh, cdh, shh, chh);
                         else
