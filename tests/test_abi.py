@@ -43,3 +43,24 @@ def test_window_struct_layout():
     from paper_2307_03763_gb300 import api
     assert ctypes.sizeof(api.Window) == 40
     assert ctypes.sizeof(api.Obs) == 24
+
+
+def test_header_is_plain_c_and_links(libpath, tmp_path):
+    # a C99 program that takes the address of every declared entry point
+    # compiles without warnings against gb.h and links against the library
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = declared_functions()
+    src = tmp_path / "use_gb.c"
+    src.write_text('#include "gb.h"\n#include <stdio.h>\nint main(void) {\n'
+                   + "".join('    printf("%%p\\n", (void*)&%s);\n' % n for n in names)
+                   + "    return 0;\n}\n")
+    exe = tmp_path / "use_gb"
+    cmd = [cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I",
+           os.path.join(ROOT, "include"), str(src), "-o", str(exe), libpath,
+           "-Wl,-rpath," + os.path.dirname(libpath)]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
