@@ -60,13 +60,15 @@ def _source(theta):
 
 
 def tdi_AE_series(theta, t, L):
-    """Real TDI A(t), E(t) at the sample times t (1-D array), exact delays."""
+    """Real TDI A(t), E(t) at the sample times t (1-D array), exact delays
+    (Eq. 5 with the link and Michelson forms of the module docstring)."""
     A, E, _ = tdi_AET_series(theta, t, L)
     return A, E
 
 
 def tdi_AET_series(theta, t, L):
-    """Real TDI A(t), E(t), T(t) = (X + Y + Z)/sqrt3 at the sample times t."""
+    """Real TDI A(t), E(t), T(t) = (X + Y + Z)/sqrt3 at the sample times t
+    (Eq. 5; T is the third channel of Sec. II, reading R11)."""
     f0, fdot, phi0, khat, H = _source(theta)
     tau = L / C_LIGHT
     # events m = 0..4: time t - m tau, every spacecraft at its position then
@@ -97,7 +99,7 @@ def tdi_AET_series(theta, t, L):
 
 
 def brute_force_spectrum_aet(theta, T, dt, bins, L=2.5e9, chunk=1 << 16):
-    """brute_force_spectrum() with T: (A~, E~, T~) at the given bins."""
+    """brute_force_spectrum() with T: (A~, E~, T~) at the given bins (Sec. II, R11)."""
     n_tot = int(round(T / dt))
     out = np.empty((3, n_tot))
     for s in range(0, n_tot, chunk):
@@ -109,7 +111,8 @@ def brute_force_spectrum_aet(theta, T, dt, bins, L=2.5e9, chunk=1 << 16):
 
 
 def brute_force_spectrum(theta, T, dt, bins, L=2.5e9, chunk=1 << 16):
-    """dt * DFT of the time-domain A, E series over [0, T), at the given bins.
+    """dt * DFT of the time-domain A, E series over [0, T), at the given bins
+    (the continuous-Fourier convention of the inner product, Eq. 3).
 
     theta: one parameter vector (8,); bins: integer frequency bins k (f = k/T).
     Returns (A~, E~) complex arrays with len(bins) entries.

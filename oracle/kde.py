@@ -81,7 +81,7 @@ def reduced_box(mle, sigma, prior_lo, prior_hi):
 
 
 def accepted_moves(chain):
-    """Number of i >= 1 where the chain moved to proposal i."""
+    """Number of i >= 1 where the chain moved to proposal i (the acceptances of Alg. 4)."""
     return sum(1 for i in range(1, len(chain)) if chain[i] == i)
 
 
@@ -96,7 +96,8 @@ def kernel_weights(sigma, G):
 
 
 def smoothing_matrix(sigma, G):
-    """G x G matrix M with (M v)_i = sum_d k_d v_(i-d), zero outside the grid."""
+    """G x G matrix M with (M v)_i = sum_d k_d v_(i-d), zero outside the grid
+    (the Gaussian smoothing of reading K3)."""
     k, r = kernel_weights(sigma, G)
     M = np.zeros((G, G))
     for i in range(G):
@@ -107,6 +108,7 @@ def smoothing_matrix(sigma, G):
 
 
 def cell_index(v, lo, hi, G):
+    """Grid cell of v on [lo, hi) with G cells, clamped to the grid (reading K3)."""
     i = math.floor((v - lo) / (hi - lo) * G)
     return min(max(i, 0), G - 1)
 
@@ -137,7 +139,7 @@ def pair_grid(x, y, n_eff, box_x, box_y, G, eps):
 
 
 def flat_grid(G):
-    """Reading K5."""
+    """The uniform first-temperature density over the box (reading K5)."""
     return np.full((G, G), 1.0 / (G * G))
 
 
@@ -147,7 +149,8 @@ def cumulative(P):
 
 
 def build_window(theta, chain, lo, hi, G, eps):
-    """Cumulative sums of the three pair grids of one window from its chain,
+    """Cumulative sums of the three pair grids of one window from its chain
+    (readings K1, K3, K4; Sec. III.G),
     and their extents: theta (n, 8) proposals, chain (n) state index after
     each step.  Returns (C (3, G^2), E (3, 4) = lo'_x, hi'_x, lo'_y, hi'_y)."""
     theta = np.asarray(theta, float)
@@ -167,6 +170,7 @@ def box_extents(lo, hi):
 
 
 def u01(word):
+    """A 32-bit Philox word as a uniform variate in (0, 1): (word + 1/2) / 2^32 (reading K7)."""
     return (int(word) + 0.5) * 2.0 ** -32
 
 

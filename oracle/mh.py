@@ -61,7 +61,8 @@ def mh_independence(logL, log_g, log_u, temperature, literal=False):
 
 
 def mh_independence_batch(logL, log_g, log_u, temperature, literal=False):
-    """Independent chains, one per row: inputs (n_chains, n); temperature (n_chains,)."""
+    """Independent chains of Alg. 4, one per row: inputs (n_chains, n);
+    temperature (n_chains,)."""
     chains, acc = [], []
     for r in range(len(logL)):
         ch, a = mh_independence(logL[r], log_g[r], log_u[r], temperature[r], literal)
