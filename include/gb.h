@@ -204,8 +204,10 @@ int gb_loglik_grad(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_wi
                    int64_t n_bins, const double* theta, int64_t n_rows,
                    double* logL, double* grad, void* stream);
 
-/* gb_loglik_phase with the T channel in the windows above f* / 2 (as
- * gb_loglik_aet): dh_im sums over A, E and T alike. */
+/* gb_loglik_phase with the T channel in the windows above f* / 2 of Sec. II
+ * (as gb_loglik_aet): dh_im sums over A, E and T alike, so it is the
+ * three-channel <d|h> at phi0 + pi/2.  dT, wT as in gb_loglik_aet (not NULL);
+ * dh_im not NULL; otherwise the inputs, outputs and errors of gb_loglik. */
 int gb_loglik_phase_aet(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win,
                         const double* dA, const double* dE, const double* dT, const double* wA,
                         const double* wE, const double* wT, int64_t n_bins, const double* theta,
