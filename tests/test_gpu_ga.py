@@ -6,7 +6,6 @@ import numpy as np
 import pytest
 import torch
 
-from oracle import gb as ogb
 from paper_2307_03763_gb300 import workloads as wk
 from tests import _data
 from tests._philox import philox4x32_10
