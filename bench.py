@@ -4,12 +4,16 @@
 One step = one 10,000-proposal posterior round on each of 16 frequency
 windows (N = 128 / 256 bins, T = 2 yr, one injected binary per window at SNR
 20-200, proposals from a Gaussian of 10x the Fisher width around it): the
-batched log-likelihood of all 160,000 proposals (one launch) followed by the
-16 independence Metropolis-Hastings chains built from them (one launch).
+mixed-precision log-likelihood of all 160,000 proposals (one persistent
+launch), the 16 independence Metropolis-Hastings chains built from them, and
+the certification that makes those chains the FP64 path's: the proposals whose
+accept/reject decision the mixed error bound cannot settle are re-evaluated in
+FP64 (gb_mh_certified).
 
-Metric: GB logL evaluations per second (higher is better), for the mixed
-precision path (headline) and the plain FP64 path, with |dlogL| of the mixed
-path against FP64 stated, and seconds per 10k-sample posterior round.
+Metric: GB logL evaluations per second (higher is better) of the certified
+round (headline), of the same round without certification and of the plain
+FP64 path, with |dlogL| of the mixed path against FP64 stated per SNR band, and
+seconds per 10k-sample posterior round.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --workload tiny|band|population|fullband   (the other
@@ -42,6 +46,7 @@ METRIC = "GB logL evals/s (FP64 vs mixed, |dlogL| stated); s per 10k-sample post
 UNIT = "evals/s"
 WORKLOAD = "posterior: 16 windows (N=128/256, f0 log-U[0.5,5] mHz), 10,000 proposals each, T=2 yr, dt=15 s"
 L2_BYTES = 129 * 1024 * 1024
+MAX_ITER = 2          # re-evaluation passes of the certified rounds
 
 
 # ---------------------------------------------------------------------------
@@ -199,54 +204,133 @@ def flops_per_grad(N, f_hz, T):
     return forward + 2 * 5 * N * math.log2(N) + N * (508 + 48 * J + 555)
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the likelihood kernel from the committed ncu
-    summary, or None when the kernel source changed since that capture."""
+def kernel_source_sha256():
+    """SHA-256 of the likelihood kernel's code: mixed_common.cuh and mixed.cu up
+    to its allocation-free section, without // comments and blank lines."""
     import hashlib
-    import re
-    try:
-        prof = open(os.path.join(ROOT, "profiles", "loglik_mixed_posterior.md")).read()
-        csrc = os.path.join(ROOT, "paper_2307_03763_gb300", "csrc")
-        common = open(os.path.join(csrc, "mixed_common.cuh")).read()
-        src = open(os.path.join(csrc, "mixed.cu")).read()
-    except OSError:
-        return None
-    # the kernel's source: the shared header and mixed.cu up to its allocation-free section
+    csrc = os.path.join(ROOT, "paper_2307_03763_gb300", "csrc")
+    common = open(os.path.join(csrc, "mixed_common.cuh")).read()
+    src = open(os.path.join(csrc, "mixed.cu")).read()
     region = common + src.split("// ---------------------------------------------------------------------------\n"
                                 "// Allocation-free variant")[0]
-    # code only: // comments and blank space do not change the kernel
     region = "\n".join(ln.split("//")[0].rstrip() for ln in region.splitlines())
     region = "\n".join(ln for ln in region.splitlines() if ln.strip())
-    sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", prof)
-    nbytes = re.search(r"traffic_bytes_per_launch:\s*(\d+)", prof)
-    if not sha or not nbytes or sha.group(1) != hashlib.sha256(region.encode()).hexdigest():
+    return hashlib.sha256(region.encode()).hexdigest()
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the likelihood kernel from the committed ncu
+    counters (profiles/loglik_mixed_posterior.json), or None when the kernel's
+    code changed since that capture."""
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", "loglik_mixed_posterior.json")))
+    except (OSError, ValueError):
         return None
-    return int(nbytes.group(1))
+    if prof.get("source_sha256") != kernel_source_sha256():
+        return None
+    return int(prof["traffic_bytes_per_launch"])
+
+
+def flops_per_eval_fp64(N, f_hz, T):
+    """Floating-point operations of one evaluation of the FP64 path (FMA = 2,
+    a sincos or sincospi counted as 20), counted from the algorithm as the
+    FP64 kernel states it.  Per sample: three receiver phases (projection 6,
+    phase in cycles 18, reduction and sincospi 22) 138; f and a 4; three arms
+    (k.n 5, n.H.n 19, two links of 20 + 4 J each: argument, series in
+    -4X^2, complex scaling and two complex products) 3 x (64 + 8 J); the delay
+    factor by its short series and D^2, 27; X, Y, Z with (1 - D^2) 72; the A/E
+    projection 12; so 445 + 24 J with J = 6, 8, 12, 16 by f/f* <= 0.22, 0.5,
+    1.3, 2.35.  FFT 2 x 5 N log2 N; window inner products 32 per bin.
+    """
+    x = f_hz / (299792458.0 / (2 * math.pi * 2.5e9))
+    J = 6 if x <= 0.22 else 8 if x <= 0.5 else 12 if x <= 1.3 else 16
+    return N * (445 + 24 * J) + 2 * 5 * N * math.log2(N) + 32 * N
+
+
+def fp64_peak_tflops(clock_mhz=2070.0):
+    """FP64 peak from unit counts: 152 SMs x 2 FP64 FMA lanes x 2 flops x clock.
+    Two lanes per SM (1/64 of the 128 FP32 lanes) is what GB300's nominal
+    1.25 TFLOP/s dense FP64 implies at 2.07 GHz."""
+    return 152 * 2 * 2 * clock_mhz * 1e6 / 1e12
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
 
 
 # ---------------------------------------------------------------------------
 
+def window_mix(wl):
+    """One window of each template size N in the step, with the share of the
+    step's evaluations that windows of that N hold."""
+    total = sum(w[5] for w in wl.windows)
+    mix = {}
+    for w in wl.windows:
+        if w[2] not in mix:
+            mix[w[2]] = [w, 0]
+        mix[w[2]][1] += w[5]
+    return [(w, cnt / total) for w, cnt in mix.values()]
+
+
+def cpu_rate(fn, wl, dA, dE, theta, seconds, n=1000):
+    """Evaluations per second of fn (the oracle's loglik or its FFT variant)
+    over the step's window mix: each distinct N timed on n proposals of one of
+    its windows for about seconds / (number of N), combined by the step's
+    shares (time per evaluation weighted by share)."""
+    mix = window_mix(wl)
+    t_per = 0.0
+    for (k0, W, N, doff, coff, nc), share in mix:
+        m = min(n, nc)
+        win = [(k0, W, N, doff, 0, m)]
+        th = theta[coff:coff + m]
+        fn(win, dA, dE, wl.w_A, wl.w_E, th, wl.T)            # warm
+        t0 = time.perf_counter()
+        done = 0
+        while True:
+            fn(win, dA, dE, wl.w_A, wl.w_E, th, wl.T)
+            done += m
+            if time.perf_counter() - t0 > seconds / len(mix):
+                break
+        t_per += share * (time.perf_counter() - t0) / done
+    return 1.0 / t_per, mix
+
+
 def cpu_baseline(wl, dA, dE, theta, seconds=12.0):
-    """The FP64 oracle timed on this host's cores on a bounded sample."""
+    """The FP64 oracle as it stands (naive DFT), and the same with a radix-2
+    FFT, timed on this host's cores on a bounded sample of the step's window mix."""
+    from oracle import cpu_fft
     from oracle import gb as ogb
-    k0, W, N, doff, coff, nc = wl.windows[0]
-    n = 2000
-    win = [(k0, W, N, doff, 0, n)]
-    th = theta[coff:coff + n]
-    t0 = time.perf_counter()
-    done = 0
-    while True:
-        ogb.loglik(win, dA, dE, wl.w_A, wl.w_E, th, wl.T)
-        done += n
-        if time.perf_counter() - t0 > seconds:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
-            "sample": "window 0 (N=%d) of the posterior workload, %d proposals, repeated for %.0f s" % (N, n, dt)}
+    rate, mix = cpu_rate(ogb.loglik, wl, dA, dE, theta, seconds)
+    rate_fft, _ = cpu_rate(cpu_fft.loglik_fft, wl, dA, dE, theta, seconds)
+    sample = ("1,000 proposals of one window of each N in the step (%s), each timed for ~%.0f s, "
+              "weighted by the step's evaluations per N" %
+              (", ".join("N=%d: %.0f%%" % (w[2], 100 * sh) for w, sh in mix), seconds / len(mix)))
+    host = {"cores": torch.get_num_threads(), "cpu_count": os.cpu_count(), "cpu_model": cpu_model()}
+    base = {"value": rate, "unit": UNIT, "kind": "oracle", "dft": "naive O(N^2)", "sample": sample, **host}
+    fft = {"value": rate_fft, "unit": UNIT, "kind": "oracle steps with a radix-2 FFT (oracle/cpu_fft.py)",
+           "dft": "radix-2 FFT", "sample": sample, **host}
+    return base, fft
 
 
 def run_reference(args, rank, world):
-    """The oracle as it stands (CPU) on the same workload and metric."""
+    """The oracle as it stands (CPU) on the same workload and metric: per step,
+    1,000 proposals of one window of each N in the step (likelihood and chain),
+    combined by the step's evaluations per N."""
     if rank != 0:
         return
     from oracle import gb as ogb
@@ -272,33 +356,40 @@ def run_reference(args, rank, world):
         a, e = on_window(s, w)
         dA[doff:doff + W] += a
         dE[doff:doff + W] += e
-        srcs.append([s])
-    k0, W, N, doff, coff, nc = wl.windows[0]
+        srcs.append(s)
     n = 1000
     rng = np.random.default_rng(1)
-    sig = np.array([0.3 / wl.T, 1e-19, 0.05, 0.05, 0.1 * srcs[0][0][4], 0.05, 0.05, 0.05])
-    th, lg = wk.gaussian_proposals(srcs[0][0], sig, n, rng)
-    lu = wk.log_uniforms(n, rng)
-    win = [(k0, W, N, doff, 0, n)]
+    parts = []
+    for (k0, W, N, doff, coff, nc), share in window_mix(wl):
+        w = [x[0] for x in wl.windows].index(k0)
+        sig = np.array([0.3 / wl.T, 1e-19, 0.05, 0.05, 0.1 * srcs[w][4], 0.05, 0.05, 0.05])
+        th, lg = wk.gaussian_proposals(srcs[w], sig, n, rng)
+        parts.append(([(k0, W, N, doff, 0, n)], th, lg, wk.log_uniforms(n, rng), share))
 
-    def step():
+    def part(p):
+        win, th, lg, lu, _ = p
         l, _, _ = ogb.loglik(win, dA, dE, wl.w_A, wl.w_E, th, wl.T)
         omh.mh_independence(l.numpy(), lg, lu, 1.0)
 
     for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    dt = time.perf_counter() - t0
-    value = n * args.steps / dt
-    sample = "window 0 (N=%d) of the posterior workload, %d proposals per step (logL + chain)" % (N, n)
+        for p in parts:
+            part(p)
+    t_per = 0.0
+    for p in parts:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            part(p)
+        t_per += p[4] * (time.perf_counter() - t0) / (args.steps * n)
+    value = 1.0 / t_per
+    sample = ("%d proposals of one window of each N in the step (%s) per step, likelihood and chain, "
+              "weighted by the step's evaluations per N" %
+              (n, ", ".join("N=%d: %.0f%%" % (p[0][0][2], 100 * p[4]) for p in parts)))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": torch.get_num_threads(),
-                             "sample": sample},
+                             "cpu_count": os.cpu_count(), "cpu_model": cpu_model(), "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -501,7 +592,21 @@ def main():
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    # certified rounds: per proposal the mixed logL, <d|h>, <h|h>; per chain the
+    # rows re-evaluated in FP64; one "pending" word per call (0: certified)
+    dh_b = torch.empty_like(logL)
+    hh_b = torch.empty_like(logL)
+    n_slots = max(args.steps, args.warmup, 8) + 1
+    pend = torch.zeros(n_slots, dtype=torch.int32, device=dev)
+    n_exact = torch.zeros((n_slots, nwin), dtype=torch.int32, device=dev)
+
+    def certified(k=0):
+        ctx.mh_certified(wl.windows, dA, dE, wA, wE, theta, log_g, log_u, temp, max_iter=MAX_ITER,
+                         out=(chain, acc, logL, dh_b, hh_b, n_exact[k], pend[k:k + 1]))
+
     def step(prec):
+        if prec == "certified":
+            return certified()
         ctx.loglik(wl.windows, dA, dE, wA, wE, theta, prec=prec, out=(logL, None, None))
         ctx.mh_independence(logL.view(nwin, n), log_g, log_u, temp, out=(chain, acc))
 
@@ -511,20 +616,25 @@ def main():
         torch.cuda.synchronize(dev)
 
     def timed(prec, steps):
-        """Per-step CUDA-event times (ms) of the step and of the likelihood launch alone."""
+        """Per-step CUDA-event times (ms) of the step and, for the plain
+        precisions, of the likelihood launch alone."""
         for _ in range(args.warmup):
             step(prec)
         barrier()
         st, kt = [], []
         n0 = ctx.launch_count()
         torch.cuda.nvtx.range_push(f"timed_{prec}")   # lets a profiler select the timed launches
-        for _ in range(steps):
+        for k in range(steps):
             flush.zero_()                      # L2 flush between timed steps
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             e0.record(stream)
-            ctx.loglik(wl.windows, dA, dE, wA, wE, theta, prec=prec, out=(logL, None, None))
-            e1.record(stream)
-            ctx.mh_independence(logL.view(nwin, n), log_g, log_u, temp, out=(chain, acc))
+            if prec == "certified":
+                certified(k)
+                e1.record(stream)
+            else:
+                ctx.loglik(wl.windows, dA, dE, wA, wE, theta, prec=prec, out=(logL, None, None))
+                e1.record(stream)
+                ctx.mh_independence(logL.view(nwin, n), log_g, log_u, temp, out=(chain, acc))
             e2.record(stream)
             st.append((e0, e1, e2))
         torch.cuda.nvtx.range_pop()
@@ -544,23 +654,41 @@ def main():
     # launch shapes for this batch from the library's autotuner (untimed)
     tuning = {p: ctx.autotune(wl.windows, dA, dE, wA, wE, theta, prec=p, reps=3) for p in ("mixed", "fp64")}
 
-    # accuracy of the mixed path against the FP64 path on this workload
-    l64 = torch.empty_like(logL)
-    ctx.loglik(wl.windows, dA, dE, wA, wE, theta, prec="fp64", out=(l64, None, None))
+    # accuracy of the mixed path against the FP64 path on this workload, and
+    # the certified chains against the chains of the FP64 path (untimed)
+    l64, dh64, hh64 = (torch.empty_like(logL) for _ in range(3))
+    ctx.loglik(wl.windows, dA, dE, wA, wE, theta, prec="fp64", out=(l64, dh64, hh64))
     lmx = torch.empty_like(logL)
     ctx.loglik(wl.windows, dA, dE, wA, wE, theta, prec="mixed", out=(lmx, None, None))
+    ch64, acc64 = ctx.mh_independence(l64.view(nwin, n), log_g, log_u, temp)
+    certified()
+    torch.cuda.synchronize(dev)
+    chains_equal = bool(torch.equal(chain, ch64)) and bool(torch.equal(acc, acc64)) and int(pend[0]) == 0
+    redo = logL != lmx
+    rows_equal = bool(torch.equal(logL[redo], l64[redo]))
     dl = (lmx - l64).abs()
+    snr = hh64.clamp(min=0).sqrt()
+    by_snr = {}
+    for lo, hi in [(0, 20), (20, 50), (50, 100), (100, 200), (200, None)]:
+        m = (snr >= lo) if hi is None else (snr >= lo) & (snr < hi)
+        if bool(m.any()):
+            by_snr["%d-%s" % (lo, hi if hi else "")] = {
+                "proposals": int(m.sum()), "max_abs_dlogL": float(dl[m].max()),
+                "p99_abs_dlogL": float(dl[m].quantile(0.99)), "median_abs_dlogL": float(dl[m].median())}
     ctx.check()
 
-    # clocks sampled over both timed regions (each alone can be shorter than
+    # clocks sampled over the timed regions (each alone can be shorter than
     # the sampling interval)
     clocks = ClockSampler(dev.index)
     clocks.start()
-    tot_mx, kern_mx, launches_mx = timed("mixed", args.steps)
+    tot_c, _, launches_c = timed("certified", args.steps)
+    pend_max = int(pend[:args.steps].max())
+    exact_rows = n_exact[:args.steps].sum(1).double()
+    tot_mx, kern_mx, _ = timed("mixed", args.steps)
     fp64_steps = args.fp64_steps or max(3, args.steps // 10)
     tot_64, kern_64, _ = timed("fp64", fp64_steps)
     clk = clocks.stop()
-    tot_mx, tot_64 = max_over_ranks(tot_mx), max_over_ranks(tot_64)
+    tot_c, tot_mx, tot_64 = max_over_ranks(tot_c), max_over_ranks(tot_mx), max_over_ranks(tot_64)
 
     # end to end through the public API with host buffers: proposals and their
     # log g, log u (and the window data) copied in from pinned memory each
@@ -574,8 +702,12 @@ def main():
               torch.empty(wl.n_cand, dtype=torch.float64).pin_memory()) for _ in range(2)]
     d_in = [[torch.empty_like(x, device=dev) for x in h_in] for _ in range(2)]
     d_out = [(torch.empty((nwin, n), dtype=torch.int32, device=dev),
+              torch.empty(nwin, dtype=torch.int32, device=dev),
               torch.empty(wl.n_cand, dtype=torch.float64, device=dev),
-              torch.empty(nwin, dtype=torch.int32, device=dev)) for _ in range(2)]
+              torch.empty(wl.n_cand, dtype=torch.float64, device=dev),
+              torch.empty(wl.n_cand, dtype=torch.float64, device=dev),
+              torch.empty(nwin, dtype=torch.int32, device=dev),
+              torch.empty(1, dtype=torch.int32, device=dev)) for _ in range(2)]
     h2d = sum(h.numel() * h.element_size() for h in h_in)
     d2h = h_out[0][0].numel() * 4 + h_out[0][1].numel() * 8
     copy = torch.cuda.Stream(dev)
@@ -596,10 +728,9 @@ def main():
     def e2e_compute(k):
         b = k % 2
         th_d, lg_d, lu_d, dA_d, dE_d, wA_d, wE_d = d_in[b]
-        ch_d, ll_d, ac_d = d_out[b]
         stream.wait_event(ev_in[b])
-        ctx.loglik(wl.windows, dA_d, dE_d, wA_d, wE_d, th_d, prec="mixed", out=(ll_d, None, None))
-        ctx.mh_independence(ll_d.view(nwin, n), lg_d, lu_d, temp, out=(ch_d, ac_d))
+        ctx.mh_certified(wl.windows, dA_d, dE_d, wA_d, wE_d, th_d, lg_d, lu_d, temp, max_iter=MAX_ITER,
+                         out=d_out[b])
         ev_comp[b].record(stream)
 
     def e2e_d2h(k):
@@ -607,7 +738,7 @@ def main():
         with torch.cuda.stream(copy):
             copy.wait_event(ev_comp[b])
             h_out[b][0].copy_(d_out[b][0], non_blocking=True)
-            h_out[b][1].copy_(d_out[b][1], non_blocking=True)
+            h_out[b][1].copy_(d_out[b][2], non_blocking=True)
             ev_free[b].record(copy)
 
     def e2e_run(steps):
@@ -626,8 +757,8 @@ def main():
     e1.record(copy)
     barrier()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1))
-    # the outputs of the last step equal a device-resident step's (untimed)
-    step("mixed")
+    # the outputs of the last step equal a device-resident certified step's (untimed)
+    certified()
     torch.cuda.synchronize(dev)
     assert torch.equal(h_out[(args.steps - 1) % 2][0], chain.cpu())
     assert torch.equal(h_out[(args.steps - 1) % 2][1], logL.cpu())
@@ -635,13 +766,16 @@ def main():
     if rank != 0:
         return
     evals = wl.n_cand * world
-    value = evals * args.steps / (tot_mx / 1e3)
+    value = evals * args.steps / (tot_c / 1e3)
+    value_mx = evals * args.steps / (tot_mx / 1e3)
     value64 = evals * fp64_steps / (tot_64 / 1e3)
-    ms_step = tot_mx / args.steps
+    ms_step = tot_c / args.steps
     f_mid = np.array([w[0] + w[1] / 2 for w in wl.windows]) / wl.T
     flops = sum(n * flops_per_eval(w[2], f, wl.T) for w, f in zip(wl.windows, f_mid))
+    flops64 = sum(n * flops_per_eval_fp64(w[2], f, wl.T) for w, f in zip(wl.windows, f_mid))
     fp32_peak = 152 * 128 * 2 * 2070e6 / 1e12
     achieved = flops / (kern_mx / 1e3) / 1e12
+    achieved64 = flops64 / (kern_64 / 1e3) / 1e12
     # Alg. 4 with its temperature ladder (15, 10, 5, 3, 2, 1): six rounds of
     # 10,000 device-drawn proposals per window, Gaussian refits between rounds
     from paper_2307_03763_gb300.posterior import AnnealedPosterior
@@ -693,36 +827,52 @@ def main():
                                 "A-iota; %d x %d cells) of each temperature's chain" % (kp.grid, kp.grid),
                     "graph": "the six rounds and five KDE builds replayed from one CUDA graph"}
 
-    traffic = profiled_traffic()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64-phase", "data": "synthetic",
         "config": {"workload": WORKLOAD, "global_batch": evals, "windows": nwin, "proposals_per_window": n,
-                   "l2": "flushed between timed steps (2x L2 buffer written)", "parallelism": "replicas"},
+                   "l2": "flushed between timed steps (2x L2 buffer written)", "parallelism": "replicas",
+                   "step": "gb_mh_certified: mixed-precision logL of every proposal, the chains, FP64 "
+                           "re-evaluation of the proposals whose decision the mixed error bound cannot settle"},
         "s_per_10k_posterior": ms_step / 1e3 / nwin,
+        "certified": {"chains_equal_fp64_chains": chains_equal, "reevaluated_rows_equal_fp64": rows_equal,
+                      "eps": api.MIXED_EPS, "max_iter": MAX_ITER, "pending_max_over_steps": pend_max,
+                      "rows_reevaluated_per_step": float(exact_rows.mean()),
+                      "reevaluated_fraction": float(exact_rows.mean()) / evals,
+                      "added_ms_per_step": ms_step - tot_mx / args.steps},
+        "mixed_uncertified": {"value": value_mx, "unit": UNIT, "ms_per_step": tot_mx / args.steps,
+                              "loglik_ms": kern_mx, "mh_ms": tot_mx / args.steps - kern_mx,
+                              "s_per_10k_posterior": tot_mx / args.steps / 1e3 / nwin},
         "annealed_posterior_6T": annealed,
         "annealed_posterior_6T_kde": annealed_kde,
         "fp64": {"value": value64, "unit": UNIT, "steps": fp64_steps, "ms_per_step": tot_64 / fp64_steps,
-                 "s_per_10k_posterior": tot_64 / fp64_steps / 1e3 / nwin, "loglik_ms": kern_64},
+                 "s_per_10k_posterior": tot_64 / fp64_steps / 1e3 / nwin, "loglik_ms": kern_64,
+                 "roofline": {"bound": "alu", "achieved": achieved64, "peak": fp64_peak_tflops(),
+                              "unit": "TFLOP/s", "frac": achieved64 / fp64_peak_tflops(), "traffic": None,
+                              "kernel": "loglik64_kernel",
+                              "peak_note": "FP64 peak from unit counts: 152 SM x 2 FP64 FMA lanes x 2 x 2070 MHz "
+                                           "(the nominal 1.25 TFLOP/s dense FP64)"}},
         "mixed_vs_fp64": {"max_abs_dlogL": float(dl.max()), "p99_abs_dlogL": float(dl.quantile(0.99)),
-                          "median_abs_dlogL": float(dl.median()), "snr_range": [20, 200]},
-        "loglik_ms": kern_mx, "mh_ms": ms_step - kern_mx,
+                          "median_abs_dlogL": float(dl.median()), "snr_range": [20, 200],
+                          "by_proposal_snr": by_snr},
+        "loglik_ms": kern_mx,
         "autotune": tuning,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": traffic,
+                     "frac": achieved / fp32_peak, "traffic": profiled_traffic(),
                      "kernel": "loglik_mixed_kernel",
-                     "peak_note": "FP32 FMA peak from unit counts: 152 SM x 128 lanes x 2 x 2070 MHz"},
+                     "peak_note": "FP32 FMA peak from unit counts: 152 SM x 128 lanes x 2 x 2070 MHz; achieved "
+                                  "from the likelihood launch of the uncertified steps (the same kernel)"},
         "e2e": {"value": evals * args.steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "clocks": clk,
-        # library kernels launched in the timed mixed-precision steps, counted
-        # by the context (window preparation, persistent likelihood kernel,
-        # chain summary and chain write per step on this workload)
-        "gpu_launches": launches_mx,
+        # library kernels launched in the timed certified steps, counted by the
+        # context (window preparation, likelihood, chains, bounds,
+        # certification passes, FP64 re-evaluation and flip checks)
+        "gpu_launches": launches_c,
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, dA_h, dE_h, th_h)
+        line["cpu_baseline"], line["cpu_baseline_fft"] = cpu_baseline(wl, dA_h, dE_h, th_h)
     print(json.dumps(line), flush=True)
 
 

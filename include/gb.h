@@ -239,6 +239,73 @@ int gb_mh_independence(gb_ctx_t* ctx, int32_t n_chains, int32_t n,
                        const double* temperature, int32_t literal,
                        int32_t* chain_idx, int32_t* n_accept, void* stream);
 
+/* FP64 log-likelihood of listed rows (Eq. 2 over each window, as gb_loglik
+ * with GB_FP64).  Window w's entries are the rows rows[cand_off + j] for j in
+ * [row_lo[w], row_hi[w]) (clamped to [0, n_cand)); an entry outside the
+ * window's rows [cand_off, cand_off + n_cand) is skipped.  Those rows of logL,
+ * dh and hh (dh, hh may be NULL) are written with exactly the bits gb_loglik
+ * (GB_FP64) gives them; every other row is left as it is.  The list lengths
+ * live on the device, so a caller can enqueue this call behind a kernel that
+ * fills the lists, without a host round trip (this is how gb_mh_certified
+ * re-evaluates the proposals it cannot settle; the paper has no counterpart).
+ *   rows    n_rows int32 (device), window w's entries from rows + cand_off
+ *   row_lo, row_hi   n_win int32 each (device)
+ * Windows, data and theta as gb_loglik; n_rows < 2^31. */
+int gb_loglik_rows(gb_ctx_t* ctx, const gb_window_t* win, int32_t n_win,
+                   const double* dA, const double* dE, const double* wA, const double* wE,
+                   int64_t n_bins, const double* theta, int64_t n_rows,
+                   const int32_t* rows, const int32_t* row_lo, const int32_t* row_hi,
+                   double* logL, double* dh, double* hh, void* stream);
+
+/* One posterior round of Alg. 4 (Sec. III.G, Eq. 13): the log-likelihood of
+ * every proposal in mixed precision and independence MH chains equal, step for
+ * step, to the chains built from GB_FP64 log-likelihoods (gb_loglik with
+ * GB_FP64, then gb_mh_independence).
+ *
+ * Window w holds one chain: its proposals are rows [w n, (w + 1) n) of theta,
+ * log_g, log_u and the outputs (n = n_cand, the same for every window,
+ * cand_off = w n).  log_g, log_u, temperature, literal: as gb_mh_independence.
+ *
+ * Method.  With the mixed template h~ = h + dh, logL~ - logL =
+ * <d - h|dh> - <dh|dh>/2 plus the float rounding of the data, weights and
+ * sums, so a mixed value differs from the FP64 one by at most
+ *     e = eps |h| |d - h| + eps^2 |h|^2/2 + 1e-6 |h| (|d| + |h|)
+ * (plus 1e-12 of the magnitudes) when the template's error is at most
+ * eps |h| in the window's weighted norm (Cauchy-Schwarz; |d|^2 = <d|d>,
+ * |h|^2 = <h|h>, |d - h| <= (-2 logL~)^1/2 + eps |h|, all from the outputs).
+ * The chain is built from the mixed values; a step whose decision
+ * log u_i < Delta could change within the bounds of proposal i and of the state
+ * before it has those two rows re-evaluated in FP64 (gb_loglik_rows, bit for
+ * bit gb_loglik's) and is decided again from the exact values.  Every other
+ * step was settled within bounds that hold, so unless one of those decisions
+ * differs from the chain's, the chain is the FP64 one; if one does, the chain
+ * is built again and certified anew, up to max_iter times.
+ *
+ *   eps        bound on the mixed template's relative error, in (0, 1e-2).
+ *              Over every row of the posterior (160,000), population
+ *              (262,144) and band (5.6 million; N = 32 ... 1024, 0.3 - 20 mHz,
+ *              SNR up to 2,000) workloads the measured |logL_mixed -
+ *              logL_fp64| is at most 0.134 of e at the binding's default
+ *              eps = 1e-5 (a factor of 7.4; 29 on the band and population
+ *              workloads).
+ *   max_iter   re-evaluation passes, in [1, 64] (2 suffice in practice)
+ *   logL       n_win n (device, written): mixed values, FP64 on re-evaluated rows
+ *   dh, hh     n_win n (device, written): the mixed <d|h>, <h|h>
+ *   chain_idx, n_accept   as gb_mh_independence (device, written)
+ *   n_exact    n_win int32 (device, written; may be NULL): rows re-evaluated
+ *   pending    one int32 (device, written): 0 when the chains are certified;
+ *              else the rows the last pass still queued -- call again with a
+ *              larger max_iter
+ * Everything is enqueued on `stream` without a host synchronisation; the
+ * context keeps the flags and queues (allocated on the first call with a
+ * given size).  Errors as gb_loglik. */
+int gb_mh_certified(gb_ctx_t* ctx, const gb_window_t* win, int32_t n_win,
+                    const double* dA, const double* dE, const double* wA, const double* wE,
+                    int64_t n_bins, const double* theta, const double* log_g, const double* log_u,
+                    const double* temperature, int32_t literal, double eps, int32_t max_iter,
+                    double* logL, double* dh, double* hh, int32_t* chain_idx, int32_t* n_accept,
+                    int32_t* n_exact, int32_t* pending, void* stream);
+
 /* Launch shapes chosen by gb_autotune: candidates per work item and resident
  * CTAs per SM of the persistent mixed-precision kernels (0 = built-in
  * heuristic), candidates per CTA tile of the FP64 kernel, and the measured
@@ -430,25 +497,33 @@ int gb_philox4x32(gb_ctx_t* ctx, uint64_t seed, uint32_t n, uint32_t* out, void*
  * Windows, data, candidates and outputs are those of gb_loglik (device
  * pointers, host window array), and so are the results.  All scratch memory
  * (geometry tables and twiddles, window descriptors and work items,
- * per-window values, float copies of the windows, work-queue heads) lives in
- * one static device array of about 8.7 MB, which every GPU that loads the
- * library holds until the process exits.  Limits: n_win <= 4096, the windows'
- * W add up to at most 262144 bins, at most 65536 work items (about two
- * million candidates); beyond them the call returns GB_EINVAL with a message.
+ * per-window values, float copies of the windows, work-queue heads, the
+ * status word) lives in one static device array of about 8.7 MB, which every
+ * GPU that loads the library holds until the process exits.  Limits:
+ * n_win <= 4096, the windows' W add up to at most 262144 bins, at most 65536
+ * work items (about two million candidates); beyond them the call returns
+ * GB_EINVAL with a message.
  *
- * The call runs on the current CUDA device.  Its first call on a device, and
- * any call with a different T_obs or arm_L, also sets the device up: it takes
- * the device address of the static array and builds the tables into it.
- * Make that first call before any stream capture.  Every call shares the one
- * array and leaves its contents behind; what must start at zero is reset by
- * the call itself.  Calls that overlap on the GPU (other streams, other host
- * threads) race on the array: the caller must serialise them.  Non-finite
- * parameters give NaN outputs.  err (may be NULL) receives a message of at
- * most err_len bytes when the call fails. */
+ * The call runs on the current CUDA device.  Each call takes the device
+ * address of the static array (cudaGetSymbolAddress, which allocates
+ * nothing); the first call on a device, a call in a new CUDA context (after a
+ * device reset) and any call with a different T_obs or arm_L also build the
+ * tables into it.  Make that first call before any stream capture.  The call
+ * itself returns GB_EINVAL on a stream that is capturing a graph: it uploads
+ * its work items from host staging that the next call overwrites.  Every call
+ * shares the one array and leaves its contents behind; what must start at
+ * zero (queue heads, status word) is reset by the call itself.  Calls that
+ * overlap on the GPU (other streams, other host threads) race on the array:
+ * the caller must serialise them.
+ *   status   one int32 (device, may be NULL), written when the call's kernels
+ *            finish: 0, or 1 when a candidate had a non-finite parameter
+ *            (its outputs are NaN); every call reports its own candidates only
+ *   err      (may be NULL) receives a message of at most err_len bytes when
+ *            the call fails on the host. */
 int gb_loglik_mixed_noalloc(const gb_obs_t* obs, const gb_window_t* win, int32_t n_win,
                             const double* dA, const double* dE, const double* wA, const double* wE,
                             int64_t n_bins, const double* theta, int64_t n_rows,
-                            double* logL, double* dh, double* hh, void* stream,
+                            double* logL, double* dh, double* hh, int32_t* status, void* stream,
                             char* err, int32_t err_len);
 
 #ifdef __cplusplus

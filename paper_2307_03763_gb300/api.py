@@ -17,6 +17,9 @@ from . import build as _build
 
 GB_OK, GB_EINVAL, GB_ECUDA, GB_ETIMEOUT, GB_ENOMEM = 0, -1, -2, -3, -4
 GB_FP64, GB_MIXED = 0, 1
+# bound on the relative template error of the mixed path, |h_mixed - h_fp64| <= EPS |h| in the
+# window's noise-weighted norm, used by mh_certified (measured maximum and margin in gb.h)
+MIXED_EPS = 1e-5
 PRECISIONS = {"fp64": GB_FP64, "mixed": GB_MIXED, GB_FP64: GB_FP64, GB_MIXED: GB_MIXED}
 
 
@@ -73,8 +76,12 @@ _SIGNATURES = {
     "gb_loglik_grad": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _I64, _P,
                                       _I64, _P, _P, _P]),
     "gb_mh_independence": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, _I32, _P, _P, _P]),
+    "gb_loglik_rows": (ctypes.c_int, [_P, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _I64, _P, _I64, _P, _P, _P,
+                                      _P, _P, _P, _P]),
+    "gb_mh_certified": (ctypes.c_int, [_P, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _I64, _P, _P, _P, _P, _I32,
+                                       ctypes.c_double, _I32, _P, _P, _P, _P, _P, _P, _P, _P]),
     "gb_loglik_mixed_noalloc": (ctypes.c_int, [ctypes.POINTER(Obs), ctypes.POINTER(Window), _I32, _P, _P, _P, _P,
-                                               _I64, _P, _I64, _P, _P, _P, _P, ctypes.c_char_p, _I32]),
+                                               _I64, _P, _I64, _P, _P, _P, _P, _P, ctypes.c_char_p, _I32]),
     "gb_ga_step": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, _P, ctypes.c_uint64, _P, _P,
                                   ctypes.POINTER(GAParams), _P, _P, _P, _P]),
     "gb_gauss_refit": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, ctypes.c_double, ctypes.c_double,
@@ -469,3 +476,52 @@ class Context:
                                              _ptr(temperature), 1 if literal else 0, _ptr(chain), _ptr(acc),
                                              _stream(self.device)))
         return chain, acc
+
+    def loglik_rows(self, windows, dA, dE, wA, wE, theta, rows, row_lo, row_hi, out=None):
+        """FP64 logL, <d|h>, <h|h> of listed rows (see gb_loglik_rows): window w's entries are
+        rows[cand_off + j], j in [row_lo[w], row_hi[w]); the other rows of the outputs are kept."""
+        arr, nw, nb, n = self._data_args(windows, dA, dE, wA, wE, theta)
+        _need(rows, torch.int32, self.device, "rows", (n,))
+        _need(row_lo, torch.int32, self.device, "row_lo", (nw,))
+        _need(row_hi, torch.int32, self.device, "row_hi", (nw,))
+        if out is None:
+            out = tuple(torch.zeros(n, dtype=torch.float64, device=self.device) for _ in range(3))
+        logL, dh, hh = out
+        for t, name in ((logL, "logL"), (dh, "dh"), (hh, "hh")):
+            if t is not None:
+                _need(t, torch.float64, self.device, name, (n,))
+        self._check(lib().gb_loglik_rows(self._h, arr, nw, _ptr(dA), _ptr(dE), _ptr(wA), _ptr(wE), nb, _ptr(theta),
+                                         n, _ptr(rows), _ptr(row_lo), _ptr(row_hi), _ptr(logL), _ptr(dh), _ptr(hh),
+                                         _stream(self.device)))
+        return logL, dh, hh
+
+    def mh_certified(self, windows, dA, dE, wA, wE, theta, log_g, log_u, temperature, literal=False, eps=MIXED_EPS,
+                     max_iter=2, out=None):
+        """Mixed-precision logL of every proposal and the chains an all-FP64 evaluation gives
+        (see gb_mh_certified).  Window w holds rows [w n, (w + 1) n).  Returns
+        (chain, n_accept, logL, dh, hh, n_exact, pending); pending (1,) int32 is 0 when every
+        decision is certified."""
+        arr, nw, nb, nrow = self._data_args(windows, dA, dE, wA, wE, theta)
+        n = nrow // max(nw, 1)
+        for t, name in ((log_g, "log_g"), (log_u, "log_u")):
+            _need(t, torch.float64, self.device, name, (nw, n))
+        _need(temperature, torch.float64, self.device, "temperature", (nw,))
+        if out is None:
+            f = lambda: torch.empty(nrow, dtype=torch.float64, device=self.device)
+            out = (torch.empty((nw, n), dtype=torch.int32, device=self.device),
+                   torch.empty(nw, dtype=torch.int32, device=self.device), f(), f(), f(),
+                   torch.empty(nw, dtype=torch.int32, device=self.device),
+                   torch.empty(1, dtype=torch.int32, device=self.device))
+        chain, acc, logL, dh, hh, n_exact, pending = out
+        _need(chain, torch.int32, self.device, "chain", (nw, n))
+        _need(acc, torch.int32, self.device, "n_accept", (nw,))
+        for t, name in ((logL, "logL"), (dh, "dh"), (hh, "hh")):
+            _need(t, torch.float64, self.device, name, (nrow,))
+        if n_exact is not None:
+            _need(n_exact, torch.int32, self.device, "n_exact", (nw,))
+        _need(pending, torch.int32, self.device, "pending", (1,))
+        self._check(lib().gb_mh_certified(self._h, arr, nw, _ptr(dA), _ptr(dE), _ptr(wA), _ptr(wE), nb, _ptr(theta),
+                                          _ptr(log_g), _ptr(log_u), _ptr(temperature), 1 if literal else 0,
+                                          float(eps), int(max_iter), _ptr(logL), _ptr(dh), _ptr(hh), _ptr(chain),
+                                          _ptr(acc), _ptr(n_exact), _ptr(pending), _stream(self.device)))
+        return chain, acc, logL, dh, hh, n_exact, pending

@@ -1,5 +1,6 @@
 // api.cu -- host entry points: argument checks, launch plans, dispatch by precision.
 #include <algorithm>
+#include <climits>
 #include <string>
 
 #include "gb_internal.cuh"
@@ -247,6 +248,145 @@ int gb_waveform(gb_ctx_t* ctx, int prec, const double* theta, int64_t B, int32_t
     if (e != cudaSuccess) return cuda_error(ctx, e, "gb_waveform: cudaSetDevice");
     if (prec == GB_FP64) return launch_waveform_fp64(ctx, theta, B, N, hA, hE, nullptr, q, (cudaStream_t)stream);
     return launch_waveform_mixed(ctx, theta, B, N, hA, hE, nullptr, q, (cudaStream_t)stream);
+}
+
+int gb_loglik_rows(gb_ctx_t* ctx, const gb_window_t* win, int32_t n_win, const double* dA, const double* dE,
+                   const double* wA, const double* wE, int64_t n_bins, const double* theta, int64_t n_rows,
+                   const int32_t* rows, const int32_t* row_lo, const int32_t* row_hi, double* logL, double* dh,
+                   double* hh, void* stream) {
+    if (!ctx) return GB_EINVAL;
+    int64_t total = 0;
+    int rc = check_windows(ctx, "gb_loglik_rows", win, n_win, n_bins, n_rows, &total);
+    if (rc != GB_OK) return rc;
+    if (total == 0) return GB_OK;
+    if (n_rows > (int64_t)INT32_MAX) return set_error(ctx, GB_EINVAL, "gb_loglik_rows: more than 2^31 - 1 rows");
+    if (!dA || !dE || !wA || !wE || !theta || !rows || !row_lo || !row_hi || !logL)
+        return set_error(ctx, GB_EINVAL, "gb_loglik_rows: null pointer");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_loglik_rows: cudaSetDevice");
+    const Plan* plan = nullptr;
+    rc = get_plan(ctx, GB_FP64, win, n_win, tile_size(ctx, total, 4), &plan);
+    if (rc != GB_OK) return rc;
+    int nc_max = 0;
+    for (int i = 0; i < n_win; ++i) nc_max = std::max(nc_max, win[i].n_cand);
+    // CTAs per window: enough for every listed row of the largest window to
+    // get its own warp, at most about two waves of the GPU in all
+    const int ctas = (int)std::max<int64_t>(
+        1, std::min<int64_t>((nc_max + 127) / 128, (2 * (int64_t)sm_count(ctx) + n_win - 1) / n_win));
+    return launch_loglik_rows64(ctx, plan->d_win, n_win, plan->n_max, ctas, dA, dE, wA, wE, theta, rows, row_lo,
+                                row_hi, logL, dh, hh, nullptr, (cudaStream_t)stream);
+}
+
+int gb_mh_certified(gb_ctx_t* ctx, const gb_window_t* win, int32_t n_win, const double* dA, const double* dE,
+                    const double* wA, const double* wE, int64_t n_bins, const double* theta, const double* log_g,
+                    const double* log_u, const double* temperature, int32_t literal, double eps, int32_t max_iter,
+                    double* logL, double* dh, double* hh, int32_t* chain_idx, int32_t* n_accept, int32_t* n_exact,
+                    int32_t* pending, void* stream) {
+    if (!ctx) return GB_EINVAL;
+    if (n_win < 0) return set_error(ctx, GB_EINVAL, "gb_mh_certified: n_win < 0");
+    if (n_win == 0) return GB_OK;
+    if (!win) return set_error(ctx, GB_EINVAL, "gb_mh_certified: null window array");
+    const int32_t n = win[0].n_cand;
+    for (int i = 0; i < n_win; ++i)
+        if (win[i].n_cand != n || win[i].cand_off != (int64_t)i * n)
+            return set_error(ctx, GB_EINVAL, "gb_mh_certified: window w must hold rows [w n, (w + 1) n) (one chain "
+                                             "of n proposals per window)");
+    const int64_t n_rows = (int64_t)n_win * n;
+    if (n_rows > (int64_t)INT32_MAX) return set_error(ctx, GB_EINVAL, "gb_mh_certified: more than 2^31 - 1 rows");
+    int64_t total = 0;
+    int rc = check_windows(ctx, "gb_mh_certified", win, n_win, n_bins, n_rows, &total);
+    if (rc != GB_OK) return rc;
+    if (n == 0) return GB_OK;
+    if (!(eps > 0.0) || !(eps < 1e-2)) return set_error(ctx, GB_EINVAL, "gb_mh_certified: eps must be in (0, 1e-2)");
+    if (max_iter < 1 || max_iter > 64) return set_error(ctx, GB_EINVAL, "gb_mh_certified: max_iter must be in [1, 64]");
+    if (literal != 0 && literal != 1) return set_error(ctx, GB_EINVAL, "gb_mh_certified: literal must be 0 or 1");
+    if (!dA || !dE || !wA || !wE || !theta || !log_g || !log_u || !temperature || !logL || !dh || !hh ||
+        !chain_idx || !n_accept || !pending)
+        return set_error(ctx, GB_EINVAL, "gb_mh_certified: null pointer");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_mh_certified: cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    // scratch (CertScratch): per row the bound, queue and step entries, then
+    // per chain the queue range, then the counters that start at zero each
+    // call: per row the mark, per pass and chain the rows, steps and finished
+    // CTAs, per pass the rows and flips
+    const size_t a = 256;
+    auto up = [a](size_t x) { return (x + a - 1) / a * a; };
+    const size_t passes = (size_t)max_iter + 1, R = (size_t)n_rows, Wn = (size_t)n_win;
+    const size_t off_q = up(sizeof(float) * R);
+    const size_t off_s = off_q + up(sizeof(int32_t) * R);
+    const size_t off_lo = off_s + up(sizeof(int32_t) * R);
+    const size_t off_hi = off_lo + up(sizeof(int32_t) * Wn);
+    const size_t off_zero = off_hi + up(sizeof(int32_t) * Wn);
+    const size_t zero_bytes = sizeof(int32_t) * (R + 3 * passes * Wn + 2 * passes);
+    const size_t bytes = off_zero + up(zero_bytes);
+    if (bytes > ctx->cert_bytes) {
+        if (ctx->d_cert) cudaFree(ctx->d_cert);
+        ctx->d_cert = nullptr;
+        ctx->cert_bytes = 0;
+        e = cudaMalloc(&ctx->d_cert, bytes);
+        if (e != cudaSuccess)
+            return e == cudaErrorMemoryAllocation ? set_error(ctx, GB_ENOMEM, "gb_mh_certified: scratch")
+                                                  : cuda_error(ctx, e, "gb_mh_certified: scratch");
+        ctx->cert_bytes = bytes;
+    }
+    unsigned char* b = (unsigned char*)ctx->d_cert;
+    CertScratch cs;
+    cs.err = (float*)b;
+    cs.queue = (int32_t*)(b + off_q);
+    cs.steps = (int32_t*)(b + off_s);
+    cs.q_lo = (int32_t*)(b + off_lo);
+    cs.q_hi = (int32_t*)(b + off_hi);
+    cs.mark = (int32_t*)(b + off_zero);
+    cs.cnt = cs.mark + R;
+    cs.scnt = cs.cnt + passes * Wn;
+    cs.done = cs.scnt + passes * Wn;
+    cs.n_new = cs.done + passes * Wn;
+    cs.n_flip = cs.n_new + passes;
+    // the FP64 plan of this layout holds the device copy of the windows
+    const Plan* plan64 = nullptr;
+    rc = get_plan(ctx, GB_FP64, win, n_win, tile_size(ctx, total, 4), &plan64);
+    if (rc != GB_OK) return rc;
+    const gb_window_t* d_win = plan64->d_win;
+    const int n_max = plan64->n_max;
+    // every proposal in mixed precision, with <d|h>, <h|h> for the bounds
+    rc = loglik_impl(ctx, "gb_mh_certified", GB_MIXED, win, n_win, dA, dE, wA, wE, n_bins, theta, n_rows, logL, dh,
+                     nullptr, hh, stream);
+    if (rc != GB_OK) return rc;
+    e = cudaMemsetAsync(cs.mark, 0, zero_bytes, s);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_mh_certified: reset");
+    const int ctas = (int)std::max<int64_t>(
+        1, std::min<int64_t>(((int64_t)n + 127) / 128, (2 * (int64_t)sm_count(ctx) + n_win - 1) / n_win));
+    // pass 0 on the mixed values; then per iteration: the rows the last pass
+    // queued in FP64 (over their mixed values), the flips of its unsettled
+    // steps, and only when one flipped the chains and a pass again
+    rc = launch_mh(ctx, n_win, n, logL, log_g, log_u, temperature, literal, chain_idx, n_accept, nullptr, s);
+    if (rc == GB_OK)
+        rc = launch_mh_certify(ctx, cs, n_win, n, logL, dh, hh, log_g, log_u, temperature, literal, eps, chain_idx, 0,
+                               nullptr, s);
+    for (int it = 1; it <= max_iter && rc == GB_OK; ++it) {
+        rc = launch_loglik_rows64(ctx, d_win, n_win, n_max, ctas, dA, dE, wA, wE, theta, cs.queue, cs.q_lo, cs.q_hi,
+                                  logL, nullptr, nullptr, cs.n_new + it - 1, s);
+        if (rc == GB_OK)
+            rc = launch_mh_flip(ctx, cs, n_win, n, logL, log_g, log_u, temperature, literal, chain_idx, it - 1, s);
+        if (rc == GB_OK)
+            rc = launch_mh(ctx, n_win, n, logL, log_g, log_u, temperature, literal, chain_idx, n_accept,
+                           cs.n_flip + it - 1, s);
+        if (rc == GB_OK)
+            rc = launch_mh_certify(ctx, cs, n_win, n, logL, dh, hh, log_g, log_u, temperature, literal, eps,
+                                   chain_idx, it, cs.n_flip + it - 1, s);
+    }
+    if (rc != GB_OK) return rc;
+    int* n_new = cs.n_new;
+    int* cnt = cs.cnt;
+    e = cudaMemcpyAsync(pending, n_new + max_iter, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && n_exact) {
+        // rows re-evaluated per chain: the queues of the passes before the last
+        rc = launch_sum_rows(ctx, cnt, n_win, max_iter, n_exact, s);
+        if (rc != GB_OK) return rc;
+    }
+    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_mh_certified: outputs");
+    return GB_OK;
 }
 
 }  // extern "C"

@@ -365,6 +365,7 @@ int gb_ctx_destroy(gb_ctx_t* ctx) {
     if (ctx->d_tw32) cudaFree(ctx->d_tw32);
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->d_mh) cudaFree(ctx->d_mh);
+    if (ctx->d_cert) cudaFree(ctx->d_cert);
     delete ctx;
     return GB_OK;
 }

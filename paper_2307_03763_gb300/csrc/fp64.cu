@@ -149,13 +149,23 @@ __device__ __forceinline__ C64 link64(double a, double X, C64 G, C64 rx) {
 // phases reach ~1e6 rad; taken in cycles and reduced modulo one first, their
 // sines come from a short argument.
 // bufT (may be null): also T = (X + Y + Z)/sqrt3
-template <int J>
+// NT threads share the candidate (NT = 32: one warp, `lane` its lane; NT > 32:
+// the whole CTA, `lane` the thread index); each sample and each butterfly is
+// computed by the same code whichever thread takes it, so the bits do not
+// depend on NT.
+template <int NT>
+__device__ __forceinline__ void sync_nt() {
+    if (NT == 32) __syncwarp();
+    else __syncthreads();
+}
+
+template <int J, int NT>
 __device__ void template64(const Cand64& c, const Geo64& g, const OrbitTables64& tab, const C64* tw,
                            C64* bufA, C64* bufE, C64* bufT, int lane) {
     const int N = g.N;
     const double inv_c = 1.0 / kC;
     const double u_step = 1.0 / (double)N;   // t/T = n/N exactly
-    for (int n = lane; n < N; n += 32) {
+    for (int n = lane; n < N; n += NT) {
         const double t = (double)n * g.T_over_N;
         C64 rx[3];
         for (int j = 0; j < 3; ++j) {
@@ -223,12 +233,12 @@ __device__ void template64(const Cand64& c, const Geo64& g, const OrbitTables64&
             bufT[br] = {(X.x + Y.x + Z.x) * r3, (X.y + Y.y + Z.y) * r3};
         }
     }
-    __syncwarp();
+    sync_nt<NT>();
     // radix-2 decimation in time, bit-reversed input, natural-order output
     for (int s = 0; s < g.logN; ++s) {
         const int h = 1 << s;
         const int tstride = kTwiddles >> s;
-        for (int b = lane; b < N / 2; b += 32) {
+        for (int b = lane; b < N / 2; b += NT) {
             const int j = b & (h - 1);
             const int i0 = ((b >> s) << (s + 1)) + j;
             const int i1 = i0 + h;
@@ -245,18 +255,19 @@ __device__ void template64(const Cand64& c, const Geo64& g, const OrbitTables64&
                 bufT[i1] = csub(ut, vt);
             }
         }
-        __syncwarp();
+        sync_nt<NT>();
     }
 }
 
+template <int NT = 32>
 __device__ void template64_dispatch(const Cand64& c, const Geo64& g, const OrbitTables64& tab, const C64* tw,
                                     C64* bufA, C64* bufE, C64* bufT, int lane) {
     switch (c.J) {
-        case 6: template64<6>(c, g, tab, tw, bufA, bufE, bufT, lane); break;
-        case 8: template64<8>(c, g, tab, tw, bufA, bufE, bufT, lane); break;
-        case 12: template64<12>(c, g, tab, tw, bufA, bufE, bufT, lane); break;
-        case 16: template64<16>(c, g, tab, tw, bufA, bufE, bufT, lane); break;
-        default: template64<0>(c, g, tab, tw, bufA, bufE, bufT, lane); break;
+        case 6: template64<6, NT>(c, g, tab, tw, bufA, bufE, bufT, lane); break;
+        case 8: template64<8, NT>(c, g, tab, tw, bufA, bufE, bufT, lane); break;
+        case 12: template64<12, NT>(c, g, tab, tw, bufA, bufE, bufT, lane); break;
+        case 16: template64<16, NT>(c, g, tab, tw, bufA, bufE, bufT, lane); break;
+        default: template64<0, NT>(c, g, tab, tw, bufA, bufE, bufT, lane); break;
     }
 }
 
@@ -265,28 +276,13 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-__global__ void __launch_bounds__(kWarps64 * 32) loglik64_kernel(
-    const gb_window_t* __restrict__ wins, const Tile* __restrict__ tiles, TabSet64 tabs,
-    const C64* __restrict__ tw_g, double T, double fstar, const C64* __restrict__ dA,
-    const C64* __restrict__ dE, const double* __restrict__ wA, const double* __restrict__ wE,
-    const double* __restrict__ theta, double* __restrict__ logL, double* __restrict__ dh_out,
-    double* __restrict__ hh_out, double* __restrict__ dhi_out, const C64* __restrict__ dT,
-    const double* __restrict__ wT, int* status, int n_max) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C64* tw = (C64*)smem_raw;                                   // kTwiddles
-    double* red = (double*)(tw + kTwiddles);                    // kWarps64
-    Cand64* cands = (Cand64*)(red + kWarps64);                  // kWarps64 * 32
-    C64* bufs = (C64*)(cands + kWarps64 * 32);                  // kWarps64 * (2 or 3) * n_max
-    const int nch = dT ? 3 : 2;
-
+// <d|d> of window `win` over the whole block, in a fixed order (deterministic);
+// every thread returns the same value.  `red` holds kWarps64 doubles.
+__device__ __forceinline__ double window_dd64(const gb_window_t& win, bool useT, const C64* __restrict__ dA,
+                                              const C64* __restrict__ dE, const double* __restrict__ wA,
+                                              const double* __restrict__ wE, const C64* __restrict__ dT,
+                                              const double* __restrict__ wT, double T, double* red) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const Tile tile = tiles[blockIdx.x];
-    const gb_window_t win = wins[tile.win];
-    for (int i = threadIdx.x; i < kTwiddles; i += blockDim.x) tw[i] = tw_g[i];
-
-    // T enters windows whose lowest frequency is at least f*/2
-    const bool useT = dT != nullptr && (double)win.k0 / T >= 0.5 * fstar;
-    // <d|d> over the window, block-wide (fixed order -> deterministic)
     double acc = 0.0;
     for (int i = threadIdx.x; i < win.W; i += blockDim.x) {
         const C64 a = dA[win.data_off + i], e = dE[win.data_off + i];
@@ -301,72 +297,172 @@ __global__ void __launch_bounds__(kWarps64 * 32) loglik64_kernel(
     __syncthreads();
     double dd = 0.0;
     for (int w = 0; w < kWarps64; ++w) dd += red[w];
-    dd *= 4.0 / T;
+    return dd * (4.0 / T);
+}
 
+// Window inner products of one computed template (one warp, in a fixed
+// order) and Eq. 2; lane 0 writes output row `row`.
+__device__ __forceinline__ void ip64(const Cand64& c, int64_t row, const Geo64& g, const C64* bufA, const C64* bufE,
+                                     const C64* bufT, const gb_window_t& win, double dd, const C64* __restrict__ dA,
+                                     const C64* __restrict__ dE, const double* __restrict__ wA,
+                                     const double* __restrict__ wE, const C64* __restrict__ dT,
+                                     const double* __restrict__ wT, double* __restrict__ logL,
+                                     double* __restrict__ dh_out, double* __restrict__ hh_out,
+                                     double* __restrict__ dhi_out, int lane) {
+    const double T = g.T;
+    const int64_t half = win.N / 2;
+    double sdh = 0.0, shh = 0.0, sdhi = 0.0;
+    for (int m = lane; m < win.N; m += 32) {
+        const int64_t kk = c.q - half + m - win.k0;
+        if (kk >= 0 && kk < win.W) {
+            const int idx = (m + (int)half) & (win.N - 1);
+            const C64 hA = cscale(bufA[idx], g.scale), hE = cscale(bufE[idx], g.scale);
+            const C64 a = dA[win.data_off + kk], e = dE[win.data_off + kk];
+            const double wa = wA[win.data_off + kk], we = wE[win.data_off + kk];
+            sdh += wa * (a.x * hA.x + a.y * hA.y) + we * (e.x * hE.x + e.y * hE.y);
+            shh += wa * (hA.x * hA.x + hA.y * hA.y) + we * (hE.x * hE.x + hE.y * hE.y);
+            if (dhi_out) sdhi += wa * (a.y * hA.x - a.x * hA.y) + we * (e.y * hE.x - e.x * hE.y);
+            if (bufT) {
+                const C64 hT = cscale(bufT[idx], g.scale), t = dT[win.data_off + kk];
+                const double wt = wT[win.data_off + kk];
+                sdh += wt * (t.x * hT.x + t.y * hT.y);
+                shh += wt * (hT.x * hT.x + hT.y * hT.y);
+                if (dhi_out) sdhi += wt * (t.y * hT.x - t.x * hT.y);
+            }
+        }
+    }
+    sdh = warp_sum(sdh) * (4.0 / T);
+    shh = warp_sum(shh) * (4.0 / T);
+    if (dhi_out) sdhi = warp_sum(sdhi) * (4.0 / T);
+    if (lane == 0) {
+        logL[row] = sdh - 0.5 * shh - 0.5 * dd;
+        if (dh_out) dh_out[row] = sdh;
+        if (hh_out) hh_out[row] = shh;
+        if (dhi_out) dhi_out[row] = sdhi;
+    }
+}
+
+// NaN outputs of a candidate with a non-finite parameter (one thread)
+__device__ __forceinline__ void bad64(int64_t row, double* logL, double* dh_out, double* hh_out, double* dhi_out,
+                                      int* status) {
+    logL[row] = nan("");
+    if (dh_out) dh_out[row] = nan("");
+    if (hh_out) hh_out[row] = nan("");
+    if (dhi_out) dhi_out[row] = nan("");
+    atomicOr(status, kStatusNonFinite);
+}
+
+// One candidate (one warp): template, window inner products and Eq. 2; lane 0
+// writes output row `row`.
+__device__ __forceinline__ void eval64(const Cand64& c, int64_t row, const Geo64& g, const OrbitTables64& tab,
+                                       const C64* tw, C64* bufA, C64* bufE, C64* bufT, const gb_window_t& win,
+                                       double dd, const C64* __restrict__ dA, const C64* __restrict__ dE,
+                                       const double* __restrict__ wA, const double* __restrict__ wE,
+                                       const C64* __restrict__ dT, const double* __restrict__ wT,
+                                       double* __restrict__ logL, double* __restrict__ dh_out,
+                                       double* __restrict__ hh_out, double* __restrict__ dhi_out, int* status,
+                                       int lane) {
+    if (c.bad) {
+        if (lane == 0) bad64(row, logL, dh_out, hh_out, dhi_out, status);
+        return;
+    }
+    template64_dispatch(c, g, tab, tw, bufA, bufE, bufT, lane);
+    ip64(c, row, g, bufA, bufE, bufT, win, dd, dA, dE, wA, wE, dT, wT, logL, dh_out, hh_out, dhi_out, lane);
+    __syncwarp();
+}
+
+__device__ __forceinline__ Geo64 geometry64(int N, double T, double fstar) {
     Geo64 g;
-    g.N = win.N;
-    g.logN = 31 - __clz(win.N);
+    g.N = N;
+    g.logN = 31 - __clz(N);
     g.T = T;
-    g.T_over_N = T / (double)win.N;
+    g.T_over_N = T / (double)N;
     g.inv_fstar = 1.0 / fstar;
-    g.scale = T / (2.0 * (double)win.N);
+    g.scale = T / (2.0 * (double)N);
+    return g;
+}
+
+// ROWS = false: one CTA per plan tile, the tile's candidates split over the
+// warps.  ROWS = true: blockIdx.x is a window and its candidates are the rows
+// listed in rows[cand_off + j], j in [row_lo[w], row_hi[w]) (device lists);
+// the gridDim.y CTAs of a window take them one at a time (few rows, each
+// spread over a CTA, for latency).
+template <bool ROWS>
+__global__ void __launch_bounds__(kWarps64 * 32) loglik64_kernel(
+    const gb_window_t* __restrict__ wins, const Tile* __restrict__ tiles, TabSet64 tabs,
+    const C64* __restrict__ tw_g, double T, double fstar, const C64* __restrict__ dA,
+    const C64* __restrict__ dE, const double* __restrict__ wA, const double* __restrict__ wE,
+    const double* __restrict__ theta, double* __restrict__ logL, double* __restrict__ dh_out,
+    double* __restrict__ hh_out, double* __restrict__ dhi_out, const C64* __restrict__ dT,
+    const double* __restrict__ wT, int* status, int n_max, const int32_t* __restrict__ rows,
+    const int32_t* __restrict__ row_lo, const int32_t* __restrict__ row_hi, const int* __restrict__ gate) {
+    if (ROWS && gate && *gate == 0) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C64* tw = (C64*)smem_raw;                                   // kTwiddles
+    double* red = (double*)(tw + kTwiddles);                    // kWarps64
+    Cand64* cands = (Cand64*)(red + kWarps64);                  // kWarps64 * 32
+    C64* bufs = (C64*)(cands + kWarps64 * 32);                  // kWarps64 * (2 or 3) * n_max
+    const int nch = dT ? 3 : 2;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Tile tile{};
+    int lo = 0, hi = 0;
+    if (ROWS) {
+        tile.win = blockIdx.x;
+    } else {
+        tile = tiles[blockIdx.x];
+    }
+    const gb_window_t win = wins[tile.win];
+    if (ROWS) {
+        lo = max(row_lo[tile.win], 0);
+        hi = min(row_hi[tile.win], win.n_cand);
+        if (lo >= hi) return;                                   // nothing listed (block-uniform)
+    }
+    for (int i = threadIdx.x; i < kTwiddles; i += blockDim.x) tw[i] = tw_g[i];
+
+    // T enters windows whose lowest frequency is at least f*/2
+    const bool useT = dT != nullptr && (double)win.k0 / T >= 0.5 * fstar;
+    const double dd = window_dd64(win, useT, dA, dE, wA, wE, dT, wT, T, red);
+
+    const Geo64 g = geometry64(win.N, T, fstar);
     const OrbitTables64 tab = tabs.t[g.logN - 5];
     C64* bufA = bufs + (size_t)warp * nch * n_max;
     C64* bufE = bufA + n_max;
     C64* bufT = useT ? bufE + n_max : nullptr;
     Cand64* mycand = cands + warp * 32;
 
-    const int64_t tlen = tile.c_end - tile.c_begin;
-    const int64_t grp = (tlen + kWarps64 - 1) / kWarps64;   // <= 32
-    const int64_t c_lo = tile.c_begin + (int64_t)warp * grp;
-    const int64_t c_hi = min(tile.c_end, c_lo + grp);
-    if (c_lo >= c_hi) return;
-    if (c_lo + lane < c_hi) setup64(theta + 8 * (c_lo + lane), T, g.inv_fstar, mycand[lane]);
-    __syncwarp();
-    const int64_t half = win.N / 2;
-    for (int64_t cidx = c_lo; cidx < c_hi; ++cidx) {
-        const Cand64& c = mycand[cidx - c_lo];
-        if (c.bad) {
-            if (lane == 0) {
-                logL[cidx] = nan("");
-                if (dh_out) dh_out[cidx] = nan("");
-                if (hh_out) hh_out[cidx] = nan("");
-                if (dhi_out) dhi_out[cidx] = nan("");
-                atomicOr(status, kStatusNonFinite);
-            }
-            continue;
-        }
-        template64_dispatch(c, g, tab, tw, bufA, bufE, bufT, lane);
-        double sdh = 0.0, shh = 0.0, sdhi = 0.0;
-        for (int m = lane; m < win.N; m += 32) {
-            const int64_t kk = c.q - half + m - win.k0;
-            if (kk >= 0 && kk < win.W) {
-                const int idx = (m + (int)half) & (win.N - 1);
-                const C64 hA = cscale(bufA[idx], g.scale), hE = cscale(bufE[idx], g.scale);
-                const C64 a = dA[win.data_off + kk], e = dE[win.data_off + kk];
-                const double wa = wA[win.data_off + kk], we = wE[win.data_off + kk];
-                sdh += wa * (a.x * hA.x + a.y * hA.y) + we * (e.x * hE.x + e.y * hE.y);
-                shh += wa * (hA.x * hA.x + hA.y * hA.y) + we * (hE.x * hE.x + hE.y * hE.y);
-                if (dhi_out) sdhi += wa * (a.y * hA.x - a.x * hA.y) + we * (e.y * hE.x - e.x * hE.y);
-                if (useT) {
-                    const C64 hT = cscale(bufT[idx], g.scale), t = dT[win.data_off + kk];
-                    const double wt = wT[win.data_off + kk];
-                    sdh += wt * (t.x * hT.x + t.y * hT.y);
-                    shh += wt * (hT.x * hT.x + hT.y * hT.y);
-                    if (dhi_out) sdhi += wt * (t.y * hT.x - t.x * hT.y);
-                }
-            }
-        }
-        sdh = warp_sum(sdh) * (4.0 / T);
-        shh = warp_sum(shh) * (4.0 / T);
-        if (dhi_out) sdhi = warp_sum(sdhi) * (4.0 / T);
-        if (lane == 0) {
-            logL[cidx] = sdh - 0.5 * shh - 0.5 * dd;
-            if (dh_out) dh_out[cidx] = sdh;
-            if (hh_out) hh_out[cidx] = shh;
-            if (dhi_out) dhi_out[cidx] = sdhi;
-        }
+    if (!ROWS) {
+        const int64_t tlen = tile.c_end - tile.c_begin;
+        const int64_t grp = (tlen + kWarps64 - 1) / kWarps64;   // <= 32
+        const int64_t c_lo = tile.c_begin + (int64_t)warp * grp;
+        const int64_t c_hi = min(tile.c_end, c_lo + grp);
+        if (c_lo >= c_hi) return;
+        if (c_lo + lane < c_hi) setup64(theta + 8 * (c_lo + lane), T, g.inv_fstar, mycand[lane]);
         __syncwarp();
+        for (int64_t cidx = c_lo; cidx < c_hi; ++cidx)
+            eval64(mycand[cidx - c_lo], cidx, g, tab, tw, bufA, bufE, bufT, win, dd, dA, dE, wA, wE, dT, wT, logL,
+                   dh_out, hh_out, dhi_out, status, lane);
+    } else {
+        // one listed row at a time for the whole CTA (entries lo + y, lo + y
+        // + Y, ... for CTA y of the window's Y): the template over all the
+        // CTA's threads, the inner products in warp 0 in a warp's order
+        C64* cA = bufs;
+        C64* cE = bufs + n_max;
+        for (int slot = lo + (int)blockIdx.y; slot < hi; slot += (int)gridDim.y) {
+            const int64_t row = rows[win.cand_off + slot];
+            if (row < win.cand_off || row >= win.cand_off + win.n_cand) continue;   // not this window's row
+            if (threadIdx.x == 0) setup64(theta + 8 * row, T, g.inv_fstar, cands[0]);
+            __syncthreads();
+            if (cands[0].bad) {
+                if (threadIdx.x == 0) bad64(row, logL, dh_out, hh_out, dhi_out, status);
+            } else {
+                template64_dispatch<kWarps64 * 32>(cands[0], g, tab, tw, cA, cE, nullptr, threadIdx.x);
+                if (warp == 0)
+                    ip64(cands[0], row, g, cA, cE, nullptr, win, dd, dA, dE, wA, wE, nullptr, nullptr, logL, dh_out,
+                         hh_out, dhi_out, lane);
+            }
+            __syncthreads();
+        }
     }
 }
 
@@ -437,15 +533,34 @@ int launch_loglik_fp64(gb_ctx* ctx, const Plan& plan, const double* dA, const do
                        cudaStream_t s) {
     if (plan.n_tiles == 0) return GB_OK;
     const size_t smem = smem64_loglik(plan.n_max, dT ? 3 : 2);
-    cudaError_t e = cudaFuncSetAttribute(loglik64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(loglik64_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_error(ctx, e, "loglik64: smem attribute");
-    loglik64_kernel<<<plan.n_tiles, kWarps64 * 32, smem, s>>>(
+    loglik64_kernel<false><<<plan.n_tiles, kWarps64 * 32, smem, s>>>(
         plan.d_win, plan.d_tiles, tabset64(ctx), (const C64*)ctx->d_tw64, ctx->obs.T_obs,
         transfer_frequency(ctx), (const C64*)dA, (const C64*)dE, wA, wE, theta, logL, dh, hh,
-        dh_im, (const C64*)dT, wT, ctx->d_status, plan.n_max);
+        dh_im, (const C64*)dT, wT, ctx->d_status, plan.n_max, nullptr, nullptr, nullptr, nullptr);
     ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "loglik64 launch");
+    return GB_OK;
+}
+
+int launch_loglik_rows64(gb_ctx* ctx, const gb_window_t* d_win, int n_win, int n_max, int ctas_per_win,
+                         const double* dA, const double* dE, const double* wA, const double* wE, const double* theta,
+                         const int32_t* rows, const int32_t* row_lo, const int32_t* row_hi, double* logL,
+                         double* dh, double* hh, const int* gate, cudaStream_t s) {
+    if (n_win == 0) return GB_OK;
+    const size_t smem = smem64_loglik(n_max, 2);
+    cudaError_t e = cudaFuncSetAttribute(loglik64_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "loglik64 rows: smem attribute");
+    const dim3 grid((unsigned)n_win, (unsigned)(ctas_per_win < 1 ? 1 : ctas_per_win));
+    loglik64_kernel<true><<<grid, kWarps64 * 32, smem, s>>>(
+        d_win, nullptr, tabset64(ctx), (const C64*)ctx->d_tw64, ctx->obs.T_obs, transfer_frequency(ctx),
+        (const C64*)dA, (const C64*)dE, wA, wE, theta, logL, dh, hh, nullptr, nullptr, nullptr, ctx->d_status,
+        n_max, rows, row_lo, row_hi, gate);
+    ++ctx->launches;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(ctx, e, "loglik64 rows launch");
     return GB_OK;
 }
 

@@ -145,6 +145,9 @@ struct gb_ctx {
     // chunk summaries of the MH scan (grown on demand)
     void* d_mh = nullptr;
     size_t mh_bytes = 0;
+    // certified chains: exact flags, re-evaluation queues, counters (grown on demand)
+    void* d_cert = nullptr;
+    size_t cert_bytes = 0;
     // kernels launched by this context's calls
     uint64_t launches = 0;
     // work budget of the persistent kernels, nanoseconds per warp (0: none)
@@ -220,6 +223,48 @@ int launch_loglik_fp64(gb_ctx* ctx, const Plan& plan, const double* dA, const do
                        const double* wA, const double* wE, const double* theta, double* logL,
                        double* dh, double* hh, double* dh_im, const double* dT, const double* wT,
                        cudaStream_t s);
+// FP64 likelihood of listed rows: window w's entries are rows[cand_off + j],
+// j in [row_lo[w], row_hi[w]) (device), each a row of that window; results
+// bit-identical to launch_loglik_fp64's for the same rows; gate (device, may
+// be null): skip the launch when *gate == 0
+int launch_loglik_rows64(gb_ctx* ctx, const gb_window_t* d_win, int n_win, int n_max, int ctas_per_win,
+                         const double* dA, const double* dE, const double* wA, const double* wE, const double* theta,
+                         const int32_t* rows, const int32_t* row_lo, const int32_t* row_hi, double* logL,
+                         double* dh, double* hh, const int* gate, cudaStream_t s);
+// chains (mh.cu); gate (device, may be null): skip the launch when *gate == 0
+int launch_mh(gb_ctx* ctx, int32_t n_chains, int32_t n, const double* logL, const double* log_g, const double* log_u,
+              const double* temperature, int32_t literal, int32_t* chain_idx, int32_t* n_accept, const int* gate,
+              cudaStream_t st);
+// Scratch of the certified chains (device): per row the bound (float), the
+// queued mark, the re-evaluation queue and the unsettled steps; per chain the
+// queue range of the last pass; per pass and chain the rows queued, the steps
+// recorded and the finished CTAs; per pass the rows queued and the flips.
+struct CertScratch {
+    float* err;
+    int32_t* mark;
+    int32_t* queue;
+    int32_t* steps;
+    int32_t* q_lo;
+    int32_t* q_hi;
+    int* cnt;
+    int* scnt;
+    int* done;
+    int* n_new;
+    int* n_flip;
+};
+// one certification pass over chains built from bounded values (mh.cu); pass
+// 0 also computes the bounds from the mixed outputs
+int launch_mh_certify(gb_ctx* ctx, const CertScratch& cs, int32_t n_chains, int32_t n, const double* logL,
+                      const double* dh, const double* hh, const double* log_g, const double* log_u,
+                      const double* temperature, int32_t literal, double eps, const int32_t* chain_idx, int pass,
+                      const int* gate, cudaStream_t st);
+// after pass `pass`'s rows are re-evaluated: their bounds to 0, and the flips
+// of the pass's unsettled steps counted into n_flip[pass] (mh.cu)
+int launch_mh_flip(gb_ctx* ctx, const CertScratch& cs, int32_t n_chains, int32_t n, const double* logL,
+                   const double* log_g, const double* log_u, const double* temperature, int32_t literal,
+                   const int32_t* chain_idx, int pass, cudaStream_t st);
+// out[r] = sum of cnt[p][r] over the first n_pass passes (mh.cu)
+int launch_sum_rows(gb_ctx* ctx, const int* cnt, int32_t n_chains, int n_pass, int32_t* out, cudaStream_t st);
 int launch_waveform_fp64(gb_ctx* ctx, const double* theta, int64_t B, int N, double* hA,
                          double* hE, double* hT, int64_t* q, cudaStream_t s);
 int launch_loglik_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const double* dE,

@@ -37,6 +37,8 @@
 #include <climits>
 #include <cmath>
 
+#include <math_constants.h>
+
 #include "gb_internal.cuh"
 
 #ifndef GB_MH_CHUNK
@@ -235,7 +237,8 @@ __global__ void __launch_bounds__(kMhThreads) mh_summary_kernel(int n, int n_chu
                                                                 const double* __restrict__ log_u,
                                                                 const double* __restrict__ temperature, int literal,
                                                                 MhSummary* __restrict__ sum, long long* __restrict__ gK,
-                                                                long long* __restrict__ gS) {
+                                                                long long* __restrict__ gS, const int* __restrict__ gate) {
+    if (gate && *gate == 0) return;   // inputs unchanged since the last chains: keep them
     __shared__ long long K[kMhChunk], S[kMhChunk];
     __shared__ signed char rec_id[kMhChunk];
     __shared__ int rec_pos[kMhRec], rec_link[kMhRec], rec_c[kMhRec], rec_n[kMhRec];
@@ -422,7 +425,9 @@ __global__ void __launch_bounds__(kMhThreads) mh_combine_kernel(int n, int n_chu
                                                                 const double* __restrict__ temperature, int literal,
                                                                 const MhSummary* __restrict__ sum,
                                                                 MhEntry* __restrict__ entry, int32_t* __restrict__ chain,
-                                                                int32_t* __restrict__ n_accept) {
+                                                                int32_t* __restrict__ n_accept,
+                                                                const int* __restrict__ gate) {
+    if (gate && *gate == 0) return;
     __shared__ StagedSummaries st;
     const int r = blockIdx.x;
     const size_t base = (size_t)r * (size_t)n;
@@ -459,7 +464,9 @@ __global__ void __launch_bounds__(kMhThreads) mh_write_kernel(int n, int n_chunk
                                                               const MhEntry* __restrict__ entry,
                                                               const long long* __restrict__ gK,
                                                               const long long* __restrict__ gS,
-                                                              int32_t* __restrict__ chain, int32_t* __restrict__ n_accept) {
+                                                              int32_t* __restrict__ chain, int32_t* __restrict__ n_accept,
+                                                              const int* __restrict__ gate) {
+    if (gate && *gate == 0) return;
     __shared__ long long K[kMhChunk], S[kMhChunk];
     __shared__ StagedSummaries st;
     __shared__ int in_c, in_acc;
@@ -534,6 +541,168 @@ __global__ void __launch_bounds__(kMhThreads) mh_write_kernel(int n, int n_chunk
     if (!entry && k == n_chunks - 1 && lane == 0 && n_accept) n_accept[r] = acc;
 }
 
+constexpr int kCertChunk = kMhThreads;   // steps per certification CTA
+// bound on the float rounding of the mixed path's data, weights and sums,
+// relative to |h| (|d| + |h|): a float copy of the data and of the weights
+// and a compensated sum each contribute about 6e-8
+constexpr float kMixedRoundingBound = 1e-6f;
+
+// Error bound of one proposal's mixed value on the chain's decision scale.
+// The mixed path returns logL~ = <d|h~> - <h~|h~>/2 - <d|d>/2 with the
+// template h~ = h + dh, so
+//     logL~ - logL = <d - h|dh> - <dh|dh>/2 + (float rounding of the data,
+//                    the weights and the compensated sums),
+// and with |dh| <= eps |h| (weighted norm over the window) and the rounding at
+// most cf |h| (|d| + |h|):
+//     |logL~ - logL| <= eps |h| |d - h| + eps^2 |h|^2/2 + cf |h| (|d| + |h|),
+//     |d - h| <= |d - h~| + eps |h|,  |d - h~|^2 = -2 logL~,  |d|^2 = <d|d>,
+// every norm taken from the outputs (in float, with 3e-7 of the magnitudes
+// added for their own rounding), plus 1e-12 of the magnitudes for the double
+// epilogue.  Divided by the chain's T, with 1e-15 of the magnitudes of
+// logL/T, log g and w added for the rounding of w = logL/T - log g (or
+// (logL - log g)/T), two rows' bounds add up to the uncertainty of
+// Delta = w_i - w_c.  Rounded up; +inf when a value is not finite.
+__device__ __forceinline__ float mixed_bound(double l, double dh, double hh, double g, float invT, float eps,
+                                             float cf) {
+    const float lf = (float)l, d1 = (float)dh, h2 = (float)hh, gf = (float)g;
+    const float mag = fabsf(d1) + fabsf(h2) + fabsf(lf);
+    const float dd = fabsf(2.0f * (d1 - 0.5f * h2 - lf)) + 3e-7f * mag;
+    const float nh = sqrtf(fmaxf(h2, 0.0f)), nd = sqrtf(dd);
+    const float nr = sqrtf(fmaxf(-2.0f * lf, 0.0f) + 3e-7f * mag) + eps * nh;
+    float b = (eps * nh * nr + 0.5f * eps * eps * fmaxf(h2, 0.0f) + cf * nh * (nd + nh) + 1e-12f * (mag + dd)) * invT +
+              1e-15f * (fabsf(lf) * invT + fabsf(gf) * fmaxf(1.0f, invT) + fabsf(lf * invT - gf));
+    b *= 1.0001f;
+    return (isfinite(b) && isfinite(lf) && isfinite(gf) && invT > 0.0f) ? b : CUDART_INF_F;
+}
+
+__device__ __forceinline__ bool accept_rt(int rule, double wj, double uj, double wc, double T) {
+    if (rule == kPlain) return accept<kPlain>(wj, uj, wc, T);
+    if (rule == kTempered) return accept<kTempered>(wj, uj, wc, T);
+    return accept<kDivide>(wj, uj, wc, T);
+}
+
+// Certification of chains built from values of which some carry an error
+// bound (one CTA per chain and chunk of kCertChunk steps).  Pass 0 computes
+// the bounds (mixed_bound) and stores them in err; later passes read them
+// (0 once a row is re-evaluated).  Step i (i >= 1)
+// compares proposal i with the state c = chain[i - 1] before it; its double
+// decision log u_i < Delta is the one exact values give unless
+// |log u_i - Delta| <= err_i + err_c (err = 0 for exact values; the bounds do
+// not change during a pass).  Every step it cannot settle is recorded in the
+// chain's step list, and the rows of i and c that are not exact and not
+// queued yet (mark) are appended to the chain's queue (rows r n + i), to be
+// re-evaluated in FP64.  Pass p's entries of chain r follow those of the
+// earlier passes; the chain's last CTA of the pass writes their range
+// [q_lo[r], q_hi[r]).  A step whose log u is NaN or >= 0 rejects under any
+// value.  When the gate is zero the launch does nothing.
+__global__ void __launch_bounds__(kMhThreads) mh_certify_kernel(
+    int n, int n_chunks, int pass, int n_chains, const double* __restrict__ logL, const double* __restrict__ dh,
+    const double* __restrict__ hh, float eps, float cf, const double* __restrict__ log_g,
+    const double* __restrict__ log_u, const double* __restrict__ temperature, int literal,
+    const int32_t* __restrict__ chain, float* __restrict__ err, int32_t* __restrict__ mark,
+    int32_t* __restrict__ queue, int32_t* __restrict__ steps, int* __restrict__ cnt, int* __restrict__ scnt,
+    int* __restrict__ done, int32_t* __restrict__ q_lo, int32_t* __restrict__ q_hi, const int* __restrict__ gate,
+    int* __restrict__ n_new) {
+    if (gate && *gate == 0) return;
+    __shared__ int local, nstep, off, soff, last;
+    __shared__ int32_t rows[2 * kCertChunk], stp[kCertChunk];
+    const int r = blockIdx.x / n_chunks, k = blockIdx.x - r * n_chunks;
+    if (threadIdx.x == 0) local = nstep = 0;
+    __syncthreads();
+    const size_t base = (size_t)r * (size_t)n;
+    const double T = temperature[r];
+    const int rule = rule_of(T, literal);
+    const int i = 1 + k * kCertChunk + (int)threadIdx.x;
+    if (i < n) {
+        const int c = chain[base + i - 1];
+        float ei, ec;
+        if (pass == 0) {
+            const float invT = (T > 0.0 && T <= DBL_MAX) ? (float)(1.0 / T) : 0.0f;
+            ei = mixed_bound(logL[base + i], dh[base + i], hh[base + i], log_g[base + i], invT, eps, cf);
+            ec = mixed_bound(logL[base + c], dh[base + c], hh[base + c], log_g[base + c], invT, eps, cf);
+            err[base + i] = ei;
+            if (i == 1) err[base] = mixed_bound(logL[base], dh[base], hh[base], log_g[base], invT, eps, cf);
+        } else {
+            ei = err[base + i];
+            ec = err[base + c];
+        }
+        const double u = log_u[base + i];
+        bool settled = (ei == 0.0f && ec == 0.0f) || is_nan(u) || !(u < 0.0);
+        if (!settled) {
+            const double wi = weight_rt(rule, logL[base + i], log_g[base + i], T);
+            const double wc = weight_rt(rule, logL[base + c], log_g[base + c], T);
+            double d = __dadd_rn(wi, -wc);
+            if (rule == kDivide) d = __ddiv_rn(d, T);
+            const double m = (double)ei + (double)ec;
+            settled = isfinite(d) && isfinite(m) && fabs(u - d) > m;
+        }
+        if (!settled) {
+            stp[atomicAdd(&nstep, 1)] = i;
+            if (ei > 0.0f && atomicExch(&mark[base + i], 1) == 0) rows[atomicAdd(&local, 1)] = (int32_t)(base + i);
+            if (ec > 0.0f && atomicExch(&mark[base + c], 1) == 0) rows[atomicAdd(&local, 1)] = (int32_t)(base + c);
+        }
+    }
+    __syncthreads();
+    int* cr = cnt + (size_t)pass * n_chains + r;
+    if (threadIdx.x == 0) {
+        off = local ? atomicAdd(cr, local) : 0;
+        soff = nstep ? atomicAdd(scnt + (size_t)pass * n_chains + r, nstep) : 0;
+        if (local) atomicAdd(n_new, local);
+    }
+    __syncthreads();
+    int lo = 0;
+    for (int q = 0; q < pass; ++q) lo += cnt[(size_t)q * n_chains + r];
+    for (int j = threadIdx.x; j < local; j += blockDim.x) queue[base + lo + off + j] = rows[j];
+    for (int j = threadIdx.x; j < nstep; j += blockDim.x) steps[base + soff + j] = stp[j];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(done + (size_t)pass * n_chains + r, 1) == n_chunks - 1;
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        q_lo[r] = lo;
+        q_hi[r] = lo + atomicAdd(cr, 0);
+    }
+}
+
+// After the FP64 re-evaluation of pass p's rows (one CTA per chain): their
+// bounds become 0, and every step the pass could not settle is decided again
+// from the exact values; n_flip counts the steps whose decision differs from
+// the chain's (chain[i] == i iff step i accepted).  Without a flip the chain
+// is the exact one: every other step was settled within bounds that hold.
+__global__ void __launch_bounds__(kMhThreads) mh_flip_kernel(
+    int n, int pass, int n_chains, const double* __restrict__ logL, const double* __restrict__ log_g,
+    const double* __restrict__ log_u, const double* __restrict__ temperature, int literal,
+    const int32_t* __restrict__ chain, float* __restrict__ err, const int32_t* __restrict__ queue,
+    const int32_t* __restrict__ steps, const int* __restrict__ scnt, const int32_t* __restrict__ q_lo,
+    const int32_t* __restrict__ q_hi, const int* __restrict__ gate, int* __restrict__ n_flip) {
+    if (gate && *gate == 0) return;
+    const int r = blockIdx.x;
+    const size_t base = (size_t)r * (size_t)n;
+    for (int j = q_lo[r] + (int)threadIdx.x; j < q_hi[r]; j += blockDim.x) err[queue[base + j]] = 0.0f;
+    const double T = temperature[r];
+    const int rule = rule_of(T, literal);
+    const int ns = scnt[(size_t)pass * n_chains + r];
+    int flips = 0;
+    for (int k = threadIdx.x; k < ns; k += blockDim.x) {
+        const int i = steps[base + k];
+        const int c = chain[base + i - 1];
+        const double wi = weight_rt(rule, logL[base + i], log_g[base + i], T);
+        const double wc = weight_rt(rule, logL[base + c], log_g[base + c], T);
+        flips += accept_rt(rule, wi, log_u[base + i], wc, T) != (chain[base + i] == i);
+    }
+    if (flips) atomicAdd(n_flip, flips);
+}
+
+// out[r] = sum over passes p < n_pass of cnt[p][r] (one thread per chain)
+__global__ void sum_rows_kernel(const int* __restrict__ cnt, int n_chains, int n_pass, int32_t* __restrict__ out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_chains) return;
+    int s = 0;
+    for (int p = 0; p < n_pass; ++p) s += cnt[(size_t)p * n_chains + r];
+    out[r] = s;
+}
+
 }  // namespace
 
 int ensure_mh_scratch(gb_ctx* ctx, size_t bytes) {
@@ -557,6 +726,79 @@ size_t mh_scratch_bytes(size_t chunk_slots, size_t proposals) {
 
 using namespace gb;
 
+namespace gb {
+
+int launch_mh(gb_ctx* ctx, int32_t n_chains, int32_t n, const double* logL, const double* log_g, const double* log_u,
+              const double* temperature, int32_t literal, int32_t* chain_idx, int32_t* n_accept, const int* gate,
+              cudaStream_t st) {
+    const int n_chunks = (n - 1 + kMhChunk - 1) / kMhChunk;
+    const size_t slots = (size_t)n_chains * (size_t)n_chunks;
+    if (slots > (size_t)INT_MAX) return set_error(ctx, GB_EINVAL, "gb_mh_independence: too many chunks");
+    const size_t props = (size_t)n_chains * (size_t)n;
+    int rc = ensure_mh_scratch(ctx, mh_scratch_bytes(slots > 0 ? slots : 1, props));
+    if (rc != GB_OK) return rc;
+    MhSummary* sum = (MhSummary*)ctx->d_mh;
+    MhEntry* entry = (MhEntry*)(sum + slots);
+    long long* gK = (long long*)(entry + slots);
+    long long* gS = gK + props;
+    const bool fused = n_chunks > 0 && n_chunks <= kCombineBatch;
+    if (n_chunks > 0)
+        mh_summary_kernel<<<(unsigned)slots, kMhThreads, 0, st>>>(n, n_chunks, logL, log_g, log_u, temperature,
+                                                                  literal, sum, gK, gS, gate);
+    if (n_chunks > 0) ++ctx->launches;
+    if (!fused)
+        mh_combine_kernel<<<n_chains, kMhThreads, 0, st>>>(n, n_chunks, logL, log_g, log_u, temperature, literal,
+                                                           sum, entry, chain_idx, n_accept, gate);
+    if (!fused) ++ctx->launches;
+    if (n_chunks > 0)
+        mh_write_kernel<<<(unsigned)slots, kMhThreads, 0, st>>>(n, n_chunks, logL, log_g, log_u, temperature,
+                                                                literal, sum, fused ? nullptr : entry, gK, gS,
+                                                                chain_idx, n_accept, gate);
+    if (n_chunks > 0) ++ctx->launches;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_mh_independence launch");
+    return GB_OK;
+}
+
+int launch_mh_certify(gb_ctx* ctx, const CertScratch& cs, int32_t n_chains, int32_t n, const double* logL,
+                      const double* dh, const double* hh, const double* log_g, const double* log_u,
+                      const double* temperature, int32_t literal, double eps, const int32_t* chain_idx, int pass,
+                      const int* gate, cudaStream_t st) {
+    const int n_chunks = (n - 1 + kCertChunk - 1) / kCertChunk;
+    if (n_chunks > 0) {
+        mh_certify_kernel<<<(unsigned)((size_t)n_chains * n_chunks), kMhThreads, 0, st>>>(
+            n, n_chunks, pass, n_chains, logL, dh, hh, (float)eps, kMixedRoundingBound, log_g, log_u, temperature,
+            literal, chain_idx, cs.err, cs.mark, cs.queue, cs.steps, cs.cnt, cs.scnt, cs.done, cs.q_lo, cs.q_hi, gate,
+            cs.n_new + pass);
+        ++ctx->launches;
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(ctx, e, "mh_certify launch");
+    return GB_OK;
+}
+
+int launch_mh_flip(gb_ctx* ctx, const CertScratch& cs, int32_t n_chains, int32_t n, const double* logL,
+                   const double* log_g, const double* log_u, const double* temperature, int32_t literal,
+                   const int32_t* chain_idx, int pass, cudaStream_t st) {
+    mh_flip_kernel<<<n_chains, kMhThreads, 0, st>>>(n, pass, n_chains, logL, log_g, log_u, temperature, literal,
+                                                    chain_idx, cs.err, cs.queue, cs.steps, cs.scnt, cs.q_lo, cs.q_hi,
+                                                    cs.n_new + pass, cs.n_flip + pass);
+    ++ctx->launches;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(ctx, e, "mh_flip launch");
+    return GB_OK;
+}
+
+int launch_sum_rows(gb_ctx* ctx, const int* cnt, int32_t n_chains, int n_pass, int32_t* out, cudaStream_t st) {
+    sum_rows_kernel<<<(n_chains + 127) / 128, 128, 0, st>>>(cnt, n_chains, n_pass, out);
+    ++ctx->launches;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(ctx, e, "sum_rows launch");
+    return GB_OK;
+}
+
+}  // namespace gb
+
 extern "C" int gb_mh_independence(gb_ctx_t* ctx, int32_t n_chains, int32_t n, const double* logL,
                                   const double* log_g, const double* log_u, const double* temperature,
                                   int32_t literal, int32_t* chain_idx, int32_t* n_accept, void* stream) {
@@ -568,32 +810,6 @@ extern "C" int gb_mh_independence(gb_ctx_t* ctx, int32_t n_chains, int32_t n, co
     if (literal != 0 && literal != 1) return set_error(ctx, GB_EINVAL, "gb_mh_independence: literal must be 0 or 1");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_error(ctx, e, "gb_mh_independence: cudaSetDevice");
-    const int n_chunks = (n - 1 + kMhChunk - 1) / kMhChunk;
-    const size_t slots = (size_t)n_chains * (size_t)n_chunks;
-    if (slots > (size_t)INT_MAX) return set_error(ctx, GB_EINVAL, "gb_mh_independence: too many chunks");
-    const size_t props = (size_t)n_chains * (size_t)n;
-    int rc = ensure_mh_scratch(ctx, mh_scratch_bytes(slots > 0 ? slots : 1, props));
-    if (rc != GB_OK) return rc;
-    MhSummary* sum = (MhSummary*)ctx->d_mh;
-    MhEntry* entry = (MhEntry*)(sum + slots);
-    long long* gK = (long long*)(entry + slots);
-    long long* gS = gK + props;
-    cudaStream_t st = (cudaStream_t)stream;
-    const bool fused = n_chunks > 0 && n_chunks <= kCombineBatch;
-    if (n_chunks > 0)
-        mh_summary_kernel<<<(unsigned)slots, kMhThreads, 0, st>>>(n, n_chunks, logL, log_g, log_u, temperature,
-                                                                  literal, sum, gK, gS);
-    if (n_chunks > 0) ++ctx->launches;
-    if (!fused)
-        mh_combine_kernel<<<n_chains, kMhThreads, 0, st>>>(n, n_chunks, logL, log_g, log_u, temperature, literal,
-                                                           sum, entry, chain_idx, n_accept);
-    if (!fused) ++ctx->launches;
-    if (n_chunks > 0)
-        mh_write_kernel<<<(unsigned)slots, kMhThreads, 0, st>>>(n, n_chunks, logL, log_g, log_u, temperature,
-                                                                literal, sum, fused ? nullptr : entry, gK, gS,
-                                                                chain_idx, n_accept);
-    if (n_chunks > 0) ++ctx->launches;
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_mh_independence launch");
-    return GB_OK;
+    return launch_mh(ctx, n_chains, n, logL, log_g, log_u, temperature, literal, chain_idx, n_accept, nullptr,
+                     (cudaStream_t)stream);
 }

@@ -150,6 +150,8 @@ int launch_waveform_mixed(gb_ctx* ctx, const double* theta, int64_t B, int N, do
 // per-window values and float copies, the work-queue heads -- lives in one
 // file-scope device array, so a call allocates no memory at all.
 // ---------------------------------------------------------------------------
+#include <cuda.h>
+
 #include <cstring>
 #include <mutex>
 
@@ -176,9 +178,14 @@ constexpr size_t kNaBytes = na_round(kNaOffHead + 4 * sizeof(int));   // two que
 // 8.7 MB per device, kept until the process exits
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
+// What the tables in a device's array were built for: the array's address,
+// the CUDA context it lives in and the observation.  A new context (after a
+// device reset, say) reloads the module, so the tables are built again.
 struct NaDevice {
-    unsigned char* base = nullptr;   // device address of g_noalloc_scratch
-    double T = 0.0, L = 0.0;         // observation the tables were built for
+    bool built = false;
+    unsigned char* base = nullptr;
+    unsigned long long ctx_id = 0;
+    double T = 0.0, L = 0.0;
 };
 constexpr int kNaMaxDevices = 64;
 NaDevice g_na_dev[kNaMaxDevices];
@@ -194,6 +201,33 @@ int na_fail(char* err, int err_len, int code, const char* msg) {
     return code;
 }
 
+// Unique id of the current CUDA context (cuCtxGetId through the runtime's
+// driver entry points, so no link against the driver library); 0 if the
+// driver does not provide it.
+unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        cudaDriverEntryPointQueryResult q1, q2;
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            get_current = (GetCurrent)f1;
+            get_id = (GetId)f2;
+        }
+    }
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&c) == CUDA_SUCCESS && c && get_id(c, &id) == CUDA_SUCCESS) return id;
+    return 0;
+}
+
 }  // namespace
 }  // namespace gb
 
@@ -202,7 +236,8 @@ using namespace gb;
 extern "C" int gb_loglik_mixed_noalloc(const gb_obs_t* obs, const gb_window_t* win, int32_t n_win,
                                        const double* dA, const double* dE, const double* wA, const double* wE,
                                        int64_t n_bins, const double* theta, int64_t n_rows, double* logL,
-                                       double* dh, double* hh, void* stream, char* err, int32_t err_len) {
+                                       double* dh, double* hh, int32_t* status, void* stream, char* err,
+                                       int32_t err_len) {
     if (err && err_len > 0) err[0] = '\0';
     if (!obs || !(obs->T_obs > 0.0) || !(obs->arm_L > 0.0) || obs->orbit_model != 0)
         return na_fail(err, err_len, GB_EINVAL, "gb_loglik_mixed_noalloc: bad observation");
@@ -223,11 +258,25 @@ extern "C" int gb_loglik_mixed_noalloc(const gb_obs_t* obs, const gb_window_t* w
     }
     if (bins > kNaMaxBins)
         return na_fail(err, err_len, GB_EINVAL, "gb_loglik_mixed_noalloc: more than 262144 window bins in total");
-    if (total == 0) return GB_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    (void)cudaGetLastError();   // an earlier call's error is not this call's
+    // the uploads below read host staging that the next call overwrites, so a
+    // captured copy of this call would replay another call's work items
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return na_fail(err, err_len, GB_ECUDA, "gb_loglik_mixed_noalloc: stream query failed");
+    if (cap != cudaStreamCaptureStatusNone)
+        return na_fail(err, err_len, GB_EINVAL, "gb_loglik_mixed_noalloc: the stream is capturing a graph; "
+                                                "this entry point cannot be captured");
+    if (total == 0) {
+        if (status && cudaMemsetAsync(status, 0, sizeof(int32_t), s) != cudaSuccess)
+            return na_fail(err, err_len, GB_ECUDA, "gb_loglik_mixed_noalloc: status reset failed");
+        return GB_OK;
+    }
     if (!dA || !dE || !wA || !wE || !theta || !logL)
         return na_fail(err, err_len, GB_EINVAL, "gb_loglik_mixed_noalloc: null pointer");
     int dev = 0, sms = 152;
-    cudaError_t e = cudaGetDevice(&dev);
+    e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kNaMaxDevices)
         return na_fail(err, err_len, GB_ECUDA, "gb_loglik_mixed_noalloc: no current device");
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -236,17 +285,14 @@ extern "C" int gb_loglik_mixed_noalloc(const gb_obs_t* obs, const gb_window_t* w
     if (items > kNaMaxItems)
         return na_fail(err, err_len, GB_EINVAL, "gb_loglik_mixed_noalloc: more than 65536 work items "
                                                 "(about 2 million candidates)");
-    cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lock(g_na_mutex);
+    // the array's device address, taken on every call (this allocates nothing)
+    unsigned char* b = nullptr;
+    e = cudaGetSymbolAddress((void**)&b, g_noalloc_scratch);
+    if (e != cudaSuccess || !b)
+        return na_fail(err, err_len, GB_ECUDA, "gb_loglik_mixed_noalloc: cudaGetSymbolAddress failed");
+    const unsigned long long ctx_id = current_context_id();
     NaDevice& d = g_na_dev[dev];
-    if (!d.base) {
-        e = cudaGetSymbolAddress((void**)&d.base, g_noalloc_scratch);
-        if (e != cudaSuccess) {
-            d.base = nullptr;
-            return na_fail(err, err_len, GB_ECUDA, "gb_loglik_mixed_noalloc: cudaGetSymbolAddress failed");
-        }
-    }
-    unsigned char* b = d.base;
     double* t64[kNumSizes];
     float* t32[kNumSizes];
     TabSet32 tabs;
@@ -263,9 +309,13 @@ extern "C" int gb_loglik_mixed_noalloc(const gb_obs_t* obs, const gb_window_t* w
     }
     double* tw64 = (double*)(b + kNaOffTw64);
     float* tw32 = (float*)(b + kNaOffTw32);
-    if (d.T != obs->T_obs || d.L != obs->arm_L) {
+    if (!d.built || d.base != b || d.ctx_id != ctx_id || d.T != obs->T_obs || d.L != obs->arm_L) {
+        d.built = false;
         e = build_tables_into(obs->T_obs, obs->arm_L, t64, t32, tw64, tw32, s);
         if (e != cudaSuccess) return na_fail(err, err_len, GB_ECUDA, "gb_loglik_mixed_noalloc: table build failed");
+        d.built = true;
+        d.base = b;
+        d.ctx_id = ctx_id;
         d.T = obs->T_obs;
         d.L = obs->arm_L;
     }
@@ -303,29 +353,32 @@ extern "C" int gb_loglik_mixed_noalloc(const gb_obs_t* obs, const gb_window_t* w
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_items, g_na_items, sizeof(Tile) * (size_t)k, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_meta, g_na_meta, sizeof(WinMeta) * (size_t)n_win, cudaMemcpyHostToDevice, s);
+    // this call's status starts clear (the queue heads are reset by the preparation kernel)
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(int), s);
     if (e != cudaSuccess) return na_fail(err, err_len, GB_ECUDA, "gb_loglik_mixed_noalloc: upload failed");
-    // the queue heads start at zero: the preparation kernel resets them
     const double fstar = kC / (2.0 * kPi * obs->arm_L);
     prep_mixed_kernel<<<n_win, 256, 0, s>>>(d_win, d_meta, d_prep, (const double2*)dA, (const double2*)dE, wA, wE,
                                             nullptr, nullptr, 0LL, obs->T_obs, fstar, d_head);
-    for (int part = 0; part < 2 && cudaGetLastError() == cudaSuccess; ++part) {
+    e = cudaGetLastError();
+    for (int part = 0; part < 2 && e == cudaSuccess; ++part) {
         const int n_items = part == 0 ? n_large : k - n_large;
         if (n_items == 0) continue;
         const int nmax = part == 0 ? 1024 : (n_max < 256 ? n_max : 256);
         const size_t smem =
             (sizeof(CandMix) + sizeof(Epi<false>)) * kWarpsMx * 32 + sizeof(float2) * kWarpsMx * 2 * (size_t)nmax;
         const void* kfn = mixed_kernel_fn(part, false, false);
-        if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) break;
+        e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) break;
         int grid = sms * resident_blocks(kfn, kWarpsMx * 32, smem);
         const int need = (n_items + kWarpsMx - 1) / kWarpsMx;
         if (grid > need) grid = need;
         const Tile* it = d_items + (part == 0 ? 0 : n_large);
         int* head = d_head + (part == 0 ? 1 : 0);
-        if (launch_mixed_part(kfn, grid, smem, s, d_win, d_meta, d_prep, it, n_items, head, tabs, (const float2*)tw32,
-                              obs->T_obs, fstar, theta, logL, dh, hh, nullptr, d_status, nmax, 0ULL, 0LL) != cudaSuccess)
-            break;
+        e = launch_mixed_part(kfn, grid, smem, s, d_win, d_meta, d_prep, it, n_items, head, tabs, (const float2*)tw32,
+                              obs->T_obs, fstar, theta, logL, dh, hh, nullptr, d_status, nmax, 0ULL, 0LL);
+        if (e == cudaSuccess) e = cudaGetLastError();
     }
-    e = cudaGetLastError();
+    if (e == cudaSuccess && status) e = cudaMemcpyAsync(status, d_status, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return na_fail(err, err_len, GB_ECUDA, cudaGetErrorString(e));
     return GB_OK;
 }

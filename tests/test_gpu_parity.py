@@ -216,10 +216,24 @@ def test_loglik_phase_mixed_at_snr50(ctx):
     assert float((dip - oq).abs().max()) <= 1e-3
 
 
-def test_loglik_posterior_workload_sampled(ctx):
+def mixed_bound(l, dh, hh, eps, cf=1e-6):
+    """Per-row bound of |logL_mixed - logL_fp64| from the mixed outputs (the
+    model gb_mh_certified settles decisions with): eps |h| |d - h| +
+    eps^2 |h|^2 / 2 + cf |h| (|d| + |h|) + 1e-12 (|logL| + |d|^2 + |h|^2), with
+    <d|d> = 2 (dh - hh/2 - logL) and |d - h| <= (-2 logL)^1/2 + eps |h|."""
+    dd = (2.0 * (dh - 0.5 * hh - l)).abs()
+    h2 = hh.clamp(min=0.0)
+    nh = h2.sqrt()
+    nr = (-2.0 * l).clamp(min=0.0).sqrt() + eps * nh
+    return eps * nh * nr + 0.5 * eps * eps * h2 + cf * nh * (dd.sqrt() + nh) + 1e-12 * (l.abs() + dd + h2)
+
+
+def test_loglik_posterior_workload_sampled(ctx, api):
     # the 16-window, 10,000-proposal workload at full size in one launch, in
-    # both precisions; outputs sampled for the oracle (first, last and 40
-    # random rows per window)
+    # both precisions.  Every row: the mixed value within half the bound of
+    # the certified chains (eps = api.MIXED_EPS) of the FP64 path's; the FP64
+    # path against the oracle on sampled rows (first, last and 40 random rows
+    # per window) at 1e-10, and the mixed path there against the oracle too
     wl = wk.posterior_windows()
     rng = np.random.default_rng(5)
     srcs = []
@@ -235,6 +249,18 @@ def test_loglik_posterior_workload_sampled(ctx):
             _cuda(wl.w_E, torch.float64), _cuda(th, torch.float64))
     g64 = [x.cpu() for x in ctx.loglik(wl.windows, *args, prec="fp64")]
     gmx = [x.cpu() for x in ctx.loglik(wl.windows, *args, prec="mixed")]
+    # every row against the FP64 GPU path
+    dl = (gmx[0] - g64[0]).abs()
+    bound = mixed_bound(gmx[0], gmx[1], gmx[2], api.MIXED_EPS)
+    assert bool(torch.isfinite(gmx[0]).all())
+    assert bool((dl <= 0.5 * bound).all()), float((dl / bound).max())
+    # per SNR band of the proposal (<h|h>^1/2): max |dlogL| <= 0.5 eps SNR (SNR_d + SNR)
+    snr = g64[2].sqrt()
+    snr_d = (2.0 * (g64[1] - 0.5 * g64[2] - g64[0])).abs().sqrt()
+    for lo, hi in [(0, 20), (20, 50), (50, 100), (100, 200), (200, 1e9)]:
+        m = (snr >= lo) & (snr < hi)
+        if bool(m.any()):
+            assert float(dl[m].max()) <= 0.5 * api.MIXED_EPS * float((snr[m] * (snr_d[m] + snr[m])).max())
     rows = []
     for (k0, W, N, doff, coff, nc) in wl.windows:
         rows += [coff, coff + nc - 1] + list(coff + rng.choice(nc, 40, replace=False))
@@ -247,7 +273,7 @@ def test_loglik_posterior_workload_sampled(ctx):
     o = ogb.loglik(sub_wins, dA, dE, wl.w_A, wl.w_E, np.array(sub_th), wl.T)
     idx = torch.tensor(rows)
     _assert_close_fp64([x[idx] for x in g64], o)
-    assert float((gmx[0][idx] - o[0]).abs().max()) <= 2e-3 * max(1.0, float(o[2].max()) / 2500.0)
+    assert bool(((gmx[0][idx] - o[0]).abs() <= 0.5 * bound[idx] + 1e-10 * o[0].abs().clamp(min=1.0)).all())
 
 
 def test_loglik_outputs_optional(ctx):
