@@ -218,6 +218,19 @@ def kernel_source_sha256():
     return hashlib.sha256(region.encode()).hexdigest()
 
 
+def flops_per_grad_fp64(N, f_hz, T):
+    """Algorithmic floating-point operations of one FP64 gradient (FMA = 2), the
+    same reverse-mode count as flops_per_grad with the FP64 path's per-sample
+    forward work (flops_per_eval_fp64) and its link-series degrees J = 6, 8,
+    12, 16: forward with 38 per window bin, the adjoint transform of both
+    channels, and per sample 508 + 48 J + 555 for the reverse step.  The FP64
+    kernel itself carries eight forward tangents, about three times this work."""
+    x = f_hz / (299792458.0 / (2 * math.pi * 2.5e9))
+    J = 6 if x <= 0.22 else 8 if x <= 0.5 else 12 if x <= 1.3 else 16
+    forward = N * (445 + 24 * J) + 2 * 5 * N * math.log2(N) + 38 * N
+    return forward + 2 * 5 * N * math.log2(N) + N * (508 + 48 * J + 555)
+
+
 def profiled_traffic():
     """DRAM bytes per launch of the likelihood kernel from the committed ncu
     counters (profiles/loglik_mixed_posterior.json), or None when the kernel's
@@ -492,8 +505,15 @@ def run_workload(args):
             "frac": gflops / (ms_g / 1e3) / 1e12 / peak, "traffic": None, "kernel": "grad_mixed_kernel",
             "peak_note": "FP32 FMA peak from unit counts: 152 SM x 128 lanes x 2 x 2070 MHz; the timed call "
                          "is the preparation kernel and the gradient kernel"}
+        gflops64 = sum(512 * flops_per_grad_fp64(w[2], f, wl.T) for w, f in zip(wl.windows, f_mid))
         line["grad_fp64"] = {"value": 512 * len(sub) / ms_g64 * 1e3, "unit": "gradients/s", "ms": ms_g64,
-                             "sample": "512 candidates per window"}
+                             "sample": "512 candidates per window",
+                             "roofline": {"bound": "alu", "achieved": gflops64 / (ms_g64 / 1e3) / 1e12,
+                                          "peak": fp64_peak_tflops(), "unit": "TFLOP/s",
+                                          "frac": gflops64 / (ms_g64 / 1e3) / 1e12 / fp64_peak_tflops(),
+                                          "traffic": None, "kernel": "grad64_kernel",
+                                          "peak_note": "FP64 peak from unit counts: 152 SM x 2 FP64 FMA lanes x 2 "
+                                                       "x 2070 MHz; achieved counts the reverse-mode work"}}
         boxes = np.array([np.concatenate([wl.theta[c:c + m].min(0), wl.theta[c:c + m].max(0)])
                           for (_, _, _, _, c, m) in wl.windows])
         ga_ms = {}
@@ -521,7 +541,7 @@ def run_fullband(args):
     clocks.start()
     st = fullband.run(ctx, n_src=args.fb_sources, rounds=args.fb_rounds, pop=args.fb_pop, generations=args.fb_gens,
                       phase=not args.fb_no_phase, posterior=args.fb_posterior, scheme=args.fb_scheme,
-                      noise=args.fb_noise)
+                      noise=args.fb_noise, joint=not args.fb_no_joint)
     line = {"metric": "total wall time, s per posterior (full-band search)", "workload": "fullband",
             "n_gpus": 1, "unit": "s", "higher_is_better": False, "data": "synthetic",
             "value": st["wall_s"], "s_per_posterior": st["s_per_posterior"],
@@ -555,6 +575,8 @@ def main():
                     help="fullband: weights from the true PSD, or each segment's median periodogram")
     ap.add_argument("--fb-posterior", default="gauss", choices=["gauss", "kde"],
                     help="fullband: Alg. 4 proposals, Gaussian refits or the paper's paired KDEs")
+    ap.add_argument("--fb-no-joint", action="store_true",
+                    help="fullband: no joint refit of a window's sources after each new one (Alg. 2)")
     ap.add_argument("--fb-no-phase", action="store_true",
                     help="fullband: rank GA individuals by the plain SNR instead of the SNR maximised over phi0")
     args = ap.parse_args()

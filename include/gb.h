@@ -306,6 +306,28 @@ int gb_mh_certified(gb_ctx_t* ctx, const gb_window_t* win, int32_t n_win,
                     double* logL, double* dh, double* hh, int32_t* chain_idx, int32_t* n_accept,
                     int32_t* n_exact, int32_t* pending, void* stream);
 
+/* Multi-signal SNR (Sec. III.D, Eq. 11) and the inner products it is made
+ * of, in FP64.  Window w's sources are its candidate rows
+ * theta[cand_off .. cand_off + n_cand) (K_w = n_cand <= kmax <= 64), each
+ * with the template of gb_waveform (GB_FP64, N of the window) restricted to
+ * the window's bins.  Writes
+ *   gram  n_win x kmax x kmax (device): G_w[i][j] = <s_i|s_j> for i, j < K_w
+ *         (the other entries are left as they are)
+ *   dh    n_rows (device, may be NULL): <d|s_i> of every source row
+ *   rho   n_win (device, may be NULL): sum_i <d|s_i> / sqrt(sum_ij G_w[i][j]),
+ *         the SNR of the sum of the window's templates; NaN for K_w = 0
+ * The scaled error and overlap of a recovered against an injected source
+ * (Sec. IV, Eqs. 19-20) follow from the Gram matrix of the pair:
+ * delta = (G_rr - 2 G_ri + G_ii)/G_rr, O = G_ri / sqrt(G_rr G_ii).
+ * wA, wE are required; dA, dE only when dh or rho is requested.  A source
+ * with a non-finite parameter gives NaN entries and sets the status word.
+ * Windows as gb_loglik; one CTA per window, sum_w K_w (K_w + 1)/2 template
+ * evaluations. */
+int gb_snr_multi(gb_ctx_t* ctx, const gb_window_t* win, int32_t n_win,
+                 const double* dA, const double* dE, const double* wA, const double* wE,
+                 int64_t n_bins, const double* theta, int64_t n_rows, int32_t kmax,
+                 double* gram, double* dh, double* rho, void* stream);
+
 /* Launch shapes chosen by gb_autotune: candidates per work item and resident
  * CTAs per SM of the persistent mixed-precision kernels (0 = built-in
  * heuristic), candidates per CTA tile of the FP64 kernel, and the measured

@@ -12,6 +12,8 @@ What the paper fixes
 * eight parameters {A, lambda, beta, f, fdot, iota, phi0, psi}, first-order
   fdot only                                                             (Sec. III, first paragraph)
 * SNR rho = <d|s>/sqrt<s|s> and A_max = <d|s'>/<s'|s'>                  (Eqs. 6-7)
+* multi-signal SNR rho = <d|sum s>/sqrt<sum s|sum s>                    (Eq. 11)
+* scaled error delta and overlap O of a recovery against an injection   (Eqs. 19-20)
 
 What the paper only cites (the signal model and the LISA response) is written
 out here from the physics, with these readings:
@@ -58,6 +60,8 @@ R11 T = (X + Y + Z)/sqrt3 (Eq. 5).  The paper drops T below f*/2 = c/(4 pi L)
     and T.
 """
 import math
+
+import numpy as np
 
 import torch
 
@@ -343,3 +347,77 @@ def amplitude_max(A, dh, hh):
     With h = A s', <d|s'> = dh/A and <s'|s'> = hh/A^2, so A_max = A dh/hh.
     """
     return A * dh / hh
+
+
+def _on_window(theta, k0, W, N, T, L=ARM_L):
+    """Templates of theta (K, 8) restricted to window bins k0..k0+W-1 (zero
+    where a template has no bin): (K, W) complex A and E (R8, R9)."""
+    q, hA, hE = template(theta, N, T, L)
+    K = theta.shape[0]
+    outA = torch.zeros((K, W), dtype=C128)
+    outE = torch.zeros((K, W), dtype=C128)
+    j = q[:, None] - N // 2 + torch.arange(N, dtype=torch.int64)[None, :] - k0
+    inside = (j >= 0) & (j < W)
+    for k in range(K):
+        outA[k, j[k][inside[k]]] = hA[k][inside[k]]
+        outE[k, j[k][inside[k]]] = hE[k][inside[k]]
+    return outA, outE
+
+
+def _inner(xA, xE, yA, yE, wA, wE, T):
+    """<x|y> over window bins (R9): (4/T) Re sum_k w_k x_k y_k*, both channels."""
+    return (4.0 / T) * ((wA * (xA * yA.conj()).real).sum(-1) + (wE * (xE * yE.conj()).real).sum(-1))
+
+
+def snr_multi(windows, dA, dE, wA, wE, theta, T, L=ARM_L):
+    """Multi-signal SNR (Eq. 11, Sec. III.D) of each window's sources, and its parts.
+
+    Window w = (k0, W, N, data_off, cand_off, n_cand) holds the K = n_cand
+    sources theta[cand_off:cand_off+K].  Eq. 11 as printed: the sum of the
+    sources' templates S, then rho = <d|S> / sqrt(<S|S>).  Also returned, for
+    the same window: the Gram matrix G_ij = <s_i|s_j> and b_i = <d|s_i>.
+    Returns (rho (n_win,), [G_w (K, K)], b (n_rows,)).
+    """
+    theta = torch.as_tensor(theta, dtype=F64)
+    dA, dE = torch.as_tensor(dA, dtype=C128), torch.as_tensor(dE, dtype=C128)
+    wA, wE = torch.as_tensor(wA, dtype=F64), torch.as_tensor(wE, dtype=F64)
+    rho = torch.full((len(windows),), float("nan"), dtype=F64)
+    grams = []
+    b = torch.zeros(theta.shape[0], dtype=F64)
+    for w, (k0, W, N, doff, coff, nc) in enumerate(windows):
+        sl = slice(doff, doff + W)
+        if nc == 0:
+            grams.append(torch.zeros((0, 0), dtype=F64))
+            continue
+        sA, sE = _on_window(theta[coff:coff + nc], k0, W, N, T, L)
+        SA, SE = sA.sum(0), sE.sum(0)                      # the sum of the templates
+        num = _inner(dA[sl], dE[sl], SA, SE, wA[sl], wE[sl], T)
+        den = _inner(SA, SE, SA, SE, wA[sl], wE[sl], T)
+        rho[w] = num / torch.sqrt(den)
+        G = torch.empty((nc, nc), dtype=F64)
+        for i in range(nc):
+            for j in range(nc):
+                G[i, j] = _inner(sA[i], sE[i], sA[j], sE[j], wA[sl], wE[sl], T)
+        grams.append(G)
+        b[coff:coff + nc] = torch.stack([_inner(dA[sl], dE[sl], sA[i], sE[i], wA[sl], wE[sl], T)
+                                         for i in range(nc)])
+    return rho, grams, b
+
+
+def match_metrics(window, wA, wE, theta_rec, theta_inj, T, L=ARM_L):
+    """Scaled error (Eq. 19) and overlap (Eq. 20) of a recovered source
+    against an injected one (Sec. IV), both templates of length N on the
+    window (k0, W, N, data_off, ...):
+        delta = <s_rec - s_inj|s_rec - s_inj> / <s_rec|s_rec>,
+        O = <s_rec|s_inj> / sqrt(<s_rec|s_rec> <s_inj|s_inj>)."""
+    k0, W, N, doff = window[:4]
+    wA = torch.as_tensor(wA, dtype=F64)[doff:doff + W]
+    wE = torch.as_tensor(wE, dtype=F64)[doff:doff + W]
+    th = torch.as_tensor(np.stack([np.asarray(theta_rec), np.asarray(theta_inj)]), dtype=F64)
+    sA, sE = _on_window(th, k0, W, N, T, L)
+    dA, dE = sA[0] - sA[1], sE[0] - sE[1]
+    rr = _inner(sA[0], sE[0], sA[0], sE[0], wA, wE, T)
+    ii = _inner(sA[1], sE[1], sA[1], sE[1], wA, wE, T)
+    ri = _inner(sA[0], sE[0], sA[1], sE[1], wA, wE, T)
+    delta = _inner(dA, dE, dA, dE, wA, wE, T) / rr
+    return delta, ri / torch.sqrt(rr * ii)

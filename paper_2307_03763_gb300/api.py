@@ -76,6 +76,8 @@ _SIGNATURES = {
     "gb_loglik_grad": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _I64, _P,
                                       _I64, _P, _P, _P]),
     "gb_mh_independence": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, _I32, _P, _P, _P]),
+    "gb_snr_multi": (ctypes.c_int, [_P, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _I64, _P, _I64, _I32, _P, _P,
+                                    _P, _P]),
     "gb_loglik_rows": (ctypes.c_int, [_P, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _I64, _P, _I64, _P, _P, _P,
                                       _P, _P, _P, _P]),
     "gb_mh_certified": (ctypes.c_int, [_P, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _I64, _P, _P, _P, _P, _I32,
@@ -525,3 +527,27 @@ class Context:
                                           float(eps), int(max_iter), _ptr(logL), _ptr(dh), _ptr(hh), _ptr(chain),
                                           _ptr(acc), _ptr(n_exact), _ptr(pending), _stream(self.device)))
         return chain, acc, logL, dh, hh, n_exact, pending
+
+    def snr_multi(self, windows, dA, dE, wA, wE, theta, kmax=None):
+        """Multi-signal SNR of each window's sources (its candidate rows; see
+        gb_snr_multi): returns rho (n_win,), gram (n_win, kmax, kmax) and
+        dh (n,) = <d|s_i>.  dA, dE may be None (then rho and dh are None)."""
+        nb = wA.shape[0]
+        _need(wA, torch.float64, self.device, "wA", (nb,))
+        _need(wE, torch.float64, self.device, "wE", (nb,))
+        if dA is not None:
+            _need(dA, torch.complex128, self.device, "dA", (nb,))
+            _need(dE, torch.complex128, self.device, "dE", (nb,))
+        n = theta.shape[0] if theta.dim() == 2 else -1
+        _need(theta, torch.float64, self.device, "theta", (n, 8))
+        arr, nw = self._windows(windows)
+        if kmax is None:
+            kmax = max([1] + [int(w[5]) for w in windows])
+        gram = torch.full((nw, kmax, kmax), float("nan"), dtype=torch.float64, device=self.device)
+        rho = dh = None
+        if dA is not None:
+            rho = torch.empty(nw, dtype=torch.float64, device=self.device)
+            dh = torch.zeros(n, dtype=torch.float64, device=self.device)
+        self._check(lib().gb_snr_multi(self._h, arr, nw, _ptr(dA), _ptr(dE), _ptr(wA), _ptr(wE), nb, _ptr(theta), n,
+                                       int(kmax), _ptr(gram), _ptr(dh), _ptr(rho), _stream(self.device)))
+        return rho, gram, dh

@@ -389,4 +389,26 @@ int gb_mh_certified(gb_ctx_t* ctx, const gb_window_t* win, int32_t n_win, const 
     return GB_OK;
 }
 
+int gb_snr_multi(gb_ctx_t* ctx, const gb_window_t* win, int32_t n_win, const double* dA, const double* dE,
+                 const double* wA, const double* wE, int64_t n_bins, const double* theta, int64_t n_rows, int32_t kmax,
+                 double* gram, double* dh, double* rho, void* stream) {
+    if (!ctx) return GB_EINVAL;
+    int64_t total = 0;
+    int rc = check_windows(ctx, "gb_snr_multi", win, n_win, n_bins, n_rows, &total);
+    if (rc != GB_OK) return rc;
+    if (kmax < 1 || kmax > 64) return set_error(ctx, GB_EINVAL, "gb_snr_multi: kmax must be in [1, 64]");
+    for (int i = 0; i < n_win; ++i)
+        if (win[i].n_cand > kmax) return set_error(ctx, GB_EINVAL, "gb_snr_multi: a window holds more than kmax sources");
+    if (n_win == 0) return GB_OK;
+    if (!wA || !wE || !gram || (total > 0 && !theta)) return set_error(ctx, GB_EINVAL, "gb_snr_multi: null pointer");
+    if ((dh || rho) && (!dA || !dE)) return set_error(ctx, GB_EINVAL, "gb_snr_multi: dh and rho need dA and dE");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "gb_snr_multi: cudaSetDevice");
+    const Plan* plan = nullptr;
+    rc = get_plan(ctx, GB_FP64, win, n_win, tile_size(ctx, std::max<int64_t>(total, 1), 4), &plan);
+    if (rc != GB_OK) return rc;
+    return launch_multi_gram(ctx, plan->d_win, n_win, plan->n_max, (dh || rho) ? dA : nullptr, dE, wA, wE, theta,
+                             kmax, gram, dh, rho, (cudaStream_t)stream);
+}
+
 }  // extern "C"

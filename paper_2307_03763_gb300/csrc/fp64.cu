@@ -520,6 +520,123 @@ __global__ void __launch_bounds__(kWarps64 * 32) waveform64_kernel(
     }
 }
 
+// Window inner product <x|y> = (4/T) Re sum_k w_k x_k y_k* of two templates
+// (or data, y) over the window's bins, block-wide in a fixed order.  A
+// template is given by its natural-order buffers (scaled by `sc`) and carrier
+// bin; bins it does not reach count zero.  `red` holds kWarps64 doubles.
+struct WinTpl {
+    const C64* A;
+    const C64* E;
+    long long q;
+    double sc;
+};
+__device__ __forceinline__ C64 tpl_at(const WinTpl& t, int N, long long k) {
+    const long long m = k - (t.q - N / 2);
+    if (m < 0 || m >= N) return {0.0, 0.0};
+    const int idx = (int)((m + N / 2) & (N - 1));
+    return {t.sc * t.A[idx].x, t.sc * t.A[idx].y};
+}
+__device__ __forceinline__ C64 tpl_at_e(const WinTpl& t, int N, long long k) {
+    const long long m = k - (t.q - N / 2);
+    if (m < 0 || m >= N) return {0.0, 0.0};
+    const int idx = (int)((m + N / 2) & (N - 1));
+    return {t.sc * t.E[idx].x, t.sc * t.E[idx].y};
+}
+__device__ double block_sum64(double v, double* red) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < kWarps64; ++w) s += red[w];
+    return s;
+}
+// <x|y> with x a template and y a template (yt) or the data (yt == nullptr)
+__device__ double win_inner(const WinTpl& x, const WinTpl* yt, const gb_window_t& win, const C64* __restrict__ dA,
+                            const C64* __restrict__ dE, const double* __restrict__ wA, const double* __restrict__ wE,
+                            double T, double* red) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < win.W; i += blockDim.x) {
+        const long long k = win.k0 + i;
+        const C64 xa = tpl_at(x, win.N, k), xe = tpl_at_e(x, win.N, k);
+        C64 ya, ye;
+        if (yt) {
+            ya = tpl_at(*yt, win.N, k);
+            ye = tpl_at_e(*yt, win.N, k);
+        } else {
+            ya = dA[win.data_off + i];
+            ye = dE[win.data_off + i];
+        }
+        acc += wA[win.data_off + i] * (xa.x * ya.x + xa.y * ya.y) + wE[win.data_off + i] * (xe.x * ye.x + xe.y * ye.y);
+    }
+    return block_sum64(acc, red) * (4.0 / T);
+}
+
+// Gram matrix G_ij = <s_i|s_j>, b_i = <d|s_i> and the multi-signal SNR
+// rho = sum_i b_i / sqrt(sum_ij G_ij) (Eq. 11) of each window's sources (one
+// CTA per window; the sources are the window's candidate rows).  Template i
+// is held in buffer P while the templates j > i pass through buffer Q.
+__global__ void __launch_bounds__(kWarps64 * 32) multi_gram_kernel(
+    const gb_window_t* __restrict__ wins, TabSet64 tabs, const C64* __restrict__ tw_g, double T, double fstar,
+    const C64* __restrict__ dA, const C64* __restrict__ dE, const double* __restrict__ wA,
+    const double* __restrict__ wE, const double* __restrict__ theta, int kmax, double* __restrict__ gram,
+    double* __restrict__ dh_out, double* __restrict__ rho_out, int* status, int n_max) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C64* tw = (C64*)smem_raw;                   // kTwiddles
+    double* red = (double*)(tw + kTwiddles);    // kWarps64
+    Cand64* cand = (Cand64*)(red + kWarps64);   // 2
+    C64* PA = (C64*)(cand + 2);                 // 4 buffers of n_max
+    C64* PE = PA + n_max;
+    C64* QA = PE + n_max;
+    C64* QE = QA + n_max;
+    const gb_window_t win = wins[blockIdx.x];
+    const int K = win.n_cand;
+    double* G = gram + (size_t)blockIdx.x * kmax * kmax;
+    for (int i = threadIdx.x; i < kTwiddles; i += blockDim.x) tw[i] = tw_g[i];
+    const Geo64 g = geometry64(win.N, T, fstar);
+    const OrbitTables64 tab = tabs.t[g.logN - 5];
+    const bool data = dA != nullptr;
+    double sum_b = 0.0, sum_g = 0.0;
+    bool bad_any = false;
+    for (int i = 0; i < K; ++i) {
+        __syncthreads();
+        if (threadIdx.x == 0) setup64(theta + 8 * (win.cand_off + i), T, g.inv_fstar, cand[0]);
+        __syncthreads();
+        const bool bad_i = cand[0].bad;
+        if (!bad_i) template64_dispatch<kWarps64 * 32>(cand[0], g, tab, tw, PA, PE, nullptr, threadIdx.x);
+        __syncthreads();
+        const WinTpl P{PA, PE, cand[0].q, g.scale};
+        const double gii = bad_i ? nan("") : win_inner(P, &P, win, dA, dE, wA, wE, T, red);
+        const double bi = bad_i || !data ? nan("") : win_inner(P, nullptr, win, dA, dE, wA, wE, T, red);
+        if (threadIdx.x == 0) {
+            G[i * kmax + i] = gii;
+            if (dh_out) dh_out[win.cand_off + i] = bi;
+            if (bad_i) atomicOr(status, kStatusNonFinite);
+            sum_b += bi;
+            sum_g += gii;
+            bad_any |= bad_i;
+        }
+        for (int j = i + 1; j < K; ++j) {
+            __syncthreads();
+            if (threadIdx.x == 0) setup64(theta + 8 * (win.cand_off + j), T, g.inv_fstar, cand[1]);
+            __syncthreads();
+            const bool bad_j = cand[1].bad;
+            if (!bad_j) template64_dispatch<kWarps64 * 32>(cand[1], g, tab, tw, QA, QE, nullptr, threadIdx.x);
+            __syncthreads();
+            const WinTpl Q{QA, QE, cand[1].q, g.scale};
+            const double gij = bad_i || bad_j ? nan("") : win_inner(P, &Q, win, dA, dE, wA, wE, T, red);
+            if (threadIdx.x == 0) {
+                G[i * kmax + j] = gij;
+                G[j * kmax + i] = gij;
+                sum_g += 2.0 * gij;
+            }
+        }
+    }
+    if (threadIdx.x == 0 && rho_out)
+        rho_out[blockIdx.x] = (K == 0 || bad_any || !data) ? nan("") : sum_b / sqrt(sum_g);
+}
+
 }  // namespace
 
 static size_t smem64_loglik(int n_max, int nch) {
@@ -582,6 +699,23 @@ int launch_waveform_fp64(gb_ctx* ctx, const double* theta, int64_t B, int N, dou
     ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "waveform64 launch");
+    return GB_OK;
+}
+
+int launch_multi_gram(gb_ctx* ctx, const gb_window_t* d_win, int n_win, int n_max, const double* dA,
+                      const double* dE, const double* wA, const double* wE, const double* theta, int kmax,
+                      double* gram, double* dh, double* rho, cudaStream_t s) {
+    if (n_win == 0) return GB_OK;
+    const size_t smem = sizeof(C64) * kTwiddles + sizeof(double) * kWarps64 + sizeof(Cand64) * 2 +
+                        sizeof(C64) * 4 * (size_t)n_max;
+    cudaError_t e = cudaFuncSetAttribute(multi_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "multi_gram: smem attribute");
+    multi_gram_kernel<<<n_win, kWarps64 * 32, smem, s>>>(d_win, tabset64(ctx), (const C64*)ctx->d_tw64, ctx->obs.T_obs,
+                                                         transfer_frequency(ctx), (const C64*)dA, (const C64*)dE, wA,
+                                                         wE, theta, kmax, gram, dh, rho, ctx->d_status, n_max);
+    ++ctx->launches;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(ctx, e, "multi_gram launch");
     return GB_OK;
 }
 

@@ -265,6 +265,10 @@ int launch_mh_flip(gb_ctx* ctx, const CertScratch& cs, int32_t n_chains, int32_t
                    const int32_t* chain_idx, int pass, cudaStream_t st);
 // out[r] = sum of cnt[p][r] over the first n_pass passes (mh.cu)
 int launch_sum_rows(gb_ctx* ctx, const int* cnt, int32_t n_chains, int n_pass, int32_t* out, cudaStream_t st);
+// Gram matrices, <d|s_i> and multi-signal SNRs of each window's sources (fp64.cu)
+int launch_multi_gram(gb_ctx* ctx, const gb_window_t* d_win, int n_win, int n_max, const double* dA,
+                      const double* dE, const double* wA, const double* wE, const double* theta, int kmax,
+                      double* gram, double* dh, double* rho, cudaStream_t s);
 int launch_waveform_fp64(gb_ctx* ctx, const double* theta, int64_t B, int N, double* hA,
                          double* hE, double* hT, int64_t* q, cudaStream_t s);
 int launch_loglik_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const double* dE,

@@ -16,7 +16,10 @@ def api():
 
 def test_fullband_narrow_band(api):
     # 400 binaries over 2-2.6 mHz (416 windows): by chance a recovery would sit
-    # within a bin of an injected source about 2% of the time
+    # within a bin of an injected source about 2% of the time.  Scored by the
+    # paper's match metrics (Sec. IV): measured 39% of recoveries with
+    # delta < 0.3 and 39% with overlap > 0.9, 201 of the 354 injections above
+    # SNR 10 matched (Gaussian posteriors, all windows at once)
     from paper_2307_03763_gb300 import fullband
     ctx = api.Context(2 * wk.YEAR)
     for post, scheme, noise in (("gauss", "all", "true"), ("kde", "all", "true"), ("gauss", "evenodd", "median")):
@@ -27,3 +30,11 @@ def test_fullband_narrow_band(api):
         assert st["within_1_bin"] >= 0.15 and st["within_3_bins"] >= 0.3, st
         assert st["posteriors"] == st["recovered"]
         assert st["median_accept_rate"] > 0.0, st
+        if noise == "true":
+            assert st["delta_lt_0.3"] >= 0.25 and st["overlap_gt_0.9"] >= 0.25, st
+            assert st["matched_injected_delta_lt_0.3"] >= 120, st
+        if post == "gauss" and scheme == "all":
+            # posteriors at the joint estimates on d - sum of the window's other
+            # sources: measured 49% median acceptance (20% without the joint refit)
+            assert st["median_accept_rate"] >= 0.3, st
+            assert st["windows_with_several_sources"] > 50 and st["joint_snr_median"] > 10.0, st

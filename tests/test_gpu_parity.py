@@ -468,8 +468,9 @@ def test_autotune_keeps_results(api, prec):
         assert t["tile"] in (0, 16, 32, 64, 128)
 
 
-def test_grad_fp64_matches_oracle(ctx):
-    wl = wk.tiny_window(n_cand=24)
+@pytest.mark.parametrize("N", [32, 64, 128])
+def test_grad_fp64_matches_oracle(ctx, N):
+    wl = wk.tiny_window(n_cand=24, N=N)
     dA, dE = _data.inject(wl)
     th = wl.theta.copy()
     args = (_cuda(dA, torch.complex128), _cuda(dE, torch.complex128), _cuda(wl.w_A, torch.float64),
@@ -483,6 +484,45 @@ def test_grad_fp64_matches_oracle(ctx):
         gn, on = gg[b] * sb, go[b] * sb
         assert float((gn - on).abs().max()) <= 1e-9 * float(on.abs().sum()), (b, gn, on)
     assert ((lg - lo).abs() <= 1e-10 * lo.abs()).all()
+
+
+@pytest.mark.parametrize("N,f0", [(64, 0.9e-3), (128, 1.5e-3), (256, 4.5e-3), (1024, 1.6e-2)])
+def test_grad_fp64_matches_central_differences(ctx, N, f0):
+    # the adjoint FP64 gradient against central differences of the FP64
+    # likelihood itself, steps of 1e-6 of each parameter's natural scale
+    # (1/T, 1/T^2, rad, A), at candidates whose carrier bin q stays fixed
+    # under the steps; bar 1e-6 of the gradient's norm (natural units)
+    rng = np.random.default_rng(N)
+    T = T2
+    src = wk.source(f0, float(wk.chirp_fdot(f0, 0.5)), 5e-22, rng)
+    kc = int(math.floor((src[0] + 0.5 * src[1] * T) * T + 0.5))
+    wins, _, _ = wk.layout([(kc - N // 2, N, N)], [8])
+    nA, nE, wA, wE = wk.noise_and_weights(wins, T, rng)
+    half = np.array([3.0 / T, abs(src[1]), 0.1, 0.1, 0.1 * src[4], 0.1, 0.1, 0.1])
+    th = wk.uniform_box(src, half, 64, rng)
+    frac = (th[:, 0] * T + 0.5 * th[:, 1] * T * T + 0.5) % 1.0
+    th = th[(frac > 1e-3) & (frac < 1 - 1e-3)][:8]          # q fixed under the steps
+    wl = wk.Workload("fd", T, wins, nA, nE, wA, wE, [[src]], th)
+    dA, dE = _data.inject(wl)
+    data = (_cuda(dA, torch.complex128), _cuda(dE, torch.complex128), _cuda(wA, torch.float64),
+            _cuda(wE, torch.float64))
+    nb = th.shape[0]
+    _, gg = (x.cpu() for x in ctx.loglik_grad([(wins[0][0], N, N, 0, 0, nb)], *data, _cuda(th, torch.float64),
+                                              prec="fp64"))
+    scale = np.stack([np.array([1 / T, 1 / T ** 2, 1, 1, th[b, 4], 1, 1, 1]) for b in range(nb)])
+    pts = []
+    for i in range(8):
+        for sgn in (1.0, -1.0):
+            t = th.copy()
+            t[:, i] += sgn * 1e-6 * scale[:, i]
+            pts.append(t)
+    allp = np.concatenate(pts)
+    l, _, _ = ctx.loglik([(wins[0][0], N, N, 0, 0, allp.shape[0])], *data, _cuda(allp, torch.float64), prec="fp64")
+    l = l.cpu().numpy().reshape(8, 2, nb)
+    fd = (l[:, 0] - l[:, 1]).T / 2e-6                        # d logL / d(theta_i / scale_i)
+    adj = gg.numpy() * scale
+    for b in range(nb):
+        assert np.max(np.abs(adj[b] - fd[b])) <= 1e-6 * np.sum(np.abs(fd[b])), (b, adj[b], fd[b])
 
 
 def test_autograd_function_uses_the_adjoint(ctx):

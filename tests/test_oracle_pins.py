@@ -558,3 +558,89 @@ def test_cpu_fft_baseline_loglik_equals_oracle():
     b = cpu_fft.loglik_fft(wl.windows, dA, dE, wl.w_A, wl.w_E, wl.theta, wl.T)
     for x, y in zip(a, b):
         assert torch.allclose(x, y, rtol=1e-10, atol=1e-10 * float(a[2].abs().max()))
+
+
+# --------------------------------------------------------------------------
+# multi-signal SNR (Eq. 11) and the match metrics (Eqs. 19-20)
+# --------------------------------------------------------------------------
+
+def _multi_window(seed, f0s, N=256, W=None, A=3e-22):
+    """One wide window holding sources at f0s (all inside it), noise + sources."""
+    rng = np.random.default_rng(seed)
+    T = T2
+    srcs = [wk.source(f, 1e-18, A, rng) for f in f0s]
+    kc = int(round(np.mean(f0s) * T))
+    W = W or N
+    wins, _, _ = wk.layout([(kc - W // 2, W, N)], [len(srcs)])
+    nA, nE, wA, wE = wk.noise_and_weights(wins, T, rng)
+    wl = wk.Workload("multi", T, wins, nA, nE, wA, wE, [srcs], np.array(srcs))
+    dA, dE = _data.inject(wl)
+    return wl, dA, dE
+
+
+def test_snr_multi_single_source_is_eq6():
+    wl, dA, dE = _multi_window(41, [2.0e-3])
+    rho, G, b = gb.snr_multi(wl.windows, dA, dE, wl.w_A, wl.w_E, wl.theta, wl.T)
+    _, dh, hh = gb.loglik(wl.windows, dA, dE, wl.w_A, wl.w_E, wl.theta, wl.T)
+    assert torch.allclose(rho, gb.snr(dh, hh), rtol=1e-12, atol=0)
+    assert torch.allclose(G[0][0, 0], hh[0], rtol=1e-12) and torch.allclose(b, dh, rtol=1e-12)
+
+
+def test_snr_multi_of_disjoint_templates_adds_the_parts():
+    # two sources 300 bins apart in a 1024-bin window, templates of N = 128:
+    # no common bins, so <S|S> = hh1 + hh2 and <d|S> = dh1 + dh2 exactly
+    T = T2
+    f1 = 3.0e-3
+    f2 = f1 + 300.0 / T
+    wl, dA, dE = _multi_window(42, [f1, f2], N=128, W=1024)
+    rho, G, b = gb.snr_multi(wl.windows, dA, dE, wl.w_A, wl.w_E, wl.theta, wl.T)
+    _, dh, hh = gb.loglik(wl.windows, dA, dE, wl.w_A, wl.w_E, wl.theta, wl.T)
+    assert float(G[0][0, 1]) == 0.0 and float(G[0][1, 0]) == 0.0
+    assert torch.allclose(rho[0], dh.sum() / torch.sqrt(hh.sum()), rtol=1e-12)
+
+
+def test_snr_multi_overlapping_sources_properties():
+    # two sources 2 bins apart: the cross term matters; Gram symmetric with the
+    # single-source <h|h> on its diagonal and 1^T G 1 = <S|S>; a duplicated
+    # source gives the single-source SNR; a common amplitude scale cancels
+    T = T2
+    wl, dA, dE = _multi_window(43, [2.5e-3, 2.5e-3 + 2.0 / T])
+    rho, G, b = gb.snr_multi(wl.windows, dA, dE, wl.w_A, wl.w_E, wl.theta, wl.T)
+    _, dh, hh = gb.loglik(wl.windows, dA, dE, wl.w_A, wl.w_E, wl.theta, wl.T)
+    G = G[0]
+    assert torch.allclose(G, G.T, rtol=1e-13, atol=0)
+    assert torch.allclose(torch.diagonal(G), hh, rtol=1e-12)
+    assert abs(float(G[0, 1])) > 1e-3 * float(hh.min())
+    assert torch.allclose(rho[0], b.sum() / torch.sqrt(G.sum()), rtol=1e-12)
+    one = [(w[0], w[1], w[2], w[3], 0, 1) for w in wl.windows]
+    dup = np.stack([wl.theta[0], wl.theta[0]])
+    r1, _, _ = gb.snr_multi(one, dA, dE, wl.w_A, wl.w_E, wl.theta[:1], wl.T)
+    r2, _, _ = gb.snr_multi(wl.windows, dA, dE, wl.w_A, wl.w_E, dup, wl.T)
+    assert torch.allclose(r1, r2, rtol=1e-12)
+    sc = wl.theta.copy()
+    sc[:, 4] *= 3.7
+    r3, _, _ = gb.snr_multi(wl.windows, dA, dE, wl.w_A, wl.w_E, sc, wl.T)
+    assert torch.allclose(rho, r3, rtol=1e-12)
+
+
+def test_match_metrics_closed_forms():
+    # the template is linear in A and carries phi0 as the factor exp(i phi0):
+    # A doubled -> delta = 1/4, O = 1; phi0 + pi -> delta = 4, O = -1;
+    # phi0 + pi/2 -> delta = 2, O = 0; itself -> 0, 1
+    wl, dA, dE = _multi_window(44, [1.8e-3])
+    th = wl.theta[0]
+    win = wl.windows[0]
+    d, o = gb.match_metrics(win, wl.w_A, wl.w_E, th, th, wl.T)
+    assert abs(float(d)) < 1e-14 and abs(float(o) - 1) < 1e-14
+    t2 = th.copy()
+    t2[4] *= 2.0
+    d, o = gb.match_metrics(win, wl.w_A, wl.w_E, t2, th, wl.T)
+    assert abs(float(d) - 0.25) < 1e-12 and abs(float(o) - 1) < 1e-12
+    t3 = th.copy()
+    t3[7] += math.pi
+    d, o = gb.match_metrics(win, wl.w_A, wl.w_E, t3, th, wl.T)
+    assert abs(float(d) - 4.0) < 1e-11 and abs(float(o) + 1) < 1e-12
+    t4 = th.copy()
+    t4[7] += 0.5 * math.pi
+    d, o = gb.match_metrics(win, wl.w_A, wl.w_E, t4, th, wl.T)
+    assert abs(float(d) - 2.0) < 1e-11 and abs(float(o)) < 1e-11
