@@ -563,6 +563,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=None, help="timed steps of the FP64 path (default: steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="time the steps with eager launches, not graph replays")
     ap.add_argument("--workload", default="posterior", choices=["posterior", "tiny", "band", "population", "fullband"],
                     help="posterior: the headline step; the others print their own figures")
     ap.add_argument("--fb-sources", type=int, default=200000, help="fullband: injected binaries")
@@ -637,20 +638,51 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
-    def timed(prec, steps):
+    pmax = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def captured(prec):
+        """One step of `prec` captured in a CUDA graph (after eager warm-up
+        calls that size the library's scratch), and the library kernels it
+        launches.  The certified step also folds its pending word into a
+        running maximum, so that every replay's certification is checked."""
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            for _ in range(2):
+                step(prec)
+        stream.wait_stream(side)
+        torch.cuda.synchronize(dev)
+        g = torch.cuda.CUDAGraph()
+        n0 = ctx.launch_count()
+        with torch.cuda.graph(g, stream=side):
+            if prec == "certified":
+                certified(0)
+                torch.maximum(pmax, pend[0:1], out=pmax)
+            else:
+                step(prec)
+        torch.cuda.synchronize(dev)
+        return g, ctx.launch_count() - n0
+
+    def timed(prec, steps, graph=False):
         """Per-step CUDA-event times (ms) of the step and, for the plain
-        precisions, of the likelihood launch alone."""
+        precisions run eagerly, of the likelihood launch alone."""
+        g = None
+        if graph:
+            g, per_step = captured(prec)
         for _ in range(args.warmup):
-            step(prec)
+            g.replay() if g is not None else step(prec)
         barrier()
-        st, kt = [], []
+        st = []
         n0 = ctx.launch_count()
         torch.cuda.nvtx.range_push(f"timed_{prec}")   # lets a profiler select the timed launches
         for k in range(steps):
             flush.zero_()                      # L2 flush between timed steps
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             e0.record(stream)
-            if prec == "certified":
+            if g is not None:
+                g.replay()
+                e1.record(stream)
+            elif prec == "certified":
                 certified(k)
                 e1.record(stream)
             else:
@@ -660,7 +692,7 @@ def main():
             e2.record(stream)
             st.append((e0, e1, e2))
         torch.cuda.nvtx.range_pop()
-        launches = ctx.launch_count() - n0
+        launches = per_step * steps if g is not None else ctx.launch_count() - n0
         barrier()
         step_ms = [a.elapsed_time(c) for a, b, c in st]
         kern_ms = [a.elapsed_time(b) for a, b, c in st]
@@ -703,14 +735,17 @@ def main():
     # the sampling interval)
     clocks = ClockSampler(dev.index)
     clocks.start()
-    tot_c, _, launches_c = timed("certified", args.steps)
-    pend_max = int(pend[:args.steps].max())
-    exact_rows = n_exact[:args.steps].sum(1).double()
-    tot_mx, kern_mx, _ = timed("mixed", args.steps)
+    graphs = not args.no_graph
+    pmax.zero_()
+    tot_c, _, launches_c = timed("certified", args.steps, graph=graphs)
+    pend_max = int(pmax.item()) if graphs else int(pend[:args.steps].max())
+    exact_rows = n_exact[:1].sum(1).double() if graphs else n_exact[:args.steps].sum(1).double()
+    tot_mxg, _, _ = timed("mixed", args.steps, graph=graphs)
+    tot_mx, kern_mx, _ = timed("mixed", args.steps)          # eager: the likelihood launch's own events
     fp64_steps = args.fp64_steps or max(3, args.steps // 10)
     tot_64, kern_64, _ = timed("fp64", fp64_steps)
     clk = clocks.stop()
-    tot_c, tot_mx, tot_64 = max_over_ranks(tot_c), max_over_ranks(tot_mx), max_over_ranks(tot_64)
+    tot_c, tot_mx, tot_mxg, tot_64 = (max_over_ranks(x) for x in (tot_c, tot_mx, tot_mxg, tot_64))
 
     # end to end through the public API with host buffers: proposals and their
     # log g, log u (and the window data) copied in from pinned memory each
@@ -789,7 +824,7 @@ def main():
         return
     evals = wl.n_cand * world
     value = evals * args.steps / (tot_c / 1e3)
-    value_mx = evals * args.steps / (tot_mx / 1e3)
+    value_mx = evals * args.steps / (tot_mxg / 1e3)
     value64 = evals * fp64_steps / (tot_64 / 1e3)
     ms_step = tot_c / args.steps
     f_mid = np.array([w[0] + w[1] / 2 for w in wl.windows]) / wl.T
@@ -855,6 +890,7 @@ def main():
         "vs_baseline": None, "dtype": "f32+f64-phase", "data": "synthetic",
         "config": {"workload": WORKLOAD, "global_batch": evals, "windows": nwin, "proposals_per_window": n,
                    "l2": "flushed between timed steps (2x L2 buffer written)", "parallelism": "replicas",
+                   "launch": "each timed step replayed from a CUDA graph" if graphs else "eager launches",
                    "step": "gb_mh_certified: mixed-precision logL of every proposal, the chains, FP64 "
                            "re-evaluation of the proposals whose decision the mixed error bound cannot settle"},
         "s_per_10k_posterior": ms_step / 1e3 / nwin,
@@ -862,10 +898,11 @@ def main():
                       "eps": api.MIXED_EPS, "max_iter": MAX_ITER, "pending_max_over_steps": pend_max,
                       "rows_reevaluated_per_step": float(exact_rows.mean()),
                       "reevaluated_fraction": float(exact_rows.mean()) / evals,
-                      "added_ms_per_step": ms_step - tot_mx / args.steps},
-        "mixed_uncertified": {"value": value_mx, "unit": UNIT, "ms_per_step": tot_mx / args.steps,
+                      "added_ms_per_step": ms_step - tot_mxg / args.steps},
+        "mixed_uncertified": {"value": value_mx, "unit": UNIT, "ms_per_step": tot_mxg / args.steps,
+                              "eager_ms_per_step": tot_mx / args.steps,
                               "loglik_ms": kern_mx, "mh_ms": tot_mx / args.steps - kern_mx,
-                              "s_per_10k_posterior": tot_mx / args.steps / 1e3 / nwin},
+                              "s_per_10k_posterior": tot_mxg / args.steps / 1e3 / nwin},
         "annealed_posterior_6T": annealed,
         "annealed_posterior_6T_kde": annealed_kde,
         "fp64": {"value": value64, "unit": UNIT, "steps": fp64_steps, "ms_per_step": tot_64 / fp64_steps,

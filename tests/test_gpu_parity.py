@@ -510,16 +510,23 @@ def test_grad_fp64_matches_central_differences(ctx, N, f0):
     _, gg = (x.cpu() for x in ctx.loglik_grad([(wins[0][0], N, N, 0, 0, nb)], *data, _cuda(th, torch.float64),
                                               prec="fp64"))
     scale = np.stack([np.array([1 / T, 1 / T ** 2, 1, 1, th[b, 4], 1, 1, 1]) for b in range(nb)])
-    pts = []
+    pts, h = [], np.empty((8, nb))
     for i in range(8):
-        for sgn in (1.0, -1.0):
-            t = th.copy()
-            t[:, i] += sgn * 1e-6 * scale[:, i]
-            pts.append(t)
+        tp, tm = th.copy(), th.copy()
+        tp[:, i] += 1e-6 * scale[:, i]
+        tm[:, i] -= 1e-6 * scale[:, i]
+        pts += [tp, tm]
+        # the step actually taken, from the doubles.  f0 enters the phase
+        # through delta = fl(f0 T) - q (all but ~1e-5 of d logL/d f0), and
+        # f0 T ~ 1e5 is rounded to ~1e-11 cycles, so for f0 the step is the
+        # change of the rounded product fl(f0 T) (IEEE products, as the kernel's)
+        h[i] = (tp[:, i] - tm[:, i]) / scale[:, i]
+        if i == 0:
+            h[i] = tp[:, 0] * T - tm[:, 0] * T
     allp = np.concatenate(pts)
     l, _, _ = ctx.loglik([(wins[0][0], N, N, 0, 0, allp.shape[0])], *data, _cuda(allp, torch.float64), prec="fp64")
     l = l.cpu().numpy().reshape(8, 2, nb)
-    fd = (l[:, 0] - l[:, 1]).T / 2e-6                        # d logL / d(theta_i / scale_i)
+    fd = ((l[:, 0] - l[:, 1]) / h).T                         # d logL / d(theta_i / scale_i)
     adj = gg.numpy() * scale
     for b in range(nb):
         assert np.max(np.abs(adj[b] - fd[b])) <= 1e-6 * np.sum(np.abs(fd[b])), (b, adj[b], fd[b])
