@@ -841,19 +841,18 @@ __device__ __forceinline__ void kahan_merge(f2 sum, f2 comp, float& s, float& c)
     c = (comp.x + comp.y) - e;
 }
 
-// Both channels of one candidate (buf: N channel-pair elements, sample n at
-// n): transform, then the window inner products (with IM also the imaginary
-// part of sum w d conj(h)); each sum is returned as s - c.  With ONE, the
-// samples are read from src (one complex float each, the second channel
-// zero) and buf is only the transform's workspace.
-template <int R, bool IM, bool ONE = false>
-__device__ void fft_inner_ch(float4* buf, const OrbitTables32& tab, const LaneTw& ltw, int lane, int off, int W,
-                             const Win32* __restrict__ pw, float& sdh, float& cdh, float& shh, float& chh, float& sim,
-                             float& cim, const float2* src = nullptr) {
+// Transform of both channels of one candidate (buf: N channel-pair elements,
+// sample n at n; with ONE the samples are read from src, one complex float
+// each, the second channel zero, and buf is only the workspace).  On return
+// x[q] holds the DFT at index K(q) = bin_of<R>(kbase, q) (returned: kbase),
+// and the transform is done with buf.
+template <int R, bool ONE = false>
+__device__ __forceinline__ int nat_transform(float4* buf, const OrbitTables32& tab, const LaneTw& ltw, int lane,
+                                             cpair (&x)[R], const float2* src = nullptr) {
     constexpr int N = 32 * R, G = 32 / R;
     constexpr int LG = G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 8 ? 3 : G == 16 ? 4 : 5;
+    (void)N;
     const int g = lane / G, j = lane % G;
-    cpair x[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         if constexpr (ONE) {
@@ -940,14 +939,35 @@ __device__ void fft_inner_ch(float4* buf, const OrbitTables32& tab, const LaneTw
     } else {
         kbase = g;   // G = 1: + R ka for x[ka]
     }
+    return kbase;
+}
+
+// DFT index of x[q] after nat_transform
+template <int R>
+__device__ __forceinline__ int bin_of(int kbase, int q) {
+    constexpr int G = 32 / R;
+    if constexpr (R == 4) return kbase + 16 * q;
+    else if constexpr (R >= G && G > 1) return kbase + R * (q / G) + R * R * (q % G);
+    else return kbase + R * q;
+}
+
+// Both channels of one candidate (buf: N channel-pair elements, sample n at
+// n): transform, then the window inner products (with IM also the imaginary
+// part of sum w d conj(h)); each sum is returned as s - c.  With ONE, the
+// samples are read from src (one complex float each, the second channel
+// zero) and buf is only the transform's workspace.
+template <int R, bool IM, bool ONE = false>
+__device__ void fft_inner_ch(float4* buf, const OrbitTables32& tab, const LaneTw& ltw, int lane, int off, int W,
+                             const Win32* __restrict__ pw, float& sdh, float& cdh, float& shh, float& chh, float& sim,
+                             float& cim, const float2* src = nullptr) {
+    constexpr int N = 32 * R;
+    cpair x[R];
+    const int kbase = nat_transform<R, ONE>(buf, tab, ltw, lane, x, src);
     const f2 z = bc(0.0f);
     f2 s_dh = z, c_dh = z, s_hh = z, c_hh = z, s_im = z, c_im = z;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-        int K;
-        if constexpr (R == 4) K = kbase + 16 * q;
-        else if constexpr (R >= G && G > 1) K = kbase + R * (q / G) + R * R * (q % G);
-        else K = kbase + R * q;
+        const int K = bin_of<R>(kbase, q);
         const int m = K < N / 2 ? K : K - N;
         const int kk = off + m;
         if (kk >= 0 && kk < W) {

@@ -342,14 +342,18 @@ __device__ __forceinline__ void sample_adjoint(const CandGx& g, const OrbitTable
 // The sample adjoints of one candidate: lane l takes the sample pairs
 // (l + 64 m, l + 64 m + 32) (cA, cE, cT: the adjoint transform's output c^_n;
 // cT may be null in the T instantiation, for windows without T).  Sums are
-// compensated per lane and sample slot, then merged.
-template <int J, bool T3 = false>
+// per lane and sample slot, then merged exactly (two-sum of the slots).
+// PACKED: the cotangents of both channels come from one array of
+// channel-pair elements (A re, E re, A im, E im) at sample n (cA; cE unused).
+template <int J, bool T3 = false, bool PACKED = false>
 __device__ void adjoint_sweep(const CandGx& g, const OrbitTables32& tab, int N, float Tf, float inv_fstar,
                               const float2* cA, const float2* cE, int lane, float (&tacc)[KT][2],
                               float (&vp)[2][2], float (&vq)[2][2], const float2* cT = nullptr) {
-    f2 sum[KT + 4], comp[KT + 4];
+    // per-lane plain sums: a lane adds N/64 terms; the warp reduction after
+    // the sweep is compensated
+    f2 sum[KT + 4];
 #pragma unroll
-    for (int k = 0; k < KT + 4; ++k) sum[k] = comp[k] = bc(0.0f);
+    for (int k = 0; k < KT + 4; ++k) sum[k] = bc(0.0f);
     for (int n0 = lane; n0 < N; n0 += 64) {
         // N = 32: the second slot repeats sample n0 with zero cotangents
         const bool two = n0 + 32 < N;
@@ -358,24 +362,35 @@ __device__ void adjoint_sweep(const CandGx& g, const OrbitTables32& tab, int N, 
             const float2 x = b[n0], y = two ? b[n1] : make_float2(0.0f, 0.0f);
             return cpair{make_float2(x.x, y.x), make_float2(x.y, y.y)};
         };
-        const cpair a = ld(cA), e = ld(cE), t = (T3 && cT) ? ld(cT) : cpair{bc(0.0f), bc(0.0f)};
+        cpair a, e;
+        if constexpr (PACKED) {
+            const float4* b4 = (const float4*)cA;
+            const float4 x = b4[n0], y = two ? b4[n1] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            a = cpair{make_float2(x.x, y.x), make_float2(x.z, y.z)};
+            e = cpair{make_float2(x.y, y.y), make_float2(x.w, y.w)};
+        } else {
+            a = ld(cA);
+            e = ld(cE);
+        }
+        const cpair t = (T3 && cT) ? ld(cT) : cpair{bc(0.0f), bc(0.0f)};
         f2 dth[KT] = {bc(0.0f), bc(0.0f), bc(0.0f), bc(0.0f)};
         cpair up{bc(0.0f), bc(0.0f)}, uq{bc(0.0f), bc(0.0f)};
         sample_adjoint<J, T3>(g, tab, N, n0, n1, Tf, inv_fstar, a, e, t, dth, up, uq);
 #pragma unroll
-        for (int k = 0; k < KT; ++k) kahan_add2(sum[k], comp[k], dth[k]);
+        for (int k = 0; k < KT; ++k) sum[k] = padd(sum[k], dth[k]);
         // V = sum c conj(P) = conj(U_P)
-        kahan_add2(sum[KT], comp[KT], up.re);
-        kahan_add2(sum[KT + 1], comp[KT + 1], pneg(up.im));
-        kahan_add2(sum[KT + 2], comp[KT + 2], uq.re);
-        kahan_add2(sum[KT + 3], comp[KT + 3], pneg(uq.im));
+        sum[KT] = padd(sum[KT], up.re);
+        sum[KT + 1] = psub(sum[KT + 1], up.im);
+        sum[KT + 2] = padd(sum[KT + 2], uq.re);
+        sum[KT + 3] = psub(sum[KT + 3], uq.im);
     }
+    const f2 z = bc(0.0f);
 #pragma unroll
-    for (int k = 0; k < KT; ++k) kahan_merge(sum[k], comp[k], tacc[k][0], tacc[k][1]);
-    kahan_merge(sum[KT], comp[KT], vp[0][0], vp[0][1]);
-    kahan_merge(sum[KT + 1], comp[KT + 1], vp[1][0], vp[1][1]);
-    kahan_merge(sum[KT + 2], comp[KT + 2], vq[0][0], vq[0][1]);
-    kahan_merge(sum[KT + 3], comp[KT + 3], vq[1][0], vq[1][1]);
+    for (int k = 0; k < KT; ++k) kahan_merge(sum[k], z, tacc[k][0], tacc[k][1]);
+    kahan_merge(sum[KT], z, vp[0][0], vp[0][1]);
+    kahan_merge(sum[KT + 1], z, vp[1][0], vp[1][1]);
+    kahan_merge(sum[KT + 2], z, vq[0][0], vq[0][1]);
+    kahan_merge(sum[KT + 3], z, vq[1][0], vq[1][1]);
 }
 
 // Forward FFT of R register values per lane: on entry lane l holds input
@@ -524,6 +539,49 @@ __device__ void residual_adjoint2(float2* bufA, float2* bufE, const OrbitTables3
     __syncwarp();
 }
 
+// Both channels at once in natural order, with the likelihood kernel's
+// transform (buf: N channel-pair elements, sample n at n, from the packed
+// slow part): forward transform and window inner products as the likelihood
+// kernel forms them, the conjugated residual conj(w^ (d^ - kappa S)) stored at
+// its DFT index, the same transform again (the adjoint, conjugated), and
+// c^_n left at sample n, each as a channel-pair element.  Sums are joined
+// into (sdh, cdh) and (shh, chh).
+template <int R>
+__device__ void residual_adjoint_nat(float4* buf, const OrbitTables32& tab, const LaneTw& ltw, int lane, int off,
+                                     int W, const Win32* __restrict__ pw, float kappa, float& sdh, float& cdh,
+                                     float& shh, float& chh) {
+    constexpr int N = 32 * R;
+    cpair x[R];
+    int kbase = nat_transform<R>(buf, tab, ltw, lane, x);
+    f2 s_dh = bc(0.0f), c_dh = bc(0.0f), s_hh = bc(0.0f), c_hh = bc(0.0f);
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int K = bin_of<R>(kbase, q);
+        const int m = K < N / 2 ? K : K - N;
+        const int kk = off + m;
+        cpair rc{bc(0.0f), bc(0.0f)};
+        if (kk >= 0 && kk < W) {
+            const Win32 v = pw[kk];
+            kahan_add2(s_dh, c_dh, pmul(v.w, pfma(v.dre, x[q].re, pmul(v.dim, x[q].im))));
+            kahan_add2(s_hh, c_hh, pmul(v.w, pfma(x[q].re, x[q].re, pmul(x[q].im, x[q].im))));
+            rc = cpair{pmul(v.w, pfma(bc(-kappa), x[q].re, v.dre)), pneg(pmul(v.w, pfma(bc(-kappa), x[q].im, v.dim)))};
+        }
+        st4(buf + K, rc);
+    }
+    float ps, pc;
+    kahan_merge(s_dh, c_dh, ps, pc);
+    kahan_join(sdh, cdh, ps, pc);
+    kahan_merge(s_hh, c_hh, ps, pc);
+    kahan_join(shh, chh, ps, pc);
+    __syncwarp();
+    kbase = nat_transform<R>(buf, tab, ltw, lane, x);
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < R; ++q) st4(buf + bin_of<R>(kbase, q), cpair{x[q].re, pneg(x[q].im)});   // c^_n
+    __syncwarp();
+}
+
 // resident CTAs per SM the N <= 256 instantiation is compiled for (register cap)
 #ifndef GB_GRAD_MINB
 #define GB_GRAD_MINB 2
@@ -576,7 +634,37 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_GRAD_MINB : 1) g
             const CandGx& g = cands[i];
             float sdh = 0.0f, cdh = 0.0f, shh = 0.0f, chh = 0.0f;
             float tacc[KT][2] = {}, vp[2][2] = {}, vq[2][2] = {};
-            if (!g.m.bad) {
+            // N <= 256 without T data (every window of the plain instantiation): the
+            // packed slow part in natural order and the likelihood kernel's transform
+            bool packed_done = false;
+            if constexpr (RMAX <= 8) {
+              if (!g.m.bad && !useT) {
+                packed_done = true;
+                slow_part_dispatch<true>(g.m, tab, N, bufA, bufE, lane);
+                __syncwarp();
+                const long long off64 = g.m.q - win.k0;
+                const int off = (off64 > -(long long)N && off64 < (long long)win.W + N) ? (int)off64 : -4 * N;
+                const float kappa = (float)(wm.sig * g.m.A * T / (2.0 * (double)N));
+                float4* buf4 = (float4*)bufA;
+                switch (N) {
+                    case 32: residual_adjoint_nat<1>(buf4, tab, ltw, lane, off, win.W, pw, kappa, sdh, cdh, shh, chh); break;
+                    case 64: residual_adjoint_nat<2>(buf4, tab, ltw, lane, off, win.W, pw, kappa, sdh, cdh, shh, chh); break;
+                    case 128: residual_adjoint_nat<4>(buf4, tab, ltw, lane, off, win.W, pw, kappa, sdh, cdh, shh, chh); break;
+                    default: residual_adjoint_nat<8>(buf4, tab, ltw, lane, off, win.W, pw, kappa, sdh, cdh, shh, chh); break;
+                }
+                switch (g.m.J) {
+                    case 4: adjoint_sweep<4, false, true>(g, tab, N, Tf, inv_fstar, bufA, nullptr, lane, tacc, vp, vq); break;
+                    case 7: adjoint_sweep<7, false, true>(g, tab, N, Tf, inv_fstar, bufA, nullptr, lane, tacc, vp, vq); break;
+                    case 10: adjoint_sweep<10, false, true>(g, tab, N, Tf, inv_fstar, bufA, nullptr, lane, tacc, vp, vq); break;
+                    default: adjoint_sweep<0, false, true>(g, tab, N, Tf, inv_fstar, bufA, nullptr, lane, tacc, vp, vq); break;
+                }
+                __syncwarp();
+              }
+            }
+            if (!T3 && RMAX <= 8) {
+              // no other path in the plain N <= 256 instantiation
+            } else {
+              if (!g.m.bad && !packed_done) {
                 slow_part_dispatch<false, T3>(g.m, tab, N, bufA, bufE, lane, useT ? bufT : nullptr);
                 __syncwarp();
                 const long long off64 = g.m.q - win.k0;
@@ -625,6 +713,7 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_GRAD_MINB : 1) g
                     default: adjoint_sweep<0, T3>(g, tab, N, Tf, inv_fstar, bufA, bufE, lane, tacc, vp, vq, cT); break;
                 }
                 __syncwarp();
+              }
             }
             EpiG s;
             warp_sum2(sdh, cdh, s.dh[0], s.dh[1]);
