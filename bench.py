@@ -21,8 +21,10 @@ seconds per 10k-sample posterior round.
       headline line)
 
 Under torchrun each rank runs its own replica of the workload (different
-seed) on its own GPU with no collective on the data path (weak scaling); only
-the timing uses a barrier and a max over ranks.  Rank 0 prints one JSON line.
+seed) on its own GPU with no collective on the data path (weak scaling); with
+--shard the ranks share one workload's windows out instead (cost-balanced,
+strong scaling).  Only the timing uses a barrier and a max over ranks.  Rank 0
+prints one JSON line.
 """
 import argparse
 import json
@@ -564,6 +566,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=None, help="timed steps of the FP64 path (default: steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time the steps with eager launches, not graph replays")
+    ap.add_argument("--shard", action="store_true",
+                    help="under torchrun: share the 16 windows out among the ranks (strong scaling) instead of "
+                         "one replica of the workload per rank (weak scaling)")
     ap.add_argument("--workload", default="posterior", choices=["posterior", "tiny", "band", "population", "fullband"],
                     help="posterior: the headline step; the others print their own figures")
     ap.add_argument("--fb-sources", type=int, default=200000, help="fullband: injected binaries")
@@ -600,7 +605,24 @@ def main():
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
     ctx = api.Context(2 * wk.YEAR, device=dev.index)
-    wl, dA_h, dE_h, th_h, lg_h = build_inputs(ctx, wk.SEED_BASE + 2 + 1000 * rank, dev)
+    shard = args.shard and world > 1
+    wl, dA_h, dE_h, th_h, lg_h = build_inputs(ctx, wk.SEED_BASE + 2 + (0 if shard else 1000 * rank), dev)
+    n_total = wl.n_cand
+    if shard:
+        # strong scaling: every rank builds the same windows and keeps its
+        # cost-balanced share (no exchange on the data path)
+        import dataclasses
+        from paper_2307_03763_gb300 import shard as sh
+        part = sh.Shard(wl.windows, world, rank)
+        if not part.windows:
+            raise SystemExit("--shard: more ranks than windows")
+        dA_h, dE_h, wA_h, wE_h = part.take_data(dA_h, dE_h, wl.w_A, wl.w_E)
+        th_h, lg_h = part.take_candidates(th_h), part.take_candidates(lg_h)
+        meta = dict(wl.meta)
+        for key in ("source", "fisher_sigma"):
+            meta[key] = np.asarray(wl.meta[key])[part.window_ids]
+        wl = dataclasses.replace(wl, windows=part.windows, w_A=wA_h, w_E=wE_h, theta=th_h,
+                                 log_u=part.take_candidates(wl.log_u), noise_A=dA_h, noise_E=dE_h, meta=meta)
     nwin, n = len(wl.windows), wl.windows[0][5]
     T_ = lambda x, dt: torch.as_tensor(np.ascontiguousarray(x)).to(dev, dt)
     dA, dE = T_(dA_h, torch.complex128), T_(dE_h, torch.complex128)
@@ -822,7 +844,7 @@ def main():
 
     if rank != 0:
         return
-    evals = wl.n_cand * world
+    evals = n_total if shard else wl.n_cand * world
     value = evals * args.steps / (tot_c / 1e3)
     value_mx = evals * args.steps / (tot_mxg / 1e3)
     value64 = evals * fp64_steps / (tot_64 / 1e3)
@@ -886,10 +908,13 @@ def main():
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "strong" if shard else "weak",
         "vs_baseline": None, "dtype": "f32+f64-phase", "data": "synthetic",
         "config": {"workload": WORKLOAD, "global_batch": evals, "windows": nwin, "proposals_per_window": n,
-                   "l2": "flushed between timed steps (2x L2 buffer written)", "parallelism": "replicas",
+                   "l2": "flushed between timed steps (2x L2 buffer written)",
+                   "parallelism": ("windows sharded over %d ranks (cost-balanced)" % world) if shard else
+                                  "replicas" if world > 1 else "single GPU",
                    "launch": "each timed step replayed from a CUDA graph" if graphs else "eager launches",
                    "step": "gb_mh_certified: mixed-precision logL of every proposal, the chains, FP64 "
                            "re-evaluation of the proposals whose decision the mixed error bound cannot settle"},
