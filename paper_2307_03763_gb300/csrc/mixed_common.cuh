@@ -120,6 +120,187 @@ __constant__ float kInvFact[24] = {
     1.5619206968586225e-16f, 8.2206352466243295e-18f, 4.1103176233121648e-19f, 1.9572941063391263e-20f,
     8.8967913924505741e-22f, 3.8681701706306835e-23f};
 
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// sin(k pi/64), cos(k pi/64) for k = 0 .. 127 as double-word float pairs
+// (sin hi, sin lo, cos hi, cos lo), from 50-digit values
+__device__ const float4 kSinCosDW[128] = {
+    {0.000000000e+00f, 0.000000000e+00f, 1.000000000e+00f, 0.000000000e+00f},
+    {4.906767607e-02f, -1.739934308e-09f, 9.987954497e-01f, 6.471438052e-09f},
+    {9.801714122e-02f, -8.933931928e-10f, 9.951847196e-01f, 7.109666189e-09f},
+    {1.467304677e-01f, 6.778245520e-09f, 9.891765118e-01f, -1.799745353e-09f},
+    {1.950903237e-01f, -1.670471428e-09f, 9.807852507e-01f, 2.973947311e-08f},
+    {2.429801822e-01f, -2.267604104e-09f, 9.700312614e-01f, -8.249547712e-09f},
+    {2.902846634e-01f, 1.381566506e-08f, 9.569403529e-01f, -1.718450804e-08f},
+    {3.368898630e-01f, -9.622000974e-09f, 9.415440559e-01f, 9.244300436e-09f},
+    {3.826834261e-01f, 6.223350724e-09f, 9.238795042e-01f, 2.830748969e-08f},
+    {4.275550842e-01f, 9.201766460e-09f, 9.039893150e-01f, -2.190951598e-08f},
+    {4.713967443e-01f, -7.425253745e-09f, 8.819212914e-01f, -2.700296342e-08f},
+    {5.141027570e-01f, -1.278385930e-08f, 8.577286005e-01f, 9.498258180e-09f},
+    {5.555702448e-01f, -1.176952136e-08f, 8.314695954e-01f, 1.687026341e-08f},
+    {5.956993103e-01f, -5.810301129e-09f, 8.032075167e-01f, 1.481041778e-08f},
+    {6.343932748e-01f, 9.379557575e-09f, 7.730104327e-01f, 2.064255256e-08f},
+    {6.715589762e-01f, -2.132638244e-08f, 7.409511209e-01f, 4.501535145e-09f},
+    {7.071067691e-01f, 1.210161749e-08f, 7.071067691e-01f, 1.210161749e-08f},
+    {7.409511209e-01f, 4.501535145e-09f, 6.715589762e-01f, -2.132638244e-08f},
+    {7.730104327e-01f, 2.064255256e-08f, 6.343932748e-01f, 9.379557575e-09f},
+    {8.032075167e-01f, 1.481041778e-08f, 5.956993103e-01f, -5.810301129e-09f},
+    {8.314695954e-01f, 1.687026341e-08f, 5.555702448e-01f, -1.176952136e-08f},
+    {8.577286005e-01f, 9.498258180e-09f, 5.141027570e-01f, -1.278385930e-08f},
+    {8.819212914e-01f, -2.700296342e-08f, 4.713967443e-01f, -7.425253745e-09f},
+    {9.039893150e-01f, -2.190951598e-08f, 4.275550842e-01f, 9.201766460e-09f},
+    {9.238795042e-01f, 2.830748969e-08f, 3.826834261e-01f, 6.223350724e-09f},
+    {9.415440559e-01f, 9.244300436e-09f, 3.368898630e-01f, -9.622000974e-09f},
+    {9.569403529e-01f, -1.718450804e-08f, 2.902846634e-01f, 1.381566506e-08f},
+    {9.700312614e-01f, -8.249547712e-09f, 2.429801822e-01f, -2.267604104e-09f},
+    {9.807852507e-01f, 2.973947311e-08f, 1.950903237e-01f, -1.670471428e-09f},
+    {9.891765118e-01f, -1.799745353e-09f, 1.467304677e-01f, 6.778245520e-09f},
+    {9.951847196e-01f, 7.109666189e-09f, 9.801714122e-02f, -8.933931928e-10f},
+    {9.987954497e-01f, 6.471438052e-09f, 4.906767607e-02f, -1.739934308e-09f},
+    {1.000000000e+00f, 0.000000000e+00f, -0.000000000e+00f, -0.000000000e+00f},
+    {9.987954497e-01f, 6.471438052e-09f, -4.906767607e-02f, 1.739934308e-09f},
+    {9.951847196e-01f, 7.109666189e-09f, -9.801714122e-02f, 8.933931928e-10f},
+    {9.891765118e-01f, -1.799745353e-09f, -1.467304677e-01f, -6.778245520e-09f},
+    {9.807852507e-01f, 2.973947311e-08f, -1.950903237e-01f, 1.670471428e-09f},
+    {9.700312614e-01f, -8.249547712e-09f, -2.429801822e-01f, 2.267604104e-09f},
+    {9.569403529e-01f, -1.718450804e-08f, -2.902846634e-01f, -1.381566506e-08f},
+    {9.415440559e-01f, 9.244300436e-09f, -3.368898630e-01f, 9.622000974e-09f},
+    {9.238795042e-01f, 2.830748969e-08f, -3.826834261e-01f, -6.223350724e-09f},
+    {9.039893150e-01f, -2.190951598e-08f, -4.275550842e-01f, -9.201766460e-09f},
+    {8.819212914e-01f, -2.700296342e-08f, -4.713967443e-01f, 7.425253745e-09f},
+    {8.577286005e-01f, 9.498258180e-09f, -5.141027570e-01f, 1.278385930e-08f},
+    {8.314695954e-01f, 1.687026341e-08f, -5.555702448e-01f, 1.176952136e-08f},
+    {8.032075167e-01f, 1.481041778e-08f, -5.956993103e-01f, 5.810301129e-09f},
+    {7.730104327e-01f, 2.064255256e-08f, -6.343932748e-01f, -9.379557575e-09f},
+    {7.409511209e-01f, 4.501535145e-09f, -6.715589762e-01f, 2.132638244e-08f},
+    {7.071067691e-01f, 1.210161749e-08f, -7.071067691e-01f, -1.210161749e-08f},
+    {6.715589762e-01f, -2.132638244e-08f, -7.409511209e-01f, -4.501535145e-09f},
+    {6.343932748e-01f, 9.379557575e-09f, -7.730104327e-01f, -2.064255256e-08f},
+    {5.956993103e-01f, -5.810301129e-09f, -8.032075167e-01f, -1.481041778e-08f},
+    {5.555702448e-01f, -1.176952136e-08f, -8.314695954e-01f, -1.687026341e-08f},
+    {5.141027570e-01f, -1.278385930e-08f, -8.577286005e-01f, -9.498258180e-09f},
+    {4.713967443e-01f, -7.425253745e-09f, -8.819212914e-01f, 2.700296342e-08f},
+    {4.275550842e-01f, 9.201766460e-09f, -9.039893150e-01f, 2.190951598e-08f},
+    {3.826834261e-01f, 6.223350724e-09f, -9.238795042e-01f, -2.830748969e-08f},
+    {3.368898630e-01f, -9.622000974e-09f, -9.415440559e-01f, -9.244300436e-09f},
+    {2.902846634e-01f, 1.381566506e-08f, -9.569403529e-01f, 1.718450804e-08f},
+    {2.429801822e-01f, -2.267604104e-09f, -9.700312614e-01f, 8.249547712e-09f},
+    {1.950903237e-01f, -1.670471428e-09f, -9.807852507e-01f, -2.973947311e-08f},
+    {1.467304677e-01f, 6.778245520e-09f, -9.891765118e-01f, 1.799745353e-09f},
+    {9.801714122e-02f, -8.933931928e-10f, -9.951847196e-01f, -7.109666189e-09f},
+    {4.906767607e-02f, -1.739934308e-09f, -9.987954497e-01f, -6.471438052e-09f},
+    {0.000000000e+00f, 0.000000000e+00f, -1.000000000e+00f, -0.000000000e+00f},
+    {-4.906767607e-02f, 1.739934308e-09f, -9.987954497e-01f, -6.471438052e-09f},
+    {-9.801714122e-02f, 8.933931928e-10f, -9.951847196e-01f, -7.109666189e-09f},
+    {-1.467304677e-01f, -6.778245520e-09f, -9.891765118e-01f, 1.799745353e-09f},
+    {-1.950903237e-01f, 1.670471428e-09f, -9.807852507e-01f, -2.973947311e-08f},
+    {-2.429801822e-01f, 2.267604104e-09f, -9.700312614e-01f, 8.249547712e-09f},
+    {-2.902846634e-01f, -1.381566506e-08f, -9.569403529e-01f, 1.718450804e-08f},
+    {-3.368898630e-01f, 9.622000974e-09f, -9.415440559e-01f, -9.244300436e-09f},
+    {-3.826834261e-01f, -6.223350724e-09f, -9.238795042e-01f, -2.830748969e-08f},
+    {-4.275550842e-01f, -9.201766460e-09f, -9.039893150e-01f, 2.190951598e-08f},
+    {-4.713967443e-01f, 7.425253745e-09f, -8.819212914e-01f, 2.700296342e-08f},
+    {-5.141027570e-01f, 1.278385930e-08f, -8.577286005e-01f, -9.498258180e-09f},
+    {-5.555702448e-01f, 1.176952136e-08f, -8.314695954e-01f, -1.687026341e-08f},
+    {-5.956993103e-01f, 5.810301129e-09f, -8.032075167e-01f, -1.481041778e-08f},
+    {-6.343932748e-01f, -9.379557575e-09f, -7.730104327e-01f, -2.064255256e-08f},
+    {-6.715589762e-01f, 2.132638244e-08f, -7.409511209e-01f, -4.501535145e-09f},
+    {-7.071067691e-01f, -1.210161749e-08f, -7.071067691e-01f, -1.210161749e-08f},
+    {-7.409511209e-01f, -4.501535145e-09f, -6.715589762e-01f, 2.132638244e-08f},
+    {-7.730104327e-01f, -2.064255256e-08f, -6.343932748e-01f, -9.379557575e-09f},
+    {-8.032075167e-01f, -1.481041778e-08f, -5.956993103e-01f, 5.810301129e-09f},
+    {-8.314695954e-01f, -1.687026341e-08f, -5.555702448e-01f, 1.176952136e-08f},
+    {-8.577286005e-01f, -9.498258180e-09f, -5.141027570e-01f, 1.278385930e-08f},
+    {-8.819212914e-01f, 2.700296342e-08f, -4.713967443e-01f, 7.425253745e-09f},
+    {-9.039893150e-01f, 2.190951598e-08f, -4.275550842e-01f, -9.201766460e-09f},
+    {-9.238795042e-01f, -2.830748969e-08f, -3.826834261e-01f, -6.223350724e-09f},
+    {-9.415440559e-01f, -9.244300436e-09f, -3.368898630e-01f, 9.622000974e-09f},
+    {-9.569403529e-01f, 1.718450804e-08f, -2.902846634e-01f, -1.381566506e-08f},
+    {-9.700312614e-01f, 8.249547712e-09f, -2.429801822e-01f, 2.267604104e-09f},
+    {-9.807852507e-01f, -2.973947311e-08f, -1.950903237e-01f, 1.670471428e-09f},
+    {-9.891765118e-01f, 1.799745353e-09f, -1.467304677e-01f, -6.778245520e-09f},
+    {-9.951847196e-01f, -7.109666189e-09f, -9.801714122e-02f, 8.933931928e-10f},
+    {-9.987954497e-01f, -6.471438052e-09f, -4.906767607e-02f, 1.739934308e-09f},
+    {-1.000000000e+00f, -0.000000000e+00f, -0.000000000e+00f, -0.000000000e+00f},
+    {-9.987954497e-01f, -6.471438052e-09f, 4.906767607e-02f, -1.739934308e-09f},
+    {-9.951847196e-01f, -7.109666189e-09f, 9.801714122e-02f, -8.933931928e-10f},
+    {-9.891765118e-01f, 1.799745353e-09f, 1.467304677e-01f, 6.778245520e-09f},
+    {-9.807852507e-01f, -2.973947311e-08f, 1.950903237e-01f, -1.670471428e-09f},
+    {-9.700312614e-01f, 8.249547712e-09f, 2.429801822e-01f, -2.267604104e-09f},
+    {-9.569403529e-01f, 1.718450804e-08f, 2.902846634e-01f, 1.381566506e-08f},
+    {-9.415440559e-01f, -9.244300436e-09f, 3.368898630e-01f, -9.622000974e-09f},
+    {-9.238795042e-01f, -2.830748969e-08f, 3.826834261e-01f, 6.223350724e-09f},
+    {-9.039893150e-01f, 2.190951598e-08f, 4.275550842e-01f, 9.201766460e-09f},
+    {-8.819212914e-01f, 2.700296342e-08f, 4.713967443e-01f, -7.425253745e-09f},
+    {-8.577286005e-01f, -9.498258180e-09f, 5.141027570e-01f, -1.278385930e-08f},
+    {-8.314695954e-01f, -1.687026341e-08f, 5.555702448e-01f, -1.176952136e-08f},
+    {-8.032075167e-01f, -1.481041778e-08f, 5.956993103e-01f, -5.810301129e-09f},
+    {-7.730104327e-01f, -2.064255256e-08f, 6.343932748e-01f, 9.379557575e-09f},
+    {-7.409511209e-01f, -4.501535145e-09f, 6.715589762e-01f, -2.132638244e-08f},
+    {-7.071067691e-01f, -1.210161749e-08f, 7.071067691e-01f, 1.210161749e-08f},
+    {-6.715589762e-01f, 2.132638244e-08f, 7.409511209e-01f, 4.501535145e-09f},
+    {-6.343932748e-01f, -9.379557575e-09f, 7.730104327e-01f, 2.064255256e-08f},
+    {-5.956993103e-01f, 5.810301129e-09f, 8.032075167e-01f, 1.481041778e-08f},
+    {-5.555702448e-01f, 1.176952136e-08f, 8.314695954e-01f, 1.687026341e-08f},
+    {-5.141027570e-01f, 1.278385930e-08f, 8.577286005e-01f, 9.498258180e-09f},
+    {-4.713967443e-01f, 7.425253745e-09f, 8.819212914e-01f, -2.700296342e-08f},
+    {-4.275550842e-01f, -9.201766460e-09f, 9.039893150e-01f, -2.190951598e-08f},
+    {-3.826834261e-01f, -6.223350724e-09f, 9.238795042e-01f, 2.830748969e-08f},
+    {-3.368898630e-01f, 9.622000974e-09f, 9.415440559e-01f, 9.244300436e-09f},
+    {-2.902846634e-01f, -1.381566506e-08f, 9.569403529e-01f, -1.718450804e-08f},
+    {-2.429801822e-01f, 2.267604104e-09f, 9.700312614e-01f, -8.249547712e-09f},
+    {-1.950903237e-01f, 1.670471428e-09f, 9.807852507e-01f, 2.973947311e-08f},
+    {-1.467304677e-01f, -6.778245520e-09f, 9.891765118e-01f, -1.799745353e-09f},
+    {-9.801714122e-02f, 8.933931928e-10f, 9.951847196e-01f, 7.109666189e-09f},
+    {-4.906767607e-02f, 1.739934308e-09f, 9.987954497e-01f, 6.471438052e-09f}};
+
+// sin and cos of a double argument to about 1e-12 absolute with little FP64
+// work (on GB300 the FP64 pipe issues at 1/64 of the FP32 rate): the
+// reduction x = k pi/64 + r (|r| <= pi/128) in double with a two-part pi/64,
+// then double-word float arithmetic: sin r = r - r^3/6 + r^5/120 and
+// cos r = 1 - r^2/2 + r^4/24 - r^6/720 with r and r^2 as double-word values
+// and the smaller terms (below 3e-6 of the leading one) in float, and
+//   sin x = S_k cos r + C_k sin r,  cos x = C_k cos r - S_k sin r
+// with the table's S_k, C_k.
+__device__ __forceinline__ void dw_mul_acc(float ah, float al, float bh, float bl, float& p, float& e) {
+    p = ah * bh;
+    e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+}
+__device__ void sincos_dw(double x, double& sn, double& cs) {
+    const double k = rint(x * 20.371832715762604);                  // 64/pi
+    double r = fma(-k, 0.04908738521234052, x);                     // pi/64, high part
+    r = fma(-k, 1.9135106236677394e-18, r);                         // low part
+    const float4 t = kSinCosDW[((int)(long long)k) & 127];
+    const float rh = (float)r, rl = (float)(r - (double)rh);
+    const float z = rh * rh;
+    float s1, e1, s2, e2;
+    const float ts = -(rh * z) * (0.16666667f - z * 0.0083333333f);
+    two_sum(rh, ts, s1, e1);
+    const float srh = s1, srl = e1 + rl;                            // sin r
+    const float p = rh * rh;
+    const float ep = fmaf(rh, rh, -p) + 2.0f * (rh * rl);
+    const float tc = (z * z) * (0.041666668f - z * 0.0013888889f);
+    two_sum(1.0f, -0.5f * p, s2, e2);
+    const float crh = s2, crl = (e2 - 0.5f * ep) + tc;             // cos r
+    float a, ae, b, be, sh, se, ch, ce;
+    dw_mul_acc(t.x, t.y, crh, crl, a, ae);
+    dw_mul_acc(t.z, t.w, srh, srl, b, be);
+    two_sum(a, b, sh, se);
+    se += ae + be;
+    dw_mul_acc(t.z, t.w, crh, crl, a, ae);
+    dw_mul_acc(t.x, t.y, srh, srl, b, be);
+    two_sum(a, -b, ch, ce);
+    ce += ae - be;
+    sn = (double)sh + (double)se;
+    cs = (double)ch + (double)ce;
+}
+
 // ifs = 1/f*, formed once per thread by the caller
 __device__ void setup_mixed(const double* th, double T, double ifs, CandMix& c) {
     const double f0 = th[0], fd = th[1], beta = th[2], lam = th[3];
@@ -140,8 +321,8 @@ __device__ void setup_mixed(const double* th, double T, double ifs, CandMix& c) 
     split(delta, c.c1h, c.c1l);
     split(0.5 * fd * T * T, c.c2h, c.c2l);
     double sb, cb, sl, cl;
-    sincos(beta, &sb, &cb);
-    sincos(lam, &sl, &cl);
+    sincos_dw(beta, sb, cb);
+    sincos_dw(lam, sl, cl);
     const double r = kAU / kC;
     const double Kc = -r * cb * cl, Ks = -r * cb * sl;
     c.Kc = (float)Kc;
@@ -239,11 +420,6 @@ __device__ __forceinline__ float2 cis_rx(float x) {
     }
 }
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
 
 // Slow part of one candidate: lane l, step r computes sample n and writes A, E
 // to buf{A,E}[r*32 + l] (conflict-free), with n = l + 32 r (NAT: natural
@@ -403,6 +579,24 @@ __constant__ float4 kLinkPair[11] = {
     {8.2206352466243295e-18f, 8.2206352466243295e-18f, 4.1103176233121648e-19f, 4.1103176233121648e-19f},
     {1.9572941063391263e-20f, 1.9572941063391263e-20f, 8.8967913924505741e-22f, 8.8967913924505741e-22f}};
 
+// The link series of a pair in x2 = X^2 with the powers of y = -4 X^2 and the
+// factor -2 of Im folded into the coefficients: (1/(2j+1)!, -2/(2j+2)!) times
+// (-4)^j.  Scalings by powers of two are exact, so every intermediate equals
+// the plain Horner value in y times (-4)^j and the results are those of
+// link_transfer<J> bit for bit, with two operations fewer per link.
+__constant__ float4 kLinkPairS[11] = {
+    {1.000000000e+00f, 1.000000000e+00f, -1.000000000e+00f, -1.000000000e+00f},
+    {-6.666666865e-01f, -6.666666865e-01f, 3.333333433e-01f, 3.333333433e-01f},
+    {1.333333403e-01f, 1.333333403e-01f, -4.444444552e-02f, -4.444444552e-02f},
+    {-1.269841287e-02f, -1.269841287e-02f, 3.174603218e-03f, 3.174603218e-03f},
+    {7.054673624e-04f, 7.054673624e-04f, -1.410934783e-04f, -1.410934783e-04f},
+    {-2.565335853e-05f, -2.565335853e-05f, 4.275559604e-06f, 4.275559604e-06f},
+    {6.577784575e-07f, 6.577784575e-07f, -9.396834599e-08f, -9.396834599e-08f},
+    {-1.252911286e-08f, -1.252911286e-08f, 1.566139107e-09f, 1.566139107e-09f},
+    {1.842516695e-10f, 1.842516695e-10f, -2.047240676e-11f, -2.047240676e-11f},
+    {-2.154990162e-12f, -2.154990162e-12f, 2.154990189e-13f, 2.154990189e-13f},
+    {2.052371673e-14f, 2.052371673e-14f, -1.865792295e-15f, -1.865792295e-15f}};
+
 // link_transfer<J> of a pair
 template <int J>
 __device__ __forceinline__ cpair plink_transfer(f2 X) {
@@ -410,16 +604,16 @@ __device__ __forceinline__ cpair plink_transfer(f2 X) {
         const float2 a = link_transfer<0>(X.x), b = link_transfer<0>(X.y);
         return cpair{make_float2(a.x, b.x), make_float2(a.y, b.y)};
     } else {
-        const f2 y = pmul(bc(-4.0f), pmul(X, X));
-        const float4 cJ = kLinkPair[J];
+        const f2 x2 = pmul(X, X);
+        const float4 cJ = kLinkPairS[J];
         f2 re = make_float2(cJ.x, cJ.y), im = make_float2(cJ.z, cJ.w);
 #pragma unroll
         for (int j = J - 1; j >= 0; --j) {
-            const float4 cj = kLinkPair[j];
-            re = pfma(re, y, make_float2(cj.x, cj.y));
-            im = pfma(im, y, make_float2(cj.z, cj.w));
+            const float4 cj = kLinkPairS[j];
+            re = pfma(re, x2, make_float2(cj.x, cj.y));
+            im = pfma(im, x2, make_float2(cj.z, cj.w));
         }
-        return cpair{re, pmul(pmul(bc(-2.0f), X), im)};
+        return cpair{re, pmul(X, im)};
     }
 }
 
@@ -538,8 +732,10 @@ __device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N
         for (int arm = 0; arm < 3; ++arm) {
             const f2 kn = kn_[arm], nu = nu_[arm], nv = nv_[arm];
             const f2 Fp = pmul(psub(nu, nv), padd(nu, nv));
-            const f2 Fx = pmul(pmul(bc(2.0f), nu), nv);
-            const cpair G{pfma(bc(c.gpr), Fp, pmul(bc(c.gxr), Fx)), pfma(bc(c.gpi), Fp, pmul(bc(c.gxi), Fx))};
+            // Fx = 2 nu nv with the exact factor 2 on the x coefficients
+            const f2 Fx1 = pmul(nu, nv);
+            const cpair G{pfma(bc(c.gpr), Fp, pmul(bc(2.0f * c.gxr), Fx1)),
+                          pfma(bc(c.gpi), Fp, pmul(bc(2.0f * c.gxi), Fx1))};
             const int rp = arm == 2 ? 0 : arm + 1;
             const int rm = arm;
             zp[arm] = pcmul(pcmul(plink_transfer<J>(pmul(a, psub(bc(1.0f), kn))), G), rx[rp]);
@@ -983,6 +1179,38 @@ __device__ void fft_inner_ch(float4* buf, const OrbitTables32& tab, const LaneTw
     if constexpr (IM) kahan_merge(s_im, c_im, sim, cim);
 }
 
+// Compensated warp sums of two Kahan pairs a and b at once (reduce-scatter):
+// at the first level the lower half-warp keeps a and the upper half keeps b,
+// each sending the other value to its partner, so that the four remaining
+// levels move one pair per lane instead of two.  Every value is combined by
+// the same tree as in warp_sum2 (TwoSum is exact and symmetric), so the
+// results are warp_sum2's bit for bit.  a's total is returned in (ah, al)
+// and b's in (bh, bl) on every lane.
+__device__ __forceinline__ void warp_sum2x2(float as, float ac, float bs, float bc_, float& ah, float& al, float& bh,
+                                            float& bl, int lane) {
+    const bool upper = (lane & 16) != 0;
+    float kh = upper ? bs : as, kl = upper ? -bc_ : -ac;      // the value this half keeps
+    const float sh = upper ? as : bs, sl = upper ? -ac : -bc_;
+    const float rh = __shfl_xor_sync(0xffffffffu, sh, 16), rl = __shfl_xor_sync(0xffffffffu, sl, 16);
+    float s, e;
+    two_sum(kh, rh, s, e);
+    kh = s;
+    kl = kl + rl + e;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, kh, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, kl, o);
+        two_sum(kh, h2, s, e);
+        kh = s;
+        kl = kl + l2 + e;
+    }
+    const float oh = __shfl_xor_sync(0xffffffffu, kh, 16), ol = __shfl_xor_sync(0xffffffffu, kl, 16);
+    ah = upper ? oh : kh;
+    al = upper ? ol : kl;
+    bh = upper ? kh : oh;
+    bl = upper ? kl : ol;
+}
+
 // Compensated warp sum of Kahan pairs: returns hi + lo on every lane.
 __device__ __forceinline__ void warp_sum2(float sum, float comp, float& hi, float& lo) {
     hi = sum;
@@ -1182,8 +1410,7 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) 
                 __syncwarp();
             }
             float dhh, dhl, hhh, hhl, imh = 0.0f, iml = 0.0f;
-            warp_sum2(sdh, cdh, dhh, dhl);
-            warp_sum2(shh, chh, hhh, hhl);
+            warp_sum2x2(sdh, cdh, shh, chh, dhh, dhl, hhh, hhl, lane);
             if constexpr (IM) warp_sum2(sim, cim, imh, iml);
             if (lane == 0) {
                 if constexpr (IM)
