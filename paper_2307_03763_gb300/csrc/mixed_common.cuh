@@ -1179,6 +1179,57 @@ __device__ void fft_inner_ch(float4* buf, const OrbitTables32& tab, const LaneTw
     if constexpr (IM) kahan_merge(s_im, c_im, sim, cim);
 }
 
+// The T channel of one candidate, N = 32 R >= 64 points, without an idle
+// half: T's even and odd samples form one channel pair (T_2m, T_2m+1) of an
+// N/2-point transform (tabh: the N/2 tables; buf: workspace of N/2
+// channel-pair elements), whose bins K < N/2 are E_K, O_K, and the radix-2
+// step X_K = E_K + w^K O_K, X_K+N/2 = E_K - w^K O_K (w = exp(-2 pi i/N),
+// from the 1024-point twiddles) gives T's N bins; then T's window inner
+// products (its data in the first slot of each element of its float copy),
+// compensated per lane, returned as s - c.
+__device__ __forceinline__ void kahan_add1(float& sum, float& comp, float x) {
+    const float y = x - comp;
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+template <int R, bool IM>
+__device__ void fft_inner_t_half(float4* buf, const float2* srcT, const OrbitTables32& tabh, const float2* tw1024,
+                                 const LaneTw& ltw, int lane, int off, int W, const Win32* __restrict__ pw, float& sdh,
+                                 float& cdh, float& shh, float& chh, float& sim, float& cim) {
+    static_assert(R >= 2, "N >= 64");
+    constexpr int N = 32 * R, H = R / 2;
+    const float4* t4 = (const float4*)srcT;   // element m: (T_2m re, T_2m im, T_2m+1 re, T_2m+1 im)
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+        const float4 v = t4[lane + 32 * j];
+        buf[lane + 32 * j] = make_float4(v.x, v.z, v.y, v.w);
+    }
+    cpair x[H];
+    const int kbase = nat_transform<H>(buf, tabh, ltw, lane, x);
+    sdh = cdh = shh = chh = sim = cim = 0.0f;
+#pragma unroll
+    for (int q = 0; q < H; ++q) {
+        const int K = bin_of<H>(kbase, q);                 // 0 <= K < N/2
+        const float2 w = __ldg(tw1024 + K * (1024 / N));
+        const float ore = x[q].re.y, oim = x[q].im.y;
+        const float tre = fmaf(w.x, ore, -w.y * oim), tim = fmaf(w.x, oim, w.y * ore);
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const float hre = half == 0 ? x[q].re.x + tre : x[q].re.x - tre;
+            const float him = half == 0 ? x[q].im.x + tim : x[q].im.x - tim;
+            const int m = half == 0 ? K : K - N / 2;       // bin q_c + m
+            const int kk = off + m;
+            if (kk >= 0 && kk < W) {
+                const Win32 v = pw[kk];
+                kahan_add1(sdh, cdh, __fmul_rn(v.w.x, fmaf(v.dre.x, hre, __fmul_rn(v.dim.x, him))));
+                kahan_add1(shh, chh, __fmul_rn(v.w.x, fmaf(hre, hre, __fmul_rn(him, him))));
+                if constexpr (IM) kahan_add1(sim, cim, __fmul_rn(v.w.x, fmaf(v.dim.x, hre, -__fmul_rn(v.dre.x, him))));
+            }
+        }
+    }
+}
+
 // Compensated warp sums of two Kahan pairs a and b at once (reduce-scatter):
 // at the first level the lower half-warp keeps a and the upper half keeps b,
 // each sending the other value to its partner, so that the four remaining
@@ -1381,15 +1432,18 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) 
                     }
 #undef GB_FFT_INNER
                     if constexpr (T3) {
-                        if (useT) {   // the T channel through the same transform, then into the sums
+                        if (useT) {   // the T channel (a half-length transform), then into the sums
                             float tdh = 0.0f, tcdh = 0.0f, thh = 0.0f, tchh = 0.0f, tim = 0.0f, tcim = 0.0f;
                             __syncwarp();
-#define GB_FFT_INNER_T(R)                                                                                 \
-    fft_inner_ch<R, IM, true>((float4*)bufA, tab, ltw, lane, off, win.W, pwT, tdh, tcdh, thh, tchh, tim, tcim, \
-                              bufT)
+#define GB_FFT_INNER_T(R)                                                                                    \
+    fft_inner_t_half<R, IM>((float4*)bufA, bufT, tabs.t[__ffs(N) - 7], tw1024, ltw, lane, off, win.W, pwT, tdh, \
+                            tcdh, thh, tchh, tim, tcim)
                             if constexpr (RMAX <= 8) {
                                 switch (N) {
-                                    case 32: GB_FFT_INNER_T(1); break;
+                                    case 32:
+                                        fft_inner_ch<1, IM, true>((float4*)bufA, tab, ltw, lane, off, win.W, pwT, tdh,
+                                                                  tcdh, thh, tchh, tim, tcim, bufT);
+                                        break;
                                     case 64: GB_FFT_INNER_T(2); break;
                                     case 128: GB_FFT_INNER_T(4); break;
                                     default: GB_FFT_INNER_T(8); break;
