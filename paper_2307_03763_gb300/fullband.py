@@ -403,7 +403,7 @@ class FullBand:
                            "median_accept_rate": float(np.median(post) / n_post) if post else None})
         return self.found
 
-    def match(self, snr_inj, owner, n_near=4, batch=8192):
+    def match(self, snr_inj, owner, n_near=4, batch=8192, snr_inj_search=None):
         """How the recoveries sit on the injections.  The paper's scores
         (Sec. IV): for every recovered source, the scaled error delta (Eq. 19)
         and the overlap O (Eq. 20) against each of the n_near injected sources
@@ -414,8 +414,12 @@ class FullBand:
         recoveries with delta < 0.3 and with O > 0.9, the injected sources
         above the SNR threshold and how many distinct ones are matched with
         delta < 0.3; also the fractions within one and three frequency bins
-        and the median ratio of recovered to that injection's optimal SNR."""
+        and the median ratio of recovered to that injection's optimal SNR
+        (snr_inj_search: the injected SNRs under the weights the search used,
+        when they differ from the instrument's, so that both SNRs of the
+        ratio see the same noise; snr_inj counts the loud injections)."""
         f_inj = self.src[:, 0]
+        snr_ref = snr_inj if snr_inj_search is None else snr_inj_search
         order = np.argsort(f_inj)
         fs = f_inj[order]
         d, ratio = [], []
@@ -423,7 +427,7 @@ class FullBand:
             i = np.clip(np.searchsorted(fs, th[0]), 1, fs.size - 1)
             j = order[i - 1] if abs(fs[i - 1] - th[0]) < abs(fs[i] - th[0]) else order[i]
             d.append(abs(f_inj[j] - th[0]) * self.T)
-            ratio.append(s / max(snr_inj[j], 1e-300))
+            ratio.append(s / max(snr_ref[j], 1e-300))
         d = np.array(d)
         loud = int(np.sum(snr_inj > self.stats.get("snr_min", 10.0)))
         out = {"within_1_bin": float(np.mean(d < 1.0)) if d.size else None,
@@ -495,7 +499,11 @@ def run(ctx, n_src=200000, f_lo=0.3e-3, f_hi=15e-3, T=2 * wk.YEAR, rounds=3, pop
     fb.search(rounds=rounds, pop=pop, generations=generations, snr_min=snr_min, n_post=n_post, phase=phase,
               posterior=posterior, scheme=scheme, noise=noise, joint=joint)
     st = dict(fb.stats)
-    st.update(fb.match(snr_inj, owner))
+    # with median-noise weights the recovered SNRs are measured against the
+    # segments' estimated PSD: compare them with the injections' SNRs under
+    # the same weights (the instrument-PSD SNRs still count the loud ones)
+    snr_search = fb.injected_snr()[0] if noise == "median" else None
+    st.update(fb.match(snr_inj, owner, snr_inj_search=snr_search))
     st["wall_s"] = _sync(ctx.device) - t0
     st["search_wall_s"] = st["ga_s"] + st["posterior_s"] + st["subtract_s"] + st["joint_refit_s"]
     return st
