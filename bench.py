@@ -226,7 +226,8 @@ def flops_per_grad_fp64(N, f_hz, T):
     forward work (flops_per_eval_fp64) and its link-series degrees J = 6, 8,
     12, 16: forward with 38 per window bin, the adjoint transform of both
     channels, and per sample 508 + 48 J + 555 for the reverse step.  The FP64
-    kernel itself carries eight forward tangents, about three times this work."""
+    kernel's reverse sweep recomputes the sample's forward values and
+    evaluates the link transfer's derivative series beside it."""
     x = f_hz / (299792458.0 / (2 * math.pi * 2.5e9))
     J = 6 if x <= 0.22 else 8 if x <= 0.5 else 12 if x <= 1.3 else 16
     forward = N * (445 + 24 * J) + 2 * 5 * N * math.log2(N) + 38 * N

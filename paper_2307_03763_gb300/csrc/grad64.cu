@@ -2,24 +2,28 @@
 //
 // With h_k = (T/2N) S_m and r_m = w_k (d_k - h_k) on window bins (0 elsewhere),
 //   d logL / d theta_i = (4/T) sum_k w_k Re[(d_k - h_k) conj(d h_k/d theta_i)]
-//                      = (2/N) Re sum_n  c_n conj(d s_n / d theta_i),
-//   c_n = sum_m r_m exp(+2 pi i m n / N)        (the adjoint of the DFT).
-// Per candidate the kernel (1) recomputes the template, (2) forms the
-// residual r and logL, (3) runs the adjoint FFT to get c_n, and (4) sweeps the
-// samples again carrying the slow-part response with eight tangents (one per
-// parameter, forward mode) and contracts them with c_n.  Nothing is stored
-// between candidates beyond the warp's shared-memory buffers.
+//                      = (2/N) Re sum_n  conj(c_n) d s_n / d theta_i,
+//   c_n = conj(sum_m conj(r_m) exp(-2 pi i m n / N))   (the adjoint of the DFT).
+// Per candidate the kernel (1) computes the template, (2) forms the residual
+// r and logL, (3) runs the adjoint FFT to get c_n, and (4) sweeps the samples
+// in reverse mode: each sample's forward values (the fast/slow response of
+// Sec. II, in the same link form as the FP64 likelihood), then the adjoints
+// of the channel samples c_n propagated back through the TDI combination,
+// the six links and the three receiver phases to the parameters.  The
+// amplitude, inclination and polarisation enter only through the two complex
+// polarisation coefficients alpha, gamma (n.H.n = alpha Fp + gamma Fx); their
+// adjoints are summed over the samples and contracted with d alpha/d theta,
+// d gamma/d theta once per candidate.
 //
-// Tangents in closed form (k = propagation direction, u, v the polarisation
-// basis, kappa_j = k.x_j/c, f = f0 + fdot t):
-//   dPsi_j/df0 = 2 pi (t - kappa_j),  dPsi_j/dfdot = pi (t - kappa_j)^2,
-//   dPsi_j/dbeta = -2 pi (f - fdot kappa_j) u.x_j/c,
-//   dPsi_j/dlambda = -2 pi (f - fdot kappa_j) cos(beta) v.x_j/c,  dPsi_j/dphi0 = 1,
+// Derivatives used (k = propagation direction, u, v the polarisation basis,
+// kappa_j = k.x_j/c, f = f0 + fdot t, receiver phase 2 pi cyc_j):
+//   d cyc_j/d f0 = t - kappa_j,  d cyc_j/d fdot = (t - kappa_j)^2 / 2,
+//   d cyc_j/d beta = -(f - fdot kappa_j) u.x_j/c,
+//   d cyc_j/d lambda = -(f - fdot kappa_j) cos(beta) v.x_j/c,  d cyc_j/d phi0 = 1/(2 pi),
 //   dk/dbeta = u, dk/dlambda = cos(beta) v, du/dbeta = -k, du/dlambda = -sin(beta) v,
 //   dv/dlambda = (cos lambda, sin lambda, 0),
-//   H = alpha e+ + gamma ex with alpha = A+ cos2psi - i Ax sin2psi,
-//   gamma = -A+ sin2psi - i Ax cos2psi (linear in A, simple in iota and psi),
-//   d/dX [sinc(X) e^{-iX}] = (e^{-2iX} - sinc(X) e^{-iX}) / X.
+//   d/dX [sinc(X) e^{-iX}] from the derivative of its series (or, evaluated
+//   directly, (e^{-2iX} - sinc(X) e^{-iX}) / X).
 #include <cmath>
 
 #include "gb_internal.cuh"
@@ -36,54 +40,50 @@ struct C {
 __device__ __forceinline__ C cadd(C a, C b) { return {a.x + b.x, a.y + b.y}; }
 __device__ __forceinline__ C csub(C a, C b) { return {a.x - b.x, a.y - b.y}; }
 __device__ __forceinline__ C cmul(C a, C b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+// a conj(b)
+__device__ __forceinline__ C cmulc(C a, C b) { return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y}; }
 __device__ __forceinline__ C cscale(C a, double s) { return {a.x * s, a.y * s}; }
+// Re(conj(a) b)
+__device__ __forceinline__ double redot(C a, C b) { return a.x * b.x + a.y * b.y; }
 
-struct DR {
-    double v, d[K];
+// Series of the link transfer V(X) = sinc(X) e^{-iX} in y = -4 X^2:
+//   Re V = sum_j y^j/(2j+1)!,          Im V = -2X sum_j y^j/(2j+2)!,
+//   d Re V/dX = X sum_j y^j (-8(j+1))/(2j+3)!,   d Im V/dX = sum_j y^j (-2(2j+1))/(2j+2)!
+// (each coefficient the double nearest its exact rational value)
+struct Series4 {
+    double re, im, dre, dim;
 };
-struct DC {
-    C v, d[K];
+__constant__ Series4 kTransferSeries[17] = {
+    {1.0, 0.5, -1.3333333333333333, -1.0},
+    {0.16666666666666666, 0.041666666666666664, -0.13333333333333333, -0.25},
+    {0.008333333333333333, 0.001388888888888889, -0.004761904761904762, -0.013888888888888888},
+    {0.0001984126984126984, 2.48015873015873e-05, -8.818342151675486e-05, -0.00034722222222222224},
+    {2.7557319223985893e-06, 2.755731922398589e-07, -1.0020843354176687e-06, -4.96031746031746e-06},
+    {2.505210838544172e-08, 2.08767569878681e-09, -7.708341041674375e-09, -4.592886537330982e-08},
+    {1.6059043836821613e-10, 1.1470745597729725e-11, -4.282411689819097e-11, -2.9823938554097286e-10},
+    {7.647163731819816e-13, 4.779477332387385e-14, -1.7993326427811332e-13, -1.4338431997162156e-12},
+    {2.8114572543455206e-15, 1.5619206968586225e-16, -5.918857377569517e-16, -5.310530369319317e-15},
+    {8.22063524662433e-18, 4.110317623312165e-19, -1.565835285071301e-18, -1.5619206968586227e-17},
+    {1.9572941063391263e-20, 8.896791392450574e-22, -3.403989750155002e-21, -3.7366523848292405e-20},
+    {3.868170170630684e-23, 1.6117375710961184e-24, -6.189072273009094e-24, -7.413992827042144e-23},
+    {6.446950284384474e-26, 2.4795962632247976e-27, -9.551037458347369e-27, -1.2397981316123987e-25},
+    {9.183689863795546e-29, 3.279889237069838e-30, -1.2667158432821444e-29, -1.7711401880177124e-28},
+    {1.1309962886447716e-31, 3.7699876288159054e-33, -1.4593500498642214e-32, -2.1865928247132253e-31},
+    {1.216125041553518e-34, 3.8003907548547434e-36, -1.4740909594588097e-35, -2.356242268009941e-34},
+    {1.151633562077195e-37, 3.387157535521162e-39, -1.3161526423739371e-38, -2.235523973443967e-37},
 };
-
-__device__ __forceinline__ DC dmul(const DC& a, const DC& b) {
-    DC o;
-    o.v = cmul(a.v, b.v);
-#pragma unroll
-    for (int k = 0; k < K; ++k) o.d[k] = cadd(cmul(a.d[k], b.v), cmul(a.v, b.d[k]));
-    return o;
-}
-__device__ __forceinline__ DC dadd(const DC& a, const DC& b) {
-    DC o;
-    o.v = cadd(a.v, b.v);
-#pragma unroll
-    for (int k = 0; k < K; ++k) o.d[k] = cadd(a.d[k], b.d[k]);
-    return o;
-}
-__device__ __forceinline__ DC dsub(const DC& a, const DC& b) {
-    DC o;
-    o.v = csub(a.v, b.v);
-#pragma unroll
-    for (int k = 0; k < K; ++k) o.d[k] = csub(a.d[k], b.d[k]);
-    return o;
-}
-__device__ __forceinline__ DC dscale(const DC& a, double s) {
-    DC o;
-    o.v = cscale(a.v, s);
-#pragma unroll
-    for (int k = 0; k < K; ++k) o.d[k] = cscale(a.d[k], s);
-    return o;
-}
 
 struct CandG {
     double k[3], u[3], v[3], w[3];   // w = dv/dlambda
     double cb, sb;
     C al, ga, al_i[3], ga_i[3];      // alpha, gamma and their derivatives wrt A, iota, psi
-    double f0, fd, delta, phi0, A;
+    double f0, fd, delta, phi0c;
+    double D0r, D0i, eps;            // exp(-i f0/f*), fdot/f*
     long long q;
-    int bad, pad;
+    int bad, J;
 };
 
-__device__ void setup_grad(const double* th, double T, CandG& c) {
+__device__ void setup_grad(const double* th, double T, double inv_fstar, CandG& c) {
     const double f0 = th[0], fd = th[1], beta = th[2], lam = th[3];
     const double A = th[4], iota = th[5], psi = th[6], phi0 = th[7];
     bool bad = false;
@@ -96,8 +96,7 @@ __device__ void setup_grad(const double* th, double T, CandG& c) {
     c.delta = __dadd_rn(f0T, -qd);
     c.f0 = f0;
     c.fd = fd;
-    c.phi0 = phi0;
-    c.A = A;
+    c.phi0c = phi0 * 0.15915494309189535;   // 1 / (2 pi)
     double sb, cb, sl, cl, s2, c2, si, ci;
     sincos(beta, &sb, &cb);
     sincos(lam, &sl, &cl);
@@ -131,169 +130,247 @@ __device__ void setup_grad(const double* th, double T, CandG& c) {
     // d/dpsi
     c.al_i[2] = {-2.0 * Ap * s2, -2.0 * Ax * c2};
     c.ga_i[2] = {-2.0 * Ap * c2, 2.0 * Ax * s2};
+    // series degree of the link transfer: first omitted term (of the
+    // transfer and of its derivative) below 1e-15 for the largest argument
+    // X = f (1 + |k.n|)/(2 f*) <= f_max / f*
+    const double xmax = fmax(fabs(f0), fabs(f0 + fd * T)) * inv_fstar;
+    c.J = xmax <= 0.22 ? 6 : xmax <= 0.5 ? 8 : xmax <= 1.3 ? 12 : xmax <= 2.35 ? 16 : 0;
+    double sD, cD;
+    sincos(f0 * inv_fstar, &sD, &cD);
+    c.D0r = cD;
+    c.D0i = -sD;
+    c.eps = fd * inv_fstar;
 }
 
-// sinc(X) e^{-iX} and its derivative in X
-__device__ __forceinline__ void transfer(double X, C& Tv, C& Td) {
-    if (fabs(X) < 0.25) {
-        // series of (e^w - 1)/w, w = -2iX, and its derivative, 18 terms
-        C t = {0.0, 0.0}, td = {0.0, 0.0};
-        C wk = {1.0, 0.0};   // (-2i)^k X^k
-        double inv = 1.0;    // 1/(k+1)!
-        C wkm1 = {0.0, 0.0}; // (-2i)^k X^(k-1) * k
-        for (int k = 0; k < 18; ++k) {
-            inv /= (double)(k + 1);
-            t = cadd(t, cscale(wk, inv));
-            if (k >= 1) td = cadd(td, cscale(wkm1, inv));
-            // advance: wkm1 for k+1 = (k+1) (-2i)^(k+1) X^k
-            const C m2i = {0.0, -2.0};
-            wkm1 = cscale(cmul(wk, m2i), (double)(k + 1));
-            wk = cmul(cscale(wk, X), m2i);
+// V = sinc(X) e^{-iX} and, with DER, dV/dX
+template <bool DER>
+__device__ __forceinline__ void transfer(double X, int J, C& V, C& Vd) {
+    if (J == 0) {
+        double s, co;
+        sincos(X, &s, &co);
+        const double sinc = X != 0.0 ? s / X : 1.0;
+        V = {sinc * co, -(sinc * s)};
+        if (DER) {
+            const C e2 = {co * co - s * s, -2.0 * s * co};
+            Vd = X != 0.0 ? cscale(csub(e2, V), 1.0 / X) : C{0.0, -1.0};
         }
-        Tv = t;
-        Td = td;
         return;
     }
-    double s, co;
-    sincos(X, &s, &co);
-    const double sc = s / X;
-    Tv = {sc * co, -(sc * s)};
-    const C e2 = {co * co - s * s, -2.0 * s * co};
-    Td = cscale(csub(e2, Tv), 1.0 / X);
+    const double y = -4.0 * X * X;
+    const Series4 cJ = kTransferSeries[J];
+    double re = cJ.re, im = cJ.im, dim = cJ.dim, dre = kTransferSeries[J - 1].dre;
+    for (int j = J - 1; j >= 0; --j) {
+        const Series4 cj = kTransferSeries[j];
+        re = fma(re, y, cj.re);
+        im = fma(im, y, cj.im);
+        if (DER) {
+            dim = fma(dim, y, cj.dim);
+            if (j > 0) dre = fma(dre, y, kTransferSeries[j - 1].dre);
+        }
+    }
+    V = {re, -2.0 * X * im};
+    if (DER) Vd = {X * dre, dim};
 }
 
 struct Geo {
-    double T, T_over_N, fstar, scale;
+    double T, T_over_N, inv_fstar, scale;
     int N, logN;
 };
 
-// Slow-part response of one sample with eight tangents: returns A and E, and
-// T = (X + Y + Z)/sqrt3 when Tout is not null.
-__device__ void sample_dual(const CandG& c, const Geo& g, const OrbitTables64& tab, int n, DC& Aout, DC& Eout,
-                            DC* Tout = nullptr) {
-    const int N = g.N;
-    const double t = (double)n * g.T_over_N;
-    const double f = c.f0 + c.fd * t;
-    DC rx[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        const double x0 = tab.x[(j * 3 + 0) * N + n], x1 = tab.x[(j * 3 + 1) * N + n],
-                     x2 = tab.x[(j * 3 + 2) * N + n];
-        const double kap = (c.k[0] * x0 + c.k[1] * x1 + c.k[2] * x2) / kC;
-        const double ux = (c.u[0] * x0 + c.u[1] * x1 + c.u[2] * x2) / kC;
-        const double vx = (c.v[0] * x0 + c.v[1] * x1 + c.v[2] * x2) / kC;
-        const double ph = 2.0 * kPi *
-                              (c.delta * t / g.T + 0.5 * c.fd * (t * t) - c.f0 * kap - c.fd * t * kap +
-                               0.5 * c.fd * (kap * kap)) +
-                          c.phi0;
-        double dph[K];
-        const double tk = t - kap;
-        const double fk = f - c.fd * kap;
-        dph[0] = 2.0 * kPi * tk;
-        dph[1] = kPi * tk * tk;
-        dph[2] = -2.0 * kPi * fk * ux;
-        dph[3] = -2.0 * kPi * fk * c.cb * vx;
-        dph[4] = 0.0;
-        dph[5] = 0.0;
-        dph[6] = 0.0;
-        dph[7] = 1.0;
-        double s, co;
-        sincos(ph, &s, &co);
-        rx[j].v = {co, s};
-#pragma unroll
-        for (int k = 0; k < K; ++k) rx[j].d[k] = {-s * dph[k], co * dph[k]};
-    }
-    const double a = f / (2.0 * g.fstar);
-    double da[K] = {1.0 / (2.0 * g.fstar), t / (2.0 * g.fstar), 0, 0, 0, 0, 0, 0};
-    DC zp[3], zm[3];
-#pragma unroll
-    for (int arm = 0; arm < 3; ++arm) {
-        const double nx = tab.arm[(arm * 3 + 0) * N + n], ny = tab.arm[(arm * 3 + 1) * N + n],
-                     nz = tab.arm[(arm * 3 + 2) * N + n];
-        const double kn = c.k[0] * nx + c.k[1] * ny + c.k[2] * nz;
-        const double nu = c.u[0] * nx + c.u[1] * ny + c.u[2] * nz;
-        const double nv = c.v[0] * nx + c.v[1] * ny + c.v[2] * nz;
-        const double nw = c.w[0] * nx + c.w[1] * ny + c.w[2] * nz;
-        double dkn[K] = {0, 0, nu, c.cb * nv, 0, 0, 0, 0};
-        const double Fp = nu * nu - nv * nv, Fx = 2.0 * nu * nv;
-        const double dFp_b = -2.0 * nu * kn, dFx_b = -2.0 * kn * nv;
-        const double dFp_l = -2.0 * c.sb * nu * nv - 2.0 * nv * nw;
-        const double dFx_l = -2.0 * c.sb * nv * nv + 2.0 * nu * nw;
-        DC G;
-        G.v = cadd(cscale(c.al, Fp), cscale(c.ga, Fx));
-        G.d[0] = {0.0, 0.0};
-        G.d[1] = {0.0, 0.0};
-        G.d[2] = cadd(cscale(c.al, dFp_b), cscale(c.ga, dFx_b));
-        G.d[3] = cadd(cscale(c.al, dFp_l), cscale(c.ga, dFx_l));
-        G.d[4] = cadd(cscale(c.al_i[0], Fp), cscale(c.ga_i[0], Fx));
-        G.d[5] = cadd(cscale(c.al_i[1], Fp), cscale(c.ga_i[1], Fx));
-        G.d[6] = cadd(cscale(c.al_i[2], Fp), cscale(c.ga_i[2], Fx));
-        G.d[7] = {0.0, 0.0};
-        const int rp = arm == 2 ? 0 : arm + 1, rm = arm;
-#pragma unroll
-        for (int sgn = 0; sgn < 2; ++sgn) {
-            const double sdir = sgn == 0 ? 1.0 : -1.0;   // +n link: X = a(1 - kn); -n link: X = a(1 + kn)
-            const double X = a * (1.0 - sdir * kn);
-            C Tv, Td;
-            transfer(X, Tv, Td);
-            DC Tl;
-            Tl.v = Tv;
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const double dX = da[k] * (1.0 - sdir * kn) - sdir * a * dkn[k];
-                Tl.d[k] = cscale(Td, dX);
-            }
-            const DC z = dmul(dmul(Tl, G), rx[sgn == 0 ? rp : rm]);
-            if (sgn == 0)
-                zp[arm] = z;
-            else
-                zm[arm] = z;
-        }
-    }
-    // D = exp(-i f/f*)
-    DC D;
-    {
-        double s, co;
-        sincos(f / g.fstar, &s, &co);
-        D.v = {co, -s};
-        const double df[K] = {1.0 / g.fstar, t / g.fstar, 0, 0, 0, 0, 0, 0};
-#pragma unroll
-        for (int k = 0; k < K; ++k) D.d[k] = {-s * df[k], -co * df[k]};   // -i D df
-    }
-    const DC Xp = dadd(dsub(zm[0], zp[2]), dmul(D, dsub(zp[0], zm[2])));
-    const DC Yp = dadd(dsub(zm[1], zp[0]), dmul(D, dsub(zp[1], zm[0])));
-    const DC Zp = dadd(dsub(zm[2], zp[1]), dmul(D, dsub(zp[2], zm[1])));
-    // F = -i a (1 - D^2)
-    const DC D2 = dmul(D, D);
-    DC F;
-    F.v = {-a * D2.v.y, -a * (1.0 - D2.v.x)};
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        // d[-i a (1 - D2)] = -i [da (1 - D2) - a dD2]
-        const C q = {da[k] * (1.0 - D2.v.x) - a * D2.d[k].x, -da[k] * D2.v.y - a * D2.d[k].y};
-        F.d[k] = {q.y, -q.x};
-    }
-    const double r2 = sqrt(2.0), r6 = sqrt(6.0);
-    const DC Ap = dscale(dsub(Zp, Xp), 1.0 / r2);
-    const DC Ep = dscale(dadd(dsub(Xp, dscale(Yp, 2.0)), Zp), 1.0 / r6);
-    Aout = dmul(F, Ap);
-    Eout = dmul(F, Ep);
-    if (Tout) *Tout = dmul(F, dscale(dadd(dadd(Xp, Yp), Zp), 1.0 / sqrt(3.0)));
+// Forward values of one sample (Sec. II): receiver phasors, the six links
+// z_ij = -i a V(a (1 -+ k.n)) (n.H.n) exp(2 pi i cyc), D = exp(-i f/f*) and
+// the combinations P of X = (1 - D^2) P (Y, Z likewise).  Link order:
+// 01, 10, 12, 21, 20, 02 (arm 0: 01, 10; arm 1: 12, 21; arm 2: 20, 02).
+struct Fwd {
+    double t, f, a, kap[3];
+    C rx[3], z[6], D, omd, PX, PY, PZ;
+};
+
+__device__ __forceinline__ void arm_geometry(const CandG& c, const OrbitTables64& tab, int arm, int N, int n,
+                                             double& kn, double& nu, double& nv, double& nw) {
+    const double nx = tab.arm[(arm * 3 + 0) * N + n], ny = tab.arm[(arm * 3 + 1) * N + n],
+                 nz = tab.arm[(arm * 3 + 2) * N + n];
+    kn = c.k[0] * nx + c.k[1] * ny + c.k[2] * nz;
+    nu = c.u[0] * nx + c.u[1] * ny + c.u[2] * nz;
+    nv = c.v[0] * nx + c.v[1] * ny;
+    nw = c.w[0] * nx + c.w[1] * ny;
 }
 
-// forward template (value only), used for the residual
-__device__ void template_value(const CandG& c, const Geo& g, const OrbitTables64& tab, const C* tw, C* bufA,
-                               C* bufE, C* bufT, int lane) {
+// receiver of link l: 01 -> 1, 10 -> 0, 12 -> 2, 21 -> 1, 20 -> 0, 02 -> 2
+__device__ __forceinline__ int link_rx(int l) { return l == 0 ? 1 : l == 1 ? 0 : l == 2 ? 2 : l == 3 ? 1 : l == 4 ? 0 : 2; }
+
+__device__ void forward(const CandG& c, const Geo& g, const OrbitTables64& tab, int n, Fwd& fw) {
+    const int N = g.N;
+    const double inv_c = 1.0 / kC;
+    fw.t = (double)n * g.T_over_N;
+    const double t = fw.t;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const double kap = (c.k[0] * tab.x[(j * 3 + 0) * N + n] + c.k[1] * tab.x[(j * 3 + 1) * N + n] +
+                            c.k[2] * tab.x[(j * 3 + 2) * N + n]) * inv_c;
+        fw.kap[j] = kap;
+        double cyc = c.delta * ((double)n / (double)N) + 0.5 * c.fd * (t * t) - c.f0 * kap - c.fd * t * kap +
+                     0.5 * c.fd * (kap * kap) + c.phi0c;
+        cyc -= rint(cyc);
+        double s, co;
+        sincospi(2.0 * cyc, &s, &co);
+        fw.rx[j] = {co, s};
+    }
+    fw.f = c.f0 + c.fd * t;
+    fw.a = fw.f * (0.5 * g.inv_fstar);
+#pragma unroll
+    for (int arm = 0; arm < 3; ++arm) {
+        double kn, nu, nv, nw;
+        arm_geometry(c, tab, arm, N, n, kn, nu, nv, nw);
+        const double Fp = (nu - nv) * (nu + nv), Fx = 2.0 * nu * nv;
+        const C G = cadd(cscale(c.al, Fp), cscale(c.ga, Fx));
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int l = 2 * arm + s;
+            C V, Vd;
+            transfer<false>(fw.a * (s == 0 ? 1.0 - kn : 1.0 + kn), c.J, V, Vd);
+            const C q = cmul(cmul(cscale(V, fw.a), G), fw.rx[link_rx(l)]);
+            fw.z[l] = {q.y, -q.x};   // times -i
+        }
+    }
+    // D = exp(-i f/f*) = exp(-i f0/f*) exp(-i th), th = fdot t/f*: a short
+    // series while |th| <= 1/64
+    const double th = c.eps * t;
+    if (fabs(th) <= 0.015625) {
+        const double t2 = th * th;
+        const double cs = fma(fma(fma(t2, -1.0 / 720.0, 1.0 / 24.0), t2, -0.5), t2, 1.0);
+        const double sn = th * fma(fma(fma(t2, -1.0 / 5040.0, 1.0 / 120.0), t2, -1.0 / 6.0), t2, 1.0);
+        fw.D = cmul({c.D0r, c.D0i}, {cs, -sn});
+    } else {
+        double sD, cD;
+        sincos(fw.f * g.inv_fstar, &sD, &cD);
+        fw.D = {cD, -sD};
+    }
+    const C D2 = cmul(fw.D, fw.D);
+    fw.omd = {1.0 - D2.x, -D2.y};
+    const C* z = fw.z;
+    fw.PX = csub(cadd(z[1], cmul(fw.D, z[0])), cadd(z[4], cmul(fw.D, z[5])));
+    fw.PY = csub(cadd(z[3], cmul(fw.D, z[2])), cadd(z[0], cmul(fw.D, z[1])));
+    fw.PZ = csub(cadd(z[5], cmul(fw.D, z[4])), cadd(z[2], cmul(fw.D, z[3])));
+}
+
+constexpr double kR2 = 0.70710678118654752, kR6 = 0.40824829046386302, kR3 = 0.57735026918962576;
+
+// template samples (values) at bit-reversed positions
+__device__ void template_value(const CandG& c, const Geo& g, const OrbitTables64& tab, C* bufA, C* bufE, C* bufT,
+                               int lane) {
     const int N = g.N;
     for (int n = lane; n < N; n += 32) {
-        DC Ad, Ed, Td;
-        sample_dual(c, g, tab, n, Ad, Ed, bufT ? &Td : nullptr);
+        Fwd fw;
+        forward(c, g, tab, n, fw);
+        const C X = cmul(fw.omd, fw.PX), Y = cmul(fw.omd, fw.PY), Z = cmul(fw.omd, fw.PZ);
         const int br = (int)(__brev((unsigned)n) >> (32 - g.logN));
-        bufA[br] = Ad.v;
-        bufE[br] = Ed.v;
-        if (bufT) bufT[br] = Td.v;
+        bufA[br] = cscale(csub(Z, X), kR2);
+        bufE[br] = cscale(cadd(csub(X, cscale(Y, 2.0)), Z), kR6);
+        if (bufT) bufT[br] = cscale(cadd(cadd(X, Y), Z), kR3);
     }
     __syncwarp();
+}
+
+// Per-lane gradient accumulators: f0, fdot, beta, lambda, phi0 directly;
+// A, iota, psi through the adjoints of alpha and gamma.
+struct Acc {
+    double f0, fd, beta, lam, phi0;
+    C al, ga;
+};
+
+// Reverse-mode step of one sample: the adjoints cA, cE (and cT) of the
+// channel samples s_n give Re(conj(c) d s_n/d theta) summed into acc.
+__device__ void sample_adjoint(const CandG& c, const Geo& g, const OrbitTables64& tab, int n, C cA, C cE, C cT,
+                               bool useT, Acc& acc) {
+    const int N = g.N;
+    Fwd fw;
+    forward(c, g, tab, n, fw);
+    // A = (Z - X)/sqrt2, E = (X - 2Y + Z)/sqrt6, T = (X + Y + Z)/sqrt3
+    C Xb = cadd(cscale(cA, -kR2), cscale(cE, kR6)), Yb = cscale(cE, -2.0 * kR6), Zb = cadd(cscale(cA, kR2),
+                                                                                        cscale(cE, kR6));
+    if (useT) {
+        Xb = cadd(Xb, cscale(cT, kR3));
+        Yb = cadd(Yb, cscale(cT, kR3));
+        Zb = cadd(Zb, cscale(cT, kR3));
+    }
+    // X = omd PX, ...
+    const C omdb = cadd(cadd(cmulc(Xb, fw.PX), cmulc(Yb, fw.PY)), cmulc(Zb, fw.PZ));
+    const C PXb = cmulc(Xb, fw.omd), PYb = cmulc(Yb, fw.omd), PZb = cmulc(Zb, fw.omd);
+    // PX = z10 + D z01 - z20 - D z02, PY = z21 + D z12 - z01 - D z10, PZ = z02 + D z20 - z12 - D z21
+    const C* z = fw.z;
+    C zb[6];
+    zb[0] = csub(cmulc(PXb, fw.D), PYb);   // z01
+    zb[1] = csub(PXb, cmulc(PYb, fw.D));   // z10
+    zb[2] = csub(cmulc(PYb, fw.D), PZb);   // z12
+    zb[3] = csub(PYb, cmulc(PZb, fw.D));   // z21
+    zb[4] = csub(cmulc(PZb, fw.D), PXb);   // z20
+    zb[5] = csub(PZb, cmulc(PXb, fw.D));   // z02
+    // D enters the combinations and omd = 1 - D^2
+    C Db = cadd(cadd(cmulc(PXb, csub(z[0], z[5])), cmulc(PYb, csub(z[2], z[1]))), cmulc(PZb, csub(z[4], z[3])));
+    Db = csub(Db, cmulc(omdb, cscale(fw.D, 2.0)));
+    // D = exp(-i f/f*): dD = -i D df/f*
+    double fb = (Db.x * fw.D.y - Db.y * fw.D.x) * g.inv_fstar;
+    double ab = 0.0;
+    C rxb[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+#pragma unroll
+    for (int arm = 0; arm < 3; ++arm) {
+        double kn, nu, nv, nw;
+        arm_geometry(c, tab, arm, N, n, kn, nu, nv, nw);
+        const double Fp = (nu - nv) * (nu + nv), Fx = 2.0 * nu * nv;
+        const C G = cadd(cscale(c.al, Fp), cscale(c.ga, Fx));
+        C Gb = {0.0, 0.0};
+        double knb = 0.0;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int l = 2 * arm + s;
+            const int j = link_rx(l);
+            const double sg = s == 0 ? -1.0 : 1.0;   // X = a (1 + sg kn)
+            const double Xa = fw.a * (1.0 + sg * kn);
+            C V, Vd;
+            transfer<true>(Xa, c.J, V, Vd);
+            // z = -i a V W, W = G rx: with zz = i zbar and P = conj(zz) W,
+            // abar += Re(P V), Xbar = a Re(P V'), Wbar = a zz conj(V)
+            const C zz = {-zb[l].y, zb[l].x};
+            const C W = cmul(G, fw.rx[j]);
+            const C P = cmulc(W, zz);
+            ab += P.x * V.x - P.y * V.y;
+            const double Xb_ = fw.a * (P.x * Vd.x - P.y * Vd.y);
+            const C Wb = cscale(cmulc(zz, V), fw.a);
+            Gb = cadd(Gb, cmulc(Wb, fw.rx[j]));
+            rxb[j] = cadd(rxb[j], cmulc(Wb, G));
+            ab += Xb_ * (1.0 + sg * kn);
+            knb += sg * fw.a * Xb_;
+        }
+        // G = alpha Fp + gamma Fx
+        acc.al = cadd(acc.al, cscale(Gb, Fp));
+        acc.ga = cadd(acc.ga, cscale(Gb, Fx));
+        const double Fpb = redot(Gb, c.al), Fxb = redot(Gb, c.ga);
+        const double nub = 2.0 * (nu * Fpb + nv * Fxb), nvb = 2.0 * (nu * Fxb - nv * Fpb);
+        acc.beta += knb * nu - nub * kn;
+        acc.lam += knb * c.cb * nv - nub * c.sb * nv + nvb * nw;
+    }
+    // receiver phases rx_j = exp(2 pi i cyc_j)
+    const double inv_c = 1.0 / kC;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const double pb = fw.rx[j].x * rxb[j].y - fw.rx[j].y * rxb[j].x;   // Re(conj(rxbar) i rx)
+        const double cycb = 2.0 * kPi * pb;
+        const double x0 = tab.x[(j * 3 + 0) * N + n], x1 = tab.x[(j * 3 + 1) * N + n],
+                     x2 = tab.x[(j * 3 + 2) * N + n];
+        const double ux = (c.u[0] * x0 + c.u[1] * x1 + c.u[2] * x2) * inv_c;
+        const double vx = (c.v[0] * x0 + c.v[1] * x1) * inv_c;
+        const double tk = fw.t - fw.kap[j], fk = fw.f - c.fd * fw.kap[j];
+        acc.f0 += cycb * tk;
+        acc.fd += 0.5 * cycb * (tk * tk);
+        acc.beta -= cycb * fk * ux;
+        acc.lam -= cycb * fk * c.cb * vx;
+        acc.phi0 += pb;
+    }
+    // a = f/(2 f*), f = f0 + fdot t
+    fb += ab * (0.5 * g.inv_fstar);
+    acc.f0 += fb;
+    acc.fd += fb * fw.t;
 }
 
 __device__ void fft_inplace(int N, int logN, const C* tw, C* bufA, C* bufE, C* bufT, int lane) {
@@ -365,7 +442,7 @@ __global__ void __launch_bounds__(kWarpsG * 32) grad64_kernel(
     g.logN = 31 - __clz(win.N);
     g.T = T;
     g.T_over_N = T / (double)win.N;
-    g.fstar = fstar;
+    g.inv_fstar = 1.0 / fstar;
     g.scale = T / (2.0 * (double)win.N);
     const OrbitTables64 tab = tabs.t[g.logN - 5];
     const int N = g.N;
@@ -378,7 +455,7 @@ __global__ void __launch_bounds__(kWarpsG * 32) grad64_kernel(
     const int64_t c_lo = tile.c_begin + (int64_t)warp * grp;
     const int64_t c_hi = min(tile.c_end, c_lo + grp);
     if (c_lo >= c_hi) return;
-    if (c_lo + lane < c_hi) setup_grad(theta + 8 * (c_lo + lane), T, mycand[lane]);
+    if (c_lo + lane < c_hi) setup_grad(theta + 8 * (c_lo + lane), T, g.inv_fstar, mycand[lane]);
     __syncwarp();
     for (int64_t cidx = c_lo; cidx < c_hi; ++cidx) {
         const CandG& c = mycand[cidx - c_lo];
@@ -391,7 +468,7 @@ __global__ void __launch_bounds__(kWarpsG * 32) grad64_kernel(
             continue;
         }
         // (1) template
-        template_value(c, g, tab, tw, bufA, bufE, bufT, lane);
+        template_value(c, g, tab, bufA, bufE, bufT, lane);
         fft_inplace(N, g.logN, tw, bufA, bufE, bufT, lane);
         // (2) logL and residual r_m = w (d - h) at DFT index m mod N, in place
         double sdh = 0.0, shh = 0.0;
@@ -446,23 +523,21 @@ __global__ void __launch_bounds__(kWarpsG * 32) grad64_kernel(
         }
         __syncwarp();
         fft_inplace(N, g.logN, tw, bufA, bufE, bufT, lane);
-        // (4) tangent sweep: g_i += Re(c_n conj(ds_n/dtheta_i)), c_n = conj(buf[n])
-        double gacc[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) gacc[k] = 0.0;
+        // (4) reverse-mode sweep: the adjoint of sample n is c_n = conj(buf[n])
+        Acc acc = {0.0, 0.0, 0.0, 0.0, 0.0, {0.0, 0.0}, {0.0, 0.0}};
         for (int n = lane; n < N; n += 32) {
-            DC Ad, Ed, Td;
-            sample_dual(c, g, tab, n, Ad, Ed, useT ? &Td : nullptr);
             const C cA = {bufA[n].x, -bufA[n].y}, cE = {bufE[n].x, -bufE[n].y};
-#pragma unroll
-            for (int k = 0; k < K; ++k)
-                gacc[k] += cA.x * Ad.d[k].x + cA.y * Ad.d[k].y + cE.x * Ed.d[k].x + cE.y * Ed.d[k].y;
-            if (useT) {
-                const C cT = {bufT[n].x, -bufT[n].y};
-#pragma unroll
-                for (int k = 0; k < K; ++k) gacc[k] += cT.x * Td.d[k].x + cT.y * Td.d[k].y;
-            }
+            const C cT = useT ? C{bufT[n].x, -bufT[n].y} : C{0.0, 0.0};
+            sample_adjoint(c, g, tab, n, cA, cE, cT, useT, acc);
         }
+        double gacc[K];
+        gacc[0] = acc.f0;
+        gacc[1] = acc.fd;
+        gacc[2] = acc.beta;
+        gacc[3] = acc.lam;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gacc[4 + k] = redot(acc.al, c.al_i[k]) + redot(acc.ga, c.ga_i[k]);
+        gacc[7] = acc.phi0;
 #pragma unroll
         for (int k = 0; k < K; ++k) gacc[k] = wsum(gacc[k]) * (2.0 / (double)N);
         if (lane == 0) {

@@ -562,9 +562,8 @@ constexpr float kMixedRoundingBound = 1e-6f;
 // logL/T, log g and w added for the rounding of w = logL/T - log g (or
 // (logL - log g)/T), two rows' bounds add up to the uncertainty of
 // Delta = w_i - w_c.  Rounded up; +inf when a value is not finite.
-__device__ __forceinline__ float mixed_bound(double l, double dh, double hh, double g, float invT, float eps,
-                                             float cf) {
-    const float lf = (float)l, d1 = (float)dh, h2 = (float)hh, gf = (float)g;
+__device__ __forceinline__ float mixed_bound_f(float lf, float d1, float h2, float gf, float invT, float eps,
+                                               float cf) {
     const float mag = fabsf(d1) + fabsf(h2) + fabsf(lf);
     const float dd = fabsf(2.0f * (d1 - 0.5f * h2 - lf)) + 3e-7f * mag;
     const float nh = sqrtf(fmaxf(h2, 0.0f)), nd = sqrtf(dd);
@@ -575,6 +574,11 @@ __device__ __forceinline__ float mixed_bound(double l, double dh, double hh, dou
     return (isfinite(b) && isfinite(lf) && isfinite(gf) && invT > 0.0f) ? b : CUDART_INF_F;
 }
 
+// logL, log g of one row in float (the bound's own inputs)
+struct RowF {
+    float l, g;
+};
+
 __device__ __forceinline__ bool accept_rt(int rule, double wj, double uj, double wc, double T) {
     if (rule == kPlain) return accept<kPlain>(wj, uj, wc, T);
     if (rule == kTempered) return accept<kTempered>(wj, uj, wc, T);
@@ -583,7 +587,7 @@ __device__ __forceinline__ bool accept_rt(int rule, double wj, double uj, double
 
 // Certification of chains built from values of which some carry an error
 // bound (one CTA per chain and chunk of kCertChunk steps).  Pass 0 computes
-// the bounds (mixed_bound) and stores them in err; later passes read them
+// the bounds (mixed_bound_f) and stores them in err; later passes read them
 // (0 once a row is re-evaluated).  Step i (i >= 1)
 // compares proposal i with the state c = chain[i - 1] before it; its double
 // decision log u_i < Delta is the one exact values give unless
@@ -604,31 +608,65 @@ __global__ void __launch_bounds__(kMhThreads) mh_certify_kernel(
     int* __restrict__ done, int32_t* __restrict__ q_lo, int32_t* __restrict__ q_hi, const int* __restrict__ gate,
     int* __restrict__ n_new) {
     if (gate && *gate == 0) return;
-    __shared__ int local, nstep, off, soff, last;
+    __shared__ int local, nstep, off, soff, last, s_rule;
+    __shared__ float s_invT;
     __shared__ int32_t rows[2 * kCertChunk], stp[kCertChunk];
     const int r = blockIdx.x / n_chunks, k = blockIdx.x - r * n_chunks;
-    if (threadIdx.x == 0) local = nstep = 0;
-    __syncthreads();
     const size_t base = (size_t)r * (size_t)n;
-    const double T = temperature[r];
-    const int rule = rule_of(T, literal);
+    if (threadIdx.x == 0) {
+        local = nstep = 0;
+        // the chain's rule and 1/T, formed once (a double division per thread
+        // would load the FP64 pipe as much as the rest of the pass)
+        const double T = temperature[r];
+        s_rule = rule_of(T, literal);
+        s_invT = (T > 0.0 && T <= DBL_MAX) ? (float)(1.0 / T) : 0.0f;
+    }
+    __syncthreads();
+    const int rule = s_rule;
+    const float invT = s_invT;
     const int i = 1 + k * kCertChunk + (int)threadIdx.x;
     if (i < n) {
         const int c = chain[base + i - 1];
+        const RowF fi{(float)logL[base + i], (float)log_g[base + i]};
+        const RowF fc{(float)logL[base + c], (float)log_g[base + c]};
         float ei, ec;
         if (pass == 0) {
-            const float invT = (T > 0.0 && T <= DBL_MAX) ? (float)(1.0 / T) : 0.0f;
-            ei = mixed_bound(logL[base + i], dh[base + i], hh[base + i], log_g[base + i], invT, eps, cf);
-            ec = mixed_bound(logL[base + c], dh[base + c], hh[base + c], log_g[base + c], invT, eps, cf);
+            ei = mixed_bound_f(fi.l, (float)dh[base + i], (float)hh[base + i], fi.g, invT, eps, cf);
+            ec = mixed_bound_f(fc.l, (float)dh[base + c], (float)hh[base + c], fc.g, invT, eps, cf);
             err[base + i] = ei;
-            if (i == 1) err[base] = mixed_bound(logL[base], dh[base], hh[base], log_g[base], invT, eps, cf);
+            if (i == 1)
+                err[base] = mixed_bound_f((float)logL[base], (float)dh[base], (float)hh[base], (float)log_g[base], invT,
+                                          eps, cf);
         } else {
             ei = err[base + i];
             ec = err[base + c];
         }
         const double u = log_u[base + i];
-        bool settled = (ei == 0.0f && ec == 0.0f) || is_nan(u) || !(u < 0.0);
+        const long long ku = __double_as_longlong(u);
+        // a NaN log u, or one that is not below zero, rejects under any value
+        bool settled = (ei == 0.0f && ec == 0.0f) || is_nan(u) || !(ku < 0 && ku != LLONG_MIN);
         if (!settled) {
+            // float test first: Delta and log u in float, with a margin of
+            // 1e-6 of the magnitudes that covers the conversions and the
+            // float operations, so that it settles only steps the double
+            // test below settles too
+            float li = fi.l, lc = fc.l;
+            if (rule == kTempered) {
+                li *= invT;
+                lc *= invT;
+            }
+            float df = (li - fi.g) - (lc - fc.g);
+            float S = fabsf(li) + fabsf(fi.g) + fabsf(lc) + fabsf(fc.g);
+            if (rule == kDivide) {
+                df *= invT;
+                S *= invT;
+            }
+            const float uf = (float)u;
+            const float thr = (ei + ec) * 1.000001f + 1e-6f * (S + fabsf(uf));
+            settled = isfinite(df) && isfinite(thr) && fabsf(uf - df) > thr;
+        }
+        if (!settled) {
+            const double T = temperature[r];
             const double wi = weight_rt(rule, logL[base + i], log_g[base + i], T);
             const double wc = weight_rt(rule, logL[base + c], log_g[base + c], T);
             double d = __dadd_rn(wi, -wc);
