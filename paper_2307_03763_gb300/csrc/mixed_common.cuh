@@ -1037,12 +1037,24 @@ __device__ __forceinline__ void kahan_merge(f2 sum, f2 comp, float& s, float& c)
     c = (comp.x + comp.y) - e;
 }
 
+// Swizzled position of element e of an N-element channel-pair buffer: the
+// low three index bits XORed with higher ones, chosen (by exhaustive search
+// over such maps) so that both the reads in sample order (r 32 + lane) and
+// the stores at the bins bin_of<R>(kbase, q) leave the eight lanes of each
+// quarter-warp in eight different 16-byte bank groups.
+__device__ __forceinline__ int nat_sw(int e, int N) {
+    if (N == 32) return e ^ ((e >> 3) & 3);
+    if (N == 64) return e ^ ((e >> 3) & 7);
+    if (N == 128) return e ^ ((e >> 3) & 1) ^ ((e >> 5) & 2);
+    return e ^ ((e >> 3) & 6);
+}
+
 // Transform of both channels of one candidate (buf: N channel-pair elements,
-// sample n at n; with ONE the samples are read from src, one complex float
-// each, the second channel zero, and buf is only the workspace).  On return
-// x[q] holds the DFT at index K(q) = bin_of<R>(kbase, q) (returned: kbase),
-// and the transform is done with buf.
-template <int R, bool ONE = false>
+// sample n at n, or at nat_sw(n) with SWIN; with ONE the samples are read
+// from src, one complex float each, the second channel zero, and buf is only
+// the workspace).  On return x[q] holds the DFT at index K(q) =
+// bin_of<R>(kbase, q) (returned: kbase), and the transform is done with buf.
+template <int R, bool ONE = false, bool SWIN = false>
 __device__ __forceinline__ int nat_transform(float4* buf, const OrbitTables32& tab, const LaneTw& ltw, int lane,
                                              cpair (&x)[R], const float2* src = nullptr) {
     constexpr int N = 32 * R, G = 32 / R;
@@ -1055,7 +1067,7 @@ __device__ __forceinline__ int nat_transform(float4* buf, const OrbitTables32& t
             const float2 v = src[r * 32 + lane];
             x[r] = cpair{make_float2(v.x, 0.0f), make_float2(v.y, 0.0f)};
         } else {
-            x[r] = ld4(buf + r * 32 + lane);
+            x[r] = ld4(buf + (SWIN ? nat_sw(r * 32 + lane, N) : r * 32 + lane));
         }
     }
     reg_fft2<R>(x);

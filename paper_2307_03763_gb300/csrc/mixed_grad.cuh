@@ -344,7 +344,8 @@ __device__ __forceinline__ void sample_adjoint(const CandGx& g, const OrbitTable
 // cT may be null in the T instantiation, for windows without T).  Sums are
 // per lane and sample slot, then merged exactly (two-sum of the slots).
 // PACKED: the cotangents of both channels come from one array of
-// channel-pair elements (A re, E re, A im, E im) at sample n (cA; cE unused).
+// channel-pair elements (A re, E re, A im, E im) at nat_sw(n, N) (cA; cE
+// unused).
 template <int J, bool T3 = false, bool PACKED = false>
 __device__ void adjoint_sweep(const CandGx& g, const OrbitTables32& tab, int N, float Tf, float inv_fstar,
                               const float2* cA, const float2* cE, int lane, float (&tacc)[KT][2],
@@ -365,7 +366,7 @@ __device__ void adjoint_sweep(const CandGx& g, const OrbitTables32& tab, int N, 
         cpair a, e;
         if constexpr (PACKED) {
             const float4* b4 = (const float4*)cA;
-            const float4 x = b4[n0], y = two ? b4[n1] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            const float4 x = b4[nat_sw(n0, N)], y = two ? b4[nat_sw(n1, N)] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             a = cpair{make_float2(x.x, y.x), make_float2(x.z, y.z)};
             e = cpair{make_float2(x.y, y.y), make_float2(x.w, y.w)};
         } else {
@@ -544,8 +545,10 @@ __device__ void residual_adjoint2(float2* bufA, float2* bufE, const OrbitTables3
 // slow part): forward transform and window inner products as the likelihood
 // kernel forms them, the conjugated residual conj(w^ (d^ - kappa S)) stored at
 // its DFT index, the same transform again (the adjoint, conjugated), and
-// c^_n left at sample n, each as a channel-pair element.  Sums are joined
-// into (sdh, cdh) and (shh, chh).
+// c^_n left at sample n, each as a channel-pair element; both stores and the
+// second transform's reads go through nat_sw, which keeps the scattered bin
+// stores free of bank conflicts.  Sums are joined into (sdh, cdh) and
+// (shh, chh).
 template <int R>
 __device__ void residual_adjoint_nat(float4* buf, const OrbitTables32& tab, const LaneTw& ltw, int lane, int off,
                                      int W, const Win32* __restrict__ pw, float kappa, float& sdh, float& cdh,
@@ -567,7 +570,7 @@ __device__ void residual_adjoint_nat(float4* buf, const OrbitTables32& tab, cons
             kahan_add2(s_hh, c_hh, pmul(v.w, pfma(x[q].re, x[q].re, pmul(x[q].im, x[q].im))));
             rc = cpair{pmul(v.w, pfma(bc(-kappa), x[q].re, v.dre)), pneg(pmul(v.w, pfma(bc(-kappa), x[q].im, v.dim)))};
         }
-        st4(buf + K, rc);
+        st4(buf + nat_sw(K, N), rc);
     }
     float ps, pc;
     kahan_merge(s_dh, c_dh, ps, pc);
@@ -575,10 +578,10 @@ __device__ void residual_adjoint_nat(float4* buf, const OrbitTables32& tab, cons
     kahan_merge(s_hh, c_hh, ps, pc);
     kahan_join(shh, chh, ps, pc);
     __syncwarp();
-    kbase = nat_transform<R>(buf, tab, ltw, lane, x);
+    kbase = nat_transform<R, false, true>(buf, tab, ltw, lane, x);
     __syncwarp();
 #pragma unroll
-    for (int q = 0; q < R; ++q) st4(buf + bin_of<R>(kbase, q), cpair{x[q].re, pneg(x[q].im)});   // c^_n
+    for (int q = 0; q < R; ++q) st4(buf + nat_sw(bin_of<R>(kbase, q), N), cpair{x[q].re, pneg(x[q].im)});   // c^_n
     __syncwarp();
 }
 
