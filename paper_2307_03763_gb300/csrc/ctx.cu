@@ -86,8 +86,14 @@ __global__ void build_tables_kernel(int N, double T, double L, double* tab64, fl
     // c_2f+1(n), c_2f+1(n+32)), at f N/2 + 32 h + lane
     const int r = n / 32, l = n % 32;
     if (N >= 64) {
+        // components 12..15: cos a, sin a (float), then cos a, sin a in Q1.31
+        // (int bits) for the fixed-point carrier phase of the paired slow part
+        auto q31 = [](double x) {
+            const double v = rint(x * 2147483648.0);
+            return __int_as_float((int)fmin(fmax(v, -2147483647.0), 2147483647.0));
+        };
         const float comp[16] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w,
-                                g2.x, g2.y, g2.z, g2.w, g3.x, g3.y, g3.z, g3.w};
+                                g2.x, g2.y, g2.z, g2.w, chi, shi, q31(ca), q31(sa)};
         float* GP = tab32 + 34 * N;
         const int odd = r & 1;
         for (int f = 0; f < 8; ++f) {

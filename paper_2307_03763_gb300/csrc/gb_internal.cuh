@@ -59,6 +59,8 @@ struct OrbitTables32 {
     const float2* ltw;   // [R][32]                exp(-2 pi i r l / N), lane twiddles
     const float4* gn;    // [4][N], the same values in natural sample order
     const float4* gp;    // [8][N/2], sample pairs (n, n + 32) of each lane, component pairs
+                         // (components 0..11 as g[0..2]; 12, 13 cos a, sin a hi; 14, 15
+                         // cos a, sin a in Q1.31 as int bits)
     const float4* ltw4;  // [R][32]                the lane twiddles as (re, re, im, im)
 };
 

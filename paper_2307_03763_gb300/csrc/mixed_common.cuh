@@ -76,6 +76,15 @@ struct CandMix {
     int bad;
     long long q;
     double A;
+    // The carrier phase in fixed point for the paired slow part (cycles as
+    // unsigned fractions, so that sums wrap modulo one exactly): phi0/2pi in
+    // units of 2^-64; delta mod 1024 in units of 2^-54 and fdot T^2/2 mod 2^20
+    // in units of 2^-44, which shifts by 10 - log2 N and 20 - 2 log2 N bring
+    // to 2^-64 per unit of n and n^2; f0 Kc and f0 Ks in units of 2^-26
+    // (|f0 K| < 31 cycles, else wide).
+    unsigned long long C0, K1, K2;
+    int Fc, Fs;
+    int wide;           // outside the fixed-point ranges: the scalar slow part
 };
 
 // per-candidate sums left by the warp for the lane-parallel epilogue
@@ -357,6 +366,17 @@ __device__ void setup_mixed(const double* th, double T, double ifs, CandMix& c) 
     c.D0r = cD;
     c.D0i = -sD;
     c.eps = (float)(fd * T * ifs);
+    // fixed-point phase coefficients (reductions exact in double)
+    c.C0 = (unsigned long long)__double2ll_rn(p0 * 0x1p62) << 2;
+    const double dr = delta - 1024.0 * rint(delta * (1.0 / 1024.0));
+    const double cq2 = 0.5 * fd * T * T;
+    const double c2r = cq2 - 0x1p20 * rint(cq2 * 0x1p-20);
+    c.K1 = (unsigned long long)__double2ll_rn(dr * 0x1p54);
+    c.K2 = (unsigned long long)__double2ll_rn(c2r * 0x1p44);
+    const double Fc = f0 * Kc, Fs = f0 * Ks;
+    c.wide = !(fabs(Fc) < 31.0 && fabs(Fs) < 31.0 && fabs(c2r) < 0x1p19 && fabs(dr) < 512.0);
+    c.Fc = c.wide ? 0 : __double2int_rn(Fc * 0x1p26);
+    c.Fs = c.wide ? 0 : __double2int_rn(Fs * 0x1p26);
     // largest link argument X = f (1 + |k.n|)/(2 f*) <= f_max / f*; the
     // tier keeps the first omitted series term below 2e-8 (few tiers: every
     // tier is a separate copy of the slow part in the instruction cache)
@@ -649,14 +669,35 @@ __device__ __forceinline__ cpair pcis_rx(f2 x) {
     }
 }
 
+// f0 (Kc cos a + Ks sin a) modulo one in units of 2^-32 of a cycle (rounded
+// down), from the Q1.31 cos a, sin a of a sample: the products are in units
+// of 2^-57, and |f0 K| < 31 keeps their sum inside 64 bits
+__device__ __forceinline__ unsigned dop_fix(const CandMix& c, int cq, int sq) {
+    const long long d = (long long)c.Fc * cq + (long long)c.Fs * sq;
+    return (unsigned)((unsigned long long)d >> 25);
+}
+
 // natural sample order (the likelihood kernel's transform), N >= 64; with
-// T3 and bufT also T = (X + Y + Z)/sqrt3, one complex float per sample
+// T3 and bufT also T = (X + Y + Z)/sqrt3, one complex float per sample.  The
+// carrier phase is taken in 64-bit fixed point (CandMix), where the sums
+// wrap modulo one exactly; the rest follows slow_part_mixed operation by
+// operation.
 template <int J, bool T3>
 __device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N, float2* bufA, float2* bufE,
                                int lane, float2* bufT) {
     const int R = N >> 5, H = N >> 1;
     const float invN = 1.0f / (float)N;
     const f2 r2 = bc(0.70710678118654752f), r6 = bc(0.40824829046386302f);
+    // c0 + c1 u + c2 u^2 (u = n/N) in units of 2^-64 of a cycle: exact
+    // second-order recurrence over the lane's samples n = lane + 64 h (ph),
+    // with e32 = phase(n + 32) - phase(n)
+    const int lg = __ffs(N) - 1;
+    const unsigned long long k1 = c.K1 << (10 - lg), k2 = c.K2 << (20 - 2 * lg);
+    const unsigned long long l = (unsigned long long)lane;
+    unsigned long long ph = c.C0 + k1 * l + k2 * (l * l);
+    unsigned long long dph = 64ull * k1 + k2 * (128ull * l + 4096ull);
+    unsigned long long e32 = 32ull * k1 + k2 * (64ull * l + 1024ull);
+    const unsigned long long ddph = 8192ull * k2, de32 = 4096ull * k2;
     for (int r = 0; r < R; r += 2) {
         const int m = (r >> 1) * 32 + lane;
         float4 t[8];
@@ -668,36 +709,32 @@ __device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N
         const f2 n0x = make_float2(t[3].x, t[3].y), n0y = make_float2(t[3].z, t[3].w);
         const f2 n0z = make_float2(t[4].x, t[4].y), n1x = make_float2(t[4].z, t[4].w);
         const f2 n1y = make_float2(t[5].x, t[5].y), n1z = make_float2(t[5].z, t[5].w);
-        const f2 cah = make_float2(t[6].x, t[6].y), cal = make_float2(t[6].z, t[6].w);
-        const f2 sah = make_float2(t[7].x, t[7].y), sal = make_float2(t[7].z, t[7].w);
+        // cos a, sin a (float) and the same in Q1.31 (int bits) for both samples
+        const f2 cah = make_float2(t[6].x, t[6].y), sah = make_float2(t[6].z, t[6].w);
+        const int cqa = __float_as_int(t[7].x), cqb = __float_as_int(t[7].y);
+        const int sqa = __float_as_int(t[7].z), sqb = __float_as_int(t[7].w);
         const int n = lane + 32 * r;
         const f2 u = pmul(make_float2((float)n, (float)(n + 32)), bc(invN));
-        const f2 uu = pmul(u, u);
-        // double-word products, reduced modulo one
-        f2 p1 = pmul(bc(c.c1h), u);
-        const f2 e1 = pfma(bc(c.c1l), u, pfma(bc(c.c1h), u, pneg(p1)));
-        f2 p2 = pmul(bc(c.c2h), uu);
-        const f2 e2 = pfma(bc(c.c2l), uu, pfma(bc(c.c2h), uu, pneg(p2)));
-        f2 p3 = pmul(bc(c.Fch), cah);
-        const f2 e3 = padd(pfma(bc(c.Fch), cah, pneg(p3)), pfma(bc(c.Fch), cal, pmul(bc(c.Fcl), cah)));
-        f2 p4 = pmul(bc(c.Fsh), sah);
-        const f2 e4 = padd(pfma(bc(c.Fsh), sah, pneg(p4)), pfma(bc(c.Fsh), sal, pmul(bc(c.Fsl), sah)));
-        p1 = psub(p1, print(p1));
-        p2 = psub(p2, print(p2));
-        p3 = psub(p3, print(p3));
-        p4 = psub(p4, print(p4));
-        f2 s, e, ea, eb, ec;
-        ptwo_sum(bc(c.c0h), p1, s, ea);
-        ptwo_sum(s, p2, s, eb);
-        ptwo_sum(s, pneg(p3), s, ec);
-        ptwo_sum(s, pneg(p4), s, e);
-        s = psub(s, print(s));
+        // carrier phase modulo one in units of 2^-32 of a cycle: c0 + c1 u +
+        // c2 u^2 from the exact 64-bit recurrence (its top word), minus
+        // f0 (Kc cos a + Ks sin a)
+        const unsigned pa = (unsigned)(ph >> 32) - dop_fix(c, cqa, sqa);
+        const unsigned pb = (unsigned)((ph + e32) >> 32) - dop_fix(c, cqb, sqb);
+        ph += dph;
+        dph += ddph;
+        e32 += de32;
+        // to floats: the top 20 bits and the low 12, both exact
+        const f2 xh = make_float2(__int_as_float(0x4B400000 + ((int)pa >> 12)),
+                                  __int_as_float(0x4B400000 + ((int)pb >> 12)));
+        const f2 xl = make_float2(__uint_as_float(0x4B000000u | (pa & 0xFFFu)),
+                                  __uint_as_float(0x4B000000u | (pb & 0xFFFu)));
+        const f2 Ph = pfma(xh, bc(0x1p-20f), bc(-12.0f));     // in [-1/2, 1/2)
+        const f2 Pt = pfma(xl, bc(0x1p-32f), bc(-0x1p-9f));   // in [0, 2^-20)
         const f2 K = pfma(bc(c.Kc), cah, pmul(bc(c.Ks), sah));
-        const f2 lo = padd(psub(psub(padd(padd(bc(c.c0l), e1), e2), e3), e4), padd(padd(padd(ea, eb), ec), e));
-        const f2 small = pfma(pneg(pmul(bc(c.fdT), u)), K, lo);
-        f2 Pc, Pl;
-        ptwo_sum(s, small, Pc, Pl);
-        Pc = psub(Pc, print(Pc));
+        const f2 small = pmul(pneg(pmul(bc(c.fdT), u)), K);
+        f2 Pc, e;
+        ptwo_sum(Ph, small, Pc, e);
+        const f2 Pl = padd(Pt, e);
         float sx, cx, sy, cy;
         sincospif(2.0f * Pc.x, &sx, &cx);
         sincospif(2.0f * Pc.y, &sy, &cy);
@@ -774,7 +811,7 @@ template <bool NAT, bool T3 = false>
 __device__ void slow_part_dispatch(const CandMix& c, const OrbitTables32& tab, int N, float2* bufA, float2* bufE,
                                    int lane, float2* bufT = nullptr) {
     if constexpr (NAT) {
-        if (N >= 64) {
+        if (N >= 64 && !c.wide) {
             switch (c.J) {
                 case 4: slow_part_pair<4, T3>(c, tab, N, bufA, bufE, lane, bufT); break;
                 case 7: slow_part_pair<7, T3>(c, tab, N, bufA, bufE, lane, bufT); break;
