@@ -85,13 +85,14 @@ __global__ void build_tables_kernel(int N, double T, double L, double* tab64, fl
     // components 2f and 2f + 1 of both samples, (c_2f(n), c_2f(n+32),
     // c_2f+1(n), c_2f+1(n+32)), at f N/2 + 32 h + lane
     const int r = n / 32, l = n % 32;
+    // cos a, sin a in Q1.31 for the fixed-point carrier phase: natural order
+    // (every N) and, below, in the paired layout
+    auto q31i = [](double x) { return (int)fmin(fmax(rint(x * 2147483648.0), -2147483647.0), 2147483647.0); };
+    auto q31 = [&](double x) { return __int_as_float(q31i(x)); };
+    ((int2*)(tab32 + 54 * N))[n] = make_int2(q31i(ca), q31i(sa));
     if (N >= 64) {
         // components 12..15: cos a, sin a (float), then cos a, sin a in Q1.31
         // (int bits) for the fixed-point carrier phase of the paired slow part
-        auto q31 = [](double x) {
-            const double v = rint(x * 2147483648.0);
-            return __int_as_float((int)fmin(fmax(v, -2147483647.0), 2147483647.0));
-        };
         const float comp[16] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w,
                                 g2.x, g2.y, g2.z, g2.w, chi, shi, q31(ca), q31(sa)};
         float* GP = tab32 + 34 * N;
@@ -143,7 +144,7 @@ OrbitTables64 tables64(const gb_ctx* ctx, int N) {
 OrbitTables32 tables32(const gb_ctx* ctx, int N) {
     const float* t = ctx->d_tab32[size_index(N)];
     return OrbitTables32{(const float4*)t, (const float2*)(t + 16 * N), (const float4*)(t + 18 * N),
-                         (const float4*)(t + 34 * N), (const float4*)(t + 50 * N)};
+                         (const float4*)(t + 34 * N), (const float4*)(t + 50 * N), (const int2*)(t + 54 * N)};
 }
 
 TabSet64 tabset64(const gb_ctx* ctx) {

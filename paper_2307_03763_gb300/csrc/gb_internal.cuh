@@ -62,12 +62,13 @@ struct OrbitTables32 {
                          // (components 0..11 as g[0..2]; 12, 13 cos a, sin a hi; 14, 15
                          // cos a, sin a in Q1.31 as int bits)
     const float4* ltw4;  // [R][32]                the lane twiddles as (re, re, im, im)
+    const int2* gq;      // [N]                    (cos a, sin a) in Q1.31, natural order
 };
 
 constexpr int kTab64PerN = 18;   // doubles per sample
 // floats per sample: 4 float4 (permuted) + lane twiddles + 4 float4 (natural) + 4 float4 (pairs)
-// + duplicated lane twiddles
-constexpr int kTab32PerN = 54;
+// + duplicated lane twiddles + the Q1.31 cos a, sin a
+constexpr int kTab32PerN = 56;
 
 __host__ __device__ inline int brev5(int l) {
     return ((l & 1) << 4) | ((l & 2) << 2) | (l & 4) | ((l & 8) >> 2) | ((l & 16) >> 4);

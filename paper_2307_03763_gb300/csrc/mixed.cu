@@ -303,7 +303,7 @@ extern "C" int gb_loglik_mixed_noalloc(const gb_obs_t* obs, const gb_window_t* w
         t32[i] = (float*)(b + o32);
         tabs.t[i] = OrbitTables32{(const float4*)t32[i], (const float2*)(t32[i] + 16 * N),
                                   (const float4*)(t32[i] + 18 * N), (const float4*)(t32[i] + 34 * N),
-                                  (const float4*)(t32[i] + 50 * N)};
+                                  (const float4*)(t32[i] + 50 * N), (const int2*)(t32[i] + 54 * N)};
         o64 += sizeof(double) * kTab64PerN * N;
         o32 += sizeof(float) * kTab32PerN * N;
     }

@@ -677,6 +677,49 @@ __device__ __forceinline__ unsigned dop_fix(const CandMix& c, int cq, int sq) {
     return (unsigned)((unsigned long long)d >> 25);
 }
 
+// Recurrence of c0 + c1 u + c2 u^2 (u = n/N) in units of 2^-64 of a cycle
+// over a lane's sample pairs (n, n + 32), n = lane + 64 h: exact modulo one
+struct PhaseRec {
+    unsigned long long ph, dph, e32, ddph, de32;
+    __device__ __forceinline__ PhaseRec(const CandMix& c, int N, int lane) {
+        const int lg = __ffs(N) - 1;
+        const unsigned long long k1 = c.K1 << (10 - lg), k2 = c.K2 << (20 - 2 * lg);
+        const unsigned long long l = (unsigned long long)lane;
+        ph = c.C0 + k1 * l + k2 * (l * l);
+        dph = 64ull * k1 + k2 * (128ull * l + 4096ull);
+        e32 = 32ull * k1 + k2 * (64ull * l + 1024ull);
+        ddph = 8192ull * k2;
+        de32 = 4096ull * k2;
+    }
+    // top words of the phases of n and n + 32, then advance to n + 64
+    __device__ __forceinline__ void next(unsigned& a, unsigned& b) {
+        a = (unsigned)(ph >> 32);
+        b = (unsigned)((ph + e32) >> 32);
+        ph += dph;
+        dph += ddph;
+        e32 += de32;
+    }
+};
+
+// The common phase P_c = Pc + Pl of a sample pair (Pc in [-1/2, 1/2] up to
+// small, |Pl| < 2^-19): the recurrence's top words pa, pb minus
+// f0 (Kc cos a + Ks sin a), modulo one in 32 bits, split into its top 20
+// and low 12 bits (both exact in float), plus small = -fdot T u K in float
+__device__ __forceinline__ void phase_fix(const CandMix& c, unsigned pa, unsigned pb, int cqa, int sqa, int cqb,
+                                          int sqb, f2 small, f2& Pc, f2& Pl) {
+    pa -= dop_fix(c, cqa, sqa);
+    pb -= dop_fix(c, cqb, sqb);
+    const f2 xh = make_float2(__int_as_float(0x4B400000 + ((int)pa >> 12)),
+                              __int_as_float(0x4B400000 + ((int)pb >> 12)));
+    const f2 xl = make_float2(__uint_as_float(0x4B000000u | (pa & 0xFFFu)),
+                              __uint_as_float(0x4B000000u | (pb & 0xFFFu)));
+    const f2 Ph = pfma(xh, bc(0x1p-20f), bc(-12.0f));     // in [-1/2, 1/2)
+    const f2 Pt = pfma(xl, bc(0x1p-32f), bc(-0x1p-9f));   // in [0, 2^-20)
+    f2 e;
+    ptwo_sum(Ph, small, Pc, e);
+    Pl = padd(Pt, e);
+}
+
 // natural sample order (the likelihood kernel's transform), N >= 64; with
 // T3 and bufT also T = (X + Y + Z)/sqrt3, one complex float per sample.  The
 // carrier phase is taken in 64-bit fixed point (CandMix), where the sums
@@ -688,16 +731,7 @@ __device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N
     const int R = N >> 5, H = N >> 1;
     const float invN = 1.0f / (float)N;
     const f2 r2 = bc(0.70710678118654752f), r6 = bc(0.40824829046386302f);
-    // c0 + c1 u + c2 u^2 (u = n/N) in units of 2^-64 of a cycle: exact
-    // second-order recurrence over the lane's samples n = lane + 64 h (ph),
-    // with e32 = phase(n + 32) - phase(n)
-    const int lg = __ffs(N) - 1;
-    const unsigned long long k1 = c.K1 << (10 - lg), k2 = c.K2 << (20 - 2 * lg);
-    const unsigned long long l = (unsigned long long)lane;
-    unsigned long long ph = c.C0 + k1 * l + k2 * (l * l);
-    unsigned long long dph = 64ull * k1 + k2 * (128ull * l + 4096ull);
-    unsigned long long e32 = 32ull * k1 + k2 * (64ull * l + 1024ull);
-    const unsigned long long ddph = 8192ull * k2, de32 = 4096ull * k2;
+    PhaseRec rec(c, N, lane);
     for (int r = 0; r < R; r += 2) {
         const int m = (r >> 1) * 32 + lane;
         float4 t[8];
@@ -715,26 +749,12 @@ __device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N
         const int sqa = __float_as_int(t[7].z), sqb = __float_as_int(t[7].w);
         const int n = lane + 32 * r;
         const f2 u = pmul(make_float2((float)n, (float)(n + 32)), bc(invN));
-        // carrier phase modulo one in units of 2^-32 of a cycle: c0 + c1 u +
-        // c2 u^2 from the exact 64-bit recurrence (its top word), minus
-        // f0 (Kc cos a + Ks sin a)
-        const unsigned pa = (unsigned)(ph >> 32) - dop_fix(c, cqa, sqa);
-        const unsigned pb = (unsigned)((ph + e32) >> 32) - dop_fix(c, cqb, sqb);
-        ph += dph;
-        dph += ddph;
-        e32 += de32;
-        // to floats: the top 20 bits and the low 12, both exact
-        const f2 xh = make_float2(__int_as_float(0x4B400000 + ((int)pa >> 12)),
-                                  __int_as_float(0x4B400000 + ((int)pb >> 12)));
-        const f2 xl = make_float2(__uint_as_float(0x4B000000u | (pa & 0xFFFu)),
-                                  __uint_as_float(0x4B000000u | (pb & 0xFFFu)));
-        const f2 Ph = pfma(xh, bc(0x1p-20f), bc(-12.0f));     // in [-1/2, 1/2)
-        const f2 Pt = pfma(xl, bc(0x1p-32f), bc(-0x1p-9f));   // in [0, 2^-20)
+        // carrier phase modulo one in fixed point (PhaseRec, phase_fix)
+        unsigned pa, pb;
+        rec.next(pa, pb);
         const f2 K = pfma(bc(c.Kc), cah, pmul(bc(c.Ks), sah));
-        const f2 small = pmul(pneg(pmul(bc(c.fdT), u)), K);
-        f2 Pc, e;
-        ptwo_sum(Ph, small, Pc, e);
-        const f2 Pl = padd(Pt, e);
+        f2 Pc, Pl;
+        phase_fix(c, pa, pb, cqa, sqa, cqb, sqb, pmul(pneg(pmul(bc(c.fdT), u)), K), Pc, Pl);
         float sx, cx, sy, cy;
         sincospif(2.0f * Pc.x, &sx, &cx);
         sincospif(2.0f * Pc.y, &sy, &cy);

@@ -145,8 +145,8 @@ __device__ __forceinline__ f2 pcim(cpair a, cpair b) { return pfma(a.re, b.im, p
 // arm's sum of mu rx T.
 template <int J, bool T3 = false>
 __device__ __forceinline__ void sample_adjoint(const CandGx& g, const OrbitTables32& tab, int N, int n0, int n1,
-                                               float Tf, float inv_fstar, cpair cA, cpair cE, cpair cT,
-                                               f2 (&dth)[KT], cpair& up, cpair& uq) {
+                                               unsigned pha, unsigned phb, float Tf, float inv_fstar, cpair cA,
+                                               cpair cE, cpair cT, f2 (&dth)[KT], cpair& up, cpair& uq) {
     const CandMix& c = g.m;
     const int R = N >> 5;
     const int pa = (n0 % R) * 32 + brev5(n0 / R), pb = (n1 % R) * 32 + brev5(n1 / R);
@@ -158,31 +158,38 @@ __device__ __forceinline__ void sample_adjoint(const CandGx& g, const OrbitTable
     const f2 uu = pmul(u, u);
     const f2 cah = make_float2(a3.x, b3.x), cal = make_float2(a3.y, b3.y);
     const f2 sah = make_float2(a3.z, b3.z), sal = make_float2(a3.w, b3.w);
-    // common phase in double-word arithmetic (as in the likelihood kernel)
-    f2 p1 = pmul(bc(c.c1h), u);
-    const f2 e1 = pfma(bc(c.c1l), u, pfma(bc(c.c1h), u, pneg(p1)));
-    f2 p2 = pmul(bc(c.c2h), uu);
-    const f2 e2 = pfma(bc(c.c2l), uu, pfma(bc(c.c2h), uu, pneg(p2)));
-    f2 p3 = pmul(bc(c.Fch), cah);
-    const f2 e3 = padd(pfma(bc(c.Fch), cah, pneg(p3)), pfma(bc(c.Fch), cal, pmul(bc(c.Fcl), cah)));
-    f2 p4 = pmul(bc(c.Fsh), sah);
-    const f2 e4 = padd(pfma(bc(c.Fsh), sah, pneg(p4)), pfma(bc(c.Fsh), sal, pmul(bc(c.Fsl), sah)));
-    p1 = psub(p1, print(p1));
-    p2 = psub(p2, print(p2));
-    p3 = psub(p3, print(p3));
-    p4 = psub(p4, print(p4));
-    f2 s, e, ea, eb, ec;
-    ptwo_sum(bc(c.c0h), p1, s, ea);
-    ptwo_sum(s, p2, s, eb);
-    ptwo_sum(s, pneg(p3), s, ec);
-    ptwo_sum(s, pneg(p4), s, e);
-    s = psub(s, print(s));
     const f2 K = pfma(bc(c.Kc), cah, pmul(bc(c.Ks), sah));
-    const f2 lo = padd(psub(psub(padd(padd(bc(c.c0l), e1), e2), e3), e4), padd(padd(padd(ea, eb), ec), e));
-    const f2 small = pfma(pneg(pmul(bc(c.fdT), u)), K, lo);
     f2 Pc, Pl;
-    ptwo_sum(s, small, Pc, Pl);
-    Pc = psub(Pc, print(Pc));
+    if (!c.wide) {
+        // common phase in fixed point, as in the likelihood kernel (pha, phb:
+        // the recurrence's top words for n0, n1)
+        const int2 qa = __ldg(tab.gq + n0), qb = __ldg(tab.gq + n1);
+        phase_fix(c, pha, phb, qa.x, qa.y, qb.x, qb.y, pmul(pneg(pmul(bc(c.fdT), u)), K), Pc, Pl);
+    } else {
+        // outside the fixed-point ranges: double-word arithmetic
+        f2 p1 = pmul(bc(c.c1h), u);
+        const f2 e1 = pfma(bc(c.c1l), u, pfma(bc(c.c1h), u, pneg(p1)));
+        f2 p2 = pmul(bc(c.c2h), uu);
+        const f2 e2 = pfma(bc(c.c2l), uu, pfma(bc(c.c2h), uu, pneg(p2)));
+        f2 p3 = pmul(bc(c.Fch), cah);
+        const f2 e3 = padd(pfma(bc(c.Fch), cah, pneg(p3)), pfma(bc(c.Fch), cal, pmul(bc(c.Fcl), cah)));
+        f2 p4 = pmul(bc(c.Fsh), sah);
+        const f2 e4 = padd(pfma(bc(c.Fsh), sah, pneg(p4)), pfma(bc(c.Fsh), sal, pmul(bc(c.Fsl), sah)));
+        p1 = psub(p1, print(p1));
+        p2 = psub(p2, print(p2));
+        p3 = psub(p3, print(p3));
+        p4 = psub(p4, print(p4));
+        f2 s, e, ea, eb, ec;
+        ptwo_sum(bc(c.c0h), p1, s, ea);
+        ptwo_sum(s, p2, s, eb);
+        ptwo_sum(s, pneg(p3), s, ec);
+        ptwo_sum(s, pneg(p4), s, e);
+        s = psub(s, print(s));
+        const f2 lo = padd(psub(psub(padd(padd(bc(c.c0l), e1), e2), e3), e4), padd(padd(padd(ea, eb), ec), e));
+        const f2 small = pfma(pneg(pmul(bc(c.fdT), u)), K, lo);
+        ptwo_sum(s, small, Pc, Pl);
+        Pc = psub(Pc, print(Pc));
+    }
     float sx, cx, sy, cy;
     sincospif(2.0f * Pc.x, &sx, &cx);
     sincospif(2.0f * Pc.y, &sy, &cy);
@@ -355,6 +362,7 @@ __device__ void adjoint_sweep(const CandGx& g, const OrbitTables32& tab, int N, 
     f2 sum[KT + 4];
 #pragma unroll
     for (int k = 0; k < KT + 4; ++k) sum[k] = bc(0.0f);
+    PhaseRec rec(g.m, N, lane);
     for (int n0 = lane; n0 < N; n0 += 64) {
         // N = 32: the second slot repeats sample n0 with zero cotangents
         const bool two = n0 + 32 < N;
@@ -376,7 +384,9 @@ __device__ void adjoint_sweep(const CandGx& g, const OrbitTables32& tab, int N, 
         const cpair t = (T3 && cT) ? ld(cT) : cpair{bc(0.0f), bc(0.0f)};
         f2 dth[KT] = {bc(0.0f), bc(0.0f), bc(0.0f), bc(0.0f)};
         cpair up{bc(0.0f), bc(0.0f)}, uq{bc(0.0f), bc(0.0f)};
-        sample_adjoint<J, T3>(g, tab, N, n0, n1, Tf, inv_fstar, a, e, t, dth, up, uq);
+        unsigned pha, phb;
+        rec.next(pha, phb);
+        sample_adjoint<J, T3>(g, tab, N, n0, n1, pha, phb, Tf, inv_fstar, a, e, t, dth, up, uq);
 #pragma unroll
         for (int k = 0; k < KT; ++k) sum[k] = padd(sum[k], dth[k]);
         // V = sum c conj(P) = conj(U_P)
