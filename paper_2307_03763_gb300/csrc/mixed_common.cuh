@@ -311,7 +311,10 @@ __device__ void sincos_dw(double x, double& sn, double& cs) {
 }
 
 // ifs = 1/f*, formed once per thread by the caller
-__device__ void setup_mixed(const double* th, double T, double ifs, CandMix& c) {
+// dw: also the double-word phase fields (c0h .. Fsl), which the scalar slow
+// part reads; the paired one reads them only for a candidate outside the
+// fixed-point ranges (wide), so the likelihood kernel skips them for N >= 64
+__device__ void setup_mixed(const double* th, double T, double ifs, CandMix& c, bool dw = true) {
     const double f0 = th[0], fd = th[1], beta = th[2], lam = th[3];
     const double A = th[4], iota = th[5], psi = th[6], phi0 = th[7];
     bool bad = false;
@@ -326,9 +329,6 @@ __device__ void setup_mixed(const double* th, double T, double ifs, CandMix& c) 
     const double inv2pi = 0.15915494309189535;
     double p0 = phi0 * inv2pi;
     p0 -= rint(p0);
-    split(p0, c.c0h, c.c0l);
-    split(delta, c.c1h, c.c1l);
-    split(0.5 * fd * T * T, c.c2h, c.c2l);
     double sb, cb, sl, cl;
     sincos_dw(beta, sb, cb);
     sincos_dw(lam, sl, cl);
@@ -336,8 +336,6 @@ __device__ void setup_mixed(const double* th, double T, double ifs, CandMix& c) 
     const double Kc = -r * cb * cl, Ks = -r * cb * sl;
     c.Kc = (float)Kc;
     c.Ks = (float)Ks;
-    split(f0 * Kc, c.Fch, c.Fcl);
-    split(f0 * Ks, c.Fsh, c.Fsl);
     const float fsb = (float)sb, fcb = (float)cb, fsl = (float)sl, fcl = (float)cl;
     c.k0 = -fcb * fcl;
     c.k1 = -fcb * fsl;
@@ -377,6 +375,13 @@ __device__ void setup_mixed(const double* th, double T, double ifs, CandMix& c) 
     c.wide = !(fabs(Fc) < 31.0 && fabs(Fs) < 31.0 && fabs(c2r) < 0x1p19 && fabs(dr) < 512.0);
     c.Fc = c.wide ? 0 : __double2int_rn(Fc * 0x1p26);
     c.Fs = c.wide ? 0 : __double2int_rn(Fs * 0x1p26);
+    if (dw || c.wide) {
+        split(p0, c.c0h, c.c0l);
+        split(delta, c.c1h, c.c1l);
+        split(cq2, c.c2h, c.c2l);
+        split(Fc, c.Fch, c.Fcl);
+        split(Fs, c.Fsh, c.Fsl);
+    }
     // largest link argument X = f (1 + |k.n|)/(2 f*) <= f_max / f*; the
     // tier keeps the first omitted series term below 2e-8 (few tiers: every
     // tier is a separate copy of the slow part in the instruction cache)
@@ -1473,7 +1478,7 @@ __global__ void __launch_bounds__(kWarpsMx * 32, RMAX <= 8 ? GB_MIXED_MINB : 2) 
         const int N = win.N;
         const OrbitTables32 tab = tabs.t[__ffs(N) - 6];
         const int cnt = (int)(t.c_end - t.c_begin);
-        if (lane < cnt) setup_mixed(theta + 8 * (t.c_begin + lane), T, ifs, cands[lane]);
+        if (lane < cnt) setup_mixed(theta + 8 * (t.c_begin + lane), T, ifs, cands[lane], N < 64);
         __syncwarp();
         for (int i = 0; i < cnt; ++i) {
             const CandMix& c = cands[i];
