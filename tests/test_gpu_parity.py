@@ -175,6 +175,63 @@ def test_loglik_mixed_multiband(ctx1):
     _assert_close_fp64(gf, of)
 
 
+def _fixed_point_problem(f0, fd_scale, seed):
+    # one window of N = 64 and one of N = 256, each with an injected source at
+    # f0 and 24 candidates in a small box around it (carrier bins in the
+    # window), T = 1 yr
+    rng = np.random.default_rng(seed)
+    T = YEAR
+    specs, th, srcs = [], [], []
+    for N in (64, 256):
+        src = wk.source(f0, fd_scale * float(wk.chirp_fdot(f0, 0.5)), 2e-21, rng)
+        if f0 > 60e-3:
+            src[2], src[3] = 0.1, 0.2          # |f0 Kc| near 31 cycles: the box straddles the bound
+        half = np.array([3.0 / T, 1e-3 * abs(src[1]), 0.3, 0.3, 0.1 * src[4], 0.1, 0.1, 0.1])
+        t = wk.uniform_box(src, half, 24, rng)
+        kc = int(math.floor((src[0] + 0.5 * src[1] * T) * T + 0.5))
+        specs.append((kc - N // 2, N, N))
+        th.append(t)
+        srcs.append([src])
+    wins, _, _ = wk.layout(specs, [24, 24])
+    nA, nE, wA, wE = wk.noise_and_weights(wins, T, rng)
+    return wk.Workload("fixed-point ranges", T, wins, nA, nE, wA, wE, srcs, np.concatenate(th))
+
+
+@pytest.mark.parametrize("f0,fd_scale", [(30e-3, 0.1), (64e-3, 0.01), (70e-3, 0.01), (5e-3, 4000.0)])
+def test_mixed_fixed_point_phase_ranges(ctx1, f0, fd_scale):
+    # the paired slow part takes the carrier phase in fixed point while
+    # |f0 K| < 31 cycles (K = -(AU/c) cos(beta) (cos lambda, sin lambda)) and
+    # in double-word floats beyond (f0 above ~62 mHz; 64 and 70 mHz put
+    # candidates on both sides in one launch); the last case chirps by
+    # thousands of cycles over T (fdot T^2/2 reduced modulo 2^20 in fixed
+    # point).  Likelihood and gradient against the oracle at the multiband bars.
+    wl = _fixed_point_problem(f0, fd_scale, int(f0 * 1e5) + int(fd_scale))
+    th = wl.theta
+    kpart = f0 * 149597870700.0 / 299792458.0 * np.cos(th[:, 2])
+    wide = (np.abs(kpart * np.cos(th[:, 3])) >= 31.0) | (np.abs(kpart * np.sin(th[:, 3])) >= 31.0)
+    if f0 >= 64e-3:
+        assert wide.any() and not wide.all()              # both forms in one launch
+    else:
+        assert not wide.any()
+    if fd_scale > 1.0:
+        assert float(np.max(0.5 * np.abs(th[:, 1]) * wl.T ** 2)) > 1000.0
+    dA, dE = _data.inject(wl)
+    g, o = _run_both(ctx1, wl.windows, dA, dE, wl.w_A, wl.w_E, th, wl.T, "mixed")
+    rel = (g[0] - o[0]).abs() / torch.clamp(o[2].abs(), min=1.0)
+    assert float(rel.max()) < 1e-5, float(rel.max())
+    assert float(o[2].max()) > 1.0                       # the injected source is seen
+    args = (_cuda(dA, torch.complex128), _cuda(dE, torch.complex128), _cuda(wl.w_A, torch.float64),
+            _cuda(wl.w_E, torch.float64), _cuda(th, torch.float64))
+    lg, gg = (x.cpu() for x in ctx1.loglik_grad(wl.windows, *args, prec="mixed"))
+    lo, go = ogb.loglik_grad(wl.windows, dA, dE, wl.w_A, wl.w_E, th, wl.T)
+    worst = 0.0
+    for b in range(th.shape[0]):
+        s = torch.tensor([1 / wl.T, 1 / wl.T ** 2, 1, 1, th[b, 4], 1, 1, 1], dtype=torch.float64)
+        gn, on = gg[b] * s, go[b] * s
+        worst = max(worst, float((gn - on).abs().max()) / float(on.abs().sum()))
+    assert worst <= 1e-4, worst
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_loglik_phase_is_dh_at_a_quarter_turn(ctx1, prec):
     # gb_loglik_phase: dh_im(theta) = <d|h> at phi0 + pi/2 (oracle), every N
