@@ -544,14 +544,15 @@ def run_fullband(args):
     clocks.start()
     st = fullband.run(ctx, n_src=args.fb_sources, rounds=args.fb_rounds, pop=args.fb_pop, generations=args.fb_gens,
                       phase=not args.fb_no_phase, posterior=args.fb_posterior, scheme=args.fb_scheme,
-                      noise=args.fb_noise, joint=not args.fb_no_joint)
+                      noise=args.fb_noise, joint=not args.fb_no_joint, amp=args.fb_amp,
+                      t_short=args.fb_short * wk.YEAR if args.fb_short > 0 else None)
     line = {"metric": "total wall time, s per posterior (full-band search)", "workload": "fullband",
             "n_gpus": 1, "unit": "s", "higher_is_better": False, "data": "synthetic",
             "value": st["wall_s"], "s_per_posterior": st["s_per_posterior"],
             "posterior": "Alg. 4: six temperatures (15..1) x 10,000 proposals per recovered source (%s)" % (
                 "uniform reduced box, then paired 2-D KDEs" if args.fb_posterior == "kde" else "Gaussian refits"),
-            "config": {"workload": "fullband: 0.3-15 mHz, T=2 yr, dt=15 s, %d binaries, Alg. 1 windows" %
-                       args.fb_sources}, "stats": st,
+            "config": {"workload": "fullband: 0.3-15 mHz, T=2 yr, dt=15 s, %d binaries (%s amplitudes), Alg. 1 "
+                                   "windows" % (args.fb_sources, args.fb_amp)}, "stats": st,
             # kernels launched from the host; the GA generations replayed from CUDA graphs are not counted
             "host_kernel_launches": ctx.launch_count(),
             "clocks": clocks.stop()}
@@ -584,6 +585,11 @@ def main():
                     help="fullband: Alg. 4 proposals, Gaussian refits or the paper's paired KDEs")
     ap.add_argument("--fb-no-joint", action="store_true",
                     help="fullband: no joint refit of a window's sources after each new one (Alg. 2)")
+    ap.add_argument("--fb-amp", default="galactic", choices=["galactic", "loguniform"],
+                    help="fullband: amplitudes N(>A) ~ A^-2 (about a tenth of the sources loud) or log-uniform")
+    ap.add_argument("--fb-short", type=float, default=0.5,
+                    help="fullband: years of a shorter observation searched first, whose signals start the "
+                         "searches of the full one (Sec. III.E); 0 for none")
     ap.add_argument("--fb-no-phase", action="store_true",
                     help="fullband: rank GA individuals by the plain SNR instead of the SNR maximised over phi0")
     args = ap.parse_args()

@@ -106,7 +106,16 @@ def newton_polish(lib_ctx, windows, dA, dE, wA, wE, theta, iters=6, prec="mixed"
         ok = np.all(np.isfinite(A), axis=(1, 2)) & np.all(np.isfinite(gs), axis=1)
         d = np.zeros((n, 8))
         if ok.any():
-            d[ok] = np.linalg.solve(A[ok], gs[ok][:, :, None])[:, :, 0]
+            try:
+                d[ok] = np.linalg.solve(A[ok], gs[ok][:, :, None])[:, :, 0]
+            except np.linalg.LinAlgError:
+                # an indefinite observed Fisher matrix made some system singular:
+                # solve one by one, no step where singular (lam then grows)
+                for i in np.nonzero(ok)[0]:
+                    try:
+                        d[i] = np.linalg.solve(A[i], gs[i])
+                    except np.linalg.LinAlgError:
+                        d[i] = 0.0
         d = np.where(np.isfinite(d), d, 0.0)
         step = torch.as_tensor(d * s, device=th.device)
         trial = th + step

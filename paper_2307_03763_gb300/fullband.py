@@ -10,11 +10,15 @@ library's kernels, batched over all windows at once:
   synthesis  templates of every injected source from ``gb_waveform`` (FP64),
              scattered into the contiguous band on top of the noise, then
              copied into the windows;
-  search     per round, one ``GASearch`` over all windows (gradient-polished
-             elites, generations replayed from a CUDA graph), then
-             Levenberg-Marquardt steps from each window's best individual
-             (adjoint gradient, observed Fisher matrix); the result counts as
-             recovered when its SNR (Eq. 6) passes the threshold;
+  search     per round, one ``GASearch`` over all windows, f0 over each
+             padded segment (gradient-polished elites, generations replayed
+             from a CUDA graph), then Levenberg-Marquardt steps from each
+             window's best individual (adjoint gradient, observed Fisher
+             matrix); the result counts as found when its SNR (Eq. 6) on the
+             window's residual passes the threshold, and as recovered when its
+             f0 also lies in the unpadded segment (Alg. 2's theta_in; a
+             signal in the padding belongs to the neighbour and is only
+             subtracted);
   posterior  for the round's recovered sources, Alg. 4: the six-temperature
              ladder (10,000 proposals per temperature) of
              ``AnnealedPosterior`` (default: Gaussian proposals from the
@@ -40,6 +44,7 @@ import time
 import numpy as np
 import torch
 
+from . import api
 from . import autograd as gbag
 from . import workloads as wk
 from .ga import GASearch
@@ -59,6 +64,9 @@ class FullBand:
     """sources: (n, 8) injected parameters; layout: ``workloads.fullband_layout``."""
 
     def __init__(self, ctx, sources, layout, T, seed=1, prec="mixed"):
+        if ctx.T_obs != float(T):
+            raise ValueError("the context's observation time (%g s) differs from T (%g s): its orbit tables and "
+                             "templates belong to T_obs" % (ctx.T_obs, T))
         self.ctx = ctx
         self.dev = ctx.device
         self.src = np.asarray(sources, dtype=np.float64)
@@ -140,10 +148,14 @@ class FullBand:
     # -- search ------------------------------------------------------------
 
     def boxes(self):
+        """Search boxes: Table 1's ranges with f0 over the padded segment, the
+        segment's bins [ka, kb) widened by a quarter of its width on each side
+        and kept inside the window."""
         b = np.empty((self.n_win, 16))
-        for w, (_, _, ka, kb) in enumerate(self.layout):
+        for w, (k0, N, ka, kb) in enumerate(self.layout):
             lo, hi = _LO.copy(), _HI.copy()
-            lo[0], hi[0] = ka / self.T, kb / self.T
+            pad = 0.25 * (kb - ka)
+            lo[0], hi[0] = max(ka - pad, k0) / self.T, min(kb + pad, k0 + N) / self.T
             hi[1] = float(wk.chirp_fdot(hi[0], 1.0))
             b[w] = np.concatenate([lo, hi])
         return b
@@ -258,15 +270,20 @@ class FullBand:
         return acc_all
 
     def _search_windows(self, active, n_rounds, tag, acc, boxes, pop, generations, snr_min, n_post, post_batch,
-                        phase, posterior, noise, joint=True):
+                        phase, posterior, noise, joint=True, polish_iters=6, seeds=None):
         """Search-and-subtract in the windows `active` (Alg. 2-3 per window):
-        each round a genetic search in every active window and the polish;
-        a window whose optimum passes the SNR threshold has its template
-        subtracted from its copy and, holding two or more sources, all of
-        them refitted jointly (_joint_refit); a window leaves the active set
-        when a round finds nothing in it.  Then each found source's
-        posterior (Alg. 4) on the window's data minus its other sources (the
-        paper's d_posterior), at the final estimates.
+        each round a genetic search over the padded segment in every active
+        window and the polish; an optimum whose SNR on the window's residual
+        (the data it was fitted to) passes the threshold has its template
+        subtracted from the window's copy.  It is
+        a source of the segment (theta_in) when its f0 lies in the unpadded
+        segment, else a neighbour's signal spilling into the padding
+        (theta_out), which stays subtracted but is not returned.  A window
+        holding two or more sources of its own refits them jointly
+        (_joint_refit) with theta_out held fixed; a window leaves the active
+        set when a round finds nothing in it.  Then each source of the
+        segment gets its posterior (Alg. 4) on the window's data minus every
+        other found signal (the paper's d_posterior), at the final estimates.
         Returns [(window, theta, snr, accepted moves of its posterior)]."""
         active = np.asarray(active, dtype=int)
         srcs = {}
@@ -278,14 +295,21 @@ class FullBand:
             wins = self._wins(active, [pop] * active.size)
             if noise == "median":   # the segment noise, updated after every subtraction
                 self.ctx.noise_median(self._wins(active), self.dA, self.dE, debias=True, weights=(self.wA, self.wE))
+            init = None
+            if seeds is not None and len(seeds):
+                # starting points from a shorter observation's search (Sec. III.E):
+                # its signals whose f0 lies in the window's padded segment
+                f = seeds[:, 0]
+                init = [seeds[(f >= boxes[w, 0]) & (f < boxes[w, 8])] for w in active]
             ga = GASearch(self.ctx, wins, self.dA, self.dE, self.wA, self.wE, boxes[active], pop,
-                          seed=self.seed + 17 * (r + 100 * tag), prec=self.prec, phase=phase)
+                          seed=self.seed + 17 * (r + 100 * tag), prec=self.prec, phase=phase, init=init)
             best = ga.run(generations, graph=True)
             del ga
             # gradient polish of every window's best
             allw = self._wins(active)
             th_b, _ = gbag.newton_polish(self.ctx, allw, self.dA, self.dE, self.wA, self.wE,
-                                         torch.as_tensor(best, device=self.dev).contiguous(), prec=self.prec)
+                                         torch.as_tensor(best, device=self.dev).contiguous(), iters=polish_iters,
+                                         prec=self.prec)
             _, dh, hh = self.ctx.loglik(self._wins(active, [1] * active.size), self.dA, self.dE, self.wA, self.wE,
                                         th_b.contiguous(), prec=self.prec)
             best = th_b.cpu().numpy()
@@ -298,10 +322,14 @@ class FullBand:
                 ws = active[hit]
                 self._subtract_windows(list(ws), best[hit])
                 for w, i in zip(ws, hit):
-                    srcs.setdefault(int(w), []).append(best[i].copy())
+                    _, _, ka, kb = self.layout[int(w)]
+                    if ka <= best[i][0] * self.T < kb:
+                        srcs.setdefault(int(w), []).append(best[i].copy())
+                    else:
+                        acc["out"] += 1
                 t2 = _sync(self.dev)
                 acc["sub"] += t2 - t1
-                multi = [int(w) for w in ws if len(srcs[int(w)]) > 1]
+                multi = [int(w) for w in ws if len(srcs.get(int(w), [])) > 1]
                 if joint and multi:
                     self._joint_refit(multi, srcs)
                     acc["joint_s"] += _sync(self.dev) - t2
@@ -328,7 +356,7 @@ class FullBand:
                                         torch.as_tensor(th, device=self.dev).contiguous(), prec=self.prec)
             snr_k = (dh / torch.sqrt(torch.clamp(hh, min=1e-300))).cpu().numpy()
             pa = self._posteriors(np.array(wk_), th, boxes, n_post, post_batch, posterior,
-                                  self.seed + 1000 * (k + 100 * tag))
+                                  self.seed + 1000 * (k + 100 * tag)) if n_post > 0 else [0] * len(wk_)
             acc["n_post"] += len(pa)
             self._add_windows(wk_, th, -1.0)
             found.extend((w, th[i].copy(), float(snr_k[i]), a) for i, (w, a) in enumerate(zip(wk_, pa)))
@@ -336,7 +364,7 @@ class FullBand:
         return found
 
     def search(self, rounds=3, pop=1024, generations=100, snr_min=10.0, n_post=10000, post_batch=4096, phase=True,
-               posterior="gauss", scheme="all", noise="true", joint=True):
+               posterior="gauss", scheme="all", noise="true", joint=True, polish_iters=6, seeds=None):
         """Search every window for up to `rounds` signals.
 
         scheme="all": all windows at once on their own copies of the data.
@@ -361,9 +389,10 @@ class FullBand:
         self.stats["autotune"] = self.ctx.autotune(wins, self.dA, self.dE, self.wA, self.wE, th0, prec=self.prec,
                                                    reps=2)
         acc = {"ga": 0.0, "post_s": 0.0, "sub": 0.0, "joint_s": 0.0, "evals": 0, "n_post": 0, "joint_snr": [],
-               "multi_windows": 0}
+               "multi_windows": 0, "out": 0}
         kw = dict(boxes=boxes, pop=pop, generations=generations, snr_min=snr_min, n_post=n_post,
-                  post_batch=post_batch, phase=phase, posterior=posterior, noise=noise, joint=joint)
+                  post_batch=post_batch, phase=phase, posterior=posterior, noise=noise, joint=joint,
+                  polish_iters=polish_iters, seeds=None if seeds is None else np.asarray(seeds, dtype=np.float64))
         if scheme == "all":
             found = self._search_windows(np.arange(self.n_win), rounds, 0, acc, **kw)
         elif scheme == "evenodd":
@@ -395,6 +424,7 @@ class FullBand:
         post = [a for _, _, _, a in found]   # the catalogue's posteriors
         t_ga, evals = acc["ga"], acc["evals"]
         self.stats.update({"joint_refit_s": acc["joint_s"], "windows_with_several_sources": acc["multi_windows"],
+                           "padding_signals_subtracted": acc["out"],
                            "joint_snr_median": float(np.median(acc["joint_snr"])) if acc["joint_snr"] else None})
         self.stats.update({"ga_s": t_ga, "posterior_s": acc["post_s"], "subtract_s": acc["sub"], "ga_evals": evals,
                            "ga_evals_per_s": evals / t_ga if t_ga > 0 else None, "recovered": len(found),
@@ -471,7 +501,14 @@ class FullBand:
                     best_d[r], best_j[r] = dl[i], inj[r, k]
                 best_o[r] = max(best_o[r], ov[i])
         good = best_d < 0.3
+        by_band = {}
+        for lo, hi in ((0.0, 2e-3), (2e-3, 5e-3), (5e-3, 10e-3), (10e-3, None)):
+            m = (rec[:, 0] >= lo) & ((rec[:, 0] < hi) if hi is not None else True)
+            if m.any():
+                by_band["%g-%s mHz" % (lo * 1e3, "%g" % (hi * 1e3) if hi is not None else "")] = {
+                    "recovered": int(m.sum()), "delta_lt_0.3": float(np.mean(good[m]))}
         out.update({"delta_lt_0.3": float(np.mean(good)), "overlap_gt_0.9": float(np.mean(best_o > 0.9)),
+                    "delta_lt_0.3_by_band": by_band,
                     "median_delta": float(np.median(best_d)),
                     "matched_injected_delta_lt_0.3": int(np.unique(best_j[good]).size),
                     "matched_over_loud": float(np.unique(best_j[good]).size / max(1, loud)),
@@ -482,10 +519,14 @@ class FullBand:
 
 def run(ctx, n_src=200000, f_lo=0.3e-3, f_hi=15e-3, T=2 * wk.YEAR, rounds=3, pop=1024, generations=100,
         snr_min=10.0, n_post=10000, seed=wk.SEED_BASE + 5, warm=True, phase=True, posterior="gauss", scheme="all",
-        noise="true", joint=True):
+        noise="true", joint=True, amp="galactic", polish_iters=6, t_short=None):
     """Config 5 end to end; returns the statistics (wall times in seconds).
     warm: run a small instance first, so that one-time library initialisation
-    (kernel modules, solver handles) is not in the times."""
+    (kernel modules, solver handles) is not in the times.  amp: the
+    population's amplitude law (workloads.fullband_sources).  t_short: if
+    given, the same sources observed for t_short seconds are searched first
+    (own context, own noise, no posteriors) and their signals start the
+    searches of the full observation in their windows (Sec. III.E)."""
     if warm:
         small = FullBand(ctx, wk.fullband_sources(200, 2e-3, 2.1e-3, seed + 1), wk.fullband_layout(2e-3, 2.1e-3, T),
                          T, seed=seed + 1).synthesize()
@@ -493,12 +534,27 @@ def run(ctx, n_src=200000, f_lo=0.3e-3, f_hi=15e-3, T=2 * wk.YEAR, rounds=3, pop
         small.search(rounds=1, pop=64, generations=4, snr_min=snr_min, n_post=256, posterior=posterior,
                      scheme=scheme, noise=noise, joint=joint)
     t0 = _sync(ctx.device)
-    fb = FullBand(ctx, wk.fullband_sources(n_src, f_lo, f_hi, seed), wk.fullband_layout(f_lo, f_hi, T), T,
-                  seed=seed).synthesize()
+    sources = wk.fullband_sources(n_src, f_lo, f_hi, seed, amp=amp)
+    seeds, short = None, {}
+    if t_short:
+        # Sec. III.E: search the same sources observed for t_short first (its
+        # own noise, no posteriors); its signals start the searches of the
+        # full observation in their windows
+        ctx_s = api.Context(t_short, arm_L=ctx.arm_L, device=ctx.device.index)
+        fs = FullBand(ctx_s, sources, wk.fullband_layout(f_lo, f_hi, t_short), t_short, seed=seed + 7).synthesize()
+        fs.search(rounds=rounds, pop=pop, generations=generations, snr_min=snr_min, n_post=0, phase=phase,
+                  scheme=scheme, noise=noise, joint=joint, polish_iters=polish_iters)
+        seeds = np.array([th for _, _, th, _ in fs.found]) if fs.found else np.zeros((0, 8))
+        short = {"t_short_yr": t_short / wk.YEAR, "short_recovered": len(fs.found),
+                 "short_wall_s": _sync(ctx.device) - t0}
+        del fs
+        ctx_s.close()
+    fb = FullBand(ctx, sources, wk.fullband_layout(f_lo, f_hi, T), T, seed=seed).synthesize()
     snr_inj, owner = fb.injected_snr()
     fb.search(rounds=rounds, pop=pop, generations=generations, snr_min=snr_min, n_post=n_post, phase=phase,
-              posterior=posterior, scheme=scheme, noise=noise, joint=joint)
+              posterior=posterior, scheme=scheme, noise=noise, joint=joint, polish_iters=polish_iters, seeds=seeds)
     st = dict(fb.stats)
+    st.update(short)
     # with median-noise weights the recovered SNRs are measured against the
     # segments' estimated PSD: compare them with the injections' SNRs under
     # the same weights (the instrument-PSD SNRs still count the loud ones)

@@ -23,13 +23,15 @@ class GASearch:
     windows: (k0, W, N, data_off, _, _) per window; data tensors as for
     ``Context.loglik``; boxes: (n_win, 16) prior boxes (lo[8], hi[8]);
     pop: individuals per window.  The initial population is drawn uniformly
-    in each box from ``seed`` (an input of the search).  phase=True ranks
+    in each box from ``seed`` (an input of the search); init (optional, one
+    (k, 8) array per window, k <= pop) replaces the first k draws of a window
+    by given starting points (kept inside its box).  phase=True ranks
     individuals by their SNR maximised over phi0 (the template carries phi0
     as a common factor exp(i phi0)) and rotates the best one to that phase.
     """
 
     def __init__(self, ctx, windows, dA, dE, wA, wE, boxes, pop, seed=1, prec="mixed", params=None, polish=True,
-                 phase=True):
+                 phase=True, init=None):
         self.ctx = ctx
         self.nw = len(windows)
         self.pop = int(pop)
@@ -46,6 +48,11 @@ class GASearch:
         lo, hi = boxes[:, :8], boxes[:, 8:]
         rng = np.random.default_rng(self.seed)
         th0 = lo[:, None, :] + (hi - lo)[:, None, :] * rng.uniform(size=(self.nw, self.pop, 8))
+        if init is not None:
+            for w, s in enumerate(init):
+                s = np.asarray(s, dtype=np.float64).reshape(-1, 8)[:self.pop]
+                if s.shape[0]:
+                    th0[w, :s.shape[0]] = np.clip(s, lo[w], hi[w])
         n = self.nw * self.pop
         self.th = [torch.as_tensor(th0.reshape(n, 8), device=dev).contiguous(),
                    torch.empty((n, 8), dtype=torch.float64, device=dev)]
