@@ -585,8 +585,9 @@ def main():
                     help="fullband: Alg. 4 proposals, Gaussian refits or the paper's paired KDEs")
     ap.add_argument("--fb-no-joint", action="store_true",
                     help="fullband: no joint refit of a window's sources after each new one (Alg. 2)")
-    ap.add_argument("--fb-amp", default="galactic", choices=["galactic", "loguniform"],
-                    help="fullband: amplitudes N(>A) ~ A^-2 (about a tenth of the sources loud) or log-uniform")
+    ap.add_argument("--fb-amp", default="loguniform", choices=["loguniform", "galactic"],
+                    help="fullband: amplitudes log-uniform on [1e-23, 1e-21] (the workload's) or N(>A) ~ A^-2 "
+                         "(about a tenth of the sources loud)")
     ap.add_argument("--fb-short", type=float, default=0.5,
                     help="fullband: years of a shorter observation searched first, whose signals start the "
                          "searches of the full one (Sec. III.E); 0 for none")

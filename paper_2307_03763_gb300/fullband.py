@@ -519,7 +519,7 @@ class FullBand:
 
 def run(ctx, n_src=200000, f_lo=0.3e-3, f_hi=15e-3, T=2 * wk.YEAR, rounds=3, pop=1024, generations=100,
         snr_min=10.0, n_post=10000, seed=wk.SEED_BASE + 5, warm=True, phase=True, posterior="gauss", scheme="all",
-        noise="true", joint=True, amp="galactic", polish_iters=6, t_short=None):
+        noise="true", joint=True, amp="loguniform", polish_iters=6, t_short=None):
     """Config 5 end to end; returns the statistics (wall times in seconds).
     warm: run a small instance first, so that one-time library initialisation
     (kernel modules, solver handles) is not in the times.  amp: the

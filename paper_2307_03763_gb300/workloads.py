@@ -204,15 +204,15 @@ def log_uniforms(n, rng):
 # the five workloads
 # ----------------------------------------------------------------------------
 
-def fullband_sources(n_src=200000, f_lo=0.3e-3, f_hi=15e-3, seed=SEED_BASE + 5, amp="galactic"):
+def fullband_sources(n_src=200000, f_lo=0.3e-3, f_hi=15e-3, seed=SEED_BASE + 5, amp="loguniform"):
     """The full-band population: f0 log-uniform in [f_lo, f_hi], fdot from
     Eq. 8 with Mc ~ U[0.2, 1] M_sun, angles on the Table 1 ranges; (n_src, 8),
-    sorted by f0.  Amplitudes: "galactic", a power law N(>A) ~ A^-2 on
-    [4e-24, 1e-21] (a disk population: most sources faint; at T = 2 yr with
-    the instrument PSD 19,493 of the 200,000 lie above SNR 10, one per ~47
-    bins, against 18,332 above SNR 10 in the 2-yr data set of Table 4);
-    "loguniform", log-uniform on [1e-23, 1e-21] (134,550 above SNR 10, one
-    per ~7 bins)."""
+    sorted by f0.  Amplitudes: "loguniform" (the full-band workload's),
+    log-uniform on [1e-23, 1e-21] (at T = 2 yr with the instrument PSD
+    134,550 of the 200,000 lie above SNR 10, one per ~7 bins); "galactic",
+    a power law N(>A) ~ A^-2 on [4e-24, 1e-21] (a disk population: most
+    sources faint, 19,493 above SNR 10, one per ~47 bins, against 18,332
+    above SNR 10 in the 2-yr data set of Table 4)."""
     rng = np.random.default_rng(seed)
     f0 = np.sort(np.exp(rng.uniform(np.log(f_lo), np.log(f_hi), n_src)))
     fdot = chirp_fdot(f0, rng.uniform(0.2, 1.0, n_src))
