@@ -545,7 +545,7 @@ def run_fullband(args):
     st = fullband.run(ctx, n_src=args.fb_sources, rounds=args.fb_rounds, pop=args.fb_pop, generations=args.fb_gens,
                       phase=not args.fb_no_phase, posterior=args.fb_posterior, scheme=args.fb_scheme,
                       noise=args.fb_noise, joint=not args.fb_no_joint, amp=args.fb_amp,
-                      t_short=args.fb_short * wk.YEAR if args.fb_short > 0 else None)
+                      t_short=[float(x) * wk.YEAR for x in args.fb_short.split(",") if float(x) > 0] or None)
     line = {"metric": "total wall time, s per posterior (full-band search)", "workload": "fullband",
             "n_gpus": 1, "unit": "s", "higher_is_better": False, "data": "synthetic",
             "value": st["wall_s"], "s_per_posterior": st["s_per_posterior"],
@@ -588,9 +588,9 @@ def main():
     ap.add_argument("--fb-amp", default="loguniform", choices=["loguniform", "galactic"],
                     help="fullband: amplitudes log-uniform on [1e-23, 1e-21] (the workload's) or N(>A) ~ A^-2 "
                          "(about a tenth of the sources loud)")
-    ap.add_argument("--fb-short", type=float, default=0.5,
-                    help="fullband: years of a shorter observation searched first, whose signals start the "
-                         "searches of the full one (Sec. III.E); 0 for none")
+    ap.add_argument("--fb-short", default="0.5,1",
+                    help="fullband: years of shorter observations searched first, comma-separated, each seeding "
+                         "the next and the last the full one (Sec. III.E); 0 for none")
     ap.add_argument("--fb-no-phase", action="store_true",
                     help="fullband: rank GA individuals by the plain SNR instead of the SNR maximised over phi0")
     args = ap.parse_args()

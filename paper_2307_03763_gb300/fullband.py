@@ -526,7 +526,9 @@ def run(ctx, n_src=200000, f_lo=0.3e-3, f_hi=15e-3, T=2 * wk.YEAR, rounds=3, pop
     population's amplitude law (workloads.fullband_sources).  t_short: if
     given, the same sources observed for t_short seconds are searched first
     (own context, own noise, no posteriors) and their signals start the
-    searches of the full observation in their windows (Sec. III.E)."""
+    searches of the full observation in their windows (Sec. III.E); a
+    sequence of durations is a ladder, each stage seeded by the one before
+    (the paper's 0.5, 1 and 2 yr)."""
     if warm:
         small = FullBand(ctx, wk.fullband_sources(200, 2e-3, 2.1e-3, seed + 1), wk.fullband_layout(2e-3, 2.1e-3, T),
                          T, seed=seed + 1).synthesize()
@@ -536,19 +538,22 @@ def run(ctx, n_src=200000, f_lo=0.3e-3, f_hi=15e-3, T=2 * wk.YEAR, rounds=3, pop
     t0 = _sync(ctx.device)
     sources = wk.fullband_sources(n_src, f_lo, f_hi, seed, amp=amp)
     seeds, short = None, {}
-    if t_short:
-        # Sec. III.E: search the same sources observed for t_short first (its
-        # own noise, no posteriors); its signals start the searches of the
-        # full observation in their windows
-        ctx_s = api.Context(t_short, arm_L=ctx.arm_L, device=ctx.device.index)
-        fs = FullBand(ctx_s, sources, wk.fullband_layout(f_lo, f_hi, t_short), t_short, seed=seed + 7).synthesize()
+    ladder = sorted(float(x) for x in (np.atleast_1d(t_short) if t_short else []))
+    for k, ts in enumerate(ladder):
+        # Sec. III.E: search the same sources observed for ts first (its own
+        # context, noise and windows, no posteriors); its signals start the
+        # searches of the next, longer observation in their windows
+        ctx_s = api.Context(ts, arm_L=ctx.arm_L, device=ctx.device.index)
+        fs = FullBand(ctx_s, sources, wk.fullband_layout(f_lo, f_hi, ts), ts, seed=seed + 7 + k).synthesize()
         fs.search(rounds=rounds, pop=pop, generations=generations, snr_min=snr_min, n_post=0, phase=phase,
-                  scheme=scheme, noise=noise, joint=joint, polish_iters=polish_iters)
+                  scheme=scheme, noise=noise, joint=joint, polish_iters=polish_iters, seeds=seeds)
         seeds = np.array([th for _, _, th, _ in fs.found]) if fs.found else np.zeros((0, 8))
-        short = {"t_short_yr": t_short / wk.YEAR, "short_recovered": len(fs.found),
-                 "short_wall_s": _sync(ctx.device) - t0}
+        short.setdefault("t_short_yr", []).append(ts / wk.YEAR)
+        short.setdefault("short_recovered", []).append(len(fs.found))
         del fs
         ctx_s.close()
+    if ladder:
+        short["short_wall_s"] = _sync(ctx.device) - t0
     fb = FullBand(ctx, sources, wk.fullband_layout(f_lo, f_hi, T), T, seed=seed).synthesize()
     snr_inj, owner = fb.injected_snr()
     fb.search(rounds=rounds, pop=pop, generations=generations, snr_min=snr_min, n_post=n_post, phase=phase,
