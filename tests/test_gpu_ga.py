@@ -68,6 +68,29 @@ def test_ga_recovers_an_injected_source(api):
     assert rho > 0.8 * 60.0
 
 
+def test_ga_seeded_population_starts_from_its_seeds(api):
+    # GASearch(init=...): the given starting points replace the first draws of
+    # the window's population (clipped into the box); seeded with the source
+    # (and a point outside the box), two generations already hold the source
+    # (the best individual is kept in slot 0), while the unseeded search has
+    # not found it yet
+    from paper_2307_03763_gb300.ga import GASearch
+    wl, src, dA, dE, box = _single_source_problem()
+    ctx = api.Context(wl.T)
+    args = (_cuda(dA, torch.complex128), _cuda(dE, torch.complex128), _cuda(wl.w_A, torch.float64),
+            _cuda(wl.w_E, torch.float64))
+    far = src.copy()
+    far[0] += 100.0 / wl.T                        # outside the f0 box: clipped to its edge
+    ga = GASearch(ctx, wl.windows, *args, box, pop=256, seed=11, init=[np.stack([src, far])])
+    th0 = ga.th[0].cpu().numpy()
+    assert np.array_equal(th0[0], np.clip(src, box[0, :8], box[0, 8:]))
+    assert th0[1, 0] == box[0, 8] and np.array_equal(th0[1, 1:], np.clip(far[1:], box[0, 1:8], box[0, 9:]))
+    best = ga.run(2, graph=False)[0]
+    assert _overlap(wl, best, src) > 0.99
+    cold = GASearch(ctx, wl.windows, *args, box, pop=256, seed=11).run(2, graph=False)[0]
+    assert _overlap(wl, cold, src) < 0.9
+
+
 def test_ga_step_phase_maximised_best(api):
     # gb_ga_step with dh_im on made-up inner products: window 0 (phi0 box of
     # 2 pi) ranks by sqrt(dh^2 + dh_im^2)/sqrt(hh) and rotates the best to
