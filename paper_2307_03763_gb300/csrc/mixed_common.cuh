@@ -5,23 +5,27 @@
 // anonymous namespace, so each translation unit instantiates what it uses.
 //
 // The mixed-precision path: the carrier phase and the bin offset keep
-// double-precision accuracy (double-word float arithmetic), while the detector
-// response, the FFT and the window inner products run in float with
-// compensated sums.  Inputs, the per-window <d|d> and every output are double.
+// double-precision accuracy, while the detector response, the FFT and the
+// window inner products run in float with compensated sums.  Inputs, the
+// per-window <d|d> and every output are double.
 //
-// Why double-word instead of native double: on GB300 the FP64 pipe issues at
-// 1/64 of the FP32 rate, so a native-double phase (about ten operations per
-// sample) would cost more than the whole float response.  A double-word
-// product with an exact FMA error term costs two or three float operations.
+// Why not native double for the phase: on GB300 the FP64 pipe issues at 1/64
+// of the FP32 rate, so a native-double phase (about ten operations per
+// sample) would cost more than the whole float response.  The paired slow
+// part takes the phase in fixed point (64-bit integer fractions of a cycle,
+// whose sums wrap modulo one exactly: PhaseRec, phase_fix); the scalar slow
+// part and candidates outside the fixed-point ranges take it in double-word
+// float arithmetic (a product with an exact FMA error term costs two or three
+// float operations).
 //
 // Phase of the receiver-j link, in cycles, at u = t/T = n/N (reading R5):
 //   P_j = phi0/2pi + delta u + (fdot T^2/2) u^2 - f0 K(n) - fdot T u K(n)
 //         - f rho_j(n) + (fdot/2) (K + rho_j)^2,
 //   K(n) = k.x_centre/c = Kc cos(alpha_n) + Ks sin(alpha_n),
 //   rho_j = k.(x_j - x_centre)/c,  f = f0 + fdot T u.
-// The first four terms can reach hundreds of cycles and are formed in
-// double-word arithmetic, each product reduced modulo one exactly; the rest
-// are below 0.1 cycle and are float.  exp(2 pi i P_j) is the common factor
+// The first four terms can reach hundreds of cycles and are formed modulo one
+// exactly (fixed point, or double-word arithmetic with each product reduced
+// modulo one); the rest are below 0.1 cycle and are float.  exp(2 pi i P_j) is the common factor
 // exp(2 pi i P_c) (one accurate sincospi, applied once per sample to A and E)
 // times exp(2 pi i dP_j) for the small per-spacecraft remainder.
 //
