@@ -538,7 +538,7 @@ def run(ctx, n_src=200000, f_lo=0.3e-3, f_hi=15e-3, T=2 * wk.YEAR, rounds=3, pop
     t0 = _sync(ctx.device)
     sources = wk.fullband_sources(n_src, f_lo, f_hi, seed, amp=amp)
     seeds, short = None, {}
-    ladder = sorted(float(x) for x in (np.atleast_1d(t_short) if t_short else []))
+    ladder = [] if t_short is None else sorted(float(x) for x in np.atleast_1d(t_short) if float(x) > 0)
     for k, ts in enumerate(ladder):
         # Sec. III.E: search the same sources observed for ts first (its own
         # context, noise and windows, no posteriors); its signals start the
