@@ -251,6 +251,45 @@ int get_plan(gb_ctx* ctx, int prec, const gb_window_t* win, int32_t n_win, int t
     }
     std::vector<Tile> sorted(tiles.size());
     for (size_t i = 0; i < order.size(); ++i) sorted[i] = tiles[order[i]];
+    if (prec == GB_MIXED && tile_cands >= 4) {
+        // The persistent warps take the items in this order, so the last ones
+        // set the tail.  With R warps resident (16 per SM for N <= 256, 8 for
+        // N >= 512), the last R/2 items of each range are split into halves
+        // and the last R/4 of those halves into halves again: the last round
+        // is shared out in smaller items, while the extra per-item set-ups
+        // stay few (a list-scheduling model of the queue with the measured
+        // set-up cost puts this near the best split; splitting the last 2R
+        // items costs more in set-ups than it saves).
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || sms <= 0)
+            sms = 152;
+        auto split_last = [](std::vector<Tile>& v, size_t k) {
+            k = std::min(k, v.size());
+            std::vector<Tile> out(v.begin(), v.end() - k);
+            for (size_t i = v.size() - k; i < v.size(); ++i) {
+                const Tile t = v[i];
+                const int64_t len = t.c_end - t.c_begin;
+                if (len >= 2) {
+                    Tile a = t, b = t;
+                    a.c_end = b.c_begin = t.c_begin + len / 2;
+                    out.push_back(a);
+                    out.push_back(b);
+                } else {
+                    out.push_back(t);
+                }
+            }
+            v.swap(out);
+        };
+        std::vector<Tile> large(sorted.begin(), sorted.begin() + n_large), small(sorted.begin() + n_large, sorted.end());
+        const size_t r_large = (size_t)sms * 8, r_small = (size_t)sms * 16;
+        split_last(large, r_large / 2);
+        split_last(large, r_large / 4);
+        split_last(small, r_small / 2);
+        split_last(small, r_small / 4);
+        n_large = (int)large.size();
+        sorted = large;
+        sorted.insert(sorted.end(), small.begin(), small.end());
+    }
 
     Plan p;
     p.key = key;
