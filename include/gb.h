@@ -118,6 +118,17 @@ const char* gb_last_error(const gb_ctx_t* ctx);
  * 0 <= seconds <= 1e9. */
 int gb_ctx_set_time_budget(gb_ctx_t* ctx, double seconds);
 
+/* Events around the next mixed-precision likelihood launch (instrumentation
+ * for benchmarks; the paper has no counterpart).  `start` and `end` are
+ * cudaEvent_t handles the caller created and owns (with timing enabled, for
+ * cudaEventElapsedTime).  The next call on this context that launches the
+ * mixed-precision likelihood kernels (gb_loglik, gb_loglik_aet,
+ * gb_loglik_phase, gb_loglik_phase_aet with GB_MIXED, or gb_mh_certified)
+ * records `start` on its stream after the window preparation, just before
+ * those kernels, and `end` just after them; the context then forgets both.
+ * NULL for both clears them.  GB_EINVAL if exactly one is NULL. */
+int gb_ctx_set_kernel_events(gb_ctx_t* ctx, void* start, void* end);
+
 /* Number of kernels the context's calls have launched so far, counted on
  * the host at each launch (the paper has no counterpart: instrumentation for
  * benchmarks).  0 for a NULL context.  Not thread safe across concurrent

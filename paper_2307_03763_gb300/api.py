@@ -61,6 +61,7 @@ _SIGNATURES = {
     "gb_ctx_check": (ctypes.c_int, [_P]),
     "gb_launch_count": (ctypes.c_uint64, [_P]),
     "gb_ctx_set_time_budget": (ctypes.c_int, [_P, ctypes.c_double]),
+    "gb_ctx_set_kernel_events": (ctypes.c_int, [_P, _P, _P]),
     "gb_waveform": (ctypes.c_int, [_P, ctypes.c_int, _P, _I64, _I32, _P, _P, _P, _P]),
     "gb_loglik": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Window), _I32, _P, _P, _P, _P, _I64, _P, _I64,
                                  _P, _P, _P, _P]),
@@ -182,6 +183,17 @@ class Context:
     def set_time_budget(self, seconds):
         """Work budget of the persistent mixed-precision kernels (0: none)."""
         self._check(lib().gb_ctx_set_time_budget(self._h, float(seconds)))
+
+    def set_kernel_events(self, start, end):
+        """Record two torch.cuda.Event objects (timing enabled, recorded at
+        least once so that they exist) around the next mixed-precision
+        likelihood kernels; None for both clears them."""
+        if (start is None) != (end is None):
+            raise ValueError("give both events or neither")
+        h = [None if e is None else ctypes.c_void_p(e.cuda_event) for e in (start, end)]
+        if start is not None and not (h[0].value and h[1].value):
+            raise ValueError("record each event once before passing it")
+        self._check(lib().gb_ctx_set_kernel_events(self._h, h[0], h[1]))
 
     def launch_count(self):
         """Kernels launched by this context's calls so far."""

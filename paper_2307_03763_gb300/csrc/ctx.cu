@@ -251,10 +251,11 @@ int get_plan(gb_ctx* ctx, int prec, const gb_window_t* win, int32_t n_win, int t
     }
     std::vector<Tile> sorted(tiles.size());
     for (size_t i = 0; i < order.size(); ++i) sorted[i] = tiles[order[i]];
-    if (prec == GB_MIXED && tile_cands >= 4) {
+    if ((prec == GB_MIXED || prec == GB_MIXED + 16) && tile_cands >= 4) {
         // The persistent warps take the items in this order, so the last ones
-        // set the tail.  With R warps resident (16 per SM for N <= 256, 8 for
-        // N >= 512), the last R/2 items of each range are split into halves
+        // set the tail.  With R warps resident (likelihood: 16 per SM for
+        // N <= 256, 8 for N >= 512; gradient: 8 and 4), the last R/2 items of
+        // each range are split into halves
         // and the last R/4 of those halves into halves again: the last round
         // is shared out in smaller items, while the extra per-item set-ups
         // stay few (a list-scheduling model of the queue with the measured
@@ -281,7 +282,8 @@ int get_plan(gb_ctx* ctx, int prec, const gb_window_t* win, int32_t n_win, int t
             v.swap(out);
         };
         std::vector<Tile> large(sorted.begin(), sorted.begin() + n_large), small(sorted.begin() + n_large, sorted.end());
-        const size_t r_large = (size_t)sms * 8, r_small = (size_t)sms * 16;
+        const size_t per_sm = prec == GB_MIXED ? 16 : 8;
+        const size_t r_large = (size_t)sms * per_sm / 2, r_small = (size_t)sms * per_sm;
         split_last(large, r_large / 2);
         split_last(large, r_large / 4);
         split_last(small, r_small / 2);
@@ -443,6 +445,15 @@ int gb_ctx_set_time_budget(gb_ctx_t* ctx, double seconds) {
         return set_error(ctx, GB_EINVAL, "gb_ctx_set_time_budget: seconds must be in [0, 1e9]");
     ctx->budget_ns = (unsigned long long)(seconds * 1.0e9);
     if (seconds > 0.0 && ctx->budget_ns == 0ULL) ctx->budget_ns = 1ULL;
+    return GB_OK;
+}
+
+int gb_ctx_set_kernel_events(gb_ctx_t* ctx, void* start, void* end) {
+    if (!ctx) return GB_EINVAL;
+    if ((start == nullptr) != (end == nullptr))
+        return set_error(ctx, GB_EINVAL, "gb_ctx_set_kernel_events: give both events or neither");
+    ctx->kev_start = (cudaEvent_t)start;
+    ctx->kev_end = (cudaEvent_t)end;
     return GB_OK;
 }
 

@@ -155,6 +155,8 @@ struct gb_ctx {
     uint64_t launches = 0;
     // work budget of the persistent kernels, nanoseconds per warp (0: none)
     unsigned long long budget_ns = 0;
+    // events recorded around the next mixed likelihood launch, then cleared
+    cudaEvent_t kev_start = nullptr, kev_end = nullptr;
 };
 
 namespace gb {

@@ -90,6 +90,13 @@ int launch_loglik_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const d
     if (e != cudaSuccess) return cuda_error(ctx, e, "prep_mixed launch");
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    // the caller's events, if set, bracket the likelihood kernels (once)
+    const cudaEvent_t ev_start = ctx->kev_start, ev_end = ctx->kev_end;
+    ctx->kev_start = ctx->kev_end = nullptr;
+    if (ev_start) {
+        e = cudaEventRecord(ev_start, s);
+        if (e != cudaSuccess) return cuda_error(ctx, e, "loglik_mixed: kernel start event");
+    }
     // two persistent launches drain the two queues: N >= 512 items, then N <= 256
     const int n_small = plan.n_tiles - plan.n_large;
     for (int part = 0; part < 2; ++part) {
@@ -116,6 +123,10 @@ int launch_loglik_mixed(gb_ctx* ctx, const Plan& plan, const double* dA, const d
         ++ctx->launches;
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_error(ctx, e, "loglik_mixed launch");
+    }
+    if (ev_end) {
+        e = cudaEventRecord(ev_end, s);
+        if (e != cudaSuccess) return cuda_error(ctx, e, "loglik_mixed: kernel end event");
     }
     return GB_OK;
 }

@@ -684,3 +684,38 @@ def test_time_budget_stops_persistent_kernels(api):
         assert not bool(torch.isnan(logL).any())
     with pytest.raises(api.GBError):
         ctx.set_time_budget(-1.0)
+
+
+def test_kernel_events_bracket_the_likelihood_kernels(api):
+    # the events set on the context are recorded once, around the likelihood
+    # kernels of the next mixed call only: inside the call's own interval,
+    # not touched by a later call; one event without the other is refused
+    wl = wk.tiny_window(n_cand=20000)
+    ctx = api.Context(wl.T)
+    data = (_cuda(wl.noise_A, torch.complex128), _cuda(wl.noise_E, torch.complex128), _cuda(wl.w_A, torch.float64),
+            _cuda(wl.w_E, torch.float64))
+    th = _cuda(wl.theta, torch.float64)
+    logL = torch.empty(wl.n_cand, dtype=torch.float64, device=DEV)
+    call = lambda: ctx.loglik(wl.windows, *data, th, prec="mixed", out=(logL, None, None))
+    call()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for e in ev:
+        e.record()
+    with pytest.raises(ValueError):
+        ctx.set_kernel_events(ev[1], None)
+    with pytest.raises(ValueError):
+        ctx.set_kernel_events(torch.cuda.Event(enable_timing=True), ev[2])   # never recorded
+    ctx.set_kernel_events(ev[1], ev[2])
+    ev[0].record()
+    call()
+    ev[3].record()
+    torch.cuda.synchronize()
+    outer, inner = ev[0].elapsed_time(ev[3]), ev[1].elapsed_time(ev[2])
+    assert 0.0 < inner <= outer
+    assert ev[0].elapsed_time(ev[1]) >= 0.0 and ev[2].elapsed_time(ev[3]) >= 0.0
+    # forgotten after one call: a second call leaves the events as they were
+    call()
+    torch.cuda.synchronize()
+    assert ev[1].elapsed_time(ev[2]) == inner
+    ctx.set_kernel_events(None, None)
+    ctx.check()
