@@ -71,7 +71,8 @@ struct CandMix {
     float k0, k1, k2;   // propagation direction
     float u0, u1, u2;   // polarisation basis
     float v0, v1, v2;
-    float gpr, gxr, gpi, gxi;   // G = (gpr F+ + gxr Fx) + i (gpi F+ + gxi Fx), unit amplitude
+    float gpr, gxr2, gpi, gxi2;   // G = (gpr F+ + gxr Fx) + i (gpi F+ + gxi Fx), unit amplitude, with
+                                  // gxr2 = 2 gxr and gxi2 = 2 gxi (Fx = 2 n.u n.v)
     float f0, fdT, fdh; // Hz, fdot T [Hz], fdot/2 [Hz/s]
     float a0, a1;       // a = f/(2 f*) = a0 + a1 u
     float D0r, D0i;     // exp(-i f0/f*)
@@ -355,9 +356,9 @@ __device__ void setup_mixed(const double* th, double T, double ifs, CandMix& c, 
     const float ci = cosf((float)iota);
     const float Ap = 1.0f + ci * ci, Ax = -2.0f * ci;
     c.gpr = Ap * c2;
-    c.gxr = -Ap * s2;
+    c.gxr2 = 2.0f * (-Ap * s2);
     c.gpi = -Ax * s2;
-    c.gxi = -Ax * c2;
+    c.gxi2 = 2.0f * (-Ax * c2);
     c.f0 = (float)f0;
     c.fdT = (float)(fd * T);
     c.fdh = (float)(0.5 * fd);
@@ -528,8 +529,8 @@ __device__ void slow_part_mixed(const CandMix& c, const OrbitTables32& tab, int 
         for (int arm = 0; arm < 3; ++arm) {
             const float kn = kn_[arm], nu = nu_[arm], nv = nv_[arm];
             const float Fp = (nu - nv) * (nu + nv);
-            const float Fx = 2.0f * nu * nv;
-            const float2 G = make_float2(fmaf(c.gpr, Fp, c.gxr * Fx), fmaf(c.gpi, Fp, c.gxi * Fx));
+            const float Fx1 = nu * nv;   // Fx / 2
+            const float2 G = make_float2(fmaf(c.gpr, Fp, c.gxr2 * Fx1), fmaf(c.gpi, Fp, c.gxi2 * Fx1));
             const int rp = arm == 2 ? 0 : arm + 1;   // receiver of the +n link
             const int rm = arm;                      // receiver of the -n link
             zp[arm] = cmulf(cmulf(link_transfer<J>(a * (1.0f - kn)), G), rx[rp]);
@@ -634,13 +635,31 @@ __device__ __forceinline__ cpair plink_transfer(f2 X) {
         return cpair{make_float2(a.x, b.x), make_float2(a.y, b.y)};
     } else {
         const f2 x2 = pmul(X, X);
-        const float4 cJ = kLinkPairS[J];
-        f2 re = make_float2(cJ.x, cJ.y), im = make_float2(cJ.z, cJ.w);
+        f2 re, im;
+        if constexpr (J <= 4) {
+            // the same coefficients as literals (measured faster for the
+            // short series, slower for the longer ones)
+            constexpr float cre[5] = {1.000000000e+00f, -6.666666865e-01f, 1.333333403e-01f, -1.269841287e-02f,
+                                      7.054673624e-04f};
+            constexpr float cim[5] = {-1.000000000e+00f, 3.333333433e-01f, -4.444444552e-02f, 3.174603218e-03f,
+                                      -1.410934783e-04f};
+            re = bc(cre[J]);
+            im = bc(cim[J]);
 #pragma unroll
-        for (int j = J - 1; j >= 0; --j) {
-            const float4 cj = kLinkPairS[j];
-            re = pfma(re, x2, make_float2(cj.x, cj.y));
-            im = pfma(im, x2, make_float2(cj.z, cj.w));
+            for (int j = J - 1; j >= 0; --j) {
+                re = pfma(re, x2, bc(cre[j]));
+                im = pfma(im, x2, bc(cim[j]));
+            }
+        } else {
+            const float4 cJ = kLinkPairS[J];
+            re = make_float2(cJ.x, cJ.y);
+            im = make_float2(cJ.z, cJ.w);
+#pragma unroll
+            for (int j = J - 1; j >= 0; --j) {
+                const float4 cj = kLinkPairS[j];
+                re = pfma(re, x2, make_float2(cj.x, cj.y));
+                im = pfma(im, x2, make_float2(cj.z, cj.w));
+            }
         }
         return cpair{re, pmul(X, im)};
     }
@@ -743,6 +762,8 @@ __device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N
     PhaseRec rec(c, N, lane);
     for (int r = 0; r < R; r += 2) {
         const int m = (r >> 1) * 32 + lane;
+        const int n = lane + 32 * r;
+        const f2 u = pmul(make_float2((float)n, (float)(n + 32)), bc(invN));
         float4 t[8];
 #pragma unroll
         for (int f = 0; f < 8; ++f) t[f] = __ldg(tab.gp + f * H + m);
@@ -756,8 +777,6 @@ __device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N
         const f2 cah = make_float2(t[6].x, t[6].y), sah = make_float2(t[6].z, t[6].w);
         const int cqa = __float_as_int(t[7].x), cqb = __float_as_int(t[7].y);
         const int sqa = __float_as_int(t[7].z), sqb = __float_as_int(t[7].w);
-        const int n = lane + 32 * r;
-        const f2 u = pmul(make_float2((float)n, (float)(n + 32)), bc(invN));
         // carrier phase modulo one in fixed point (PhaseRec, phase_fix)
         unsigned pa, pb;
         rec.next(pa, pb);
@@ -786,10 +805,10 @@ __device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N
         f2 kn_[3], nu_[3], nv_[3];
         kn_[0] = pfma(bc(c.k0), n0x, pfma(bc(c.k1), n0y, pmul(bc(c.k2), n0z)));
         nu_[0] = pfma(bc(c.u0), n0x, pfma(bc(c.u1), n0y, pmul(bc(c.u2), n0z)));
-        nv_[0] = pfma(bc(c.v0), n0x, pfma(bc(c.v1), n0y, pmul(bc(c.v2), n0z)));
+        nv_[0] = pfma(bc(c.v0), n0x, pmul(bc(c.v1), n0y));   // v has no z component
         kn_[1] = pfma(bc(c.k0), n1x, pfma(bc(c.k1), n1y, pmul(bc(c.k2), n1z)));
         nu_[1] = pfma(bc(c.u0), n1x, pfma(bc(c.u1), n1y, pmul(bc(c.u2), n1z)));
-        nv_[1] = pfma(bc(c.v0), n1x, pfma(bc(c.v1), n1y, pmul(bc(c.v2), n1z)));
+        nv_[1] = pfma(bc(c.v0), n1x, pmul(bc(c.v1), n1y));
         kn_[2] = psub(pneg(kn_[0]), kn_[1]);
         nu_[2] = psub(pneg(nu_[0]), nu_[1]);
         nv_[2] = psub(pneg(nv_[0]), nv_[1]);
@@ -800,8 +819,7 @@ __device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N
             const f2 Fp = pmul(psub(nu, nv), padd(nu, nv));
             // Fx = 2 nu nv with the exact factor 2 on the x coefficients
             const f2 Fx1 = pmul(nu, nv);
-            const cpair G{pfma(bc(c.gpr), Fp, pmul(bc(2.0f * c.gxr), Fx1)),
-                          pfma(bc(c.gpi), Fp, pmul(bc(2.0f * c.gxi), Fx1))};
+            const cpair G{pfma(bc(c.gpr), Fp, pmul(bc(c.gxr2), Fx1)), pfma(bc(c.gpi), Fp, pmul(bc(c.gxi2), Fx1))};
             const int rp = arm == 2 ? 0 : arm + 1;
             const int rm = arm;
             zp[arm] = pcmul(pcmul(plink_transfer<J>(pmul(a, psub(bc(1.0f), kn))), G), rx[rp]);
@@ -816,8 +834,9 @@ __device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N
         const f2 sa2 = pmul(pmul(bc(-2.0f), a), D.im);
         const cpair F = pcmul(cpair{pmul(sa2, D.re), pmul(sa2, D.im)}, ePc);
         const cpair Ap{pmul(psub(Zp.re, Xp.re), r2), pmul(psub(Zp.im, Xp.im), r2)};
-        const cpair Ep{pmul(padd(psub(Xp.re, pmul(bc(2.0f), Yp.re)), Zp.re), r6),
-                       pmul(padd(psub(Xp.im, pmul(bc(2.0f), Yp.im)), Zp.im), r6)};
+        // X - 2Y in one fused operation (2Y is exact)
+        const cpair Ep{pmul(padd(pfma(bc(-2.0f), Yp.re, Xp.re), Zp.re), r6),
+                       pmul(padd(pfma(bc(-2.0f), Yp.im, Xp.im), Zp.im), r6)};
         const cpair oA = pcmul(F, Ap), oE = pcmul(F, Ep);
         // channel-pair elements (A re, E re, A im, E im) for the transform
         const int p = r * 32 + lane;
