@@ -425,26 +425,28 @@ __device__ __forceinline__ float2 cis_rx(float x) {
         sincospif(2.0f * x, &sn, &cs);
         return make_float2(cs, sn);
     } else {
-        const float t = 6.2831853071795865f * x;
-        const float t2 = t * t;
+        // the Taylor series in x (cycles) with the powers of 2 pi folded into
+        // the coefficients: sin to x^7 and cos to x^6 (J <= 4), one more term
+        // each above
+        const float x2 = x * x;
         float s, co;
         if constexpr (J <= 4) {
-            s = fmaf(t2, -1.9841269841269841e-04f, 8.3333333333333332e-03f);
-            s = fmaf(s, t2, -1.6666666666666666e-01f);
-            s = fmaf(s * t2, t, t);
-            co = fmaf(t2, -1.3888888888888889e-03f, 4.1666666666666664e-02f);
-            co = fmaf(co, t2, -0.5f);
-            co = fmaf(co, t2, 1.0f);
+            s = fmaf(x2, -76.70585975306136f, 81.60524927607504f);
+            s = fmaf(s, x2, -41.341702240399755f);
+            s = fmaf(s, x2, 6.283185307179586f) * x;
+            co = fmaf(x2, -85.45681720669371f, 64.93939402266828f);
+            co = fmaf(co, x2, -19.739208802178716f);
+            co = fmaf(co, x2, 1.0f);
         } else {
-            s = fmaf(t2, 2.7557319223985893e-06f, -1.9841269841269841e-04f);
-            s = fmaf(s, t2, 8.3333333333333332e-03f);
-            s = fmaf(s, t2, -1.6666666666666666e-01f);
-            s = fmaf(s * t2, t, t);
-            co = fmaf(t2, -2.7557319223985888e-07f, 2.4801587301587302e-05f);
-            co = fmaf(co, t2, -1.3888888888888889e-03f);
-            co = fmaf(co, t2, 4.1666666666666664e-02f);
-            co = fmaf(co, t2, -0.5f);
-            co = fmaf(co, t2, 1.0f);
+            s = fmaf(x2, 42.058693944897634f, -76.70585975306136f);
+            s = fmaf(s, x2, 81.60524927607504f);
+            s = fmaf(s, x2, -41.341702240399755f);
+            s = fmaf(s, x2, 6.283185307179586f) * x;
+            co = fmaf(x2, -26.426256783374388f, 60.24464137187664f);
+            co = fmaf(co, x2, -85.45681720669371f);
+            co = fmaf(co, x2, 64.93939402266828f);
+            co = fmaf(co, x2, -19.739208802178716f);
+            co = fmaf(co, x2, 1.0f);
         }
         return make_float2(co, s);
     }
@@ -517,10 +519,10 @@ __device__ void slow_part_mixed(const CandMix& c, const OrbitTables32& tab, int 
         float kn_[3], nu_[3], nv_[3];
         kn_[0] = fmaf(c.k0, g1.z, fmaf(c.k1, g1.w, c.k2 * g2.x));
         nu_[0] = fmaf(c.u0, g1.z, fmaf(c.u1, g1.w, c.u2 * g2.x));
-        nv_[0] = fmaf(c.v0, g1.z, fmaf(c.v1, g1.w, c.v2 * g2.x));
+        nv_[0] = fmaf(c.v0, g1.z, c.v1 * g1.w);   // v has no z component
         kn_[1] = fmaf(c.k0, g2.y, fmaf(c.k1, g2.z, c.k2 * g2.w));
         nu_[1] = fmaf(c.u0, g2.y, fmaf(c.u1, g2.z, c.u2 * g2.w));
-        nv_[1] = fmaf(c.v0, g2.y, fmaf(c.v1, g2.z, c.v2 * g2.w));
+        nv_[1] = fmaf(c.v0, g2.y, c.v1 * g2.z);
         kn_[2] = -kn_[0] - kn_[1];
         nu_[2] = -nu_[0] - nu_[1];
         nv_[2] = -nv_[0] - nv_[1];
@@ -533,8 +535,8 @@ __device__ void slow_part_mixed(const CandMix& c, const OrbitTables32& tab, int 
             const float2 G = make_float2(fmaf(c.gpr, Fp, c.gxr2 * Fx1), fmaf(c.gpi, Fp, c.gxi2 * Fx1));
             const int rp = arm == 2 ? 0 : arm + 1;   // receiver of the +n link
             const int rm = arm;                      // receiver of the -n link
-            zp[arm] = cmulf(cmulf(link_transfer<J>(a * (1.0f - kn)), G), rx[rp]);
-            zm[arm] = cmulf(cmulf(link_transfer<J>(a * (1.0f + kn)), G), rx[rm]);
+            zp[arm] = cmulf(cmulf(link_transfer<J>(fmaf(-a, kn, a)), G), rx[rp]);   // a (1 - kn)
+            zm[arm] = cmulf(cmulf(link_transfer<J>(fmaf(a, kn, a)), G), rx[rm]);    // a (1 + kn)
         }
         // links: z01 = zp[0], z10 = zm[0], z12 = zp[1], z21 = zm[1], z20 = zp[2], z02 = zm[2]
         const float du = c.eps * u;
@@ -672,26 +674,29 @@ __device__ __forceinline__ cpair pcis_rx(f2 x) {
         const float2 a = cis_rx<J>(x.x), b = cis_rx<J>(x.y);
         return cpair{make_float2(a.x, b.x), make_float2(a.y, b.y)};
     } else {
-        const f2 t = pmul(bc(6.2831853071795865f), x);
-        const f2 t2 = pmul(t, t);
         f2 s, co;
         if constexpr (J <= 4) {
-            s = pfma(t2, bc(-1.9841269841269841e-04f), bc(8.3333333333333332e-03f));
-            s = pfma(s, t2, bc(-1.6666666666666666e-01f));
-            s = pfma(pmul(s, t2), t, t);
-            co = pfma(t2, bc(-1.3888888888888889e-03f), bc(4.1666666666666664e-02f));
-            co = pfma(co, t2, bc(-0.5f));
-            co = pfma(co, t2, bc(1.0f));
+            // the Taylor series in x (cycles) with the powers of 2 pi folded
+            // into the coefficients: sin to x^7, cos to x^6
+            const f2 x2 = pmul(x, x);
+            s = pfma(x2, bc(-76.70585975306136f), bc(81.60524927607504f));
+            s = pfma(s, x2, bc(-41.341702240399755f));
+            s = pmul(pfma(s, x2, bc(6.283185307179586f)), x);
+            co = pfma(x2, bc(-85.45681720669371f), bc(64.93939402266828f));
+            co = pfma(co, x2, bc(-19.739208802178716f));
+            co = pfma(co, x2, bc(1.0f));
         } else {
-            s = pfma(t2, bc(2.7557319223985893e-06f), bc(-1.9841269841269841e-04f));
-            s = pfma(s, t2, bc(8.3333333333333332e-03f));
-            s = pfma(s, t2, bc(-1.6666666666666666e-01f));
-            s = pfma(pmul(s, t2), t, t);
-            co = pfma(t2, bc(-2.7557319223985888e-07f), bc(2.4801587301587302e-05f));
-            co = pfma(co, t2, bc(-1.3888888888888889e-03f));
-            co = pfma(co, t2, bc(4.1666666666666664e-02f));
-            co = pfma(co, t2, bc(-0.5f));
-            co = pfma(co, t2, bc(1.0f));
+            // the same with one more term each: sin to x^9, cos to x^10
+            const f2 x2 = pmul(x, x);
+            s = pfma(x2, bc(42.058693944897634f), bc(-76.70585975306136f));
+            s = pfma(s, x2, bc(81.60524927607504f));
+            s = pfma(s, x2, bc(-41.341702240399755f));
+            s = pmul(pfma(s, x2, bc(6.283185307179586f)), x);
+            co = pfma(x2, bc(-26.426256783374388f), bc(60.24464137187664f));
+            co = pfma(co, x2, bc(-85.45681720669371f));
+            co = pfma(co, x2, bc(64.93939402266828f));
+            co = pfma(co, x2, bc(-19.739208802178716f));
+            co = pfma(co, x2, bc(1.0f));
         }
         return cpair{co, s};
     }
@@ -822,8 +827,8 @@ __device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N
             const cpair G{pfma(bc(c.gpr), Fp, pmul(bc(c.gxr2), Fx1)), pfma(bc(c.gpi), Fp, pmul(bc(c.gxi2), Fx1))};
             const int rp = arm == 2 ? 0 : arm + 1;
             const int rm = arm;
-            zp[arm] = pcmul(pcmul(plink_transfer<J>(pmul(a, psub(bc(1.0f), kn))), G), rx[rp]);
-            zm[arm] = pcmul(pcmul(plink_transfer<J>(pmul(a, padd(bc(1.0f), kn))), G), rx[rm]);
+            zp[arm] = pcmul(pcmul(plink_transfer<J>(pfma(pneg(a), kn, a)), G), rx[rp]);   // a (1 - kn)
+            zm[arm] = pcmul(pcmul(plink_transfer<J>(pfma(a, kn, a)), G), rx[rm]);         // a (1 + kn)
         }
         const f2 du = pmul(bc(c.eps), u);
         const cpair Dc{pfma(pmul(bc(-0.5f), du), du, bc(1.0f)), pneg(du)};
