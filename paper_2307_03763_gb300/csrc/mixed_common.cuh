@@ -507,13 +507,12 @@ __device__ void slow_part_mixed(const CandMix& c, const OrbitTables32& tab, int 
         krho[0] = fmaf(c.k0, g0.x, fmaf(c.k1, g0.y, c.k2 * g0.z));
         krho[1] = fmaf(c.k0, g0.w, fmaf(c.k1, g1.x, c.k2 * g1.y));
         krho[2] = -krho[0] - krho[1];
+        // dP_j = -f k.rho_j + (fdot/2) (K + k.rho_j)^2 as a quadratic in k.rho_j
+        const float q1 = fmaf(2.0f * c.fdh, K, -f), q0 = c.fdh * K * K;
         float2 rx[3];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const float kap = K + krho[j];
-            const float dP = fmaf(-f, krho[j], c.fdh * kap * kap);
-            rx[j] = cis_rx<J>(dP);   // the common factor exp(2 pi i P_c) is applied once, below
-        }
+        for (int j = 0; j < 3; ++j)   // the common factor exp(2 pi i P_c) is applied once, below
+            rx[j] = cis_rx<J>(fmaf(fmaf(c.fdh, krho[j], q1), krho[j], q0));
         const float a = fmaf(c.a1, u, c.a0);
         // projections of the arms on k, u, v; arm 2->0 closes the triangle
         float kn_[3], nu_[3], nv_[3];
@@ -530,7 +529,7 @@ __device__ void slow_part_mixed(const CandMix& c, const OrbitTables32& tab, int 
 #pragma unroll
         for (int arm = 0; arm < 3; ++arm) {
             const float kn = kn_[arm], nu = nu_[arm], nv = nv_[arm];
-            const float Fp = (nu - nv) * (nu + nv);
+            const float Fp = fmaf(nu, nu, -(nv * nv));
             const float Fx1 = nu * nv;   // Fx / 2
             const float2 G = make_float2(fmaf(c.gpr, Fp, c.gxr2 * Fx1), fmaf(c.gpi, Fp, c.gxi2 * Fx1));
             const int rp = arm == 2 ? 0 : arm + 1;   // receiver of the +n link
@@ -748,8 +747,11 @@ __device__ __forceinline__ void phase_fix(const CandMix& c, unsigned pa, unsigne
                               __uint_as_float(0x4B000000u | (pb & 0xFFFu)));
     const f2 Ph = pfma(xh, bc(0x1p-20f), bc(-12.0f));     // in [-1/2, 1/2)
     const f2 Pt = pfma(xl, bc(0x1p-32f), bc(-0x1p-9f));   // in [0, 2^-20)
-    f2 e;
-    ptwo_sum(Ph, small, Pc, e);
+    // Ph + small with its exact rounding error by Fast2Sum: Ph is a multiple
+    // of 2^-20 and so of ulp(small) (|small| < 8), so Ph + small - RN(...) is
+    // exact whichever is larger; the result is TwoSum's
+    Pc = padd(Ph, small);
+    const f2 e = psub(small, psub(Pc, Ph));
     Pl = padd(Pt, e);
 }
 
@@ -799,13 +801,13 @@ __device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N
         krho[0] = pfma(bc(c.k0), rho0x, pfma(bc(c.k1), rho0y, pmul(bc(c.k2), rho0z)));
         krho[1] = pfma(bc(c.k0), rho1x, pfma(bc(c.k1), rho1y, pmul(bc(c.k2), rho1z)));
         krho[2] = psub(pneg(krho[0]), krho[1]);
+        // dP_j = -f k.rho_j + (fdot/2) (K + k.rho_j)^2 as a quadratic in
+        // k.rho_j: ((fdot/2) k.rho_j + fdot K - f) k.rho_j + (fdot/2) K^2
+        const f2 g1 = pfma(bc(2.0f * c.fdh), K, pneg(fr));
+        const f2 g0 = pmul(pmul(bc(c.fdh), K), K);
         cpair rx[3];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const f2 kap = padd(K, krho[j]);
-            const f2 dP = pfma(pneg(fr), krho[j], pmul(pmul(bc(c.fdh), kap), kap));
-            rx[j] = pcis_rx<J>(dP);
-        }
+        for (int j = 0; j < 3; ++j) rx[j] = pcis_rx<J>(pfma(pfma(bc(c.fdh), krho[j], g1), krho[j], g0));
         const f2 a = pfma(bc(c.a1), u, bc(c.a0));
         f2 kn_[3], nu_[3], nv_[3];
         kn_[0] = pfma(bc(c.k0), n0x, pfma(bc(c.k1), n0y, pmul(bc(c.k2), n0z)));
@@ -821,7 +823,7 @@ __device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N
 #pragma unroll
         for (int arm = 0; arm < 3; ++arm) {
             const f2 kn = kn_[arm], nu = nu_[arm], nv = nv_[arm];
-            const f2 Fp = pmul(psub(nu, nv), padd(nu, nv));
+            const f2 Fp = pfma(nu, nu, pneg(pmul(nv, nv)));
             // Fx = 2 nu nv with the exact factor 2 on the x coefficients
             const f2 Fx1 = pmul(nu, nv);
             const cpair G{pfma(bc(c.gpr), Fp, pmul(bc(c.gxr2), Fx1)), pfma(bc(c.gpi), Fp, pmul(bc(c.gxi2), Fx1))};
