@@ -377,7 +377,11 @@ __device__ void setup_mixed(const double* th, double T, double ifs, CandMix& c, 
     c.K1 = (unsigned long long)__double2ll_rn(dr * 0x1p54);
     c.K2 = (unsigned long long)__double2ll_rn(c2r * 0x1p44);
     const double Fc = f0 * Kc, Fs = f0 * Ks;
-    c.wide = !(fabs(Fc) < 31.0 && fabs(Fs) < 31.0 && fabs(c2r) < 0x1p19 && fabs(dr) < 512.0);
+    // the paired slow part also drops (fdot/2) (k.rho)^2 from the receiver
+    // phases: below 2^-32 cycles while |fdot| (L/c)^2 / 6 is, with
+    // |k.rho| <= L/(sqrt3 c) and L/c = 1/(2 pi f*)
+    const bool fd_ok = fabs(fd) * (ifs * ifs) < 0x1p-32 * 24.0 * kPi * kPi;
+    c.wide = !(fabs(Fc) < 31.0 && fabs(Fs) < 31.0 && fabs(c2r) < 0x1p19 && fabs(dr) < 512.0 && fd_ok);
     c.Fc = c.wide ? 0 : __double2int_rn(Fc * 0x1p26);
     c.Fs = c.wide ? 0 : __double2int_rn(Fs * 0x1p26);
     if (dw || c.wide) {
@@ -734,11 +738,11 @@ struct PhaseRec {
 };
 
 // The common phase P_c = Pc + Pl of a sample pair (Pc in [-1/2, 1/2] up to
-// small, |Pl| < 2^-19): the recurrence's top words pa, pb minus
+// small, |Pl| < 2^-19; returned as Pc and 2 pi Pl): the recurrence's top words pa, pb minus
 // f0 (Kc cos a + Ks sin a), modulo one in 32 bits, split into its top 20
 // and low 12 bits (both exact in float), plus small = -fdot T u K in float
 __device__ __forceinline__ void phase_fix(const CandMix& c, unsigned pa, unsigned pb, int cqa, int sqa, int cqb,
-                                          int sqb, f2 small, f2& Pc, f2& Pl) {
+                                          int sqb, f2 small, f2& Pc, f2& tl) {
     pa -= dop_fix(c, cqa, sqa);
     pb -= dop_fix(c, cqb, sqb);
     const f2 xh = make_float2(__int_as_float(0x4B400000 + ((int)pa >> 12)),
@@ -746,13 +750,14 @@ __device__ __forceinline__ void phase_fix(const CandMix& c, unsigned pa, unsigne
     const f2 xl = make_float2(__uint_as_float(0x4B000000u | (pa & 0xFFFu)),
                               __uint_as_float(0x4B000000u | (pb & 0xFFFu)));
     const f2 Ph = pfma(xh, bc(0x1p-20f), bc(-12.0f));     // in [-1/2, 1/2)
-    const f2 Pt = pfma(xl, bc(0x1p-32f), bc(-0x1p-9f));   // in [0, 2^-20)
+    // 2 pi times the low bits' value (in [0, 2^-20) cycles)
+    const f2 Pt = pfma(xl, bc(6.2831853071795865f * 0x1p-32f), bc(-6.2831853071795865f * 0x1p-9f));
     // Ph + small with its exact rounding error by Fast2Sum: Ph is a multiple
     // of 2^-20 and so of ulp(small) (|small| < 8), so Ph + small - RN(...) is
     // exact whichever is larger; the result is TwoSum's
     Pc = padd(Ph, small);
     const f2 e = psub(small, psub(Pc, Ph));
-    Pl = padd(Pt, e);
+    tl = pfma(bc(6.2831853071795865f), e, Pt);
 }
 
 // natural sample order (the likelihood kernel's transform), N >= 64; with
@@ -765,7 +770,8 @@ __device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N
                                int lane, float2* bufT) {
     const int R = N >> 5, H = N >> 1;
     const float invN = 1.0f / (float)N;
-    const f2 r2 = bc(0.70710678118654752f), r6 = bc(0.40824829046386302f);
+    // 1/sqrt2, 1/sqrt6 times the factor -2 of F (exact: a power of two)
+    const f2 r2 = bc(-2.0f * 0.70710678118654752f), r6 = bc(-2.0f * 0.40824829046386302f);
     PhaseRec rec(c, N, lane);
     for (int r = 0; r < R; r += 2) {
         const int m = (r >> 1) * 32 + lane;
@@ -788,26 +794,27 @@ __device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N
         unsigned pa, pb;
         rec.next(pa, pb);
         const f2 K = pfma(bc(c.Kc), cah, pmul(bc(c.Ks), sah));
-        f2 Pc, Pl;
-        phase_fix(c, pa, pb, cqa, sqa, cqb, sqb, pmul(pneg(pmul(bc(c.fdT), u)), K), Pc, Pl);
+        f2 Pc, tl;
+        phase_fix(c, pa, pb, cqa, sqa, cqb, sqb, pmul(pneg(pmul(bc(c.fdT), u)), K), Pc, tl);
         float sx, cx, sy, cy;
         sincospif(2.0f * Pc.x, &sx, &cx);
         sincospif(2.0f * Pc.y, &sy, &cy);
         const f2 sP = make_float2(sx, sy), cP = make_float2(cx, cy);
-        const f2 tl = pmul(bc(6.2831853071795865f), Pl);
         const cpair ePc{pfma(pneg(tl), sP, cP), pfma(tl, cP, sP)};
         const f2 fr = pfma(bc(c.fdT), u, bc(c.f0));
         f2 krho[3];
         krho[0] = pfma(bc(c.k0), rho0x, pfma(bc(c.k1), rho0y, pmul(bc(c.k2), rho0z)));
         krho[1] = pfma(bc(c.k0), rho1x, pfma(bc(c.k1), rho1y, pmul(bc(c.k2), rho1z)));
         krho[2] = psub(pneg(krho[0]), krho[1]);
-        // dP_j = -f k.rho_j + (fdot/2) (K + k.rho_j)^2 as a quadratic in
-        // k.rho_j: ((fdot/2) k.rho_j + fdot K - f) k.rho_j + (fdot/2) K^2
+        // dP_j = -f k.rho_j + (fdot/2) (K + k.rho_j)^2 to first order in
+        // k.rho_j: (fdot K - f) k.rho_j + (fdot/2) K^2; the (fdot/2) (k.rho_j)^2
+        // left out is below 2^-32 cycles for every candidate this path takes
+        // (setup_mixed sends the others to the scalar slow part)
         const f2 g1 = pfma(bc(2.0f * c.fdh), K, pneg(fr));
         const f2 g0 = pmul(pmul(bc(c.fdh), K), K);
         cpair rx[3];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) rx[j] = pcis_rx<J>(pfma(pfma(bc(c.fdh), krho[j], g1), krho[j], g0));
+        for (int j = 0; j < 3; ++j) rx[j] = pcis_rx<J>(pfma(g1, krho[j], g0));
         const f2 a = pfma(bc(c.a1), u, bc(c.a0));
         f2 kn_[3], nu_[3], nv_[3];
         kn_[0] = pfma(bc(c.k0), n0x, pfma(bc(c.k1), n0y, pmul(bc(c.k2), n0z)));
@@ -838,8 +845,9 @@ __device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N
         const cpair Xp = pcadd(pcsub(zm[0], zp[2]), pcmul(D, pcsub(zp[0], zm[2])));
         const cpair Yp = pcadd(pcsub(zm[1], zp[0]), pcmul(D, pcsub(zp[1], zm[0])));
         const cpair Zp = pcadd(pcsub(zm[2], zp[1]), pcmul(D, pcsub(zp[2], zm[1])));
-        const f2 sa2 = pmul(pmul(bc(-2.0f), a), D.im);
-        const cpair F = pcmul(cpair{pmul(sa2, D.re), pmul(sa2, D.im)}, ePc);
+        // F / -2 (its -2 is in r2, r6, r3)
+        const f2 sa = pmul(a, D.im);
+        const cpair F = pcmul(cpair{pmul(sa, D.re), pmul(sa, D.im)}, ePc);
         const cpair Ap{pmul(psub(Zp.re, Xp.re), r2), pmul(psub(Zp.im, Xp.im), r2)};
         // X - 2Y in one fused operation (2Y is exact)
         const cpair Ep{pmul(padd(pfma(bc(-2.0f), Yp.re, Xp.re), Zp.re), r6),
@@ -852,7 +860,7 @@ __device__ void slow_part_pair(const CandMix& c, const OrbitTables32& tab, int N
         buf[p + 32] = make_float4(oA.re.y, oE.re.y, oA.im.y, oE.im.y);
         if constexpr (T3) {
             if (bufT) {
-                const f2 r3 = bc(0.57735026918962576f);
+                const f2 r3 = bc(-2.0f * 0.57735026918962576f);
                 const cpair Tp{pmul(padd(padd(Xp.re, Yp.re), Zp.re), r3), pmul(padd(padd(Xp.im, Yp.im), Zp.im), r3)};
                 const cpair oT = pcmul(F, Tp);
                 bufT[p] = make_float2(oT.re.x, oT.im.x);

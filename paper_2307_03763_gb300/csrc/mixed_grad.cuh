@@ -159,12 +159,12 @@ __device__ __forceinline__ void sample_adjoint(const CandGx& g, const OrbitTable
     const f2 cah = make_float2(a3.x, b3.x), cal = make_float2(a3.y, b3.y);
     const f2 sah = make_float2(a3.z, b3.z), sal = make_float2(a3.w, b3.w);
     const f2 K = pfma(bc(c.Kc), cah, pmul(bc(c.Ks), sah));
-    f2 Pc, Pl;
+    f2 Pc, tl;   // the common phase: Pc + tl / (2 pi) cycles
     if (!c.wide) {
         // common phase in fixed point, as in the likelihood kernel (pha, phb:
         // the recurrence's top words for n0, n1)
         const int2 qa = __ldg(tab.gq + n0), qb = __ldg(tab.gq + n1);
-        phase_fix(c, pha, phb, qa.x, qa.y, qb.x, qb.y, pmul(pneg(pmul(bc(c.fdT), u)), K), Pc, Pl);
+        phase_fix(c, pha, phb, qa.x, qa.y, qb.x, qb.y, pmul(pneg(pmul(bc(c.fdT), u)), K), Pc, tl);
     } else {
         // outside the fixed-point ranges: double-word arithmetic
         f2 p1 = pmul(bc(c.c1h), u);
@@ -187,14 +187,15 @@ __device__ __forceinline__ void sample_adjoint(const CandGx& g, const OrbitTable
         s = psub(s, print(s));
         const f2 lo = padd(psub(psub(padd(padd(bc(c.c0l), e1), e2), e3), e4), padd(padd(padd(ea, eb), ec), e));
         const f2 small = pfma(pneg(pmul(bc(c.fdT), u)), K, lo);
+        f2 Pl;
         ptwo_sum(s, small, Pc, Pl);
         Pc = psub(Pc, print(Pc));
+        tl = pmul(bc(6.2831853071795865f), Pl);
     }
     float sx, cx, sy, cy;
     sincospif(2.0f * Pc.x, &sx, &cx);
     sincospif(2.0f * Pc.y, &sy, &cy);
     const f2 sP = make_float2(sx, sy), cP = make_float2(cx, cy);
-    const f2 tl = pmul(bc(6.2831853071795865f), Pl);
     const cpair ePc{pfma(pneg(tl), sP, cP), pfma(tl, cP, sP)};
     const f2 f = pfma(bc(c.fdT), u, bc(c.f0));
     const f2 tu = pmul(bc(Tf), u);
