@@ -58,10 +58,11 @@ extern "C" {
 #define GB_ENOMEM   -4   /* device allocation failed */
 
 #define GB_FP64   0      /* every step in IEEE double */
-#define GB_MIXED  1      /* phase and carrier offset in double-word arithmetic
-                            (>= 44 significant bits), response, FFT and inner
-                            products in float with compensated sums; inputs and
-                            outputs stay double */
+#define GB_MIXED  1      /* carrier phase modulo one cycle in 64-bit fixed point
+                            (double-word float arithmetic for candidates outside
+                            its ranges), per-candidate set-up and carrier offset
+                            in double; response, FFT and inner products in float
+                            with compensated sums; inputs and outputs stay double */
 
 #define GB_N_MIN  32
 #define GB_N_MAX  1024
@@ -185,8 +186,9 @@ int gb_loglik(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win,
  * k0/T_obs is at least f* / 2 sums A, E and T in every inner product
  * (including <d|d>); the others use A and E only.  dT (complex, interleaved)
  * and wT (1/S_T) are laid out like dA and wA (device, n_bins entries, not
- * NULL).  Everything else as gb_loglik.  The mixed path transforms T
- * through the same packed kernel, paired with zero. */
+ * NULL).  Everything else as gb_loglik.  The mixed path transforms T as
+ * one channel pair of T's even and odd samples (an N/2-point transform),
+ * then takes the radix-2 step to T's N bins. */
 int gb_loglik_aet(gb_ctx_t* ctx, int prec, const gb_window_t* win, int32_t n_win,
                   const double* dA, const double* dE, const double* dT, const double* wA, const double* wE,
                   const double* wT, int64_t n_bins, const double* theta, int64_t n_rows,

@@ -22,4 +22,6 @@ kde     reduced box and paired 2-D kernel-density proposals of the annealed
 noise   median-periodogram noise estimate of a segment (Sec. III.C)
 brute   brute-force time-domain simulation of the same physics (no fast/slow
         split, exact delays), used only to pin ``gb`` against the physics
+cpu_fft the oracle's likelihood with a radix-2 FFT in place of the naive DFT,
+        timed as a second CPU baseline (not a checker of the GPU path)
 """
