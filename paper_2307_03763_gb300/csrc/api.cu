@@ -296,7 +296,14 @@ int gb_mh_certified(gb_ctx_t* ctx, const gb_window_t* win, int32_t n_win, const 
     int64_t total = 0;
     int rc = check_windows(ctx, "gb_mh_certified", win, n_win, n_bins, n_rows, &total);
     if (rc != GB_OK) return rc;
-    if (n == 0) return GB_OK;
+    if (n == 0) {
+        // empty chains: nothing to certify, so nothing is pending and no row was re-evaluated
+        if (!pending) return set_error(ctx, GB_EINVAL, "gb_mh_certified: null pointer");
+        cudaError_t e = cudaSetDevice(ctx->device);
+        if (e == cudaSuccess) e = cudaMemsetAsync(pending, 0, sizeof(int32_t), (cudaStream_t)stream);
+        if (e == cudaSuccess && n_exact) e = cudaMemsetAsync(n_exact, 0, sizeof(int32_t) * (size_t)n_win, (cudaStream_t)stream);
+        return e == cudaSuccess ? GB_OK : cuda_error(ctx, e, "gb_mh_certified: outputs");
+    }
     if (!(eps > 0.0) || !(eps < 1e-2)) return set_error(ctx, GB_EINVAL, "gb_mh_certified: eps must be in (0, 1e-2)");
     if (max_iter < 1 || max_iter > 64) return set_error(ctx, GB_EINVAL, "gb_mh_certified: max_iter must be in [1, 64]");
     if (literal != 0 && literal != 1) return set_error(ctx, GB_EINVAL, "gb_mh_certified: literal must be 0 or 1");

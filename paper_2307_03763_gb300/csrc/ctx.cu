@@ -216,7 +216,8 @@ int get_plan(gb_ctx* ctx, int prec, const gb_window_t* win, int32_t n_win, int t
     key = fnv1a(win, sizeof(gb_window_t) * (size_t)n_win, key);
     ctx->clock++;
     for (auto& p : ctx->plans)
-        if (p.key == key && p.prec == prec && p.n_win == n_win) {
+        if (p.key == key && p.prec == prec && p.n_win == n_win && p.tile_cands == tile_cands &&
+            (n_win == 0 || std::memcmp(p.win.data(), win, sizeof(gb_window_t) * (size_t)n_win) == 0)) {
             p.last_use = ctx->clock;
             *out = &p;
             return GB_OK;
@@ -302,6 +303,7 @@ int get_plan(gb_ctx* ctx, int prec, const gb_window_t* win, int32_t n_win, int t
     p.w_max = w_max;
     p.n_large = n_large;
     p.tile_cands = tile_cands;
+    p.win.assign(win, win + n_win);
     p.last_use = ctx->clock;
     cudaError_t e;
     if (n_win > 0) {

@@ -118,6 +118,7 @@ struct Plan {
     long long n_prep = 0;           // total window bins (scratch entries)
     int n_large = 0;                // mixed plans: items with N >= 512 come first
     int tile_cands = 0;             // candidates per work item at most
+    std::vector<gb_window_t> win;   // host copy of the layout: a lookup compares it, not only the hash
     gb_window_t* d_win = nullptr;
     Tile* d_tiles = nullptr;
     // scratch of the mixed-precision path (owned by the plan)

@@ -137,6 +137,26 @@ def test_certified_pending_reports_unfinished_passes(api, posterior):
     assert int(out[6].item()) > 0
 
 
+def test_certified_empty_chains_report_nothing_pending(api, posterior):
+    # windows of zero proposals: no chain to build, so pending and the
+    # re-evaluation counts are written as zero (not left as they were)
+    P = posterior
+    dA, dE, wA, wE, _ = P["args"]
+    wins = [(k0, W, N, doff, 0, 0) for (k0, W, N, doff, coff, nc) in P["wl"].windows[:3]]
+    theta = torch.empty((0, 8), dtype=torch.float64, device=DEV)
+    z = torch.empty((3, 0), dtype=torch.float64, device=DEV)
+    temp = torch.ones(3, dtype=torch.float64, device=DEV)
+    e = lambda: torch.empty(0, dtype=torch.float64, device=DEV)
+    n_exact = torch.full((3,), -7, dtype=torch.int32, device=DEV)
+    pending = torch.full((1,), -7, dtype=torch.int32, device=DEV)
+    out = (torch.empty((3, 0), dtype=torch.int32, device=DEV), torch.zeros(3, dtype=torch.int32, device=DEV),
+           e(), e(), e(), n_exact, pending)
+    P["ctx"].mh_certified(wins, dA, dE, wA, wE, theta, z, z, temp, out=out)
+    torch.cuda.synchronize()
+    assert int(pending.item()) == 0
+    assert torch.equal(n_exact, torch.zeros(3, dtype=torch.int32, device=DEV))
+
+
 def test_loglik_rows_bit_identical_to_loglik(api):
     # ragged windows of every N; listed subsets, partial ranges, entries of
     # another window (skipped), empty lists; unlisted rows untouched
