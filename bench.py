@@ -206,18 +206,33 @@ def flops_per_grad(N, f_hz, T):
     return forward + 2 * 5 * N * math.log2(N) + N * (508 + 48 * J + 555)
 
 
-def kernel_source_sha256():
-    """SHA-256 of the likelihood kernel's code: mixed_common.cuh and mixed.cu up
-    to its allocation-free section, without // comments and blank lines."""
+def source_sha256(sources):
+    """SHA-256 of a kernel's code: the listed files (each up to its optional
+    `until` marker) concatenated, without // comments and blank lines."""
     import hashlib
-    csrc = os.path.join(ROOT, "paper_2307_03763_gb300", "csrc")
-    common = open(os.path.join(csrc, "mixed_common.cuh")).read()
-    src = open(os.path.join(csrc, "mixed.cu")).read()
-    region = common + src.split("// ---------------------------------------------------------------------------\n"
-                                "// Allocation-free variant")[0]
+    region = ""
+    for src in sources:
+        text = open(os.path.join(ROOT, src["path"])).read()
+        if src.get("until"):
+            text = text.split(src["until"])[0]
+        region += text
     region = "\n".join(ln.split("//")[0].rstrip() for ln in region.splitlines())
     region = "\n".join(ln for ln in region.splitlines() if ln.strip())
     return hashlib.sha256(region.encode()).hexdigest()
+
+
+def profiled_traffic(name="loglik_mixed_posterior"):
+    """DRAM bytes per launch of a kernel from its committed ncu counters
+    (profiles/<name>.json: dram__bytes_read.sum + dram__bytes_write.sum of one
+    captured launch), or None when the kernel's code changed since that
+    capture (the hash of the source files the file lists differs)."""
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", name + ".json")))
+        if prof.get("source_sha256") != source_sha256(prof["sources"]):
+            return None
+    except (OSError, ValueError, KeyError):
+        return None
+    return int(prof["traffic_bytes_per_launch"])
 
 
 def flops_per_grad_fp64(N, f_hz, T):
@@ -232,19 +247,6 @@ def flops_per_grad_fp64(N, f_hz, T):
     J = 6 if x <= 0.22 else 8 if x <= 0.5 else 12 if x <= 1.3 else 16
     forward = N * (445 + 24 * J) + 2 * 5 * N * math.log2(N) + 38 * N
     return forward + 2 * 5 * N * math.log2(N) + N * (508 + 48 * J + 555)
-
-
-def profiled_traffic():
-    """DRAM bytes per launch of the likelihood kernel from the committed ncu
-    counters (profiles/loglik_mixed_posterior.json), or None when the kernel's
-    code changed since that capture."""
-    try:
-        prof = json.load(open(os.path.join(ROOT, "profiles", "loglik_mixed_posterior.json")))
-    except (OSError, ValueError):
-        return None
-    if prof.get("source_sha256") != kernel_source_sha256():
-        return None
-    return int(prof["traffic_bytes_per_launch"])
 
 
 def flops_per_eval_fp64(N, f_hz, T):
@@ -505,7 +507,8 @@ def run_workload(args):
         peak = 152 * 128 * 2 * 2070e6 / 1e12
         line["grad_mixed"]["roofline"] = {
             "bound": "alu", "achieved": gflops / (ms_g / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-            "frac": gflops / (ms_g / 1e3) / 1e12 / peak, "traffic": None, "kernel": "grad_mixed_kernel",
+            "frac": gflops / (ms_g / 1e3) / 1e12 / peak, "traffic": profiled_traffic("grad_mixed_population"),
+            "kernel": "grad_mixed_kernel",
             "peak_note": "FP32 FMA peak from unit counts: 152 SM x 128 lanes x 2 x 2070 MHz; the timed call "
                          "is the preparation kernel and the gradient kernel"}
         gflops64 = sum(512 * flops_per_grad_fp64(w[2], f, wl.T) for w, f in zip(wl.windows, f_mid))
@@ -514,7 +517,8 @@ def run_workload(args):
                              "roofline": {"bound": "alu", "achieved": gflops64 / (ms_g64 / 1e3) / 1e12,
                                           "peak": fp64_peak_tflops(), "unit": "TFLOP/s",
                                           "frac": gflops64 / (ms_g64 / 1e3) / 1e12 / fp64_peak_tflops(),
-                                          "traffic": None, "kernel": "grad64_kernel",
+                                          "traffic": profiled_traffic("grad_fp64_population"),
+                                          "kernel": "grad64_kernel",
                                           "peak_note": "FP64 peak from unit counts: 152 SM x 2 FP64 FMA lanes x 2 "
                                                        "x 2070 MHz; achieved counts the reverse-mode work"}}
         boxes = np.array([np.concatenate([wl.theta[c:c + m].min(0), wl.theta[c:c + m].max(0)])
@@ -982,7 +986,8 @@ def main():
         "fp64": {"value": value64, "unit": UNIT, "steps": fp64_steps, "ms_per_step": tot_64 / fp64_steps,
                  "s_per_10k_posterior": tot_64 / fp64_steps / 1e3 / nwin, "loglik_ms": kern_64,
                  "roofline": {"bound": "alu", "achieved": achieved64, "peak": fp64_peak_tflops(),
-                              "unit": "TFLOP/s", "frac": achieved64 / fp64_peak_tflops(), "traffic": None,
+                              "unit": "TFLOP/s", "frac": achieved64 / fp64_peak_tflops(),
+                              "traffic": profiled_traffic("loglik_fp64_posterior"),
                               "kernel": "loglik64_kernel",
                               "peak_note": "FP64 peak from unit counts: 152 SM x 2 FP64 FMA lanes x 2 x 2070 MHz "
                                            "(the nominal 1.25 TFLOP/s dense FP64)"}},
