@@ -503,7 +503,9 @@ int gb_gauss_refit(gb_ctx_t* ctx, int32_t n_win, int32_t n, const double* theta,
  *   dA, dE     complex data (device, interleaved, n_bins entries)
  *   S          n_win x 2 estimates (device, written; NaN for W = 0)
  *   wA, wE     weights (device, may both be NULL): the window's bins are set
- *              to 1/S, the segment's constant noise weight
+ *              to 1/S, the segment's constant noise weight; windows whose
+ *              bins overlap must not ask for weights (each window writes all
+ *              of its bins, so overlapping windows would race)
  * The estimate is re-run after signals are subtracted (the paper's dynamic
  * noise estimate). */
 int gb_noise_median(gb_ctx_t* ctx, const gb_window_t* win, int32_t n_win, const double* dA, const double* dE,
